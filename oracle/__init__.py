@@ -1,0 +1,247 @@
+"""CPU oracle for isotropic Gaussian splatting (arXiv 2403.14244).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
+of the benchmark are the only callers. The product path never imports this
+package, and this package imports nothing from the product path except the
+seeded input generators (``paper_2403_14244_gb300.scenes``), which hold none of
+the method's arithmetic.
+
+The arithmetic lives in ``igs_oracle.c`` (plain C, FP64 compositing and
+gradients, canonical FP32 key path), built here with gcc and loaded with
+ctypes. Every function states the passage of the paper it follows; the readings
+taken where the paper is silent are listed at the top of ``igs_oracle.c``.
+
+Parity pins: every function here is checked by the ``-m "not gpu"`` tests
+against closed forms, brute force, invariants, finite differences, scipy's
+spherical harmonics and torch's Adam / L1 (see tests/test_oracle_*.py).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "igs_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+          "-fPIC", "-shared", "-Wall", "-Wno-unused-function"]
+
+
+def build(force=False):
+    """Compile the oracle with gcc (FP contraction off: the FP32 key path must
+    round every operation exactly once)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrcCamera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("znear", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class OrcOpts(C.Structure):
+    _fields_ = [("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
+                ("bg", C.c_float * 3), ("sh_degree", C.c_int32), ("log_params", C.c_int32),
+                ("proj64", C.c_int32), ("mode", C.c_int32), ("flag_margin", C.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            i64 = C.c_int64
+            lib.orc_num_threads.restype = C.c_int
+            lib.orc_project.argtypes = [i64, P, P, C.POINTER(OrcCamera), C.c_int32, P, P, P, P, P, P]
+            lib.orc_keys.argtypes = [i64, P, P, P, C.c_int32, C.c_int32, C.c_uint32, P, P, P]
+            lib.orc_keys.restype = i64
+            lib.orc_render.argtypes = [i64, P, P, P, C.POINTER(OrcCamera), C.POINTER(OrcOpts), P, P, P, P, P, P]
+            lib.orc_render.restype = i64
+            lib.orc_backward.argtypes = [i64, P, P, P, C.POINTER(OrcCamera), C.POINTER(OrcOpts), P,
+                                         P, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_backward.restype = i64
+            lib.orc_activate.argtypes = [i64, P, i64, P, P, P]
+            lib.orc_sh_basis.argtypes = [C.c_int32, i64, P, P, P]
+            lib.orc_l1.argtypes = [i64, P, P, P]
+            lib.orc_l1.restype = C.c_double
+            lib.orc_adam.argtypes = [i64, P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double, i64]
+            _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _cam(cam) -> OrcCamera:
+    c = OrcCamera()
+    c.R[:] = [float(x) for x in np.asarray(cam.R, np.float32).reshape(9)]
+    c.t[:] = [float(x) for x in np.asarray(cam.t, np.float32).reshape(3)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.znear = cam.znear
+    c.width, c.height = cam.width, cam.height
+    return c
+
+
+def _opts(scene, mode, proj64, bg, alpha_min, alpha_max, t_min, flag_margin) -> OrcOpts:
+    o = OrcOpts()
+    o.alpha_min, o.alpha_max, o.t_min = alpha_min, alpha_max, t_min
+    o.bg[:] = list(bg)
+    o.sh_degree = scene.sh_degree
+    o.log_params = int(scene.log_params)
+    o.proj64 = int(proj64)
+    o.mode = int(mode)
+    o.flag_margin = float(flag_margin)
+    return o
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+# ------------------------------------------------------------ key path ------
+
+def project(means_sigma, opacity, cam, tile):
+    """Canonical FP32 projection (linear sigma/opacity): u, v, s, depth, rect
+    (x0, y0, x1, y1 inclusive tile bounds) and tiles touched (0 = culled).
+    Eq. 7 with Sigma = sigma^2 I; footprint radius 3.33 s (support of Eq. 2)."""
+    ms, op = _c32(means_sigma), _c32(opacity)
+    n = ms.shape[0]
+    out = {k: np.zeros(n, np.float32) for k in ("u", "v", "s", "depth")}
+    rect = np.zeros((n, 4), np.int32)
+    count = np.zeros(n, np.int32)
+    _load().orc_project(n, _ptr(ms), _ptr(op), C.byref(_cam(cam)), int(tile), _ptr(out["u"]),
+                        _ptr(out["v"]), _ptr(out["s"]), _ptr(out["depth"]), _ptr(rect), _ptr(count))
+    out["rect"], out["count"] = rect, count
+    return out
+
+
+def keys(proj, cam, tile, tile_base=0):
+    """Sorted (key, value) pairs and per-tile [start, end) ranges of the
+    depth-ordered tile lists: key = tile << 32 | FP32 depth bits (front-to-back
+    order of Eq. 4 within each tile, ties by Gaussian index)."""
+    tiles_x = (cam.width + tile - 1) // tile
+    tiles_y = (cam.height + tile - 1) // tile
+    m = int(proj["count"].astype(np.int64).sum())
+    k = np.zeros(m, np.uint64)
+    v = np.zeros(m, np.uint32)
+    r = np.zeros((tiles_x * tiles_y, 2), np.uint32)
+    got = _load().orc_keys(proj["count"].shape[0], _ptr(np.ascontiguousarray(proj["rect"])),
+                           _ptr(np.ascontiguousarray(proj["count"])),
+                           _ptr(np.ascontiguousarray(proj["depth"])), tiles_x, tiles_y, int(tile_base),
+                           _ptr(k), _ptr(v), _ptr(r))
+    assert got == m
+    return k, v, r
+
+
+def activate(log_sigma, logit):
+    """sigma = exp(log sigma), opacity = sigmoid(logit), in FP64 then rounded
+    once to FP32 (the 4 kernel parameters of Sec. 2.1 kept unconstrained)."""
+    ls, lg = _c32(log_sigma), _c32(logit)
+    n = ls.shape[0]
+    s = np.zeros(n, np.float32)
+    o = np.zeros(n, np.float32)
+    _load().orc_activate(n, _ptr(ls), 1, _ptr(lg), _ptr(s), _ptr(o))
+    return s, o
+
+
+def sh_basis(deg, dirs):
+    """Real orthonormal SH basis (no Condon-Shortley phase) up to ``deg`` at unit
+    directions [n, 3] (FP64), with gradients of the polynomial extension."""
+    d = np.ascontiguousarray(dirs, np.float64)
+    n = d.shape[0]
+    K = (deg + 1) ** 2
+    Y = np.zeros((n, K))
+    dY = np.zeros((n, K, 3))
+    _load().orc_sh_basis(int(deg), n, _ptr(d), _ptr(Y), _ptr(dY))
+    return Y, dY
+
+
+# ----------------------------------------------------------- compositing ----
+
+DEFAULTS = dict(bg=(0.0, 0.0, 0.0), alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4)
+
+
+def render(scene, cam, *, mode=1, proj64=False, flag_margin=1e-5, bg=(0.0, 0.0, 0.0),
+           alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4):
+    """FP64 front-to-back compositing (Eq. 4) of every visible Gaussian at every
+    pixel centre, with no tiling. Returns img [3,H,W], T [H,W], nb [H,W] (entries
+    blended), last [H,W] (index of the last blended Gaussian, -1 if none),
+    flag [H,W] (a cutoff or stop decision within ``flag_margin`` relative of its
+    threshold) and hash [H,W] (digest of the decision sequence)."""
+    ms, op, col = _c32(scene.means_sigma), _c32(scene.opacity), _c32(scene.color)
+    H, W = cam.height, cam.width
+    img = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    nb = np.zeros((H, W), np.int32)
+    last = np.zeros((H, W), np.int32)
+    flag = np.zeros((H, W), np.uint8)
+    hsh = np.zeros((H, W), np.uint64)
+    o = _opts(scene, mode, proj64, bg, alpha_min, alpha_max, t_min, flag_margin)
+    nv = _load().orc_render(scene.n, _ptr(ms), _ptr(op), _ptr(col), C.byref(_cam(cam)), C.byref(o),
+                            _ptr(img), _ptr(T), _ptr(nb), _ptr(last), _ptr(flag), _ptr(hsh))
+    return dict(img=img, T=T, nb=nb, last=last, flag=flag, hash=hsh, n_visible=int(nv))
+
+
+def backward(scene, cam, dL_dimg, *, mode=1, proj64=False, flag_margin=1e-5, bg=(0.0, 0.0, 0.0),
+             alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4):
+    """Forward plus adjoint (Eq. 3 and the position gradient after it, through
+    Eq. 4, Eq. 8 and the projection). Gradients are w.r.t. the stored
+    parameters: sigma or log sigma, opacity or its logit, RGB or SH."""
+    ms, op, col = _c32(scene.means_sigma), _c32(scene.opacity), _c32(scene.color)
+    n = scene.n
+    H, W = cam.height, cam.width
+    G = np.ascontiguousarray(dL_dimg, np.float64).reshape(3, H, W)
+    out = dict(d_means=np.zeros((n, 3)), d_sigma=np.zeros(n), d_opac=np.zeros(n),
+               d_color=np.zeros(col.shape), g2d=np.zeros((n, 7)),
+               img=np.zeros((3, H, W)), T=np.zeros((H, W)), nb=np.zeros((H, W), np.int32),
+               last=np.zeros((H, W), np.int32), flag=np.zeros((H, W), np.uint8),
+               hash=np.zeros((H, W), np.uint64))
+    o = _opts(scene, mode, proj64, bg, alpha_min, alpha_max, t_min, flag_margin)
+    nv = _load().orc_backward(n, _ptr(ms), _ptr(op), _ptr(col), C.byref(_cam(cam)), C.byref(o), _ptr(G),
+                              _ptr(out["d_means"]), _ptr(out["d_sigma"]), _ptr(out["d_opac"]),
+                              _ptr(out["d_color"]), _ptr(out["g2d"]), _ptr(out["img"]), _ptr(out["T"]),
+                              _ptr(out["nb"]), _ptr(out["last"]), _ptr(out["flag"]), _ptr(out["hash"]))
+    out["n_visible"] = int(nv)
+    return out
+
+
+# ------------------------------------------------------------ loss, Adam ----
+
+def l1(img, target):
+    """Mean absolute error over all 3 H W entries and its gradient (the L1 term
+    of the loss of Sec. 3, with lambda = 0)."""
+    im = np.ascontiguousarray(img, np.float64)
+    tg = _c32(target)
+    grad = np.zeros(im.shape)
+    loss = _load().orc_l1(im.size, _ptr(im), _ptr(tg), _ptr(grad))
+    return float(loss), grad
+
+
+def adam(p, grad, m, v, *, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, t=1):
+    """One bias-corrected Adam step in FP64, in place on copies; returns (p, m, v)."""
+    p = np.array(p, np.float64, copy=True)
+    m = np.array(m, np.float64, copy=True)
+    v = np.array(v, np.float64, copy=True)
+    g = np.ascontiguousarray(grad, np.float64)
+    _load().orc_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), lr, b1, b2, eps, int(t))
+    return p, m, v

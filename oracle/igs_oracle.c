@@ -1,0 +1,663 @@
+/*
+ * CPU oracle for isotropic Gaussian splatting (arXiv 2403.14244).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path may call, link or
+ * load this file: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do. It shares no code, header, table or constant with the
+ * CUDA path; the only thing the two sides share is the seeded input
+ * generator, which holds none of the method's arithmetic.
+ *
+ * What it computes, and where the paper states it:
+ *   - isotropic kernel g = exp(-|x - mu|^2 / (2 s^2))          Eq. 8 (reading: the
+ *     paper writes sigma^2 in the denominator; with s = sigma/sqrt(2) the two agree)
+ *   - projection of an isotropic Gaussian to a screen disc      Eq. 7 with Sigma = sigma^2 I,
+ *     radius s = f sigma / z_c, "size only depends on the distance to the view
+ *     point" (Sec. 2.4); centre u = fx x_c/z_c + cx, v = fy y_c/z_c + cy
+ *   - front-to-back alpha compositing                           Eq. 4
+ *     C = sum_k c_k a_k prod_{j<k} (1 - a_j), a_k = min(0.99, o_k g_k),
+ *     entries with a_k < 1/255 skipped, stop before the entry that would take
+ *     the transmittance below 1e-4, background added with the final T
+ *   - compact support of each particle                           Eq. 2 (support D):
+ *     footprint radius r = 3.33 s, so o exp(-r^2/(2 s^2)) < 1/255 for o <= 1
+ *   - gradients of the loss w.r.t. every particle parameter      Eq. 3 and the
+ *     position gradient that follows it, by the chain rule through Eq. 4, Eq. 8
+ *     and the projection
+ *   - colour as real spherical harmonics up to degree 3 (the particle property
+ *     A_k of Sec. 3, view dependent)
+ *
+ * Two arithmetics:
+ *   - the key path (culling, tile rectangle, depth key) is canonical FP32 with
+ *     every operation rounded once, in a fixed order (compile with
+ *     -ffp-contract=off), so that keys and tile ranges can be compared bit for bit;
+ *   - compositing and gradients are FP64. With proj64 = 0 the disc (u, v, s) is
+ *     the canonical FP32 value widened to FP64; with proj64 = 1 it is computed in
+ *     FP64 from the inputs (used for finite differences).
+ *
+ * Two traversal modes give bit-identical results, because each pixel sees the
+ * same Gaussians in the same order with the same arithmetic:
+ *   mode 0 "literal": every pixel walks every visible Gaussian, front to back;
+ *   mode 1 "lists":   each image row walks only the Gaussians whose support
+ *                     reaches the row, still front to back.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    float R[9];          /* world -> camera rotation, row-major */
+    float t[3];          /* x_c = R x_w + t */
+    float fx, fy, cx, cy;
+    float znear;
+    int32_t width, height;
+} orc_camera;
+
+typedef struct {
+    float alpha_min;     /* 1/255 */
+    float alpha_max;     /* 0.99 */
+    float t_min;         /* 1e-4 */
+    float bg[3];
+    int32_t sh_degree;   /* -1: RGB, 0..3: SH */
+    int32_t log_params;  /* 1: sigma column is log sigma, opacity is a logit */
+    int32_t proj64;      /* 1: disc in FP64 from the inputs */
+    int32_t mode;        /* 0 literal, 1 lists */
+    double flag_margin;  /* relative margin for near-threshold decisions */
+} orc_opts;
+
+#define ORC_RADIUS_K 3.33f
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static uint32_t f32_bits(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+
+/* ------------------------------------------------------------ activation -- */
+/* sigma = exp(log sigma), o = 1/(1+exp(-logit)); FP64, rounded once to FP32. */
+void orc_activate(int64_t n, const float* log_sigma, int64_t ls_stride, const float* logit,
+                  float* sigma_out, float* opac_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        double l = (double)log_sigma[i * ls_stride];
+        sigma_out[i] = (float)exp(l);
+        opac_out[i] = (float)(1.0 / (1.0 + exp(-(double)logit[i])));
+    }
+}
+
+/* ------------------------------------------------------ FP32 key path ----- */
+/* Canonical FP32 projection of one Gaussian. Returns 1 if it is kept.
+ * Culled when: an input is not finite, sigma <= 0, z_c <= znear,
+ * o < 1/255 (no pixel could reach the alpha cutoff), or the tile rectangle
+ * of [u-r, u+r] x [v-r, v+r] misses the tile grid. */
+static int key_path_one(const orc_camera* c, int tile, int tiles_x, int tiles_y,
+                        float mx, float my, float mz, float sg, float o,
+                        float* pu, float* pv, float* ps, float* pz, int32_t rect[4]) {
+    if (!(isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(sg) && isfinite(o)))
+        return 0;
+    float xc = ((c->R[0] * mx + c->R[1] * my) + c->R[2] * mz) + c->t[0];
+    float yc = ((c->R[3] * mx + c->R[4] * my) + c->R[5] * mz) + c->t[1];
+    float zc = ((c->R[6] * mx + c->R[7] * my) + c->R[8] * mz) + c->t[2];
+    if (!(zc > c->znear)) return 0;
+    if (!(sg > 0.0f)) return 0;
+    if (!(o >= 1.0f / 255.0f)) return 0;
+    float s = (c->fx * sg) / zc;
+    float u = (c->fx * xc) / zc + c->cx;
+    float v = (c->fy * yc) / zc + c->cy;
+    float r = ORC_RADIUS_K * s;
+    if (!(isfinite(u) && isfinite(v) && isfinite(r))) return 0;
+    float ts = (float)tile;
+    float fx0 = floorf((u - r) / ts), fx1 = floorf((u + r) / ts);
+    float fy0 = floorf((v - r) / ts), fy1 = floorf((v + r) / ts);
+    if (fx1 < 0.0f || fx0 > (float)(tiles_x - 1) || fy1 < 0.0f || fy0 > (float)(tiles_y - 1))
+        return 0;
+    rect[0] = (int32_t)fmaxf(fx0, 0.0f);
+    rect[1] = (int32_t)fmaxf(fy0, 0.0f);
+    rect[2] = (int32_t)fminf(fx1, (float)(tiles_x - 1));
+    rect[3] = (int32_t)fminf(fy1, (float)(tiles_y - 1));
+    *pu = u; *pv = v; *ps = s; *pz = zc;
+    return 1;
+}
+
+/* Per-Gaussian canonical projection (linear sigma and opacity given in FP32).
+ * rect = (x0, y0, x1, y1) inclusive tile bounds; count = tiles touched (0 if culled). */
+void orc_project(int64_t n, const float* means_sigma, const float* opacity, const orc_camera* cam,
+                 int32_t tile, float* u, float* v, float* s, float* depth, int32_t* rect, int32_t* count) {
+    int tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
+    for (int64_t i = 0; i < n; ++i) {
+        const float* m = means_sigma + 4 * i;
+        int32_t rc[4] = {0, 0, -1, -1};
+        float uu = 0, vv = 0, ss = 0, zz = 0;
+        int keep = key_path_one(cam, tile, tiles_x, tiles_y, m[0], m[1], m[2], m[3], opacity[i],
+                                &uu, &vv, &ss, &zz, rc);
+        u[i] = uu; v[i] = vv; s[i] = ss; depth[i] = zz;
+        memcpy(rect + 4 * i, rc, sizeof rc);
+        count[i] = keep ? (rc[2] - rc[0] + 1) * (rc[3] - rc[1] + 1) : 0;
+    }
+}
+
+typedef struct { uint64_t key; int64_t pos; uint32_t val; } key_entry;
+
+static int cmp_key_entry(const void* a, const void* b) {
+    const key_entry* x = (const key_entry*)a;
+    const key_entry* y = (const key_entry*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->pos < y->pos ? -1 : (x->pos > y->pos);  /* generation order: a stable sort */
+}
+
+/* Duplicate every kept Gaussian into one (key, value) pair per tile it touches,
+ * key = (tile_base + ty*tiles_x + tx) << 32 | bits(depth), generated in index
+ * order and row-major tile order; sort by key keeping generation order among
+ * equal keys; record for every tile the half-open range [start, end) of its
+ * entries ((0, 0) if it has none). Returns M. */
+int64_t orc_keys(int64_t n, const int32_t* rect, const int32_t* count, const float* depth,
+                 int32_t tiles_x, int32_t tiles_y, uint32_t tile_base,
+                 uint64_t* keys_out, uint32_t* vals_out, uint32_t* ranges_out) {
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) m += count[i];
+    key_entry* e = (key_entry*)malloc(sizeof(key_entry) * (size_t)(m > 0 ? m : 1));
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (count[i] == 0) continue;
+        const int32_t* rc = rect + 4 * i;
+        for (int32_t ty = rc[1]; ty <= rc[3]; ++ty)
+            for (int32_t tx = rc[0]; tx <= rc[2]; ++tx) {
+                uint64_t tid = (uint64_t)tile_base + (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;
+                e[k].key = (tid << 32) | (uint64_t)f32_bits(depth[i]);
+                e[k].pos = k;
+                e[k].val = (uint32_t)i;
+                ++k;
+            }
+    }
+    qsort(e, (size_t)m, sizeof(key_entry), cmp_key_entry);
+    int64_t tiles = (int64_t)tiles_x * tiles_y;
+    if (ranges_out) memset(ranges_out, 0, sizeof(uint32_t) * 2 * (size_t)tiles);
+    for (int64_t j = 0; j < m; ++j) {
+        if (keys_out) keys_out[j] = e[j].key;
+        if (vals_out) vals_out[j] = e[j].val;
+        if (ranges_out) {
+            int64_t t = (int64_t)(e[j].key >> 32) - (int64_t)tile_base;
+            if (j == 0 || (e[j - 1].key >> 32) != (e[j].key >> 32)) ranges_out[2 * t] = (uint32_t)j;
+            ranges_out[2 * t + 1] = (uint32_t)(j + 1);
+        }
+    }
+    free(e);
+    return m;
+}
+
+/* ---------------------------------------------- real spherical harmonics -- */
+/* Real orthonormal SH on the unit sphere, without the Condon-Shortley phase:
+ *   Y_l0  = K_l0 P_l(z)
+ *   Y_lm  = sqrt(2) K_lm P_l^m(z) cos(m phi)        m > 0
+ *   Y_l-m = sqrt(2) K_lm P_l^m(z) sin(m phi)        m > 0
+ * with K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), P_l^m(z) = (1-z^2)^{m/2} d^m P_l/dz^m.
+ * On the sphere (1-z^2)^{m/2} cos(m phi) = Re (x+iy)^m and ... sin = Im (x+iy)^m,
+ * so Y is the polynomial K d^mP_l/dz^m(z) * {Re,Im}(x+iy)^m, evaluated and
+ * differentiated below from the explicit expansion of P_l. Index k = l^2 + l + m. */
+static double fact(int a) { double r = 1; for (int i = 2; i <= a; ++i) r *= i; return r; }
+static double binom(int a, int b) { return fact(a) / (fact(b) * fact(a - b)); }
+
+/* d^m/dz^m of P_l at z, from P_l(z) = 2^-l sum_k (-1)^k C(l,k) C(2l-2k,l) z^(l-2k). */
+static double legendre_deriv(int l, int m, double z) {
+    double acc = 0.0;
+    for (int k = 0; 2 * k <= l; ++k) {
+        int p = l - 2 * k;
+        if (p < m) continue;
+        double coef = ((k & 1) ? -1.0 : 1.0) * binom(l, k) * binom(2 * l - 2 * k, l) / pow(2.0, l);
+        double falling = fact(p) / fact(p - m);
+        acc += coef * falling * pow(z, p - m);
+    }
+    return acc;
+}
+
+/* (x+iy)^m as (re, im); m >= 0. */
+static void cpow_xy(double x, double y, int m, double* re, double* im) {
+    double a = 1.0, b = 0.0;
+    for (int i = 0; i < m; ++i) { double na = a * x - b * y, nb = a * y + b * x; a = na; b = nb; }
+    *re = a; *im = b;
+}
+
+/* Basis values Y[k] and gradients dY[k][3] of the polynomial extension at d. */
+static void sh_basis(int deg, const double d[3], double* Y, double (*dY)[3]) {
+    const double x = d[0], y = d[1], z = d[2];
+    for (int l = 0; l <= deg; ++l) {
+        for (int m = -l; m <= l; ++m) {
+            int am = m < 0 ? -m : m;
+            int k = l * l + l + m;
+            double K = sqrt((2 * l + 1) / (4.0 * M_PI) * fact(l - am) / fact(l + am));
+            if (m != 0) K *= sqrt(2.0);
+            double P = legendre_deriv(l, am, z);
+            double P1 = legendre_deriv(l, am + 1, z);
+            double re, im, re1 = 0, im1 = 0;
+            cpow_xy(x, y, am, &re, &im);
+            if (am > 0) cpow_xy(x, y, am - 1, &re1, &im1);
+            double A, Ax, Ay;
+            if (m >= 0) { A = re; Ax = am * re1; Ay = -am * im1; }
+            else        { A = im; Ax = am * im1; Ay = am * re1; }
+            if (m == 0) { A = 1.0; Ax = 0.0; Ay = 0.0; }
+            Y[k] = K * P * A;
+            if (dY) { dY[k][0] = K * P * Ax; dY[k][1] = K * P * Ay; dY[k][2] = K * P1 * A; }
+        }
+    }
+}
+
+void orc_sh_basis(int32_t deg, int64_t n, const double* dirs, double* Y, double* dY) {
+    int K = (deg + 1) * (deg + 1);
+    for (int64_t i = 0; i < n; ++i)
+        sh_basis(deg, dirs + 3 * i, Y + (size_t)K * i, dY ? (double (*)[3])(dY + (size_t)3 * K * i) : NULL);
+}
+
+/* --------------------------------------------------- prepared Gaussians --- */
+typedef struct {
+    double u, v, s, o, sigma;
+    double xc, yc, zc;
+    double rgb[3], raw[3];
+    double dir[3], dist;
+    double reach;        /* distance beyond which a < alpha_min, with margin */
+    uint32_t zbits;      /* FP32 depth bits (canonical order key) */
+    int vis;
+} orc_g;
+
+static int ncoef(int deg) { return deg < 0 ? 3 : 3 * (deg + 1) * (deg + 1); }
+
+static void prepare(int64_t n, const float* ms, const float* op, const float* color, const orc_camera* c,
+                    const orc_opts* o, orc_g* g) {
+    int C = ncoef(o->sh_degree);
+    double R[9], t[3];
+    for (int i = 0; i < 9; ++i) R[i] = c->R[i];
+    for (int i = 0; i < 3; ++i) t[i] = c->t[i];
+    /* camera centre -R^T t */
+    double cc[3];
+    for (int a = 0; a < 3; ++a) cc[a] = -(R[0 * 3 + a] * t[0] + R[1 * 3 + a] * t[1] + R[2 * 3 + a] * t[2]);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        orc_g* G = &g[i];
+        memset(G, 0, sizeof *G);
+        const float* m = ms + 4 * i;
+        double sig_d, op_d;
+        float sig_f, op_f;
+        if (o->log_params) {
+            sig_d = exp((double)m[3]);
+            op_d = 1.0 / (1.0 + exp(-(double)op[i]));
+            sig_f = (float)sig_d; op_f = (float)op_d;
+        } else {
+            sig_f = m[3]; op_f = op[i];
+            sig_d = sig_f; op_d = op_f;
+        }
+        /* visibility: the FP32 decisions of the key path, without the tile test
+         * (a Gaussian off the tile grid cannot reach alpha_min on any pixel). */
+        if (!(isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && isfinite(sig_f) && isfinite(op_f))) continue;
+        float xf = ((c->R[0] * m[0] + c->R[1] * m[1]) + c->R[2] * m[2]) + c->t[0];
+        float yf = ((c->R[3] * m[0] + c->R[4] * m[1]) + c->R[5] * m[2]) + c->t[1];
+        float zf = ((c->R[6] * m[0] + c->R[7] * m[1]) + c->R[8] * m[2]) + c->t[2];
+        if (!(zf > c->znear) || !(sig_f > 0.0f) || !(op_f >= 1.0f / 255.0f)) continue;
+        float sf = (c->fx * sig_f) / zf;
+        float uf = (c->fx * xf) / zf + c->cx;
+        float vf = (c->fy * yf) / zf + c->cy;
+        if (!(isfinite(uf) && isfinite(vf) && isfinite(sf))) continue;
+        G->vis = 1;
+        G->zbits = f32_bits(zf);
+        double mx = m[0], my = m[1], mz = m[2];
+        G->xc = R[0] * mx + R[1] * my + R[2] * mz + t[0];
+        G->yc = R[3] * mx + R[4] * my + R[5] * mz + t[1];
+        G->zc = R[6] * mx + R[7] * my + R[8] * mz + t[2];
+        G->sigma = sig_d;
+        if (o->proj64) {
+            G->s = (double)c->fx * sig_d / G->zc;
+            G->u = (double)c->fx * G->xc / G->zc + (double)c->cx;
+            G->v = (double)c->fy * G->yc / G->zc + (double)c->cy;
+            G->o = op_d;
+        } else {
+            G->s = sf; G->u = uf; G->v = vf; G->o = op_f;
+        }
+        /* distance beyond which o g < alpha_min (1 - margin): nothing there can be
+         * blended or flagged, so the lists mode may skip it (same result as literal) */
+        double am = (double)o->alpha_min * (1.0 - o->flag_margin);
+        G->reach = (G->o > am) ? G->s * sqrt(2.0 * log(G->o / am)) * (1.0 + 1e-6) + 1e-9 : 0.0;
+        /* colour */
+        const float* col = color + (size_t)C * i;
+        double dv[3] = {mx - cc[0], my - cc[1], mz - cc[2]};
+        double dist = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        G->dist = dist;
+        for (int a = 0; a < 3; ++a) G->dir[a] = dv[a] / dist;
+        if (o->sh_degree < 0) {
+            for (int ch = 0; ch < 3; ++ch) { G->rgb[ch] = col[ch]; G->raw[ch] = col[ch]; }
+        } else {
+            double Y[16];
+            sh_basis(o->sh_degree, G->dir, Y, NULL);
+            int K = (o->sh_degree + 1) * (o->sh_degree + 1);
+            for (int ch = 0; ch < 3; ++ch) {
+                double acc = 0.0;
+                for (int k = 0; k < K; ++k) acc += (double)col[3 * k + ch] * Y[k];
+                G->raw[ch] = acc + 0.5;
+                G->rgb[ch] = G->raw[ch] > 0.0 ? G->raw[ch] : 0.0;
+            }
+        }
+    }
+}
+
+typedef struct { uint32_t zb; int64_t id; double z; } ord_entry;
+static int cmp_ord32(const void* a, const void* b) {
+    const ord_entry* x = (const ord_entry*)a; const ord_entry* y = (const ord_entry*)b;
+    if (x->zb != y->zb) return x->zb < y->zb ? -1 : 1;
+    return x->id < y->id ? -1 : (x->id > y->id);
+}
+static int cmp_ord64(const void* a, const void* b) {
+    const ord_entry* x = (const ord_entry*)a; const ord_entry* y = (const ord_entry*)b;
+    if (x->z != y->z) return x->z < y->z ? -1 : 1;
+    return x->id < y->id ? -1 : (x->id > y->id);
+}
+
+/* Front-to-back order of the visible Gaussians: ascending depth (the FP32
+ * depth bits on the canonical path, the FP64 depth with proj64), ties by index. */
+static int64_t depth_order(int64_t n, const orc_g* g, int proj64, int64_t* order) {
+    ord_entry* e = (ord_entry*)malloc(sizeof(ord_entry) * (size_t)(n > 0 ? n : 1));
+    int64_t nv = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (g[i].vis) { e[nv].zb = g[i].zbits; e[nv].id = i; e[nv].z = g[i].zc; ++nv; }
+    qsort(e, (size_t)nv, sizeof(ord_entry), proj64 ? cmp_ord64 : cmp_ord32);
+    for (int64_t k = 0; k < nv; ++k) order[k] = e[k].id;
+    free(e);
+    return nv;
+}
+
+/* --------------------------------------------------------- compositing ---- */
+typedef struct { int64_t id; double a, gval, T; int clamped; } blend_rec;
+
+typedef struct {
+    double C[3], T;
+    int32_t nb;
+    int64_t last;
+    int alive, flag;
+    uint64_t hash;
+    blend_rec* rec; int64_t nrec, cap;   /* blended entries, only when recording */
+} pix_state;
+
+static void pix_init(pix_state* p) {
+    p->C[0] = p->C[1] = p->C[2] = 0.0; p->T = 1.0; p->nb = 0; p->last = -1;
+    p->alive = 1; p->flag = 0; p->hash = 1469598103934665603ull; p->nrec = 0;
+}
+
+static void hash_mix(uint64_t* h, uint64_t v) {
+    for (int b = 0; b < 8; ++b) { *h ^= (v >> (8 * b)) & 0xff; *h *= 1099511628211ull; }
+}
+
+/* One front-to-back step of Eq. 4 for pixel centre (px, py). */
+static void composite_step(pix_state* p, const orc_g* G, int64_t id, double px, double py,
+                           const orc_opts* o, int record) {
+    double dx = px - G->u, dy = py - G->v;
+    double d2 = dx * dx + dy * dy;
+    double gval = exp(-d2 / (2.0 * G->s * G->s));
+    double og = G->o * gval;
+    int clamped = og > (double)o->alpha_max;
+    double a = clamped ? (double)o->alpha_max : og;
+    double amin = (double)o->alpha_min, tmin = (double)o->t_min, mg = o->flag_margin;
+    if (fabs(a - amin) <= mg * amin) p->flag = 1;
+    if (a < amin) return;
+    double Tn = p->T * (1.0 - a);
+    if (fabs(Tn - tmin) <= mg * tmin) p->flag = 1;
+    if (Tn < tmin) { p->alive = 0; hash_mix(&p->hash, (uint64_t)id ^ 0x8000000000000000ull); return; }
+    for (int ch = 0; ch < 3; ++ch) p->C[ch] += G->rgb[ch] * a * p->T;
+    if (record) {
+        if (p->nrec == p->cap) {
+            p->cap = p->cap ? 2 * p->cap : 16;
+            p->rec = (blend_rec*)realloc(p->rec, sizeof(blend_rec) * (size_t)p->cap);
+        }
+        blend_rec* r = &p->rec[p->nrec++];
+        r->id = id; r->a = a; r->gval = gval; r->T = p->T; r->clamped = clamped;
+    }
+    p->T = Tn;
+    p->nb += 1;
+    p->last = id;
+    hash_mix(&p->hash, (uint64_t)id * 2u + (uint64_t)clamped);
+}
+
+/* 2D gradient accumulators per Gaussian: du, dv, ds, do, dr, dg, db. */
+static void atomic_add(double* x, double v) {
+#pragma omp atomic
+    *x += v;
+}
+
+/* Reverse walk of one pixel (adjoint of Eq. 4). dC/da_k = T_k c_k - S_k/(1-a_k)
+ * where S_k is everything composited behind entry k, background included. */
+static void pixel_backward(const pix_state* p, const orc_g* g, double px, double py, const double G3[3],
+                           const orc_opts* o, double* g2d) {
+    double S[3];
+    for (int ch = 0; ch < 3; ++ch) S[ch] = p->T * (double)o->bg[ch];
+    for (int64_t k = p->nrec - 1; k >= 0; --k) {
+        const blend_rec* r = &p->rec[k];
+        const orc_g* G = &g[r->id];
+        double* acc = g2d + 7 * r->id;
+        double da = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            atomic_add(&acc[4 + ch], r->a * r->T * G3[ch]);
+            da += G3[ch] * (r->T * G->rgb[ch] - S[ch] / (1.0 - r->a));
+            S[ch] += r->a * r->T * G->rgb[ch];
+        }
+        if (r->clamped) continue;
+        double d_o = da * r->gval;
+        double dgv = da * G->o;
+        double s2 = G->s * G->s;
+        double dx = px - G->u, dy = py - G->v;
+        atomic_add(&acc[0], dgv * r->gval * dx / s2);
+        atomic_add(&acc[1], dgv * r->gval * dy / s2);
+        atomic_add(&acc[2], dgv * r->gval * (dx * dx + dy * dy) / (s2 * G->s));
+        atomic_add(&acc[3], d_o);
+    }
+}
+
+static void write_pixel(const pix_state* p, int64_t pix, int64_t P, const orc_opts* o,
+                        double* img, double* T, int32_t* nb, int32_t* last, uint8_t* flag, uint64_t* hash) {
+    for (int ch = 0; ch < 3; ++ch) img[ch * P + pix] = p->C[ch] + p->T * (double)o->bg[ch];
+    if (T) T[pix] = p->T;
+    if (nb) nb[pix] = p->nb;
+    if (last) last[pix] = (int32_t)p->last;
+    if (flag) flag[pix] = (uint8_t)p->flag;
+    if (hash) hash[pix] = p->hash;
+}
+
+/* Core renderer. dL_dimg != NULL additionally runs the adjoint into g2d [n][7]. */
+static void render_core(int64_t n, const orc_g* g, const int64_t* order, int64_t nv, const orc_camera* c,
+                        const orc_opts* o, double* img, double* T, int32_t* nb, int32_t* last,
+                        uint8_t* flag, uint64_t* hash, const double* dL, double* g2d) {
+    const int W = c->width, H = c->height;
+    const int64_t P = (int64_t)W * H;
+    const int record = dL != NULL;
+    if (o->mode == 0) {
+#pragma omp parallel
+        {
+            pix_state ps; memset(&ps, 0, sizeof ps);
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t pix = 0; pix < P; ++pix) {
+                double px = (double)(pix % W) + 0.5, py = (double)(pix / W) + 0.5;
+                pix_init(&ps);
+                for (int64_t k = 0; k < nv && ps.alive; ++k)
+                    composite_step(&ps, &g[order[k]], order[k], px, py, o, record);
+                write_pixel(&ps, pix, P, o, img, T, nb, last, flag, hash);
+                if (record) {
+                    double G3[3] = {dL[pix], dL[P + pix], dL[2 * P + pix]};
+                    pixel_backward(&ps, g, px, py, G3, o, g2d);
+                }
+            }
+            free(ps.rec);
+        }
+        return;
+    }
+    /* lists mode: bucket the Gaussians by the rows their support reaches, in depth order */
+    int64_t* rcount = (int64_t*)calloc((size_t)H + 1, sizeof(int64_t));
+    int32_t* r0 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    int32_t* r1 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    for (int64_t k = 0; k < nv; ++k) {
+        const orc_g* G = &g[order[k]];
+        double lo = ceil(G->v - G->reach - 0.5), hi = floor(G->v + G->reach - 0.5);
+        if (lo < 0) lo = 0;
+        if (hi > H - 1) hi = H - 1;
+        if (!(G->reach > 0.0) || lo > hi) { r0[k] = 1; r1[k] = 0; continue; }
+        r0[k] = (int32_t)lo; r1[k] = (int32_t)hi;
+        for (int32_t y = r0[k]; y <= r1[k]; ++y) rcount[y + 1]++;
+    }
+    for (int y = 0; y < H; ++y) rcount[y + 1] += rcount[y];
+    int64_t total = rcount[H];
+    int64_t* bucket = (int64_t*)malloc(sizeof(int64_t) * (size_t)(total > 0 ? total : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)H);
+    for (int y = 0; y < H; ++y) fill[y] = rcount[y];
+    for (int64_t k = 0; k < nv; ++k)
+        for (int32_t y = r0[k]; y <= r1[k]; ++y) bucket[fill[y]++] = order[k];
+    free(fill); free(r0); free(r1);
+#pragma omp parallel
+    {
+        pix_state* row = (pix_state*)calloc((size_t)W, sizeof(pix_state));
+#pragma omp for schedule(dynamic, 1)
+        for (int y = 0; y < H; ++y) {
+            double py = (double)y + 0.5;
+            for (int x = 0; x < W; ++x) pix_init(&row[x]);
+            int alive = W;
+            for (int64_t b = rcount[y]; b < rcount[y + 1] && alive > 0; ++b) {
+                int64_t id = bucket[b];
+                const orc_g* G = &g[id];
+                double dy = py - G->v;
+                double w2 = G->reach * G->reach - dy * dy;
+                if (w2 < 0) continue;
+                double w = sqrt(w2);
+                double lo = ceil(G->u - w - 0.5), hi = floor(G->u + w - 0.5);
+                if (lo < 0) lo = 0;
+                if (hi > W - 1) hi = W - 1;
+                for (int x = (int)lo; x <= (int)hi; ++x) {
+                    if (!row[x].alive) continue;
+                    composite_step(&row[x], G, id, (double)x + 0.5, py, o, record);
+                    if (!row[x].alive) --alive;
+                }
+            }
+            for (int x = 0; x < W; ++x) {
+                int64_t pix = (int64_t)y * W + x;
+                write_pixel(&row[x], pix, P, o, img, T, nb, last, flag, hash);
+                if (record) {
+                    double G3[3] = {dL[pix], dL[P + pix], dL[2 * P + pix]};
+                    pixel_backward(&row[x], g, (double)x + 0.5, py, G3, o, g2d);
+                }
+            }
+        }
+        for (int x = 0; x < W; ++x) free(row[x].rec);
+        free(row);
+    }
+    free(bucket); free(rcount);
+}
+
+/* Forward render. img [3][H][W], T [H][W], nb (entries blended), last (index of
+ * the last blended Gaussian or -1), flag (a cutoff/stop decision within the
+ * relative margin), hash (digest of the decision sequence). Any output may be NULL
+ * except img. Returns the number of visible Gaussians. */
+int64_t orc_render(int64_t n, const float* means_sigma, const float* opacity, const float* color,
+                   const orc_camera* cam, const orc_opts* o, double* img, double* T, int32_t* nb,
+                   int32_t* last, uint8_t* flag, uint64_t* hash) {
+    orc_g* g = (orc_g*)malloc(sizeof(orc_g) * (size_t)(n > 0 ? n : 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    prepare(n, means_sigma, opacity, color, cam, o, g);
+    int64_t nv = depth_order(n, g, o->proj64, order);
+    render_core(n, g, order, nv, cam, o, img, T, nb, last, flag, hash, NULL, NULL);
+    free(g); free(order);
+    return nv;
+}
+
+/* Chain rule from the screen-space disc to the parameters of one Gaussian. */
+static void chain_one(const orc_g* G, const double* acc, const float* ms, const float* col,
+                      const orc_camera* c, const orc_opts* o,
+                      double* dmean, double* dsig, double* dop, double* dcol) {
+    int C = ncoef(o->sh_degree);
+    double fx = c->fx, fy = c->fy;
+    double du = acc[0], dv = acc[1], ds = acc[2], d_o = acc[3];
+    double zc = G->zc, xc = G->xc, yc = G->yc;
+    double dxc = du * fx / zc;
+    double dyc = dv * fy / zc;
+    double dzc = -du * fx * xc / (zc * zc) - dv * fy * yc / (zc * zc) - ds * fx * G->sigma / (zc * zc);
+    for (int a = 0; a < 3; ++a)
+        dmean[a] = c->R[0 * 3 + a] * dxc + c->R[1 * 3 + a] * dyc + c->R[2 * 3 + a] * dzc;
+    double dsigma = ds * fx / zc;
+    *dsig = o->log_params ? dsigma * G->sigma : dsigma;
+    *dop = o->log_params ? d_o * G->o * (1.0 - G->o) : d_o;
+    if (o->sh_degree < 0) {
+        for (int ch = 0; ch < 3; ++ch) dcol[ch] = acc[4 + ch];
+        return;
+    }
+    int K = (o->sh_degree + 1) * (o->sh_degree + 1);
+    double Y[16], dY[16][3];
+    sh_basis(o->sh_degree, G->dir, Y, dY);
+    double draw[3];
+    for (int ch = 0; ch < 3; ++ch) draw[ch] = G->raw[ch] > 0.0 ? acc[4 + ch] : 0.0;
+    for (int k = 0; k < K; ++k)
+        for (int ch = 0; ch < 3; ++ch) dcol[3 * k + ch] = Y[k] * draw[ch];
+    double ddir[3] = {0, 0, 0};
+    for (int k = 0; k < K; ++k)
+        for (int ch = 0; ch < 3; ++ch) {
+            double w = draw[ch] * (double)col[3 * k + ch];
+            for (int a = 0; a < 3; ++a) ddir[a] += w * dY[k][a];
+        }
+    double dot = ddir[0] * G->dir[0] + ddir[1] * G->dir[1] + ddir[2] * G->dir[2];
+    for (int a = 0; a < 3; ++a) dmean[a] += (ddir[a] - dot * G->dir[a]) / G->dist;
+    (void)ms; (void)C;
+}
+
+/* Forward + adjoint. dL_dimg [3][H][W]. Outputs: d_means [n][3], d_sigma [n]
+ * (w.r.t. sigma, or log sigma), d_opac [n] (opacity, or logit), d_color [n][C],
+ * g2d [n][7] (du, dv, ds, do, dr, dg, db; may be NULL). The forward outputs
+ * are as in orc_render and may be NULL. */
+int64_t orc_backward(int64_t n, const float* means_sigma, const float* opacity, const float* color,
+                     const orc_camera* cam, const orc_opts* o, const double* dL_dimg,
+                     double* d_means, double* d_sigma, double* d_opac, double* d_color, double* g2d_out,
+                     double* img, double* T, int32_t* nb, int32_t* last, uint8_t* flag, uint64_t* hash) {
+    orc_g* g = (orc_g*)malloc(sizeof(orc_g) * (size_t)(n > 0 ? n : 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    double* g2d = (double*)calloc((size_t)(n > 0 ? n : 1) * 7, sizeof(double));
+    int64_t P = (int64_t)cam->width * cam->height;
+    double* img_tmp = img ? img : (double*)malloc(sizeof(double) * 3 * (size_t)P);
+    prepare(n, means_sigma, opacity, color, cam, o, g);
+    int64_t nv = depth_order(n, g, o->proj64, order);
+    render_core(n, g, order, nv, cam, o, img_tmp, T, nb, last, flag, hash, dL_dimg, g2d);
+    int C = ncoef(o->sh_degree);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double* dm = d_means + 3 * i;
+        double* dc = d_color + (size_t)C * i;
+        if (!g[i].vis) {
+            dm[0] = dm[1] = dm[2] = 0.0; d_sigma[i] = 0.0; d_opac[i] = 0.0;
+            for (int k = 0; k < C; ++k) dc[k] = 0.0;
+            continue;
+        }
+        chain_one(&g[i], g2d + 7 * i, means_sigma + 4 * i, color + (size_t)C * i, cam, o,
+                  dm, &d_sigma[i], &d_opac[i], dc);
+    }
+    if (g2d_out) memcpy(g2d_out, g2d, sizeof(double) * 7 * (size_t)n);
+    if (!img) free(img_tmp);
+    free(g); free(order); free(g2d);
+    return nv;
+}
+
+/* ------------------------------------------------------- loss and Adam ---- */
+/* L1 loss, mean over 3 H W entries, and its gradient sign(C - target)/(3HW)
+ * (the l1 part of the training loss of Sec. 3, lambda = 0). */
+double orc_l1(int64_t count, const double* img, const float* target, double* grad) {
+    double acc = 0.0;
+    for (int64_t i = 0; i < count; ++i) {
+        double d = img[i] - (double)target[i];
+        acc += fabs(d);
+        if (grad) grad[i] = (d > 0) ? 1.0 / (double)count : (d < 0 ? -1.0 / (double)count : 0.0);
+    }
+    return acc / (double)count;
+}
+
+/* Adam with bias correction (step t >= 1), FP64, in place on p, m, v. */
+void orc_adam(int64_t count, double* p, const double* grad, double* m, double* v,
+              double lr, double b1, double b2, double eps, int64_t t) {
+    double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (int64_t i = 0; i < count; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * grad[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * grad[i] * grad[i];
+        double mh = m[i] / c1, vh = v[i] / c2;
+        p[i] -= lr * mh / (sqrt(vh) + eps);
+    }
+}
