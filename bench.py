@@ -1,0 +1,423 @@
+"""Benchmark of the isotropic Gaussian splatting hot path on GB300.
+
+Workload (one GPU): the training step of a 3M-Gaussian scene (means U[-1,1]^3,
+sigma log-uniform [0.005, 0.05] stored as log sigma, opacity U[0.05, 0.95]
+stored as a logit, degree-3 SH with DC from U[0,1] RGB), 1297x840 images, 16
+cameras on a ring of radius 4. One step = one view: project, bin + sort,
+forward blend, L1 loss against that view's seeded target, backward blend,
+projection backward, Adam over all 53 parameters of every Gaussian. Steps cycle
+through the 16 views. All inputs are synthetic and seeded; they live in HBM
+before the timed region; the per-step working set (parameters, Adam state,
+gradients: 2.5 GB) is far larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0). --impl reference times the CPU oracle (the
+reference arm of this method: the paper ships no code) on the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s & fwd+bwd steps/s at 3M isotropic Gaussians; serve p50/p99 ms"
+WORKLOAD = "train_step_3M_sh3_1297x840_ring16"
+STAGES = ("project", "bin_sort", "blend_fwd", "l1", "blend_bwd", "project_bwd", "adam")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("mine", "reference"), default="mine")
+    ap.add_argument("--n", type=int, default=3_000_000, help="Gaussians (default: the 3M workload)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 1080p forward / fwd+bwd lines")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.out = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={device_index}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- GPU arm --------
+
+def build_workload(n, device):
+    import numpy as np
+    import torch
+
+    from paper_2403_14244_gb300 import igs, scenes
+    from paper_2403_14244_gb300.render import TrainStep
+
+    sc, cams = scenes.workload_train_3m(n=n)
+    ts = TrainStep(torch.from_numpy(sc.means_sigma).to(device), torch.from_numpy(sc.opacity).to(device),
+                   torch.from_numpy(sc.color).to(device), sh_degree=3, tile=16, lr=1e-3, device=device)
+    targets_host = [torch.from_numpy(scenes.train_target(k)).pin_memory() for k in range(len(cams))]
+    targets = [t.to(device) for t in targets_host]
+    cam_s = [igs.camera(c) for c in cams]
+    return sc, cams, cam_s, ts, targets, targets_host, np
+
+
+def run_mine(args, world, rank, local):
+    import torch
+
+    from paper_2403_14244_gb300 import igs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    igs.load()
+    sc, cams, cam_s, ts, targets, targets_host, np = build_workload(args.n, dev)
+    V = len(cams)
+    stream = torch.cuda.current_stream(dev)
+    # capacity calibration: every view once with a status check (untimed set-up)
+    for k in range(V):
+        ts.step(cam_s[k], targets[k], check=True)
+    for k in range(args.warmup):
+        ts.step(cam_s[k % V], targets[k % V])
+    torch.cuda.synchronize(dev)
+
+    # -------- timed region: K steps, device time on the launching stream
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    launches0 = igs.launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    stage_ev = []
+    start.record(stream)
+    for k in range(args.steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+        evs[0].record(stream)
+        it = iter(evs[1:])
+        ts.step(cam_s[k % V], targets[k % V], marks=lambda name, it=it: next(it).record(stream))
+        stage_ev.append(evs)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = igs.launch_count() - launches0
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(end)
+    stage_ms = {s: 0.0 for s in STAGES}
+    for evs in stage_ev:
+        for i, s in enumerate(STAGES):
+            stage_ms[s] += evs[i].elapsed_time(evs[i + 1])
+    stage_ms = {s: v / args.steps for s, v in stage_ms.items()}
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    # the entry capacity used in the timed region held for every view: re-run
+    # each view's binning at that capacity (untimed) and read its status
+    for k in range(V):
+        _, f = ts.renderer.run_forward(ts.scene, cam_s[k], check=False)
+        st, info = igs.frame_status(f)
+        assert st == igs.OK, f"view {k}: device status {st} after the timed region"
+    ms_per_step = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms / 1e3)
+
+    # -------- end to end: host target in pinned memory -> device, step, loss -> host
+    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+    tgt_dev = torch.empty_like(targets[0])
+    e2e_steps = max(10, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        tgt_dev.copy_(targets_host[k % V], non_blocking=True)
+        ts.step(cam_s[k % V], tgt_dev)
+        loss_host.copy_(ts.loss, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "steps/s",
+           "h2d_bytes_per_step": int(targets[0].numel() * 4 + 80), "d2h_bytes_per_step": 4}
+
+    # -------- roofline of the dominant kernel
+    peak_hbm, peak_kind = load_peaks()
+    n, C = ts.n, ts.C
+    P = cams[0].width * cams[0].height
+    dominant = max(stage_ms, key=stage_ms.get)
+    algo_bytes = {
+        # per launch, from the data the step must move ("Roofline")
+        "adam": 28 * n * (5 + C),                          # read p, g, m, v; write p, m, v
+        "project": n * (16 + 4 + 4 * C) + n * (32 + 8 + 4 + 4),
+        "project_bwd": n * (16 + 4 + 4 * C + 32 + 4) + n * (16 + 4 + 4 * C),
+        "l1": P * 3 * 4 * 3,
+    }
+    roofline = None
+    if dominant in algo_bytes:
+        achieved = algo_bytes[dominant] / (stage_ms[dominant] / 1e3) / 1e9
+        roofline = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm,
+                    "unit": "GB/s", "frac": round(achieved / peak_hbm, 4), "traffic": None,
+                    "peak_kind": peak_kind}
+    else:
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                    "frac": None, "traffic": None}
+
+    extra = {}
+    if not args.no_extra:
+        extra = run_extra(dev, np)
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators, no dataset)",
+        "config": {"workload": WORKLOAD, "n_gaussians": n, "sh_degree": 3, "image": [cams[0].width, cams[0].height],
+                   "views": V, "tile": 16, "optimizer": "adam lr 1e-3", "params": "mu, log sigma, logit o, SH",
+                   "l2": "no flush: per-step working set 2.5 GB > 129 MB L2",
+                   "parallelism": f"replicas x{world} (no collective)"},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
+        "roofline": roofline, "extra": extra,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_extra(dev, np):
+    """1080p forward frames/s and fwd+bwd steps/s on the 1M clustered SH3 scene."""
+    import torch
+
+    from paper_2403_14244_gb300 import igs, scenes
+    from paper_2403_14244_gb300.render import Renderer
+
+    sc, cam, target = scenes.workload_fwd_bwd_1m()
+    scene = igs.Scene.from_numpy(sc, dev)
+    r = Renderer(tile=16, sh_degree=3, param_mode=0, device=dev)
+    c = igs.camera(cam)
+    img, f = r.run_forward(scene, c, check=True)
+    tg = torch.from_numpy(target).to(dev)
+    loss = torch.zeros(1, device=dev)
+    dimg = torch.empty_like(img)
+    g2d = torch.empty((scene.n, 8), device=dev)
+    grads = (torch.empty_like(scene.means_sigma), torch.empty_like(scene.opacity), torch.empty_like(scene.color))
+    reps = 50
+
+    def fwd():
+        igs.project(scene, c, r.opts, f)
+        igs.bin_sort(f, r.opts)
+        igs.render_fwd(f, r.opts, img)
+
+    def fwdbwd():
+        fwd()
+        igs.l1_loss(img, tg, loss, dimg)
+        igs.render_bwd(scene, c, r.opts, f, dimg, g2d, *grads)
+
+    out = {}
+    for name, fn in (("fwd_1080p_1M", fwd), ("fwd_bwd_1080p_1M", fwdbwd)):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"ms": round(ms, 4), "per_s": round(1e3 / ms, 1)}
+    st, info = igs.frame_status(f)
+    assert st == igs.OK
+    out["fwd_bwd_1080p_1M"]["entries_M"] = info[0]
+    return out
+
+
+# ------------------------------------------------------------ CPU oracle ----
+
+def oracle_step(sc, cam, target, band=None, param_frac=1.0):
+    """One training step of the CPU oracle: FP64 forward + adjoint (row-list
+    mode, all host cores), L1 loss, Adam over a fraction of the parameters.
+    band = (y0, h) renders only rows [y0, y0 + h) of the view."""
+    import numpy as np
+
+    import oracle
+    from paper_2403_14244_gb300 import scenes
+
+    if band is not None:
+        y0, h = band
+        cam = scenes.Camera(R=cam.R, t=cam.t, fx=cam.fx, fy=cam.fy, cx=cam.cx, cy=cam.cy - y0, width=cam.width,
+                            height=h, znear=cam.znear)
+        target = np.ascontiguousarray(target[:, y0:y0 + h])
+    fwd = oracle.render(sc, cam, mode=1)
+    loss, G = oracle.l1(fwd["img"], target)
+    g = oracle.backward(sc, cam, G, mode=1)
+    flat_g = np.concatenate([np.concatenate([g["d_means"], g["d_sigma"][:, None]], 1).reshape(-1), g["d_opac"],
+                             g["d_color"].reshape(-1)])
+    m = int(flat_g.size * param_frac)
+    p = np.concatenate([sc.means_sigma.reshape(-1), sc.opacity, sc.color.reshape(-1)])[:m].astype(np.float64)
+    oracle.adam(p, flat_g[:m], np.zeros(m), np.zeros(m), lr=1e-3, t=1)
+    return loss
+
+
+def cpu_baseline(sc, cams, budget_s):
+    import oracle
+    from paper_2403_14244_gb300 import scenes
+
+    oracle.build()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        oracle_step(sc, cams[steps % len(cams)], scenes.train_target(steps % len(cams)))
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s or steps >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(steps / dt, 5), "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} full training step(s) of the same workload (views 0..{steps - 1}): FP64 forward + "
+                      f"adjoint over all 1297x840 pixels, L1, Adam over all 53 x 3M parameters; {dt:.1f} s",
+            "cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle on the same workload, each step a
+    bounded sample (a band of rows of one view plus the same fraction of the
+    Adam update), sized so the whole run stays within a few minutes."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2403_14244_gb300 import scenes
+
+    oracle.build()
+    sc, cams = scenes.workload_train_3m(n=args.n)
+    H = cams[0].height
+    # calibrate on a 1/8 band, then size the band so (W + K) steps take ~150 s
+    t0 = time.perf_counter()
+    oracle_step(sc, cams[0], scenes.train_target(0), band=(H // 2 - H // 16, H // 8), param_frac=1 / 8)
+    t_eighth = time.perf_counter() - t0
+    per_full = 8 * t_eighth
+    frac = min(1.0, 150.0 / max(1e-9, (args.steps + args.warmup) * per_full))
+    h = max(8, int(H * frac))
+    frac = h / H
+    for k in range(args.warmup):
+        oracle_step(sc, cams[k % 16], scenes.train_target(k % 16), band=((H - h) // 2, h), param_frac=frac)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle_step(sc, cams[k % 16], scenes.train_target(k % 16), band=((H - h) // 2, h), param_frac=frac)
+    dt = time.perf_counter() - t0
+    value = args.steps * frac / dt
+    sample = (f"each step: oracle forward + adjoint of rows [{(H - h) // 2}, {(H - h) // 2 + h}) of one 1297x840 "
+              f"view ({frac:.3f} of the image) and Adam over the same fraction of the 53 x {args.n} parameters; "
+              f"value scaled to whole steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps / frac, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generators, no dataset)",
+        "config": {"workload": WORKLOAD, "n_gaussians": args.n, "image": [1297, 840], "views": 16},
+        "cpu_baseline": {"value": round(value, 6), "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_mine(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

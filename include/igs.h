@@ -1,0 +1,225 @@
+/*
+ * igs.h — C ABI of the GB300 (sm_103a) isotropic Gaussian splatting library.
+ *
+ * Method: arXiv 2403.14244, "Isotropic Gaussian Splatting for Real-Time
+ * Radiance Field Rendering". Each particle is an isotropic Gaussian (Eq. 8)
+ * with centre mu, one scale sigma, an opacity and a colour (plain RGB or real
+ * spherical harmonics up to degree 3). A view is rendered by projecting every
+ * Gaussian to a screen-space disc (Eq. 7 with Sigma = sigma^2 I: centre
+ * u = fx x_c/z_c + cx, v = fy y_c/z_c + cy, radius s = fx sigma / z_c, which
+ * depends only on the depth, Sec. 2.4), by compositing the discs front to
+ * back per pixel (Eq. 4), and trained by the gradients of Eq. 3 and the
+ * position gradient after it. Compositing rules fixed by this library where
+ * the paper is silent:
+ *   alpha = min(alpha_max, o * exp(-d^2 / (2 s^2)))  (Eq. 8 with s = sigma/sqrt 2)
+ *   entries with alpha < alpha_min are skipped;
+ *   an entry that would take the transmittance below t_min is not blended and
+ *   ends the pixel; the final colour is C + T_final * bg;
+ *   pixel centres are at (x + 0.5, y + 0.5);
+ *   footprint radius r = 3.33 s (compact support, Eq. 2): beyond it alpha < 1/255.
+ *
+ * Conventions for every entry point
+ *   - Pointers marked "device" are CUDA device pointers of the current device;
+ *     "host" pointers are ordinary host memory. The caller owns every buffer it
+ *     passes. The library never allocates device memory: scratch comes from the
+ *     caller through igs_frame_layout().
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Every call
+ *     is asynchronous on `stream` unless it says otherwise.
+ *   - Argument errors (NULL pointers, sizes out of range, tile not 8/16/32,
+ *     fx != fy, a frame laid out for other sizes) return IGS_ERR_INVALID_ARG
+ *     synchronously and launch nothing. Launch failures return IGS_ERR_CUDA.
+ *   - Errors found on the device (capacity overflow, a bounded spin-wait that
+ *     ran out) are written to the frame's device status words; read them with
+ *     igs_frame_status(). A kernel never traps: it records the error and returns.
+ *   - igs_last_error() gives a thread-local message for the last failed call.
+ *
+ * Data layout (structure of arrays, FP32, C order):
+ *   means_sigma [n][4]  (x, y, z, sigma) or (x, y, z, log sigma) with param_mode 1
+ *   opacity     [n]     opacity, or its logit with param_mode 1
+ *   color       [n][C]  C = 3 (RGB, sh_degree -1) or 3 (deg+1)^2 SH coefficients,
+ *                       coefficient-major: color[i][3*k + channel], k = l^2 + l + m,
+ *                       real orthonormal basis without Condon-Shortley phase;
+ *                       rgb = max(0, sum_k color[k] Y_k(dir) + 0.5), dir from the
+ *                       camera centre to mu.
+ *   images      [3][H][W] planar RGB; per-pixel buffers [H][W].
+ */
+#ifndef IGS_H
+#define IGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IGS_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define IGS_API __attribute__((visibility("default")))
+#else
+#define IGS_API
+#endif
+
+typedef enum igs_status {
+    IGS_OK = 0,
+    IGS_ERR_INVALID_ARG = 1,
+    IGS_ERR_OOM = 2,             /* a caller-sized buffer is too small */
+    IGS_ERR_CUDA = 3,            /* a CUDA launch or call failed */
+    IGS_ERR_CAPACITY = 4,        /* more (Gaussian, tile) entries than the frame holds */
+    IGS_ERR_NOT_READY = 5,
+    IGS_ERR_DEVICE_TIMEOUT = 6,  /* a bounded device spin-wait gave up */
+    IGS_ERR_UNSUPPORTED = 7
+} igs_status;
+
+/* Pinhole camera, world -> camera x_c = R x_w + t (R row-major); image x to the
+ * right, y down, z forward. fx must equal fy (an isotropic Gaussian projects to
+ * a disc only then). znear: Gaussians with z_c <= znear are culled. */
+typedef struct igs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float znear;
+    int32_t width, height;
+} igs_camera;
+
+typedef struct igs_opts {
+    int32_t tile;        /* tile edge in pixels: 8, 16 or 32 */
+    int32_t sh_degree;   /* -1: colour is RGB; 0..3: SH of that degree */
+    int32_t param_mode;  /* 0: sigma and opacity stored as is; 1: log sigma and logit */
+    float alpha_min;     /* 1/255 */
+    float alpha_max;     /* 0.99 */
+    float t_min;         /* 1e-4 */
+    float bg[3];         /* background colour, added with the final transmittance */
+} igs_opts;
+
+/* Scene buffers (device), layout above. */
+typedef struct igs_scene {
+    const float* means_sigma;
+    const float* opacity;
+    const float* color;
+    int64_t n;
+} igs_scene;
+
+/* Per-view state. igs_frame_layout() carves every pointer out of ONE caller
+ * buffer; the same frame serves igs_project, igs_bin_sort, igs_render_fwd and
+ * igs_render_bwd of one view, and can be reused for the next view of the same
+ * size. Contents after each step:
+ *   igs_project:    rec, rect, count, depth_key
+ *   igs_bin_sort:   order, offset, tile_key, vals, ranges, info[0..1]
+ *   igs_render_fwd: T_final, n_contrib
+ * Status words (device, uint32): info[0] = M entries, info[1] = Gaussians kept,
+ * info[2] = error code (igs_status, 0 = none), info[3] = M the view needs. */
+typedef struct igs_frame {
+    int64_t n;               /* Gaussians the frame was laid out for */
+    int64_t capacity;        /* (Gaussian, tile) entries it can hold */
+    int32_t width, height, tile, tiles_x, tiles_y, _pad;
+    float* rec;              /* [n][8] u, v, w2 = log2(e)/(2 s^2), o, r, g, b, s */
+    uint32_t* rect;          /* [n][2] x0 | y0 << 16, x1 | y1 << 16 (inclusive tiles) */
+    uint32_t* count;         /* [n] tiles touched; 0 = culled */
+    uint32_t* depth_key;     /* [n] bits of the FP32 depth z_c; 0xFFFFFFFF if culled */
+    uint32_t* order;         /* [n] Gaussian ids, front to back (culled ones last) */
+    uint32_t* offset;        /* [n] first entry of order[p]: exclusive scan of count in depth order */
+    uint32_t* tile_key;      /* [capacity] tile id of each sorted entry */
+    uint32_t* vals;          /* [capacity] Gaussian id of each sorted entry */
+    uint32_t* ranges;        /* [tiles][2] [start, end) of each tile's entries; (0, 0) if empty */
+    float* T_final;          /* [H][W] transmittance after the last blended entry */
+    uint32_t* n_contrib;     /* [H][W] 1 + list position (within the tile) of the last blended entry */
+    uint32_t* info;          /* [16] status words, see above */
+    void* scratch;           /* sort double buffers, histograms, look-back state */
+    size_t scratch_bytes;
+} igs_frame;
+
+/* Lay out a frame for n Gaussians, at most `capacity` entries, and the camera's
+ * image size and opts->tile. With workspace == NULL only *bytes is written (the
+ * size to allocate, 256-byte aligned). Otherwise `workspace` (device, >= *bytes,
+ * 256-byte aligned) is carved into `frame`; nothing is launched and the
+ * workspace is not cleared (each step initialises what it reads). */
+IGS_API igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, const igs_opts* opts,
+                            void* workspace, size_t* bytes, igs_frame* frame);
+
+/* Project every Gaussian to its screen disc and tile rectangle
+ * (Eq. 7 with Sigma = sigma^2 I, Eq. 2 support radius 3.33 s; culling of z_c <=
+ * znear, sigma <= 0, opacity < 1/255, non-finite input, off-grid rectangle), and
+ * evaluate its colour (RGB, or SH at the direction from the camera centre).
+ * With param_mode 1 sigma = exp(log sigma) and opacity = sigmoid(logit) here.
+ * The culling decisions, depth key and rectangle use FP32 with every operation
+ * rounded once in a fixed order (bit-reproducible). Writes rec, rect, count,
+ * depth_key. */
+IGS_API igs_status igs_project(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                       igs_frame* frame, void* stream);
+
+/* Order the kept Gaussians front to back (stable radix sort of the
+ * depth keys; ties keep index order), scan their tile counts, duplicate each
+ * into one entry per touched tile in that order, stable radix sort of the
+ * entries by tile id, and per-tile ranges. The resulting entry order is that of
+ * the 64-bit key (tile << 32 | depth bits) sorted stably: within a tile, front
+ * to back as Eq. 4 requires. If M exceeds frame->capacity, info[2] is set to
+ * IGS_ERR_CAPACITY, info[3] to M, and the later steps leave their outputs
+ * untouched. Writes order, offset, tile_key, vals, ranges, info. */
+IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* stream);
+
+/* Export the sorted 64-bit keys (tile << 32 | depth bits), M = info[0] of them,
+ * into keys (device, >= capacity entries). For inspection and tests. */
+IGS_API igs_status igs_export_keys(const igs_frame* frame, uint64_t* keys, void* stream);
+
+/* Per tile, front-to-back compositing of its entries (Eq. 4) at every pixel
+ * centre. Writes img (device, [3][H][W]) = C + T_final * bg, and the frame's
+ * T_final and n_contrib (saved for the backward pass). */
+IGS_API igs_status igs_render_fwd(igs_frame* frame, const igs_opts* opts, float* img, void* stream);
+
+/* Adjoint of igs_render_fwd and igs_project for dL_dimg (device,
+ * [3][H][W]). Walks each pixel's blended entries back to front, recovering the
+ * transmittance from T_final (no forward re-run), accumulates per-Gaussian
+ * screen-space gradients in g2d (device, [n][8], caller scratch, cleared here),
+ * then chains them to the stored parameters. Gradients are OVERWRITTEN:
+ * d_means_sigma [n][4] (mu, and sigma or log sigma), d_opacity [n] (opacity or
+ * logit), d_color [n][C]. Culled Gaussians get 0. The set of blended entries is
+ * held fixed (almost-everywhere derivative). */
+IGS_API igs_status igs_render_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                          const igs_frame* frame, const float* dL_dimg, float* g2d,
+                          float* d_means_sigma, float* d_opacity, float* d_color, void* stream);
+
+/* The two halves of igs_render_bwd, for callers that time or overlap them:
+ * igs_blend_bwd clears g2d ([n][8], device) and accumulates the screen-space
+ * gradients (du, dv, dw2, do, dr, dg, db, 0) of every Gaussian over all pixels;
+ * igs_project_bwd chains g2d to the stored parameters (same outputs and rules
+ * as igs_render_bwd). */
+IGS_API igs_status igs_blend_bwd(const igs_frame* frame, const igs_opts* opts, const float* dL_dimg, float* g2d,
+                                 void* stream);
+IGS_API igs_status igs_project_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                   const igs_frame* frame, const float* g2d, float* d_means_sigma,
+                                   float* d_opacity, float* d_color, void* stream);
+
+/* L1 loss of Sec. 3 (lambda = 0): loss = mean |img - target| over `count`
+ * entries, written to *loss (device float, overwritten), and
+ * dL_dimg = sign(img - target) / count (device, count entries; sign(0) = 0). */
+IGS_API igs_status igs_l1_loss(const float* img, const float* target, int64_t count, float* loss,
+                       float* dL_dimg, void* stream);
+
+/* One bias-corrected Adam step (step >= 1) in place on p, m, v (device,
+ * count FP32 each), from gradient g. The host scalars are double so that 1 - b1,
+ * 1 - b2 and the bias corrections are formed exactly before rounding to FP32:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr (m/(1-b1^step)) / (sqrt(v/(1-b2^step)) + eps). */
+IGS_API igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_t count, double lr, double b1,
+                            double b2, double eps, int64_t step, void* stream);
+
+/* Copy the frame's four status words to host_info (host, 4 uint32) and wait for
+ * `stream`. Returns the recorded device error (IGS_OK if none). Synchronous. */
+IGS_API igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info, void* stream);
+
+/* Clear the frame's status words (asynchronous). */
+IGS_API igs_status igs_frame_reset_status(igs_frame* frame, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads). For accounting in benchmarks; host-only, never fails. */
+IGS_API uint64_t igs_launch_count(void);
+
+IGS_API const char* igs_status_string(igs_status s);
+IGS_API const char* igs_last_error(void);
+IGS_API int32_t igs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGS_H */

@@ -1,0 +1,315 @@
+// C ABI of libigs (declared in include/igs.h): argument checks, frame layout,
+// and the launches of each step. Nothing here allocates device memory.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace igs {
+std::atomic<uint64_t> g_launches{0};
+}
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+igs_status fail(igs_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+igs_status fail(igs_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+igs_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return IGS_OK;
+    return fail(IGS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+igs_status check_camera(const igs_camera* cam) {
+    if (!cam) return fail(IGS_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width <= 0 || cam->height <= 0) return fail(IGS_ERR_INVALID_ARG, "image size must be positive");
+    if (!(cam->fx > 0.f) || cam->fx != cam->fy)
+        return fail(IGS_ERR_INVALID_ARG, "fx must be positive and equal fy (isotropic discs)");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(cam->R[i])) return fail(IGS_ERR_INVALID_ARG, "camera R not finite");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(cam->t[i])) return fail(IGS_ERR_INVALID_ARG, "camera t not finite");
+    if (!std::isfinite(cam->cx) || !std::isfinite(cam->cy) || !std::isfinite(cam->znear))
+        return fail(IGS_ERR_INVALID_ARG, "camera intrinsics not finite");
+    return IGS_OK;
+}
+
+igs_status check_opts(const igs_opts* o) {
+    if (!o) return fail(IGS_ERR_INVALID_ARG, "opts is NULL");
+    if (o->tile != 8 && o->tile != 16 && o->tile != 32) return fail(IGS_ERR_INVALID_ARG, "tile must be 8, 16 or 32");
+    if (o->sh_degree < -1 || o->sh_degree > 3) return fail(IGS_ERR_INVALID_ARG, "sh_degree must be -1..3");
+    if (o->param_mode != 0 && o->param_mode != 1) return fail(IGS_ERR_INVALID_ARG, "param_mode must be 0 or 1");
+    if (!(o->alpha_min > 0.f) || !(o->alpha_max <= 1.f) || !(o->alpha_min < o->alpha_max) || !(o->t_min > 0.f) ||
+        !(o->t_min < 1.f))
+        return fail(IGS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max <= 1 and 0 < t_min < 1");
+    return IGS_OK;
+}
+
+igs_status check_scene(const igs_scene* s) {
+    if (!s) return fail(IGS_ERR_INVALID_ARG, "scene is NULL");
+    if (s->n < 0 || s->n >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "n out of range");
+    if (s->n > 0 && (!s->means_sigma || !s->opacity || !s->color))
+        return fail(IGS_ERR_INVALID_ARG, "scene buffer is NULL");
+    if (reinterpret_cast<uintptr_t>(s->means_sigma) & 15)
+        return fail(IGS_ERR_INVALID_ARG, "means_sigma must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(s->color) & 15)
+        return fail(IGS_ERR_INVALID_ARG, "color must be 16-byte aligned");
+    return IGS_OK;
+}
+
+igs_status check_frame(const igs_frame* f) {
+    if (!f || !f->info || !f->rec) return fail(IGS_ERR_INVALID_ARG, "frame is NULL or not laid out");
+    return IGS_OK;
+}
+
+igs::ViewParams view_params(const igs_camera* c, const igs_opts* o, const igs_frame* f) {
+    igs::ViewParams v;
+    std::memcpy(v.R, c->R, sizeof v.R);
+    std::memcpy(v.t, c->t, sizeof v.t);
+    v.fx = c->fx; v.fy = c->fy; v.cx = c->cx; v.cy = c->cy; v.znear = c->znear;
+    for (int a = 0; a < 3; ++a) {
+        double acc = 0.0;
+        for (int r = 0; r < 3; ++r) acc -= (double)c->R[3 * r + a] * (double)c->t[r];
+        v.cam_center[a] = (float)acc;
+    }
+    v.width = c->width; v.height = c->height;
+    v.tile = o->tile;
+    v.tiles_x = f ? f->tiles_x : (c->width + o->tile - 1) / o->tile;
+    v.tiles_y = f ? f->tiles_y : (c->height + o->tile - 1) / o->tile;
+    v.sh_degree = o->sh_degree;
+    v.param_mode = o->param_mode;
+    return v;
+}
+
+igs::BlendParams blend_params(const igs_frame* f, const igs_opts* o) {
+    igs::BlendParams b;
+    b.width = f->width; b.height = f->height; b.tiles_x = f->tiles_x; b.tiles_y = f->tiles_y;
+    b.alpha_min = o->alpha_min; b.alpha_max = o->alpha_max; b.t_min = o->t_min;
+    for (int i = 0; i < 3; ++i) b.bg[i] = o->bg[i];
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t igs_abi_version(void) { return IGS_ABI_VERSION; }
+
+uint64_t igs_launch_count(void) { return igs::g_launches.load(std::memory_order_relaxed); }
+
+const char* igs_last_error(void) { return g_last_error; }
+
+const char* igs_status_string(igs_status s) {
+    switch (s) {
+        case IGS_OK: return "ok";
+        case IGS_ERR_INVALID_ARG: return "invalid argument";
+        case IGS_ERR_OOM: return "buffer too small";
+        case IGS_ERR_CUDA: return "CUDA error";
+        case IGS_ERR_CAPACITY: return "entry capacity exceeded";
+        case IGS_ERR_NOT_READY: return "not ready";
+        case IGS_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+        case IGS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, const igs_opts* opts,
+                            void* workspace, size_t* bytes, igs_frame* frame) {
+    igs_status st;
+    if ((st = check_camera(cam)) != IGS_OK || (st = check_opts(opts)) != IGS_OK) return st;
+    if (!bytes) return fail(IGS_ERR_INVALID_ARG, "bytes is NULL");
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "n out of range");
+    if (capacity < 0 || capacity >= ((int64_t)1 << 30)) return fail(IGS_ERR_INVALID_ARG, "capacity must be < 2^30");
+    const int64_t tx = (cam->width + opts->tile - 1) / opts->tile, ty = (cam->height + opts->tile - 1) / opts->tile;
+    if (tx >= 65536 || ty >= 65536) return fail(IGS_ERR_INVALID_ARG, "too many tiles per axis");
+    const int64_t tiles = tx * ty, P = (int64_t)cam->width * cam->height;
+    size_t off = 0;
+    size_t o_rec = off; off += align256((size_t)n * 32);
+    size_t o_rect = off; off += align256((size_t)n * 8);
+    size_t o_count = off; off += align256((size_t)n * 4);
+    size_t o_dkey = off; off += align256((size_t)n * 4);
+    size_t o_order = off; off += align256((size_t)n * 4);
+    size_t o_offset = off; off += align256((size_t)n * 4);
+    size_t o_tkey = off; off += align256((size_t)capacity * 4);
+    size_t o_vals = off; off += align256((size_t)capacity * 4);
+    size_t o_ranges = off; off += align256((size_t)tiles * 8);
+    size_t o_T = off; off += align256((size_t)P * 4);
+    size_t o_nc = off; off += align256((size_t)P * 4);
+    size_t o_info = off; off += align256(igs::kInfoWords * 4);
+    size_t o_scr = off;
+    const size_t scr = igs::sort_scratch_bytes(n, capacity, tiles);
+    off += align256(scr);
+    *bytes = off;
+    if (!workspace) return IGS_OK;
+    if (!frame) return fail(IGS_ERR_INVALID_ARG, "frame is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return fail(IGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    char* b = static_cast<char*>(workspace);
+    std::memset(frame, 0, sizeof *frame);
+    frame->n = n;
+    frame->capacity = capacity;
+    frame->width = cam->width;
+    frame->height = cam->height;
+    frame->tile = opts->tile;
+    frame->tiles_x = (int32_t)tx;
+    frame->tiles_y = (int32_t)ty;
+    frame->rec = reinterpret_cast<float*>(b + o_rec);
+    frame->rect = reinterpret_cast<uint32_t*>(b + o_rect);
+    frame->count = reinterpret_cast<uint32_t*>(b + o_count);
+    frame->depth_key = reinterpret_cast<uint32_t*>(b + o_dkey);
+    frame->order = reinterpret_cast<uint32_t*>(b + o_order);
+    frame->offset = reinterpret_cast<uint32_t*>(b + o_offset);
+    frame->tile_key = reinterpret_cast<uint32_t*>(b + o_tkey);
+    frame->vals = reinterpret_cast<uint32_t*>(b + o_vals);
+    frame->ranges = reinterpret_cast<uint32_t*>(b + o_ranges);
+    frame->T_final = reinterpret_cast<float*>(b + o_T);
+    frame->n_contrib = reinterpret_cast<uint32_t*>(b + o_nc);
+    frame->info = reinterpret_cast<uint32_t*>(b + o_info);
+    frame->scratch = b + o_scr;
+    frame->scratch_bytes = scr;
+    return IGS_OK;
+}
+
+static igs_status frame_matches(const igs_frame* f, const igs_scene* s, const igs_camera* cam, const igs_opts* o) {
+    if (s && s->n != f->n) return fail(IGS_ERR_INVALID_ARG, "frame laid out for n=%lld, scene has %lld",
+                                       (long long)f->n, (long long)s->n);
+    if (cam && (cam->width != f->width || cam->height != f->height))
+        return fail(IGS_ERR_INVALID_ARG, "frame laid out for another image size");
+    if (o && o->tile != f->tile) return fail(IGS_ERR_INVALID_ARG, "frame laid out for another tile size");
+    return IGS_OK;
+}
+
+igs_status igs_project(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts, igs_frame* frame,
+                       void* stream) {
+    igs_status st;
+    if ((st = check_scene(scene)) || (st = check_camera(cam)) || (st = check_opts(opts)) || (st = check_frame(frame)) ||
+        (st = frame_matches(frame, scene, cam, opts)))
+        return st;
+    const igs::ViewParams vp = view_params(cam, opts, frame);
+    return cuda_status(igs::launch_project(*scene, vp, *frame, (cudaStream_t)stream), "igs_project");
+}
+
+igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* stream) {
+    igs_status st;
+    if ((st = check_opts(opts)) || (st = check_frame(frame)) || (st = frame_matches(frame, nullptr, nullptr, opts)))
+        return st;
+    return cuda_status(igs::launch_bin_sort(*frame, (cudaStream_t)stream), "igs_bin_sort");
+}
+
+igs_status igs_export_keys(const igs_frame* frame, uint64_t* keys, void* stream) {
+    igs_status st;
+    if ((st = check_frame(frame))) return st;
+    if (!keys) return fail(IGS_ERR_INVALID_ARG, "keys is NULL");
+    return cuda_status(igs::launch_export_keys(*frame, keys, (cudaStream_t)stream), "igs_export_keys");
+}
+
+igs_status igs_render_fwd(igs_frame* frame, const igs_opts* opts, float* img, void* stream) {
+    igs_status st;
+    if ((st = check_opts(opts)) || (st = check_frame(frame)) || (st = frame_matches(frame, nullptr, nullptr, opts)))
+        return st;
+    if (!img) return fail(IGS_ERR_INVALID_ARG, "img is NULL");
+    const igs::BlendParams bp = blend_params(frame, opts);
+    return cuda_status(igs::launch_blend_fwd(*frame, bp, img, (cudaStream_t)stream), "igs_render_fwd");
+}
+
+igs_status igs_blend_bwd(const igs_frame* frame, const igs_opts* opts, const float* dL_dimg, float* g2d,
+                         void* stream) {
+    igs_status st;
+    if ((st = check_opts(opts)) || (st = check_frame(frame)) || (st = frame_matches(frame, nullptr, nullptr, opts)))
+        return st;
+    if (!dL_dimg || !g2d) return fail(IGS_ERR_INVALID_ARG, "dL_dimg or g2d is NULL");
+    if (reinterpret_cast<uintptr_t>(g2d) & 15) return fail(IGS_ERR_INVALID_ARG, "g2d must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(g2d, 0, (size_t)frame->n * 32, s);
+    if (e != cudaSuccess) return cuda_status(e, "igs_blend_bwd");
+    const igs::BlendParams bp = blend_params(frame, opts);
+    return cuda_status(igs::launch_blend_bwd(*frame, bp, dL_dimg, g2d, s), "igs_blend_bwd");
+}
+
+igs_status igs_project_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                           const igs_frame* frame, const float* g2d, float* d_means_sigma, float* d_opacity,
+                           float* d_color, void* stream) {
+    igs_status st;
+    if ((st = check_scene(scene)) || (st = check_camera(cam)) || (st = check_opts(opts)) || (st = check_frame(frame)) ||
+        (st = frame_matches(frame, scene, cam, opts)))
+        return st;
+    if (!g2d || !d_means_sigma || !d_opacity || !d_color) return fail(IGS_ERR_INVALID_ARG, "gradient buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(g2d) | reinterpret_cast<uintptr_t>(d_means_sigma)) & 15)
+        return fail(IGS_ERR_INVALID_ARG, "g2d and d_means_sigma must be 16-byte aligned");
+    const igs::ViewParams vp = view_params(cam, opts, frame);
+    return cuda_status(igs::launch_project_bwd(*scene, vp, *frame, g2d, d_means_sigma, d_opacity, d_color,
+                                               (cudaStream_t)stream),
+                       "igs_project_bwd");
+}
+
+igs_status igs_render_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts, const igs_frame* frame,
+                          const float* dL_dimg, float* g2d, float* d_means_sigma, float* d_opacity, float* d_color,
+                          void* stream) {
+    igs_status st;
+    if ((st = check_scene(scene)) || (st = check_camera(cam)) || (st = check_opts(opts)) || (st = check_frame(frame)) ||
+        (st = frame_matches(frame, scene, cam, opts)))
+        return st;
+    if (!dL_dimg || !g2d || !d_means_sigma || !d_opacity || !d_color)
+        return fail(IGS_ERR_INVALID_ARG, "gradient buffer is NULL");
+    if ((st = igs_blend_bwd(frame, opts, dL_dimg, g2d, stream))) return st;
+    return igs_project_bwd(scene, cam, opts, frame, g2d, d_means_sigma, d_opacity, d_color, stream);
+}
+
+igs_status igs_l1_loss(const float* img, const float* target, int64_t count, float* loss, float* dL_dimg,
+                       void* stream) {
+    if (!img || !target || !loss || !dL_dimg || count < 0) return fail(IGS_ERR_INVALID_ARG, "bad l1 arguments");
+    return cuda_status(igs::launch_l1(img, target, count, loss, dL_dimg, (cudaStream_t)stream), "igs_l1_loss");
+}
+
+igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_t count, double lr, double b1, double b2,
+                    double eps, int64_t step, void* stream) {
+    if (!p || !g || !m || !v || count < 0 || step < 1) return fail(IGS_ERR_INVALID_ARG, "bad adam arguments");
+    if (!(b1 >= 0.0 && b1 < 1.0 && b2 >= 0.0 && b2 < 1.0 && lr >= 0.0 && eps > 0.0))
+        return fail(IGS_ERR_INVALID_ARG, "need 0 <= b1, b2 < 1, lr >= 0, eps > 0");
+    const double bc1 = 1.0 - std::pow(b1, (double)step);
+    const double bc2 = 1.0 - std::pow(b2, (double)step);
+    igs::AdamParams a;
+    a.b1 = (float)b1;
+    a.b2 = (float)b2;
+    a.omb1 = (float)(1.0 - b1);
+    a.omb2 = (float)(1.0 - b2);
+    a.step_size = (float)(lr / bc1);
+    a.bc2_sqrt = (float)std::sqrt(bc2);
+    a.eps = (float)eps;
+    return cuda_status(igs::launch_adam(p, g, m, v, count, a, (cudaStream_t)stream), "igs_adam");
+}
+
+igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info, void* stream) {
+    igs_status st;
+    if ((st = check_frame(frame))) return st;
+    if (!host_info) return fail(IGS_ERR_INVALID_ARG, "host_info is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(host_info, frame->info, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "igs_frame_status");
+    if (host_info[igs::kInfoErr] != 0) {
+        const igs_status d = (igs_status)host_info[igs::kInfoErr];
+        return fail(d, "device reported: %s (M needed = %u)", igs_status_string(d), host_info[igs::kInfoNeed]);
+    }
+    return IGS_OK;
+}
+
+igs_status igs_frame_reset_status(igs_frame* frame, void* stream) {
+    igs_status st;
+    if ((st = check_frame(frame))) return st;
+    return cuda_status(cudaMemsetAsync(frame->info, 0, igs::kInfoWords * 4, (cudaStream_t)stream),
+                       "igs_frame_reset_status");
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// Per-tile front-to-back compositing (Eq. 4) and its adjoint.
+//
+// One CTA per tile, one thread per pixel. The tile's entries (already in
+// front-to-back order) are staged in shared memory in batches; each pixel walks
+// them with
+//   alpha = min(alpha_max, o * 2^(-w2 d^2)),  w2 = log2(e) / (2 s^2)   (Eq. 8)
+//   skip if alpha < alpha_min; stop (without blending) if T (1 - alpha) < t_min
+//   C += c alpha T; T *= (1 - alpha)
+// and the CTA leaves the batch loop as soon as every pixel has stopped
+// (__syncthreads_count). The backward pass walks each pixel's blended entries
+// in reverse from n_contrib, recovering T_k = T_{k+1} / (1 - alpha_k) from the
+// saved T_final, and reduces the per-pixel gradient terms of each entry over
+// the tile before one vector atomic per (entry, 4 floats).
+#include "common.cuh"
+
+namespace igs {
+namespace {
+
+struct Alpha {
+    float alpha, g, og, d2, dx, dy;
+};
+
+// The alpha of one (pixel, entry) pair, written with explicit roundings so the
+// forward and backward kernels take exactly the same skip / stop / clamp decisions.
+__device__ __forceinline__ Alpha eval_alpha(float px, float py, float4 a, float alpha_max) {
+    Alpha r;
+    r.dx = __fsub_rn(px, a.x);
+    r.dy = __fsub_rn(py, a.y);
+    r.d2 = __fmaf_rn(r.dx, r.dx, __fmul_rn(r.dy, r.dy));
+    r.g = fast_exp2(-__fmul_rn(a.z, r.d2));
+    r.og = __fmul_rn(a.w, r.g);
+    r.alpha = fminf(alpha_max, r.og);
+    return r;
+}
+
+template <int TS>
+__global__ void __launch_bounds__(TS* TS) k_blend_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                      const float4* __restrict__ rec, BlendParams P,
+                                                      float* __restrict__ img, float* __restrict__ T_final,
+                                                      uint32_t* __restrict__ n_contrib,
+                                                      const uint32_t* __restrict__ info) {
+    constexpr int NT = TS * TS;
+    __shared__ float4 s_a[NT];
+    __shared__ float4 s_c[NT];
+    if (info[kInfoAbort]) return;
+    const int tile = blockIdx.x;
+    const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+    const int x = tx * TS + (threadIdx.x % TS), y = ty * TS + (threadIdx.x / TS);
+    const bool inside = x < P.width && y < P.height;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const uint2 rg = ranges[tile];
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += NT) {
+        if (__syncthreads_count(done) == NT) break;
+        const uint32_t j = b0 + threadIdx.x;
+        if (j < rg.y) {
+            const uint32_t g = vals[j];
+            s_a[threadIdx.x] = rec[2 * g];
+            s_c[threadIdx.x] = rec[2 * g + 1];
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)NT, rg.y - b0);
+        for (int k = 0; k < nb && !done; ++k) {
+            const Alpha a = eval_alpha(px, py, s_a[k], P.alpha_max);
+            if (a.alpha < P.alpha_min) continue;
+            const float Tn = T * (1.f - a.alpha);
+            if (Tn < P.t_min) {
+                done = true;
+                break;
+            }
+            const float4 c = s_c[k];
+            const float w = a.alpha * T;
+            C0 = fmaf(c.x, w, C0);
+            C1 = fmaf(c.y, w, C1);
+            C2 = fmaf(c.z, w, C2);
+            T = Tn;
+            last = b0 - rg.x + k + 1;
+        }
+    }
+    if (!inside) return;
+    const size_t pix = (size_t)y * P.width + x, plane = (size_t)P.width * P.height;
+    img[pix] = fmaf(T, P.bg[0], C0);
+    img[plane + pix] = fmaf(T, P.bg[1], C1);
+    img[2 * plane + pix] = fmaf(T, P.bg[2], C2);
+    T_final[pix] = T;
+    n_contrib[pix] = last;
+}
+
+// Butterfly reduce-scatter of 8 values over a warp in 9 shuffles: afterwards
+// lane l holds the warp total of value (l >> 2) & 7.
+__device__ __forceinline__ float warp_reduce8(float v[8], int lane) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[i] : v[i + 4];
+        const float keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[i] : v[i + 2];
+        const float keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool hi = lane & 4;
+        const float send = hi ? v[0] : v[1];
+        const float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
+constexpr int kBwdBatch = 32;
+
+template <int TS>
+__global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                      const float4* __restrict__ rec, BlendParams P,
+                                                      const float* __restrict__ dL, const float* __restrict__ T_final,
+                                                      const uint32_t* __restrict__ n_contrib,
+                                                      float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
+    constexpr int NT = TS * TS;
+    constexpr int NW = NT / 32;
+    __shared__ float4 s_a[kBwdBatch];
+    __shared__ float4 s_c[kBwdBatch];
+    __shared__ uint32_t s_id[kBwdBatch];
+    __shared__ float s_red[NW][kBwdBatch][8];
+    __shared__ uint32_t s_max;
+    if (info[kInfoAbort]) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x;
+    const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+    const int x = tx * TS + (threadIdx.x % TS), y = ty * TS + (threadIdx.x / TS);
+    const bool inside = x < P.width && y < P.height;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const uint2 rg = ranges[tile];
+    const size_t pix = (size_t)y * P.width + x, plane = (size_t)P.width * P.height;
+    float G0 = 0.f, G1 = 0.f, G2 = 0.f, T = 1.f;
+    uint32_t nc = 0;
+    if (inside) {
+        G0 = dL[pix];
+        G1 = dL[plane + pix];
+        G2 = dL[2 * plane + pix];
+        T = T_final[pix];
+        nc = n_contrib[pix];
+    }
+    float S0 = T * P.bg[0], S1 = T * P.bg[1], S2 = T * P.bg[2];
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nc);
+    if (lane == 0 && wmax) atomicMax(&s_max, wmax);
+    __syncthreads();
+    // no pixel blended anything at or past this entry
+    const uint32_t hi_end = rg.x + min(s_max, rg.y - rg.x);
+    for (uint32_t hi = hi_end; hi > rg.x;) {
+        const uint32_t lo = hi - min((uint32_t)kBwdBatch, hi - rg.x);
+        const int nb = (int)(hi - lo);
+        if (threadIdx.x < nb) {
+            const uint32_t j = hi - 1 - threadIdx.x;  // k = 0 is the last entry of the batch
+            const uint32_t g = vals[j];
+            s_id[threadIdx.x] = g;
+            s_a[threadIdx.x] = rec[2 * g];
+            s_c[threadIdx.x] = rec[2 * g + 1];
+        }
+        __syncthreads();
+        for (int k = 0; k < nb; ++k) {
+            const uint32_t pos = hi - 1 - k - rg.x;  // list position within the tile
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool active = false;
+            if (pos < nc) {
+                const float4 a4 = s_a[k];
+                const Alpha a = eval_alpha(px, py, a4, P.alpha_max);
+                if (a.alpha >= P.alpha_min) {
+                    active = true;
+                    const float4 c = s_c[k];
+                    const float oma = 1.f - a.alpha;
+                    const float inv = 1.f / oma;
+                    const float Tk = T * inv;                    // transmittance before this entry
+                    const float wT = a.alpha * Tk;
+                    v[4] = wT * G0;
+                    v[5] = wT * G1;
+                    v[6] = wT * G2;
+                    const float dalpha = Tk * (G0 * c.x + G1 * c.y + G2 * c.z) - (G0 * S0 + G1 * S1 + G2 * S2) * inv;
+                    S0 = fmaf(wT, c.x, S0);
+                    S1 = fmaf(wT, c.y, S1);
+                    S2 = fmaf(wT, c.z, S2);
+                    T = Tk;
+                    if (a.og <= P.alpha_max) {                   // alpha not clamped
+                        v[3] = dalpha * a.g;                     // d/do
+                        const float dpow = -kLn2 * a.g * (dalpha * a4.w);  // d/d(power), power = w2 d^2
+                        v[2] = dpow * a.d2;                      // d/dw2
+                        const float k2 = -2.f * dpow * a4.z;
+                        v[0] = k2 * a.dx;                        // d/du  (dx = px - u)
+                        v[1] = k2 * a.dy;                        // d/dv
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, active)) {
+                const float r = warp_reduce8(v, lane);
+                if ((lane & 3) == 0) s_red[w][k][lane >> 2] = r;
+            } else if (lane < 8) {
+                s_red[w][k][lane] = 0.f;
+            }
+        }
+        __syncthreads();
+        // sum the warps' partials of each (entry, half) and add them to the entry's Gaussian
+        for (int q = threadIdx.x; q < nb * 2; q += NT) {
+            const int k = q >> 1, h = (q & 1) * 4;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int ww = 0; ww < NW; ++ww) {
+                acc.x += s_red[ww][k][h + 0];
+                acc.y += s_red[ww][k][h + 1];
+                acc.z += s_red[ww][k][h + 2];
+                acc.w += s_red[ww][k][h + 3];
+            }
+            if (acc.x != 0.f || acc.y != 0.f || acc.z != 0.f || acc.w != 0.f)
+                atomicAdd(&g2d[2 * s_id[k] + (h >> 2)], acc);
+        }
+        __syncthreads();
+        hi = lo;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t st) {
+    const unsigned tiles = (unsigned)(f.tiles_x * f.tiles_y);
+    if (tiles == 0) return cudaSuccess;
+    auto rg = reinterpret_cast<const uint2*>(f.ranges);
+    auto rec = reinterpret_cast<const float4*>(f.rec);
+    switch (f.tile) {
+        case 8: k_blend_fwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        case 16: k_blend_fwd<16><<<tiles, 256, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        case 32: k_blend_fwd<32><<<tiles, 1024, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const float* dL, float* g2d, cudaStream_t st) {
+    const unsigned tiles = (unsigned)(f.tiles_x * f.tiles_y);
+    if (tiles == 0) return cudaSuccess;
+    auto rg = reinterpret_cast<const uint2*>(f.ranges);
+    auto rec = reinterpret_cast<const float4*>(f.rec);
+    auto g = reinterpret_cast<float4*>(g2d);
+    switch (f.tile) {
+        case 8: k_blend_bwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 16: k_blend_bwd<16><<<tiles, 256, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 32: k_blend_bwd<32><<<tiles, 1024, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches();
+    return cudaGetLastError();
+}
+
+}  // namespace igs

@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA translation units of libigs.
+// Nothing here is part of the C ABI (include/igs.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "igs.h"
+
+namespace igs {
+
+// Footprint radius in units of the screen-space scale s: o exp(-K^2/2) < 1/255
+// for every o <= 1 (compact support of the particle, Eq. 2).
+constexpr float kRadiusK = 3.33f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Status words of a frame (igs_frame::info).
+enum : int { kInfoM = 0, kInfoKept = 1, kInfoErr = 2, kInfoNeed = 3, kInfoAbort = 4, kInfoWords = 16 };
+
+// Radix sort geometry: 256 threads x 16 keys per block, 8-bit digits.
+constexpr int kSortThreads = 256;
+constexpr int kSortIpt = 16;
+constexpr int kSortTile = kSortThreads * kSortIpt;
+constexpr int kRadix = 256;
+constexpr int kScanThreads = 256;
+constexpr int kScanIpt = 16;
+constexpr int kScanTile = kScanThreads * kScanIpt;
+// Upper bound on polls of a look-back flag before a block gives up (about 0.1 s).
+constexpr int kMaxSpin = 1 << 21;
+
+// Kernel launches made by the library (igs_launch_count).
+extern std::atomic<uint64_t> g_launches;
+inline void count_launches(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Record the first device error of a frame and tell every later step to skip
+// its work (outputs are left untouched).
+__device__ __forceinline__ void record_error(uint32_t* info, uint32_t code) {
+    atomicCAS(&info[kInfoErr], 0u, code);
+    atomicExch(&info[kInfoAbort], 1u);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// 2^x with the SFU (ex2.approx, flush-to-zero): alpha only needs ~22 bits.
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Everything a projection kernel needs about the view (passed by value).
+struct ViewParams {
+    float R[9], t[3];
+    float fx, fy, cx, cy, znear;
+    float cam_center[3];  // -R^T t, for the SH view direction
+    int32_t width, height, tile, tiles_x, tiles_y;
+    int32_t sh_degree, param_mode;
+};
+
+struct BlendParams {
+    int32_t width, height, tiles_x, tiles_y;
+    float alpha_min, alpha_max, t_min;
+    float bg[3];
+};
+
+// ---- launchers (defined in the .cu files, called from api.cu) ----
+cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, cudaStream_t s);
+cudaError_t launch_project_bwd(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d,
+                               float* d_ms, float* d_op, float* d_col, cudaStream_t s);
+cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t s);
+cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t s);
+cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t s);
+cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const float* dL, float* g2d,
+                             cudaStream_t s);
+cudaError_t launch_l1(const float* img, const float* target, int64_t count, float* loss, float* grad,
+                      cudaStream_t s);
+// Adam constants, formed in double on the host and rounded once.
+struct AdamParams {
+    float b1, b2, omb1, omb2;  // beta1, beta2, 1 - beta1, 1 - beta2
+    float step_size;           // lr / (1 - beta1^t)
+    float bc2_sqrt;            // sqrt(1 - beta2^t)
+    float eps;
+};
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, const AdamParams& a,
+                        cudaStream_t s);
+
+// Scratch layout of a frame (byte offsets inside igs_frame::scratch).
+struct SortScratch {
+    uint32_t* dkeys_a;      // [n]
+    uint32_t* dkeys_b;      // [n]
+    uint32_t* dvals_a;      // [n]
+    uint32_t* hist;         // [8][256]: 4 depth passes, then up to 4 tile passes
+    uint32_t* counters;     // [16] virtual block counters
+    uint32_t* status_depth; // [4][blocks(n)][256]
+    uint32_t* status_tile;  // [tile_passes][blocks(capacity)][256]
+    unsigned long long* scan_status;  // [scan blocks(n)]
+    uint32_t* tkey_alt;     // [capacity]
+    uint32_t* vals_alt;     // [capacity]
+    int tile_passes;
+};
+SortScratch sort_scratch(const igs_frame& f);
+size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles);
+int tile_passes_for(int64_t tiles);
+
+}  // namespace igs

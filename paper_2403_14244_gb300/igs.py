@@ -1,0 +1,307 @@
+"""Python binding of libigs (include/igs.h): argument marshalling only.
+
+Every step of the splatting path runs in the library's CUDA kernels; this
+module converts torch tensors to device pointers, passes torch's current
+stream, and raises on any non-OK status. There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+
+Functions keep the C names without the ``igs_`` prefix: ``project``,
+``bin_sort``, ``render_fwd``, ``render_bwd``, ``l1_loss``, ``adam``,
+``export_keys``, ``frame_status``. ``Frame`` owns one view's workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import _build
+
+ABI_VERSION = 1
+_lock = threading.Lock()
+_lib = None
+
+
+class IgsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_NOT_READY, ERR_DEVICE_TIMEOUT, ERR_UNSUPPORTED = range(8)
+
+
+class IgsCamera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("znear", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32)]
+
+
+class IgsOpts(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("sh_degree", C.c_int32), ("param_mode", C.c_int32),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("bg", C.c_float * 3)]
+
+
+class IgsScene(C.Structure):
+    _fields_ = [("means_sigma", C.c_void_p), ("opacity", C.c_void_p), ("color", C.c_void_p), ("n", C.c_int64)]
+
+
+class IgsFrame(C.Structure):
+    _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("width", C.c_int32), ("height", C.c_int32),
+                ("tile", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("_pad", C.c_int32),
+                ("rec", C.c_void_p), ("rect", C.c_void_p), ("count", C.c_void_p), ("depth_key", C.c_void_p),
+                ("order", C.c_void_p), ("offset", C.c_void_p), ("tile_key", C.c_void_p), ("vals", C.c_void_p),
+                ("ranges", C.c_void_p), ("T_final", C.c_void_p), ("n_contrib", C.c_void_p), ("info", C.c_void_p),
+                ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t)]
+
+
+SYMBOLS = {
+    # name: (restype, argtypes)
+    "igs_abi_version": (C.c_int32, []),
+    "igs_launch_count": (C.c_uint64, []),
+    "igs_last_error": (C.c_char_p, []),
+    "igs_status_string": (C.c_char_p, [C.c_int]),
+    "igs_frame_layout": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.c_void_p,
+                                   C.POINTER(C.c_size_t), C.POINTER(IgsFrame)]),
+    "igs_project": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.POINTER(IgsFrame),
+                              C.c_void_p]),
+    "igs_bin_sort": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(IgsOpts), C.c_void_p]),
+    "igs_export_keys": (C.c_int, [C.POINTER(IgsFrame), C.c_void_p, C.c_void_p]),
+    "igs_render_fwd": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(IgsOpts), C.c_void_p, C.c_void_p]),
+    "igs_render_bwd": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.POINTER(IgsFrame),
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "igs_blend_bwd": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(IgsOpts), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "igs_project_bwd": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
+                                  C.POINTER(IgsFrame), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "igs_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "igs_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double,
+                           C.c_double, C.c_double, C.c_int64, C.c_void_p]),
+    "igs_frame_status": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_uint32), C.c_void_p]),
+    "igs_frame_reset_status": (C.c_int, [C.POINTER(IgsFrame), C.c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libigs.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libigs.so not found at {path}: build it with __graft_entry__.build()")
+            lib = C.CDLL(path)
+            for name, (res, args) in SYMBOLS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            if lib.igs_abi_version() != ABI_VERSION:
+                raise RuntimeError("libigs ABI version mismatch")
+            _lib = lib
+    return _lib
+
+
+def _check(status, what):
+    if status != OK:
+        msg = load().igs_last_error().decode(errors="replace")
+        raise IgsError(status, f"{what}: {msg}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------ structures ----
+
+def camera(cam) -> IgsCamera:
+    """igs_camera from an object with R (3x3), t (3), fx, fy, cx, cy, znear, width, height."""
+    c = IgsCamera()
+    R = [float(x) for x in torch.as_tensor(cam.R, dtype=torch.float32).reshape(9).tolist()]
+    t = [float(x) for x in torch.as_tensor(cam.t, dtype=torch.float32).reshape(3).tolist()]
+    c.R[:] = R
+    c.t[:] = t
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.znear = float(getattr(cam, "znear", 0.01))
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def opts(tile=16, sh_degree=-1, param_mode=0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4,
+         bg=(0.0, 0.0, 0.0)) -> IgsOpts:
+    o = IgsOpts()
+    o.tile, o.sh_degree, o.param_mode = int(tile), int(sh_degree), int(param_mode)
+    o.alpha_min, o.alpha_max, o.t_min = alpha_min, alpha_max, t_min
+    o.bg[:] = [float(x) for x in bg]
+    return o
+
+
+class Scene:
+    """Device scene: means_sigma [N,4], opacity [N], color [N,C] (FP32, CUDA)."""
+
+    def __init__(self, means_sigma, opacity, color):
+        self.means_sigma, self.opacity, self.color = means_sigma, opacity, color
+        self.n = int(means_sigma.shape[0])
+        s = IgsScene()
+        s.means_sigma = _ptr(means_sigma).value if self.n else None
+        s.opacity = _ptr(opacity).value if self.n else None
+        s.color = _ptr(color).value if self.n else None
+        s.n = self.n
+        self.struct = s
+
+    @staticmethod
+    def from_numpy(sc, device="cuda"):
+        return Scene(torch.from_numpy(sc.means_sigma).to(device), torch.from_numpy(sc.opacity).to(device),
+                     torch.from_numpy(sc.color).to(device))
+
+
+_DT = {"f32": torch.float32, "u32": torch.int32, "u64": torch.int64}
+
+
+class Frame:
+    """One view's workspace, carved by igs_frame_layout from one uint8 tensor."""
+
+    def __init__(self, n, capacity, cam, o, device="cuda"):
+        lib = load()
+        self.cam = cam if isinstance(cam, IgsCamera) else camera(cam)
+        self.opts = o
+        nbytes = C.c_size_t(0)
+        _check(lib.igs_frame_layout(int(n), int(capacity), C.byref(self.cam), C.byref(o), None, C.byref(nbytes),
+                                    None), "igs_frame_layout")
+        self.nbytes = int(nbytes.value)
+        self.ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.ws.data_ptr()
+        self._shift = (-base) % 256
+        self.struct = IgsFrame()
+        _check(lib.igs_frame_layout(int(n), int(capacity), C.byref(self.cam), C.byref(o),
+                                    C.c_void_p(base + self._shift), C.byref(nbytes), C.byref(self.struct)),
+               "igs_frame_layout")
+        self.n, self.capacity = int(n), int(capacity)
+        self.width, self.height = self.struct.width, self.struct.height
+        self.tiles_x, self.tiles_y = self.struct.tiles_x, self.struct.tiles_y
+        self.tiles = self.tiles_x * self.tiles_y
+
+    def view(self, field, count, dtype=torch.int32):
+        """A tensor view of `count` elements of a frame buffer (for inspection)."""
+        addr = getattr(self.struct, field)
+        off = addr - self.ws.data_ptr()
+        nb = count * torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + nb].view(dtype)
+
+    # typed views of the documented buffers
+    def rec(self):
+        return self.view("rec", self.n * 8, torch.float32).view(self.n, 8)
+
+    def count(self):
+        return self.view("count", self.n)
+
+    def depth_key(self):
+        return self.view("depth_key", self.n)
+
+    def rect(self):
+        return self.view("rect", self.n * 2).view(self.n, 2)
+
+    def order(self):
+        return self.view("order", self.n)
+
+    def tile_key(self, m):
+        return self.view("tile_key", m)
+
+    def vals(self, m):
+        return self.view("vals", m)
+
+    def ranges(self):
+        return self.view("ranges", self.tiles * 2).view(self.tiles, 2)
+
+    def T_final(self):
+        return self.view("T_final", self.width * self.height, torch.float32).view(self.height, self.width)
+
+    def n_contrib(self):
+        return self.view("n_contrib", self.width * self.height).view(self.height, self.width)
+
+    def info(self):
+        return self.view("info", 16)
+
+
+# ------------------------------------------------------------ entry points --
+
+def project(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, stream=None):
+    _check(load().igs_project(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
+                              _stream(stream)), "igs_project")
+
+
+def bin_sort(frame: Frame, o: IgsOpts, stream=None):
+    _check(load().igs_bin_sort(C.byref(frame.struct), C.byref(o), _stream(stream)), "igs_bin_sort")
+
+
+def export_keys(frame: Frame, stream=None):
+    keys = torch.empty(max(frame.capacity, 1), dtype=torch.int64, device=frame.ws.device)
+    _check(load().igs_export_keys(C.byref(frame.struct), _ptr(keys), _stream(stream)), "igs_export_keys")
+    return keys
+
+
+def render_fwd(frame: Frame, o: IgsOpts, img, stream=None):
+    _check(load().igs_render_fwd(C.byref(frame.struct), C.byref(o), _ptr(img), _stream(stream)), "igs_render_fwd")
+
+
+def render_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, dL_dimg, g2d, d_means_sigma, d_opacity,
+               d_color, stream=None):
+    _check(load().igs_render_bwd(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
+                                 _ptr(dL_dimg), _ptr(g2d), _ptr(d_means_sigma), _ptr(d_opacity), _ptr(d_color),
+                                 _stream(stream)), "igs_render_bwd")
+
+
+def blend_bwd(frame: Frame, o: IgsOpts, dL_dimg, g2d, stream=None):
+    _check(load().igs_blend_bwd(C.byref(frame.struct), C.byref(o), _ptr(dL_dimg), _ptr(g2d), _stream(stream)),
+           "igs_blend_bwd")
+
+
+def project_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, d_means_sigma, d_opacity, d_color,
+                stream=None):
+    _check(load().igs_project_bwd(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
+                                  _ptr(g2d), _ptr(d_means_sigma), _ptr(d_opacity), _ptr(d_color),
+                                  _stream(stream)), "igs_project_bwd")
+
+
+def l1_loss(img, target, loss, dL_dimg, stream=None):
+    _check(load().igs_l1_loss(_ptr(img), _ptr(target), int(img.numel()), _ptr(loss), _ptr(dL_dimg),
+                              _stream(stream)), "igs_l1_loss")
+
+
+def adam(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _check(load().igs_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), int(p.numel()), lr, b1, b2, eps, int(step),
+                           _stream(stream)), "igs_adam")
+
+
+def frame_status(frame: Frame, stream=None):
+    """(status, [M, kept, error, M needed]); synchronises the stream."""
+    info = (C.c_uint32 * 4)()
+    st = load().igs_frame_status(C.byref(frame.struct), info, _stream(stream))
+    if st not in (OK, ERR_CAPACITY, ERR_DEVICE_TIMEOUT):
+        _check(st, "igs_frame_status")
+    return st, list(info)
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process."""
+    return int(load().igs_launch_count())
+
+
+def frame_reset_status(frame: Frame, stream=None):
+    _check(load().igs_frame_reset_status(C.byref(frame.struct), _stream(stream)), "igs_frame_reset_status")

@@ -1,0 +1,172 @@
+"""One-view rendering and training on top of the C ABI.
+
+``Renderer`` chains igs_project -> igs_bin_sort -> igs_render_fwd for a view,
+keeps one frame workspace per image size, and sizes the (Gaussian, tile) entry
+capacity from the last frame it saw (a frame that overflows reports the entries
+it needed and is redone with room to spare). ``IGSRender`` is the
+torch.autograd.Function over the same path; ``TrainStep`` is one
+forward + L1 + backward + Adam step with no host synchronisation except the
+optional loss read.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import igs
+
+DEFAULT_MIN_CAPACITY = 1 << 16
+
+
+class Renderer:
+    def __init__(self, tile=16, sh_degree=-1, param_mode=0, bg=(0.0, 0.0, 0.0), alpha_min=1.0 / 255.0,
+                 alpha_max=0.99, t_min=1e-4, device="cuda"):
+        self.opts = igs.opts(tile=tile, sh_degree=sh_degree, param_mode=param_mode, alpha_min=alpha_min,
+                             alpha_max=alpha_max, t_min=t_min, bg=bg)
+        self.device = device
+        self._frames = {}
+        self._cap_hint = {}
+
+    def frame(self, n, cam, capacity):
+        key = (n, cam.width, cam.height)
+        f = self._frames.get(key)
+        if f is None or f.capacity < capacity:
+            f = igs.Frame(n, capacity, cam, self.opts, self.device)
+            self._frames[key] = f
+        f.cam = cam
+        return f
+
+    def capacity_for(self, n, cam):
+        key = (n, cam.width, cam.height)
+        hint = self._cap_hint.get(key)
+        if hint is None:
+            # first frame of this size: a generous guess, corrected after the fact
+            hint = max(DEFAULT_MIN_CAPACITY, 16 * n)
+        return int(min(hint, (1 << 30) - 1))
+
+    def note_needed(self, n, cam, needed):
+        """Remember the entries a view of this size needed; the capacity only grows."""
+        key = (n, cam.width, cam.height)
+        want = int(min(math.ceil(needed * 1.15) + 4096, (1 << 30) - 1))
+        self._cap_hint[key] = max(want, self._cap_hint.get(key, 0))
+
+    def run_forward(self, scene: igs.Scene, cam, img=None, check=True, stream=None):
+        """project + bin_sort + render_fwd. Returns (img [3,H,W], frame). With
+        check=True the stream is synchronised to read the frame status, and an
+        overflowing frame is redone with the capacity it reported."""
+        c = cam if isinstance(cam, igs.IgsCamera) else igs.camera(cam)
+        if img is None:
+            img = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device)
+        for _ in range(3):
+            f = self.frame(scene.n, c, self.capacity_for(scene.n, c))
+            igs.project(scene, c, self.opts, f, stream)
+            igs.bin_sort(f, self.opts, stream)
+            igs.render_fwd(f, self.opts, img, stream)
+            if not check:
+                return img, f
+            st, info = igs.frame_status(f, stream)
+            if st == igs.OK:
+                self.note_needed(scene.n, c, max(info[0], 1))
+                return img, f
+            if st != igs.ERR_CAPACITY:
+                raise igs.IgsError(st, "device error during render")
+            self.note_needed(scene.n, c, info[3])
+        raise igs.IgsError(igs.ERR_CAPACITY, "entry capacity kept overflowing")
+
+    def run_backward(self, scene: igs.Scene, cam, frame, dL_dimg, grads=None, stream=None):
+        """Gradients w.r.t. means_sigma [N,4], opacity [N], color [N,C] (overwritten)."""
+        c = cam if isinstance(cam, igs.IgsCamera) else igs.camera(cam)
+        n = scene.n
+        if grads is None:
+            grads = (torch.empty_like(scene.means_sigma), torch.empty_like(scene.opacity),
+                     torch.empty_like(scene.color))
+        g2d = torch.empty((n, 8), dtype=torch.float32, device=self.device)
+        igs.render_bwd(scene, c, self.opts, frame, dL_dimg.contiguous(), g2d, *grads, stream)
+        return grads
+
+
+class IGSRender(torch.autograd.Function):
+    """img = render(means_sigma, opacity, color; camera) with the CUDA adjoint."""
+
+    @staticmethod
+    def forward(ctx, means_sigma, opacity, color, renderer: Renderer, cam):
+        scene = igs.Scene(means_sigma.contiguous(), opacity.contiguous(), color.contiguous())
+        img, frame = renderer.run_forward(scene, cam, check=True)
+        ctx.renderer, ctx.cam, ctx.frame, ctx.scene = renderer, cam, frame, scene
+        ctx.save_for_backward(means_sigma, opacity, color)
+        return img
+
+    @staticmethod
+    def backward(ctx, dimg):
+        d_ms, d_op, d_col = ctx.renderer.run_backward(ctx.scene, ctx.cam, ctx.frame, dimg.contiguous())
+        return d_ms, d_op, d_col, None, None
+
+
+def render(means_sigma, opacity, color, renderer: Renderer, cam):
+    return IGSRender.apply(means_sigma, opacity, color, renderer, cam)
+
+
+class TrainStep:
+    """Flat parameter buffer [N*(4+1+C)] with views means_sigma [N,4] (log sigma),
+    opacity [N] (logit), color [N,C] (SH); Adam state m, v of the same shape.
+    step(cam, target) runs forward, L1, backward and Adam on the GPU."""
+
+    def __init__(self, means_sigma, opacity, color, sh_degree, tile=16, lr=1e-3, device="cuda"):
+        n = means_sigma.shape[0]
+        C = color.shape[1]
+        self.n, self.C = n, C
+        self.flat = torch.empty(n * (5 + C), dtype=torch.float32, device=device)
+        self.grad = torch.zeros_like(self.flat)
+        self.m = torch.zeros_like(self.flat)
+        self.v = torch.zeros_like(self.flat)
+        self.ms, self.op, self.col = self._views(self.flat)
+        self.g_ms, self.g_op, self.g_col = self._views(self.grad)
+        self.ms.copy_(means_sigma)
+        self.op.copy_(opacity)
+        self.col.copy_(color)
+        self.scene = igs.Scene(self.ms, self.op, self.col)
+        self.renderer = Renderer(tile=tile, sh_degree=sh_degree, param_mode=1, device=device)
+        self.g2d = torch.empty((n, 8), dtype=torch.float32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.lr = lr
+        self.t = 0
+        self._img = {}
+        self._dimg = {}
+
+    def _views(self, flat):
+        n, C = self.n, self.C
+        return (flat[:4 * n].view(n, 4), flat[4 * n:5 * n], flat[5 * n:].view(n, C))
+
+    def step(self, cam, target, check=False, stream=None, marks=None):
+        """One training step on `stream`. `marks`, if given, is called with a
+        stage name after each stage is enqueued (the benchmark records CUDA
+        events there)."""
+        c = cam if isinstance(cam, igs.IgsCamera) else igs.camera(cam)
+        key = (c.width, c.height)
+        if key not in self._img:
+            self._img[key] = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.flat.device)
+            self._dimg[key] = torch.empty_like(self._img[key])
+        img, dimg = self._img[key], self._dimg[key]
+        r = self.renderer
+        mark = marks or (lambda name: None)
+        if check:
+            img, frame = r.run_forward(self.scene, c, img=img, check=True, stream=stream)
+        else:
+            frame = r.frame(self.scene.n, c, r.capacity_for(self.scene.n, c))
+            igs.project(self.scene, c, r.opts, frame, stream)
+            mark("project")
+            igs.bin_sort(frame, r.opts, stream)
+            mark("bin_sort")
+            igs.render_fwd(frame, r.opts, img, stream)
+        mark("blend_fwd")
+        igs.l1_loss(img, target, self.loss, dimg, stream)
+        mark("l1")
+        igs.blend_bwd(frame, r.opts, dimg, self.g2d, stream)
+        mark("blend_bwd")
+        igs.project_bwd(self.scene, c, r.opts, frame, self.g2d, self.g_ms, self.g_op, self.g_col, stream)
+        mark("project_bwd")
+        self.t += 1
+        igs.adam(self.flat, self.grad, self.m, self.v, self.t, lr=self.lr, stream=stream)
+        mark("adam")
+        return frame

@@ -9,8 +9,9 @@ def scene_from(means, sigma, opac, color, sh_degree=-1, log_params=False):
     ms = np.zeros((n, 4), np.float32)
     ms[:, :3] = np.asarray(means, np.float64).reshape(n, 3)
     ms[:, 3] = np.asarray(sigma, np.float64)
+    C = 3 if sh_degree < 0 else 3 * (sh_degree + 1) ** 2
     return scenes.Scene(means_sigma=ms, opacity=np.asarray(opac, np.float32).reshape(n),
-                        color=np.ascontiguousarray(np.asarray(color, np.float32).reshape(n, -1)),
+                        color=np.ascontiguousarray(np.asarray(color, np.float32).reshape(n, C)),
                         sh_degree=sh_degree, log_params=log_params)
 
 

@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and
+exports every function include/igs.h declares; the host-only logic (frame
+sizing, argument checks, status strings) behaves as documented."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2403_14244_gb300 import _build, igs, scenes
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "igs.h")
+
+
+def _declared():
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^IGS_API\s+[\w\s\*]+?\b(igs_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for want in ("igs_project", "igs_bin_sort", "igs_render_fwd", "igs_render_bwd", "igs_l1_loss", "igs_adam",
+                 "igs_frame_layout", "igs_frame_status"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = C.CDLL(_build.build())
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) <= set(igs.SYMBOLS)           # the binding covers the whole ABI
+
+
+def test_abi_version_and_status_strings():
+    lib = igs.load()
+    assert lib.igs_abi_version() == igs.ABI_VERSION
+    assert lib.igs_status_string(igs.OK) == b"ok"
+    assert lib.igs_status_string(igs.ERR_CAPACITY) == b"entry capacity exceeded"
+
+
+def test_frame_layout_sizes_without_gpu():
+    lib = igs.load()
+    sc, cam = scenes.workload_forward_4k()
+    c = igs.camera(cam)
+    nb = C.c_size_t(0)
+    assert lib.igs_frame_layout(4096, 1 << 16, C.byref(c), C.byref(igs.opts(tile=16)), None, C.byref(nb), None) == 0
+    small = nb.value
+    assert small % 256 == 0
+    assert lib.igs_frame_layout(4096, 1 << 20, C.byref(c), C.byref(igs.opts(tile=16)), None, C.byref(nb), None) == 0
+    assert nb.value > small + 8 * ((1 << 20) - (1 << 16))    # two entry buffers and their double buffers grow
+
+
+@pytest.mark.parametrize("bad", ["tile", "fx", "capacity", "n", "sh"])
+def test_frame_layout_rejects_bad_arguments(bad):
+    lib = igs.load()
+    sc, cam = scenes.workload_forward_4k()
+    o = igs.opts(tile=16)
+    n, cap = 4096, 1 << 16
+    if bad == "tile":
+        o = igs.opts(tile=12)
+    elif bad == "fx":
+        cam.fy = cam.fx + 1
+    elif bad == "capacity":
+        cap = 1 << 30
+    elif bad == "n":
+        n = -1
+    elif bad == "sh":
+        o = igs.opts(tile=16, sh_degree=4)
+    nb = C.c_size_t(0)
+    st = lib.igs_frame_layout(n, cap, C.byref(igs.camera(cam)), C.byref(o), None, C.byref(nb), None)
+    assert st == igs.ERR_INVALID_ARG
+    assert lib.igs_last_error()                             # a message for the caller
+
+
+def test_null_arguments_rejected_before_any_launch():
+    lib = igs.load()
+    assert lib.igs_project(None, None, None, None, None) == igs.ERR_INVALID_ARG
+    assert lib.igs_bin_sort(None, None, None) == igs.ERR_INVALID_ARG
+    assert lib.igs_render_fwd(None, None, None, None) == igs.ERR_INVALID_ARG
+    assert lib.igs_l1_loss(None, None, 0, None, None, None) == igs.ERR_INVALID_ARG
+    assert lib.igs_adam(None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, 1, None) == igs.ERR_INVALID_ARG
+
+
+def test_product_path_has_no_oracle_or_cpu_fallback():
+    pkg = os.path.dirname(igs.__file__)
+    for root, _, files in os.walk(pkg):
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                with open(os.path.join(root, name)) as f:
+                    text = f.read()
+                assert "import oracle" not in text and "from oracle" not in text, name
+                assert "liboracle" not in text, name

@@ -1,0 +1,128 @@
+"""GPU parity of the adjoint (backward blend + projection backward) against
+the oracle's FP64 analytic gradients (themselves pinned by finite differences
+and torch autograd), and of the L1 loss and Adam kernels."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_14244_gb300 import igs, scenes
+from paper_2403_14244_gb300.render import TrainStep
+from tests import _gpu
+from tests._tiny import random_small
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_grads(sc, cam, W, tile=16, bg=(0.0, 0.0, 0.0)):
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile, bg=bg)
+    dimg = torch.from_numpy(np.ascontiguousarray(W, np.float32)).cuda()
+    d_ms, d_op, d_col = r.run_backward(scene, cam, f, dimg)
+    torch.cuda.synchronize()
+    return img, d_ms.cpu().numpy(), d_op.cpu().numpy(), d_col.cpu().numpy()
+
+
+def _compare(sc, cam, W, tile=16, bg=(0.0, 0.0, 0.0), **tol):
+    img, d_ms, d_op, d_col = _gpu_grads(sc, cam, W, tile, bg)
+    ref = oracle.backward(sc, cam, W, mode=1, bg=bg)
+    out = {}
+    out["means"] = _gpu.grad_close(d_ms[:, :3], ref["d_means"], "means", **tol)
+    out["sigma"] = _gpu.grad_close(d_ms[:, 3], ref["d_sigma"], "sigma", **tol)
+    out["opacity"] = _gpu.grad_close(d_op, ref["d_opac"], "opacity", **tol)
+    out["color"] = _gpu.grad_close(d_col, ref["d_color"], "color", **tol)
+    return out, ref
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_backward_rgb_small(tile):
+    sc, cam = random_small(300, 41, w=80, h=60, spread=0.8)
+    W = np.random.default_rng(1).normal(size=(3, cam.height, cam.width))
+    _compare(sc, cam, W, tile=tile)
+
+
+def test_backward_sh3_log_background():
+    sc, cam = random_small(300, 42, w=80, h=60, sh_degree=3, log_params=True, spread=0.8)
+    W = np.random.default_rng(2).normal(size=(3, cam.height, cam.width))
+    _compare(sc, cam, W, bg=(0.25, 0.5, 0.125))
+
+
+def test_backward_clamp_active():
+    sc, cam = random_small(200, 43, w=64, h=48, spread=0.6)
+    sc.opacity[::3] = np.float32(0.999)
+    W = np.random.default_rng(3).normal(size=(3, cam.height, cam.width))
+    _compare(sc, cam, W)
+
+
+def test_backward_clustered_1080p_full():
+    """Full 1M-Gaussian SH3 1080p case with the L1 gradient of a seeded target;
+    every Gaussian in norm, and a 64-Gaussian subset (seed 202, among those that
+    were blended somewhere) element by element."""
+    sc, cam, target = scenes.workload_fwd_bwd_1m()
+    r, f, scene, img = _gpu.run_forward(sc, cam)
+    ref_fwd = oracle.render(sc, cam, mode=1)
+    # the same dL/dimg on both sides: the oracle's L1 gradient of its own image
+    _, G = oracle.l1(ref_fwd["img"], target)
+    img_gpu, d_ms, d_op, d_col = _gpu_grads(sc, cam, G)
+    ref = oracle.backward(sc, cam, G, mode=1)
+    _gpu.grad_close(d_ms[:, :3], ref["d_means"], "means")
+    _gpu.grad_close(d_ms[:, 3], ref["d_sigma"], "sigma")
+    _gpu.grad_close(d_op, ref["d_opac"], "opacity")
+    _gpu.grad_close(d_col, ref["d_color"], "color")
+    hit = np.nonzero(np.abs(ref["g2d"]).sum(axis=1) > 0)[0]
+    sub = np.random.default_rng(202).choice(hit, size=64, replace=False)
+    for name, g, w in (("means", d_ms[sub, :3], ref["d_means"][sub]), ("sigma", d_ms[sub, 3], ref["d_sigma"][sub]),
+                       ("opacity", d_op[sub], ref["d_opac"][sub]), ("color", d_col[sub], ref["d_color"][sub])):
+        _gpu.grad_close(g, w, name + "[subset]", rel_norm=2e-3, elem_rel=2e-3, elem_abs_frac=2e-3)
+
+
+def test_l1_loss_matches_oracle():
+    rng = np.random.default_rng(5)
+    img = rng.uniform(size=(3, 70, 90)).astype(np.float32)
+    tg = rng.uniform(size=(3, 70, 90)).astype(np.float32)
+    tg[0, :5, :5] = img[0, :5, :5]
+    ti, tt = torch.from_numpy(img).cuda(), torch.from_numpy(tg).cuda()
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(ti)
+    igs.l1_loss(ti, tt, loss, grad)
+    want, g_ref = oracle.l1(img.astype(np.float64), tg)
+    assert float(loss) == pytest.approx(want, rel=1e-5)
+    np.testing.assert_allclose(grad.cpu().numpy(), g_ref, rtol=1e-6)
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(6)
+    n = 10_001                                                   # odd: vector body plus scalar tail
+    p0 = rng.normal(size=n).astype(np.float32)
+    p, m, v = (torch.from_numpy(p0).cuda(), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda"))
+    rp, rm, rv = p0.astype(np.float64), np.zeros(n), np.zeros(n)
+    for t in range(1, 6):
+        g = (rng.normal(size=n) * (0.01 if t % 2 else 3.0)).astype(np.float32)
+        igs.adam(p, torch.from_numpy(g).cuda(), m, v, t, lr=1e-3)
+        rp, rm, rv = oracle.adam(rp, g, rm, rv, lr=1e-3, t=t)
+    np.testing.assert_allclose(p.cpu().numpy(), rp, rtol=0, atol=2e-6)
+    # m mixes terms of size (1 - b1) |g| <= 0.3 whose sum can cancel: a few FP32 ulp of 0.3
+    np.testing.assert_allclose(m.cpu().numpy(), rm, rtol=1e-5, atol=4 * np.spacing(np.float32(0.3)))
+    np.testing.assert_allclose(v.cpu().numpy(), rv, rtol=1e-5, atol=1e-12)
+
+
+def test_train_step_matches_oracle():
+    """One full step (forward, L1, backward, Adam) on a log-parameter SH3 scene."""
+    sc, cam = random_small(500, 44, w=96, h=64, sh_degree=3, log_params=True, spread=0.8)
+    target = scenes.target_image(cam.width, cam.height, 9)
+    ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                   torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-3)
+    ts.step(cam, torch.from_numpy(target).cuda(), check=True)
+    torch.cuda.synchronize()
+    ref_fwd = oracle.render(sc, cam, mode=1)
+    loss_ref, G = oracle.l1(ref_fwd["img"], target)
+    assert float(ts.loss) == pytest.approx(loss_ref, rel=1e-4)
+    ref = oracle.backward(sc, cam, G, mode=1)
+    g_ref = np.concatenate([np.concatenate([ref["d_means"], ref["d_sigma"][:, None]], 1).reshape(-1),
+                            ref["d_opac"], ref["d_color"].reshape(-1)])
+    g = ts.grad.cpu().numpy()
+    _gpu.grad_close(g, g_ref, "flat grad")
+    p0 = np.concatenate([sc.means_sigma.reshape(-1), sc.opacity, sc.color.reshape(-1)]).astype(np.float64)
+    p_ref, _, _ = oracle.adam(p0, g_ref, np.zeros_like(p0), np.zeros_like(p0), lr=1e-3, t=1)
+    # first Adam step moves every parameter with a non-tiny gradient by ~lr * sign(g)
+    moved = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+    np.testing.assert_allclose(ts.flat.cpu().numpy()[moved], p_ref[moved], atol=2e-6)

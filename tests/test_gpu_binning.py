@@ -1,0 +1,118 @@
+"""GPU parity of the key path: projection, culling, tile rectangles, the
+front-to-back (tile, depth) order and per-tile ranges, bit-exact against the
+oracle's canonical FP32 key path and stable sort."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_14244_gb300 import igs, scenes
+from tests import _gpu
+from tests._tiny import random_small, scene_from, small_camera
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_bitexact(sc, cam, tile):
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile)
+    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile)
+    count = f.count().cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(count, p["count"].astype(np.uint32))
+    kept = p["count"] > 0
+    rec = f.rec().cpu().numpy()
+    np.testing.assert_array_equal(rec[kept, 0].view(np.uint32), p["u"][kept].view(np.uint32))
+    np.testing.assert_array_equal(rec[kept, 1].view(np.uint32), p["v"][kept].view(np.uint32))
+    np.testing.assert_array_equal(rec[kept, 7].view(np.uint32), p["s"][kept].view(np.uint32))
+    dk = f.depth_key().cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(dk[kept], p["depth"][kept].view(np.uint32))
+    assert np.all(dk[~kept] == 0xFFFFFFFF)
+    rect = f.rect().cpu().numpy().view(np.uint32)
+    x0, y0, x1, y1 = rect[:, 0] & 0xFFFF, rect[:, 0] >> 16, rect[:, 1] & 0xFFFF, rect[:, 1] >> 16
+    np.testing.assert_array_equal(np.stack([x0, y0, x1, y1], 1)[kept], p["rect"][kept])
+    keys, vals, ranges, info = _gpu.frame_keys(f)
+    k_ref, v_ref, r_ref = oracle.keys(p, cam, tile)
+    assert info[0] == len(k_ref)
+    assert info[1] == int(kept.sum())
+    np.testing.assert_array_equal(keys, k_ref)
+    np.testing.assert_array_equal(vals, v_ref)
+    np.testing.assert_array_equal(ranges, r_ref)
+    return len(k_ref)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_keys_forward_4k(tile):
+    sc, cam = scenes.workload_forward_4k()
+    m = _check_bitexact(sc, cam, tile)
+    assert m > 4096
+
+
+def test_keys_ragged_large():
+    # 1297 x 840 (ragged edge tiles), 300k Gaussians: many sort blocks, partial last block
+    sc = scenes.uniform_scene(300_000, 7)
+    cam = scenes.ring_cameras(16, 4.0, 1297, 840, 1100.0, cx=648.5, cy=420.0)[3]
+    assert _check_bitexact(sc, cam, 16) > 1_000_000
+
+
+def test_keys_clustered_sh_1080p_full():
+    sc, cam, _ = scenes.workload_fwd_bwd_1m()
+    _check_bitexact(sc, cam, 16)
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+def test_keys_clustered_tiles(tile):
+    sc = scenes.clustered_scene(200_000, 12)
+    cam = scenes.pinhole((0.3, -0.1, -3.5), 1920, 1080, 1100.0)
+    _check_bitexact(sc, cam, tile)
+
+
+def test_keys_edge_cases():
+    cam = small_camera(40, 24, 64.0)
+    # one Gaussian covering every tile, one off screen, one behind the near plane,
+    # one with opacity below 1/255, one exactly on a tile corner, duplicates of depth
+    means = [[0, 0, 0], [30, 0, 0], [0, 0, -3.999], [0.1, 0.1, 0], [0.5, 0.25, 0], [0.5, 0.25, 0]]
+    sigma = [5.0, 0.1, 0.1, 0.1, 0.05, 0.05]
+    opac = [0.5, 0.5, 0.5, 0.003, 0.7, 0.7]
+    col = np.random.default_rng(0).uniform(size=(6, 3))
+    sc = scene_from(means, sigma, opac, col)
+    for tile in (8, 16, 32):
+        _check_bitexact(sc, cam, tile)
+
+
+def test_empty_and_all_culled():
+    cam = small_camera(48, 32, 64.0)
+    sc = scene_from(np.zeros((0, 3)), [], [], np.zeros((0, 3)))
+    r, f, scene, img = _gpu.run_forward(sc, cam)
+    assert np.all(img == 0.0)
+    sc = scene_from([[0, 0, -10.0]] * 5, [0.1] * 5, [0.5] * 5, np.ones((5, 3)))   # all behind the camera
+    r, f, scene, img = _gpu.run_forward(sc, cam, bg=(0.25, 0.5, 1.0))
+    np.testing.assert_array_equal(img, np.broadcast_to(np.array([0.25, 0.5, 1.0])[:, None, None], img.shape))
+    st, info = igs.frame_status(f)
+    assert st == igs.OK and info[0] == 0 and info[1] == 0
+
+
+def test_capacity_overflow_is_reported():
+    sc, cam = scenes.workload_forward_4k()
+    scene = _gpu.to_device(sc)
+    o = igs.opts(tile=16)
+    c = igs.camera(cam)
+    f = igs.Frame(scene.n, 1000, c, o)
+    img = torch.full((3, 256, 256), -1.0, device="cuda")
+    igs.project(scene, c, o, f)
+    igs.bin_sort(f, o)
+    igs.render_fwd(f, o, img)
+    st, info = igs.frame_status(f)
+    p = oracle.project(sc.means_sigma, sc.opacity, cam, 16)
+    assert st == igs.ERR_CAPACITY
+    assert info[3] == int(p["count"].sum())
+    assert torch.all(img == -1.0)                      # outputs left untouched
+
+
+def test_invalid_arguments_rejected():
+    sc, cam = scenes.workload_forward_4k()
+    o = igs.opts(tile=12)
+    with pytest.raises(igs.IgsError) as e:
+        igs.Frame(sc.n, 1 << 16, igs.camera(cam), o)
+    assert e.value.status == igs.ERR_INVALID_ARG
+    cam.fy = cam.fx * 1.01
+    with pytest.raises(igs.IgsError):
+        igs.Frame(sc.n, 1 << 16, igs.camera(cam), igs.opts(tile=16))
