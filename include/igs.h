@@ -159,6 +159,26 @@ IGS_API igs_status igs_project(const igs_scene* scene, const igs_camera* cam, co
  * untouched. Writes order, offset, tile_key, vals, ranges, info. */
 IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* stream);
 
+/* Front-to-back order of n depth keys WITHOUT allocating anything. The paper
+ * has no counterpart: this exists for callers that cannot allocate device
+ * memory around the call, such as code that runs while a CUDA graph is being
+ * captured (allocation is not allowed there) or a host application whose
+ * device memory is owned by its own allocator and is not reachable from here.
+ * It computes exactly what igs_bin_sort writes to frame->order for the same
+ * depth_key: a stable ascending sort of the keys (ties keep index order), the
+ * output being the indices. depth_key (device, n) is read; order (device, n)
+ * is overwritten. Limit: n <= 1048576 (2^20); larger n returns
+ * IGS_ERR_INVALID_ARG and launches nothing.
+ * Scratch lives in one fixed 13.6 MB device array compiled into the library,
+ * which every GPU that loads the library holds until the process exits. The
+ * first call on each device looks up that array's device address; make that
+ * first call before any stream capture. Every call on a device shares the
+ * array (the call clears what must start at zero), so calls that overlap on
+ * the GPU race: serialise them (one stream, or events). Asynchronous on
+ * `stream`; a device-side bounded wait that runs out leaves order incomplete
+ * and is not reported here. */
+IGS_API igs_status igs_sort_depth_noalloc(const uint32_t* depth_key, int64_t n, uint32_t* order, void* stream);
+
 /* Export the sorted 64-bit keys (tile << 32 | depth bits), M = info[0] of them,
  * into keys (device, >= capacity entries). For inspection and tests. */
 IGS_API igs_status igs_export_keys(const igs_frame* frame, uint64_t* keys, void* stream);

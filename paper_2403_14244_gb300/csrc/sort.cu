@@ -21,6 +21,7 @@
 // look-back). Every wait on another block is bounded (kMaxSpin polls); on
 // expiry the block records IGS_ERR_DEVICE_TIMEOUT and carries on.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -478,3 +479,86 @@ cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t 
 }
 
 }  // namespace igs
+
+// ---------------------------------------------------------------------------
+// Front-to-back ordering without any allocation (igs_sort_depth_noalloc).
+//
+// Some callers cannot allocate device memory around a call: code that runs
+// while a CUDA graph is being captured, or an embedding host whose memory is
+// owned by its own allocator. This entry point orders n depth keys exactly as
+// igs_bin_sort orders its frame's depth_key into order (stable, ties by index),
+// but takes its scratch from one fixed device array compiled into the library.
+// ---------------------------------------------------------------------------
+namespace igs {
+namespace {
+
+constexpr int64_t kNoAllocMaxKeys = (int64_t)1 << 20;
+constexpr int64_t kNoAllocBlocks = kNoAllocMaxKeys / kSortTile;
+// word offsets inside the static scratch
+constexpr int64_t kNaKeysA = 0;
+constexpr int64_t kNaKeysB = kNaKeysA + kNoAllocMaxKeys;
+constexpr int64_t kNaValsA = kNaKeysB + kNoAllocMaxKeys;
+constexpr int64_t kNaHist = kNaValsA + kNoAllocMaxKeys;     // [4][256]
+constexpr int64_t kNaCounters = kNaHist + 4 * kRadix;       // [64]
+constexpr int64_t kNaInfo = kNaCounters + 64;               // [64]
+constexpr int64_t kNaStatus = kNaInfo + 64;                 // [4][blocks][256]
+constexpr int64_t kNaWords = kNaStatus + 4 * kNoAllocBlocks * kRadix;
+// words that must be zero at the start of every call
+constexpr int64_t kNaZeroFrom = kNaHist;
+
+// 13.6 MB (3409024 words), held by every device that loads the library until the process exits.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNaWords];
+
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[128] = {};
+
+// Device address of the static scratch on the current device (looked up once per device).
+cudaError_t noalloc_scratch(uint32_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace igs
+
+extern "C" igs_status igs_sort_depth_noalloc(const uint32_t* depth_key, int64_t n, uint32_t* order, void* stream) {
+    using namespace igs;
+    if (n < 0 || n > kNoAllocMaxKeys) return IGS_ERR_INVALID_ARG;
+    if (n > 0 && (!depth_key || !order)) return IGS_ERR_INVALID_ARG;
+    if (n == 0) return IGS_OK;
+    uint32_t* s = nullptr;
+    if (noalloc_scratch(&s) != cudaSuccess) return IGS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(s + kNaZeroFrom, 0, (size_t)(kNaWords - kNaZeroFrom) * 4, st) != cudaSuccess)
+        return IGS_ERR_CUDA;
+    const uint32_t nn = (uint32_t)n;
+    const unsigned blocks = (unsigned)ceil_div(n, kSortTile);
+    const int hist_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 4);
+    k_hist<<<hist_blocks, 256, 0, st>>>(depth_key, nullptr, nn, 4, s + kNaHist);
+    count_launches();
+    const uint32_t* kin = depth_key;
+    const uint32_t* vin = nullptr;
+    for (int p = 0; p < 4; ++p) {
+        uint32_t* kout = (p % 2 == 0) ? s + kNaKeysA : s + kNaKeysB;
+        uint32_t* vout = (p % 2 == 0) ? s + kNaValsA : order;
+        k_onesweep<<<blocks, kSortThreads, 0, st>>>(kin, vin, p == 3 ? nullptr : kout, vout, nullptr, nn, 8 * p,
+                                                    s + kNaHist + p * kRadix,
+                                                    s + kNaStatus + (size_t)p * kNoAllocBlocks * kRadix,
+                                                    s + kNaCounters + p, s + kNaInfo);
+        count_launches();
+        kin = kout;
+        vin = vout;
+    }
+    return cudaGetLastError() == cudaSuccess ? IGS_OK : IGS_ERR_CUDA;
+}

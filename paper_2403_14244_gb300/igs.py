@@ -81,6 +81,7 @@ SYMBOLS = {
                            C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "igs_frame_status": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_uint32), C.c_void_p]),
     "igs_frame_reset_status": (C.c_int, [C.POINTER(IgsFrame), C.c_void_p]),
+    "igs_sort_depth_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -296,6 +297,13 @@ def frame_status(frame: Frame, stream=None):
     if st not in (OK, ERR_CAPACITY, ERR_DEVICE_TIMEOUT):
         _check(st, "igs_frame_status")
     return st, list(info)
+
+
+def sort_depth_noalloc(depth_key, order, stream=None):
+    """igs_sort_depth_noalloc: order = stable argsort of depth_key (int32 views of
+    uint32 data, n <= 2^20), scratch from the library's static device array."""
+    _check(load().igs_sort_depth_noalloc(_ptr(depth_key), int(depth_key.numel()), _ptr(order), _stream(stream)),
+           "igs_sort_depth_noalloc")
 
 
 def launch_count() -> int:
