@@ -106,7 +106,7 @@ typedef struct igs_scene {
  * igs_render_bwd of one view, and can be reused for the next view of the same
  * size. Contents after each step:
  *   igs_project:    rec, rect, count, depth_key
- *   igs_bin_sort:   order, offset, tile_key, vals, ranges, info[0..1]
+ *   igs_bin_sort:   order, offset, vals, ranges, info[0..1]
  *   igs_render_fwd: T_final, n_contrib
  * Status words (device, uint32): info[0] = M entries, info[1] = Gaussians kept,
  * info[2] = error code (igs_status, 0 = none), info[3] = M the view needs. */
@@ -120,7 +120,7 @@ typedef struct igs_frame {
     uint32_t* depth_key;     /* [n] bits of the FP32 depth z_c; 0xFFFFFFFF if culled */
     uint32_t* order;         /* [n] Gaussian ids, front to back (culled ones last) */
     uint32_t* offset;        /* [n] first entry of order[p]: exclusive scan of count in depth order */
-    uint32_t* tile_key;      /* [capacity] tile id of each sorted entry */
+    uint32_t* tile_key;      /* [capacity] tile id of each sorted entry (written by igs_export_keys) */
     uint32_t* vals;          /* [capacity] Gaussian id of each sorted entry */
     uint32_t* ranges;        /* [tiles][2] [start, end) of each tile's entries; (0, 0) if empty */
     float* T_final;          /* [H][W] transmittance after the last blended entry */
@@ -169,7 +169,7 @@ IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* st
  * output being the indices. depth_key (device, n) is read; order (device, n)
  * is overwritten. Limit: n <= 1048576 (2^20); larger n returns
  * IGS_ERR_INVALID_ARG and launches nothing.
- * Scratch lives in one fixed 13.6 MB device array compiled into the library,
+ * Scratch lives in one fixed 17.8 MB device array compiled into the library,
  * which every GPU that loads the library holds until the process exits. The
  * first call on each device looks up that array's device address; make that
  * first call before any stream capture. Every call on a device shares the
@@ -180,7 +180,8 @@ IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* st
 IGS_API igs_status igs_sort_depth_noalloc(const uint32_t* depth_key, int64_t n, uint32_t* order, void* stream);
 
 /* Export the sorted 64-bit keys (tile << 32 | depth bits), M = info[0] of them,
- * into keys (device, >= capacity entries). For inspection and tests. */
+ * into keys (device, >= capacity entries), and the tile id of every sorted entry
+ * into frame->tile_key. For inspection and tests. */
 IGS_API igs_status igs_export_keys(const igs_frame* frame, uint64_t* keys, void* stream);
 
 /* Per tile, front-to-back compositing of its entries (Eq. 4) at every pixel

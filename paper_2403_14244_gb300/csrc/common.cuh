@@ -18,9 +18,10 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
 // Status words of a frame (igs_frame::info).
-enum : int { kInfoM = 0, kInfoKept = 1, kInfoErr = 2, kInfoNeed = 3, kInfoAbort = 4, kInfoWords = 16 };
+enum : int { kInfoM = 0, kInfoKept = 1, kInfoErr = 2, kInfoNeed = 3, kInfoAbort = 4, kInfoTileTotal = 5,
+             kInfoWords = 16 };
 
-// Radix sort geometry: 256 threads x 16 keys per block, 8-bit digits.
+// Radix sort geometry: 256 threads x 16 (key | value) items per block, 8-bit digits.
 constexpr int kSortThreads = 256;
 constexpr int kSortIpt = 16;
 constexpr int kSortTile = kSortThreads * kSortIpt;
@@ -28,6 +29,8 @@ constexpr int kRadix = 256;
 constexpr int kScanThreads = 256;
 constexpr int kScanIpt = 16;
 constexpr int kScanTile = kScanThreads * kScanIpt;
+// Entries written per block by the duplication kernel.
+constexpr int kDupTile = 2048;
 // Upper bound on polls of a look-back flag before a block gives up (about 0.1 s).
 constexpr int kMaxSpin = 1 << 21;
 
@@ -44,21 +47,25 @@ __device__ __forceinline__ void record_error(uint32_t* info, uint32_t code) {
     atomicExch(&info[kInfoAbort], 1u);
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+// Look-back status words carry their own flag and count in one word, and a
+// reader uses nothing else its predecessor wrote, so relaxed GPU-scope accesses
+// suffice (an acquire load would also hold back every later load until it
+// completes, serialising a window of polls).
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // 2^x with the SFU (ex2.approx, flush-to-zero): alpha only needs ~22 bits.
@@ -104,19 +111,21 @@ struct AdamParams {
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, const AdamParams& a,
                         cudaStream_t s);
 
-// Scratch layout of a frame (byte offsets inside igs_frame::scratch).
+// Scratch layout of a frame (pieces of igs_frame::scratch).
 struct SortScratch {
-    uint32_t* dkeys_a;      // [n]
-    uint32_t* dkeys_b;      // [n]
-    uint32_t* dvals_a;      // [n]
-    uint32_t* hist;         // [8][256]: 4 depth passes, then up to 4 tile passes
-    uint32_t* counters;     // [16] virtual block counters
-    uint32_t* status_depth; // [4][blocks(n)][256]
-    uint32_t* status_tile;  // [tile_passes][blocks(capacity)][256]
+    unsigned long long* ditems_a;     // [n] (depth key | index) items
+    unsigned long long* ditems_b;     // [n]
+    unsigned long long* items_a;      // [capacity] (tile id | Gaussian id) items
+    unsigned long long* items_b;      // [capacity]
+    uint32_t* hist;                   // [8][256]: 4 depth passes, then up to 4 tile passes
+    uint32_t* counters;               // [16] virtual block counters
+    uint32_t* status_depth;           // [4][blocks(n)][256]
+    uint32_t* status_tile;            // [tile_passes][blocks(capacity)][256]
     unsigned long long* scan_status;  // [scan blocks(n)]
-    uint32_t* tkey_alt;     // [capacity]
-    uint32_t* vals_alt;     // [capacity]
+    uint32_t* dup_start;              // [blocks(capacity) + 1] first Gaussian (in depth order) of each duplication block
+    int32_t* grid;                    // [(tiles_y + 1) * (tiles_x + 1)] rectangle corner counts -> per-tile counts
     int tile_passes;
+    int tile_bits;
 };
 SortScratch sort_scratch(const igs_frame& f);
 size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles);
