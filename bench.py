@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 
 METRIC = "1080p frames/s & fwd+bwd steps/s at 3M isotropic Gaussians; serve p50/p99 ms"
 WORKLOAD = "train_step_3M_sh3_1297x840_ring16"
-STAGES = ("project", "bin_sort", "blend_fwd", "l1", "blend_bwd", "project_bwd", "adam")
+STAGES = ("project", "bin_sort", "blend_fwd", "l1", "blend_bwd", "project_bwd_adam")
 
 
 def parse():
@@ -222,10 +222,10 @@ def run_mine(args, world, rank, local):
     P = cams[0].width * cams[0].height
     dominant = max(stage_ms, key=stage_ms.get)
     algo_bytes = {
-        # per launch, from the data the step must move ("Roofline")
-        "adam": 28 * n * (5 + C),                          # read p, g, m, v; write p, m, v
+        # per launch, from the data the step must move (per-unit figures in the design doc)
         "project": n * (16 + 4 + 4 * C) + n * (32 + 8 + 4 + 4),
-        "project_bwd": n * (16 + 4 + 4 * C + 32 + 4) + n * (16 + 4 + 4 * C),
+        # read params, g2d, count, m, v; write params, m, v
+        "project_bwd_adam": n * (4 * (5 + C) + 32 + 4 + 8 * (5 + C)) + n * 12 * (5 + C),
         "l1": P * 3 * 4 * 3,
     }
     roofline = None

@@ -212,6 +212,20 @@ IGS_API igs_status igs_project_bwd(const igs_scene* scene, const igs_camera* cam
                                    const igs_frame* frame, const float* g2d, float* d_means_sigma,
                                    float* d_opacity, float* d_color, void* stream);
 
+/* The projection backward fused with one Adam step, for training: the same
+ * gradient as igs_project_bwd, applied at once to the parameters without
+ * writing it out. scene->means_sigma, scene->opacity and scene->color (device,
+ * layout above, log sigma / logit with param_mode 1) are UPDATED IN PLACE; m_*
+ * and v_* (device, same shapes; 16-byte aligned means_sigma and color rows) are
+ * the Adam moments, updated in place. Every Gaussian is stepped, culled ones with
+ * a zero gradient (their moments decay), exactly as igs_adam over the gradient
+ * of igs_project_bwd would. Step and hyper-parameters as in igs_adam. */
+IGS_API igs_status igs_project_bwd_adam(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                        const igs_frame* frame, const float* g2d, float* m_means_sigma,
+                                        float* m_opacity, float* m_color, float* v_means_sigma, float* v_opacity,
+                                        float* v_color, double lr, double b1, double b2, double eps, int64_t step,
+                                        void* stream);
+
 /* L1 loss of Sec. 3 (lambda = 0): loss = mean |img - target| over `count`
  * entries, written to *loss (device float, overwritten), and
  * dL_dimg = sign(img - target) / count (device, count entries; sign(0) = 0). */

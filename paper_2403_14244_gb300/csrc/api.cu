@@ -253,6 +253,44 @@ igs_status igs_project_bwd(const igs_scene* scene, const igs_camera* cam, const 
                        "igs_project_bwd");
 }
 
+static igs_status adam_params(double lr, double b1, double b2, double eps, int64_t step, igs::AdamParams* a) {
+    if (step < 1) return fail(IGS_ERR_INVALID_ARG, "Adam step must be >= 1");
+    if (!(b1 >= 0.0 && b1 < 1.0 && b2 >= 0.0 && b2 < 1.0 && lr >= 0.0 && eps > 0.0))
+        return fail(IGS_ERR_INVALID_ARG, "need 0 <= b1, b2 < 1, lr >= 0, eps > 0");
+    const double bc1 = 1.0 - std::pow(b1, (double)step);
+    const double bc2 = 1.0 - std::pow(b2, (double)step);
+    a->b1 = (float)b1;
+    a->b2 = (float)b2;
+    a->omb1 = (float)(1.0 - b1);
+    a->omb2 = (float)(1.0 - b2);
+    a->step_size = (float)(lr / bc1);
+    a->bc2_sqrt = (float)std::sqrt(bc2);
+    a->eps = (float)eps;
+    return IGS_OK;
+}
+
+igs_status igs_project_bwd_adam(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                const igs_frame* frame, const float* g2d, float* m_means_sigma, float* m_opacity,
+                                float* m_color, float* v_means_sigma, float* v_opacity, float* v_color, double lr,
+                                double b1, double b2, double eps, int64_t step, void* stream) {
+    igs_status st;
+    if ((st = check_scene(scene)) || (st = check_camera(cam)) || (st = check_opts(opts)) || (st = check_frame(frame)) ||
+        (st = frame_matches(frame, scene, cam, opts)))
+        return st;
+    if (!g2d || !m_means_sigma || !m_opacity || !m_color || !v_means_sigma || !v_opacity || !v_color)
+        return fail(IGS_ERR_INVALID_ARG, "g2d or an Adam moment buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(g2d) | reinterpret_cast<uintptr_t>(m_means_sigma) |
+         reinterpret_cast<uintptr_t>(v_means_sigma) | reinterpret_cast<uintptr_t>(m_color) |
+         reinterpret_cast<uintptr_t>(v_color)) & 15)
+        return fail(IGS_ERR_INVALID_ARG, "g2d, means_sigma and color moments must be 16-byte aligned");
+    igs::AdamParams a;
+    if ((st = adam_params(lr, b1, b2, eps, step, &a))) return st;
+    const igs::ViewParams vp = view_params(cam, opts, frame);
+    return cuda_status(igs::launch_project_bwd_adam(*scene, vp, *frame, g2d, m_means_sigma, m_opacity, m_color,
+                                                    v_means_sigma, v_opacity, v_color, a, (cudaStream_t)stream),
+                       "igs_project_bwd_adam");
+}
+
 igs_status igs_render_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts, const igs_frame* frame,
                           const float* dL_dimg, float* g2d, float* d_means_sigma, float* d_opacity, float* d_color,
                           void* stream) {
@@ -274,19 +312,10 @@ igs_status igs_l1_loss(const float* img, const float* target, int64_t count, flo
 
 igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_t count, double lr, double b1, double b2,
                     double eps, int64_t step, void* stream) {
-    if (!p || !g || !m || !v || count < 0 || step < 1) return fail(IGS_ERR_INVALID_ARG, "bad adam arguments");
-    if (!(b1 >= 0.0 && b1 < 1.0 && b2 >= 0.0 && b2 < 1.0 && lr >= 0.0 && eps > 0.0))
-        return fail(IGS_ERR_INVALID_ARG, "need 0 <= b1, b2 < 1, lr >= 0, eps > 0");
-    const double bc1 = 1.0 - std::pow(b1, (double)step);
-    const double bc2 = 1.0 - std::pow(b2, (double)step);
+    if (!p || !g || !m || !v || count < 0) return fail(IGS_ERR_INVALID_ARG, "bad adam arguments");
     igs::AdamParams a;
-    a.b1 = (float)b1;
-    a.b2 = (float)b2;
-    a.omb1 = (float)(1.0 - b1);
-    a.omb2 = (float)(1.0 - b2);
-    a.step_size = (float)(lr / bc1);
-    a.bc2_sqrt = (float)std::sqrt(bc2);
-    a.eps = (float)eps;
+    igs_status st;
+    if ((st = adam_params(lr, b1, b2, eps, step, &a))) return st;
     return cuda_status(igs::launch_adam(p, g, m, v, count, a, (cudaStream_t)stream), "igs_adam");
 }
 

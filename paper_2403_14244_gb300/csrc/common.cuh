@@ -94,6 +94,10 @@ struct BlendParams {
 cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, cudaStream_t s);
 cudaError_t launch_project_bwd(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d,
                                float* d_ms, float* d_op, float* d_col, cudaStream_t s);
+struct AdamParams;
+cudaError_t launch_project_bwd_adam(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d,
+                                    float* m_ms, float* m_op, float* m_col, float* v_ms, float* v_op, float* v_col,
+                                    const AdamParams& ap, cudaStream_t s);
 cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t s);
 cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t s);

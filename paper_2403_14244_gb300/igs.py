@@ -76,6 +76,9 @@ SYMBOLS = {
     "igs_project_bwd": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
                                   C.POINTER(IgsFrame), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
+    "igs_project_bwd_adam": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
+                                       C.POINTER(IgsFrame), C.c_void_p] + [C.c_void_p] * 6 +
+                             [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "igs_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double,
                            C.c_double, C.c_double, C.c_int64, C.c_void_p]),
@@ -278,6 +281,15 @@ def project_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, d_m
     _check(load().igs_project_bwd(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                   _ptr(g2d), _ptr(d_means_sigma), _ptr(d_opacity), _ptr(d_color),
                                   _stream(stream)), "igs_project_bwd")
+
+
+def project_bwd_adam(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, m, v, step, lr=1e-3, b1=0.9,
+                     b2=0.999, eps=1e-8, stream=None):
+    """Projection backward fused with Adam: scene parameters and the moments
+    m = (m_ms, m_op, m_col), v = (v_ms, v_op, v_col) are updated in place."""
+    _check(load().igs_project_bwd_adam(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
+                                       _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
+                                       int(step), _stream(stream)), "igs_project_bwd_adam")
 
 
 def l1_loss(img, target, loss, dL_dimg, stream=None):

@@ -108,20 +108,32 @@ def render(means_sigma, opacity, color, renderer: Renderer, cam):
 
 
 class TrainStep:
-    """Flat parameter buffer [N*(4+1+C)] with views means_sigma [N,4] (log sigma),
-    opacity [N] (logit), color [N,C] (SH); Adam state m, v of the same shape.
-    step(cam, target) runs forward, L1, backward and Adam on the GPU."""
+    """Training state for one scene: a flat FP32 parameter buffer holding
+    means_sigma [N,4] (log sigma), opacity [N] (logit) and color [N,C] (SH) as
+    views, each segment starting on a 256-byte boundary, and the Adam moments m, v
+    in flat buffers of the same layout.
 
-    def __init__(self, means_sigma, opacity, color, sh_degree, tile=16, lr=1e-3, device="cuda"):
+    step(cam, target) runs forward, L1, backward and Adam on the GPU. By default
+    the projection backward and Adam run as one fused kernel and the gradient is
+    never written; fused=False writes the gradient to `grad` and applies igs_adam
+    over the flat buffer (same update)."""
+
+    def __init__(self, means_sigma, opacity, color, sh_degree, tile=16, lr=1e-3, device="cuda", fused=True):
         n = means_sigma.shape[0]
         C = color.shape[1]
         self.n, self.C = n, C
-        self.flat = torch.empty(n * (5 + C), dtype=torch.float32, device=device)
+        a = lambda x: (x + 63) // 64 * 64  # noqa: E731  (floats per 256 bytes)
+        self.o_op = a(4 * n)
+        self.o_col = a(self.o_op + n)
+        size = a(self.o_col + C * n)
+        self.flat = torch.zeros(size, dtype=torch.float32, device=device)
         self.grad = torch.zeros_like(self.flat)
         self.m = torch.zeros_like(self.flat)
         self.v = torch.zeros_like(self.flat)
         self.ms, self.op, self.col = self._views(self.flat)
         self.g_ms, self.g_op, self.g_col = self._views(self.grad)
+        self.m_views = self._views(self.m)
+        self.v_views = self._views(self.v)
         self.ms.copy_(means_sigma)
         self.op.copy_(opacity)
         self.col.copy_(color)
@@ -130,13 +142,14 @@ class TrainStep:
         self.g2d = torch.empty((n, 8), dtype=torch.float32, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         self.lr = lr
+        self.fused = fused
         self.t = 0
         self._img = {}
         self._dimg = {}
 
     def _views(self, flat):
         n, C = self.n, self.C
-        return (flat[:4 * n].view(n, 4), flat[4 * n:5 * n], flat[5 * n:].view(n, C))
+        return (flat[:4 * n].view(n, 4), flat[self.o_op:self.o_op + n], flat[self.o_col:self.o_col + C * n].view(n, C))
 
     def step(self, cam, target, check=False, stream=None, marks=None):
         """One training step on `stream`. `marks`, if given, is called with a
@@ -164,9 +177,14 @@ class TrainStep:
         mark("l1")
         igs.blend_bwd(frame, r.opts, dimg, self.g2d, stream)
         mark("blend_bwd")
-        igs.project_bwd(self.scene, c, r.opts, frame, self.g2d, self.g_ms, self.g_op, self.g_col, stream)
-        mark("project_bwd")
         self.t += 1
-        igs.adam(self.flat, self.grad, self.m, self.v, self.t, lr=self.lr, stream=stream)
-        mark("adam")
+        if self.fused:
+            igs.project_bwd_adam(self.scene, c, r.opts, frame, self.g2d, self.m_views, self.v_views, self.t,
+                                 lr=self.lr, stream=stream)
+            mark("project_bwd_adam")
+        else:
+            igs.project_bwd(self.scene, c, r.opts, frame, self.g2d, self.g_ms, self.g_op, self.g_col, stream)
+            mark("project_bwd")
+            igs.adam(self.flat, self.grad, self.m, self.v, self.t, lr=self.lr, stream=stream)
+            mark("adam")
         return frame

@@ -105,24 +105,56 @@ def test_adam_matches_oracle():
     np.testing.assert_allclose(v.cpu().numpy(), rv, rtol=1e-5, atol=1e-12)
 
 
+def _flat_ref(sc, ref):
+    return (np.concatenate([ref["d_means"], ref["d_sigma"][:, None]], 1), ref["d_opac"], ref["d_color"])
+
+
 def test_train_step_matches_oracle():
-    """One full step (forward, L1, backward, Adam) on a log-parameter SH3 scene."""
+    """One full step (forward, L1, backward, Adam) on a log-parameter SH3 scene,
+    unfused (gradient written, then Adam) and fused (projection backward + Adam)."""
     sc, cam = random_small(500, 44, w=96, h=64, sh_degree=3, log_params=True, spread=0.8)
     target = scenes.target_image(cam.width, cam.height, 9)
-    ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
-                   torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-3)
-    ts.step(cam, torch.from_numpy(target).cuda(), check=True)
-    torch.cuda.synchronize()
     ref_fwd = oracle.render(sc, cam, mode=1)
     loss_ref, G = oracle.l1(ref_fwd["img"], target)
-    assert float(ts.loss) == pytest.approx(loss_ref, rel=1e-4)
     ref = oracle.backward(sc, cam, G, mode=1)
-    g_ref = np.concatenate([np.concatenate([ref["d_means"], ref["d_sigma"][:, None]], 1).reshape(-1),
-                            ref["d_opac"], ref["d_color"].reshape(-1)])
-    g = ts.grad.cpu().numpy()
-    _gpu.grad_close(g, g_ref, "flat grad")
-    p0 = np.concatenate([sc.means_sigma.reshape(-1), sc.opacity, sc.color.reshape(-1)]).astype(np.float64)
-    p_ref, _, _ = oracle.adam(p0, g_ref, np.zeros_like(p0), np.zeros_like(p0), lr=1e-3, t=1)
-    # first Adam step moves every parameter with a non-tiny gradient by ~lr * sign(g)
-    moved = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
-    np.testing.assert_allclose(ts.flat.cpu().numpy()[moved], p_ref[moved], atol=2e-6)
+    g_ms, g_op, g_col = _flat_ref(sc, ref)
+    outs = {}
+    for fused in (False, True):
+        ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                       torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-3, fused=fused)
+        ts.step(cam, torch.from_numpy(target).cuda(), check=True)
+        torch.cuda.synchronize()
+        assert float(ts.loss) == pytest.approx(loss_ref, rel=1e-4)
+        if not fused:
+            _gpu.grad_close(ts.g_ms.cpu().numpy(), g_ms, "means_sigma grad")
+            _gpu.grad_close(ts.g_op.cpu().numpy(), g_op, "opacity grad")
+            _gpu.grad_close(ts.g_col.cpu().numpy(), g_col, "color grad")
+        outs[fused] = [t.cpu().numpy() for t in (ts.ms, ts.op, ts.col, *ts.m_views, *ts.v_views)]
+        for name, p0, g, got in (("means_sigma", sc.means_sigma, g_ms, outs[fused][0]),
+                                 ("opacity", sc.opacity, g_op, outs[fused][1]),
+                                 ("color", sc.color, g_col, outs[fused][2])):
+            p_ref, _, _ = oracle.adam(p0.astype(np.float64), g, np.zeros(g.shape), np.zeros(g.shape), lr=1e-3, t=1)
+            # first Adam step moves a parameter with a non-tiny gradient by ~lr * sign(g)
+            moved = np.abs(g) > 1e-3 * np.abs(g).max()
+            np.testing.assert_allclose(got[moved], p_ref[moved], atol=2e-6, err_msg=name)
+            still = g == 0
+            np.testing.assert_array_equal(got[still], p0[still])
+    # fused and unfused steps agree (same FP32 arithmetic up to the gradient's summation order)
+    for a, b in zip(outs[False], outs[True]):
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-7)
+
+
+def test_fused_adam_ragged_and_repeated():
+    """Fused projection backward + Adam on a scene whose size is not a multiple of
+    the 32-Gaussian warp tile, over three steps, against the unfused path."""
+    sc, cam = random_small(1001, 45, w=80, h=60, sh_degree=3, log_params=True, spread=0.8)
+    target = torch.from_numpy(scenes.target_image(cam.width, cam.height, 10)).cuda()
+    states = []
+    for fused in (False, True):
+        ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                       torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-2, fused=fused)
+        for _ in range(3):
+            ts.step(cam, target, check=True)
+        torch.cuda.synchronize()
+        states.append(torch.cat([ts.flat, ts.m, ts.v]).cpu().numpy())
+    np.testing.assert_allclose(states[0], states[1], rtol=1e-4, atol=1e-6)
