@@ -246,6 +246,68 @@ IGS_API igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info,
 /* Clear the frame's status words (asynchronous). */
 IGS_API igs_status igs_frame_reset_status(igs_frame* frame, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Multi-view batch: V views of one scene, each with its own pose and image
+ * size, rendered by one chain of launches with no host synchronisation: one
+ * projection launch over every (view, Gaussian), per-view depth sorts in one
+ * segmented launch per pass, one scan and one duplication over all views with
+ * global tile ids, one tile-id sort, and one persistent blend whose CTAs take
+ * (view, tile) work items from an atomic counter. The chain can be captured in
+ * a CUDA graph once and replayed. Each view's image is bit-identical to
+ * rendering it alone with igs_project / igs_bin_sort / igs_render_fwd.
+ * ------------------------------------------------------------------------- */
+#define IGS_MAX_VIEWS 256
+
+typedef struct igs_batch {
+    int64_t n;                  /* Gaussians */
+    int64_t capacity;           /* (view, Gaussian, tile) entries over all views */
+    int32_t views;              /* V, 1 .. IGS_MAX_VIEWS */
+    int32_t tile;               /* 8, 16 or 32 */
+    int32_t blend_batch;        /* entries staged per shared-memory batch in the blend */
+    int32_t persistent_blocks;  /* CTAs of the persistent blend (set by igs_batch_set_views) */
+    int64_t tiles_total;        /* tiles over all views */
+    int64_t image_floats;       /* size of the packed image buffer: sum over views of 3 W H */
+    int64_t image_offset[IGS_MAX_VIEWS];  /* first float of view v's [3][H][W] image */
+    uint32_t tile_base[IGS_MAX_VIEWS];    /* global id of view v's first tile */
+    int32_t width[IGS_MAX_VIEWS], height[IGS_MAX_VIEWS];
+    float* rec;                 /* [V n][8] records of every (view, Gaussian), view-major */
+    uint32_t* rect;             /* [V n][2] */
+    uint32_t* count;            /* [V n] */
+    uint32_t* depth_key;        /* [V n] */
+    uint32_t* order;            /* [V n] record ids front to back, view after view */
+    uint32_t* offset;           /* [V n] */
+    uint32_t* vals;             /* [capacity] record id of each entry, sorted by global tile */
+    uint32_t* ranges;           /* [tiles_total][2] */
+    uint32_t* info;             /* [16] status words, as for a frame */
+    void* scratch;
+    size_t scratch_bytes;
+} igs_batch;
+
+/* Lay out a batch for n Gaussians and the V cameras' image sizes (the poses may
+ * change later, the sizes may not). capacity = entries over all views;
+ * blend_batch = entries per shared-memory batch of the blend: 32 or 64 for tile
+ * 8, 64, 128 or 256 for tile 16, 256, 512 or 1024 for tile 32 (0 = tile^2).
+ * Requires V n < 2^32. workspace == NULL: only *bytes. Host-only, no launch. */
+IGS_API igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, const igs_opts* opts,
+                                    int64_t capacity, int32_t blend_batch, void* workspace, size_t* bytes,
+                                    igs_batch* batch);
+
+/* Upload the V cameras (same sizes as at layout) to the batch's device view
+ * table, asynchronously on `stream` (cams may be reused on return). Call it
+ * before igs_render_batch whenever the poses change, outside any stream capture. */
+IGS_API igs_status igs_batch_set_views(igs_batch* batch, const igs_camera* cams, const igs_opts* opts,
+                                       void* stream);
+
+/* Render every view of the batch into `images` (device, batch->image_floats
+ * floats; view v at image_offset[v], [3][H][W]). No host synchronisation, so
+ * the call can be captured in a CUDA graph. An entry overflow sets info[2] to
+ * IGS_ERR_CAPACITY (info[3] = entries needed) and leaves the images untouched. */
+IGS_API igs_status igs_render_batch(igs_batch* batch, const igs_scene* scene, const igs_opts* opts, float* images,
+                                    void* stream);
+
+/* Copy the batch's four status words to host_info and wait for `stream`. */
+IGS_API igs_status igs_batch_status(const igs_batch* batch, uint32_t* host_info, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all threads). For accounting in benchmarks; host-only, never fails. */
 IGS_API uint64_t igs_launch_count(void);

@@ -319,6 +319,132 @@ igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_t count,
     return cuda_status(igs::launch_adam(p, g, m, v, count, a, (cudaStream_t)stream), "igs_adam");
 }
 
+// ------------------------------------------------------------------- batch --
+
+igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, const igs_opts* opts, int64_t capacity,
+                            int32_t blend_batch, void* workspace, size_t* bytes, igs_batch* batch) {
+    igs_status st;
+    if ((st = check_opts(opts))) return st;
+    if (!bytes || !cams) return fail(IGS_ERR_INVALID_ARG, "bytes or cams is NULL");
+    if (views < 1 || views > IGS_MAX_VIEWS) return fail(IGS_ERR_INVALID_ARG, "views must be 1..%d", IGS_MAX_VIEWS);
+    if (n < 0 || n * views >= ((int64_t)1 << 32)) return fail(IGS_ERR_INVALID_ARG, "views * n must be < 2^32");
+    if (capacity < 0 || capacity >= ((int64_t)1 << 30)) return fail(IGS_ERR_INVALID_ARG, "capacity must be < 2^30");
+    const int bb = blend_batch == 0 ? opts->tile * opts->tile : blend_batch;
+    if (!igs::batch_blend_variant_ok(opts->tile, bb))
+        return fail(IGS_ERR_INVALID_ARG, "unsupported blend batch %d for tile %d", bb, opts->tile);
+    igs_batch b;
+    std::memset(&b, 0, sizeof b);
+    b.n = n;
+    b.capacity = capacity;
+    b.views = views;
+    b.tile = opts->tile;
+    b.blend_batch = bb;
+    int64_t tiles = 0, floats = 0;
+    for (int v = 0; v < views; ++v) {
+        if ((st = check_camera(&cams[v]))) return st;
+        const int64_t tx = (cams[v].width + opts->tile - 1) / opts->tile, ty = (cams[v].height + opts->tile - 1) / opts->tile;
+        if (tx >= 65536 || ty >= 65536) return fail(IGS_ERR_INVALID_ARG, "too many tiles per axis");
+        b.width[v] = cams[v].width;
+        b.height[v] = cams[v].height;
+        b.tile_base[v] = (uint32_t)tiles;
+        b.image_offset[v] = floats;
+        tiles += tx * ty;
+        floats += 3 * (int64_t)cams[v].width * cams[v].height;
+    }
+    if (tiles >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "too many tiles");
+    b.tiles_total = tiles;
+    b.image_floats = floats;
+    const int64_t Vn = n * views;
+    size_t off = 0;
+    const size_t o_rec = off; off += align256((size_t)Vn * 32);
+    const size_t o_rect = off; off += align256((size_t)Vn * 8);
+    const size_t o_count = off; off += align256((size_t)Vn * 4);
+    const size_t o_dkey = off; off += align256((size_t)Vn * 4);
+    const size_t o_order = off; off += align256((size_t)Vn * 4);
+    const size_t o_offset = off; off += align256((size_t)Vn * 4);
+    const size_t o_vals = off; off += align256((size_t)capacity * 4);
+    const size_t o_ranges = off; off += align256((size_t)tiles * 8);
+    const size_t o_info = off; off += align256(igs::kInfoWords * 4);
+    const size_t o_scr = off;
+    const size_t scr = igs::batch_scratch_bytes(b);
+    off += align256(scr);
+    *bytes = off;
+    if (!workspace) return IGS_OK;
+    if (!batch) return fail(IGS_ERR_INVALID_ARG, "batch is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return fail(IGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    char* w = static_cast<char*>(workspace);
+    b.rec = reinterpret_cast<float*>(w + o_rec);
+    b.rect = reinterpret_cast<uint32_t*>(w + o_rect);
+    b.count = reinterpret_cast<uint32_t*>(w + o_count);
+    b.depth_key = reinterpret_cast<uint32_t*>(w + o_dkey);
+    b.order = reinterpret_cast<uint32_t*>(w + o_order);
+    b.offset = reinterpret_cast<uint32_t*>(w + o_offset);
+    b.vals = reinterpret_cast<uint32_t*>(w + o_vals);
+    b.ranges = reinterpret_cast<uint32_t*>(w + o_ranges);
+    b.info = reinterpret_cast<uint32_t*>(w + o_info);
+    b.scratch = w + o_scr;
+    b.scratch_bytes = scr;
+    *batch = b;
+    return IGS_OK;
+}
+
+igs_status igs_batch_set_views(igs_batch* batch, const igs_camera* cams, const igs_opts* opts, void* stream) {
+    igs_status st;
+    if (!batch || !batch->info || !cams) return fail(IGS_ERR_INVALID_ARG, "batch or cams is NULL");
+    if ((st = check_opts(opts))) return st;
+    if (opts->tile != batch->tile) return fail(IGS_ERR_INVALID_ARG, "batch laid out for another tile size");
+    static thread_local igs::BatchView host[IGS_MAX_VIEWS];
+    for (int v = 0; v < batch->views; ++v) {
+        if ((st = check_camera(&cams[v]))) return st;
+        if (cams[v].width != batch->width[v] || cams[v].height != batch->height[v])
+            return fail(IGS_ERR_INVALID_ARG, "view %d: image size differs from the layout", v);
+        host[v].vp = view_params(&cams[v], opts, nullptr);
+        host[v].tile_base = batch->tile_base[v];
+        host[v].img_off = batch->image_offset[v];
+    }
+    uint32_t goff = 0;
+    for (int v = 0; v < batch->views; ++v) {
+        host[v].grid_off = goff;
+        goff += (uint32_t)((host[v].vp.tiles_x + 1) * (host[v].vp.tiles_y + 1));
+    }
+    cudaError_t e = igs::batch_prepare_kernels(*batch);
+    if (e != cudaSuccess) return cuda_status(e, "igs_batch_set_views");
+    const int pb = igs::batch_persistent_blocks(batch->tile, batch->blend_batch);
+    if (pb <= 0) return fail(IGS_ERR_CUDA, "could not size the persistent blend");
+    batch->persistent_blocks = pb;
+    return cuda_status(igs::batch_set_views(*batch, host, (cudaStream_t)stream), "igs_batch_set_views");
+}
+
+igs_status igs_render_batch(igs_batch* batch, const igs_scene* scene, const igs_opts* opts, float* images,
+                            void* stream) {
+    igs_status st;
+    if (!batch || !batch->info) return fail(IGS_ERR_INVALID_ARG, "batch is NULL or not laid out");
+    if ((st = check_scene(scene)) || (st = check_opts(opts))) return st;
+    if (scene->n != batch->n) return fail(IGS_ERR_INVALID_ARG, "batch laid out for another n");
+    if (opts->tile != batch->tile) return fail(IGS_ERR_INVALID_ARG, "batch laid out for another tile size");
+    if (!images) return fail(IGS_ERR_INVALID_ARG, "images is NULL");
+    if (batch->persistent_blocks <= 0) return fail(IGS_ERR_INVALID_ARG, "call igs_batch_set_views first");
+    igs::BlendParams bp;
+    bp.width = bp.height = bp.tiles_x = bp.tiles_y = 0;
+    bp.alpha_min = opts->alpha_min; bp.alpha_max = opts->alpha_max; bp.t_min = opts->t_min;
+    for (int i = 0; i < 3; ++i) bp.bg[i] = opts->bg[i];
+    return cuda_status(igs::launch_render_batch(*batch, *scene, bp, opts->sh_degree, images, (cudaStream_t)stream),
+                       "igs_render_batch");
+}
+
+igs_status igs_batch_status(const igs_batch* batch, uint32_t* host_info, void* stream) {
+    if (!batch || !batch->info || !host_info) return fail(IGS_ERR_INVALID_ARG, "batch or host_info is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(host_info, batch->info, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "igs_batch_status");
+    if (host_info[igs::kInfoErr] != 0) {
+        const igs_status d = (igs_status)host_info[igs::kInfoErr];
+        return fail(d, "device reported: %s (entries needed = %u)", igs_status_string(d), host_info[igs::kInfoNeed]);
+    }
+    return IGS_OK;
+}
+
 igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info, void* stream) {
     igs_status st;
     if ((st = check_frame(frame))) return st;

@@ -11,27 +11,10 @@
 // in reverse from n_contrib, recovering T_k = T_{k+1} / (1 - alpha_k) from the
 // saved T_final, and reduces the per-pixel gradient terms of each entry over
 // the tile before one vector atomic per (entry, 4 floats).
-#include "common.cuh"
+#include "blendtile.cuh"
 
 namespace igs {
 namespace {
-
-struct Alpha {
-    float alpha, g, og, d2, dx, dy;
-};
-
-// The alpha of one (pixel, entry) pair, written with explicit roundings so the
-// forward and backward kernels take exactly the same skip / stop / clamp decisions.
-__device__ __forceinline__ Alpha eval_alpha(float px, float py, float4 a, float alpha_max) {
-    Alpha r;
-    r.dx = __fsub_rn(px, a.x);
-    r.dy = __fsub_rn(py, a.y);
-    r.d2 = __fmaf_rn(r.dx, r.dx, __fmul_rn(r.dy, r.dy));
-    r.g = fast_exp2(-__fmul_rn(a.z, r.d2));
-    r.og = __fmul_rn(a.w, r.g);
-    r.alpha = fminf(alpha_max, r.og);
-    return r;
-}
 
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
@@ -44,48 +27,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend_fwd(const uint2* __restrict__ 
     __shared__ float4 s_c[NT];
     if (info[kInfoAbort]) return;
     const int tile = blockIdx.x;
-    const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-    const int x = tx * TS + (threadIdx.x % TS), y = ty * TS + (threadIdx.x / TS);
-    const bool inside = x < P.width && y < P.height;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-    const uint2 rg = ranges[tile];
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += NT) {
-        if (__syncthreads_count(done) == NT) break;
-        const uint32_t j = b0 + threadIdx.x;
-        if (j < rg.y) {
-            const uint32_t g = vals[j];
-            s_a[threadIdx.x] = rec[2 * g];
-            s_c[threadIdx.x] = rec[2 * g + 1];
-        }
-        __syncthreads();
-        const int nb = (int)min((uint32_t)NT, rg.y - b0);
-        for (int k = 0; k < nb && !done; ++k) {
-            const Alpha a = eval_alpha(px, py, s_a[k], P.alpha_max);
-            if (a.alpha < P.alpha_min) continue;
-            const float Tn = T * (1.f - a.alpha);
-            if (Tn < P.t_min) {
-                done = true;
-                break;
-            }
-            const float4 c = s_c[k];
-            const float w = a.alpha * T;
-            C0 = fmaf(c.x, w, C0);
-            C1 = fmaf(c.y, w, C1);
-            C2 = fmaf(c.z, w, C2);
-            T = Tn;
-            last = b0 - rg.x + k + 1;
-        }
-    }
-    if (!inside) return;
-    const size_t pix = (size_t)y * P.width + x, plane = (size_t)P.width * P.height;
-    img[pix] = fmaf(T, P.bg[0], C0);
-    img[plane + pix] = fmaf(T, P.bg[1], C1);
-    img[2 * plane + pix] = fmaf(T, P.bg[2], C2);
-    T_final[pix] = T;
-    n_contrib[pix] = last;
+    blend_tile_fwd<TS, NT>(tile % P.tiles_x, tile / P.tiles_x, P.width, P.height, ranges[tile], vals, rec, P.alpha_min,
+                           P.alpha_max, P.t_min, P.bg, s_a, s_c, img, T_final, n_contrib);
 }
 
 // Butterfly reduce-scatter of 8 values over a warp in 9 shuffles: afterwards

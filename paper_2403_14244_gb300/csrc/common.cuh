@@ -115,6 +115,22 @@ struct AdamParams {
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, const AdamParams& a,
                         cudaStream_t s);
 
+// Multi-view batch (batch.cu): per-view record in device memory (the view table).
+struct BatchView {
+    ViewParams vp;
+    uint32_t tile_base;  // global id of the view's first tile
+    uint32_t grid_off;   // first cell of the view's corner grid
+    int64_t img_off;     // first float of the view's image in the packed buffer
+};
+int64_t batch_grid_cells(const igs_batch& b);
+size_t batch_scratch_bytes(const igs_batch& b);
+bool batch_blend_variant_ok(int tile, int batch);
+cudaError_t batch_set_views(const igs_batch& b, const BatchView* host_views, cudaStream_t st);
+cudaError_t batch_prepare_kernels(const igs_batch& b);
+cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const BlendParams& bp, int sh_degree,
+                                float* images, cudaStream_t st);
+int batch_persistent_blocks(int tile, int batch);
+
 // Scratch layout of a frame (pieces of igs_frame::scratch).
 struct SortScratch {
     unsigned long long* ditems_a;     // [n] (depth key | index) items

@@ -1,137 +1,10 @@
 // Projection of isotropic Gaussians to screen-space discs (with the
-// activation of log sigma and the opacity logit fused in) and its adjoint.
-//
-// Eq. 7 with Sigma = sigma^2 I projects to a disc; the on-axis radius
-// s = fx sigma / z_c depends only on the depth (Sec. 2.4). The support radius
-// r = 3.33 s bounds the tiles a Gaussian can touch (compact support, Eq. 2).
-// The key path (cull decisions, depth bits, tile rectangle) uses explicitly
-// rounded FP32 operations in a fixed order so that it is bit-reproducible.
-#include "common.cuh"
+// activation of log sigma and the opacity logit fused in) and its adjoint; the
+// per-Gaussian math is in projection.cuh.
+#include "projection.cuh"
 
 namespace igs {
 namespace {
-
-// Real orthonormal spherical harmonics without Condon-Shortley phase, written
-// as polynomials of the unit direction (x, y, z); index k = l^2 + l + m.
-// Constants: sqrt(2) K_lm times the leading factor of d^m P_l / dz^m, with
-// K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).
-constexpr float kSh0 = 0.28209479177387814f;
-constexpr float kSh1 = 0.4886025119029199f;
-constexpr float kSh2a = 1.0925484305920792f;   // xy, yz, xz
-constexpr float kSh2b = 0.31539156525252005f;  // (3z^2 - 1)
-constexpr float kSh2c = 0.5462742152960396f;   // (x^2 - y^2)
-constexpr float kSh3a = 0.5900435899266435f;   // (3x^2 y - y^3), (x^3 - 3 x y^2)
-constexpr float kSh3b = 2.890611442640554f;    // xyz
-constexpr float kSh3c = 0.4570457994644658f;   // y (5z^2 - 1), x (5z^2 - 1)
-constexpr float kSh3d = 0.3731763325901154f;   // (5z^3 - 3z)
-constexpr float kSh3e = 1.445305721320277f;    // z (x^2 - y^2)
-
-__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16]) {
-    Y[0] = kSh0;
-    if (deg < 1) return;
-    Y[1] = kSh1 * y;
-    Y[2] = kSh1 * z;
-    Y[3] = kSh1 * x;
-    if (deg < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = kSh2a * x * y;
-    Y[5] = kSh2a * y * z;
-    Y[6] = kSh2b * (3.f * zz - 1.f);
-    Y[7] = kSh2a * x * z;
-    Y[8] = kSh2c * (xx - yy);
-    if (deg < 3) return;
-    Y[9] = kSh3a * y * (3.f * xx - yy);
-    Y[10] = kSh3b * x * y * z;
-    Y[11] = kSh3c * y * (5.f * zz - 1.f);
-    Y[12] = kSh3d * z * (5.f * zz - 3.f);
-    Y[13] = kSh3c * x * (5.f * zz - 1.f);
-    Y[14] = kSh3e * z * (xx - yy);
-    Y[15] = kSh3a * x * (xx - 3.f * yy);
-}
-
-// Gradient of the polynomial extension of each basis function.
-__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float G[16][3]) {
-    G[0][0] = G[0][1] = G[0][2] = 0.f;
-    if (deg < 1) return;
-    G[1][0] = 0.f;   G[1][1] = kSh1; G[1][2] = 0.f;
-    G[2][0] = 0.f;   G[2][1] = 0.f;  G[2][2] = kSh1;
-    G[3][0] = kSh1;  G[3][1] = 0.f;  G[3][2] = 0.f;
-    if (deg < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    G[4][0] = kSh2a * y;        G[4][1] = kSh2a * x;         G[4][2] = 0.f;
-    G[5][0] = 0.f;              G[5][1] = kSh2a * z;         G[5][2] = kSh2a * y;
-    G[6][0] = 0.f;              G[6][1] = 0.f;               G[6][2] = kSh2b * 6.f * z;
-    G[7][0] = kSh2a * z;        G[7][1] = 0.f;               G[7][2] = kSh2a * x;
-    G[8][0] = kSh2c * 2.f * x;  G[8][1] = -kSh2c * 2.f * y;  G[8][2] = 0.f;
-    if (deg < 3) return;
-    G[9][0] = kSh3a * 6.f * x * y;        G[9][1] = kSh3a * 3.f * (xx - yy);   G[9][2] = 0.f;
-    G[10][0] = kSh3b * y * z;             G[10][1] = kSh3b * x * z;            G[10][2] = kSh3b * x * y;
-    G[11][0] = 0.f;                       G[11][1] = kSh3c * (5.f * zz - 1.f); G[11][2] = kSh3c * 10.f * y * z;
-    G[12][0] = 0.f;                       G[12][1] = 0.f;                      G[12][2] = kSh3d * (15.f * zz - 3.f);
-    G[13][0] = kSh3c * (5.f * zz - 1.f);  G[13][1] = 0.f;                      G[13][2] = kSh3c * 10.f * x * z;
-    G[14][0] = kSh3e * 2.f * x * z;       G[14][1] = -kSh3e * 2.f * y * z;     G[14][2] = kSh3e * (xx - yy);
-    G[15][0] = kSh3a * 3.f * (xx - yy);   G[15][1] = -kSh3a * 6.f * x * y;    G[15][2] = 0.f;
-}
-
-// Gradient of basis function k alone (k is a compile-time constant after unrolling).
-__device__ __forceinline__ void sh_grad_one(int k, float x, float y, float z, float& gx, float& gy, float& gz) {
-    const float xx = x * x, yy = y * y, zz = z * z;
-    switch (k) {
-        case 1: gx = 0.f; gy = kSh1; gz = 0.f; break;
-        case 2: gx = 0.f; gy = 0.f; gz = kSh1; break;
-        case 3: gx = kSh1; gy = 0.f; gz = 0.f; break;
-        case 4: gx = kSh2a * y; gy = kSh2a * x; gz = 0.f; break;
-        case 5: gx = 0.f; gy = kSh2a * z; gz = kSh2a * y; break;
-        case 6: gx = 0.f; gy = 0.f; gz = kSh2b * 6.f * z; break;
-        case 7: gx = kSh2a * z; gy = 0.f; gz = kSh2a * x; break;
-        case 8: gx = kSh2c * 2.f * x; gy = -kSh2c * 2.f * y; gz = 0.f; break;
-        case 9: gx = kSh3a * 6.f * x * y; gy = kSh3a * 3.f * (xx - yy); gz = 0.f; break;
-        case 10: gx = kSh3b * y * z; gy = kSh3b * x * z; gz = kSh3b * x * y; break;
-        case 11: gx = 0.f; gy = kSh3c * (5.f * zz - 1.f); gz = kSh3c * 10.f * y * z; break;
-        case 12: gx = 0.f; gy = 0.f; gz = kSh3d * (15.f * zz - 3.f); break;
-        case 13: gx = kSh3c * (5.f * zz - 1.f); gy = 0.f; gz = kSh3c * 10.f * x * z; break;
-        case 14: gx = kSh3e * 2.f * x * z; gy = -kSh3e * 2.f * y * z; gz = kSh3e * (xx - yy); break;
-        case 15: gx = kSh3a * 3.f * (xx - yy); gy = -kSh3a * 6.f * x * y; gz = 0.f; break;
-        default: gx = gy = gz = 0.f; break;
-    }
-}
-
-__device__ __forceinline__ bool finite4(float a, float b, float c, float d) {
-    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
-}
-
-// Camera-space position in the canonical order ((R0 x + R1 y) + R2 z) + t0,
-// every operation rounded once.
-__device__ __forceinline__ float cam_row(const float* R, float t, float x, float y, float z) {
-    return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(R[0], x), __fmul_rn(R[1], y)), __fmul_rn(R[2], z)), t);
-}
-
-__device__ __forceinline__ void activate(int mode, float raw_sigma, float raw_op, float& sg, float& o) {
-    if (mode == 1) {
-        sg = expf(raw_sigma);
-        o = 1.f / (1.f + expf(-raw_op));
-    } else {
-        sg = raw_sigma;
-        o = raw_op;
-    }
-}
-
-template <int DEG>
-__device__ __forceinline__ void load_color(const float* __restrict__ col, int64_t i, float c[48]) {
-    constexpr int C = DEG < 0 ? 3 : 3 * (DEG + 1) * (DEG + 1);
-    const float* p = col + (size_t)C * (size_t)i;
-    if constexpr (C % 4 == 0) {
-        const float4* p4 = reinterpret_cast<const float4*>(p);
-#pragma unroll
-        for (int q = 0; q < C / 4; ++q) {
-            float4 v = __ldg(p4 + q);
-            c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < C; ++q) c[q] = __ldg(p + q);
-    }
-}
 
 template <int DEG>
 __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ ms, const float* __restrict__ op,
@@ -140,75 +13,7 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ ms, 
                                                  uint32_t* __restrict__ count, uint32_t* __restrict__ depth_key) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float4 m = __ldg(ms + i);
-    float sg, o;
-    activate(P.param_mode, m.w, __ldg(op + i), sg, o);
-    bool keep = finite4(m.x, m.y, m.z, sg) && isfinite(o);
-    float xc = 0.f, yc = 0.f, zc = 0.f;
-    if (keep) {
-        xc = cam_row(P.R + 0, P.t[0], m.x, m.y, m.z);
-        yc = cam_row(P.R + 3, P.t[1], m.x, m.y, m.z);
-        zc = cam_row(P.R + 6, P.t[2], m.x, m.y, m.z);
-        keep = (zc > P.znear) && (sg > 0.f) && (o >= 1.0f / 255.0f);
-    }
-    float s = 0.f, u = 0.f, v = 0.f;
-    int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
-    if (keep) {
-        s = __fdiv_rn(__fmul_rn(P.fx, sg), zc);
-        u = __fadd_rn(__fdiv_rn(__fmul_rn(P.fx, xc), zc), P.cx);
-        v = __fadd_rn(__fdiv_rn(__fmul_rn(P.fy, yc), zc), P.cy);
-        const float r = __fmul_rn(kRadiusK, s);
-        keep = isfinite(u) && isfinite(v) && isfinite(r);
-        if (keep) {
-            const float ts = (float)P.tile;
-            const float fx0 = floorf(__fdiv_rn(__fsub_rn(u, r), ts));
-            const float fx1 = floorf(__fdiv_rn(__fadd_rn(u, r), ts));
-            const float fy0 = floorf(__fdiv_rn(__fsub_rn(v, r), ts));
-            const float fy1 = floorf(__fdiv_rn(__fadd_rn(v, r), ts));
-            keep = !(fx1 < 0.f || fx0 > (float)(P.tiles_x - 1) || fy1 < 0.f || fy0 > (float)(P.tiles_y - 1));
-            if (keep) {
-                x0 = (int)fmaxf(fx0, 0.f);
-                y0 = (int)fmaxf(fy0, 0.f);
-                x1 = (int)fminf(fx1, (float)(P.tiles_x - 1));
-                y1 = (int)fminf(fy1, (float)(P.tiles_y - 1));
-            }
-        }
-    }
-    if (!keep) {
-        count[i] = 0;
-        depth_key[i] = 0xFFFFFFFFu;
-        rect[i] = make_uint2(0u, 0u);
-        rec[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        rec[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    count[i] = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-    depth_key[i] = __float_as_uint(zc);
-    rect[i] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
-    // colour
-    float c[48];
-    load_color<DEG>(col, i, c);
-    float rgb[3];
-    if constexpr (DEG < 0) {
-        rgb[0] = c[0]; rgb[1] = c[1]; rgb[2] = c[2];
-    } else {
-        float dx = m.x - P.cam_center[0], dy = m.y - P.cam_center[1], dz = m.z - P.cam_center[2];
-        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= inv; dy *= inv; dz *= inv;
-        float Y[16];
-        sh_basis(DEG, dx, dy, dz, Y);
-        constexpr int K = (DEG + 1) * (DEG + 1);
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc = fmaf(c[3 * k + ch], Y[k], acc);
-            rgb[ch] = fmaxf(acc + 0.5f, 0.f);
-        }
-    }
-    const float w2 = 0.5f * kLog2e / (s * s);
-    rec[2 * i] = make_float4(u, v, w2, o);
-    rec[2 * i + 1] = make_float4(rgb[0], rgb[1], rgb[2], s);
+    project_one<DEG>(ms, op, col, i, P, rec + 2 * i, rect + i, count + i, depth_key + i);
 }
 
 // Colour rows of a warp's 32 Gaussians are staged in shared memory so that

@@ -57,6 +57,19 @@ class IgsFrame(C.Structure):
                 ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t)]
 
 
+MAX_VIEWS = 256
+
+
+class IgsBatch(C.Structure):
+    _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("views", C.c_int32), ("tile", C.c_int32),
+                ("blend_batch", C.c_int32), ("persistent_blocks", C.c_int32), ("tiles_total", C.c_int64),
+                ("image_floats", C.c_int64), ("image_offset", C.c_int64 * MAX_VIEWS),
+                ("tile_base", C.c_uint32 * MAX_VIEWS), ("width", C.c_int32 * MAX_VIEWS),
+                ("height", C.c_int32 * MAX_VIEWS), ("rec", C.c_void_p), ("rect", C.c_void_p), ("count", C.c_void_p),
+                ("depth_key", C.c_void_p), ("order", C.c_void_p), ("offset", C.c_void_p), ("vals", C.c_void_p),
+                ("ranges", C.c_void_p), ("info", C.c_void_p), ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t)]
+
+
 SYMBOLS = {
     # name: (restype, argtypes)
     "igs_abi_version": (C.c_int32, []),
@@ -85,6 +98,12 @@ SYMBOLS = {
     "igs_frame_status": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_uint32), C.c_void_p]),
     "igs_frame_reset_status": (C.c_int, [C.POINTER(IgsFrame), C.c_void_p]),
     "igs_sort_depth_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "igs_batch_layout": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.c_int64,
+                                   C.c_int32, C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(IgsBatch)]),
+    "igs_batch_set_views": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.c_void_p]),
+    "igs_render_batch": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(IgsScene), C.POINTER(IgsOpts), C.c_void_p,
+                                   C.c_void_p]),
+    "igs_batch_status": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(C.c_uint32), C.c_void_p]),
 }
 
 
@@ -316,6 +335,51 @@ def sort_depth_noalloc(depth_key, order, stream=None):
     uint32 data, n <= 2^20), scratch from the library's static device array."""
     _check(load().igs_sort_depth_noalloc(_ptr(depth_key), int(depth_key.numel()), _ptr(order), _stream(stream)),
            "igs_sort_depth_noalloc")
+
+
+class Batch:
+    """One multi-view batch: workspace from igs_batch_layout and the packed image buffer."""
+
+    def __init__(self, n, cams, o, capacity, blend_batch=0, device="cuda"):
+        lib = load()
+        self.cams = [c if isinstance(c, IgsCamera) else camera(c) for c in cams]
+        self.opts = o
+        arr = (IgsCamera * len(self.cams))(*self.cams)
+        nbytes = C.c_size_t(0)
+        _check(lib.igs_batch_layout(int(n), len(self.cams), arr, C.byref(o), int(capacity), int(blend_batch), None,
+                                    C.byref(nbytes), None), "igs_batch_layout")
+        self.nbytes = int(nbytes.value)
+        self.ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.ws.data_ptr()
+        self.struct = IgsBatch()
+        _check(lib.igs_batch_layout(int(n), len(self.cams), arr, C.byref(o), int(capacity), int(blend_batch),
+                                    C.c_void_p(base + (-base) % 256), C.byref(nbytes), C.byref(self.struct)),
+               "igs_batch_layout")
+        self.images = torch.empty(int(self.struct.image_floats), dtype=torch.float32, device=device)
+        self.n, self.capacity = int(n), int(capacity)
+
+    def set_views(self, cams=None, stream=None):
+        if cams is not None:
+            self.cams = [c if isinstance(c, IgsCamera) else camera(c) for c in cams]
+        arr = (IgsCamera * len(self.cams))(*self.cams)
+        _check(load().igs_batch_set_views(C.byref(self.struct), arr, C.byref(self.opts), _stream(stream)),
+               "igs_batch_set_views")
+
+    def render(self, scene: "Scene", stream=None):
+        _check(load().igs_render_batch(C.byref(self.struct), C.byref(scene.struct), C.byref(self.opts),
+                                       _ptr(self.images), _stream(stream)), "igs_render_batch")
+
+    def status(self, stream=None):
+        info = (C.c_uint32 * 4)()
+        st = load().igs_batch_status(C.byref(self.struct), info, _stream(stream))
+        if st not in (OK, ERR_CAPACITY, ERR_DEVICE_TIMEOUT):
+            _check(st, "igs_batch_status")
+        return st, list(info)
+
+    def image(self, v):
+        off = int(self.struct.image_offset[v])
+        h, w = int(self.struct.height[v]), int(self.struct.width[v])
+        return self.images[off:off + 3 * h * w].view(3, h, w)
 
 
 def launch_count() -> int:
