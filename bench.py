@@ -308,6 +308,150 @@ def run_extra(dev, np):
     st, info = igs.frame_status(f)
     assert st == igs.OK
     out["fwd_bwd_1080p_1M"]["entries_M"] = info[0]
+    del scene, r, f, img, g2d, grads
+    torch.cuda.empty_cache()
+    out["batched_32view_2M"] = run_batched(dev)
+    out["serve_4scenes_poisson200"] = run_serving(dev)
+    return out
+
+
+def run_batched(dev, reps=10):
+    """32 views (sphere poses, mixed 360p..1440p) of a 2M-Gaussian RGB scene:
+    autotuned batched graph replays vs a loop of one-view renders, frames/s."""
+    import torch
+
+    from paper_2403_14244_gb300 import igs, scenes
+    from paper_2403_14244_gb300.batch import BatchRenderer, autotune
+    from paper_2403_14244_gb300.render import Renderer
+
+    sc = scenes.uniform_scene(2_000_000, 4)
+    scene = igs.Scene.from_numpy(sc, dev)
+    cams = [igs.camera(c) for c in scenes.sphere_cameras(32, 4)]
+    cache = os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
+        else None
+    (tile, bb), timings = autotune(scene, cams, candidates=[(8, 64), (16, 128), (16, 256), (32, 512)], reps=3,
+                                   cache_path=cache, use_cache=False, device=dev)
+    br = BatchRenderer(scene, cams, tile=tile, blend_batch=bb, device=dev)
+    br.capture()
+    for _ in range(2):
+        br.replay()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        br.replay()
+    b.record()
+    torch.cuda.synchronize(dev)
+    br.check()
+    batched_ms = a.elapsed_time(b) / reps
+    entries = sum(br.entries)
+    del br
+    torch.cuda.empty_cache()
+    # one view at a time through the one-view path (capacity from a checked first
+    # pass), at each tile size; the best one is the baseline
+    loop = {}
+    for lt in (16, 32):
+        r = Renderer(tile=lt, device=dev)
+        imgs = {}
+        for c in cams:
+            imgs[(c.width, c.height)] = r.run_forward(scene, c, check=True)[0]
+        for _ in range(2):
+            for c in cams:
+                r.run_forward(scene, c, img=imgs[(c.width, c.height)], check=False)
+        torch.cuda.synchronize(dev)
+        a.record()
+        for _ in range(reps):
+            for c in cams:
+                r.run_forward(scene, c, img=imgs[(c.width, c.height)], check=False)
+        b.record()
+        torch.cuda.synchronize(dev)
+        loop[lt] = a.elapsed_time(b) / reps
+        del r, imgs
+        torch.cuda.empty_cache()
+    lt = min(loop, key=loop.get)
+    return {"views": len(cams), "tile": tile, "blend_batch": bb, "entries": entries,
+            "autotune_ms": {k: round(v, 3) for k, v in timings.items()},
+            "batched_ms": round(batched_ms, 3), "batched_frames_per_s": round(len(cams) * 1e3 / batched_ms, 1),
+            "loop_ms_by_tile": {str(k): round(v, 3) for k, v in loop.items()}, "loop_tile": lt,
+            "loop_frames_per_s": round(len(cams) * 1e3 / loop[lt], 1)}
+
+
+def run_serving(dev, n_req=2000, warm=200, rate=200.0, budget=8 << 30, seed=5, tile=32):
+    """Four resident scenes (0.5, 1, 2, 4M Gaussians), open-loop Poisson arrivals
+    at `rate`/s, random scene, sphere pose, 480p..2160p; served with 4 slots
+    (continuous batching) and strictly one at a time, on the same arrivals."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2403_14244_gb300 import igs, scenes
+
+    rng = np.random.default_rng(seed)
+    scs = [igs.Scene.from_numpy(scenes.uniform_scene(int(m * 1_000_000), 50 + k), dev)
+           for k, m in enumerate((0.5, 1, 2, 4))]
+    total = n_req + warm
+    gaps = rng.exponential(1.0 / rate, size=total)
+    which = rng.integers(0, 4, size=total)
+    cams = scenes.sphere_cameras(total, seed, resolutions=scenes.RESOLUTIONS_SERVE)
+    ring = 48
+    bufs = {(w, h): [torch.empty((3, h, w), device=dev) for _ in range(ring)] for w, h in scenes.RESOLUTIONS_SERVE}
+    out = {}
+
+    def serve(slots, gaps):
+        srv = igs.Server(pool_bytes=budget, slots=slots, tile=tile, device=dev)
+        sids = [srv.add_scene(sc) for sc in scs]
+        cam_s = [igs.camera(c) for c in cams]
+        ids = [None] * total
+        done = [threading.Event() for _ in range(total)]
+        timings = [None] * total
+        use = {k: [None] * ring for k in bufs}  # request last using each buffer
+
+        def poller():
+            for i in range(total):
+                while ids[i] is None:
+                    time.sleep(1e-4)
+                st, t = srv.poll(ids[i], timeout_s=120.0)
+                timings[i] = (st, t)
+                done[i].set()
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        arrive = time.perf_counter()
+        for i in range(total):
+            arrive += gaps[i]
+            c = cam_s[i]
+            key = (c.width, c.height)
+            slot = i % ring
+            prev = use[key][slot]
+            if prev is not None:
+                done[prev].wait()
+            use[key][slot] = i
+            delay = arrive - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = srv.submit(sids[which[i]], c, bufs[key][slot])
+        th.join()
+        stats = srv.stats()
+        srv.close()
+        meas = [timings[i][1] for i in range(warm, total)]
+        bad = sum(1 for i in range(warm, total) if timings[i][0] != igs.OK)
+        lat = np.array([(t["done_ns"] - t["arrival_ns"]) / 1e6 for t in meas])
+        span = (max(t["done_ns"] for t in meas) - min(t["arrival_ns"] for t in meas)) / 1e9
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "max_ms": round(float(lat.max()), 3), "frames_per_s": round((n_req - bad) / span, 1), "failed": bad,
+                "pool_peak_bytes": int(stats["pool_peak"]), "retries": int(sum(t["retries"] for t in meas))}
+
+    for slots in (4, 1):
+        out["poisson_slots%d" % slots] = serve(slots, gaps)
+    # the same requests submitted back to back: the throughput each mode can sustain
+    for slots in (4, 1):
+        out["burst_slots%d" % slots] = serve(slots, np.zeros(total))
+    out["tile"] = tile
+    out["requests"] = n_req
+    out["warmup"] = warm
+    out["rate_per_s"] = rate
+    out["pool_bytes"] = budget
     return out
 
 

@@ -121,7 +121,8 @@ typedef struct igs_frame {
     uint32_t* order;         /* [n] Gaussian ids, front to back (culled ones last) */
     uint32_t* offset;        /* [n] first entry of order[p]: exclusive scan of count in depth order */
     uint32_t* tile_key;      /* [capacity] tile id of each sorted entry (written by igs_export_keys) */
-    uint32_t* vals;          /* [capacity] Gaussian id of each sorted entry */
+    uint32_t* vals;          /* [capacity] Gaussian id of each sorted entry (tile_key and vals share
+                                the sort's scratch: valid until the next igs_bin_sort of this frame) */
     uint32_t* ranges;        /* [tiles][2] [start, end) of each tile's entries; (0, 0) if empty */
     float* T_final;          /* [H][W] transmittance after the last blended entry */
     uint32_t* n_contrib;     /* [H][W] 1 + list position (within the tile) of the last blended entry */
@@ -307,6 +308,55 @@ IGS_API igs_status igs_render_batch(igs_batch* batch, const igs_scene* scene, co
 
 /* Copy the batch's four status words to host_info and wait for `stream`. */
 IGS_API igs_status igs_batch_status(const igs_batch* batch, uint32_t* host_info, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Render server with continuous batching. Scenes stay resident (the caller
+ * keeps their buffers alive); requests are queued and admitted in arrival
+ * order as soon as a slot (a CUDA stream) is free and the request's frame
+ * workspace fits in the caller's device pool, so requests that arrive while
+ * others run overlap with them on the GPU. The entries a request needs are
+ * sized from earlier requests of the same scene and image size; a request that
+ * overflows is re-queued at the head with the capacity it reported. One host
+ * thread per server schedules; the library allocates no device memory (the pool
+ * is the caller's) and 16 bytes of pinned host memory per slot.
+ * ------------------------------------------------------------------------- */
+typedef struct igs_server igs_server;
+
+typedef struct igs_timing {
+    int64_t arrival_ns;  /* submit time (steady clock) */
+    int64_t admit_ns;    /* slot and memory granted */
+    int64_t start_ns;    /* first launch enqueued */
+    int64_t done_ns;     /* completion seen by the scheduler */
+    uint32_t entries;    /* (Gaussian, tile) entries of the view */
+    int32_t status;      /* igs_status of the request */
+    int32_t retries;     /* re-queues after a capacity overflow */
+    int32_t _pad;
+} igs_timing;
+
+/* Create a server on the current device. pool (device, 256-byte aligned,
+ * pool_bytes) holds every in-flight frame workspace; max_slots (1..64) requests
+ * run at once, each on its own stream. opts->tile, thresholds and background
+ * apply to every request; sh_degree / param_mode come with each scene. */
+IGS_API igs_status igs_serve_create(void* pool, size_t pool_bytes, int32_t max_slots, const igs_opts* opts,
+                                    igs_server** out);
+/* Register a resident scene (device buffers, layout as above); *scene_id
+ * identifies it in igs_serve_submit. */
+IGS_API igs_status igs_serve_add_scene(igs_server* server, const igs_scene* scene, int32_t sh_degree,
+                                       int32_t param_mode, int32_t* scene_id);
+/* Queue one render of scene_id from cam into img_out (device, [3][H][W]);
+ * returns at once with *req_id. IGS_ERR_CAPACITY if even an empty frame of this
+ * size cannot fit the pool. */
+IGS_API igs_status igs_serve_submit(igs_server* server, int32_t scene_id, const igs_camera* cam, float* img_out,
+                                    uint64_t* req_id);
+/* Wait up to timeout_ns for request req_id; IGS_ERR_NOT_READY if it is still
+ * running (poll again), otherwise the request's status, its timings in *t, and
+ * the request is forgotten (poll a finished request once). */
+IGS_API igs_status igs_serve_poll(igs_server* server, uint64_t req_id, int64_t timeout_ns, igs_timing* t);
+/* Queue length, requests in flight, pool bytes in use and the peak in use. */
+IGS_API igs_status igs_serve_stats(igs_server* server, int64_t* pending, int64_t* in_flight, int64_t* pool_used,
+                                   int64_t* pool_peak);
+/* Finish every queued request, then free the server's streams and host state. */
+IGS_API void igs_serve_destroy(igs_server* server);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all threads). For accounting in benchmarks; host-only, never fails. */

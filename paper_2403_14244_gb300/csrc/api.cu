@@ -142,8 +142,6 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     size_t o_dkey = off; off += align256((size_t)n * 4);
     size_t o_order = off; off += align256((size_t)n * 4);
     size_t o_offset = off; off += align256((size_t)n * 4);
-    size_t o_tkey = off; off += align256((size_t)capacity * 4);
-    size_t o_vals = off; off += align256((size_t)capacity * 4);
     size_t o_ranges = off; off += align256((size_t)tiles * 8);
     size_t o_T = off; off += align256((size_t)P * 4);
     size_t o_nc = off; off += align256((size_t)P * 4);
@@ -170,14 +168,17 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     frame->depth_key = reinterpret_cast<uint32_t*>(b + o_dkey);
     frame->order = reinterpret_cast<uint32_t*>(b + o_order);
     frame->offset = reinterpret_cast<uint32_t*>(b + o_offset);
-    frame->tile_key = reinterpret_cast<uint32_t*>(b + o_tkey);
-    frame->vals = reinterpret_cast<uint32_t*>(b + o_vals);
     frame->ranges = reinterpret_cast<uint32_t*>(b + o_ranges);
     frame->T_final = reinterpret_cast<float*>(b + o_T);
     frame->n_contrib = reinterpret_cast<uint32_t*>(b + o_nc);
     frame->info = reinterpret_cast<uint32_t*>(b + o_info);
     frame->scratch = b + o_scr;
     frame->scratch_bytes = scr;
+    // vals and tile_key live in the sort's ping-pong item buffers (each is free
+    // when they are written), so a frame costs 16 bytes per entry of capacity
+    const igs::SortScratch ss = igs::sort_scratch(*frame);
+    frame->vals = ss.vals;
+    frame->tile_key = ss.tile_key;
     return IGS_OK;
 }
 

@@ -144,6 +144,8 @@ struct SortScratch {
     unsigned long long* scan_status;  // [scan blocks(n)]
     uint32_t* dup_start;              // [blocks(capacity) + 1] first Gaussian (in depth order) of each duplication block
     int32_t* grid;                    // [(tiles_y + 1) * (tiles_x + 1)] rectangle corner counts -> per-tile counts
+    uint32_t* vals;                   // sorted values: in the item buffer the last tile pass does not read
+    uint32_t* tile_key;               // exported tile ids: in the item buffer the last tile pass reads
     int tile_passes;
     int tile_bits;
 };

@@ -192,6 +192,14 @@ SortScratch sort_scratch(const igs_frame& f) {
     s.scan_status = (unsigned long long*)take((size_t)bs * 8);
     s.dup_start = (uint32_t*)take((size_t)(ceil_div(cap, kDupTile) + 1) * 4);
     s.grid = (int32_t*)take((size_t)(2 * tiles + 2) * 4);
+    // the last tile pass (p = passes - 1) reads items_a when p is even, items_b when odd
+    const bool last_reads_a = s.tile_passes > 0 && (s.tile_passes - 1) % 2 == 0;
+    s.vals = reinterpret_cast<uint32_t*>(last_reads_a ? s.items_b : s.items_a);
+    s.tile_key = reinterpret_cast<uint32_t*>(last_reads_a ? s.items_a : s.items_b);
+    if (s.tile_passes == 0) {  // the duplication writes the values directly
+        s.vals = reinterpret_cast<uint32_t*>(s.items_a);
+        s.tile_key = reinterpret_cast<uint32_t*>(s.items_b);
+    }
     return s;
 }
 

@@ -70,6 +70,11 @@ class IgsBatch(C.Structure):
                 ("ranges", C.c_void_p), ("info", C.c_void_p), ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t)]
 
 
+class IgsTiming(C.Structure):
+    _fields_ = [("arrival_ns", C.c_int64), ("admit_ns", C.c_int64), ("start_ns", C.c_int64), ("done_ns", C.c_int64),
+                ("entries", C.c_uint32), ("status", C.c_int32), ("retries", C.c_int32), ("_pad", C.c_int32)]
+
+
 SYMBOLS = {
     # name: (restype, argtypes)
     "igs_abi_version": (C.c_int32, []),
@@ -104,6 +109,14 @@ SYMBOLS = {
     "igs_render_batch": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(IgsScene), C.POINTER(IgsOpts), C.c_void_p,
                                    C.c_void_p]),
     "igs_batch_status": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(C.c_uint32), C.c_void_p]),
+    "igs_serve_create": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(IgsOpts), C.POINTER(C.c_void_p)]),
+    "igs_serve_add_scene": (C.c_int, [C.c_void_p, C.POINTER(IgsScene), C.c_int32, C.c_int32,
+                                      C.POINTER(C.c_int32)]),
+    "igs_serve_submit": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(IgsCamera), C.c_void_p,
+                                   C.POINTER(C.c_uint64)]),
+    "igs_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(IgsTiming)]),
+    "igs_serve_stats": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int64)] * 4),
+    "igs_serve_destroy": (None, [C.c_void_p]),
 }
 
 
@@ -380,6 +393,57 @@ class Batch:
         off = int(self.struct.image_offset[v])
         h, w = int(self.struct.height[v]), int(self.struct.width[v])
         return self.images[off:off + 3 * h * w].view(3, h, w)
+
+
+class Server:
+    """Render server (igs_serve_*): resident scenes, continuous batching over
+    `slots` streams, admission against a device pool of `pool_bytes`."""
+
+    def __init__(self, pool_bytes, slots=4, tile=16, bg=(0.0, 0.0, 0.0), device="cuda"):
+        self.pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=device)
+        base = self.pool.data_ptr()
+        self.opts = opts(tile=tile, bg=bg)
+        h = C.c_void_p()
+        _check(load().igs_serve_create(C.c_void_p(base + (-base) % 256), int(pool_bytes), int(slots),
+                                       C.byref(self.opts), C.byref(h)), "igs_serve_create")
+        self.handle = h
+        self.scenes = []
+
+    def add_scene(self, scene: Scene, sh_degree=-1, param_mode=0):
+        sid = C.c_int32()
+        _check(load().igs_serve_add_scene(self.handle, C.byref(scene.struct), int(sh_degree), int(param_mode),
+                                          C.byref(sid)), "igs_serve_add_scene")
+        self.scenes.append(scene)  # keep the buffers alive
+        return int(sid.value)
+
+    def submit(self, scene_id, cam, img_out):
+        c = cam if isinstance(cam, IgsCamera) else camera(cam)
+        rid = C.c_uint64()
+        _check(load().igs_serve_submit(self.handle, int(scene_id), C.byref(c), _ptr(img_out), C.byref(rid)),
+               "igs_serve_submit")
+        return int(rid.value)
+
+    def poll(self, req_id, timeout_s=10.0):
+        """(status, timing dict); status NOT_READY if still running after the timeout."""
+        t = IgsTiming()
+        st = load().igs_serve_poll(self.handle, C.c_uint64(req_id), int(timeout_s * 1e9), C.byref(t))
+        return st, {k: getattr(t, k) for k, _ in IgsTiming._fields_ if k != "_pad"}
+
+    def stats(self):
+        v = [C.c_int64() for _ in range(4)]
+        _check(load().igs_serve_stats(self.handle, *[C.byref(x) for x in v]), "igs_serve_stats")
+        return dict(zip(("pending", "in_flight", "pool_used", "pool_peak"), [x.value for x in v]))
+
+    def close(self):
+        if self.handle:
+            load().igs_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:
