@@ -266,6 +266,7 @@ static igs_status adam_params(double lr, double b1, double b2, double eps, int64
     a->omb2 = (float)(1.0 - b2);
     a->step_size = (float)(lr / bc1);
     a->bc2_sqrt = (float)std::sqrt(bc2);
+    a->inv_bc2_sqrt = (float)(1.0 / std::sqrt(bc2));
     a->eps = (float)eps;
     return IGS_OK;
 }

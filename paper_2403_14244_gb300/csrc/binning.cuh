@@ -24,6 +24,8 @@ constexpr unsigned long long kScanMask = 3ull << 62;
 constexpr unsigned long long kScanVal = kScanAgg - 1;
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kLookWindow = 8;
+// Consecutive entries one duplication thread writes.
+constexpr int kDupPerThread = kDupTile / 256;
 
 using u64 = unsigned long long;
 
@@ -206,6 +208,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
             run += c;
         }
     }
+    __syncthreads();
+    // stage the block's items in digit order (needs only block-local offsets, so it
+    // runs before the look-back and gives earlier blocks time to publish)
+#pragma unroll
+    for (int i = 0; i < kSortIpt; ++i) {
+        const uint32_t d = (uint32_t)(it[i] >> (32 + shift)) & 0xFFu;
+        s_items[s_whist[w][d] + ((rank2[i >> 1] >> (16 * (i & 1))) & 0xFFFFu)] = it[i];
+    }
     uint32_t excl = 0;
     if (blk > 0) {
         int64_t b = (int64_t)blk - 1;
@@ -226,7 +236,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
                         done = true;
                         break;
                     }
-                    __nanosleep(32);
+                    __nanosleep(200);
                     v[j] = ld_relaxed_u32(status + (size_t)(b - j) * kRadix + tid);
                 }
                 if (done) break;
@@ -238,13 +248,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
         st_relaxed_u32(&my[tid], kFlagPre | ((excl + cnt) & kValMask));
     }
     s_delta[tid] = (int32_t)(digit_base[tid] + excl) - (int32_t)local;
-    __syncthreads();
-    // stage the block's items in digit order
-#pragma unroll
-    for (int i = 0; i < kSortIpt; ++i) {
-        const uint32_t d = (uint32_t)(it[i] >> (32 + shift)) & 0xFFu;
-        s_items[s_whist[w][d] + ((rank2[i >> 1] >> (16 * (i & 1))) & 0xFFFFu)] = it[i];
-    }
     __syncthreads();
     // write out: runs of one digit land contiguously; past-the-end items hold the last slots
 #pragma unroll
@@ -407,45 +410,81 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
     // happens when culled Gaussians (no entries) sit inside the order, i.e. at the
     // end of each view of a batch; those entries search the global offsets.
     const uint32_t reach = s_off[cnt];
-    for (uint32_t e = (uint32_t)e0 + threadIdx.x; e < e_end; e += blockDim.x) {
-        uint32_t g, start;
+    // each thread: kDupPerThread consecutive entries, one search then a walk
+    const uint32_t first = (uint32_t)e0 + threadIdx.x * kDupPerThread;
+    if (first >= e_end) return;
+    const uint32_t last = min(first + kDupPerThread, e_end);
+    uint32_t k;       // window slot (or global position) of the current Gaussian
+    bool global;
+    auto locate = [&](uint32_t e) {
         if (e < reach) {
             uint32_t lo = 0, hi = cnt;  // largest k with s_off[k] <= e
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (s_off[mid] <= e) lo = mid; else hi = mid;
             }
-            g = s_ord[lo];
-            start = s_off[lo];
+            k = lo;
+            global = false;
         } else {
             uint32_t lo = pb, hi = n;  // largest p with offset[p] <= e
             while (hi - lo > 1) {
                 const uint32_t mid = lo + ((hi - lo) >> 1);
                 if (offset[mid] <= e) lo = mid; else hi = mid;
             }
-            g = order[lo];
-            start = offset[lo];
+            k = lo;
+            global = true;
         }
-        if (g >= n) continue;
-        const uint32_t j = e - start;
-        const uint2 r = rect[g];
-        const uint32_t x0 = r.x & 0xFFFF, y0 = r.x >> 16, wdt = (r.y & 0xFFFF) - x0 + 1;
-        // row = j / wdt: float estimate, then exact integer correction (j, wdt < 2^24)
-        uint32_t row = (uint32_t)__fmul_rz((float)j, __frcp_rz((float)wdt));
-        int32_t rem = (int32_t)j - (int32_t)(row * wdt);
-        if (rem < 0) { --row; rem += (int32_t)wdt; }
-        if (rem >= (int32_t)wdt) { ++row; rem -= (int32_t)wdt; }
-        uint32_t t;
-        if (BATCHED) {
-            const uint32_t v = g / view_len;
-            t = view_tile_base[v] + (y0 + row) * (uint32_t)view_tiles_x[v] + x0 + (uint32_t)rem;
+    };
+    locate(first);
+    uint32_t e = first;
+    while (e < last) {
+        const uint32_t g = global ? order[k] : s_ord[k];
+        const uint32_t start = global ? offset[k] : s_off[k];
+        const uint32_t next = global ? (k + 1 < n ? offset[k + 1] : M) : s_off[k + 1];
+        const uint32_t stop = min(last, next);
+        if (g < n && start <= e) {
+            const uint2 r = rect[g];
+            const uint32_t x0 = r.x & 0xFFFF, y0 = r.x >> 16, wdt = (r.y & 0xFFFF) - x0 + 1;
+            const uint32_t j = e - start;
+            // (row, col) of entry j in the rectangle: float estimate, exact correction
+            uint32_t row = (uint32_t)__fmul_rz((float)j, __frcp_rz((float)wdt));
+            int32_t col = (int32_t)j - (int32_t)(row * wdt);
+            if (col < 0) { --row; col += (int32_t)wdt; }
+            if (col >= (int32_t)wdt) { ++row; col -= (int32_t)wdt; }
+            uint32_t tpr, base;  // tiles per row and first tile id of the view
+            if (BATCHED) {
+                const uint32_t v = g / view_len;
+                tpr = (uint32_t)view_tiles_x[v];
+                base = view_tile_base[v];
+            } else {
+                tpr = (uint32_t)tiles_x;
+                base = 0;
+            }
+            uint32_t t = base + (y0 + row) * tpr + x0 + (uint32_t)col;
+            for (; e < stop; ++e) {
+                if (vals_direct)
+                    vals_direct[e] = g;
+                else
+                    items[e] = ((u64)t << 32) | g;
+                // next tile of the rectangle, row-major
+                if (++col == (int32_t)wdt) {
+                    col = 0;
+                    t += tpr - wdt + 1;
+                } else {
+                    ++t;
+                }
+            }
         } else {
-            t = (y0 + row) * (uint32_t)tiles_x + x0 + (uint32_t)rem;
+            e = stop;
         }
-        if (vals_direct)
-            vals_direct[e] = g;
-        else
-            items[e] = ((u64)t << 32) | g;
+        if (e >= last) break;
+        // the next Gaussian with entries
+        if (!global && k + 1 < cnt && e < reach) {
+            ++k;
+            while (k + 1 < cnt && s_off[k + 1] <= e) ++k;
+        } else {
+            locate(e);
+        }
     }
 }
 

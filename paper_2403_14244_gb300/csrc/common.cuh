@@ -110,6 +110,7 @@ struct AdamParams {
     float b1, b2, omb1, omb2;  // beta1, beta2, 1 - beta1, 1 - beta2
     float step_size;           // lr / (1 - beta1^t)
     float bc2_sqrt;            // sqrt(1 - beta2^t)
+    float inv_bc2_sqrt;        // 1 / sqrt(1 - beta2^t)
     float eps;
 };
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, const AdamParams& a,

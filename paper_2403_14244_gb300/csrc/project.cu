@@ -34,10 +34,12 @@ struct ColorTile {
 
 constexpr int kPbThreads = 128;
 
+// Adam on one parameter (the fused kernel's hot loop: 53 updates per Gaussian);
+// the bias correction is a multiplication and the step a fast division (2 ulp).
 __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, const AdamParams& a) {
     m = a.b1 * m + a.omb1 * g;
     v = a.b2 * v + a.omb2 * g * g;
-    p -= a.step_size * m / (sqrtf(v) / a.bc2_sqrt + a.eps);
+    p -= __fdividef(a.step_size * m, fmaf(sqrtf(v), a.inv_bc2_sqrt, a.eps));
 }
 __device__ __forceinline__ void adam_update4(float4& p, float4 g, float4& m, float4& v, const AdamParams& a) {
     adam_update(p.x, g.x, m.x, v.x, a);
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
         }
         __syncwarp();
         const size_t row0 = (size_t)wb * CT::kF4;
+#pragma unroll 4
         for (int q = lane; q < nv * CT::kF4; q += 32) {
             const int g = q / CT::kF4;
             const int c0 = 4 * (q - g * CT::kF4);  // first coefficient of this float4

@@ -126,6 +126,68 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* _
     for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) hist_tile[k] = (&s_h[0][0])[k];
 }
 
+// One block, grid in shared memory (cells <= kGridSmemCells): the 2D prefix of
+// the corner grid, the tile ranges, the tile-digit histograms, and every digit
+// histogram (4 depth + `passes` tile rows) turned into exclusive offsets.
+constexpr int kTilesSmallThreads = 1024;
+__global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_t* __restrict__ grid, int tiles_x,
+                                                                    int tiles_y, int passes,
+                                                                    uint2* __restrict__ ranges,
+                                                                    uint32_t* __restrict__ hist,
+                                                                    uint32_t* __restrict__ info) {
+    extern __shared__ int32_t s_g[];
+    __shared__ uint32_t s_h[8][kRadix];
+    __shared__ uint32_t s_warp[kTilesSmallThreads / 32];
+    const int gx = tiles_x + 1, cells = gx * (tiles_y + 1);
+    const int tid = threadIdx.x;
+    for (int k = tid; k < cells; k += blockDim.x) s_g[k] = grid[k];
+    for (int k = tid; k < 4 * kRadix; k += blockDim.x) (&s_h[0][0])[k] = hist[k];          // depth counts
+    for (int k = tid; k < 4 * kRadix; k += blockDim.x) (&s_h[4][0])[k] = 0;                // tile counts
+    __syncthreads();
+    for (int y = tid; y < tiles_y; y += blockDim.x) {
+        int32_t run = 0;
+        for (int x = 0; x < tiles_x; ++x) { run += s_g[y * gx + x]; s_g[y * gx + x] = run; }
+    }
+    __syncthreads();
+    for (int x = tid; x < tiles_x; x += blockDim.x) {
+        int32_t run = 0;
+        for (int y = 0; y < tiles_y; ++y) { run += s_g[y * gx + x]; s_g[y * gx + x] = run; }
+    }
+    __syncthreads();
+    const uint32_t tiles = (uint32_t)tiles_x * tiles_y;
+    const uint32_t per = (tiles + kTilesSmallThreads - 1) / kTilesSmallThreads;
+    const uint32_t t0 = min(tiles, tid * per), t1 = min(tiles, t0 + per);
+    uint32_t sum = 0;
+    for (uint32_t t = t0; t < t1; ++t) sum += (uint32_t)s_g[(t / tiles_x) * gx + (t % tiles_x)];
+    uint32_t start = block_excl_scan<kTilesSmallThreads>(sum, s_warp);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t c = (uint32_t)s_g[(t / tiles_x) * gx + (t % tiles_x)];
+        ranges[t] = c ? make_uint2(start, start + c) : make_uint2(0u, 0u);
+        start += c;
+        if (c)
+            for (int p = 0; p < passes; ++p) atomicAdd(&s_h[4 + p][(t >> (8 * p)) & 0xFF], c);
+    }
+    if (t1 == tiles && t0 < t1) info[kInfoTileTotal] = start;
+    __syncthreads();
+    // exclusive offsets of every histogram row
+    const int rows = 4 + passes;
+    uint32_t v[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int idx = tid + r * kTilesSmallThreads;
+        v[r] = 0;
+        if (idx < rows * kRadix) {
+            const uint32_t* row = &s_h[idx >> 8][0];
+            for (int k = 0; k < (idx & 255); ++k) v[r] += row[k];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int idx = tid + r * kTilesSmallThreads;
+        if (idx < rows * kRadix) hist[idx] = v[r];
+    }
+}
+
 // Sorted 64-bit keys (tile << 32 | depth bits) and the tile id of every entry,
 // from the ranges: block t fills the entries of tile t.
 __global__ void k_export_keys(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
@@ -235,19 +297,27 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
                                                        nn, gx, gy, s.hist, s.grid);
     count_launches();
     CK(cudaGetLastError());
-    k_grid_rows<<<(unsigned)ceil_div(f.tiles_y, 128), 128, 0, st>>>(s.grid, gx, f.tiles_x, f.tiles_y);
-    count_launches();
-    CK(cudaGetLastError());
-    k_grid_cols<<<(unsigned)ceil_div(f.tiles_x, 128), 128, 0, st>>>(s.grid, gx, f.tiles_x, f.tiles_y);
-    count_launches();
-    CK(cudaGetLastError());
-    k_tile_scan<<<1, kTileScanThreads, 0, st>>>(s.grid, gx, f.tiles_x, (uint32_t)tiles, tp,
-                                                reinterpret_cast<uint2*>(f.ranges), s.hist + 4 * kRadix, f.info);
-    count_launches();
-    CK(cudaGetLastError());
-    k_hist_to_offsets<<<1, 1024, 0, st>>>(s.hist, 4 + tp);
-    count_launches();
-    CK(cudaGetLastError());
+    if ((int64_t)gx * gy <= kGridSmemCells) {
+        k_tiles_small<<<1, kTilesSmallThreads, (size_t)gx * gy * 4, st>>>(s.grid, f.tiles_x, f.tiles_y, tp,
+                                                                           reinterpret_cast<uint2*>(f.ranges), s.hist,
+                                                                           f.info);
+        count_launches();
+        CK(cudaGetLastError());
+    } else {
+        k_grid_rows<<<(unsigned)ceil_div(f.tiles_y, 128), 128, 0, st>>>(s.grid, gx, f.tiles_x, f.tiles_y);
+        count_launches();
+        CK(cudaGetLastError());
+        k_grid_cols<<<(unsigned)ceil_div(f.tiles_x, 128), 128, 0, st>>>(s.grid, gx, f.tiles_x, f.tiles_y);
+        count_launches();
+        CK(cudaGetLastError());
+        k_tile_scan<<<1, kTileScanThreads, 0, st>>>(s.grid, gx, f.tiles_x, (uint32_t)tiles, tp,
+                                                    reinterpret_cast<uint2*>(f.ranges), s.hist + 4 * kRadix, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        k_hist_to_offsets<<<1, 1024, 0, st>>>(s.hist, 4 + tp);
+        count_launches();
+        CK(cudaGetLastError());
+    }
     // 1. depth sort: (depth_key, index) -> A -> B -> A -> order
     for (int p = 0; p < 4; ++p) {
         uint32_t* status = s.status_depth + (size_t)p * bn * kRadix;
