@@ -114,7 +114,8 @@ typedef struct igs_frame {
     int64_t n;               /* Gaussians the frame was laid out for */
     int64_t capacity;        /* (Gaussian, tile) entries it can hold */
     int32_t width, height, tile, tiles_x, tiles_y, _pad;
-    float* rec;              /* [n][8] u, v, w2 = log2(e)/(2 s^2), o, r, g, b, s */
+    float* rec;              /* [n][8] u, v, w2 = log2(e)/(2 s^2), pmax, r, g, b, o; pmax = log2(o / alpha_min)
+                                + 2^-10 bounds the exponent w2 d^2 of every pixel with alpha >= alpha_min */
     uint32_t* rect;          /* [n][2] x0 | y0 << 16, x1 | y1 << 16 (inclusive tiles) */
     uint32_t* count;         /* [n] tiles touched; 0 = culled */
     uint32_t* depth_key;     /* [n] bits of the FP32 depth z_c; 0xFFFFFFFF if culled */

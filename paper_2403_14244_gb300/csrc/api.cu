@@ -79,6 +79,7 @@ igs::ViewParams view_params(const igs_camera* c, const igs_opts* o, const igs_fr
     std::memcpy(v.R, c->R, sizeof v.R);
     std::memcpy(v.t, c->t, sizeof v.t);
     v.fx = c->fx; v.fy = c->fy; v.cx = c->cx; v.cy = c->cy; v.znear = c->znear;
+    v.alpha_min = o->alpha_min;
     for (int a = 0; a < 3; ++a) {
         double acc = 0.0;
         for (int r = 0; r < 3; ++r) acc -= (double)c->R[3 * r + a] * (double)c->t[r];

@@ -7,7 +7,10 @@
 //   skip if alpha < alpha_min; stop (without blending) if T (1 - alpha) < t_min
 //   C += c alpha T; T *= (1 - alpha)
 // and the CTA leaves the batch loop as soon as every pixel has stopped
-// (__syncthreads_count). The backward pass walks each pixel's blended entries
+// (__syncthreads_count). Each warp first ballots which staged entries can reach
+// its rows at all (w2 d^2 <= pmax at the nearest pixel centre) and walks only
+// those; the per-pixel test w2 d^2 > pmax skips the exponential where alpha must
+// fall below alpha_min. The backward pass walks each pixel's blended entries
 // in reverse from n_contrib, recovering T_k = T_{k+1} / (1 - alpha_k) from the
 // saved T_final, and reduces the per-pixel gradient terms of each entry over
 // the tile before one vector atomic per (entry, 4 floats).
@@ -62,17 +65,19 @@ __device__ __forceinline__ float warp_reduce8(float v[8], int lane) {
 constexpr int kBwdBatch = 32;
 
 template <int TS>
-__global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(TS* TS, 1536 / (TS * TS)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                       const float4* __restrict__ rec, BlendParams P,
                                                       const float* __restrict__ dL, const float* __restrict__ T_final,
                                                       const uint32_t* __restrict__ n_contrib,
                                                       float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
     constexpr int NT = TS * TS;
     constexpr int NW = NT / 32;
+    constexpr int ROWS = 32 / TS;
     __shared__ float4 s_a[kBwdBatch];
     __shared__ float4 s_c[kBwdBatch];
     __shared__ uint32_t s_id[kBwdBatch];
     __shared__ float s_red[NW][kBwdBatch][8];
+    __shared__ uint32_t s_bits[NW];
     __shared__ uint32_t s_max;
     if (info[kInfoAbort]) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -81,6 +86,8 @@ __global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint2* __restrict__ 
     const int x = tx * TS + (threadIdx.x % TS), y = ty * TS + (threadIdx.x / TS);
     const bool inside = x < P.width && y < P.height;
     const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const float bx0 = (float)(tx * TS) + 0.5f, bx1 = bx0 + (float)(TS - 1);
+    const float by0 = (float)(ty * TS + w * ROWS) + 0.5f, by1 = by0 + (float)(ROWS - 1);
     const uint2 rg = ranges[tile];
     const size_t pix = (size_t)y * P.width + x, plane = (size_t)P.width * P.height;
     float G0 = 0.f, G1 = 0.f, G2 = 0.f, T = 1.f;
@@ -95,7 +102,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint2* __restrict__ 
     float S0 = T * P.bg[0], S1 = T * P.bg[1], S2 = T * P.bg[2];
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nc);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nc);  // this warp blended nothing at or past wmax
     if (lane == 0 && wmax) atomicMax(&s_max, wmax);
     __syncthreads();
     // no pixel blended anything at or past this entry
@@ -111,35 +118,47 @@ __global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint2* __restrict__ 
             s_c[threadIdx.x] = rec[2 * g + 1];
         }
         __syncthreads();
-        for (int k = 0; k < nb; ++k) {
+        // the entries this warp may have blended: before its last contributor, reaching its rows
+        const bool reach = lane < nb && hi - 1 - lane - rg.x < wmax && may_reach(s_a[lane], bx0, bx1, by0, by1);
+        uint32_t bits = __ballot_sync(0xffffffffu, reach);
+        if (lane == 0) s_bits[w] = bits;
+        while (bits) {
+            const int k = __ffs(bits) - 1;
+            bits &= bits - 1;
             const uint32_t pos = hi - 1 - k - rg.x;  // list position within the tile
             float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool active = false;
             if (pos < nc) {
                 const float4 a4 = s_a[k];
-                const Alpha a = eval_alpha(px, py, a4, P.alpha_max);
-                if (a.alpha >= P.alpha_min) {
-                    active = true;
+                const Dist d = eval_dist(px, py, a4);
+                if (!(d.pw > a4.w)) {
                     const float4 c = s_c[k];
-                    const float oma = 1.f - a.alpha;
-                    const float inv = 1.f / oma;
-                    const float Tk = T * inv;                    // transmittance before this entry
-                    const float wT = a.alpha * Tk;
-                    v[4] = wT * G0;
-                    v[5] = wT * G1;
-                    v[6] = wT * G2;
-                    const float dalpha = Tk * (G0 * c.x + G1 * c.y + G2 * c.z) - (G0 * S0 + G1 * S1 + G2 * S2) * inv;
-                    S0 = fmaf(wT, c.x, S0);
-                    S1 = fmaf(wT, c.y, S1);
-                    S2 = fmaf(wT, c.z, S2);
-                    T = Tk;
-                    if (a.og <= P.alpha_max) {                   // alpha not clamped
-                        v[3] = dalpha * a.g;                     // d/do
-                        const float dpow = -kLn2 * a.g * (dalpha * a4.w);  // d/d(power), power = w2 d^2
-                        v[2] = dpow * a.d2;                      // d/dw2
-                        const float k2 = -2.f * dpow * a4.z;
-                        v[0] = k2 * a.dx;                        // d/du  (dx = px - u)
-                        v[1] = k2 * a.dy;                        // d/dv
+                    const float g = fast_exp2(-d.pw);
+                    const float og = __fmul_rn(c.w, g);
+                    const float alpha = fminf(P.alpha_max, og);
+                    if (alpha >= P.alpha_min) {
+                        active = true;
+                        const float oma = 1.f - alpha;
+                        const float inv = 1.f / oma;
+                        const float Tk = T * inv;                    // transmittance before this entry
+                        const float wT = alpha * Tk;
+                        v[4] = wT * G0;
+                        v[5] = wT * G1;
+                        v[6] = wT * G2;
+                        const float dalpha =
+                            Tk * (G0 * c.x + G1 * c.y + G2 * c.z) - (G0 * S0 + G1 * S1 + G2 * S2) * inv;
+                        S0 = fmaf(wT, c.x, S0);
+                        S1 = fmaf(wT, c.y, S1);
+                        S2 = fmaf(wT, c.z, S2);
+                        T = Tk;
+                        if (og <= P.alpha_max) {                     // alpha not clamped
+                            v[3] = dalpha * g;                       // d/do
+                            const float dpow = -kLn2 * g * (dalpha * c.w);  // d/d(power), power = w2 d^2
+                            v[2] = dpow * d.d2;                      // d/dw2
+                            const float k2 = -2.f * dpow * a4.z;
+                            v[0] = k2 * d.dx;                        // d/du  (dx = px - u)
+                            v[1] = k2 * d.dy;                        // d/dv
+                        }
                     }
                 }
             }
@@ -157,6 +176,7 @@ __global__ void __launch_bounds__(TS* TS) k_blend_bwd(const uint2* __restrict__ 
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int ww = 0; ww < NW; ++ww) {
+                if (!((s_bits[ww] >> k) & 1u)) continue;
                 acc.x += s_red[ww][k][h + 0];
                 acc.y += s_red[ww][k][h + 1];
                 acc.z += s_red[ww][k][h + 2];

@@ -8,27 +8,41 @@
 namespace igs {
 namespace {
 
-struct Alpha {
-    float alpha, g, og, d2, dx, dy;
+// A record's first float4 is (u, v, w2, pmax), its second (r, g, b, o); the
+// exponent of a pixel is w2 d^2 and pmax = log2(o / alpha_min) + margin bounds
+// it: a larger exponent gives alpha < alpha_min.
+struct Dist {
+    float dx, dy, d2, pw;
 };
 
-// The alpha of one (pixel, entry) pair, written with explicit roundings so the
-// forward and backward kernels take exactly the same skip / stop / clamp decisions.
-__device__ __forceinline__ Alpha eval_alpha(float px, float py, float4 a, float alpha_max) {
-    Alpha r;
+// Squared distance and exponent of one (pixel, entry) pair, each step rounded
+// once in a fixed order, so that forward and backward take the same decisions.
+__device__ __forceinline__ Dist eval_dist(float px, float py, float4 a) {
+    Dist r;
     r.dx = __fsub_rn(px, a.x);
     r.dy = __fsub_rn(py, a.y);
     r.d2 = __fmaf_rn(r.dx, r.dx, __fmul_rn(r.dy, r.dy));
-    r.g = fast_exp2(-__fmul_rn(a.z, r.d2));
-    r.og = __fmul_rn(a.w, r.g);
-    r.alpha = fminf(alpha_max, r.og);
+    r.pw = __fmul_rn(a.z, r.d2);
     return r;
+}
+
+// Whether the entry can reach a pixel centre in [xlo, xhi] x [ylo, yhi] (first
+// and last centres of a block of rows): the exponent test at the centre nearest
+// to (u, v). Each rounded step of eval_dist is monotone in |dx| and |dy|, so that
+// centre has the smallest exponent of the block and a false answer never drops
+// a pair that the per-pixel test would keep.
+__device__ __forceinline__ bool may_reach(float4 a, float xlo, float xhi, float ylo, float yhi) {
+    const float cx = fminf(fmaxf(floorf(a.x) + 0.5f, xlo), xhi);
+    const float cy = fminf(fmaxf(floorf(a.y) + 0.5f, ylo), yhi);
+    return !(eval_dist(cx, cy, a).pw > a.w);
 }
 
 // One CTA of TS*TS threads composites one tile (one thread per pixel), staging
 // B entries at a time in shared memory (s_a, s_c hold B float4 each), and leaves
-// the batch loop once every pixel has stopped. Writes img (planar, `plane`
-// floats per channel, row stride `width`) and, if given, T_final / n_contrib.
+// the batch loop once every pixel has stopped. Each warp owns 32 / TS rows of the
+// tile and walks, in order, only the staged entries that may reach them (one
+// ballot per 32 entries). Writes img (planar, `plane` floats per channel, row
+// stride `width`) and, if given, T_final / n_contrib.
 template <int TS, int B>
 __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int height, uint2 rg,
                                                const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
@@ -36,10 +50,16 @@ __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int he
                                                float4* s_a, float4* s_c, float* __restrict__ img,
                                                float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
     constexpr int NT = TS * TS;
+    constexpr int ROWS = 32 / TS;  // rows of the tile per warp
     static_assert(B <= NT, "staging batch larger than the tile");
+    static_assert(TS >= 8 && TS <= 32, "a warp covers whole rows of the tile");
+    const int lane = threadIdx.x & 31;
     const int x = tx * TS + (threadIdx.x % TS), y = ty * TS + (threadIdx.x / TS);
     const bool inside = x < width && y < height;
     const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    // pixel centres of this warp's rows
+    const float bx0 = (float)(tx * TS) + 0.5f, bx1 = bx0 + (float)(TS - 1);
+    const float by0 = (float)(ty * TS + (threadIdx.x >> 5) * ROWS) + 0.5f, by1 = by0 + (float)(ROWS - 1);
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
     bool done = !inside;
@@ -53,21 +73,31 @@ __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int he
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)B, rg.y - b0);
-        for (int k = 0; k < nb && !done; ++k) {
-            const Alpha a = eval_alpha(px, py, s_a[k], alpha_max);
-            if (a.alpha < alpha_min) continue;
-            const float Tn = T * (1.f - a.alpha);
-            if (Tn < t_min) {
-                done = true;
-                break;
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const bool reach = c0 + lane < nb && may_reach(s_a[c0 + lane], bx0, bx1, by0, by1);
+            uint32_t bits = __ballot_sync(0xffffffffu, reach);
+            while (bits && !done) {
+                const int k = c0 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const float4 a = s_a[k];
+                const float pw = eval_dist(px, py, a).pw;
+                if (pw > a.w) continue;
+                const float4 c = s_c[k];
+                const float alpha = fminf(alpha_max, __fmul_rn(c.w, fast_exp2(-pw)));
+                if (alpha < alpha_min) continue;
+                const float Tn = T * (1.f - alpha);
+                if (Tn < t_min) {
+                    done = true;
+                    break;
+                }
+                const float w = alpha * T;
+                C0 = fmaf(c.x, w, C0);
+                C1 = fmaf(c.y, w, C1);
+                C2 = fmaf(c.z, w, C2);
+                T = Tn;
+                last = b0 - rg.x + k + 1;
             }
-            const float4 c = s_c[k];
-            const float w = a.alpha * T;
-            C0 = fmaf(c.x, w, C0);
-            C1 = fmaf(c.y, w, C1);
-            C2 = fmaf(c.z, w, C2);
-            T = Tn;
-            last = b0 - rg.x + k + 1;
         }
     }
     if (!inside) return;

@@ -16,6 +16,10 @@ namespace igs {
 constexpr float kRadiusK = 3.33f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
+// Slack added to the record's exponent bound pmax = log2(o / alpha_min): it
+// covers the rounding of that logarithm and the relative error of ex2.approx
+// (both below 2^-19), so w2 d^2 > pmax proves alpha < alpha_min.
+constexpr float kPowMargin = 1.0f / 1024.0f;
 
 // Status words of a frame (igs_frame::info).
 enum : int { kInfoM = 0, kInfoKept = 1, kInfoErr = 2, kInfoNeed = 3, kInfoAbort = 4, kInfoTileTotal = 5,
@@ -79,6 +83,7 @@ __device__ __forceinline__ float fast_exp2(float x) {
 struct ViewParams {
     float R[9], t[3];
     float fx, fy, cx, cy, znear;
+    float alpha_min;      // the blend's skip threshold, for the record's exponent bound
     float cam_center[3];  // -R^T t, for the SH view direction
     int32_t width, height, tile, tiles_x, tiles_y;
     int32_t sh_degree, param_mode;

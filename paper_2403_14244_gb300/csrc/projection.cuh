@@ -211,8 +211,10 @@ __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const
         }
     }
     const float w2 = 0.5f * kLog2e / (s * s);
-    rec[0] = make_float4(u, v, w2, o);
-    rec[1] = make_float4(rgb[0], rgb[1], rgb[2], s);
+    // every pixel with w2 d^2 above pmax has alpha < alpha_min (skipped in Eq. 4)
+    const float pmax = __fadd_rn(log2f(__fdiv_rn(o, P.alpha_min)), kPowMargin);
+    rec[0] = make_float4(u, v, w2, pmax);
+    rec[1] = make_float4(rgb[0], rgb[1], rgb[2], o);
 }
 
 }  // namespace

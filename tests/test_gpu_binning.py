@@ -22,7 +22,15 @@ def _check_bitexact(sc, cam, tile):
     rec = f.rec().cpu().numpy()
     np.testing.assert_array_equal(rec[kept, 0].view(np.uint32), p["u"][kept].view(np.uint32))
     np.testing.assert_array_equal(rec[kept, 1].view(np.uint32), p["v"][kept].view(np.uint32))
-    np.testing.assert_array_equal(rec[kept, 7].view(np.uint32), p["s"][kept].view(np.uint32))
+    # w2 = log2(e) / (2 s^2) rounded from the oracle's s; o as given; pmax a
+    # bound on the exponent of every pixel whose alpha reaches alpha_min
+    s_ = p["s"][kept]
+    w2 = np.float32(np.float32(0.5) * np.float32(np.log2(np.e))) / (s_ * s_)
+    np.testing.assert_array_equal(rec[kept, 2].view(np.uint32), w2.view(np.uint32))
+    if not sc.log_params:
+        np.testing.assert_array_equal(rec[kept, 7].view(np.uint32), sc.opacity[kept].view(np.uint32))
+    bound = np.log2(rec[kept, 7].astype(np.float64) / np.float64(np.float32(1.0 / 255.0)))
+    assert np.all(rec[kept, 3] >= bound + 2.0 ** -11) and np.all(rec[kept, 3] <= bound + 2.0 ** -9)
     dk = f.depth_key().cpu().numpy().view(np.uint32)
     np.testing.assert_array_equal(dk[kept], p["depth"][kept].view(np.uint32))
     assert np.all(dk[~kept] == 0xFFFFFFFF)

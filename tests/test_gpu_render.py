@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_2403_14244_gb300 import scenes
 from tests import _gpu
-from tests._tiny import random_small
+from tests._tiny import random_small, scene_from
 
 pytestmark = pytest.mark.gpu
 
@@ -89,3 +89,52 @@ def test_autograd_function_forward_matches_renderer():
     ref = _gpu.run_forward(sc, cam)[3]
     np.testing.assert_array_equal(img.detach().cpu().numpy().astype(np.float64), ref)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_alpha_threshold_decisions_exact(tile):
+    """One small Gaussian per 16x16 block and one probe pixel at the edge of its
+    disc, where alpha = alpha_min (1 + eps) with 1e-4 <= |eps| <= 2e-3 (in FP64
+    from the FP32 u, v, s). The forward blends the probe exactly when eps > 0,
+    and the backward sees it exactly then: no early skip (block of rows or
+    per-pixel exponent bound) may drop a pair that reaches alpha_min."""
+    rng = np.random.default_rng(77)
+    W = H = 512
+    f = 1000.0
+    cam = scenes.Camera(R=np.eye(3, dtype=np.float32), t=np.zeros(3, np.float32), fx=f, fy=f,
+                        cx=W / 2, cy=H / 2, width=W, height=H)
+    amin = float(np.float32(1.0 / 255.0))
+    n = (W // 16) * (H // 16)
+    s_px = 1.5
+    means, sig, opac, probes, eps_t = [], [], [], [], []
+    for k in range(n):
+        bi, bj = k % (W // 16), k // (W // 16)
+        th = rng.uniform(0, 2 * np.pi)
+        d = np.array([np.cos(th), np.sin(th)])
+        o = rng.uniform(0.3, 0.9)
+        eps = rng.uniform(2e-4, 1.5e-3) * (1 if k % 2 else -1)
+        dist = s_px * np.sqrt(2 * np.log(o / (amin * (1 + eps))))
+        P = np.floor(np.array([16 * bi + 8, 16 * bj + 8]) + 4.6 * d) + 0.5
+        c = P - dist * d
+        z = rng.uniform(3, 5)
+        means.append([(c[0] - cam.cx) * z / f, (c[1] - cam.cy) * z / f, z])
+        sig.append(s_px * z / f)
+        opac.append(o)
+        probes.append(P)
+    sc = scene_from(means, sig, opac, rng.uniform(0.2, 1.0, size=(n, 3)))
+    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile)
+    probes = np.array(probes)
+    d2 = (probes[:, 0] - p["u"].astype(np.float64)) ** 2 + (probes[:, 1] - p["v"].astype(np.float64)) ** 2
+    s64 = p["s"].astype(np.float64)
+    eps_a = sc.opacity.astype(np.float64) * np.exp(-d2 / (2 * s64 * s64)) / amin - 1.0
+    sel = (np.abs(eps_a) >= 1e-4) & (np.abs(eps_a) <= 2e-3)
+    assert sel.sum() > 0.9 * n and (eps_a[sel] > 0).sum() > 0.4 * n
+    r, fr, scene, img = _gpu.run_forward(sc, cam, tile=tile)
+    px, py = probes[:, 0].astype(np.int64), probes[:, 1].astype(np.int64)
+    nc = fr.n_contrib().cpu().numpy()[py, px]
+    np.testing.assert_array_equal((nc > 0)[sel], (eps_a > 0)[sel])
+    dimg = torch.zeros((3, H, W), device="cuda")
+    dimg[:, torch.from_numpy(py).cuda(), torch.from_numpy(px).cuda()] = 1.0
+    _, _, d_col = r.run_backward(scene, cam, fr, dimg)
+    g = d_col.abs().sum(1).cpu().numpy()
+    np.testing.assert_array_equal((g > 0)[sel], (eps_a > 0)[sel])
