@@ -113,7 +113,9 @@ typedef struct igs_scene {
 typedef struct igs_frame {
     int64_t n;               /* Gaussians the frame was laid out for */
     int64_t capacity;        /* (Gaussian, tile) entries it can hold */
-    int32_t width, height, tile, tiles_x, tiles_y, _pad;
+    int32_t width, height, tile, tiles_x, tiles_y;
+    int32_t sort_chunks;     /* > 0: entries placed by a counting sort over this many chunks of
+                                the depth order; 0: duplication + radix sort on the tile id */
     float* rec;              /* [n][8] u, v, w2 = log2(e)/(2 s^2), pmax, r, g, b, o; pmax = log2(o / alpha_min)
                                 + 2^-10 bounds the exponent w2 d^2 of every pixel with alpha >= alpha_min */
     uint32_t* rect;          /* [n][2] x0 | y0 << 16, x1 | y1 << 16 (inclusive tiles) */

@@ -10,6 +10,7 @@
 
 namespace igs {
 std::atomic<uint64_t> g_launches{0};
+thread_local const char* g_failed_call = nullptr;
 }
 
 namespace {
@@ -26,7 +27,10 @@ igs_status fail(igs_status s, const char* fmt, ...) {
 }
 
 igs_status cuda_status(cudaError_t e, const char* what) {
+    const char* call = igs::g_failed_call;
+    igs::g_failed_call = nullptr;
     if (e == cudaSuccess) return IGS_OK;
+    if (call) return fail(IGS_ERR_CUDA, "%s: %s (at %.160s)", what, cudaGetErrorString(e), call);
     return fail(IGS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -148,7 +152,8 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     size_t o_nc = off; off += align256((size_t)P * 4);
     size_t o_info = off; off += align256(igs::kInfoWords * 4);
     size_t o_scr = off;
-    const size_t scr = igs::sort_scratch_bytes(n, capacity, tiles);
+    const int64_t chunks = igs::sort_walk_chunks(tx, ty);
+    const size_t scr = igs::sort_scratch_bytes(n, capacity, tx, ty, chunks);
     off += align256(scr);
     *bytes = off;
     if (!workspace) return IGS_OK;
@@ -163,6 +168,7 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     frame->tile = opts->tile;
     frame->tiles_x = (int32_t)tx;
     frame->tiles_y = (int32_t)ty;
+    frame->sort_chunks = (int32_t)chunks;
     frame->rec = reinterpret_cast<float*>(b + o_rec);
     frame->rect = reinterpret_cast<uint32_t*>(b + o_rect);
     frame->count = reinterpret_cast<uint32_t*>(b + o_count);
@@ -175,8 +181,9 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     frame->info = reinterpret_cast<uint32_t*>(b + o_info);
     frame->scratch = b + o_scr;
     frame->scratch_bytes = scr;
-    // vals and tile_key live in the sort's ping-pong item buffers (each is free
-    // when they are written), so a frame costs 16 bytes per entry of capacity
+    // vals and tile_key live in the sort's entry buffers: a frame costs 8 bytes per
+    // entry of capacity (counting sort) or 16 (radix tile passes: the ping-pong
+    // item buffers, each free when they are written)
     const igs::SortScratch ss = igs::sort_scratch(*frame);
     frame->vals = ss.vals;
     frame->tile_key = ss.tile_key;

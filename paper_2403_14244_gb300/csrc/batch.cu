@@ -378,7 +378,7 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const B
     const uint32_t Vn = (uint32_t)(n * V);
     const int tp = s.tile_passes;
     cudaError_t e;
-#define CK(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+#define CK(x) do { if ((e = (x)) != cudaSuccess) { g_failed_call = #x " (batch.cu:" IGS_STR(__LINE__) ")"; return e; } } while (0)
     CK(cudaMemsetAsync(b.info, 0, kInfoWords * 4, st));
     CK(cudaMemsetAsync(s.hist_depth, 0, 4 * 4 * (size_t)V * kRadix, st));
     CK(cudaMemsetAsync(s.hist_tile, 0, 4 * 4 * kRadix, st));

@@ -41,6 +41,10 @@ constexpr int kMaxSpin = 1 << 21;
 // Kernel launches made by the library (igs_launch_count).
 extern std::atomic<uint64_t> g_launches;
 inline void count_launches(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// The CUDA call of a multi-launch step that failed last on this thread (for the error message).
+extern thread_local const char* g_failed_call;
+#define IGS_STR2(x) #x
+#define IGS_STR(x) IGS_STR2(x)
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -152,11 +156,17 @@ struct SortScratch {
     int32_t* grid;                    // [(tiles_y + 1) * (tiles_x + 1)] rectangle corner counts -> per-tile counts
     uint32_t* vals;                   // sorted values: in the item buffer the last tile pass does not read
     uint32_t* tile_key;               // exported tile ids: in the item buffer the last tile pass reads
+    uint32_t* walk_h1;                // [tiles_y][walk_chunks] level-1 row counts per chunk, then offsets
+    uint32_t* walk_len;               // [tiles_y] items per tile-row list
+    uint32_t* walk_rows;              // [tiles_y] list starts, first level-2 chunks, chunk sizes; [1] chunk total
+    uint32_t* walk_h2;                // [level-2 chunks][tiles_x] level-2 tile counts per chunk, then slots
+    int64_t walk_chunks;              // > 0: counting sort of the entries; 0: duplication + tile radix passes
     int tile_passes;
     int tile_bits;
 };
 SortScratch sort_scratch(const igs_frame& f);
-size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles);
+size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t tiles_y, int64_t chunks);
+int64_t sort_walk_chunks(int64_t tiles_x, int64_t tiles_y);
 int tile_passes_for(int64_t tiles);
 
 }  // namespace igs

@@ -1,31 +1,37 @@
 // Binning and sorting: front-to-back order of the kept Gaussians, their
-// duplication into one entry per touched tile, a stable sort of the entries by
-// tile id, and per-tile ranges.
+// entries (one per touched tile) grouped by tile id, and per-tile ranges.
 //
 // Eq. 4 composites each pixel front to back, so every tile needs its Gaussians
 // in depth order. Instead of one radix sort over 64-bit (tile << 32 | depth)
 // keys, this does:
 //   1. a stable 32-bit LSD radix sort of the n depth keys (culled ones carry
 //      0xFFFFFFFF and sort last), which gives `order`;
-//   2. an exclusive scan of the tile counts in that order and the duplication
-//      of each Gaussian, in that order, into (tile id | Gaussian id) items;
-//   3. a stable LSD radix sort of the M items on the tile id only
-//      (ceil(bits(tiles) / 8) passes).
-// Stability makes the result identical to the stable 64-bit key sort: within a
-// tile, entries are in (depth bits, Gaussian index) order.
+//   2. an exclusive scan of the tile counts in that order (M, capacity check);
+//   3. the entries in tile order, by one of two routes:
+//      a. counting sort (at most 2048 tiles per axis): the tile ranges are
+//         known in advance (below), so each entry's slot is its tile's start
+//         plus the number of earlier Gaussians, in depth order, whose
+//         rectangle holds the tile. Two counting sorts with few buckets each
+//         get there: Gaussians into the lists of the tile rows they span, then
+//         each row's items into the row's tiles. No (tile, Gaussian) item is
+//         materialised before its final slot.
+//      b. radix (larger frames): duplication of each Gaussian, in depth order,
+//         into (tile id | Gaussian id) items, then a stable LSD radix sort of
+//         the M items on the tile id (ceil(bits(tiles) / 8) passes).
+// Both give the stable 64-bit key order: within a tile, entries are in
+// (depth bits, Gaussian index) order.
 //
 // The per-tile entry counts, hence the tile ranges and the digit histograms of
 // the tile passes, come from the rectangles alone: every kept Gaussian adds its
 // rectangle to a 2D difference grid (four corner updates) whose 2D prefix sum is
-// the number of entries of each tile. No pass over the M entries is needed for
-// them.
+// the number of entries of each tile.
 //
 // Each radix pass is a single sweep over (key | value) items: a block counts
 // the digits of its 4096 items and publishes those counts at once, ranks the
 // items within each warp with ballots, looks back over earlier blocks (eight
 // at a time) for its global digit offsets, and scatters the items staged in
-// digit order. Every wait on another block is bounded (kMaxSpin polls); on
-// expiry the block records IGS_ERR_DEVICE_TIMEOUT, which aborts the frame.
+// digit order. Every wait on another block or warp is bounded (kMaxSpin polls);
+// on expiry it records IGS_ERR_DEVICE_TIMEOUT, which aborts the frame.
 #include <algorithm>
 #include <mutex>
 
@@ -188,6 +194,398 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
     }
 }
 
+// ---- counting sort of the entries by tile (route a) ----
+//
+// Two levels, each a counting sort with few buckets:
+//   level 1 places each kept Gaussian, in depth order, into the list of every
+//            tile row its rectangle spans (buckets: rows; items: Gaussian ids);
+//   level 2 places each item of a row, in list order, into every tile of that
+//            row its rectangle spans (buckets: the row's tiles; items: entries).
+// A level counts its chunks' items per bucket (shared memory), scans the counts
+// down each bucket over the chunks, and walks the chunks again placing items.
+// Placement keeps order within a bucket (Placer below). Chunks are sized
+// so that their items fill about 4/5 of a shared-memory stage.
+
+constexpr int kRowWalkMax = 2048;          // tiles per axis for route a (shared-memory buckets)
+constexpr uint32_t kL1ChunksMax = 16384;   // most level-1 chunks (columns of H1), fewer for tall frames
+constexpr uint32_t kL1ChunksMin = 1024;
+constexpr uint32_t kH1Words = 1u << 22;    // H1 budget: rows x chunks
+constexpr uint32_t kStage = 2048;          // staged items per chunk
+constexpr uint32_t kChunkTarget = kStage * 4 / 5;
+constexpr int kWalkWarps = 4;              // warps per CTA of the walk kernels (one chunk each)
+constexpr int kWalkUnroll = 4;             // items per lane per round of the counting walks
+
+// Level-1 chunk c: positions [p0, p1) of the depth order among the kept
+// Gaussians; `used` chunks hold Gaussians. A chunk takes about kChunkTarget /
+// sqrt(M / kept) Gaussians (the rows of an isotropic footprint are about the
+// square root of its tiles).
+struct Chunk {
+    uint32_t p0, p1, used;
+};
+__device__ __forceinline__ Chunk l1_chunk(uint32_t c, uint32_t cmax, const uint32_t* __restrict__ info) {
+    const uint32_t kept = info[kInfoKept], M = info[kInfoM];
+    const float rows_per = kept ? fmaxf(1.f, sqrtf((float)M / (float)kept)) : 1.f;
+    const uint32_t target = max(32u, (uint32_t)((float)kChunkTarget / rows_per));
+    const uint32_t per = max(target, (uint32_t)ceil_div(kept, cmax));
+    Chunk ch;
+    ch.used = (uint32_t)ceil_div(kept, per);
+    ch.p0 = (uint32_t)min((uint64_t)kept, (uint64_t)c * per);
+    ch.p1 = (uint32_t)min((uint64_t)kept, (uint64_t)ch.p0 + per);
+    return ch;
+}
+
+// A warp's stable placement of one chunk whose items each span a contiguous
+// range of buckets [lo, hi], one batch of 32 items (one per lane, in order) at
+// a time, in three passes over each item's buckets: mark the item's lane bit
+// in the bucket's mask; slot = bucket cursor + earlier lanes in the mask; the
+// highest lane of the mask advances the cursor by the mask's size and clears
+// it. Items go to a shared-memory stage grouped by bucket and leave as one run
+// per bucket written by consecutive lanes (a chunk too large for the stage
+// writes its items directly). Shared memory: words(B).
+struct Placer {
+    uint32_t *pos, *mask, *first, *lstart, *stage;
+    uint32_t B;
+    bool staged;
+    __host__ __device__ static constexpr uint32_t words(uint32_t B) { return 4 * B + 1 + kStage; }
+    __device__ __forceinline__ Placer(uint32_t* ws, uint32_t nb) : B(nb), staged(false) {
+        pos = ws;
+        mask = pos + nb;
+        first = mask + nb;
+        lstart = first + nb;
+        stage = lstart + nb + 1;
+    }
+    // first_slot(q): the chunk's first slot in bucket q of the output; count(q): its items there
+    template <typename First, typename Count>
+    __device__ __forceinline__ void init(int lane, First first_slot, Count count) {
+        for (uint32_t q = lane; q < B; q += 32) {  // coalesced, independent loads
+            first[q] = first_slot(q);
+            lstart[q] = count(q);
+        }
+        __syncwarp();
+        const uint32_t per = (B + 31) / 32, q0 = min(B, lane * per), q1 = min(B, q0 + per);
+        uint32_t sum = 0;
+        for (uint32_t q = q0; q < q1; ++q) sum += lstart[q];
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        staged = total <= kStage;
+        uint32_t run = incl - sum;
+        for (uint32_t q = q0; q < q1; ++q) {
+            const uint32_t c = lstart[q];
+            mask[q] = 0u;
+            lstart[q] = run;
+            pos[q] = staged ? run : first[q];
+            run += c;
+        }
+        if (lane == 31) lstart[B] = total;
+        __syncwarp();
+    }
+    // one batch: this lane's item (none if lo > hi) spans buckets lo..hi
+    __device__ __forceinline__ void batch(uint32_t lo, uint32_t hi, uint32_t item, int lane,
+                                          uint32_t* __restrict__ out) {
+        const uint32_t bit = 1u << lane, lt = bit - 1u;
+        for (uint32_t q = lo; q <= hi; ++q) atomicOr(&mask[q], bit);
+        __syncwarp();
+        for (uint32_t q = lo; q <= hi; ++q) {
+            const uint32_t at = pos[q] + __popc(mask[q] & lt);
+            if (staged) stage[at] = item; else out[at] = item;
+        }
+        __syncwarp();
+        // the highest lane of a mask advances the bucket and clears the mask; any
+        // other lane reads either a mask with a higher bit or zero, and does nothing
+        for (uint32_t q = lo; q <= hi; ++q) {
+            const uint32_t m = mask[q];
+            if ((m >> lane) == 1u) {
+                pos[q] += __popc(m);
+                mask[q] = 0u;
+            }
+        }
+        __syncwarp();
+    }
+    // staged chunk: every bucket's run to out[first[q] ...], consecutive lanes
+    __device__ __forceinline__ void flush(uint32_t* __restrict__ out, int lane) {
+        if (!staged) return;
+        for (uint32_t q = 0; q < B; ++q) {
+            const uint32_t s0 = lstart[q], n = lstart[q + 1] - s0;
+            const uint32_t f = first[q];
+            for (uint32_t i = lane; i < n; i += 32) out[f + i] = stage[s0 + i];
+        }
+    }
+};
+
+// Level 1, count: for each of its chunks c (grid-stride over warps), a warp adds,
+// for each Gaussian of the chunk, one to every row of its rectangle; writes
+// column c of H1 [rows][cmax].
+__global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* __restrict__ order,
+                                                                const uint2* __restrict__ rect, uint32_t rows,
+                                                                uint32_t cmax, uint32_t* __restrict__ H1,
+                                                                const uint32_t* __restrict__ info) {
+    extern __shared__ uint32_t s_walk[];
+    const int lane = threadIdx.x & 31;
+    uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * rows;
+    if (info[kInfoAbort]) return;
+    const uint32_t used = l1_chunk(0, cmax, info).used;
+    for (uint32_t c = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); c < used; c += gridDim.x * kWalkWarps) {
+        const Chunk ch = l1_chunk(c, cmax, info);
+        for (uint32_t y = lane; y < rows; y += 32) cnt[y] = 0u;
+        __syncwarp();
+        for (uint32_t b = ch.p0; b < ch.p1; b += 32 * kWalkUnroll) {
+            uint32_t g[kWalkUnroll];
+            uint32_t ry[kWalkUnroll];
+#pragma unroll
+            for (int k = 0; k < kWalkUnroll; ++k) {
+                const uint32_t p = b + k * 32 + lane;
+                g[k] = p < ch.p1 ? order[p] : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalkUnroll; ++k) {
+                const uint2 r = g[k] != 0xFFFFFFFFu ? rect[g[k]] : make_uint2(1u << 16, 0u);  // rows 1..0: none
+                ry[k] = (r.x >> 16) | (r.y & 0xFFFF0000u);
+            }
+#pragma unroll
+            for (int k = 0; k < kWalkUnroll; ++k)
+                for (uint32_t y = ry[k] & 0xFFFF; y <= (ry[k] >> 16); ++y) atomicAdd(&cnt[y], 1u);
+        }
+        __syncwarp();
+        for (uint32_t y = lane; y < rows; y += 32) H1[(size_t)y * cmax + c] = cnt[y];
+    }
+}
+
+// Level 1, scan: block y turns row y of H1 (the used chunks' counts) into
+// exclusive offsets in place and writes the row's item count to len[y].
+constexpr int kRowScanThreads = 256;
+__global__ void __launch_bounds__(kRowScanThreads) k_rows_scan(uint32_t* __restrict__ H1, uint32_t cmax,
+                                                               uint32_t* __restrict__ len,
+                                                               const uint32_t* __restrict__ info) {
+    __shared__ uint32_t s_warp[kRowScanThreads / 32];
+    if (info[kInfoAbort]) return;
+    uint32_t* row = H1 + (size_t)blockIdx.x * cmax;
+    const uint32_t used = l1_chunk(0, cmax, info).used;
+    const uint32_t per = (used + kRowScanThreads - 1) / kRowScanThreads;
+    const uint32_t c0 = min(used, threadIdx.x * per), c1 = min(used, c0 + per);
+    uint32_t sum = 0;
+    for (uint32_t c = c0; c < c1; ++c) sum += row[c];
+    uint32_t run = block_excl_scan<kRowScanThreads>(sum, s_warp);
+    if (threadIdx.x == kRowScanThreads - 1) len[blockIdx.x] = run + sum;
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t h = row[c];
+        row[c] = run;
+        run += h;
+    }
+}
+
+// Row layout (one block). rowinfo = [rows] list starts, [rows] first level-2
+// chunk, [rows] items per level-2 chunk, [1] level-2 chunk total. A row's chunk
+// takes about kChunkTarget entries: kChunkTarget * items / entries of the row
+// items, at least 32. Records an error if the chunks exceed `max_chunks`.
+constexpr int kLayoutThreads = 1024;
+__global__ void __launch_bounds__(kLayoutThreads) k_rows_layout(const uint32_t* __restrict__ len,
+                                                                const uint2* __restrict__ ranges, uint32_t rows,
+                                                                uint32_t tiles_x, uint32_t max_chunks,
+                                                                uint32_t* __restrict__ rowinfo,
+                                                                uint32_t* __restrict__ info) {
+    __shared__ uint32_t s_warp[kLayoutThreads / 32];
+    __shared__ unsigned long long s_entries[kRowWalkMax];
+    if (info[kInfoAbort]) return;
+    for (uint32_t y = threadIdx.x; y < rows; y += kLayoutThreads) s_entries[y] = 0ull;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < rows * tiles_x; t += kLayoutThreads) {
+        const uint2 r = ranges[t];
+        if (r.y > r.x) atomicAdd(&s_entries[t / tiles_x], (unsigned long long)(r.y - r.x));
+    }
+    __syncthreads();
+    const uint32_t per = (rows + kLayoutThreads - 1) / kLayoutThreads;
+    const uint32_t y0 = min(rows, threadIdx.x * per), y1 = min(rows, y0 + per);
+    uint32_t items = 0, chunks = 0;
+    for (uint32_t y = y0; y < y1; ++y) {
+        const uint64_t entries = s_entries[y];
+        const uint32_t size =
+            (uint32_t)max((uint64_t)32, entries ? (uint64_t)kChunkTarget * len[y] / entries : (uint64_t)kChunkTarget);
+        rowinfo[2 * rows + y] = size;
+        items += len[y];
+        chunks += (len[y] + size - 1) / size;
+    }
+    uint32_t start = block_excl_scan<kLayoutThreads>(items, s_warp);
+    uint32_t base = block_excl_scan<kLayoutThreads>(chunks, s_warp);
+    if (threadIdx.x == kLayoutThreads - 1) {
+        rowinfo[3 * rows] = base + chunks;
+        if (base + chunks > max_chunks) record_error(info, IGS_ERR_CUDA);  // never expected: chunks are bounded
+    }
+    for (uint32_t y = y0; y < y1; ++y) {
+        rowinfo[y] = start;
+        rowinfo[rows + y] = base;
+        start += len[y];
+        base += (len[y] + rowinfo[2 * rows + y] - 1) / rowinfo[2 * rows + y];
+    }
+}
+
+// Level 1, place: a warp walks each of its chunks again and puts each Gaussian
+// id into the list of every row of its rectangle (R1, rows one after another).
+__global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* __restrict__ order,
+                                                                const uint2* __restrict__ rect, uint32_t rows,
+                                                                uint32_t cmax, const uint32_t* __restrict__ H1,
+                                                                const uint32_t* __restrict__ len,
+                                                                const uint32_t* __restrict__ rowinfo,
+                                                                uint32_t* __restrict__ R1,
+                                                                const uint32_t* __restrict__ info) {
+    extern __shared__ uint32_t s_walk[];
+    const int lane = threadIdx.x & 31;
+    if (info[kInfoAbort]) return;
+    const uint32_t used = l1_chunk(0, cmax, info).used;
+    for (uint32_t c = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); c < used; c += gridDim.x * kWalkWarps) {
+        const Chunk ch = l1_chunk(c, cmax, info);
+        Placer rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer::words(rows), rows);
+        auto first = [&](uint32_t y) { return rowinfo[y] + H1[(size_t)y * cmax + c]; };
+        rs.init(lane, first, [&](uint32_t y) {
+            const uint32_t* h = H1 + (size_t)y * cmax;
+            return (c + 1 < ch.used ? h[c + 1] : len[y]) - h[c];
+        });
+        uint32_t g_next = ch.p0 + lane < ch.p1 ? order[ch.p0 + lane] : 0xFFFFFFFFu;
+        for (uint32_t b = ch.p0; b < ch.p1; b += 32) {
+            const uint32_t g = g_next;
+            const uint2 r = g != 0xFFFFFFFFu ? rect[g] : make_uint2(1u << 16, 0u);  // rows 1..0: none
+            g_next = b + 32 + lane < ch.p1 ? order[b + 32 + lane] : 0xFFFFFFFFu;
+            rs.batch(r.x >> 16, r.y >> 16, g, lane, R1);
+        }
+        rs.flush(R1, lane);
+        __syncwarp();  // the next chunk's init rewrites what the flush reads
+    }
+}
+
+// Level-2 chunk j: row y (largest y whose first chunk is <= j; rows without
+// chunks share the next row's base) and items [i0, i1) of R1.
+struct RowChunk {
+    uint32_t y, i0, i1;
+};
+__device__ __forceinline__ RowChunk l2_chunk(uint32_t j, uint32_t rows, const uint32_t* __restrict__ rowinfo,
+                                             const uint32_t* __restrict__ len) {
+    uint32_t lo = 0, hi = rows;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (rowinfo[rows + mid] <= j) lo = mid; else hi = mid;
+    }
+    RowChunk rc;
+    rc.y = lo;
+    const uint32_t start = rowinfo[lo], size = rowinfo[2 * rows + lo];
+    rc.i0 = start + (j - rowinfo[rows + lo]) * size;
+    rc.i1 = min(start + len[lo], rc.i0 + size);
+    return rc;
+}
+
+// Level 2, count: for each of its chunks j, a warp adds, for each item of the
+// chunk, one to every tile of the row that the item's rectangle spans; writes
+// row j of H2 [chunks][tiles_x].
+__global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* __restrict__ R1,
+                                                                const uint2* __restrict__ rect, uint32_t rows,
+                                                                uint32_t tiles_x, const uint32_t* __restrict__ len,
+                                                                const uint32_t* __restrict__ rowinfo,
+                                                                uint32_t* __restrict__ H2,
+                                                                const uint32_t* __restrict__ info) {
+    extern __shared__ uint32_t s_walk[];
+    const int lane = threadIdx.x & 31;
+    uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * tiles_x;
+    if (info[kInfoAbort]) return;
+    const uint32_t total = rowinfo[3 * rows];
+    for (uint32_t j = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); j < total; j += gridDim.x * kWalkWarps) {
+        const RowChunk rc = l2_chunk(j, rows, rowinfo, len);
+        for (uint32_t x = lane; x < tiles_x; x += 32) cnt[x] = 0u;
+        __syncwarp();
+        for (uint32_t b = rc.i0; b < rc.i1; b += 32 * kWalkUnroll) {
+            uint32_t g[kWalkUnroll];
+            uint32_t rx[kWalkUnroll];
+#pragma unroll
+            for (int k = 0; k < kWalkUnroll; ++k) {
+                const uint32_t i = b + k * 32 + lane;
+                g[k] = i < rc.i1 ? R1[i] : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalkUnroll; ++k) {
+                const uint2 r = g[k] != 0xFFFFFFFFu ? rect[g[k]] : make_uint2(1u, 0u);  // columns 1..0: none
+                rx[k] = (r.x & 0xFFFF) | (r.y << 16);
+            }
+#pragma unroll
+            for (int k = 0; k < kWalkUnroll; ++k)
+                for (uint32_t x = rx[k] & 0xFFFF; x <= (rx[k] >> 16); ++x) atomicAdd(&cnt[x], 1u);
+        }
+        __syncwarp();
+        uint32_t* out = H2 + (size_t)j * tiles_x;
+        for (uint32_t x = lane; x < tiles_x; x += 32) out[x] = cnt[x];
+    }
+}
+
+// Level 2, scan: block y turns, for every tile x of row y, the counts of the
+// row's chunks into slots (tile start + earlier chunks), in place. Lanes take
+// tiles, the block's warps take consecutive segments of the row's chunks.
+constexpr int kColScanWarps = 16;
+__global__ void __launch_bounds__(32 * kColScanWarps) k_cols_scan(uint32_t* __restrict__ H2, uint32_t rows,
+                                                                  uint32_t tiles_x, const uint2* __restrict__ ranges,
+                                                                  const uint32_t* __restrict__ rowinfo,
+                                                                  const uint32_t* __restrict__ info) {
+    __shared__ uint32_t s_seg[kColScanWarps][32];
+    if (info[kInfoAbort]) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t y = blockIdx.x;
+    const uint32_t j0 = rowinfo[rows + y], j1 = y + 1 < rows ? rowinfo[rows + y + 1] : rowinfo[3 * rows];
+    const uint32_t per = (j1 - j0 + kColScanWarps - 1) / kColScanWarps;
+    const uint32_t s0 = min(j1, j0 + w * per), s1 = min(j1, s0 + per);
+    for (uint32_t x0 = 0; x0 < tiles_x; x0 += 32) {
+        const uint32_t x = x0 + lane;
+        const bool on = x < tiles_x;
+        uint32_t sum = 0;
+        if (on)
+            for (uint32_t j = s0; j < s1; ++j) sum += H2[(size_t)j * tiles_x + x];
+        s_seg[w][lane] = sum;
+        __syncthreads();
+        uint32_t run = on ? ranges[(size_t)y * tiles_x + x].x : 0u;
+        for (int k = 0; k < w; ++k) run += s_seg[k][lane];
+        if (on)
+            for (uint32_t j = s0; j < s1; ++j) {
+                const uint32_t h = H2[(size_t)j * tiles_x + x];
+                H2[(size_t)j * tiles_x + x] = run;
+                run += h;
+            }
+        __syncthreads();
+    }
+}
+
+// Level 2, place: a warp walks each of its chunks again and puts each item's
+// Gaussian id into its slot in every tile of the row that its rectangle spans.
+__global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* __restrict__ R1,
+                                                                const uint2* __restrict__ rect, uint32_t rows,
+                                                                uint32_t tiles_x, const uint32_t* __restrict__ len,
+                                                                const uint32_t* __restrict__ rowinfo,
+                                                                const uint32_t* __restrict__ H2,
+                                                                const uint2* __restrict__ ranges,
+                                                                uint32_t* __restrict__ vals,
+                                                                const uint32_t* __restrict__ info) {
+    extern __shared__ uint32_t s_walk[];
+    const int lane = threadIdx.x & 31;
+    if (info[kInfoAbort]) return;
+    const uint32_t total = rowinfo[3 * rows];
+    for (uint32_t j = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); j < total; j += gridDim.x * kWalkWarps) {
+        const RowChunk rc = l2_chunk(j, rows, rowinfo, len);
+        const bool last = j + 1 == (rc.y + 1 < rows ? rowinfo[rows + rc.y + 1] : rowinfo[3 * rows]);
+        Placer rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer::words(tiles_x), tiles_x);
+        const uint32_t* h = H2 + (size_t)j * tiles_x;
+        const uint2* rg = ranges + (size_t)rc.y * tiles_x;
+        auto first = [&](uint32_t x) { return h[x]; };
+        rs.init(lane, first, [&](uint32_t x) { return (last ? rg[x].y : h[x + tiles_x]) - h[x]; });
+        uint32_t g_next = rc.i0 + lane < rc.i1 ? R1[rc.i0 + lane] : 0xFFFFFFFFu;
+        for (uint32_t b = rc.i0; b < rc.i1; b += 32) {
+            const uint32_t g = g_next;
+            const uint2 r = g != 0xFFFFFFFFu ? rect[g] : make_uint2(1u, 0u);  // columns 1..0: none
+            g_next = b + 32 + lane < rc.i1 ? R1[b + 32 + lane] : 0xFFFFFFFFu;
+            rs.batch(r.x & 0xFFFF, r.y & 0xFFFF, g, lane, vals);
+        }
+        rs.flush(vals, lane);
+        __syncwarp();  // the next chunk's init rewrites what the flush reads
+    }
+}
+
 // Sorted 64-bit keys (tile << 32 | depth bits) and the tile id of every entry,
 // from the ranges: block t fills the entries of tile t.
 __global__ void k_export_keys(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
@@ -217,21 +615,96 @@ int tile_passes_for(int64_t tiles) {
     return (bits + 7) / 8;
 }
 
+// Blocks of a grid-stride walk kernel: enough for `warps` chunks, at most as
+// many as the GPU holds at once (cached per device, kernel and size).
+static unsigned walk_blocks(const void* kernel, size_t smem, int64_t warps) {
+    static std::mutex mu;
+    struct Entry {
+        int dev;
+        const void* k;
+        size_t smem;
+        int64_t blocks;
+    };
+    static Entry cache[64];
+    static int used = 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    int64_t resident = -1;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (int i = 0; i < used; ++i)
+            if (cache[i].dev == dev && cache[i].k == kernel && cache[i].smem == smem) resident = cache[i].blocks;
+        if (resident < 0) {
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * kWalkWarps, smem) != cudaSuccess) {
+                cudaGetLastError();
+                sms = 1;
+                per_sm = 1;
+            }
+            resident = (int64_t)std::max(per_sm, 1) * sms;
+            if (used < 64) cache[used++] = Entry{dev, kernel, smem, resident};
+        }
+    }
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(warps, kWalkWarps), resident));
+}
+
+// Lets the placing kernels use the route's largest shared-memory size
+// (kWalkWarps placement states for kRowWalkMax buckets), once per device; never lowers it.
+static cudaError_t walk_opt_in() {
+    static std::mutex mu;
+    static bool done[128] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    const int bytes = kWalkWarps * (int)Placer::words(kRowWalkMax) * 4;
+    if ((e = cudaFuncSetAttribute(k_rows_place, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_cols_place, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        return e;
+    done[dev] = true;
+    return cudaSuccess;
+}
+
+// Level-1 chunks of a route-a frame (a multiple of kWalkWarps), or 0 for route b.
+int64_t sort_walk_chunks(int64_t tiles_x, int64_t tiles_y) {
+    if (tiles_x < 1 || tiles_y < 1 || tiles_x > kRowWalkMax || tiles_y > kRowWalkMax) return 0;
+    const int64_t c = std::min<int64_t>(kL1ChunksMax, std::max<int64_t>(kL1ChunksMin, kH1Words / tiles_y));
+    return c / kWalkWarps * kWalkWarps;
+}
+
+// Level-2 chunks a frame can need: a row's chunks hold at least kChunkTarget * len /
+// entries items (or 32, which is more), so a row needs at most entries /
+// kChunkTarget + 1 of them; twice that over all rows, for rounding.
+static int64_t l2_chunks_max(int64_t capacity, int64_t tiles_y) {
+    return 2 * (ceil_div(capacity, kChunkTarget) + tiles_y) + 16;
+}
+
 // The corner grid has (tiles_y + 1)(tiles_x + 1) = tiles + tiles_x + tiles_y + 1
-// <= 2 tiles + 2 cells.
-size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles) {
+// <= 2 tiles + 2 cells. Route a needs no item buffers: vals and tile_key take
+// 4 bytes per entry each (the level-1 lists live in tile_key's buffer until the
+// keys are exported); route b's two 8-byte item buffers hold them.
+size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t tiles_y, int64_t chunks) {
+    const int64_t tiles = tiles_x * tiles_y;
     const int64_t bn = ceil_div(n, kSortTile), bc = ceil_div(capacity, kSortTile), bs = ceil_div(n, kScanTile);
-    const int tp = tile_passes_for(tiles);
+    const int tp = chunks > 0 ? 0 : tile_passes_for(tiles);
+    const size_t entry = chunks > 0 ? 4 : 8;
+    const int64_t rows = chunks > 0 ? tiles_y : 0;
     size_t b = 0;
-    b += 2 * align256((size_t)n * 8);                               // ditems_a, ditems_b
-    b += 2 * align256((size_t)capacity * 8);                        // items_a, items_b
-    b += align256(8 * kRadix * 4);                                  // hist
-    b += align256(16 * 4);                                          // counters
-    b += align256((size_t)4 * bn * kRadix * 4);                     // status_depth
-    b += align256((size_t)(tp > 0 ? tp : 1) * bc * kRadix * 4);     // status_tile
-    b += align256((size_t)bs * 8);                                  // scan_status
-    b += align256((size_t)(ceil_div(capacity, kDupTile) + 1) * 4);  // dup_start
-    b += align256((size_t)(2 * tiles + 2) * 4);                     // grid
+    b += 2 * align256((size_t)n * 8);                                        // ditems_a, ditems_b
+    b += 2 * align256((size_t)capacity * entry);                             // items_a, items_b
+    b += align256(8 * kRadix * 4);                                           // hist
+    b += align256(16 * 4);                                                   // counters
+    b += align256((size_t)4 * bn * kRadix * 4);                              // status_depth
+    b += align256((size_t)(tp > 0 ? tp : 1) * bc * kRadix * 4);              // status_tile
+    b += align256((size_t)bs * 8);                                           // scan_status
+    b += align256((size_t)(ceil_div(capacity, kDupTile) + 1) * 4);           // dup_start
+    b += align256((size_t)(2 * tiles + 2) * 4);                              // grid
+    b += align256((size_t)chunks * rows * 4);                                // walk_h1 [rows][chunks]
+    b += align256((size_t)rows * 4);                                         // walk_len
+    b += align256((size_t)(3 * rows + 1) * 4);                               // walk_rows
+    b += align256((size_t)(chunks > 0 ? l2_chunks_max(capacity, tiles_y) * tiles_x : 0) * 4);  // walk_h2
     return b;
 }
 
@@ -239,14 +712,17 @@ SortScratch sort_scratch(const igs_frame& f) {
     SortScratch s;
     const int64_t n = f.n, cap = f.capacity, tiles = (int64_t)f.tiles_x * f.tiles_y;
     const int64_t bn = ceil_div(n, kSortTile), bc = ceil_div(cap, kSortTile), bs = ceil_div(n, kScanTile);
+    const int64_t chunks = f.sort_chunks;
+    const size_t entry = chunks > 0 ? 4 : 8;
     s.tile_bits = tile_bits_for(tiles);
-    s.tile_passes = tile_passes_for(tiles);
+    s.tile_passes = chunks > 0 ? 0 : tile_passes_for(tiles);
+    s.walk_chunks = chunks;
     char* p = static_cast<char*>(f.scratch);
     auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
     s.ditems_a = (u64*)take((size_t)n * 8);
     s.ditems_b = (u64*)take((size_t)n * 8);
-    s.items_a = (u64*)take((size_t)cap * 8);
-    s.items_b = (u64*)take((size_t)cap * 8);
+    s.items_a = (u64*)take((size_t)cap * entry);
+    s.items_b = (u64*)take((size_t)cap * entry);
     s.hist = (uint32_t*)take(8 * kRadix * 4);
     s.counters = (uint32_t*)take(16 * 4);
     s.status_depth = (uint32_t*)take((size_t)4 * bn * kRadix * 4);
@@ -254,11 +730,16 @@ SortScratch sort_scratch(const igs_frame& f) {
     s.scan_status = (unsigned long long*)take((size_t)bs * 8);
     s.dup_start = (uint32_t*)take((size_t)(ceil_div(cap, kDupTile) + 1) * 4);
     s.grid = (int32_t*)take((size_t)(2 * tiles + 2) * 4);
+    const int64_t rows = chunks > 0 ? f.tiles_y : 0;
+    s.walk_h1 = (uint32_t*)take((size_t)chunks * rows * 4);
+    s.walk_len = (uint32_t*)take((size_t)rows * 4);
+    s.walk_rows = (uint32_t*)take((size_t)(3 * rows + 1) * 4);
+    s.walk_h2 = (uint32_t*)take((size_t)(chunks > 0 ? l2_chunks_max(cap, f.tiles_y) * f.tiles_x : 0) * 4);
     // the last tile pass (p = passes - 1) reads items_a when p is even, items_b when odd
     const bool last_reads_a = s.tile_passes > 0 && (s.tile_passes - 1) % 2 == 0;
     s.vals = reinterpret_cast<uint32_t*>(last_reads_a ? s.items_b : s.items_a);
     s.tile_key = reinterpret_cast<uint32_t*>(last_reads_a ? s.items_a : s.items_b);
-    if (s.tile_passes == 0) {  // the duplication writes the values directly
+    if (s.tile_passes == 0) {  // route a, or one tile: the values are written directly
         s.vals = reinterpret_cast<uint32_t*>(s.items_a);
         s.tile_key = reinterpret_cast<uint32_t*>(s.items_b);
     }
@@ -273,7 +754,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
     const int tp = s.tile_passes;
     const int gx = f.tiles_x + 1, gy = f.tiles_y + 1;
     cudaError_t e;
-#define CK(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+#define CK(x) do { if ((e = (x)) != cudaSuccess) { g_failed_call = #x " (sort.cu:" IGS_STR(__LINE__) ")"; return e; } } while (0)
     // reset state: status words, histograms, counters, look-back words, corner grid
     CK(cudaMemsetAsync(f.info, 0, kInfoWords * 4, st));
     CK(cudaMemsetAsync(s.hist, 0, 8 * kRadix * 4, st));
@@ -340,14 +821,53 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
                                                           s.scan_status, s.counters + 4, f.info, (uint64_t)cap);
     count_launches();
     CK(cudaGetLastError());
-    // 3. duplication, in depth order, by output position
+    if (s.walk_chunks > 0) {
+        // 3a. two-level counting sort: Gaussians into tile-row lists, then row items into tiles
+        const uint32_t rows = (uint32_t)f.tiles_y, cols = (uint32_t)f.tiles_x;
+        uint32_t* R1 = f.tile_key;  // level-1 lists: free until the keys are exported
+        const size_t count1 = (size_t)kWalkWarps * rows * 4, count2 = (size_t)kWalkWarps * cols * 4;
+        const size_t place1 = (size_t)kWalkWarps * Placer::words(rows) * 4;
+        const size_t place2 = (size_t)kWalkWarps * Placer::words(cols) * 4;
+        if (std::max(place1, place2) > 48 * 1024) CK(walk_opt_in());
+        const int64_t max2 = l2_chunks_max(cap, rows);
+        const uint32_t cmax = (uint32_t)s.walk_chunks;
+
+        const uint2* rect = reinterpret_cast<const uint2*>(f.rect);
+        const uint2* rg = reinterpret_cast<const uint2*>(f.ranges);
+        k_rows_count<<<walk_blocks((const void*)k_rows_count, count1, cmax), 32 * kWalkWarps, count1, st>>>(f.order, rect, rows, cmax, s.walk_h1, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        k_rows_scan<<<rows, kRowScanThreads, 0, st>>>(s.walk_h1, cmax, s.walk_len, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        k_rows_layout<<<1, kLayoutThreads, 0, st>>>(s.walk_len, rg, rows, cols, (uint32_t)max2, s.walk_rows, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        k_rows_place<<<walk_blocks((const void*)k_rows_place, place1, cmax), 32 * kWalkWarps, place1, st>>>(f.order, rect, rows, cmax, s.walk_h1, s.walk_len,
+                                                                s.walk_rows, R1, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        k_cols_count<<<walk_blocks((const void*)k_cols_count, count2, max2), 32 * kWalkWarps, count2, st>>>(R1, rect, rows, cols, s.walk_len, s.walk_rows,
+                                                                s.walk_h2, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        k_cols_scan<<<rows, 32 * kColScanWarps, 0, st>>>(s.walk_h2, rows, cols, rg, s.walk_rows, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        k_cols_place<<<walk_blocks((const void*)k_cols_place, place2, max2), 32 * kWalkWarps, place2, st>>>(R1, rect, rows, cols, s.walk_len, s.walk_rows,
+                                                                s.walk_h2, rg, f.vals, f.info);
+        count_launches();
+        CK(cudaGetLastError());
+        return cudaSuccess;
+    }
+    // 3b. duplication, in depth order, by output position
     const unsigned dup_blocks = (unsigned)std::max<int64_t>(1, ceil_div(cap, kDupTile));
     k_duplicate<false><<<dup_blocks, 256, 0, st>>>(f.order, f.offset, s.dup_start,
                                                    reinterpret_cast<const uint2*>(f.rect), nn, f.tiles_x, s.items_a,
                                                    tp == 0 ? f.vals : nullptr, f.info, nn, nullptr, nullptr);
     count_launches();
     CK(cudaGetLastError());
-    // 4. stable tile-id sort of the M items (M read on the device; grid sized by capacity)
+    // 4b. stable tile-id sort of the M items (M read on the device; grid sized by capacity)
     for (int p = 0; p < tp; ++p) {
         const u64* in = (p % 2 == 0) ? s.items_a : s.items_b;
         uint32_t* status = s.status_tile + (size_t)p * bc * kRadix;

@@ -50,7 +50,7 @@ class IgsScene(C.Structure):
 
 class IgsFrame(C.Structure):
     _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("width", C.c_int32), ("height", C.c_int32),
-                ("tile", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("_pad", C.c_int32),
+                ("tile", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("sort_chunks", C.c_int32),
                 ("rec", C.c_void_p), ("rect", C.c_void_p), ("count", C.c_void_p), ("depth_key", C.c_void_p),
                 ("order", C.c_void_p), ("offset", C.c_void_p), ("tile_key", C.c_void_p), ("vals", C.c_void_p),
                 ("ranges", C.c_void_p), ("T_final", C.c_void_p), ("n_contrib", C.c_void_p), ("info", C.c_void_p),

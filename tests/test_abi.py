@@ -48,7 +48,7 @@ def test_frame_layout_sizes_without_gpu():
     small = nb.value
     assert small % 256 == 0
     assert lib.igs_frame_layout(4096, 1 << 20, C.byref(c), C.byref(igs.opts(tile=16)), None, C.byref(nb), None) == 0
-    assert nb.value > small + 8 * ((1 << 20) - (1 << 16))    # two entry buffers and their double buffers grow
+    assert nb.value >= small + 8 * ((1 << 20) - (1 << 16))   # the entry buffers grow (8 or 16 bytes per entry)
 
 
 @pytest.mark.parametrize("bad", ["tile", "fx", "capacity", "n", "sh"])

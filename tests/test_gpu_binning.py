@@ -73,6 +73,25 @@ def test_keys_clustered_tiles(tile):
     _check_bitexact(sc, cam, tile)
 
 
+@pytest.mark.parametrize("width,route", [(16384, "counting"), (16392, "radix")])
+def test_keys_both_routes(width, route):
+    # 2048 tiles across at tile 8 is the widest frame the counting sort takes;
+    # one more tile column sends the entries through duplication + radix passes
+    sc = scenes.clustered_scene(200_000, 14)
+    cam = scenes.pinhole((0.0, 0.0, -3.0), width, 40, 2000.0)
+    f = igs.Frame(sc.n, 1 << 16, igs.camera(cam), igs.opts(tile=8))
+    assert (f.struct.sort_chunks > 0) == (route == "counting")
+    assert _check_bitexact(sc, cam, 8) > 10_000
+
+
+@pytest.mark.parametrize("n", [1, 255, 257, 5000])
+def test_keys_counting_sort_few_gaussians(n):
+    # fewer Gaussians than one chunk, one chunk plus one, a handful of chunks
+    sc = scenes.uniform_scene(n, 13)
+    cam = scenes.pinhole((0.0, 0.0, -2.5), 640, 360, 600.0)
+    _check_bitexact(sc, cam, 16)
+
+
 def test_keys_edge_cases():
     cam = small_camera(40, 24, 64.0)
     # one Gaussian covering every tile, one off screen, one behind the near plane,
