@@ -64,6 +64,70 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm):
+    """Algorithmic bytes per launch of every stage (per-unit figures in the design doc)
+    and the bandwidth they imply over the stage's measured time. The blends are
+    bound by issue slots, not HBM: their bytes (entry gathers, per-pixel buffers)
+    are listed for context."""
+    params = 5 + C
+    model = {
+        # read means_sigma, opacity, colour; write record, rectangle, count, depth key
+        "project": ("hbm", n * (16 + 4 + 4 * C) + n * (32 + 8 + 4 + 4)),
+        # lower bound of the binning: depth keys, rectangles, counts in; order, entries, ranges out
+        "bin_sort": ("hbm", n * (4 + 8 + 4) + n * 4 + 4 * M + 8 * tiles),
+        # per entry: id + 32-byte record; per pixel: image, T_final, n_contrib
+        "blend_fwd": ("alu", M * (4 + 32) + P * (12 + 4 + 4)),
+        "l1": ("hbm", P * 3 * 4 * 3),
+        # per entry: id + record; per pixel: dL, T_final, n_contrib; per Gaussian: 2D gradient
+        "blend_bwd": ("alu", M * (4 + 32) + P * (12 + 4 + 4) + n * 32),
+        # read params, 2D gradient, count, m, v; write params, m, v
+        "project_bwd_adam": ("hbm", n * (4 * params + 32 + 4 + 8 * params) + n * 12 * params),
+    }
+    total = sum(stage_ms.values())
+    out = []
+    for s, ms in stage_ms.items():
+        bound, nbytes = model[s]
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out.append({"stage": s, "ms": round(ms, 4), "share": round(ms / total, 4), "bound": bound,
+                    "bytes": int(nbytes), "achieved": round(gbs, 1), "frac": round(gbs / peak_hbm, 4)})
+    return out
+
+
+# ncu DRAM traffic per launch, from profiles/dram_traffic.md, valid only while the
+# kernel's sources hash to the value recorded with the capture.
+TRAFFIC_SOURCES = {
+    "project_bwd_adam": ("project.cu", "projection.cuh", "common.cuh"),
+    "project": ("project.cu", "projection.cuh", "common.cuh"),
+    "l1": ("train.cu", "common.cuh"),
+}
+
+
+def sources_sha(stage):
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES[stage]:
+        with open(os.path.join(ROOT, "paper_2403_14244_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(stage, n):
+    if stage not in TRAFFIC_SOURCES:
+        return None
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.md")) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    sha = sources_sha(stage)
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 5 and cells[0] == stage and cells[2] == sha:
+            return int(float(cells[4]) * n / float(cells[3]))
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
@@ -188,10 +252,13 @@ def run_mine(args, world, rank, local):
         elapsed_ms = float(t.item())
     # the entry capacity used in the timed region held for every view: re-run
     # each view's binning at that capacity (untimed) and read its status
+    entries = []
     for k in range(V):
         _, f = ts.renderer.run_forward(ts.scene, cam_s[k], check=False)
         st, info = igs.frame_status(f)
         assert st == igs.OK, f"view {k}: device status {st} after the timed region"
+        entries.append(int(info[0]))
+    tiles = f.tiles
     ms_per_step = elapsed_ms / args.steps
     value = world * args.steps / (elapsed_ms / 1e3)
 
@@ -216,27 +283,18 @@ def run_mine(args, world, rank, local):
     e2e = {"value": world * e2e_steps / e2e_s, "unit": "steps/s",
            "h2d_bytes_per_step": int(targets[0].numel() * 4 + 80), "d2h_bytes_per_step": 4}
 
-    # -------- roofline of the dominant kernel
+    # -------- rooflines: every stage against its bound, headline = largest HBM-bound stage
     peak_hbm, peak_kind = load_peaks()
     n, C = ts.n, ts.C
     P = cams[0].width * cams[0].height
-    dominant = max(stage_ms, key=stage_ms.get)
-    algo_bytes = {
-        # per launch, from the data the step must move (per-unit figures in the design doc)
-        "project": n * (16 + 4 + 4 * C) + n * (32 + 8 + 4 + 4),
-        # read params, g2d, count, m, v; write params, m, v
-        "project_bwd_adam": n * (4 * (5 + C) + 32 + 4 + 8 * (5 + C)) + n * 12 * (5 + C),
-        "l1": P * 3 * 4 * 3,
-    }
-    roofline = None
-    if dominant in algo_bytes:
-        achieved = algo_bytes[dominant] / (stage_ms[dominant] / 1e3) / 1e9
-        roofline = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_hbm,
-                    "unit": "GB/s", "frac": round(achieved / peak_hbm, 4), "traffic": None,
-                    "peak_kind": peak_kind}
-    else:
-        roofline = {"kernel": dominant, "bound": "alu", "achieved": None, "peak": None, "unit": None,
-                    "frac": None, "traffic": None}
+    M = sum(entries) / len(entries)
+    stages = stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm)
+    hbm = [r for r in stages if r["bound"] == "hbm"]
+    top = max(hbm, key=lambda r: r["ms"])
+    roofline = {"kernel": top["stage"], "bound": "hbm", "achieved": top["achieved"], "peak": peak_hbm,
+                "unit": "GB/s", "frac": top["frac"], "traffic": traffic_per_launch(top["stage"], n),
+                "peak_kind": peak_kind, "share_of_step": top["share"]}
+    dominant = max(stages, key=lambda r: r["ms"])
 
     extra = {}
     if not args.no_extra:
@@ -252,7 +310,9 @@ def run_mine(args, world, rank, local):
                    "parallelism": f"replicas x{world} (no collective)"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
-        "roofline": roofline, "extra": extra,
+        "roofline": roofline, "dominant": {"stage": dominant["stage"], "bound": dominant["bound"],
+                                           "share_of_step": dominant["share"]},
+        "stages": stages, "entries_mean": round(M), "extra": extra,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_budget)
@@ -327,8 +387,7 @@ def run_batched(dev, reps=10):
     sc = scenes.uniform_scene(2_000_000, 4)
     scene = igs.Scene.from_numpy(sc, dev)
     cams = [igs.camera(c) for c in scenes.sphere_cameras(32, 4)]
-    cache = os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
-        else None
+    cache = os.environ.get("IGS_AUTOTUNE_CACHE")  # where to keep the tuner's choice, if anywhere
     (tile, bb), timings = autotune(scene, cams, candidates=[(8, 64), (16, 128), (16, 256), (32, 512)], reps=3,
                                    cache_path=cache, use_cache=False, device=dev)
     br = BatchRenderer(scene, cams, tile=tile, blend_batch=bb, device=dev)
