@@ -62,121 +62,153 @@ __device__ __forceinline__ float warp_reduce8(float v[8], int lane) {
     return v[0];
 }
 
-constexpr int kBwdBatch = 32;
-
+// Entries staged per barrier pair in the backward: 64 (two ballot words per
+// warp), 32 for 32x32 tiles (whose per-warp partials would not fit otherwise).
 template <int TS>
-__global__ void __launch_bounds__(TS* TS, 1536 / (TS * TS)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+constexpr int bwd_batch() { return TS == 32 ? 32 : 64; }
+
+// One pixel's state in the reverse walk.
+struct BwdPixel {
+    float px, py, G0, G1, G2, T, S0, S1, S2;
+    uint32_t nc;
+};
+
+// The adjoint of one (pixel, entry) pair, added to v[0..6]; false if the pixel
+// did not blend the entry.
+__device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, float4 a4, const float4* s_c, int k,
+                                         const BlendParams& P, float v[8]) {
+    if (pos >= q.nc) return false;
+    const Dist d = eval_dist(q.px, q.py, a4);
+    if (d.pw > a4.w) return false;
+    const float4 c = s_c[k];
+    const float g = fast_exp2(-d.pw);
+    const float og = __fmul_rn(c.w, g);
+    const float alpha = fminf(P.alpha_max, og);
+    if (alpha < P.alpha_min) return false;
+    const float oma = 1.f - alpha;              // >= 1 - alpha_max > 0
+    const float inv = __fdividef(1.f, oma);
+    const float Tk = q.T * inv;                 // transmittance before this entry
+    const float wT = alpha * Tk;
+    v[4] += wT * q.G0;
+    v[5] += wT * q.G1;
+    v[6] += wT * q.G2;
+    const float dalpha = Tk * (q.G0 * c.x + q.G1 * c.y + q.G2 * c.z) - (q.G0 * q.S0 + q.G1 * q.S1 + q.G2 * q.S2) * inv;
+    q.S0 = fmaf(wT, c.x, q.S0);
+    q.S1 = fmaf(wT, c.y, q.S1);
+    q.S2 = fmaf(wT, c.z, q.S2);
+    q.T = Tk;
+    if (og <= P.alpha_max) {                    // alpha not clamped
+        v[3] += dalpha * g;                     // d/do
+        const float dpow = -kLn2 * g * (dalpha * c.w);  // d/d(power), power = w2 d^2
+        v[2] += dpow * d.d2;                    // d/dw2
+        const float k2 = -2.f * dpow * a4.z;
+        v[0] += k2 * d.dx;                      // d/du  (dx = px - u)
+        v[1] += k2 * d.dy;                      // d/dv
+    }
+    return true;
+}
+
+// Two pixels per thread: warp w holds rows [w 2R, w 2R + 2R) of the tile (R =
+// 32 / TS), pixel A in the first R rows and pixel B R rows below, so one warp
+// reduction per entry serves 64 pixels.
+template <int TS>
+__global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                       const float4* __restrict__ rec, BlendParams P,
                                                       const float* __restrict__ dL, const float* __restrict__ T_final,
                                                       const uint32_t* __restrict__ n_contrib,
                                                       float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
-    constexpr int NT = TS * TS;
+    constexpr int NT = TS * TS / 2;
     constexpr int NW = NT / 32;
-    constexpr int ROWS = 32 / TS;
-    __shared__ float4 s_a[kBwdBatch];
-    __shared__ float4 s_c[kBwdBatch];
-    __shared__ uint32_t s_id[kBwdBatch];
-    __shared__ float s_red[NW][kBwdBatch][8];
-    __shared__ uint32_t s_bits[NW];
+    constexpr int R = 32 / TS;
+    constexpr int BB = bwd_batch<TS>();
+    constexpr int NBW = BB / 32;  // ballot words per warp
+    __shared__ float4 s_a[BB];
+    __shared__ float4 s_c[BB];
+    __shared__ uint32_t s_id[BB];
+    __shared__ float s_red[NW][BB][8];
+    __shared__ uint32_t s_bits[NW][NBW];
     __shared__ uint32_t s_max;
     if (info[kInfoAbort]) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x;
     const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-    const int x = tx * TS + (threadIdx.x % TS), y = ty * TS + (threadIdx.x / TS);
-    const bool inside = x < P.width && y < P.height;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const int x = tx * TS + (lane % TS);
+    const int yA = ty * TS + w * 2 * R + lane / TS, yB = yA + R;
     const float bx0 = (float)(tx * TS) + 0.5f, bx1 = bx0 + (float)(TS - 1);
-    const float by0 = (float)(ty * TS + w * ROWS) + 0.5f, by1 = by0 + (float)(ROWS - 1);
+    const float by0 = (float)(ty * TS + w * 2 * R) + 0.5f, by1 = by0 + (float)(2 * R - 1);
     const uint2 rg = ranges[tile];
-    const size_t pix = (size_t)y * P.width + x, plane = (size_t)P.width * P.height;
-    float G0 = 0.f, G1 = 0.f, G2 = 0.f, T = 1.f;
-    uint32_t nc = 0;
-    if (inside) {
-        G0 = dL[pix];
-        G1 = dL[plane + pix];
-        G2 = dL[2 * plane + pix];
-        T = T_final[pix];
-        nc = n_contrib[pix];
+    const size_t plane = (size_t)P.width * P.height;
+    BwdPixel q[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int y = i ? yB : yA;
+        BwdPixel& p = q[i];
+        p.px = (float)x + 0.5f;
+        p.py = (float)y + 0.5f;
+        p.G0 = p.G1 = p.G2 = 0.f;
+        p.T = 1.f;
+        p.nc = 0;
+        if (x < P.width && y < P.height) {
+            const size_t pix = (size_t)y * P.width + x;
+            p.G0 = dL[pix];
+            p.G1 = dL[plane + pix];
+            p.G2 = dL[2 * plane + pix];
+            p.T = T_final[pix];
+            p.nc = n_contrib[pix];
+        }
+        p.S0 = p.T * P.bg[0];
+        p.S1 = p.T * P.bg[1];
+        p.S2 = p.T * P.bg[2];
     }
-    float S0 = T * P.bg[0], S1 = T * P.bg[1], S2 = T * P.bg[2];
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nc);  // this warp blended nothing at or past wmax
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(q[0].nc, q[1].nc));  // nothing blended past wmax
     if (lane == 0 && wmax) atomicMax(&s_max, wmax);
     __syncthreads();
     // no pixel blended anything at or past this entry
     const uint32_t hi_end = rg.x + min(s_max, rg.y - rg.x);
     for (uint32_t hi = hi_end; hi > rg.x;) {
-        const uint32_t lo = hi - min((uint32_t)kBwdBatch, hi - rg.x);
+        const uint32_t lo = hi - min((uint32_t)BB, hi - rg.x);
         const int nb = (int)(hi - lo);
-        if (threadIdx.x < nb) {
-            const uint32_t j = hi - 1 - threadIdx.x;  // k = 0 is the last entry of the batch
+        for (int t = threadIdx.x; t < nb; t += NT) {
+            const uint32_t j = hi - 1 - t;  // k = 0 is the last entry of the batch
             const uint32_t g = vals[j];
-            s_id[threadIdx.x] = g;
-            s_a[threadIdx.x] = rec[2 * g];
-            s_c[threadIdx.x] = rec[2 * g + 1];
+            s_id[t] = g;
+            s_a[t] = rec[2 * g];
+            s_c[t] = rec[2 * g + 1];
         }
         __syncthreads();
-        // the entries this warp may have blended: before its last contributor, reaching its rows
-        const bool reach = lane < nb && hi - 1 - lane - rg.x < wmax && may_reach(s_a[lane], bx0, bx1, by0, by1);
-        uint32_t bits = __ballot_sync(0xffffffffu, reach);
-        if (lane == 0) s_bits[w] = bits;
-        while (bits) {
-            const int k = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const uint32_t pos = hi - 1 - k - rg.x;  // list position within the tile
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool active = false;
-            if (pos < nc) {
+#pragma unroll
+        for (int hw = 0; hw < NBW; ++hw) {
+            // the entries this warp may have blended: before its last contributor, reaching its rows
+            const int kl = hw * 32 + lane;
+            const bool reach = kl < nb && hi - 1 - kl - rg.x < wmax && may_reach(s_a[kl], bx0, bx1, by0, by1);
+            uint32_t bits = __ballot_sync(0xffffffffu, reach);
+            if (lane == 0) s_bits[w][hw] = bits;
+            while (bits) {
+                const int k = hw * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const uint32_t pos = hi - 1 - k - rg.x;  // list position within the tile
                 const float4 a4 = s_a[k];
-                const Dist d = eval_dist(px, py, a4);
-                if (!(d.pw > a4.w)) {
-                    const float4 c = s_c[k];
-                    const float g = fast_exp2(-d.pw);
-                    const float og = __fmul_rn(c.w, g);
-                    const float alpha = fminf(P.alpha_max, og);
-                    if (alpha >= P.alpha_min) {
-                        active = true;
-                        const float oma = 1.f - alpha;
-                        const float inv = 1.f / oma;
-                        const float Tk = T * inv;                    // transmittance before this entry
-                        const float wT = alpha * Tk;
-                        v[4] = wT * G0;
-                        v[5] = wT * G1;
-                        v[6] = wT * G2;
-                        const float dalpha =
-                            Tk * (G0 * c.x + G1 * c.y + G2 * c.z) - (G0 * S0 + G1 * S1 + G2 * S2) * inv;
-                        S0 = fmaf(wT, c.x, S0);
-                        S1 = fmaf(wT, c.y, S1);
-                        S2 = fmaf(wT, c.z, S2);
-                        T = Tk;
-                        if (og <= P.alpha_max) {                     // alpha not clamped
-                            v[3] = dalpha * g;                       // d/do
-                            const float dpow = -kLn2 * g * (dalpha * c.w);  // d/d(power), power = w2 d^2
-                            v[2] = dpow * d.d2;                      // d/dw2
-                            const float k2 = -2.f * dpow * a4.z;
-                            v[0] = k2 * d.dx;                        // d/du  (dx = px - u)
-                            v[1] = k2 * d.dy;                        // d/dv
-                        }
-                    }
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const bool active0 = bwd_pair(q[0], pos, a4, s_c, k, P, v);
+                const bool active1 = bwd_pair(q[1], pos, a4, s_c, k, P, v);
+                if (__any_sync(0xffffffffu, active0 || active1)) {
+                    const float r = warp_reduce8(v, lane);
+                    if ((lane & 3) == 0) s_red[w][k][lane >> 2] = r;
+                } else if (lane < 8) {
+                    s_red[w][k][lane] = 0.f;
                 }
-            }
-            if (__any_sync(0xffffffffu, active)) {
-                const float r = warp_reduce8(v, lane);
-                if ((lane & 3) == 0) s_red[w][k][lane >> 2] = r;
-            } else if (lane < 8) {
-                s_red[w][k][lane] = 0.f;
             }
         }
         __syncthreads();
         // sum the warps' partials of each (entry, half) and add them to the entry's Gaussian
-        for (int q = threadIdx.x; q < nb * 2; q += NT) {
-            const int k = q >> 1, h = (q & 1) * 4;
+        for (int t = threadIdx.x; t < nb * 2; t += NT) {
+            const int k = t >> 1, h = (t & 1) * 4;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int ww = 0; ww < NW; ++ww) {
-                if (!((s_bits[ww] >> k) & 1u)) continue;
+                if (!((s_bits[ww][k >> 5] >> (k & 31)) & 1u)) continue;
                 acc.x += s_red[ww][k][h + 0];
                 acc.y += s_red[ww][k][h + 1];
                 acc.z += s_red[ww][k][h + 2];
@@ -214,9 +246,9 @@ cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const fl
     auto rec = reinterpret_cast<const float4*>(f.rec);
     auto g = reinterpret_cast<float4*>(g2d);
     switch (f.tile) {
-        case 8: k_blend_bwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 16: k_blend_bwd<16><<<tiles, 256, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 32: k_blend_bwd<32><<<tiles, 1024, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 8: k_blend_bwd<8><<<tiles, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 16: k_blend_bwd<16><<<tiles, 128, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 32: k_blend_bwd<32><<<tiles, 512, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();
