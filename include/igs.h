@@ -106,7 +106,7 @@ typedef struct igs_scene {
  * igs_render_bwd of one view, and can be reused for the next view of the same
  * size. Contents after each step:
  *   igs_project:    rec, rect, count, depth_key
- *   igs_bin_sort:   order, offset, vals, ranges, info[0..1]
+ *   igs_bin_sort:   order, vals, ranges, info[0..1]; offset only when sort_chunks == 0
  *   igs_render_fwd: T_final, n_contrib
  * Status words (device, uint32): info[0] = M entries, info[1] = Gaussians kept,
  * info[2] = error code (igs_status, 0 = none), info[3] = M the view needs. */

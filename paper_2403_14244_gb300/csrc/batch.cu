@@ -469,7 +469,7 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const B
     }
     // 4. scan over all views, 5. duplication with global tile ids
     k_scan_offsets<<<(unsigned)z.bs, kScanThreads, 0, st>>>(b.order, b.count, Vn, b.offset, s.dup_start,
-                                                            s.scan_status, s.counters + 4 * V, b.info, (uint64_t)cap);
+                                                            s.scan_status, s.counters + 4 * V, b.info, (uint64_t)cap, true);
     count_launches();
     CK(cudaGetLastError());
     const unsigned dup_blocks = (unsigned)std::max<int64_t>(1, ceil_div(cap, kDupTile));

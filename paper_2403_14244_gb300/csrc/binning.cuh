@@ -266,15 +266,16 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
 
 // Exclusive scan of count[order[p]] over p (the tile counts in front-to-back
 // order) with decoupled look-back (one warp reads 32 predecessors at a time);
-// writes offset[p], M, the kept count, and for every duplication block the
-// position in `order` of the Gaussian that holds its first entry.
+// writes offset[p], M, the kept count (if add_kept), and for every duplication
+// block the position in `order` of the Gaussian that holds its first entry.
 __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* __restrict__ order,
                                                                const uint32_t* __restrict__ count, uint32_t n,
                                                                uint32_t* __restrict__ offset,
                                                                uint32_t* __restrict__ dup_start,
                                                                unsigned long long* __restrict__ status,
                                                                uint32_t* __restrict__ block_counter,
-                                                               uint32_t* __restrict__ info, uint64_t capacity) {
+                                                               uint32_t* __restrict__ info, uint64_t capacity,
+                                                               bool add_kept) {
     __shared__ uint32_t s_blk;
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     __shared__ unsigned long long s_excl;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* _
         btotal += s_warp[k];
     }
     const unsigned warp_kept = __reduce_add_sync(0xffffffffu, kept);
-    if (lane == 0 && warp_kept) atomicAdd(&info[kInfoKept], warp_kept);
+    if (add_kept && lane == 0 && warp_kept) atomicAdd(&info[kInfoKept], warp_kept);
     if (w == 0) {
         unsigned long long* my = status + blk;
         if (lane == 0) st_relaxed_u64(my, (blk == 0 ? kScanPre : kScanAgg) | btotal);

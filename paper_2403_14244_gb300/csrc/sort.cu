@@ -43,12 +43,14 @@ namespace {
 // 2D corner grid kept in shared memory by the preparation kernel up to this many cells.
 constexpr int kGridSmemCells = 10240;
 
-// Depth-digit histograms of all n depth keys, and the rectangle corners of every
-// kept Gaussian added into the (tiles_y+1) x (tiles_x+1) difference grid.
+// Depth-digit histograms of all n depth keys, the kept count, and the rectangle
+// corners of every kept Gaussian added into the (tiles_y+1) x (tiles_x+1)
+// difference grid.
 template <bool SMEM_GRID>
 __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ depth_key, const uint2* __restrict__ rect,
                                                   const uint32_t* __restrict__ count, uint32_t n, int gx, int gy,
-                                                  uint32_t* __restrict__ hist, int32_t* __restrict__ grid) {
+                                                  uint32_t* __restrict__ hist, int32_t* __restrict__ grid,
+                                                  uint32_t* __restrict__ info) {
     extern __shared__ int32_t s_grid[];
     __shared__ uint32_t s_h[4][kRadix];
     const int cells = gx * gy;
@@ -57,11 +59,13 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
         for (int k = threadIdx.x; k < cells; k += blockDim.x) s_grid[k] = 0;
     __syncthreads();
     int32_t* g = SMEM_GRID ? s_grid : grid;
+    uint32_t kept = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t k = depth_key[i];
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(k >> (8 * p)) & 0xFF], 1u);
         if (count[i]) {
+            ++kept;
             const uint2 r = rect[i];
             const int x0 = r.x & 0xFFFF, y0 = r.x >> 16, x1 = (r.y & 0xFFFF) + 1, y1 = (r.y >> 16) + 1;
             atomicAdd(&g[y0 * gx + x0], 1);
@@ -70,6 +74,8 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
             atomicAdd(&g[y1 * gx + x1], 1);
         }
     }
+    kept = __reduce_add_sync(0xffffffffu, kept);
+    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&info[kInfoKept], kept);
     __syncthreads();
     for (int k = threadIdx.x; k < 4 * kRadix; k += blockDim.x) {
         const uint32_t v = (&s_h[0][0])[k];
@@ -103,6 +109,25 @@ __global__ void k_grid_cols(int32_t* __restrict__ grid, int gx, int tiles_x, int
     }
 }
 
+// The tile total M (summed in 64 bits over the block's threads): entries the
+// frame needs; over the capacity, the frame is aborted with IGS_ERR_CAPACITY.
+__device__ __forceinline__ void publish_tile_total(unsigned long long* s_total, uint32_t sum, uint64_t capacity,
+                                                   uint32_t* __restrict__ info) {
+    atomicAdd(s_total, (unsigned long long)sum);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long M = *s_total;
+        const uint32_t m32 = (uint32_t)min(M, (unsigned long long)0xFFFFFFFFu);
+        info[kInfoTileTotal] = m32;
+        info[kInfoM] = m32;
+        info[kInfoNeed] = m32;
+        if (M > capacity) {
+            atomicCAS(&info[kInfoErr], 0u, (uint32_t)IGS_ERR_CAPACITY);
+            info[kInfoAbort] = 1u;
+        }
+    }
+}
+
 // One block: tile ranges = exclusive scan of the per-tile counts (row-major tile
 // order), (0, 0) for empty tiles; digit histograms of the tile-id passes.
 constexpr int kTileScanThreads = 1024;
@@ -110,9 +135,11 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* _
                                                                 uint32_t tiles, int passes,
                                                                 uint2* __restrict__ ranges,
                                                                 uint32_t* __restrict__ hist_tile,
-                                                                uint32_t* __restrict__ info) {
+                                                                uint32_t* __restrict__ info, uint64_t capacity) {
     __shared__ uint32_t s_h[4][kRadix];
     __shared__ uint32_t s_warp[kTileScanThreads / 32];
+    __shared__ unsigned long long s_total;
+    if (threadIdx.x == 0) s_total = 0ull;
     for (int k = threadIdx.x; k < 4 * kRadix; k += blockDim.x) (&s_h[0][0])[k] = 0;
     const uint32_t per = (tiles + kTileScanThreads - 1) / kTileScanThreads;
     const uint32_t t0 = min(tiles, threadIdx.x * per), t1 = min(tiles, t0 + per);
@@ -127,8 +154,7 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* _
         if (c)
             for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(t >> (8 * p)) & 0xFF], c);
     }
-    if (t1 == tiles && t0 < t1) info[kInfoTileTotal] = start;  // checked against M by the scan
-    __syncthreads();
+    publish_tile_total(&s_total, sum, capacity, info);
     for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) hist_tile[k] = (&s_h[0][0])[k];
 }
 
@@ -140,10 +166,12 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
                                                                     int tiles_y, int passes,
                                                                     uint2* __restrict__ ranges,
                                                                     uint32_t* __restrict__ hist,
-                                                                    uint32_t* __restrict__ info) {
+                                                                    uint32_t* __restrict__ info, uint64_t capacity) {
     extern __shared__ int32_t s_g[];
     __shared__ uint32_t s_h[8][kRadix];
     __shared__ uint32_t s_warp[kTilesSmallThreads / 32];
+    __shared__ unsigned long long s_total;
+    if (threadIdx.x == 0) s_total = 0ull;
     const int gx = tiles_x + 1, cells = gx * (tiles_y + 1);
     const int tid = threadIdx.x;
     for (int k = tid; k < cells; k += blockDim.x) s_g[k] = grid[k];
@@ -173,8 +201,7 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
         if (c)
             for (int p = 0; p < passes; ++p) atomicAdd(&s_h[4 + p][(t >> (8 * p)) & 0xFF], c);
     }
-    if (t1 == tiles && t0 < t1) info[kInfoTileTotal] = start;
-    __syncthreads();
+    publish_tile_total(&s_total, sum, capacity, info);
     // exclusive offsets of every histogram row
     const int rows = 4 + passes;
     uint32_t v[2];
@@ -772,16 +799,16 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
     const int prep_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 4);
     if ((int64_t)gx * gy <= kGridSmemCells)
         k_bin_prep<true><<<prep_blocks, 256, (size_t)gx * gy * 4, st>>>(
-            f.depth_key, reinterpret_cast<const uint2*>(f.rect), f.count, nn, gx, gy, s.hist, s.grid);
+            f.depth_key, reinterpret_cast<const uint2*>(f.rect), f.count, nn, gx, gy, s.hist, s.grid, f.info);
     else
         k_bin_prep<false><<<prep_blocks, 256, 0, st>>>(f.depth_key, reinterpret_cast<const uint2*>(f.rect), f.count,
-                                                       nn, gx, gy, s.hist, s.grid);
+                                                       nn, gx, gy, s.hist, s.grid, f.info);
     count_launches();
     CK(cudaGetLastError());
     if ((int64_t)gx * gy <= kGridSmemCells) {
         k_tiles_small<<<1, kTilesSmallThreads, (size_t)gx * gy * 4, st>>>(s.grid, f.tiles_x, f.tiles_y, tp,
                                                                            reinterpret_cast<uint2*>(f.ranges), s.hist,
-                                                                           f.info);
+                                                                           f.info, (uint64_t)cap);
         count_launches();
         CK(cudaGetLastError());
     } else {
@@ -792,7 +819,8 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
         count_launches();
         CK(cudaGetLastError());
         k_tile_scan<<<1, kTileScanThreads, 0, st>>>(s.grid, gx, f.tiles_x, (uint32_t)tiles, tp,
-                                                    reinterpret_cast<uint2*>(f.ranges), s.hist + 4 * kRadix, f.info);
+                                                    reinterpret_cast<uint2*>(f.ranges), s.hist + 4 * kRadix, f.info,
+                                                    (uint64_t)cap);
         count_launches();
         CK(cudaGetLastError());
         k_hist_to_offsets<<<1, 1024, 0, st>>>(s.hist, 4 + tp);
@@ -816,11 +844,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
         count_launches();
         CK(cudaGetLastError());
     }
-    // 2. scan of tile counts in depth order, M, capacity check, duplication block starts
-    k_scan_offsets<<<(unsigned)bs, kScanThreads, 0, st>>>(f.order, f.count, nn, f.offset, s.dup_start,
-                                                          s.scan_status, s.counters + 4, f.info, (uint64_t)cap);
-    count_launches();
-    CK(cudaGetLastError());
+    // kept count (k_bin_prep), M and the capacity check (tile-range kernel) are known here
     if (s.walk_chunks > 0) {
         // 3a. two-level counting sort: Gaussians into tile-row lists, then row items into tiles
         const uint32_t rows = (uint32_t)f.tiles_y, cols = (uint32_t)f.tiles_x;
@@ -860,6 +884,11 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
         CK(cudaGetLastError());
         return cudaSuccess;
     }
+    // 2b. scan of tile counts in depth order (checked against the tile total), duplication block starts
+    k_scan_offsets<<<(unsigned)bs, kScanThreads, 0, st>>>(f.order, f.count, nn, f.offset, s.dup_start,
+                                                          s.scan_status, s.counters + 4, f.info, (uint64_t)cap, false);
+    count_launches();
+    CK(cudaGetLastError());
     // 3b. duplication, in depth order, by output position
     const unsigned dup_blocks = (unsigned)std::max<int64_t>(1, ceil_div(cap, kDupTile));
     k_duplicate<false><<<dup_blocks, 256, 0, st>>>(f.order, f.offset, s.dup_start,
