@@ -93,6 +93,27 @@ def stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm):
     return out
 
 
+def keysort_equivalent(stage_ms, n, C, M, tiles, peak_hbm):
+    """Projection + binning measured against the bytes the key-sort formulation
+    of the same result must move: projection, offset scan, duplication into
+    (tile << 32 | depth, id) pairs, an LSD radix sort of the pairs (histogram read
+    + P passes of 8-bit digits over 32 + bits(tiles) key bits, 24 B per pair per
+    pass) and the tile ranges. Above 1.0: binning finishes sooner than that
+    formulation could at the measured copy peak."""
+    import math
+    bits = 32 + max(1, math.ceil(math.log2(max(tiles, 2))))
+    passes = math.ceil(bits / 8)
+    nbytes = (n * (16 + 4 + 4 * C) + n * 44        # projection
+              + 8 * n                              # offset scan
+              + n * (32 + 4) + 12 * M              # duplication
+              + 8 * M + passes * 24 * M            # radix sort
+              + 8 * M + 8 * tiles)                 # ranges
+    ms = stage_ms["project"] + stage_ms["bin_sort"]
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"bytes": int(nbytes), "passes": passes, "ms": round(ms, 4), "equiv_gbs": round(gbs, 1),
+            "frac_of_peak": round(gbs / peak_hbm, 4)}
+
+
 # ncu DRAM traffic per launch, from profiles/dram_traffic.md, valid only while the
 # kernel's sources hash to the value recorded with the capture.
 TRAFFIC_SOURCES = {
@@ -289,6 +310,7 @@ def run_mine(args, world, rank, local):
     P = cams[0].width * cams[0].height
     M = sum(entries) / len(entries)
     stages = stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm)
+    keysort = keysort_equivalent(stage_ms, n, C, M, tiles, peak_hbm)
     hbm = [r for r in stages if r["bound"] == "hbm"]
     top = max(hbm, key=lambda r: r["ms"])
     roofline = {"kernel": top["stage"], "bound": "hbm", "achieved": top["achieved"], "peak": peak_hbm,
@@ -312,7 +334,7 @@ def run_mine(args, world, rank, local):
         "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
         "roofline": roofline, "dominant": {"stage": dominant["stage"], "bound": dominant["bound"],
                                            "share_of_step": dominant["share"]},
-        "stages": stages, "entries_mean": round(M), "extra": extra,
+        "stages": stages, "entries_mean": round(M), "binning_vs_keysort": keysort, "extra": extra,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_budget)

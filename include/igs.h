@@ -16,7 +16,8 @@
  *   an entry that would take the transmittance below t_min is not blended and
  *   ends the pixel; the final colour is C + T_final * bg;
  *   pixel centres are at (x + 0.5, y + 0.5);
- *   footprint radius r = 3.33 s (compact support, Eq. 2): beyond it alpha < 1/255.
+ *   footprint radius r >= s sqrt(2 (ln(255 o) + 2^-9)) (compact support, Eq. 2, per
+ *   particle): beyond it alpha < 1/255.
  *
  * Conventions for every entry point
  *   - Pointers marked "device" are CUDA device pointers of the current device;
@@ -87,7 +88,7 @@ typedef struct igs_opts {
     int32_t tile;        /* tile edge in pixels: 8, 16 or 32 */
     int32_t sh_degree;   /* -1: colour is RGB; 0..3: SH of that degree */
     int32_t param_mode;  /* 0: sigma and opacity stored as is; 1: log sigma and logit */
-    float alpha_min;     /* 1/255 */
+    float alpha_min;     /* 1/255 (at least 1/255: the footprint holds every pixel with alpha >= 1/255) */
     float alpha_max;     /* 0.99 */
     float t_min;         /* 1e-4 */
     float bg[3];         /* background colour, added with the final transmittance */
@@ -143,7 +144,7 @@ IGS_API igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camer
                             void* workspace, size_t* bytes, igs_frame* frame);
 
 /* Project every Gaussian to its screen disc and tile rectangle
- * (Eq. 7 with Sigma = sigma^2 I, Eq. 2 support radius 3.33 s; culling of z_c <=
+ * (Eq. 7 with Sigma = sigma^2 I, Eq. 2 support radius from s and o; culling of z_c <=
  * znear, sigma <= 0, opacity < 1/255, non-finite input, off-grid rectangle), and
  * evaluate its colour (RGB, or SH at the direction from the camera centre).
  * With param_mode 1 sigma = exp(log sigma) and opacity = sigmoid(logit) here.

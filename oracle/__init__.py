@@ -68,6 +68,7 @@ def _load():
             i64 = C.c_int64
             lib.orc_num_threads.restype = C.c_int
             lib.orc_project.argtypes = [i64, P, P, C.POINTER(OrcCamera), C.c_int32, P, P, P, P, P, P]
+            lib.orc_radius.argtypes = [i64, P, P, P]
             lib.orc_keys.argtypes = [i64, P, P, P, C.c_int32, C.c_int32, C.c_uint32, P, P, P]
             lib.orc_keys.restype = i64
             lib.orc_render.argtypes = [i64, P, P, P, C.POINTER(OrcCamera), C.POINTER(OrcOpts), P, P, P, P, P, P]
@@ -120,10 +121,19 @@ def _c32(a):
 
 # ------------------------------------------------------------ key path ------
 
+def radius(s, o):
+    """Footprint radius (Eq. 2's support, per particle) of screen size s and
+    opacity o: an FP32 upper bound of s sqrt(2 (ln(255 o) + 2^-9))."""
+    s, o = _c32(np.atleast_1d(s)), _c32(np.atleast_1d(o))
+    r = np.zeros(s.shape[0], np.float32)
+    _load().orc_radius(s.shape[0], _ptr(s), _ptr(o), _ptr(r))
+    return r
+
+
 def project(means_sigma, opacity, cam, tile):
-    """Canonical FP32 projection (linear sigma/opacity): u, v, s, depth, rect
-    (x0, y0, x1, y1 inclusive tile bounds) and tiles touched (0 = culled).
-    Eq. 7 with Sigma = sigma^2 I; footprint radius 3.33 s (support of Eq. 2)."""
+    """Canonical FP32 projection (linear sigma/opacity): u, v, s, r (footprint
+    radius), depth, rect (x0, y0, x1, y1 inclusive tile bounds) and tiles
+    touched (0 = culled). Eq. 7 with Sigma = sigma^2 I; support of Eq. 2."""
     ms, op = _c32(means_sigma), _c32(opacity)
     n = ms.shape[0]
     out = {k: np.zeros(n, np.float32) for k in ("u", "v", "s", "depth")}
@@ -132,6 +142,7 @@ def project(means_sigma, opacity, cam, tile):
     _load().orc_project(n, _ptr(ms), _ptr(op), C.byref(_cam(cam)), int(tile), _ptr(out["u"]),
                         _ptr(out["v"]), _ptr(out["s"]), _ptr(out["depth"]), _ptr(rect), _ptr(count))
     out["rect"], out["count"] = rect, count
+    out["r"] = radius(out["s"], op)
     return out
 
 

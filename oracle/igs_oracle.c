@@ -17,8 +17,9 @@
  *     C = sum_k c_k a_k prod_{j<k} (1 - a_j), a_k = min(0.99, o_k g_k),
  *     entries with a_k < 1/255 skipped, stop before the entry that would take
  *     the transmittance below 1e-4, background added with the final T
- *   - compact support of each particle                           Eq. 2 (support D):
- *     footprint radius r = 3.33 s, so o exp(-r^2/(2 s^2)) < 1/255 for o <= 1
+ *   - compact support of each particle                           Eq. 2 (support D),
+ *     read per particle: the footprint radius r bounds s sqrt(2 ln(255 o)) from
+ *     above (plus a small slack), so o exp(-d^2/(2 s^2)) < 1/255 beyond it
  *   - gradients of the loss w.r.t. every particle parameter      Eq. 3 and the
  *     position gradient that follows it, by the chain rule through Eq. 4, Eq. 8
  *     and the projection
@@ -67,7 +68,40 @@ typedef struct {
     double flag_margin;  /* relative margin for near-threshold decisions */
 } orc_opts;
 
-#define ORC_RADIUS_K 3.33f
+/* Footprint radius of a Gaussian of screen size s and opacity o (Eq. 2's
+ * support, per particle): r >= s sqrt(2 (ln(255 o) + 2^-9)). With
+ * x = 255 o = 2^e m, m in [1, 2): ln x = e ln 2 + ln m, and ln m =
+ * 2 (t + t^3/3 + t^5/5 + ...) with t = (m - 1)/(m + 1) in [0, 1/3); the sum is
+ * cut after t^7 (remainder < 1.2e-5) with its coefficients and ln 2 rounded up,
+ * and 2^-9 of slack covers the remainder and the roundings. Every step is one
+ * FP32 operation rounded once, in this order (no contraction). */
+static float support_radius(float s, float o) {
+    float x = 255.0f * o;
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    const int e = (int)((b >> 23) & 0xFFu) - 127;
+    const uint32_t mb = (b & 0x007FFFFFu) | 0x3F800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    const float t = (m - 1.0f) / (m + 1.0f);
+    const float t2 = t * t;
+    float p = 0.2857143f;
+    p = 0.4f + t2 * p;
+    p = 0.6666667f + t2 * p;
+    p = 2.0f + t2 * p;
+    const float a = (float)e * 0.6931472f;
+    const float q = t * p;
+    float U = a + q;
+    U = fmaxf(U, 0.0f) + 0.001953125f;
+    const float k = sqrtf(2.0f * U);
+    const float r = s * k;
+    return r * 1.000244140625f;
+}
+
+/* the radius for given (s, o) pairs (for the tests) */
+void orc_radius(int64_t n, const float* s, const float* o, float* r) {
+    for (int64_t i = 0; i < n; ++i) r[i] = support_radius(s[i], o[i]);
+}
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
@@ -109,7 +143,7 @@ static int key_path_one(const orc_camera* c, int tile, int tiles_x, int tiles_y,
     float s = (c->fx * sg) / zc;
     float u = (c->fx * xc) / zc + c->cx;
     float v = (c->fy * yc) / zc + c->cy;
-    float r = ORC_RADIUS_K * s;
+    float r = support_radius(s, o);
     if (!(isfinite(u) && isfinite(v) && isfinite(r))) return 0;
     float ts = (float)tile;
     float fx0 = floorf((u - r) / ts), fx1 = floorf((u + r) / ts);

@@ -55,9 +55,10 @@ igs_status check_opts(const igs_opts* o) {
     if (o->tile != 8 && o->tile != 16 && o->tile != 32) return fail(IGS_ERR_INVALID_ARG, "tile must be 8, 16 or 32");
     if (o->sh_degree < -1 || o->sh_degree > 3) return fail(IGS_ERR_INVALID_ARG, "sh_degree must be -1..3");
     if (o->param_mode != 0 && o->param_mode != 1) return fail(IGS_ERR_INVALID_ARG, "param_mode must be 0 or 1");
-    if (!(o->alpha_min > 0.f) || !(o->alpha_max <= 1.f) || !(o->alpha_min < o->alpha_max) || !(o->t_min > 0.f) ||
-        !(o->t_min < 1.f))
-        return fail(IGS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max <= 1 and 0 < t_min < 1");
+    if (!(o->alpha_min >= 1.0f / 255.0f) || !(o->alpha_max <= 1.f) || !(o->alpha_min < o->alpha_max) ||
+        !(o->t_min > 0.f) || !(o->t_min < 1.f))
+        return fail(IGS_ERR_INVALID_ARG,
+                    "need 1/255 <= alpha_min < alpha_max <= 1 and 0 < t_min < 1 (the footprint holds alpha >= 1/255)");
     return IGS_OK;
 }
 

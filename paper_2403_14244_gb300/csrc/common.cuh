@@ -13,7 +13,6 @@ namespace igs {
 
 // Footprint radius in units of the screen-space scale s: o exp(-K^2/2) < 1/255
 // for every o <= 1 (compact support of the particle, Eq. 2).
-constexpr float kRadiusK = 3.33f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 // Slack added to the record's exponent bound pmax = log2(o / alpha_min): it

@@ -3,8 +3,8 @@
 //
 // Eq. 7 with Sigma = sigma^2 I projects an isotropic Gaussian to a disc; the
 // on-axis radius s = fx sigma / z_c depends only on the depth (Sec. 2.4). The
-// support radius r = 3.33 s bounds the tiles a Gaussian can touch (compact
-// support, Eq. 2). The key path (cull decisions, depth bits, tile rectangle)
+// support radius r (support_radius, from s and the opacity) bounds the tiles a
+// Gaussian can touch (compact support, Eq. 2). The key path (cull decisions, depth bits, tile rectangle)
 // uses explicitly rounded FP32 operations in a fixed order so that it is
 // bit-reproducible.
 #pragma once
@@ -139,6 +139,29 @@ __device__ __forceinline__ void load_color(const float* __restrict__ col, int64_
 
 // Projection of Gaussian i for one view: disc, culling, tile rectangle, depth
 // key and colour (the per-Gaussian body shared by the one-view and batch kernels).
+// Footprint radius (Eq. 2's support, per particle): an FP32 upper bound of
+// s sqrt(2 (ln(255 o) + 2^-9)). x = 255 o = 2^e m with m in [1, 2); ln m =
+// 2 (t + t^3/3 + t^5/5 + t^7/7 + ...), t = (m - 1)/(m + 1) < 1/3, cut after t^7
+// with the coefficients and ln 2 rounded up; the 2^-9 of slack covers the cut
+// (< 1.2e-5), the roundings and the blend's exponent slack (2^-10 ln 2). Every
+// step is rounded once in a fixed order, so the rectangle is reproducible.
+__device__ __forceinline__ float support_radius(float s, float o) {
+    const float x = __fmul_rn(255.0f, o);
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu) - 127;
+    const float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    const float t = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float t2 = __fmul_rn(t, t);
+    float p = 0.2857143f;
+    p = __fadd_rn(0.4f, __fmul_rn(t2, p));
+    p = __fadd_rn(0.6666667f, __fmul_rn(t2, p));
+    p = __fadd_rn(2.0f, __fmul_rn(t2, p));
+    float U = __fadd_rn(__fmul_rn((float)e, 0.6931472f), __fmul_rn(t, p));
+    U = __fadd_rn(fmaxf(U, 0.0f), 0.001953125f);
+    const float k = __fsqrt_rn(__fmul_rn(2.0f, U));
+    return __fmul_rn(__fmul_rn(s, k), 1.000244140625f);
+}
+
 template <int DEG>
 __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const float* __restrict__ op,
                                             const float* __restrict__ col, int64_t i, const ViewParams& P,
@@ -161,7 +184,7 @@ __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const
         s = __fdiv_rn(__fmul_rn(P.fx, sg), zc);
         u = __fadd_rn(__fdiv_rn(__fmul_rn(P.fx, xc), zc), P.cx);
         v = __fadd_rn(__fdiv_rn(__fmul_rn(P.fy, yc), zc), P.cy);
-        const float r = __fmul_rn(kRadiusK, s);
+        const float r = support_radius(s, o);
         keep = isfinite(u) && isfinite(v) && isfinite(r);
         if (keep) {
             const float ts = (float)P.tile;

@@ -2,8 +2,9 @@
 (tile, depth) keys, their stable order and the per-tile ranges.
 
 The rectangle is pinned by what it must be (the smallest set of tiles that
-holds every pixel a Gaussian can reach with alpha >= 1/255, up to the fixed
-3.33 s radius), the order by numpy's stable sort, the ranges by searchsorted.
+holds every pixel a Gaussian can reach with alpha >= 1/255, up to the
+footprint radius, itself pinned against FP64 logarithms), the order by numpy's
+stable sort, the ranges by searchsorted.
 """
 import math
 
@@ -42,7 +43,7 @@ def test_rect_is_minimal_cover(tile):
     kept = p["count"] > 0
     assert kept.sum() > 100
     for i in np.nonzero(kept)[0]:
-        u, v, r = float(p["u"][i]), float(p["v"][i]), 3.33 * float(p["s"][i])
+        u, v, r = float(p["u"][i]), float(p["v"][i]), float(p["r"][i])
         x0, y0, x1, y1 = p["rect"][i]
         assert 0 <= x0 <= x1 < tx_n and 0 <= y0 <= y1 < ty_n
         assert p["count"][i] == (x1 - x0 + 1) * (y1 - y0 + 1)
@@ -80,9 +81,26 @@ def test_rect_holds_every_reachable_pixel():
             assert np.all((ys // tile >= y0) & (ys // tile <= y1))
 
 
-def test_radius_constant_bounds_the_cutoff():
-    # o exp(-K^2/2) < 1/255 for every o <= 1 with K = 3.33 (the footprint reading of Eq. 2)
-    assert math.exp(-3.33 ** 2 / 2) < float(np.float32(1 / 255))
+def test_radius_bounds_the_cutoff_tightly():
+    """Eq. 2's support per particle: beyond r, alpha = o exp(-d^2/(2 s^2)) falls
+    below 1/255 with room to spare (r^2 >= 2 s^2 (ln(255 o) + 2^-9), which holds
+    the blend's own exponent slack of 2^-10 ln 2), and r is no more than 0.1 %
+    above that bound. FP64 logarithms against the oracle's FP32 series."""
+    o = np.concatenate([np.float32(1 / 255) * (1 + np.arange(64, dtype=np.float32) / 8),
+                        np.linspace(0.01, 1.0, 4001, dtype=np.float32), np.float32([2.0, 7.5, 100.0])])
+    o = o[o >= np.float32(1 / 255)].astype(np.float32)
+    for s in (np.float32(0.37), np.float32(1.0), np.float32(23.5)):
+        r = oracle.radius(np.full(o.shape, s, np.float32), o).astype(np.float64)
+        ln = np.log(255.0 * o.astype(np.float64))
+        need = float(s) * np.sqrt(2 * (ln + 2.0 ** -9))
+        assert np.all(r >= need * (1 - 1e-6))
+        assert np.all(r <= need * (1 + 1e-3))
+        # alpha at the radius: below the cutoff by more than the blend's exponent slack
+        alpha_r = o.astype(np.float64) * np.exp(-(r / float(s)) ** 2 / 2)
+        assert np.all(alpha_r * 2 ** (2.0 ** -10) < 1 / 255)
+    # the bound follows the opacity: a faint Gaussian reaches less far
+    r1 = oracle.radius([1.0, 1.0], [1.0, 0.05])
+    assert r1[1] < 0.7 * r1[0]
 
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
