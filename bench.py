@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the 1080p forward / fwd+bwd lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--footprint", type=int, default=0, choices=(0, 1),
+                    help="tiles of a Gaussian: 0 its bounding rectangle, 1 the tiles its disc meets")
     return ap.parse_args()
 
 
@@ -197,7 +199,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------- GPU arm --------
 
-def build_workload(n, device):
+def build_workload(n, device, footprint=0):
     import numpy as np
     import torch
 
@@ -206,7 +208,8 @@ def build_workload(n, device):
 
     sc, cams = scenes.workload_train_3m(n=n)
     ts = TrainStep(torch.from_numpy(sc.means_sigma).to(device), torch.from_numpy(sc.opacity).to(device),
-                   torch.from_numpy(sc.color).to(device), sh_degree=3, tile=16, lr=1e-3, device=device)
+                   torch.from_numpy(sc.color).to(device), sh_degree=3, tile=16, lr=1e-3, device=device,
+                   footprint=footprint)
     targets_host = [torch.from_numpy(scenes.train_target(k)).pin_memory() for k in range(len(cams))]
     targets = [t.to(device) for t in targets_host]
     cam_s = [igs.camera(c) for c in cams]
@@ -224,7 +227,7 @@ def run_mine(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     igs.load()
-    sc, cams, cam_s, ts, targets, targets_host, np = build_workload(args.n, dev)
+    sc, cams, cam_s, ts, targets, targets_host, np = build_workload(args.n, dev, args.footprint)
     V = len(cams)
     stream = torch.cuda.current_stream(dev)
     # capacity calibration: every view once with a status check (untimed set-up)
@@ -327,7 +330,8 @@ def run_mine(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators, no dataset)",
         "config": {"workload": WORKLOAD, "n_gaussians": n, "sh_degree": 3, "image": [cams[0].width, cams[0].height],
-                   "views": V, "tile": 16, "optimizer": "adam lr 1e-3", "params": "mu, log sigma, logit o, SH",
+                   "views": V, "tile": 16, "footprint": "rectangle" if args.footprint == 0 else "disc rows",
+                   "optimizer": "adam lr 1e-3", "params": "mu, log sigma, logit o, SH",
                    "l2": "no flush: per-step working set 2.5 GB > 129 MB L2",
                    "parallelism": f"replicas x{world} (no collective)"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,

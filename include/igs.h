@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define IGS_ABI_VERSION 1
+#define IGS_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define IGS_API __attribute__((visibility("default")))
@@ -92,6 +92,10 @@ typedef struct igs_opts {
     float alpha_max;     /* 0.99 */
     float t_min;         /* 1e-4 */
     float bg[3];         /* background colour, added with the final transmittance */
+    int32_t footprint;   /* tiles of a Gaussian (Eq. 2's support, radius r from s and o): 0 = every tile of
+                            the bounding rectangle of its disc; 1 = in each row of that rectangle, only the
+                            tiles whose column meets the disc (fewer entries, more arithmetic). The image
+                            is the same either way; igs_project and igs_bin_sort of a frame take the same. */
 } igs_opts;
 
 /* Scene buffers (device), layout above. */
@@ -119,7 +123,11 @@ typedef struct igs_frame {
                                 the depth order; 0: duplication + radix sort on the tile id */
     float* rec;              /* [n][8] u, v, w2 = log2(e)/(2 s^2), pmax, r, g, b, o; pmax = log2(o / alpha_min)
                                 + 2^-10 bounds the exponent w2 d^2 of every pixel with alpha >= alpha_min */
-    uint32_t* rect;          /* [n][2] x0 | y0 << 16, x1 | y1 << 16 (inclusive tiles) */
+    uint32_t* rect;          /* [n][2] x0 | y0 << 16, x1 | y1 << 16 (inclusive tiles): the bounding
+                                rectangle of the tiles the footprint disc meets */
+    float* disc;             /* [n][4] u, v, footprint radius r, x0 | x1 << 16 (as float bits); zero if
+                                culled. In tile row ty of the rectangle the Gaussian touches the tiles
+                                whose column meets u +- sqrt(r^2 - dy^2) (dy: distance from v to the row) */
     uint32_t* count;         /* [n] tiles touched; 0 = culled */
     uint32_t* depth_key;     /* [n] bits of the FP32 depth z_c; 0xFFFFFFFF if culled */
     uint32_t* order;         /* [n] Gaussian ids, front to back (culled ones last) */
@@ -277,6 +285,7 @@ typedef struct igs_batch {
     int32_t width[IGS_MAX_VIEWS], height[IGS_MAX_VIEWS];
     float* rec;                 /* [V n][8] records of every (view, Gaussian), view-major */
     uint32_t* rect;             /* [V n][2] */
+    float* disc;                /* [V n][4] */
     uint32_t* count;            /* [V n] */
     uint32_t* depth_key;        /* [V n] */
     uint32_t* order;            /* [V n] record ids front to back, view after view */

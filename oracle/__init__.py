@@ -67,9 +67,11 @@ def _load():
             P = C.c_void_p
             i64 = C.c_int64
             lib.orc_num_threads.restype = C.c_int
-            lib.orc_project.argtypes = [i64, P, P, C.POINTER(OrcCamera), C.c_int32, P, P, P, P, P, P]
+            lib.orc_project.argtypes = [i64, P, P, C.POINTER(OrcCamera), C.c_int32, C.c_int32, P, P, P, P, P, P, P]
             lib.orc_radius.argtypes = [i64, P, P, P]
-            lib.orc_keys.argtypes = [i64, P, P, P, C.c_int32, C.c_int32, C.c_uint32, P, P, P]
+            lib.orc_row_span.argtypes = [i64, P, P, P, P, P, P, C.c_int32, P, P]
+            lib.orc_keys.argtypes = [i64, P, P, P, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint32,
+                                     P, P, P]
             lib.orc_keys.restype = i64
             lib.orc_render.argtypes = [i64, P, P, P, C.POINTER(OrcCamera), C.POINTER(OrcOpts), P, P, P, P, P, P]
             lib.orc_render.restype = i64
@@ -130,20 +132,37 @@ def radius(s, o):
     return r
 
 
-def project(means_sigma, opacity, cam, tile):
+def project(means_sigma, opacity, cam, tile, footprint=0):
     """Canonical FP32 projection (linear sigma/opacity): u, v, s, r (footprint
     radius), depth, rect (x0, y0, x1, y1 inclusive tile bounds) and tiles
-    touched (0 = culled). Eq. 7 with Sigma = sigma^2 I; support of Eq. 2."""
+    touched (0 = culled): every tile of rect (footprint 0) or, per row, the
+    tiles the disc meets (footprint 1). Eq. 7 with Sigma = sigma^2 I; support
+    of Eq. 2."""
     ms, op = _c32(means_sigma), _c32(opacity)
     n = ms.shape[0]
-    out = {k: np.zeros(n, np.float32) for k in ("u", "v", "s", "depth")}
+    out = {k: np.zeros(n, np.float32) for k in ("u", "v", "s", "depth", "r")}
     rect = np.zeros((n, 4), np.int32)
     count = np.zeros(n, np.int32)
-    _load().orc_project(n, _ptr(ms), _ptr(op), C.byref(_cam(cam)), int(tile), _ptr(out["u"]),
-                        _ptr(out["v"]), _ptr(out["s"]), _ptr(out["depth"]), _ptr(rect), _ptr(count))
+    _load().orc_project(n, _ptr(ms), _ptr(op), C.byref(_cam(cam)), int(tile), int(footprint), _ptr(out["u"]),
+                        _ptr(out["v"]), _ptr(out["s"]), _ptr(out["depth"]), _ptr(out["r"]), _ptr(rect),
+                        _ptr(count))
     out["rect"], out["count"] = rect, count
-    out["r"] = radius(out["s"], op)
+    out["footprint"] = int(footprint)
     return out
+
+
+def row_span(u, v, r, ty, x0, x1, tile):
+    """Tiles [xa, xb] of tile row ty (within [x0, x1]) that the disc of radius r
+    around (u, v) touches; empty when xa > xb. Vectorised over the arguments."""
+    shape = np.broadcast_shapes(*(np.shape(np.atleast_1d(a)) for a in (u, v, r, ty, x0, x1)))
+    u, v, r = (_c32(np.broadcast_to(np.atleast_1d(np.asarray(a, np.float32)), shape).ravel()) for a in (u, v, r))
+    ty, x0, x1 = (np.ascontiguousarray(np.broadcast_to(np.atleast_1d(a), shape).ravel(), np.int32)
+                  for a in (ty, x0, x1))
+    xa = np.zeros(u.shape[0], np.int32)
+    xb = np.zeros(u.shape[0], np.int32)
+    _load().orc_row_span(u.shape[0], _ptr(u), _ptr(v), _ptr(r), _ptr(ty), _ptr(x0), _ptr(x1), int(tile),
+                         _ptr(xa), _ptr(xb))
+    return xa, xb
 
 
 def keys(proj, cam, tile, tile_base=0):
@@ -158,8 +177,10 @@ def keys(proj, cam, tile, tile_base=0):
     r = np.zeros((tiles_x * tiles_y, 2), np.uint32)
     got = _load().orc_keys(proj["count"].shape[0], _ptr(np.ascontiguousarray(proj["rect"])),
                            _ptr(np.ascontiguousarray(proj["count"])),
-                           _ptr(np.ascontiguousarray(proj["depth"])), tiles_x, tiles_y, int(tile_base),
-                           _ptr(k), _ptr(v), _ptr(r))
+                           _ptr(np.ascontiguousarray(proj["depth"])), _ptr(np.ascontiguousarray(proj["u"])),
+                           _ptr(np.ascontiguousarray(proj["v"])), _ptr(np.ascontiguousarray(proj["r"])),
+                           int(tile), int(proj.get("footprint", 0)), tiles_x, tiles_y, int(tile_base), _ptr(k),
+                           _ptr(v), _ptr(r))
     assert got == m
     return k, v, r
 

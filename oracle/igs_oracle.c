@@ -103,6 +103,46 @@ void orc_radius(int64_t n, const float* s, const float* o, float* r) {
     for (int64_t i = 0; i < n; ++i) r[i] = support_radius(s[i], o[i]);
 }
 
+/* Tiles of tile row ty that the disc of radius r around (u, v) touches, within
+ * [x0, x1]: [*xa, *xb] (empty when *xa > *xb). The row's band
+ * [ty*tile, (ty+1)*tile) lies dy = max(0, ty*tile - v, v - (ty+1)*tile) from v,
+ * where the disc spans u +- sqrt(r^2 - dy^2); a tile is touched when its column
+ * meets that span. One rounding per step, in this order. */
+static void row_span(float u, float v, float r, int tile, int ty, int x0, int x1, int* xa, int* xb) {
+    const float ts = (float)tile;
+    const float lo = (float)(ty * tile), hi = (float)((ty + 1) * tile);
+    const float d1 = lo - v, d2 = v - hi;
+    const float dy = fmaxf(0.0f, fmaxf(d1, d2));
+    const float rr = r * r, dd = dy * dy;
+    const float h2 = rr - dd;
+    const float hw = sqrtf(fmaxf(h2, 0.0f));
+    const float fa = floorf((u - hw) / ts), fb = floorf((u + hw) / ts);
+    *xa = (int)fminf(fmaxf(fa, (float)x0), (float)(x1 + 1));
+    *xb = (int)fmaxf(fminf(fb, (float)x1), (float)(x0 - 1));
+}
+
+/* Tiles touched over the rows of the rectangle. */
+static int32_t span_count(float u, float v, float r, int tile, const int32_t rc[4]) {
+    int32_t c = 0;
+    for (int ty = rc[1]; ty <= rc[3]; ++ty) {
+        int xa, xb;
+        row_span(u, v, r, tile, ty, rc[0], rc[2], &xa, &xb);
+        if (xb >= xa) c += xb - xa + 1;
+    }
+    return c;
+}
+
+/* spans of given rows (for the tests): per query (u, v, r, ty, x0, x1) -> (xa, xb) */
+void orc_row_span(int64_t n, const float* u, const float* v, const float* r, const int32_t* ty,
+                  const int32_t* x0, const int32_t* x1, int32_t tile, int32_t* xa, int32_t* xb) {
+    for (int64_t i = 0; i < n; ++i) {
+        int a, b;
+        row_span(u[i], v[i], r[i], tile, ty[i], x0[i], x1[i], &a, &b);
+        xa[i] = a;
+        xb[i] = b;
+    }
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -125,13 +165,15 @@ void orc_activate(int64_t n, const float* log_sigma, int64_t ls_stride, const fl
 }
 
 /* ------------------------------------------------------ FP32 key path ----- */
-/* Canonical FP32 projection of one Gaussian. Returns 1 if it is kept.
+/* Canonical FP32 projection of one Gaussian. Returns the tiles it touches (0 = culled).
  * Culled when: an input is not finite, sigma <= 0, z_c <= znear,
- * o < 1/255 (no pixel could reach the alpha cutoff), or the tile rectangle
- * of [u-r, u+r] x [v-r, v+r] misses the tile grid. */
-static int key_path_one(const orc_camera* c, int tile, int tiles_x, int tiles_y,
+ * o < 1/255 (no pixel could reach the alpha cutoff), or its tiles miss the
+ * grid. rect is the bounding rectangle of the disc's tiles; the Gaussian touches
+ * every tile of it (footprint 0) or, in each row ty, the tiles of row_span
+ * (footprint 1). */
+static int key_path_one(const orc_camera* c, int tile, int tiles_x, int tiles_y, int footprint,
                         float mx, float my, float mz, float sg, float o,
-                        float* pu, float* pv, float* ps, float* pz, int32_t rect[4]) {
+                        float* pu, float* pv, float* ps, float* pz, float* pr, int32_t rect[4]) {
     if (!(isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(sg) && isfinite(o)))
         return 0;
     float xc = ((c->R[0] * mx + c->R[1] * my) + c->R[2] * mz) + c->t[0];
@@ -154,24 +196,29 @@ static int key_path_one(const orc_camera* c, int tile, int tiles_x, int tiles_y,
     rect[1] = (int32_t)fmaxf(fy0, 0.0f);
     rect[2] = (int32_t)fminf(fx1, (float)(tiles_x - 1));
     rect[3] = (int32_t)fminf(fy1, (float)(tiles_y - 1));
-    *pu = u; *pv = v; *ps = s; *pz = zc;
-    return 1;
+    const int32_t cnt = footprint ? span_count(u, v, r, tile, rect)
+                                  : (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1);
+    if (cnt == 0) return 0;  /* the disc meets no tile of the grid */
+    *pu = u; *pv = v; *ps = s; *pz = zc; *pr = r;
+    return cnt;
 }
 
 /* Per-Gaussian canonical projection (linear sigma and opacity given in FP32).
  * rect = (x0, y0, x1, y1) inclusive tile bounds; count = tiles touched (0 if culled). */
 void orc_project(int64_t n, const float* means_sigma, const float* opacity, const orc_camera* cam,
-                 int32_t tile, float* u, float* v, float* s, float* depth, int32_t* rect, int32_t* count) {
+                 int32_t tile, int32_t footprint, float* u, float* v, float* s, float* depth, float* radius,
+                 int32_t* rect, int32_t* count) {
     int tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
     for (int64_t i = 0; i < n; ++i) {
         const float* m = means_sigma + 4 * i;
         int32_t rc[4] = {0, 0, -1, -1};
-        float uu = 0, vv = 0, ss = 0, zz = 0;
-        int keep = key_path_one(cam, tile, tiles_x, tiles_y, m[0], m[1], m[2], m[3], opacity[i],
-                                &uu, &vv, &ss, &zz, rc);
-        u[i] = uu; v[i] = vv; s[i] = ss; depth[i] = zz;
+        float uu = 0, vv = 0, ss = 0, zz = 0, rr = 0;
+        int cnt = key_path_one(cam, tile, tiles_x, tiles_y, footprint, m[0], m[1], m[2], m[3], opacity[i],
+                               &uu, &vv, &ss, &zz, &rr, rc);
+        if (cnt == 0) { rc[0] = 0; rc[1] = 0; rc[2] = -1; rc[3] = -1; }
+        u[i] = uu; v[i] = vv; s[i] = ss; depth[i] = zz; radius[i] = rr;
         memcpy(rect + 4 * i, rc, sizeof rc);
-        count[i] = keep ? (rc[2] - rc[0] + 1) * (rc[3] - rc[1] + 1) : 0;
+        count[i] = cnt;
     }
 }
 
@@ -184,12 +231,13 @@ static int cmp_key_entry(const void* a, const void* b) {
     return x->pos < y->pos ? -1 : (x->pos > y->pos);  /* generation order: a stable sort */
 }
 
-/* Duplicate every kept Gaussian into one (key, value) pair per tile it touches,
- * key = (tile_base + ty*tiles_x + tx) << 32 | bits(depth), generated in index
- * order and row-major tile order; sort by key keeping generation order among
+/* Duplicate every kept Gaussian into one (key, value) pair per tile it touches
+ * (its rectangle, or row_span of each row of it with footprint 1), key = (tile_base + ty*tiles_x + tx)
+ * << 32 | bits(depth), generated in index order and row-major tile order; sort by key keeping generation order among
  * equal keys; record for every tile the half-open range [start, end) of its
  * entries ((0, 0) if it has none). Returns M. */
 int64_t orc_keys(int64_t n, const int32_t* rect, const int32_t* count, const float* depth,
+                 const float* u, const float* v, const float* radius, int32_t tile, int32_t footprint,
                  int32_t tiles_x, int32_t tiles_y, uint32_t tile_base,
                  uint64_t* keys_out, uint32_t* vals_out, uint32_t* ranges_out) {
     int64_t m = 0;
@@ -199,14 +247,17 @@ int64_t orc_keys(int64_t n, const int32_t* rect, const int32_t* count, const flo
     for (int64_t i = 0; i < n; ++i) {
         if (count[i] == 0) continue;
         const int32_t* rc = rect + 4 * i;
-        for (int32_t ty = rc[1]; ty <= rc[3]; ++ty)
-            for (int32_t tx = rc[0]; tx <= rc[2]; ++tx) {
+        for (int32_t ty = rc[1]; ty <= rc[3]; ++ty) {
+            int xa = rc[0], xb = rc[2];
+            if (footprint) row_span(u[i], v[i], radius[i], tile, ty, rc[0], rc[2], &xa, &xb);
+            for (int32_t tx = xa; tx <= xb; ++tx) {
                 uint64_t tid = (uint64_t)tile_base + (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;
                 e[k].key = (tid << 32) | (uint64_t)f32_bits(depth[i]);
                 e[k].pos = k;
                 e[k].val = (uint32_t)i;
                 ++k;
             }
+        }
     }
     qsort(e, (size_t)m, sizeof(key_entry), cmp_key_entry);
     int64_t tiles = (int64_t)tiles_x * tiles_y;

@@ -25,9 +25,9 @@ DEFAULT_ENTRY_BUDGET = 400_000_000
 BLEND_BATCHES = {8: (32, 64), 16: (64, 128, 256), 32: (256, 512, 1024)}
 
 
-def views_entries(scene: igs.Scene, cams, tile, sh_degree, param_mode=0, device="cuda"):
+def views_entries(scene: igs.Scene, cams, tile, sh_degree, param_mode=0, device="cuda", footprint=0):
     """Entries each view needs (one binning pass per view, synchronising)."""
-    r = Renderer(tile=tile, sh_degree=sh_degree, param_mode=param_mode, device=device)
+    r = Renderer(tile=tile, sh_degree=sh_degree, param_mode=param_mode, device=device, footprint=footprint)
     out = []
     for c in cams:
         _, f = r.run_forward(scene, c, check=True)
@@ -52,13 +52,13 @@ def pack_groups(entries, budget):
 
 class BatchRenderer:
     def __init__(self, scene: igs.Scene, cams, tile=16, blend_batch=0, sh_degree=-1, param_mode=0,
-                 bg=(0.0, 0.0, 0.0), entry_budget=DEFAULT_ENTRY_BUDGET, margin=1.10, device="cuda"):
+                 bg=(0.0, 0.0, 0.0), entry_budget=DEFAULT_ENTRY_BUDGET, margin=1.10, device="cuda", footprint=0):
         self.scene = scene
         self.cams = [c if isinstance(c, igs.IgsCamera) else igs.camera(c) for c in cams]
-        self.opts = igs.opts(tile=tile, sh_degree=sh_degree, param_mode=param_mode, bg=bg)
+        self.opts = igs.opts(tile=tile, sh_degree=sh_degree, param_mode=param_mode, bg=bg, footprint=footprint)
         self.tile, self.blend_batch = tile, blend_batch
         self.device = device
-        ent = views_entries(scene, self.cams, tile, sh_degree, param_mode, device)
+        ent = views_entries(scene, self.cams, tile, sh_degree, param_mode, device, footprint)
         self.entries = ent
         cap_budget = min(entry_budget, int(((1 << 30) - 1) / margin) - 65536)
         self.groups = pack_groups([int(m * margin) + 65536 for m in ent], cap_budget)

@@ -55,6 +55,7 @@ igs_status check_opts(const igs_opts* o) {
     if (o->tile != 8 && o->tile != 16 && o->tile != 32) return fail(IGS_ERR_INVALID_ARG, "tile must be 8, 16 or 32");
     if (o->sh_degree < -1 || o->sh_degree > 3) return fail(IGS_ERR_INVALID_ARG, "sh_degree must be -1..3");
     if (o->param_mode != 0 && o->param_mode != 1) return fail(IGS_ERR_INVALID_ARG, "param_mode must be 0 or 1");
+    if (o->footprint != 0 && o->footprint != 1) return fail(IGS_ERR_INVALID_ARG, "footprint must be 0 or 1");
     if (!(o->alpha_min >= 1.0f / 255.0f) || !(o->alpha_max <= 1.f) || !(o->alpha_min < o->alpha_max) ||
         !(o->t_min > 0.f) || !(o->t_min < 1.f))
         return fail(IGS_ERR_INVALID_ARG,
@@ -96,6 +97,7 @@ igs::ViewParams view_params(const igs_camera* c, const igs_opts* o, const igs_fr
     v.tiles_y = f ? f->tiles_y : (c->height + o->tile - 1) / o->tile;
     v.sh_degree = o->sh_degree;
     v.param_mode = o->param_mode;
+    v.footprint = o->footprint;
     return v;
 }
 
@@ -144,6 +146,7 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     size_t off = 0;
     size_t o_rec = off; off += align256((size_t)n * 32);
     size_t o_rect = off; off += align256((size_t)n * 8);
+    size_t o_disc = off; off += align256((size_t)n * 16);
     size_t o_count = off; off += align256((size_t)n * 4);
     size_t o_dkey = off; off += align256((size_t)n * 4);
     size_t o_order = off; off += align256((size_t)n * 4);
@@ -172,6 +175,7 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     frame->sort_chunks = (int32_t)chunks;
     frame->rec = reinterpret_cast<float*>(b + o_rec);
     frame->rect = reinterpret_cast<uint32_t*>(b + o_rect);
+    frame->disc = reinterpret_cast<float*>(b + o_disc);
     frame->count = reinterpret_cast<uint32_t*>(b + o_count);
     frame->depth_key = reinterpret_cast<uint32_t*>(b + o_dkey);
     frame->order = reinterpret_cast<uint32_t*>(b + o_order);
@@ -214,7 +218,7 @@ igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* stream) {
     igs_status st;
     if ((st = check_opts(opts)) || (st = check_frame(frame)) || (st = frame_matches(frame, nullptr, nullptr, opts)))
         return st;
-    return cuda_status(igs::launch_bin_sort(*frame, (cudaStream_t)stream), "igs_bin_sort");
+    return cuda_status(igs::launch_bin_sort(*frame, opts->footprint, (cudaStream_t)stream), "igs_bin_sort");
 }
 
 igs_status igs_export_keys(const igs_frame* frame, uint64_t* keys, void* stream) {
@@ -369,6 +373,7 @@ igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, co
     size_t off = 0;
     const size_t o_rec = off; off += align256((size_t)Vn * 32);
     const size_t o_rect = off; off += align256((size_t)Vn * 8);
+    const size_t o_disc = off; off += align256((size_t)Vn * 16);
     const size_t o_count = off; off += align256((size_t)Vn * 4);
     const size_t o_dkey = off; off += align256((size_t)Vn * 4);
     const size_t o_order = off; off += align256((size_t)Vn * 4);
@@ -386,6 +391,7 @@ igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, co
     char* w = static_cast<char*>(workspace);
     b.rec = reinterpret_cast<float*>(w + o_rec);
     b.rect = reinterpret_cast<uint32_t*>(w + o_rect);
+    b.disc = reinterpret_cast<float*>(w + o_disc);
     b.count = reinterpret_cast<uint32_t*>(w + o_count);
     b.depth_key = reinterpret_cast<uint32_t*>(w + o_dkey);
     b.order = reinterpret_cast<uint32_t*>(w + o_order);
@@ -439,7 +445,8 @@ igs_status igs_render_batch(igs_batch* batch, const igs_scene* scene, const igs_
     bp.width = bp.height = bp.tiles_x = bp.tiles_y = 0;
     bp.alpha_min = opts->alpha_min; bp.alpha_max = opts->alpha_max; bp.t_min = opts->t_min;
     for (int i = 0; i < 3; ++i) bp.bg[i] = opts->bg[i];
-    return cuda_status(igs::launch_render_batch(*batch, *scene, bp, opts->sh_degree, images, (cudaStream_t)stream),
+    return cuda_status(igs::launch_render_batch(*batch, *scene, bp, opts->sh_degree, images, (cudaStream_t)stream,
+                                                opts->footprint),
                        "igs_render_batch");
 }
 

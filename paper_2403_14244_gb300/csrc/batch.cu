@@ -2,7 +2,7 @@
 // image size, rendered by one chain of launches with no host synchronisation
 // (so the chain can be captured in a CUDA graph and replayed):
 //   project all (view, Gaussian) pairs            one launch, grid (blocks, V)
-//   depth-digit histograms, rectangle corners     one launch per step, per view in grid.y
+//   depth-digit histograms, footprint rows        one launch per step, per view in grid.y
 //   per-view tile counts -> global tile ranges
 //   per-view depth sorts                          4 segmented radix passes
 //   scan of tile counts over all views            one launch (view-major entry order)
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_project_batch(const float4* __restrict_
                                                        const float* __restrict__ col, int64_t n,
                                                        const BatchView* __restrict__ views,
                                                        float4* __restrict__ rec, uint2* __restrict__ rect,
-                                                       uint32_t* __restrict__ count,
+                                                       float4* __restrict__ disc, uint32_t* __restrict__ count,
                                                        uint32_t* __restrict__ depth_key) {
     __shared__ ViewParams s_vp;
     const int v = blockIdx.y;
@@ -112,13 +112,15 @@ __global__ void __launch_bounds__(256) k_project_batch(const float4* __restrict_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t r = (int64_t)v * n + i;
-    project_one<DEG>(ms, op, col, i, s_vp, rec + 2 * r, rect + r, count + r, depth_key + r);
+    project_one<DEG>(ms, op, col, i, s_vp, rec + 2 * r, rect + r, disc + r, count + r, depth_key + r);
 }
 
-// Per view (grid.y): depth-digit histograms and rectangle corners of its records.
+// Per view (grid.y): depth-digit histograms, and for each record, in each tile
+// row it touches, +1 at its first tile and -1 past its last (difference grid).
 template <bool SMEM_GRID>
 __global__ void __launch_bounds__(kPrepThreads) k_bin_prep_batch(const uint32_t* __restrict__ depth_key,
                                                                  const uint2* __restrict__ rect,
+                                                                 const float4* __restrict__ disc,
                                                                  const uint32_t* __restrict__ count, uint32_t n,
                                                                  int V, const BatchView* __restrict__ views,
                                                                  uint32_t* __restrict__ hist_depth,
@@ -141,11 +143,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_bin_prep_batch(const uint32_t*
         for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(k >> (8 * p)) & 0xFF], 1u);
         if (count[r0 + i]) {
             const uint2 r = rect[r0 + i];
-            const int x0 = r.x & 0xFFFF, y0 = r.x >> 16, x1 = (r.y & 0xFFFF) + 1, y1 = (r.y >> 16) + 1;
-            atomicAdd(&g[y0 * gx + x0], 1);
-            atomicAdd(&g[y0 * gx + x1], -1);
-            atomicAdd(&g[y1 * gx + x0], -1);
-            atomicAdd(&g[y1 * gx + x1], 1);
+            const int tile = views[v].vp.tile, fp = views[v].vp.footprint;
+            const float inv = 1.0f / (float)tile;
+            const int y0 = r.x >> 16, y1 = r.y >> 16;
+            for (int ty = y0; ty <= y1; ++ty) {  // +1 at the row's first touched tile, -1 past its last
+                const int2 sp = tile_span(fp, r, disc, r0 + i, tile, inv, ty);
+                if (sp.y < sp.x) continue;
+                atomicAdd(&g[ty * gx + sp.x], 1);
+                atomicAdd(&g[ty * gx + sp.y + 1], -1);
+            }
         }
     }
     __syncthreads();
@@ -159,6 +165,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_bin_prep_batch(const uint32_t*
             if (s_grid[k]) atomicAdd(&vg[k], s_grid[k]);
 }
 
+// Prefix of each view's difference grid along its rows: per-tile entry counts.
 __global__ void k_grid_rows_batch(int32_t* __restrict__ grid, const BatchView* __restrict__ views) {
     const int v = blockIdx.y;
     const int tx = views[v].vp.tiles_x, ty = views[v].vp.tiles_y, gx = tx + 1;
@@ -169,19 +176,6 @@ __global__ void k_grid_rows_batch(int32_t* __restrict__ grid, const BatchView* _
     for (int x = 0; x < tx; ++x) {
         run += row[x];
         row[x] = run;
-    }
-}
-
-__global__ void k_grid_cols_batch(int32_t* __restrict__ grid, const BatchView* __restrict__ views) {
-    const int v = blockIdx.y;
-    const int tx = views[v].vp.tiles_x, ty = views[v].vp.tiles_y, gx = tx + 1;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= tx) return;
-    int32_t* g = grid + views[v].grid_off;
-    int32_t run = 0;
-    for (int y = 0; y < ty; ++y) {
-        run += g[(size_t)y * gx + x];
-        g[(size_t)y * gx + x] = run;
     }
 }
 
@@ -368,7 +362,7 @@ cudaError_t batch_prepare_kernels(const igs_batch& b) {
 }
 
 cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const BlendParams& bp, int sh_degree,
-                                float* images, cudaStream_t st) {
+                                float* images, cudaStream_t st, int opts_footprint) {
     BatchScratch s;
     const int64_t cells = batch_grid_cells(b);
     const Sizes z = sizes_of(b, cells);
@@ -395,7 +389,7 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const B
         auto ms = reinterpret_cast<const float4*>(sc.means_sigma);
         auto rec = reinterpret_cast<float4*>(b.rec);
         auto rect = reinterpret_cast<uint2*>(b.rect);
-#define IGS_PB(D) k_project_batch<D><<<grid, 256, 0, st>>>(ms, sc.opacity, sc.color, n, s.views, rec, rect, b.count, b.depth_key)
+#define IGS_PB(D) k_project_batch<D><<<grid, 256, 0, st>>>(ms, sc.opacity, sc.color, n, s.views, rec, rect, reinterpret_cast<float4*>(b.disc), b.count, b.depth_key)
         switch (sh_degree) {
             case -1: IGS_PB(-1); break;
             case 0: IGS_PB(0); break;
@@ -414,12 +408,12 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const B
         const dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, kPrepThreads), 64), (unsigned)V);
         if (mc <= kBatchGridSmemCells)
             k_bin_prep_batch<true><<<grid, kPrepThreads, (size_t)mc * 4, st>>>(
-                b.depth_key, reinterpret_cast<const uint2*>(b.rect), b.count, (uint32_t)n, V, s.views, s.hist_depth,
-                s.grid);
+                b.depth_key, reinterpret_cast<const uint2*>(b.rect), reinterpret_cast<const float4*>(b.disc),
+                b.count, (uint32_t)n, V, s.views, s.hist_depth, s.grid);
         else
-            k_bin_prep_batch<false><<<grid, kPrepThreads, 0, st>>>(b.depth_key, reinterpret_cast<const uint2*>(b.rect),
-                                                                   b.count, (uint32_t)n, V, s.views, s.hist_depth,
-                                                                   s.grid);
+            k_bin_prep_batch<false><<<grid, kPrepThreads, 0, st>>>(
+                b.depth_key, reinterpret_cast<const uint2*>(b.rect), reinterpret_cast<const float4*>(b.disc),
+                b.count, (uint32_t)n, V, s.views, s.hist_depth, s.grid);
         count_launches();
         CK(cudaGetLastError());
         int max_tx = 1, max_ty = 1;
@@ -428,8 +422,6 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const B
             max_ty = std::max(max_ty, (b.height[v] + b.tile - 1) / b.tile);
         }
         k_grid_rows_batch<<<dim3((unsigned)ceil_div(max_ty, 128), V), 128, 0, st>>>(s.grid, s.views);
-        count_launches();
-        k_grid_cols_batch<<<dim3((unsigned)ceil_div(max_tx, 128), V), 128, 0, st>>>(s.grid, s.views);
         count_launches();
         k_tile_scan_batch<<<V, kTsThreads, 0, st>>>(s.grid, s.views, tp, reinterpret_cast<uint2*>(b.ranges),
                                                      s.hist_tile, s.view_total);
@@ -474,7 +466,8 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const B
     CK(cudaGetLastError());
     const unsigned dup_blocks = (unsigned)std::max<int64_t>(1, ceil_div(cap, kDupTile));
     k_duplicate<true><<<dup_blocks, 256, 0, st>>>(b.order, b.offset, s.dup_start, reinterpret_cast<const uint2*>(b.rect),
-                                                  Vn, 0, s.items_a, tp == 0 ? b.vals : nullptr, b.info, (uint32_t)n,
+                                                  reinterpret_cast<const float4*>(b.disc), b.tile, opts_footprint, Vn, 0,
+                                                  s.items_a, tp == 0 ? b.vals : nullptr, b.info, (uint32_t)n,
                                                   s.tiles_x, s.tile_base);
     count_launches();
     CK(cudaGetLastError());

@@ -380,8 +380,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* _
 
 // Duplication by output position: block b writes entries [b*kDupTile, ...) of
 // the front-to-back entry list. Each entry finds its Gaussian by a binary
-// search of the block's window of offsets, then its tile inside the Gaussian's
-// rectangle (row-major). Writes (tile id << 32 | Gaussian id), or only the
+// search of the block's window of offsets, then its tile among the tiles the
+// Gaussian touches (row by row of its rectangle, row_span in each row). Writes (tile id << 32 | Gaussian id), or only the
 // Gaussian id when no tile pass follows.
 // Batched (several views): Gaussian ids are record indices v * view_len + g,
 // and view v's tile ids start at view_tile_base[v] with view_tiles_x[v] per row.
@@ -389,7 +389,9 @@ template <bool BATCHED>
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ offset,
                                                    const uint32_t* __restrict__ dup_start,
-                                                   const uint2* __restrict__ rect, uint32_t n, int tiles_x,
+                                                   const uint2* __restrict__ rect,
+                                                   const float4* __restrict__ disc, int tile, int footprint,
+                                                   uint32_t n, int tiles_x,
                                                    u64* __restrict__ items, uint32_t* __restrict__ vals_direct,
                                                    const uint32_t* __restrict__ info, uint32_t view_len,
                                                    const int32_t* __restrict__ view_tiles_x,
@@ -445,13 +447,18 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
         const uint32_t stop = min(last, next);
         if (g < n && start <= e) {
             const uint2 r = rect[g];
-            const uint32_t x0 = r.x & 0xFFFF, y0 = r.x >> 16, wdt = (r.y & 0xFFFF) - x0 + 1;
-            const uint32_t j = e - start;
-            // (row, col) of entry j in the rectangle: float estimate, exact correction
-            uint32_t row = (uint32_t)__fmul_rz((float)j, __frcp_rz((float)wdt));
-            int32_t col = (int32_t)j - (int32_t)(row * wdt);
-            if (col < 0) { --row; col += (int32_t)wdt; }
-            if (col >= (int32_t)wdt) { ++row; col -= (int32_t)wdt; }
+            const float inv = 1.0f / (float)tile;
+            const int y0 = r.x >> 16, y1 = r.y >> 16;
+            // the row holding entry j (rows in order, each its touched tiles) and its span
+            uint32_t j = e - start;
+            int ty = y0;
+            int2 sp = tile_span(footprint, r, disc, g, tile, inv, ty);
+            for (;;) {
+                const uint32_t w = sp.y >= sp.x ? (uint32_t)(sp.y - sp.x + 1) : 0u;
+                if (j < w || ty >= y1) break;
+                j -= w;
+                sp = tile_span(footprint, r, disc, g, tile, inv, ++ty);
+            }
             uint32_t tpr, base;  // tiles per row and first tile id of the view
             if (BATCHED) {
                 const uint32_t v = g / view_len;
@@ -461,20 +468,24 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                 tpr = (uint32_t)tiles_x;
                 base = 0;
             }
-            uint32_t t = base + (y0 + row) * tpr + x0 + (uint32_t)col;
+            int col = sp.x + (int)j;
             for (; e < stop; ++e) {
+                if (col > sp.y) break;  // never: the count is the total of the spans
+                const uint32_t t = base + (uint32_t)ty * tpr + (uint32_t)col;
                 if (vals_direct)
                     vals_direct[e] = g;
                 else
                     items[e] = ((u64)t << 32) | g;
-                // next tile of the rectangle, row-major
-                if (++col == (int32_t)wdt) {
-                    col = 0;
-                    t += tpr - wdt + 1;
-                } else {
-                    ++t;
+                // next touched tile, row by row
+                if (++col > sp.y) {
+                    while (ty < y1) {
+                        sp = tile_span(footprint, r, disc, g, tile, inv, ++ty);
+                        if (sp.y >= sp.x) break;
+                    }
+                    col = sp.x;
                 }
             }
+            e = stop;
         } else {
             e = stop;
         }

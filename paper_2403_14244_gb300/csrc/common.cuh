@@ -90,6 +90,7 @@ struct ViewParams {
     float cam_center[3];  // -R^T t, for the SH view direction
     int32_t width, height, tile, tiles_x, tiles_y;
     int32_t sh_degree, param_mode;
+    int32_t footprint;  // 0: the bounding rectangle's tiles; 1: the tiles the disc meets
 };
 
 struct BlendParams {
@@ -97,6 +98,43 @@ struct BlendParams {
     float alpha_min, alpha_max, t_min;
     float bg[3];
 };
+
+// Tiles [x, y] (inclusive) of tile row ty that the disc of radius r around
+// (u, v) touches, within [x0, x1] (empty when x > y). The row's band
+// [ty tile, (ty + 1) tile) lies dy = max(0, ty tile - v, v - (ty + 1) tile) from
+// v, where the disc spans u +- sqrt(r^2 - dy^2); a tile is touched when its
+// column meets that span. One rounding per step in a fixed order, so that every
+// kernel (and the key path) finds the same tiles. The tile size is a power of
+// two, so dividing by it is exact and equals multiplying by inv_tile.
+__device__ __forceinline__ int2 row_span(float u, float v, float r, int tile, float inv_tile, int ty, int x0,
+                                         int x1) {
+    const float lo = (float)(ty * tile), hi = (float)((ty + 1) * tile);
+    const float dy = fmaxf(0.0f, fmaxf(__fsub_rn(lo, v), __fsub_rn(v, hi)));
+    // the row holding v: sqrt(fl(r r)) is r exactly (correctly rounded square and root)
+    const float hw = dy == 0.0f ? r : __fsqrt_rn(fmaxf(__fsub_rn(__fmul_rn(r, r), __fmul_rn(dy, dy)), 0.0f));
+    const float fa = floorf(__fmul_rn(__fsub_rn(u, hw), inv_tile));
+    const float fb = floorf(__fmul_rn(__fadd_rn(u, hw), inv_tile));
+    return make_int2((int)fminf(fmaxf(fa, (float)x0), (float)(x1 + 1)),
+                     (int)fmaxf(fminf(fb, (float)x1), (float)(x0 - 1)));
+}
+
+// A kept Gaussian's footprint for the tile walks: centre, radius, and the
+// column range of its bounding rectangle (x0 | x1 << 16, as float bits).
+__device__ __forceinline__ float4 make_disc(float u, float v, float r, int x0, int x1) {
+    return make_float4(u, v, r, __uint_as_float((uint32_t)x0 | ((uint32_t)x1 << 16)));
+}
+// Tiles of tile row ty (inside the rectangle's rows) that the footprint touches.
+__device__ __forceinline__ int2 disc_span(float4 d, int tile, float inv_tile, int ty) {
+    const uint32_t xr = __float_as_uint(d.w);
+    return row_span(d.x, d.y, d.z, tile, inv_tile, ty, (int)(xr & 0xFFFF), (int)(xr >> 16));
+}
+// Tiles of tile row ty that kept Gaussian g touches: the whole row of its
+// rectangle (footprint 0, the disc record is not read) or the disc's columns.
+__device__ __forceinline__ int2 tile_span(int footprint, uint2 rect, const float4* __restrict__ disc, size_t g,
+                                          int tile, float inv_tile, int ty) {
+    if (footprint == 0) return make_int2((int)(rect.x & 0xFFFF), (int)(rect.y & 0xFFFF));
+    return disc_span(disc[g], tile, inv_tile, ty);
+}
 
 // ---- launchers (defined in the .cu files, called from api.cu) ----
 cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, cudaStream_t s);
@@ -106,7 +144,7 @@ struct AdamParams;
 cudaError_t launch_project_bwd_adam(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d,
                                     float* m_ms, float* m_op, float* m_col, float* v_ms, float* v_op, float* v_col,
                                     const AdamParams& ap, cudaStream_t s);
-cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t s);
+cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t s);
 cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t s);
 cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const float* dL, float* g2d,
@@ -137,7 +175,7 @@ bool batch_blend_variant_ok(int tile, int batch);
 cudaError_t batch_set_views(const igs_batch& b, const BatchView* host_views, cudaStream_t st);
 cudaError_t batch_prepare_kernels(const igs_batch& b);
 cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const BlendParams& bp, int sh_degree,
-                                float* images, cudaStream_t st);
+                                float* images, cudaStream_t st, int footprint);
 int batch_persistent_blocks(int tile, int batch);
 
 // Scratch layout of a frame (pieces of igs_frame::scratch).

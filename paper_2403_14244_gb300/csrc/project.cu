@@ -10,10 +10,11 @@ template <int DEG>
 __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ ms, const float* __restrict__ op,
                                                  const float* __restrict__ col, int64_t n, ViewParams P,
                                                  float4* __restrict__ rec, uint2* __restrict__ rect,
-                                                 uint32_t* __restrict__ count, uint32_t* __restrict__ depth_key) {
+                                                 float4* __restrict__ disc, uint32_t* __restrict__ count,
+                                                 uint32_t* __restrict__ depth_key) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    project_one<DEG>(ms, op, col, i, P, rec + 2 * i, rect + i, count + i, depth_key + i);
+    project_one<DEG>(ms, op, col, i, P, rec + 2 * i, rect + i, disc + i, count + i, depth_key + i);
 }
 
 // Colour rows of a warp's 32 Gaussians are staged in shared memory so that
@@ -259,7 +260,7 @@ cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_
     auto ms = reinterpret_cast<const float4*>(sc.means_sigma);
     auto rec = reinterpret_cast<float4*>(f.rec);
     auto rect = reinterpret_cast<uint2*>(f.rect);
-#define IGS_PROJ(D) k_project<D><<<blocks, threads, 0, st>>>(ms, sc.opacity, sc.color, sc.n, vp, rec, rect, f.count, f.depth_key)
+#define IGS_PROJ(D) k_project<D><<<blocks, threads, 0, st>>>(ms, sc.opacity, sc.color, sc.n, vp, rec, rect, reinterpret_cast<float4*>(f.disc), f.count, f.depth_key)
     switch (vp.sh_degree) {
         case -1: IGS_PROJ(-1); break;
         case 0: IGS_PROJ(0); break;

@@ -166,7 +166,8 @@ template <int DEG>
 __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const float* __restrict__ op,
                                             const float* __restrict__ col, int64_t i, const ViewParams& P,
                                             float4* __restrict__ rec, uint2* __restrict__ rect,
-                                            uint32_t* __restrict__ count, uint32_t* __restrict__ depth_key) {
+                                            float4* __restrict__ disc, uint32_t* __restrict__ count,
+                                            uint32_t* __restrict__ depth_key) {
     const float4 m = __ldg(ms + i);
     float sg, o;
     activate(P.param_mode, m.w, __ldg(op + i), sg, o);
@@ -178,26 +179,36 @@ __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const
         zc = cam_row(P.R + 6, P.t[2], m.x, m.y, m.z);
         keep = (zc > P.znear) && (sg > 0.f) && (o >= 1.0f / 255.0f);
     }
-    float s = 0.f, u = 0.f, v = 0.f;
+    float s = 0.f, u = 0.f, v = 0.f, r = 0.f;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+    uint32_t touched = 0;
     if (keep) {
         s = __fdiv_rn(__fmul_rn(P.fx, sg), zc);
         u = __fadd_rn(__fdiv_rn(__fmul_rn(P.fx, xc), zc), P.cx);
         v = __fadd_rn(__fdiv_rn(__fmul_rn(P.fy, yc), zc), P.cy);
-        const float r = support_radius(s, o);
+        r = support_radius(s, o);
         keep = isfinite(u) && isfinite(v) && isfinite(r);
         if (keep) {
-            const float ts = (float)P.tile;
-            const float fx0 = floorf(__fdiv_rn(__fsub_rn(u, r), ts));
-            const float fx1 = floorf(__fdiv_rn(__fadd_rn(u, r), ts));
-            const float fy0 = floorf(__fdiv_rn(__fsub_rn(v, r), ts));
-            const float fy1 = floorf(__fdiv_rn(__fadd_rn(v, r), ts));
+            const float inv = 1.0f / (float)P.tile;  // exact: the tile size is a power of two
+            const float fx0 = floorf(__fmul_rn(__fsub_rn(u, r), inv));
+            const float fx1 = floorf(__fmul_rn(__fadd_rn(u, r), inv));
+            const float fy0 = floorf(__fmul_rn(__fsub_rn(v, r), inv));
+            const float fy1 = floorf(__fmul_rn(__fadd_rn(v, r), inv));
             keep = !(fx1 < 0.f || fx0 > (float)(P.tiles_x - 1) || fy1 < 0.f || fy0 > (float)(P.tiles_y - 1));
             if (keep) {
                 x0 = (int)fmaxf(fx0, 0.f);
                 y0 = (int)fmaxf(fy0, 0.f);
                 x1 = (int)fminf(fx1, (float)(P.tiles_x - 1));
                 y1 = (int)fminf(fy1, (float)(P.tiles_y - 1));
+                if (P.footprint == 0) {
+                    touched = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+                } else {  // the tiles the disc meets, row by row of its bounding rectangle
+                    for (int ty = y0; ty <= y1; ++ty) {
+                        const int2 sp = row_span(u, v, r, P.tile, inv, ty, x0, x1);
+                        if (sp.y >= sp.x) touched += (uint32_t)(sp.y - sp.x + 1);
+                    }
+                }
+                keep = touched > 0;
             }
         }
     }
@@ -205,11 +216,13 @@ __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const
         *count = 0;
         *depth_key = 0xFFFFFFFFu;
         *rect = make_uint2(0u, 0u);
+        if (P.footprint) *disc = make_float4(0.f, 0.f, 0.f, 0.f);
         rec[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         rec[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    *count = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+    *count = touched;
+    if (P.footprint) *disc = make_disc(u, v, r, x0, x1);  // read only by the per-row walks
     *depth_key = __float_as_uint(zc);
     *rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
     // colour

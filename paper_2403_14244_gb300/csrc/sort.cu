@@ -22,9 +22,11 @@
 // (depth bits, Gaussian index) order.
 //
 // The per-tile entry counts, hence the tile ranges and the digit histograms of
-// the tile passes, come from the rectangles alone: every kept Gaussian adds its
-// rectangle to a 2D difference grid (four corner updates) whose 2D prefix sum is
-// the number of entries of each tile.
+// the tile passes, come from the footprints alone: in each tile row it touches,
+// a kept Gaussian adds +1 at its first tile and -1 past its last to a
+// difference grid whose prefix sum along the row is the entries of each tile.
+// (A Gaussian touches, in each row of its bounding rectangle, the tiles whose
+// column meets its footprint disc: row_span.)
 //
 // Each radix pass is a single sweep over (key | value) items: a block counts
 // the digits of its 4096 items and publishes those counts at once, ranks the
@@ -40,16 +42,18 @@
 namespace igs {
 namespace {
 
-// 2D corner grid kept in shared memory by the preparation kernel up to this many cells.
+// Difference grid kept in shared memory by the preparation kernel up to this many cells.
 constexpr int kGridSmemCells = 10240;
 
-// Depth-digit histograms of all n depth keys, the kept count, and the rectangle
-// corners of every kept Gaussian added into the (tiles_y+1) x (tiles_x+1)
-// difference grid.
+// Depth-digit histograms of all n depth keys, the kept count, and for every kept
+// Gaussian, in each tile row, +1 at its first touched tile and -1 past its last
+// in the (tiles_y+1) x (tiles_x+1) grid (a prefix sum along each row then gives
+// the entries of every tile).
 template <bool SMEM_GRID>
 __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ depth_key, const uint2* __restrict__ rect,
-                                                  const uint32_t* __restrict__ count, uint32_t n, int gx, int gy,
-                                                  uint32_t* __restrict__ hist, int32_t* __restrict__ grid,
+                                                  const float4* __restrict__ disc, int tile, int footprint,
+                                                  const uint32_t* __restrict__ count, uint32_t n, int gx,
+                                                  int gy, uint32_t* __restrict__ hist, int32_t* __restrict__ grid,
                                                   uint32_t* __restrict__ info) {
     extern __shared__ int32_t s_grid[];
     __shared__ uint32_t s_h[4][kRadix];
@@ -67,11 +71,14 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
         if (count[i]) {
             ++kept;
             const uint2 r = rect[i];
-            const int x0 = r.x & 0xFFFF, y0 = r.x >> 16, x1 = (r.y & 0xFFFF) + 1, y1 = (r.y >> 16) + 1;
-            atomicAdd(&g[y0 * gx + x0], 1);
-            atomicAdd(&g[y0 * gx + x1], -1);
-            atomicAdd(&g[y1 * gx + x0], -1);
-            atomicAdd(&g[y1 * gx + x1], 1);
+            const float inv = 1.0f / (float)tile;
+            const int y0 = r.x >> 16, y1 = r.y >> 16;
+            for (int ty = y0; ty <= y1; ++ty) {  // +1 at the row's first touched tile, -1 past its last
+                const int2 sp = tile_span(footprint, r, disc, i, tile, inv, ty);
+                if (sp.y < sp.x) continue;
+                atomicAdd(&g[ty * gx + sp.x], 1);
+                atomicAdd(&g[ty * gx + sp.y + 1], -1);
+            }
         }
     }
     kept = __reduce_add_sync(0xffffffffu, kept);
@@ -86,8 +93,8 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
             if (s_grid[k]) atomicAdd(&grid[k], s_grid[k]);
 }
 
-// 2D inclusive prefix of the corner grid, rows then columns: afterwards grid[y][x]
-// holds the number of kept Gaussians whose rectangle contains tile (x, y).
+// Inclusive prefix of the difference grid along each row: afterwards grid[y][x]
+// holds the number of kept Gaussians that touch tile (x, y).
 __global__ void k_grid_rows(int32_t* __restrict__ grid, int gx, int tiles_x, int tiles_y) {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= tiles_y) return;
@@ -99,21 +106,14 @@ __global__ void k_grid_rows(int32_t* __restrict__ grid, int gx, int tiles_x, int
     }
 }
 
-__global__ void k_grid_cols(int32_t* __restrict__ grid, int gx, int tiles_x, int tiles_y) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= tiles_x) return;
-    int32_t run = 0;
-    for (int y = 0; y < tiles_y; ++y) {
-        run += grid[(size_t)y * gx + x];
-        grid[(size_t)y * gx + x] = run;
-    }
-}
-
 // The tile total M (summed in 64 bits over the block's threads): entries the
 // frame needs; over the capacity, the frame is aborted with IGS_ERR_CAPACITY.
 __device__ __forceinline__ void publish_tile_total(unsigned long long* s_total, uint32_t sum, uint64_t capacity,
                                                    uint32_t* __restrict__ info) {
-    atomicAdd(s_total, (unsigned long long)sum);
+    unsigned long long w = sum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(s_total, w);  // one per warp
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned long long M = *s_total;
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* _
     for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) hist_tile[k] = (&s_h[0][0])[k];
 }
 
-// One block, grid in shared memory (cells <= kGridSmemCells): the 2D prefix of
-// the corner grid, the tile ranges, the tile-digit histograms, and every digit
+// One block, grid in shared memory (cells <= kGridSmemCells): the row prefix of
+// the difference grid, the tile ranges, the tile-digit histograms, and every digit
 // histogram (4 depth + `passes` tile rows) turned into exclusive offsets.
 constexpr int kTilesSmallThreads = 1024;
 __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_t* __restrict__ grid, int tiles_x,
@@ -181,11 +181,6 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
     for (int y = tid; y < tiles_y; y += blockDim.x) {
         int32_t run = 0;
         for (int x = 0; x < tiles_x; ++x) { run += s_g[y * gx + x]; s_g[y * gx + x] = run; }
-    }
-    __syncthreads();
-    for (int x = tid; x < tiles_x; x += blockDim.x) {
-        int32_t run = 0;
-        for (int y = 0; y < tiles_y; ++y) { run += s_g[y * gx + x]; s_g[y * gx + x] = run; }
     }
     __syncthreads();
     const uint32_t tiles = (uint32_t)tiles_x * tiles_y;
@@ -503,11 +498,32 @@ __device__ __forceinline__ RowChunk l2_chunk(uint32_t j, uint32_t rows, const ui
     return rc;
 }
 
+// Tiles of row y that Gaussian g touches (row_span within its rectangle); none
+// (returned as (1, 0)) for an id of ~0 (past the chunk) or an empty span.
+struct DiscRef {
+    const uint2* rect;
+    const float4* disc;
+    int tile;
+    float inv_tile;
+    int footprint;
+    __device__ __forceinline__ int2 span(uint32_t g, int y) const {
+        if (g == 0xFFFFFFFFu) return make_int2(1, 0);
+        int2 sp;
+        if (footprint == 0) {
+            const uint2 r = rect[g];
+            sp = make_int2((int)(r.x & 0xFFFF), (int)(r.y & 0xFFFF));
+        } else {
+            sp = disc_span(disc[g], tile, inv_tile, y);
+        }
+        return sp.y < sp.x ? make_int2(1, 0) : sp;  // an empty span as (1, 0): lo > hi, both >= 0
+    }
+};
+
 // Level 2, count: for each of its chunks j, a warp adds, for each item of the
-// chunk, one to every tile of the row that the item's rectangle spans; writes
+// chunk, one to every tile of the row that the item's Gaussian touches; writes
 // row j of H2 [chunks][tiles_x].
 __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* __restrict__ R1,
-                                                                const uint2* __restrict__ rect, uint32_t rows,
+                                                                DiscRef disc, uint32_t rows,
                                                                 uint32_t tiles_x, const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 uint32_t* __restrict__ H2,
@@ -523,20 +539,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* 
         __syncwarp();
         for (uint32_t b = rc.i0; b < rc.i1; b += 32 * kWalkUnroll) {
             uint32_t g[kWalkUnroll];
-            uint32_t rx[kWalkUnroll];
+            int2 sp[kWalkUnroll];
 #pragma unroll
             for (int k = 0; k < kWalkUnroll; ++k) {
                 const uint32_t i = b + k * 32 + lane;
                 g[k] = i < rc.i1 ? R1[i] : 0xFFFFFFFFu;
             }
 #pragma unroll
-            for (int k = 0; k < kWalkUnroll; ++k) {
-                const uint2 r = g[k] != 0xFFFFFFFFu ? rect[g[k]] : make_uint2(1u, 0u);  // columns 1..0: none
-                rx[k] = (r.x & 0xFFFF) | (r.y << 16);
-            }
+            for (int k = 0; k < kWalkUnroll; ++k) sp[k] = disc.span(g[k], (int)rc.y);
 #pragma unroll
             for (int k = 0; k < kWalkUnroll; ++k)
-                for (uint32_t x = rx[k] & 0xFFFF; x <= (rx[k] >> 16); ++x) atomicAdd(&cnt[x], 1u);
+                for (int x = sp[k].x; x <= sp[k].y; ++x) atomicAdd(&cnt[x], 1u);
         }
         __syncwarp();
         uint32_t* out = H2 + (size_t)j * tiles_x;
@@ -580,9 +593,9 @@ __global__ void __launch_bounds__(32 * kColScanWarps) k_cols_scan(uint32_t* __re
 }
 
 // Level 2, place: a warp walks each of its chunks again and puts each item's
-// Gaussian id into its slot in every tile of the row that its rectangle spans.
+// Gaussian id into its slot in every tile of the row that the Gaussian touches.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* __restrict__ R1,
-                                                                const uint2* __restrict__ rect, uint32_t rows,
+                                                                DiscRef disc, uint32_t rows,
                                                                 uint32_t tiles_x, const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 const uint32_t* __restrict__ H2,
@@ -604,9 +617,9 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* 
         uint32_t g_next = rc.i0 + lane < rc.i1 ? R1[rc.i0 + lane] : 0xFFFFFFFFu;
         for (uint32_t b = rc.i0; b < rc.i1; b += 32) {
             const uint32_t g = g_next;
-            const uint2 r = g != 0xFFFFFFFFu ? rect[g] : make_uint2(1u, 0u);  // columns 1..0: none
+            const int2 sp = disc.span(g, (int)rc.y);
             g_next = b + 32 + lane < rc.i1 ? R1[b + 32 + lane] : 0xFFFFFFFFu;
-            rs.batch(r.x & 0xFFFF, r.y & 0xFFFF, g, lane, vals);
+            rs.batch((uint32_t)sp.x, (uint32_t)sp.y, g, lane, vals);
         }
         rs.flush(vals, lane);
         __syncwarp();  // the next chunk's init rewrites what the flush reads
@@ -708,7 +721,7 @@ static int64_t l2_chunks_max(int64_t capacity, int64_t tiles_y) {
     return 2 * (ceil_div(capacity, kChunkTarget) + tiles_y) + 16;
 }
 
-// The corner grid has (tiles_y + 1)(tiles_x + 1) = tiles + tiles_x + tiles_y + 1
+// The difference grid has (tiles_y + 1)(tiles_x + 1) = tiles + tiles_x + tiles_y + 1
 // <= 2 tiles + 2 cells. Route a needs no item buffers: vals and tile_key take
 // 4 bytes per entry each (the level-1 lists live in tile_key's buffer until the
 // keys are exported); route b's two 8-byte item buffers hold them.
@@ -773,7 +786,7 @@ SortScratch sort_scratch(const igs_frame& f) {
     return s;
 }
 
-cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
+cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) {
     const SortScratch s = sort_scratch(f);
     const int64_t n = f.n, cap = f.capacity;
     const int64_t tiles = (int64_t)f.tiles_x * f.tiles_y;
@@ -782,7 +795,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
     const int gx = f.tiles_x + 1, gy = f.tiles_y + 1;
     cudaError_t e;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { g_failed_call = #x " (sort.cu:" IGS_STR(__LINE__) ")"; return e; } } while (0)
-    // reset state: status words, histograms, counters, look-back words, corner grid
+    // reset state: status words, histograms, counters, look-back words, difference grid
     CK(cudaMemsetAsync(f.info, 0, kInfoWords * 4, st));
     CK(cudaMemsetAsync(s.hist, 0, 8 * kRadix * 4, st));
     CK(cudaMemsetAsync(s.counters, 0, 16 * 4, st));
@@ -795,14 +808,16 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
         return cudaSuccess;
     }
     const uint32_t nn = (uint32_t)n;
-    // 0. depth-digit histograms; rectangle corners -> per-tile counts -> ranges, tile-digit histograms
+    // 0. depth-digit histograms; footprint rows -> per-tile counts -> ranges, tile-digit histograms
     const int prep_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 4);
     if ((int64_t)gx * gy <= kGridSmemCells)
         k_bin_prep<true><<<prep_blocks, 256, (size_t)gx * gy * 4, st>>>(
-            f.depth_key, reinterpret_cast<const uint2*>(f.rect), f.count, nn, gx, gy, s.hist, s.grid, f.info);
+            f.depth_key, reinterpret_cast<const uint2*>(f.rect), reinterpret_cast<const float4*>(f.disc), f.tile,
+            footprint, f.count, nn, gx, gy, s.hist, s.grid, f.info);
     else
-        k_bin_prep<false><<<prep_blocks, 256, 0, st>>>(f.depth_key, reinterpret_cast<const uint2*>(f.rect), f.count,
-                                                       nn, gx, gy, s.hist, s.grid, f.info);
+        k_bin_prep<false><<<prep_blocks, 256, 0, st>>>(f.depth_key, reinterpret_cast<const uint2*>(f.rect),
+                                                       reinterpret_cast<const float4*>(f.disc), f.tile, footprint,
+                                                       f.count, nn, gx, gy, s.hist, s.grid, f.info);
     count_launches();
     CK(cudaGetLastError());
     if ((int64_t)gx * gy <= kGridSmemCells) {
@@ -813,9 +828,6 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
         CK(cudaGetLastError());
     } else {
         k_grid_rows<<<(unsigned)ceil_div(f.tiles_y, 128), 128, 0, st>>>(s.grid, gx, f.tiles_x, f.tiles_y);
-        count_launches();
-        CK(cudaGetLastError());
-        k_grid_cols<<<(unsigned)ceil_div(f.tiles_x, 128), 128, 0, st>>>(s.grid, gx, f.tiles_x, f.tiles_y);
         count_launches();
         CK(cudaGetLastError());
         k_tile_scan<<<1, kTileScanThreads, 0, st>>>(s.grid, gx, f.tiles_x, (uint32_t)tiles, tp,
@@ -871,14 +883,15 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
                                                                 s.walk_rows, R1, f.info);
         count_launches();
         CK(cudaGetLastError());
-        k_cols_count<<<walk_blocks((const void*)k_cols_count, count2, max2), 32 * kWalkWarps, count2, st>>>(R1, rect, rows, cols, s.walk_len, s.walk_rows,
+        const DiscRef disc{rect, reinterpret_cast<const float4*>(f.disc), f.tile, 1.0f / (float)f.tile, footprint};
+        k_cols_count<<<walk_blocks((const void*)k_cols_count, count2, max2), 32 * kWalkWarps, count2, st>>>(R1, disc, rows, cols, s.walk_len, s.walk_rows,
                                                                 s.walk_h2, f.info);
         count_launches();
         CK(cudaGetLastError());
         k_cols_scan<<<rows, 32 * kColScanWarps, 0, st>>>(s.walk_h2, rows, cols, rg, s.walk_rows, f.info);
         count_launches();
         CK(cudaGetLastError());
-        k_cols_place<<<walk_blocks((const void*)k_cols_place, place2, max2), 32 * kWalkWarps, place2, st>>>(R1, rect, rows, cols, s.walk_len, s.walk_rows,
+        k_cols_place<<<walk_blocks((const void*)k_cols_place, place2, max2), 32 * kWalkWarps, place2, st>>>(R1, disc, rows, cols, s.walk_len, s.walk_rows,
                                                                 s.walk_h2, rg, f.vals, f.info);
         count_launches();
         CK(cudaGetLastError());
@@ -892,7 +905,9 @@ cudaError_t launch_bin_sort(const igs_frame& f, cudaStream_t st) {
     // 3b. duplication, in depth order, by output position
     const unsigned dup_blocks = (unsigned)std::max<int64_t>(1, ceil_div(cap, kDupTile));
     k_duplicate<false><<<dup_blocks, 256, 0, st>>>(f.order, f.offset, s.dup_start,
-                                                   reinterpret_cast<const uint2*>(f.rect), nn, f.tiles_x, s.items_a,
+                                                   reinterpret_cast<const uint2*>(f.rect),
+                                                   reinterpret_cast<const float4*>(f.disc), f.tile, footprint, nn,
+                                                   f.tiles_x, s.items_a,
                                                    tp == 0 ? f.vals : nullptr, f.info, nn, nullptr, nullptr);
     count_launches();
     CK(cudaGetLastError());

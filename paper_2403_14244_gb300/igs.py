@@ -19,7 +19,7 @@ import torch
 
 from . import _build
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 _lock = threading.Lock()
 _lib = None
 
@@ -41,7 +41,8 @@ class IgsCamera(C.Structure):
 
 class IgsOpts(C.Structure):
     _fields_ = [("tile", C.c_int32), ("sh_degree", C.c_int32), ("param_mode", C.c_int32),
-                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("bg", C.c_float * 3)]
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("bg", C.c_float * 3),
+                ("footprint", C.c_int32)]
 
 
 class IgsScene(C.Structure):
@@ -51,8 +52,9 @@ class IgsScene(C.Structure):
 class IgsFrame(C.Structure):
     _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("width", C.c_int32), ("height", C.c_int32),
                 ("tile", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("sort_chunks", C.c_int32),
-                ("rec", C.c_void_p), ("rect", C.c_void_p), ("count", C.c_void_p), ("depth_key", C.c_void_p),
-                ("order", C.c_void_p), ("offset", C.c_void_p), ("tile_key", C.c_void_p), ("vals", C.c_void_p),
+                ("rec", C.c_void_p), ("rect", C.c_void_p), ("disc", C.c_void_p), ("count", C.c_void_p),
+                ("depth_key", C.c_void_p), ("order", C.c_void_p), ("offset", C.c_void_p), ("tile_key", C.c_void_p),
+                ("vals", C.c_void_p),
                 ("ranges", C.c_void_p), ("T_final", C.c_void_p), ("n_contrib", C.c_void_p), ("info", C.c_void_p),
                 ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t)]
 
@@ -65,7 +67,8 @@ class IgsBatch(C.Structure):
                 ("blend_batch", C.c_int32), ("persistent_blocks", C.c_int32), ("tiles_total", C.c_int64),
                 ("image_floats", C.c_int64), ("image_offset", C.c_int64 * MAX_VIEWS),
                 ("tile_base", C.c_uint32 * MAX_VIEWS), ("width", C.c_int32 * MAX_VIEWS),
-                ("height", C.c_int32 * MAX_VIEWS), ("rec", C.c_void_p), ("rect", C.c_void_p), ("count", C.c_void_p),
+                ("height", C.c_int32 * MAX_VIEWS), ("rec", C.c_void_p), ("rect", C.c_void_p), ("disc", C.c_void_p),
+                ("count", C.c_void_p),
                 ("depth_key", C.c_void_p), ("order", C.c_void_p), ("offset", C.c_void_p), ("vals", C.c_void_p),
                 ("ranges", C.c_void_p), ("info", C.c_void_p), ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t)]
 
@@ -180,11 +183,12 @@ def camera(cam) -> IgsCamera:
 
 
 def opts(tile=16, sh_degree=-1, param_mode=0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4,
-         bg=(0.0, 0.0, 0.0)) -> IgsOpts:
+         bg=(0.0, 0.0, 0.0), footprint=0) -> IgsOpts:
     o = IgsOpts()
     o.tile, o.sh_degree, o.param_mode = int(tile), int(sh_degree), int(param_mode)
     o.alpha_min, o.alpha_max, o.t_min = alpha_min, alpha_max, t_min
     o.bg[:] = [float(x) for x in bg]
+    o.footprint = int(footprint)
     return o
 
 
@@ -249,6 +253,9 @@ class Frame:
 
     def depth_key(self):
         return self.view("depth_key", self.n)
+
+    def disc(self):
+        return self.view("disc", self.n * 4, torch.float32).view(self.n, 4)
 
     def rect(self):
         return self.view("rect", self.n * 2).view(self.n, 2)

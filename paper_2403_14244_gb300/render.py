@@ -21,9 +21,9 @@ DEFAULT_MIN_CAPACITY = 1 << 16
 
 class Renderer:
     def __init__(self, tile=16, sh_degree=-1, param_mode=0, bg=(0.0, 0.0, 0.0), alpha_min=1.0 / 255.0,
-                 alpha_max=0.99, t_min=1e-4, device="cuda"):
+                 alpha_max=0.99, t_min=1e-4, device="cuda", footprint=0):
         self.opts = igs.opts(tile=tile, sh_degree=sh_degree, param_mode=param_mode, alpha_min=alpha_min,
-                             alpha_max=alpha_max, t_min=t_min, bg=bg)
+                             alpha_max=alpha_max, t_min=t_min, bg=bg, footprint=footprint)
         self.device = device
         self._frames = {}
         self._cap_hint = {}
@@ -118,7 +118,8 @@ class TrainStep:
     never written; fused=False writes the gradient to `grad` and applies igs_adam
     over the flat buffer (same update)."""
 
-    def __init__(self, means_sigma, opacity, color, sh_degree, tile=16, lr=1e-3, device="cuda", fused=True):
+    def __init__(self, means_sigma, opacity, color, sh_degree, tile=16, lr=1e-3, device="cuda", fused=True,
+                 footprint=0):
         n = means_sigma.shape[0]
         C = color.shape[1]
         self.n, self.C = n, C
@@ -138,7 +139,7 @@ class TrainStep:
         self.op.copy_(opacity)
         self.col.copy_(color)
         self.scene = igs.Scene(self.ms, self.op, self.col)
-        self.renderer = Renderer(tile=tile, sh_degree=sh_degree, param_mode=1, device=device)
+        self.renderer = Renderer(tile=tile, sh_degree=sh_degree, param_mode=1, device=device, footprint=footprint)
         self.g2d = torch.empty((n, 8), dtype=torch.float32, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         self.lr = lr

@@ -11,9 +11,9 @@ def to_device(sc):
     return igs.Scene.from_numpy(sc, "cuda")
 
 
-def run_forward(sc, cam, tile=16, bg=(0.0, 0.0, 0.0), capacity=None):
+def run_forward(sc, cam, tile=16, bg=(0.0, 0.0, 0.0), capacity=None, footprint=0):
     """project + bin_sort + render_fwd; returns (renderer, frame, scene, img numpy)."""
-    r = Renderer(tile=tile, sh_degree=sc.sh_degree, param_mode=int(sc.log_params), bg=bg)
+    r = Renderer(tile=tile, sh_degree=sc.sh_degree, param_mode=int(sc.log_params), bg=bg, footprint=footprint)
     scene = to_device(sc)
     if capacity is not None:
         r._cap_hint[(scene.n, cam.width, cam.height)] = capacity

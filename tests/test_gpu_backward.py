@@ -14,16 +14,16 @@ from tests._tiny import random_small
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_grads(sc, cam, W, tile=16, bg=(0.0, 0.0, 0.0)):
-    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile, bg=bg)
+def _gpu_grads(sc, cam, W, tile=16, bg=(0.0, 0.0, 0.0), footprint=0):
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile, bg=bg, footprint=footprint)
     dimg = torch.from_numpy(np.ascontiguousarray(W, np.float32)).cuda()
     d_ms, d_op, d_col = r.run_backward(scene, cam, f, dimg)
     torch.cuda.synchronize()
     return img, d_ms.cpu().numpy(), d_op.cpu().numpy(), d_col.cpu().numpy()
 
 
-def _compare(sc, cam, W, tile=16, bg=(0.0, 0.0, 0.0), **tol):
-    img, d_ms, d_op, d_col = _gpu_grads(sc, cam, W, tile, bg)
+def _compare(sc, cam, W, tile=16, bg=(0.0, 0.0, 0.0), footprint=0, **tol):
+    img, d_ms, d_op, d_col = _gpu_grads(sc, cam, W, tile, bg, footprint)
     ref = oracle.backward(sc, cam, W, mode=1, bg=bg)
     out = {}
     out["means"] = _gpu.grad_close(d_ms[:, :3], ref["d_means"], "means", **tol)
@@ -33,11 +33,12 @@ def _compare(sc, cam, W, tile=16, bg=(0.0, 0.0, 0.0), **tol):
     return out, ref
 
 
+@pytest.mark.parametrize("footprint", [0, 1])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_backward_rgb_small(tile):
+def test_backward_rgb_small(tile, footprint):
     sc, cam = random_small(300, 41, w=80, h=60, spread=0.8)
     W = np.random.default_rng(1).normal(size=(3, cam.height, cam.width))
-    _compare(sc, cam, W, tile=tile)
+    _compare(sc, cam, W, tile=tile, footprint=footprint)
 
 
 def test_backward_sh3_log_background():

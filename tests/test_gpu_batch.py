@@ -25,22 +25,23 @@ def _cams(seed=3):
     return cams
 
 
-def _single(scene_np, cam, tile):
-    return _gpu.run_forward(scene_np, cam, tile=tile)[3]
+def _single(scene_np, cam, tile, footprint=0):
+    return _gpu.run_forward(scene_np, cam, tile=tile, footprint=footprint)[3]
 
 
-@pytest.mark.parametrize("tile,bb", [(16, 0), (16, 64), (8, 32), (32, 512)])
-def test_batch_bit_identical_to_single_renders(tile, bb):
+@pytest.mark.parametrize("tile,bb,footprint", [(16, 0, 0), (16, 64, 0), (8, 32, 0), (32, 512, 0), (16, 128, 1),
+                                               (8, 64, 1)])
+def test_batch_bit_identical_to_single_renders(tile, bb, footprint):
     sc = scenes.uniform_scene(200_000, 41)
     scene = _gpu.to_device(sc)
     cams = _cams()
-    br = BatchRenderer(scene, cams, tile=tile, blend_batch=bb)
+    br = BatchRenderer(scene, cams, tile=tile, blend_batch=bb, footprint=footprint)
     br.render()
     torch.cuda.synchronize()
     br.check()
     for v, cam in enumerate(cams):
         got = br.image(v).cpu().numpy().astype(np.float64)
-        np.testing.assert_array_equal(got, _single(sc, cam, tile), err_msg=f"view {v}")
+        np.testing.assert_array_equal(got, _single(sc, cam, tile, footprint), err_msg=f"view {v}")
 
 
 def test_batch_graph_replay_and_new_poses():

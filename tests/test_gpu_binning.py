@@ -13,9 +13,9 @@ from tests._tiny import random_small, scene_from, small_camera
 pytestmark = pytest.mark.gpu
 
 
-def _check_bitexact(sc, cam, tile):
-    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile)
-    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile)
+def _check_bitexact(sc, cam, tile, footprint=0):
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile, footprint=footprint)
+    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile, footprint)
     count = f.count().cpu().numpy().view(np.uint32)
     np.testing.assert_array_equal(count, p["count"].astype(np.uint32))
     kept = p["count"] > 0
@@ -47,18 +47,20 @@ def _check_bitexact(sc, cam, tile):
     return len(k_ref)
 
 
+@pytest.mark.parametrize("footprint", [0, 1])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_keys_forward_4k(tile):
+def test_keys_forward_4k(tile, footprint):
     sc, cam = scenes.workload_forward_4k()
-    m = _check_bitexact(sc, cam, tile)
+    m = _check_bitexact(sc, cam, tile, footprint)
     assert m > 4096
 
 
-def test_keys_ragged_large():
+@pytest.mark.parametrize("footprint", [0, 1])
+def test_keys_ragged_large(footprint):
     # 1297 x 840 (ragged edge tiles), 300k Gaussians: many sort blocks, partial last block
     sc = scenes.uniform_scene(300_000, 7)
     cam = scenes.ring_cameras(16, 4.0, 1297, 840, 1100.0, cx=648.5, cy=420.0)[3]
-    assert _check_bitexact(sc, cam, 16) > 1_000_000
+    assert _check_bitexact(sc, cam, 16, footprint) > 1_000_000
 
 
 def test_keys_clustered_sh_1080p_full():
@@ -66,22 +68,24 @@ def test_keys_clustered_sh_1080p_full():
     _check_bitexact(sc, cam, 16)
 
 
+@pytest.mark.parametrize("footprint", [0, 1])
 @pytest.mark.parametrize("tile", [8, 32])
-def test_keys_clustered_tiles(tile):
+def test_keys_clustered_tiles(tile, footprint):
     sc = scenes.clustered_scene(200_000, 12)
     cam = scenes.pinhole((0.3, -0.1, -3.5), 1920, 1080, 1100.0)
-    _check_bitexact(sc, cam, tile)
+    _check_bitexact(sc, cam, tile, footprint)
 
 
+@pytest.mark.parametrize("footprint", [0, 1])
 @pytest.mark.parametrize("width,route", [(16384, "counting"), (16392, "radix")])
-def test_keys_both_routes(width, route):
+def test_keys_both_routes(width, route, footprint):
     # 2048 tiles across at tile 8 is the widest frame the counting sort takes;
     # one more tile column sends the entries through duplication + radix passes
     sc = scenes.clustered_scene(200_000, 14)
     cam = scenes.pinhole((0.0, 0.0, -3.0), width, 40, 2000.0)
     f = igs.Frame(sc.n, 1 << 16, igs.camera(cam), igs.opts(tile=8))
     assert (f.struct.sort_chunks > 0) == (route == "counting")
-    assert _check_bitexact(sc, cam, 8) > 10_000
+    assert _check_bitexact(sc, cam, 8, footprint) > 10_000
 
 
 @pytest.mark.parametrize("n", [1, 255, 257, 5000])
@@ -102,7 +106,8 @@ def test_keys_edge_cases():
     col = np.random.default_rng(0).uniform(size=(6, 3))
     sc = scene_from(means, sigma, opac, col)
     for tile in (8, 16, 32):
-        _check_bitexact(sc, cam, tile)
+        for footprint in (0, 1):
+            _check_bitexact(sc, cam, tile, footprint)
 
 
 def test_empty_and_all_culled():

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2403_14244_gb300 import scenes
+from paper_2403_14244_gb300 import igs, scenes
 from tests import _gpu
 from tests._tiny import random_small, scene_from
 
@@ -26,10 +26,11 @@ def _last_ids(f, vals_all, tile):
     return np.where(nc > 0, vals_all[np.clip(pos, 0, None)], -1)
 
 
+@pytest.mark.parametrize("footprint", [0, 1])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_forward_4k_matches_oracle(tile):
+def test_forward_4k_matches_oracle(tile, footprint):
     sc, cam = scenes.workload_forward_4k()
-    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile)
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile, footprint=footprint)
     ref = oracle.render(sc, cam, mode=1, flag_margin=MARGIN)
     _gpu.compare_images(img, ref["img"], ref["flag"])
     ok = ref["flag"] == 0
@@ -38,6 +39,20 @@ def test_forward_4k_matches_oracle(tile):
     keys, vals, ranges, info = _gpu.frame_keys(f)
     last = _last_ids(f, vals.astype(np.int64), tile)
     assert np.mean(last[ok] == ref["last"][ok]) == 1.0
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_footprints_give_the_same_image(tile):
+    """Footprint 1 leaves out only tiles the disc does not meet, where no pixel
+    reaches alpha_min: image and final transmittance are bit-identical, with
+    fewer entries."""
+    sc = scenes.clustered_scene(150_000, 23, sh_degree=3)
+    cam = scenes.pinhole((0.4, -0.2, -3.2), 1280, 720, 1100.0)
+    r0, f0, _, img0 = _gpu.run_forward(sc, cam, tile=tile, footprint=0)
+    r1, f1, _, img1 = _gpu.run_forward(sc, cam, tile=tile, footprint=1)
+    np.testing.assert_array_equal(img0, img1)
+    np.testing.assert_array_equal(f0.T_final().cpu().numpy(), f1.T_final().cpu().numpy())
+    assert igs.frame_status(f1)[1][0] < igs.frame_status(f0)[1][0]
 
 
 def test_tile_sizes_bit_identical():

@@ -35,10 +35,11 @@ def test_projection_close_to_fp64(tile):
     np.testing.assert_allclose(p["depth"], z, rtol=4e-7)
 
 
+@pytest.mark.parametrize("footprint", [0, 1])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_rect_is_minimal_cover(tile):
+def test_rect_is_minimal_cover(tile, footprint):
     sc, cam = random_small(400, 3, w=70, h=50, spread=1.2)
-    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile)
+    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile, footprint)
     tx_n, ty_n = -(-cam.width // tile), -(-cam.height // tile)
     kept = p["count"] > 0
     assert kept.sum() > 100
@@ -46,7 +47,11 @@ def test_rect_is_minimal_cover(tile):
         u, v, r = float(p["u"][i]), float(p["v"][i]), float(p["r"][i])
         x0, y0, x1, y1 = p["rect"][i]
         assert 0 <= x0 <= x1 < tx_n and 0 <= y0 <= y1 < ty_n
-        assert p["count"][i] == (x1 - x0 + 1) * (y1 - y0 + 1)
+        if footprint:
+            xa, xb = oracle.row_span(p["u"][i], p["v"][i], p["r"][i], np.arange(y0, y1 + 1), x0, x1, tile)
+            assert p["count"][i] == np.maximum(xb - xa + 1, 0).sum()
+        else:
+            assert p["count"][i] == (x1 - x0 + 1) * (y1 - y0 + 1)
         # the first and last tile of each axis hold the ends of [u-r, u+r] (resp. v), unless
         # the end lies off the grid and the rect is clamped; so the rect is the smallest
         # run of tiles covering the interval (allowing FP32 rounding of the ends)
@@ -62,12 +67,13 @@ def test_rect_is_minimal_cover(tile):
                 assert c + r >= hi_t * tile - eps
 
 
-def test_rect_holds_every_reachable_pixel():
+@pytest.mark.parametrize("footprint", [0, 1])
+def test_rect_holds_every_reachable_pixel(footprint):
     """Every pixel where a Gaussian has alpha >= 1/255 (FP64 render of the
-    Gaussian alone) lies in a tile of its rectangle; off-grid ones never reach one."""
+    Gaussian alone) lies in a tile it touches; off-grid ones never reach one."""
     sc, cam = random_small(60, 8, w=48, h=40, spread=1.0, smin=0.05, smax=0.3)
     for tile in (8, 16):
-        p = oracle.project(sc.means_sigma, sc.opacity, cam, tile)
+        p = oracle.project(sc.means_sigma, sc.opacity, cam, tile, footprint)
         for i in range(sc.n):
             one = scenes.Scene(sc.means_sigma[i:i + 1].copy(), sc.opacity[i:i + 1].copy(),
                                sc.color[i:i + 1].copy(), -1)
@@ -79,6 +85,42 @@ def test_rect_holds_every_reachable_pixel():
             x0, y0, x1, y1 = p["rect"][i]
             assert np.all((xs // tile >= x0) & (xs // tile <= x1))
             assert np.all((ys // tile >= y0) & (ys // tile <= y1))
+            # and in the touched tiles of its row
+            xa, xb = oracle.row_span(np.full(len(ys), p["u"][i]), np.full(len(ys), p["v"][i]),
+                                     np.full(len(ys), p["r"][i]), ys // tile, x0, x1, tile)
+            assert np.all((xs // tile >= xa) & (xs // tile <= xb))
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_row_spans_are_the_tiles_the_disc_meets(tile):
+    """Within the rectangle, a tile is in its row's span exactly when the disc
+    of radius r meets the tile's square (FP64 distance from the centre to the
+    square), up to a 1e-5 relative band for the FP32 roundings."""
+    sc, cam = random_small(300, 21, w=150, h=110, spread=1.1, smin=0.05, smax=0.4)
+    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile, footprint=1)
+    kept = np.nonzero(p["count"] > 0)[0]
+    assert len(kept) > 100
+    inside = outside = 0
+    for i in kept:
+        u, v, r = (float(p[k][i]) for k in ("u", "v", "r"))
+        x0, y0, x1, y1 = p["rect"][i]
+        rows = np.arange(y0, y1 + 1)
+        xa, xb = oracle.row_span(np.full(len(rows), p["u"][i]), np.full(len(rows), p["v"][i]),
+                                 np.full(len(rows), p["r"][i]), rows, x0, x1, tile)
+        total = 0
+        for ty, a, b in zip(rows, xa, xb):
+            tx = np.arange(x0, x1 + 1)
+            dx = np.maximum(0.0, np.maximum(tx * tile - u, u - (tx + 1) * tile))
+            dy = max(0.0, ty * tile - v, v - (ty + 1) * tile)
+            d = np.hypot(dx, dy)
+            span = (tx >= a) & (tx <= b)
+            assert np.all(span[d < r * (1 - 1e-5)]), (i, ty)
+            assert not np.any(span[d > r * (1 + 1e-5)]), (i, ty)
+            inside += int(span.sum())
+            outside += int((~span).sum())
+            total += int(span.sum())
+        assert total == p["count"][i]
+    assert outside > 0                      # the corner tiles of larger discs are left out
 
 
 def test_radius_bounds_the_cutoff_tightly():
@@ -103,10 +145,11 @@ def test_radius_bounds_the_cutoff_tightly():
     assert r1[1] < 0.7 * r1[0]
 
 
+@pytest.mark.parametrize("footprint", [0, 1])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_keys_match_library_stable_sort(tile):
+def test_keys_match_library_stable_sort(tile, footprint):
     sc, cam = random_small(500, 4, w=90, h=60, spread=1.0)
-    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile)
+    p = oracle.project(sc.means_sigma, sc.opacity, cam, tile, footprint)
     k, v, r = oracle.keys(p, cam, tile)
     tx_n = -(-cam.width // tile)
     gen_k, gen_v = [], []
@@ -116,7 +159,8 @@ def test_keys_match_library_stable_sort(tile):
         x0, y0, x1, y1 = p["rect"][i]
         zb = int(np.float32(p["depth"][i]).view(np.uint32))
         for ty in range(y0, y1 + 1):
-            for tx in range(x0, x1 + 1):
+            xa, xb = oracle.row_span(p["u"][i], p["v"][i], p["r"][i], ty, x0, x1, tile) if footprint else ([x0], [x1])
+            for tx in range(int(xa[0]), int(xb[0]) + 1):
                 gen_k.append(((ty * tx_n + tx) << 32) | zb)
                 gen_v.append(i)
     gen_k = np.array(gen_k, np.uint64)
