@@ -13,7 +13,8 @@ taken where the paper is silent are listed at the top of ``igs_oracle.c``.
 
 Parity pins: every function here is checked by the ``-m "not gpu"`` tests
 against closed forms, brute force, invariants, finite differences, scipy's
-spherical harmonics and torch's Adam / L1 (see tests/test_oracle_*.py).
+spherical harmonics and Gaussian filter, and torch's Adam / L1 / conv2d autograd
+(see tests/test_oracle_*.py).
 """
 
 from __future__ import annotations
@@ -83,6 +84,8 @@ def _load():
             lib.orc_l1.argtypes = [i64, P, P, P]
             lib.orc_l1.restype = C.c_double
             lib.orc_adam.argtypes = [i64, P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double, i64]
+            lib.orc_l1_ssim.argtypes = [i64, i64, i64, P, P, C.c_double, P, P, P]
+            lib.orc_l1_ssim.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -267,6 +270,27 @@ def l1(img, target):
     grad = np.zeros(im.shape)
     loss = _load().orc_l1(im.size, _ptr(im), _ptr(tg), _ptr(grad))
     return float(loss), grad
+
+
+def l1_ssim(img, target, lam=0.2, grad=True, ssim_map=False):
+    """The loss of Sec. 3 with its structural term: (1 - lam) mean |img - target|
+    + lam (1 - SSIM), SSIM with the 11 x 11 Gaussian window (std 1.5, zero
+    outside the image), C1 = 0.01^2, C2 = 0.03^2, per channel of planar
+    [channels][height][width] images (a 2-D image is one channel). FP64.
+    Returns (loss, ssim, dL/dimg or None), plus the per-entry SSIM if ssim_map."""
+    im = np.array(img, np.float64, copy=True)
+    tg = np.array(target, np.float64, copy=True)
+    if im.shape != tg.shape or im.ndim not in (2, 3):
+        raise ValueError("img and target: equal [C][H][W] or [H][W] shapes")
+    shp = im.shape if im.ndim == 3 else (1,) + im.shape
+    g = np.zeros(im.shape) if grad else None
+    ssim = np.zeros(1)
+    smap = np.zeros(im.shape) if ssim_map else None
+    loss = _load().orc_l1_ssim(shp[0], shp[1], shp[2], _ptr(im), _ptr(tg), float(lam), _ptr(ssim),
+                               _ptr(smap) if ssim_map else None, _ptr(g) if grad else None)
+    if ssim_map:
+        return float(loss), float(ssim[0]), g, smap
+    return float(loss), float(ssim[0]), g
 
 
 def adam(p, grad, m, v, *, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, t=1):

@@ -25,6 +25,8 @@
  *     and the projection
  *   - colour as real spherical harmonics up to degree 3 (the particle property
  *     A_k of Sec. 3, view dependent)
+ *   - the training loss of Sec. 3, (1 - lambda) L1 + lambda (1 - SSIM), and its
+ *     gradient w.r.t. the rendered image
  *
  * Two arithmetics:
  *   - the key path (culling, tile rectangle, depth key) is canonical FP32 with
@@ -733,6 +735,117 @@ double orc_l1(int64_t count, const double* img, const float* target, double* gra
         if (grad) grad[i] = (d > 0) ? 1.0 / (double)count : (d < 0 ? -1.0 / (double)count : 0.0);
     }
     return acc / (double)count;
+}
+
+/* The loss of Sec. 3 with its structural term, L = (1 - lambda) |f - f^|_1 +
+ * lambda (1 - SSIM(f, f^)) (the paper prints "+ lambda SSIM"; a loss has to
+ * fall as the images grow alike, so the term is read as 1 - SSIM). The L1 part
+ * is the mean absolute difference over all channels x height x width entries.
+ * SSIM (the paper gives no definition; read as the structural similarity index
+ * of Wang et al.): per channel and pixel q,
+ *   S_q = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sxx + syy + C2)),
+ * with mx, my, E[x^2], E[y^2], E[xy] the window means around q, sxx = E[x^2] -
+ * mx^2, syy = E[y^2] - my^2, sxy = E[xy] - mx my; the window is the 11 x 11
+ * Gaussian of standard deviation 1.5 pixels, normalised to sum 1, with zero
+ * values outside the image (the "same"-size, zero-padded convention);
+ * C1 = 0.01^2, C2 = 0.03^2 (dynamic range 1). SSIM is the mean of S over all
+ * entries. Images are planar [channels][height][width].
+ *
+ * Gradient w.r.t. img (FP64, analytic): with A_q = dS_q/dmx, B_q = dS_q/dE[x^2],
+ * Cq = dS_q/dE[xy] (holding the other window means), and w the window,
+ *   dSSIM/dx_p = (1/count) sum_q w(q - p) (A_q + 2 x_p B_q + y_p C_q),
+ * the sum over pixels q of the image within 5 of p in both axes.
+ * Returns L; *ssim_out = SSIM (if not NULL); smap (if not NULL) = S per entry;
+ * grad (if not NULL) = dL/dimg. */
+static void ssim_window2d(double w[11][11]) {
+    double sum = 0.0;
+    for (int a = 0; a < 11; ++a)
+        for (int b = 0; b < 11; ++b) {
+            double da = a - 5, db = b - 5;
+            w[a][b] = exp(-(da * da + db * db) / (2.0 * 1.5 * 1.5));
+            sum += w[a][b];
+        }
+    for (int a = 0; a < 11; ++a)
+        for (int b = 0; b < 11; ++b) w[a][b] /= sum;
+}
+
+double orc_l1_ssim(int64_t channels, int64_t height, int64_t width, const double* img, const double* target,
+                   double lambda, double* ssim_out, double* smap, double* grad) {
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    const int64_t plane = height * width, count = channels * plane;
+    double w[11][11];
+    ssim_window2d(w);
+    double* dA = (double*)calloc((size_t)count * 3 + 1, sizeof(double));
+    double* dB = dA + count;
+    double* dC = dB + count;
+    double s_sum = 0.0, l1_sum = 0.0;
+    for (int64_t c = 0; c < channels; ++c) {
+        const double* x = img + c * plane;
+        const double* y = target + c * plane;
+#pragma omp parallel for reduction(+ : s_sum) schedule(static)
+        for (int64_t i = 0; i < height; ++i)
+            for (int64_t j = 0; j < width; ++j) {
+                double mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+                for (int a = 0; a < 11; ++a) {
+                    int64_t ii = i + a - 5;
+                    if (ii < 0 || ii >= height) continue;
+                    for (int b = 0; b < 11; ++b) {
+                        int64_t jj = j + b - 5;
+                        if (jj < 0 || jj >= width) continue;
+                        double xv = x[ii * width + jj], yv = y[ii * width + jj], wv = w[a][b];
+                        mx += wv * xv;
+                        my += wv * yv;
+                        exx += wv * xv * xv;
+                        eyy += wv * yv * yv;
+                        exy += wv * xv * yv;
+                    }
+                }
+                double sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+                double n1 = 2 * mx * my + C1, n2 = 2 * sxy + C2;
+                double d1 = mx * mx + my * my + C1, d2 = sxx + syy + C2;
+                double S = (n1 * n2) / (d1 * d2);
+                s_sum += S;
+                int64_t q = c * plane + i * width + j;
+                if (smap) smap[q] = S;
+                /* dS/dmx: n1' = 2 my, n2' = -2 my, d1' = 2 mx, d2' = -2 mx */
+                dA[q] = (2 * my * n2 - 2 * my * n1) / (d1 * d2) - S * (2 * mx / d1 - 2 * mx / d2);
+                dB[q] = -S / d2;
+                dC[q] = 2 * n1 / (d1 * d2);
+            }
+    }
+    for (int64_t q = 0; q < count; ++q) l1_sum += fabs(img[q] - target[q]);
+    if (grad) {
+        for (int64_t c = 0; c < channels; ++c) {
+            const double* x = img + c * plane;
+            const double* y = target + c * plane;
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < height; ++i)
+                for (int64_t j = 0; j < width; ++j) {
+                    double fa = 0, fb = 0, fc = 0;
+                    for (int a = 0; a < 11; ++a) {
+                        int64_t ii = i + (a - 5);   /* q = p + (a - 5, b - 5), weight w(q - p) */
+                        if (ii < 0 || ii >= height) continue;
+                        for (int b = 0; b < 11; ++b) {
+                            int64_t jj = j + (b - 5);
+                            if (jj < 0 || jj >= width) continue;
+                            int64_t q = c * plane + ii * width + jj;
+                            fa += w[a][b] * dA[q];
+                            fb += w[a][b] * dB[q];
+                            fc += w[a][b] * dC[q];
+                        }
+                    }
+                    int64_t p = i * width + j;
+                    double d = x[p] - y[p];
+                    double g1 = d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0);
+                    double gs = fa + 2 * x[p] * fb + y[p] * fc;
+                    grad[c * plane + p] = ((1.0 - lambda) * g1 - lambda * gs) / (double)count;
+                }
+        }
+    }
+    free(dA);
+    double ssim = s_sum / (double)count;
+    if (ssim_out) *ssim_out = ssim;
+    return (1.0 - lambda) * l1_sum / (double)count + lambda * (1.0 - ssim);
 }
 
 /* Adam with bias correction (step t >= 1), FP64, in place on p, m, v. */
