@@ -31,7 +31,8 @@ if ROOT not in sys.path:
 
 METRIC = "1080p frames/s & fwd+bwd steps/s at 3M isotropic Gaussians; serve p50/p99 ms"
 WORKLOAD = "train_step_3M_sh3_1297x840_ring16"
-STAGES = ("project", "bin_sort", "blend_fwd", "l1", "blend_bwd", "project_bwd_adam")
+STAGES_L1 = ("project", "bin_sort", "blend_fwd", "l1", "blend_bwd", "project_bwd_adam")
+STAGES_SSIM = ("project", "bin_sort", "blend_fwd", "l1_ssim", "blend_bwd", "project_bwd_adam")
 
 
 def parse():
@@ -46,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--footprint", type=int, default=0, choices=(0, 1),
                     help="tiles of a Gaussian: 0 its bounding rectangle, 1 the tiles its disc meets")
+    ap.add_argument("--ssim", type=float, default=0.0,
+                    help="lambda of the loss (1 - lambda) L1 + lambda (1 - SSIM) in the timed step (0: L1)")
     return ap.parse_args()
 
 
@@ -80,6 +83,8 @@ def stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm):
         # per entry: id + 32-byte record; per pixel: image, T_final, n_contrib
         "blend_fwd": ("alu", M * (4 + 32) + P * (12 + 4 + 4)),
         "l1": ("hbm", P * 3 * 4 * 3),
+        # per entry: img, target in and three partial maps out; maps, img, target in and gradient out
+        "l1_ssim": ("hbm", P * 3 * 44),
         # per entry: id + record; per pixel: dL, T_final, n_contrib; per Gaussian: 2D gradient
         "blend_bwd": ("alu", M * (4 + 32) + P * (12 + 4 + 4) + n * 32),
         # read params, 2D gradient, count, m, v; write params, m, v
@@ -228,6 +233,8 @@ def run_mine(args, world, rank, local):
         dist.init_process_group("nccl")
     igs.load()
     sc, cams, cam_s, ts, targets, targets_host, np = build_workload(args.n, dev, args.footprint)
+    ts.ssim_lambda = args.ssim
+    STAGES = STAGES_L1 if args.ssim == 0 else STAGES_SSIM
     V = len(cams)
     stream = torch.cuda.current_stream(dev)
     # capacity calibration: every view once with a status check (untimed set-up)
@@ -322,8 +329,11 @@ def run_mine(args, world, rank, local):
     dominant = max(stages, key=lambda r: r["ms"])
 
     extra = {}
+    if not args.no_extra and args.ssim == 0:
+        extra["train_step_l1_ssim"] = run_ssim_steps(ts, cam_s, targets, stream, dev, min(args.steps, 100),
+                                                     peak_hbm)
     if not args.no_extra:
-        extra = run_extra(dev, np)
+        extra.update(run_extra(dev, np))
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -332,6 +342,7 @@ def run_mine(args, world, rank, local):
         "config": {"workload": WORKLOAD, "n_gaussians": n, "sh_degree": 3, "image": [cams[0].width, cams[0].height],
                    "views": V, "tile": 16, "footprint": "rectangle" if args.footprint == 0 else "disc rows",
                    "optimizer": "adam lr 1e-3", "params": "mu, log sigma, logit o, SH",
+                   "loss": "l1" if args.ssim == 0 else f"(1 - {args.ssim}) l1 + {args.ssim} (1 - ssim)",
                    "l2": "no flush: per-step working set 2.5 GB > 129 MB L2",
                    "parallelism": f"replicas x{world} (no collective)"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
@@ -341,12 +352,51 @@ def run_mine(args, world, rank, local):
         "stages": stages, "entries_mean": round(M), "binning_vs_keysort": keysort, "extra": extra,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_budget)
+        result["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_budget, args.ssim)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_ssim_steps(ts, cam_s, targets, stream, dev, steps, peak_hbm, lam=0.2):
+    """The same training step with the paper's loss (1 - lam) L1 + lam (1 - SSIM)
+    in place of L1: steps/s, stage times, and the loss kernels' bandwidth over
+    their algorithmic bytes (per image entry: img, target read and three partial
+    maps written by the forward kernel; the maps, img and target read and the
+    gradient written by the backward kernel: 44 bytes)."""
+    import torch
+
+    stages = ("project", "bin_sort", "blend_fwd", "l1_ssim", "blend_bwd", "project_bwd_adam")
+    V = len(cam_s)
+    ts.ssim_lambda = lam
+    try:
+        for k in range(3):
+            ts.step(cam_s[k % V], targets[k % V])
+        torch.cuda.synchronize(dev)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stage_ev = []
+        start.record(stream)
+        for k in range(steps):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+            evs[0].record(stream)
+            it = iter(evs[1:])
+            ts.step(cam_s[k % V], targets[k % V], marks=lambda name, it=it: next(it).record(stream))
+            stage_ev.append(evs)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    finally:
+        ts.ssim_lambda = 0.0
+    ms = start.elapsed_time(end) / steps
+    stage_ms = {s: sum(e[i].elapsed_time(e[i + 1]) for e in stage_ev) / steps for i, s in enumerate(stages)}
+    entries = targets[0].numel()
+    nbytes = 44 * entries
+    gbs = nbytes / (stage_ms["l1_ssim"] / 1e3) / 1e9
+    return {"lambda": lam, "steps": steps, "steps_per_s": round(1e3 / ms, 3), "ms_per_step": round(ms, 4),
+            "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
+            "l1_ssim_roofline": {"bound": "hbm", "bytes": nbytes, "achieved": round(gbs, 1), "peak": peak_hbm,
+                                 "unit": "GB/s", "frac": round(gbs / peak_hbm, 4)}}
 
 
 def run_extra(dev, np):
@@ -542,9 +592,10 @@ def run_serving(dev, n_req=2000, warm=200, rate=200.0, budget=8 << 30, seed=5, t
 
 # ------------------------------------------------------------ CPU oracle ----
 
-def oracle_step(sc, cam, target, band=None, param_frac=1.0):
+def oracle_step(sc, cam, target, band=None, param_frac=1.0, lam=0.0):
     """One training step of the CPU oracle: FP64 forward + adjoint (row-list
-    mode, all host cores), L1 loss, Adam over a fraction of the parameters.
+    mode, all host cores), L1 loss (or (1 - lam) L1 + lam (1 - SSIM)), Adam
+    over a fraction of the parameters.
     band = (y0, h) renders only rows [y0, y0 + h) of the view."""
     import numpy as np
 
@@ -557,7 +608,10 @@ def oracle_step(sc, cam, target, band=None, param_frac=1.0):
                             height=h, znear=cam.znear)
         target = np.ascontiguousarray(target[:, y0:y0 + h])
     fwd = oracle.render(sc, cam, mode=1)
-    loss, G = oracle.l1(fwd["img"], target)
+    if lam > 0:
+        loss, _, G = oracle.l1_ssim(fwd["img"], target, lam=lam)
+    else:
+        loss, G = oracle.l1(fwd["img"], target)
     g = oracle.backward(sc, cam, G, mode=1)
     flat_g = np.concatenate([np.concatenate([g["d_means"], g["d_sigma"][:, None]], 1).reshape(-1), g["d_opac"],
                              g["d_color"].reshape(-1)])
@@ -567,7 +621,7 @@ def oracle_step(sc, cam, target, band=None, param_frac=1.0):
     return loss
 
 
-def cpu_baseline(sc, cams, budget_s):
+def cpu_baseline(sc, cams, budget_s, lam=0.0):
     import oracle
     from paper_2403_14244_gb300 import scenes
 
@@ -575,14 +629,15 @@ def cpu_baseline(sc, cams, budget_s):
     t0 = time.perf_counter()
     steps = 0
     while True:
-        oracle_step(sc, cams[steps % len(cams)], scenes.train_target(steps % len(cams)))
+        oracle_step(sc, cams[steps % len(cams)], scenes.train_target(steps % len(cams)), lam=lam)
         steps += 1
         if time.perf_counter() - t0 >= budget_s or steps >= 8:
             break
     dt = time.perf_counter() - t0
     return {"value": round(steps / dt, 5), "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{steps} full training step(s) of the same workload (views 0..{steps - 1}): FP64 forward + "
-                      f"adjoint over all 1297x840 pixels, L1, Adam over all 53 x 3M parameters; {dt:.1f} s",
+                      f"adjoint over all 1297x840 pixels, {'L1' if lam == 0 else 'L1 + SSIM'}, Adam over all "
+                      f"53 x 3M parameters; {dt:.1f} s",
             "cpu": _cpu_model()}
 
 

@@ -245,6 +245,30 @@ IGS_API igs_status igs_project_bwd_adam(const igs_scene* scene, const igs_camera
 IGS_API igs_status igs_l1_loss(const float* img, const float* target, int64_t count, float* loss,
                        float* dL_dimg, void* stream);
 
+/* Bytes of device scratch igs_l1_ssim_loss needs for planar [channels][height]
+ * [width] images (three FP32 maps of that size); 0 for an empty or invalid size. */
+IGS_API size_t igs_ssim_work_bytes(int32_t channels, int32_t height, int32_t width);
+
+/* The loss of Sec. 3 with its structural term,
+ *   loss = (1 - lambda) mean |img - target| + lambda (1 - SSIM(img, target)),
+ * (the paper prints "+ lambda SSIM"; as a loss it is read as 1 - SSIM;
+ * lambda = 0.2 in the paper). SSIM is the mean over all entries of Wang et al.'s
+ * index, per channel, with the 11 x 11 Gaussian window of standard deviation
+ * 1.5 (normalised to sum 1; zero values outside the image), C1 = 0.01^2,
+ * C2 = 0.03^2 (dynamic range 1).
+ * img, target: device FP32, planar [channels][height][width]. *loss (device
+ * float) is overwritten; *ssim (device float, may be NULL) receives the mean
+ * SSIM; dL_dimg (device, same layout) receives dloss/dimg, with
+ * sign(0) = 0 in the L1 part. work: device scratch of igs_ssim_work_bytes bytes,
+ * 16-byte aligned, caller-owned, overwritten. Asynchronous on `stream`.
+ * Errors: NULL buffers, channels outside 1..65535, height or width < 1, lambda
+ * outside [0, 1], work not 16-byte aligned -> IGS_ERR_INVALID_ARG; launch failures -> IGS_ERR_CUDA.
+ * loss and ssim are sums of per-tile partials added in arbitrary order (not
+ * bit-reproducible); dL_dimg is deterministic. */
+IGS_API igs_status igs_l1_ssim_loss(const float* img, const float* target, int32_t channels, int32_t height,
+                                    int32_t width, float lambda, float* loss, float* ssim, float* dL_dimg,
+                                    void* work, void* stream);
+
 /* One bias-corrected Adam step (step >= 1) in place on p, m, v (device,
  * count FP32 each), from gradient g. The host scalars are double so that 1 - b1,
  * 1 - b2 and the bias corrections are formed exactly before rounding to FP32:

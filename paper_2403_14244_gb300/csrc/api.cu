@@ -325,6 +325,25 @@ igs_status igs_l1_loss(const float* img, const float* target, int64_t count, flo
     return cuda_status(igs::launch_l1(img, target, count, loss, dL_dimg, (cudaStream_t)stream), "igs_l1_loss");
 }
 
+size_t igs_ssim_work_bytes(int32_t channels, int32_t height, int32_t width) {
+    if (channels < 1 || height < 1 || width < 1) return 0;
+    return igs::ssim_work_floats(channels, height, width) * sizeof(float);
+}
+
+igs_status igs_l1_ssim_loss(const float* img, const float* target, int32_t channels, int32_t height, int32_t width,
+                            float lambda, float* loss, float* ssim, float* dL_dimg, void* work, void* stream) {
+    if (!img || !target || !loss || !dL_dimg || !work) return fail(IGS_ERR_INVALID_ARG, "l1_ssim: NULL buffer");
+    if (channels < 1 || channels > 65535 || height < 1 || width < 1)
+        return fail(IGS_ERR_INVALID_ARG, "l1_ssim: channels must be 1..65535, height and width positive");
+    if ((int64_t)channels * height * width >= ((int64_t)1 << 40))
+        return fail(IGS_ERR_INVALID_ARG, "l1_ssim: image too large");
+    if (!(lambda >= 0.f && lambda <= 1.f)) return fail(IGS_ERR_INVALID_ARG, "l1_ssim: lambda must be in [0, 1]");
+    if (reinterpret_cast<uintptr_t>(work) & 15) return fail(IGS_ERR_INVALID_ARG, "l1_ssim: work not 16-byte aligned");
+    return cuda_status(igs::launch_l1_ssim(img, target, channels, height, width, lambda, loss, ssim, dL_dimg,
+                                           static_cast<float*>(work), (cudaStream_t)stream),
+                       "igs_l1_ssim_loss");
+}
+
 igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_t count, double lr, double b1, double b2,
                     double eps, int64_t step, void* stream) {
     if (!p || !g || !m || !v || count < 0) return fail(IGS_ERR_INVALID_ARG, "bad adam arguments");

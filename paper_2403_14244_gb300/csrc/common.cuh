@@ -151,6 +151,10 @@ cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const fl
                              cudaStream_t s);
 cudaError_t launch_l1(const float* img, const float* target, int64_t count, float* loss, float* grad,
                       cudaStream_t s);
+// (1 - lambda) L1 + lambda (1 - SSIM) and its image gradient (ssim.cu); work holds ssim_work_floats floats.
+size_t ssim_work_floats(int channels, int height, int width);
+cudaError_t launch_l1_ssim(const float* img, const float* target, int channels, int height, int width, float lambda,
+                           float* loss, float* ssim, float* grad, float* work, cudaStream_t s);
 // Adam constants, formed in double on the host and rounded once.
 struct AdamParams {
     float b1, b2, omb1, omb2;  // beta1, beta2, 1 - beta1, 1 - beta2

@@ -6,7 +6,7 @@ stream, and raises on any non-OK status. There is no CPU fallback: if the
 library is missing or no GPU is present, the calls raise.
 
 Functions keep the C names without the ``igs_`` prefix: ``project``,
-``bin_sort``, ``render_fwd``, ``render_bwd``, ``l1_loss``, ``adam``,
+``bin_sort``, ``render_fwd``, ``render_bwd``, ``l1_loss``, ``l1_ssim_loss``, ``adam``,
 ``export_keys``, ``frame_status``. ``Frame`` owns one view's workspace.
 """
 from __future__ import annotations
@@ -101,6 +101,9 @@ SYMBOLS = {
                                        C.POINTER(IgsFrame), C.c_void_p] + [C.c_void_p] * 6 +
                              [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "igs_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "igs_ssim_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+    "igs_l1_ssim_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double,
                            C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "igs_frame_status": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_uint32), C.c_void_p]),
@@ -334,6 +337,25 @@ def project_bwd_adam(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d
 def l1_loss(img, target, loss, dL_dimg, stream=None):
     _check(load().igs_l1_loss(_ptr(img), _ptr(target), int(img.numel()), _ptr(loss), _ptr(dL_dimg),
                               _stream(stream)), "igs_l1_loss")
+
+
+def ssim_work_bytes(channels, height, width):
+    return int(load().igs_ssim_work_bytes(int(channels), int(height), int(width)))
+
+
+def l1_ssim_loss(img, target, lam, loss, dL_dimg, work, ssim=None, stream=None):
+    """(1 - lam) L1 + lam (1 - SSIM) of planar [C][H][W] (or [H][W]) images into
+    loss (device float) and dL_dimg; ssim (device float) optional; work: a device
+    buffer of at least ssim_work_bytes bytes."""
+    shp = tuple(img.shape) if img.dim() == 3 else (1,) + tuple(img.shape)
+    if tuple(target.shape) != tuple(img.shape) or tuple(dL_dimg.shape) != tuple(img.shape) or len(shp) != 3:
+        raise ValueError("img, target and dL_dimg must share a [C][H][W] or [H][W] shape")
+    need = ssim_work_bytes(*shp)
+    if work.numel() * work.element_size() < need:
+        raise ValueError(f"work holds {work.numel() * work.element_size()} bytes, needs {need}")
+    _check(load().igs_l1_ssim_loss(_ptr(img), _ptr(target), shp[0], shp[1], shp[2], float(lam), _ptr(loss),
+                                   _ptr(ssim) if ssim is not None else None, _ptr(dL_dimg), _ptr(work),
+                                   _stream(stream)), "igs_l1_ssim_loss")
 
 
 def adam(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):

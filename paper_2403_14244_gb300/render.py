@@ -113,13 +113,15 @@ class TrainStep:
     views, each segment starting on a 256-byte boundary, and the Adam moments m, v
     in flat buffers of the same layout.
 
-    step(cam, target) runs forward, L1, backward and Adam on the GPU. By default
-    the projection backward and Adam run as one fused kernel and the gradient is
-    never written; fused=False writes the gradient to `grad` and applies igs_adam
-    over the flat buffer (same update)."""
+    step(cam, target) runs forward, loss, backward and Adam on the GPU. The loss
+    is L1 (ssim_lambda = 0) or the paper's (1 - lambda) L1 + lambda (1 - SSIM)
+    (ssim_lambda = lambda, 0.2 in the paper). By default the projection backward
+    and Adam run as one fused kernel and the gradient is never written;
+    fused=False writes the gradient to `grad` and applies igs_adam over the flat
+    buffer (same update)."""
 
     def __init__(self, means_sigma, opacity, color, sh_degree, tile=16, lr=1e-3, device="cuda", fused=True,
-                 footprint=0):
+                 footprint=0, ssim_lambda=0.0):
         n = means_sigma.shape[0]
         C = color.shape[1]
         self.n, self.C = n, C
@@ -142,6 +144,10 @@ class TrainStep:
         self.renderer = Renderer(tile=tile, sh_degree=sh_degree, param_mode=1, device=device, footprint=footprint)
         self.g2d = torch.empty((n, 8), dtype=torch.float32, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        if not 0.0 <= ssim_lambda <= 1.0:
+            raise ValueError("ssim_lambda must be in [0, 1]")
+        self.ssim_lambda = float(ssim_lambda)
+        self._work = {}
         self.lr = lr
         self.fused = fused
         self.t = 0
@@ -174,8 +180,15 @@ class TrainStep:
             mark("bin_sort")
             igs.render_fwd(frame, r.opts, img, stream)
         mark("blend_fwd")
-        igs.l1_loss(img, target, self.loss, dimg, stream)
-        mark("l1")
+        if self.ssim_lambda > 0.0:
+            if key not in self._work:
+                self._work[key] = torch.empty(igs.ssim_work_bytes(3, c.height, c.width) // 4, dtype=torch.float32,
+                                              device=self.flat.device)
+            igs.l1_ssim_loss(img, target, self.ssim_lambda, self.loss, dimg, self._work[key], stream=stream)
+            mark("l1_ssim")
+        else:
+            igs.l1_loss(img, target, self.loss, dimg, stream)
+            mark("l1")
         igs.blend_bwd(frame, r.opts, dimg, self.g2d, stream)
         mark("blend_bwd")
         self.t += 1
