@@ -86,6 +86,10 @@ def _load():
             lib.orc_adam.argtypes = [i64, P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double, i64]
             lib.orc_l1_ssim.argtypes = [i64, i64, i64, P, P, C.c_double, P, P, P]
             lib.orc_l1_ssim.restype = C.c_double
+            lib.orc_fit2d_render.argtypes = [i64, P, C.c_float, C.c_int32, C.c_int32, P]
+            lib.orc_fit2d_backward.argtypes = [i64, P, C.c_float, C.c_int32, C.c_int32, P, P]
+            lib.orc_quadtree_init.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P]
+            lib.orc_quadtree_init.restype = i64
             _lib = lib
     return _lib
 
@@ -301,3 +305,42 @@ def adam(p, grad, m, v, *, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, t=1):
     g = np.ascontiguousarray(grad, np.float64)
     _load().orc_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), lr, b1, b2, eps, int(t))
     return p, m, v
+
+
+# ------------------------------------------------- 2D additive fitting ----
+
+def fit2d_render(params, D, width, height):
+    """The paper's 2D model (Sec. 3): f^(x) = sum over particles with
+    |mu_k - x| < D of A_k exp(-|x - mu_k|^2 / (2 sigma_k^2)), the support test in
+    canonical FP32, values in FP64. params [K][8] = (mu_x, mu_y, log sigma,
+    A_r, A_g, A_b, 0, 0). Returns [3][H][W] float64."""
+    p = _c32(params).reshape(-1, 8)
+    img = np.zeros((3, height, width))
+    _load().orc_fit2d_render(p.shape[0], _ptr(p), float(D), int(width), int(height), _ptr(img))
+    return img
+
+
+def fit2d_backward(params, D, G):
+    """Gradient w.r.t. the particles ([K][8], FP64) of a loss whose image
+    gradient is G ([3][H][W])."""
+    p = _c32(params).reshape(-1, 8)
+    g = np.ascontiguousarray(G, np.float64)
+    out = np.zeros((p.shape[0], 8))
+    _load().orc_fit2d_backward(p.shape[0], _ptr(p), float(D), int(g.shape[2]), int(g.shape[1]), _ptr(g), _ptr(out))
+    return out
+
+
+def quadtree_init(img, k_max, min_cell):
+    """QuadTree initialisation (Sec. 3.1) of a square power-of-two RGB image
+    ([3][S][S], S <= 512): one particle per leaf at the cell centre, A = the
+    cell's mean colour, sigma = half the cell width; the leaf with the largest
+    squared error is split while the leaves stay <= k_max and the children are
+    >= min_cell wide. Returns [L][8] float32."""
+    im = _c32(img)
+    if im.ndim != 3 or im.shape[0] != 3 or im.shape[1] != im.shape[2]:
+        raise ValueError("img must be [3][S][S]")
+    out = np.zeros((max(k_max, 1), 8), np.float32)
+    n = _load().orc_quadtree_init(_ptr(im), im.shape[1], int(k_max), int(min_cell), _ptr(out))
+    if n < 0:
+        raise ValueError("side must be a power of two <= 512, k_max and min_cell >= 1")
+    return out[:n].copy()

@@ -27,6 +27,9 @@
  *     A_k of Sec. 3, view dependent)
  *   - the training loss of Sec. 3, (1 - lambda) L1 + lambda (1 - SSIM), and its
  *     gradient w.r.t. the rendered image
+ *   - the paper's 2D experiment (Sec. 3): the additive image model
+ *     f^ = sum A_k g(x - mu_k, sigma_k) over particles within the support D,
+ *     its gradient, and the QuadTree initialisation of Sec. 3.1
  *
  * Two arithmetics:
  *   - the key path (culling, tile rectangle, depth key) is canonical FP32 with
@@ -858,4 +861,192 @@ void orc_adam(int64_t count, double* p, const double* grad, double* m, double* v
         double mh = m[i] / c1, vh = v[i] / c2;
         p[i] -= lr * mh / (sqrt(vh) + eps);
     }
+}
+
+/* ---------------------------------------------------------------------------
+ * The paper's 2D experiment (Sec. 3): an image as a sum of isotropic kernels,
+ *   f^(x) = sum over k with |tau_k - x| < D of A_k g(x - mu_k, sigma_k),
+ * with tau_k read as the particle centre mu_k and g = exp(-d^2 / (2 sigma^2))
+ * (Eq. 8 with the normalisation of reading 1). A particle is 8 floats:
+ * (mu_x, mu_y, log sigma, A_r, A_g, A_b, 0, 0) in pixel units (x right, y down);
+ * pixel (x, y) samples at (x + 0.5, y + 0.5). Images are planar [3][H][W].
+ *
+ * The support test is canonical FP32 with one rounding per step, so that both
+ * implementations take the same decision: dx = px - mu_x, dy = py - mu_y,
+ * d2 = dx*dx + dy*dy, reached iff d2 < D*D. Values and gradients are FP64 on
+ * the FP32 parameters.
+ * ------------------------------------------------------------------------- */
+static int fit_reach(float px, float py, const float* p, float D2) {
+    float dx = px - p[0];
+    float dy = py - p[1];
+    float a = dx * dx;
+    float b = dy * dy;
+    float d2 = a + b;
+    return d2 < D2;
+}
+
+void orc_fit2d_render(int64_t k, const float* params, float D, int32_t width, int32_t height, double* img) {
+    const float D2 = D * D;
+    const int64_t plane = (int64_t)width * height;
+#pragma omp parallel for schedule(static)
+    for (int32_t y = 0; y < height; ++y)
+        for (int32_t x = 0; x < width; ++x) {
+            const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (int64_t i = 0; i < k; ++i) {
+                const float* p = params + 8 * i;
+                if (!fit_reach(px, py, p, D2)) continue;
+                double dx = (double)px - p[0], dy = (double)py - p[1], s = exp((double)p[2]);
+                double g = exp(-(dx * dx + dy * dy) / (2.0 * s * s));
+                for (int c = 0; c < 3; ++c) acc[c] += (double)p[3 + c] * g;
+            }
+            for (int c = 0; c < 3; ++c) img[c * plane + (int64_t)y * width + x] = acc[c];
+        }
+}
+
+/* Gradient of a loss with image gradient G ([3][H][W]) w.r.t. every particle
+ * (grad [k][8], overwritten; the last two slots are 0), the set of reached
+ * pixels held fixed: with g as above and s = sum_c A_c G_c(x),
+ *   dA_c = sum_x g G_c,  dmu = sum_x s g (x - mu) / sigma^2,
+ *   dlog sigma = sum_x s g |x - mu|^2 / sigma^2. */
+void orc_fit2d_backward(int64_t k, const float* params, float D, int32_t width, int32_t height, const double* G,
+                        double* grad) {
+    const float D2 = D * D;
+    const int64_t plane = (int64_t)width * height;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < k; ++i) {
+        const float* p = params + 8 * i;
+        double* gr = grad + 8 * i;
+        for (int j = 0; j < 8; ++j) gr[j] = 0.0;
+        /* every pixel the FP32 test can accept lies within D + 1 of the centre */
+        int64_t x0 = (int64_t)floor((double)p[0] - D - 1.0), x1 = (int64_t)ceil((double)p[0] + D + 1.0);
+        int64_t y0 = (int64_t)floor((double)p[1] - D - 1.0), y1 = (int64_t)ceil((double)p[1] + D + 1.0);
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 > width - 1) x1 = width - 1;
+        if (y1 > height - 1) y1 = height - 1;
+        const double s = exp((double)p[2]), inv_s2 = 1.0 / (s * s);
+        for (int64_t y = y0; y <= y1; ++y)
+            for (int64_t x = x0; x <= x1; ++x) {
+                const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+                if (!fit_reach(px, py, p, D2)) continue;
+                double dx = (double)px - p[0], dy = (double)py - p[1], d2 = dx * dx + dy * dy;
+                double g = exp(-d2 * inv_s2 / 2.0);
+                double sg = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double Gc = G[c * plane + y * width + x];
+                    gr[3 + c] += g * Gc;
+                    sg += (double)p[3 + c] * Gc;
+                }
+                gr[0] += sg * g * dx * inv_s2;
+                gr[1] += sg * g * dy * inv_s2;
+                gr[2] += sg * g * d2 * inv_s2;
+            }
+    }
+}
+
+/* QuadTree initialisation (Sec. 3.1): each leaf cell of a quad tree over the
+ * image holds one particle at the cell centre, with A = the cell's mean colour
+ * and sigma = half the cell width. The paper does not say how the tree is
+ * grown; read as: starting from the whole image, split the leaf with the
+ * largest squared error about its mean colour (SSE, summed over channels) into
+ * four, as long as the leaves stay at most k_max (each split adds 3) and the
+ * children are at least min_cell pixels wide. The image is square with a power
+ * of two side of at most 512; the split statistics use it quantised to 12 bits,
+ * q = rint(clamp(v, 0, 1) * 4096), so that they are exact integers:
+ * T = sum_c (n S2_c - S1_c^2) with S1, S2 the sums of q and q^2 over the n
+ * pixels, and the order key n * SSE * 4096^2 / n^2 = T / n is the double
+ * quotient of (double)T and n. Ties: the lower level, then the upper row,
+ * then the left column. A_c = S1_c / (4096 n) (double, rounded once to
+ * float); log sigma = log2(side / 2) * ln 2 (double, rounded once).
+ * Particles are written in (level, row, column) order; returns their number. */
+typedef struct {
+    int32_t level, iy, ix, side;
+    double key;
+    int64_t s1[3];
+} orc_cell;
+
+static void cell_stats(const int32_t* q, int32_t W, orc_cell* c) {
+    uint64_t T = 0;
+    const int64_t n = (int64_t)c->side * c->side, plane = (int64_t)W * W;
+    for (int ch = 0; ch < 3; ++ch) {
+        int64_t s1 = 0, s2 = 0;
+        for (int32_t y = c->iy * c->side; y < (c->iy + 1) * c->side; ++y)
+            for (int32_t x = c->ix * c->side; x < (c->ix + 1) * c->side; ++x) {
+                int64_t v = q[ch * plane + (int64_t)y * W + x];
+                s1 += v;
+                s2 += v * v;
+            }
+        c->s1[ch] = s1;
+        T += (uint64_t)(n * s2) - (uint64_t)(s1 * s1);
+    }
+    c->key = (double)T / (double)n;
+}
+
+static int cell_before(const orc_cell* a, const orc_cell* b) { /* a split before b? */
+    if (a->key != b->key) return a->key > b->key;
+    if (a->level != b->level) return a->level < b->level;
+    if (a->iy != b->iy) return a->iy < b->iy;
+    return a->ix < b->ix;
+}
+
+static int cell_order(const void* pa, const void* pb) {
+    const orc_cell *a = (const orc_cell*)pa, *b = (const orc_cell*)pb;
+    if (a->level != b->level) return a->level < b->level ? -1 : 1;
+    if (a->iy != b->iy) return a->iy < b->iy ? -1 : 1;
+    return a->ix < b->ix ? -1 : (a->ix > b->ix);
+}
+
+int64_t orc_quadtree_init(const float* img, int32_t side, int32_t k_max, int32_t min_cell, float* params) {
+    if (side < 1 || side > 512 || (side & (side - 1)) || k_max < 1 || min_cell < 1) return -1;
+    const int64_t plane = (int64_t)side * side;
+    int32_t* q = (int32_t*)malloc(sizeof(int32_t) * 3 * plane);
+    for (int64_t i = 0; i < 3 * plane; ++i) {
+        float v = img[i];
+        v = v < 0.f ? 0.f : (v > 1.f ? 1.f : v);
+        q[i] = (int32_t)rint((double)v * 4096.0);
+    }
+    orc_cell* leaves = (orc_cell*)malloc(sizeof(orc_cell) * (size_t)(k_max + 3));
+    int64_t n_leaves = 1;
+    leaves[0].level = 0;
+    leaves[0].iy = leaves[0].ix = 0;
+    leaves[0].side = side;
+    cell_stats(q, side, &leaves[0]);
+    while (n_leaves + 3 <= k_max) {
+        int64_t best = -1;
+        for (int64_t i = 0; i < n_leaves; ++i) {
+            if (leaves[i].side / 2 < min_cell) continue;
+            if (best < 0 || cell_before(&leaves[i], &leaves[best])) best = i;
+        }
+        if (best < 0) break;
+        orc_cell parent = leaves[best];
+        for (int j = 0; j < 4; ++j) {
+            orc_cell c;
+            c.level = parent.level + 1;
+            c.side = parent.side / 2;
+            c.iy = 2 * parent.iy + (j >> 1);
+            c.ix = 2 * parent.ix + (j & 1);
+            cell_stats(q, side, &c);
+            if (j == 0)
+                leaves[best] = c;
+            else
+                leaves[n_leaves++] = c;
+        }
+    }
+    qsort(leaves, (size_t)n_leaves, sizeof(orc_cell), cell_order);
+    for (int64_t i = 0; i < n_leaves; ++i) {
+        const orc_cell* c = &leaves[i];
+        const double n = (double)c->side * c->side;
+        float* p = params + 8 * i;
+        p[0] = (float)((double)c->ix * c->side + 0.5 * c->side);
+        p[1] = (float)((double)c->iy * c->side + 0.5 * c->side);
+        int32_t lg = 0;
+        while ((1 << lg) < c->side) ++lg;
+        p[2] = (float)((double)(lg - 1) * 0.6931471805599453);
+        for (int ch = 0; ch < 3; ++ch) p[3 + ch] = (float)((double)c->s1[ch] / (4096.0 * n));
+        p[6] = p[7] = 0.f;
+    }
+    free(leaves);
+    free(q);
+    return n_leaves;
 }

@@ -223,3 +223,47 @@ def workload_train_3m(seed=3, n=3_000_000, views=16):
 
 def train_target(k, width=1297, height=840):
     return target_image(width, height, 300 + k)
+
+
+# ------------------------------------------------ 2D image-fitting inputs ----
+
+def fit2d_image(side=512, seed=6):
+    """Seeded synthetic RGB image, float32 [3, side, side] in [0, 1], standing
+    in for the paper's 2D test image (not available): a smooth colour gradient,
+    20 filled discs and 12 axis-aligned rectangles of random colours (sharp
+    edges at many scales), a sinusoidal texture patch and mild pixel noise."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid((np.arange(side) + 0.5) / side, (np.arange(side) + 0.5) / side, indexing="ij")
+    c0, c1 = rng.uniform(0.1, 0.9, size=(2, 3))
+    img = np.empty((3, side, side))
+    for c in range(3):
+        img[c] = c0[c] * (1 - xx) * (1 - yy) + c1[c] * xx * yy + 0.3 * (xx * (1 - yy))
+    for _ in range(20):
+        cx, cy = rng.uniform(0, 1, size=2)
+        r = rng.uniform(0.02, 0.15)
+        col = rng.uniform(0, 1, size=3)
+        m = (xx - cx) ** 2 + (yy - cy) ** 2 < r * r
+        img[:, m] = col[:, None]
+    for _ in range(12):
+        x0, y0 = rng.uniform(0, 0.9, size=2)
+        w, h = rng.uniform(0.03, 0.25, size=2)
+        col = rng.uniform(0, 1, size=3)
+        m = (xx >= x0) & (xx < x0 + w) & (yy >= y0) & (yy < y0 + h)
+        img[:, m] = col[:, None]
+    px, py, pw = rng.uniform(0.1, 0.6), rng.uniform(0.1, 0.6), 0.3
+    m = (xx >= px) & (xx < px + pw) & (yy >= py) & (yy < py + pw)
+    tex = 0.5 + 0.4 * np.sin(2 * np.pi * 24 * xx) * np.sin(2 * np.pi * 17 * yy)
+    img[:, m] = tex[m][None, :] * rng.uniform(0.3, 1.0, size=(3, 1))
+    img += rng.normal(0.0, 0.01, size=img.shape)
+    return np.clip(img, 0.0, 1.0).astype(np.float32)
+
+
+def fit2d_particles(k, side, seed, sigma=(1.0, 12.0)):
+    """Seeded random 2D particles [k][8] = (mu_x, mu_y, log sigma, A_r, A_g,
+    A_b, 0, 0): centres uniform over the image, sigma log-uniform, A ~ U[0, 1]."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros((k, 8), np.float32)
+    p[:, 0:2] = rng.uniform(0.0, side, size=(k, 2))
+    p[:, 2] = rng.uniform(np.log(sigma[0]), np.log(sigma[1]), size=k)
+    p[:, 3:6] = rng.uniform(0.0, 1.0, size=(k, 3))
+    return p

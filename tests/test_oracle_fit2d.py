@@ -1,0 +1,172 @@
+"""Pins of the oracle's 2D additive model and QuadTree initialisation (the
+paper's 2D experiment, Sec. 3).
+
+Render: the single-particle closed form with the FP32 support test replayed in
+numpy float32; additivity over disjoint particle sets; order invariance.
+Gradient: FP64 central differences (support far away), torch autograd of a
+dense formulation with the same support mask. QuadTree: K = 1 is the image
+mean; four constant quadrants give their colours; the leaves tile the image;
+the greedy rule holds (every split cell's error is at least every splittable
+leaf's, recomputed with numpy); the leaf count is 3m + 1 <= K."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_14244_gb300 import scenes
+
+
+def _reach32(px, py, mx, my, D):
+    f = np.float32
+    dx = f(px) - f(mx)
+    dy = f(py) - f(my)
+    return f(f(dx * dx) + f(dy * dy)) < f(f(D) * f(D))
+
+
+@pytest.mark.parametrize("D", [3.0, 7.5, 50.0])
+def test_single_particle_closed_form(D):
+    W, H = 37, 29
+    p = np.array([[13.3, 11.7, np.log(4.2), 0.2, 0.5, 0.9, 0, 0]], np.float32)
+    img = oracle.fit2d_render(p, D, W, H)
+    s = float(np.exp(np.float64(p[0, 2])))
+    for y in range(H):
+        for x in range(W):
+            px, py = np.float32(x + 0.5), np.float32(y + 0.5)
+            if _reach32(px, py, p[0, 0], p[0, 1], D):
+                d2 = (float(px) - float(p[0, 0])) ** 2 + (float(py) - float(p[0, 1])) ** 2
+                want = p[0, 3:6].astype(np.float64) * np.exp(-d2 / (2 * s * s))
+            else:
+                want = np.zeros(3)
+            np.testing.assert_allclose(img[:, y, x], want, rtol=1e-13, atol=1e-15)
+
+
+def test_additive_and_order_invariant():
+    p = scenes.fit2d_particles(60, 48, 1)
+    a = oracle.fit2d_render(p[:25], 9.0, 48, 40)
+    b = oracle.fit2d_render(p[25:], 9.0, 48, 40)
+    ab = oracle.fit2d_render(p, 9.0, 48, 40)
+    np.testing.assert_allclose(ab, a + b, rtol=1e-13, atol=1e-14)
+    perm = np.random.default_rng(2).permutation(60)
+    np.testing.assert_allclose(oracle.fit2d_render(p[perm], 9.0, 48, 40), ab, rtol=1e-13, atol=1e-14)
+
+
+def _loss(p, D, Wt):
+    return float((oracle.fit2d_render(p, D, Wt.shape[2], Wt.shape[1]) * Wt).sum())
+
+
+def test_gradient_central_differences():
+    # support far larger than the image: no pixel changes side under the steps
+    p = scenes.fit2d_particles(6, 20, 3, sigma=(2.0, 6.0)).astype(np.float64)
+    Wt = np.random.default_rng(4).normal(size=(3, 20, 22))
+    g = oracle.fit2d_backward(p.astype(np.float32), 1000.0, Wt)
+    assert np.all(g[:, 6:] == 0)
+    for i in range(6):
+        for j in range(6):
+            h = 1e-3 if j < 2 else 1e-4
+            pp, pm = p.copy(), p.copy()
+            pp[i, j] += h
+            pm[i, j] -= h
+            # parameters move in FP32: use the rounded steps
+            hp = float(np.float32(pp[i, j])) - float(np.float32(p[i, j]))
+            hm = float(np.float32(p[i, j])) - float(np.float32(pm[i, j]))
+            fd = (_loss(pp, 1000.0, Wt) - _loss(pm, 1000.0, Wt)) / (hp + hm)
+            assert fd == pytest.approx(g[i, j], rel=2e-5, abs=1e-9), (i, j)
+
+
+def test_gradient_matches_torch_autograd_with_cutoff():
+    W, H, D = 40, 34, 8.0
+    p32 = scenes.fit2d_particles(30, 36, 5, sigma=(1.5, 9.0))
+    G = np.random.default_rng(6).normal(size=(3, H, W))
+    g = oracle.fit2d_backward(p32, D, G)
+    ys, xs = np.meshgrid(np.arange(H, dtype=np.float32) + np.float32(0.5),
+                         np.arange(W, dtype=np.float32) + np.float32(0.5), indexing="ij")
+    mask = np.stack([_reach32(xs, ys, p32[k, 0], p32[k, 1], D) for k in range(30)])   # [K][H][W]
+    tp = torch.tensor(p32.astype(np.float64), requires_grad=True)
+    tx, ty = torch.tensor(xs.astype(np.float64)), torch.tensor(ys.astype(np.float64))
+    d2 = (tx[None] - tp[:, 0, None, None]) ** 2 + (ty[None] - tp[:, 1, None, None]) ** 2
+    s = torch.exp(tp[:, 2])[:, None, None]
+    gk = torch.exp(-d2 / (2 * s * s)) * torch.tensor(mask, dtype=torch.float64)
+    img = torch.einsum("kc,khw->chw", tp[:, 3:6], gk)
+    (img * torch.tensor(G)).sum().backward()
+    np.testing.assert_allclose(img.detach().numpy(), oracle.fit2d_render(p32, D, W, H), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(g, tp.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------- QuadTree --
+
+def _quant(img):
+    return np.rint(np.clip(img.astype(np.float64), 0, 1) * 4096)
+
+
+def _cell_of(p):
+    side = int(round(2 * np.exp(np.float64(p[2]))))
+    return int(round(p[0] - side / 2)), int(round(p[1] - side / 2)), side
+
+
+def test_quadtree_single_leaf_is_the_mean():
+    img = scenes.fit2d_image(64, 7)
+    p = oracle.quadtree_init(img, 1, 4)
+    assert p.shape == (1, 8)
+    assert tuple(p[0, :2]) == (32.0, 32.0)
+    assert p[0, 2] == pytest.approx(np.log(32.0), rel=1e-7)
+    np.testing.assert_allclose(p[0, 3:6], _quant(img).reshape(3, -1).mean(1) / 4096, rtol=1e-6)
+
+
+def test_quadtree_constant_quadrants():
+    img = np.zeros((3, 32, 32), np.float32)
+    cols = np.array([[0.25, 0.5, 0.75], [1.0, 0.0, 0.5], [0.125, 0.875, 0.375], [0.625, 0.25, 1.0]], np.float32)
+    for j, (y0, x0) in enumerate(((0, 0), (0, 16), (16, 0), (16, 16))):
+        img[:, y0:y0 + 16, x0:x0 + 16] = cols[j][:, None, None]
+    p = oracle.quadtree_init(img, 4, 2)
+    assert p.shape == (4, 8)
+    np.testing.assert_array_equal(p[:, :2], [[8, 8], [24, 8], [8, 24], [24, 24]])
+    np.testing.assert_array_equal(p[:, 3:6], cols)
+    np.testing.assert_allclose(np.exp(p[:, 2].astype(np.float64)), 8.0, rtol=1e-7)
+    # a further split budget finds nothing to gain but still splits (all errors are 0): ties by level, row, column
+    p7 = oracle.quadtree_init(img, 7, 2)
+    assert p7.shape == (7, 8) and _cell_of(p7[0]) == (16, 0, 16)
+
+
+@pytest.mark.parametrize("k,min_cell", [(100, 2), (334, 4), (1000, 1), (40, 16)])
+def test_quadtree_tiles_the_image_and_is_greedy(k, min_cell):
+    S = 64
+    img = scenes.fit2d_image(S, 8)
+    p = oracle.quadtree_init(img, k, min_cell)
+    L = p.shape[0]
+    assert L <= k and (L - 1) % 3 == 0
+    cover = np.zeros((S, S), int)
+    cells = [_cell_of(q) for q in p]
+    for x0, y0, side in cells:
+        cover[y0:y0 + side, x0:x0 + side] += 1
+        assert side >= min_cell
+    assert np.all(cover == 1)
+    q = _quant(img)
+
+    def err(x0, y0, side):  # SSE of the quantised cell, summed over channels (numpy)
+        blk = q[:, y0:y0 + side, x0:x0 + side].reshape(3, -1)
+        return float(((blk - blk.mean(1, keepdims=True)) ** 2).sum())
+
+    # the split cells are the ancestors of the leaves
+    split = set()
+    for x0, y0, side in cells:
+        s = side
+        while s < S:
+            s *= 2
+            split.add((x0 // s * s, y0 // s * s, s))
+    leaf_err = [err(*c) for c in cells if c[2] // 2 >= min_cell]
+    if leaf_err and L + 3 <= k:
+        pytest.fail("budget left but a splittable leaf was not split")
+    worst_split = min(err(*c) for c in split) if split else np.inf
+    if leaf_err:
+        assert worst_split >= max(leaf_err) * (1 - 1e-12)
+    # each particle's colour is its cell's mean of the quantised image
+    for (x0, y0, side), pp in zip(cells, p):
+        np.testing.assert_allclose(pp[3:6], q[:, y0:y0 + side, x0:x0 + side].reshape(3, -1).mean(1) / 4096,
+                                   rtol=1e-6)
+
+
+def test_quadtree_rejects_bad_sizes():
+    with pytest.raises(ValueError):
+        oracle.quadtree_init(np.zeros((3, 48, 48), np.float32), 10, 2)
+    with pytest.raises(ValueError):
+        oracle.quadtree_init(np.zeros((3, 1024, 1024), np.float32), 10, 2)
