@@ -446,8 +446,79 @@ def run_extra(dev, np):
     out["fwd_bwd_1080p_1M"]["entries_M"] = info[0]
     del scene, r, f, img, g2d, grads
     torch.cuda.empty_cache()
+    out["fit2d_512"] = run_fit2d(dev)
     out["batched_32view_2M"] = run_batched(dev)
     out["serve_4scenes_poisson200"] = run_serving(dev)
+    return out
+
+
+def run_fit2d(dev, iters=2000, side=512, min_cell=3):
+    """The paper's 2D experiment at its Table 2 settings (support D in {15, 50}
+    pixels, K in {1000, 2000} particles): QuadTree initialisation, then `iters`
+    iterations of render + (0.8 L1 + 0.2 (1 - SSIM)) + adjoint + Adam, replayed
+    from a CUDA graph of 50 iterations, on a seeded synthetic 512x512 image.
+    Reports the time of the initialisation and of the iterations, the per-kernel
+    split of one eager iteration, and the fit (loss, PSNR) before and after."""
+    import math
+
+    import torch
+
+    from paper_2403_14244_gb300 import scenes
+    from paper_2403_14244_gb300.fit2d import Fit2D
+
+    target = torch.from_numpy(scenes.fit2d_image(side, 6)).to(dev)
+    paper_min = {(15, 1000): 0.12, (50, 1000): 0.13, (15, 2000): 0.25, (50, 2000): 0.27}
+    out = {"image": [side, side], "iters": iters, "min_cell": min_cell, "lambda": 0.2,
+           "paper_table2_iso_minutes": "context only (2D image and hardware not given)"}
+
+    def psnr(f):
+        f.render()
+        mse = float(((f.img - f.target) ** 2).mean())
+        return round(10 * math.log10(1.0 / mse), 2)
+
+    Fit2D(target, 16, 15.0, min_cell=min_cell)   # loads the kernels: the timed set-ups below exclude that
+
+    for (D, K), ref_min in paper_min.items():
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record()
+        f = Fit2D(target, K, float(D), min_cell=min_cell)
+        b.record()
+        torch.cuda.synchronize(dev)
+        init_ms = a.elapsed_time(b)
+        psnr0 = psnr(f)
+        # per-kernel split of one eager iteration
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        from paper_2403_14244_gb300 import igs
+        igs.fit2d_render(f.particles, f.D, f.img)
+        ev[1].record()
+        igs.l1_ssim_loss(f.img, f.target, f.lam, f.loss, f.dimg, f.work, ssim=f.ssim)
+        ev[2].record()
+        igs.fit2d_backward(f.particles, f.D, f.dimg, f.grad)
+        ev[3].record()
+        igs.fit2d_adam(f.particles, f.grad, f.m, f.v, f.lr, f.state)
+        ev[4].record()
+        torch.cuda.synchronize(dev)
+        loss0 = float(f.loss)
+        split = {n: round(ev[i].elapsed_time(ev[i + 1]), 4)
+                 for i, n in enumerate(("render", "loss", "backward", "adam"))}
+        f.capture(inner=50)
+        torch.cuda.synchronize(dev)
+        a.record()
+        n = f.run(iters)
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        f.render()
+        igs.l1_ssim_loss(f.img, f.target, f.lam, f.loss, f.dimg, f.work, ssim=f.ssim)
+        out[f"D{D}_K{K}"] = {
+            "particles": f.k, "init_ms": round(init_ms, 3), "iter_ms": round(ms / n, 4),
+            "iters_per_s": round(1e3 * n / ms, 1),
+            "fit_minutes": round((init_ms + ms) / 60000.0, 6), "paper_iso_minutes": ref_min,
+            "eager_split_ms": split, "loss_first": round(loss0, 5), "loss_last": round(float(f.loss), 5),
+            "ssim_last": round(float(f.ssim), 4), "psnr_init_db": psnr0, "psnr_last_db": psnr(f)}
+        del f
     return out
 
 

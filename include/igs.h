@@ -269,6 +269,65 @@ IGS_API igs_status igs_l1_ssim_loss(const float* img, const float* target, int32
                                     int32_t width, float lambda, float* loss, float* ssim, float* dL_dimg,
                                     void* work, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * The paper's 2D experiment (Sec. 3): an image as a sum of isotropic kernels,
+ *   f^(x) = sum over k with |mu_k - x| < D of A_k exp(-|x - mu_k|^2 / (2 sigma_k^2))
+ * (Eq. 8 with the 1/2 of the Gaussian; the support centre tau_k read as mu_k).
+ * A particle is 8 floats (mu_x, mu_y, log sigma, A_r, A_g, A_b, 0, 0) in pixel
+ * units (x right, y down); particle arrays are device [k][8], 16-byte aligned.
+ * Pixel (x, y) samples at (x + 0.5, y + 0.5); images are planar [3][H][W] FP32.
+ * The support test is canonical FP32: dx = px - mu_x, dy = py - mu_y,
+ * d2 = dx*dx + dy*dy, each step rounded once; reached iff d2 < D*D (D*D rounded
+ * once). Non-finite particles reach nothing. All calls are asynchronous.
+ * ------------------------------------------------------------------------- */
+
+/* img = f^ over all width x height pixels (overwritten). Each pixel sums its
+ * particles in index order (deterministic). D > 0 (+inf: no cutoff).
+ * Errors: k outside 0..2^27, size outside 1..2^20, D <= 0 or NaN, NULL or
+ * misaligned buffers -> IGS_ERR_INVALID_ARG. */
+IGS_API igs_status igs_fit2d_render(const float* particles, int32_t k, float D, int32_t width, int32_t height,
+                                    float* img, void* stream);
+
+/* d_particles [k][8] (device, overwritten) = the gradient of a loss whose image
+ * gradient is dL_dimg ([3][H][W]), the reached pixels held fixed:
+ *   dA_c = sum_x g G_c,  dmu = sum_x s g (x - mu) / sigma^2,
+ *   dlog sigma = sum_x s g |x - mu|^2 / sigma^2,  s = sum_c A_c G_c(x);
+ * slots 6, 7 are 0. Sums over tiles are added atomically (not bit-reproducible). */
+IGS_API igs_status igs_fit2d_backward(const float* particles, int32_t k, float D, int32_t width, int32_t height,
+                                      const float* dL_dimg, float* d_particles, void* stream);
+
+/* One bias-corrected Adam step over the particles in place (m, v: device [k][8],
+ * the moments), slot j of every particle with learning rate lr[j] (host, 8
+ * floats >= 0). The step count lives on the device so that captured graphs can
+ * replay steps: d_state is device int32[2], zero before the first step; the
+ * step uses t = d_state[0] + 1 and increments d_state[0] when it completes
+ * (d_state[1] is internal). Update as igs_adam: m = b1 m + (1-b1) g;
+ * v = b2 v + (1-b2) g^2; p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps). */
+IGS_API igs_status igs_fit2d_adam(float* particles, const float* d_particles, float* m, float* v, int32_t k,
+                                  const float* lr, double b1, double b2, double eps, int32_t* d_state,
+                                  void* stream);
+
+/* Bytes of device scratch igs_quadtree_init needs (0 for an invalid size). */
+IGS_API size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell);
+
+/* QuadTree initialisation (Sec. 3.1) of a square RGB image (device
+ * [3][side][side], side a power of two <= 512): one particle per leaf cell, at
+ * the cell centre, with A = the cell's mean colour and sigma = half the cell
+ * width. Growth rule (the paper gives none): starting from the whole image,
+ * split the leaf with the largest squared error about its mean colour, summed
+ * over channels, while the leaves stay at most k_max (a split adds 3) and the
+ * children are at least min_cell pixels wide. The errors use the image
+ * quantised to 12 bits, q = rint(clamp(v, 0, 1) 4096), as exact integers; the
+ * key is T / n in double, T = sum_c n S2_c - S1_c^2 over the cell's n pixels;
+ * ties go to the lower level, then the upper row, then the left column.
+ * A_c = S1_c / (4096 n) (double, rounded once to float); log sigma =
+ * log2(width / 2) ln 2 (double, rounded once). Writes the particles in (level,
+ * row, column) order to particles (device, >= k_max x 8 floats, 16-byte
+ * aligned) and their number to *d_count (device int32). work: device scratch
+ * of igs_quadtree_work_bytes(side, min_cell) bytes, 16-byte aligned. */
+IGS_API igs_status igs_quadtree_init(const float* img, int32_t side, int32_t k_max, int32_t min_cell,
+                                     float* particles, int32_t* d_count, void* work, void* stream);
+
 /* One bias-corrected Adam step (step >= 1) in place on p, m, v (device,
  * count FP32 each), from gradient g. The host scalars are double so that 1 - b1,
  * 1 - b2 and the bias corrections are formed exactly before rounding to FP32:

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "fit2d.cuh"
 
 namespace igs {
 std::atomic<uint64_t> g_launches{0};
@@ -342,6 +343,84 @@ igs_status igs_l1_ssim_loss(const float* img, const float* target, int32_t chann
     return cuda_status(igs::launch_l1_ssim(img, target, channels, height, width, lambda, loss, ssim, dL_dimg,
                                            static_cast<float*>(work), (cudaStream_t)stream),
                        "igs_l1_ssim_loss");
+}
+
+// ------------------------------------------------------------ 2D fitting --
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+static igs_status check_fit2d(const float* particles, int32_t k, float D, int32_t width, int32_t height) {
+    if (!particles && k > 0) return fail(IGS_ERR_INVALID_ARG, "fit2d: particles is NULL");
+    if (!aligned16(particles)) return fail(IGS_ERR_INVALID_ARG, "fit2d: particles not 16-byte aligned");
+    if (k < 0 || k > (1 << 27)) return fail(IGS_ERR_INVALID_ARG, "fit2d: k must be 0..2^27");
+    if (width < 1 || height < 1 || width > (1 << 20) || height > (1 << 20))
+        return fail(IGS_ERR_INVALID_ARG, "fit2d: width and height must be 1..2^20");
+    if (!(D > 0.f)) return fail(IGS_ERR_INVALID_ARG, "fit2d: D must be positive");
+    return IGS_OK;
+}
+
+igs_status igs_fit2d_render(const float* particles, int32_t k, float D, int32_t width, int32_t height, float* img,
+                            void* stream) {
+    igs_status st;
+    if ((st = check_fit2d(particles, k, D, width, height))) return st;
+    if (!img) return fail(IGS_ERR_INVALID_ARG, "fit2d_render: img is NULL");
+    return cuda_status(igs::launch_fit2d_render(particles, k, D, width, height, img, (cudaStream_t)stream),
+                       "igs_fit2d_render");
+}
+
+igs_status igs_fit2d_backward(const float* particles, int32_t k, float D, int32_t width, int32_t height,
+                              const float* dL_dimg, float* d_particles, void* stream) {
+    igs_status st;
+    if ((st = check_fit2d(particles, k, D, width, height))) return st;
+    if (!dL_dimg || (!d_particles && k > 0)) return fail(IGS_ERR_INVALID_ARG, "fit2d_backward: NULL buffer");
+    return cuda_status(igs::launch_fit2d_backward(particles, k, D, width, height, dL_dimg, d_particles,
+                                                  (cudaStream_t)stream),
+                       "igs_fit2d_backward");
+}
+
+igs_status igs_fit2d_adam(float* particles, const float* d_particles, float* m, float* v, int32_t k,
+                          const float* lr, double b1, double b2, double eps, int32_t* d_state, void* stream) {
+    if (k < 0 || k > (1 << 27)) return fail(IGS_ERR_INVALID_ARG, "fit2d_adam: k must be 0..2^27");
+    if (!lr || !d_state) return fail(IGS_ERR_INVALID_ARG, "fit2d_adam: lr or d_state is NULL");
+    if (k > 0 && (!particles || !d_particles || !m || !v))
+        return fail(IGS_ERR_INVALID_ARG, "fit2d_adam: NULL buffer");
+    if (!aligned16(particles) || !aligned16(d_particles) || !aligned16(m) || !aligned16(v))
+        return fail(IGS_ERR_INVALID_ARG, "fit2d_adam: buffers must be 16-byte aligned");
+    if (!(b1 >= 0.0 && b1 < 1.0 && b2 >= 0.0 && b2 < 1.0 && eps > 0.0))
+        return fail(IGS_ERR_INVALID_ARG, "fit2d_adam: need 0 <= b1, b2 < 1 and eps > 0");
+    igs::Fit2dAdam a;
+    for (int j = 0; j < 8; ++j) {
+        if (!std::isfinite(lr[j]) || lr[j] < 0.f) return fail(IGS_ERR_INVALID_ARG, "fit2d_adam: lr must be >= 0");
+        a.lr[j] = lr[j];
+    }
+    a.b1 = (float)b1;
+    a.b2 = (float)b2;
+    a.omb1 = (float)(1.0 - b1);
+    a.omb2 = (float)(1.0 - b2);
+    a.eps = (float)eps;
+    a.b1d = b1;
+    a.b2d = b2;
+    return cuda_status(igs::launch_fit2d_adam(particles, d_particles, m, v, k, a, d_state, (cudaStream_t)stream),
+                       "igs_fit2d_adam");
+}
+
+size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell) {
+    if (side < 1 || side > 512 || (side & (side - 1)) || min_cell < 1) return 0;
+    return igs::quadtree_work_bytes(side, min_cell);
+}
+
+igs_status igs_quadtree_init(const float* img, int32_t side, int32_t k_max, int32_t min_cell, float* particles,
+                             int32_t* d_count, void* work, void* stream) {
+    if (side < 1 || side > 512 || (side & (side - 1)))
+        return fail(IGS_ERR_INVALID_ARG, "quadtree_init: side must be a power of two <= 512");
+    if (k_max < 1 || k_max > (1 << 27) || min_cell < 1)
+        return fail(IGS_ERR_INVALID_ARG, "quadtree_init: need 1 <= k_max <= 2^27 and min_cell >= 1");
+    if (!img || !particles || !d_count || !work) return fail(IGS_ERR_INVALID_ARG, "quadtree_init: NULL buffer");
+    if (!aligned16(particles) || !aligned16(work))
+        return fail(IGS_ERR_INVALID_ARG, "quadtree_init: particles and work must be 16-byte aligned");
+    return cuda_status(igs::launch_quadtree_init(img, side, k_max, min_cell, particles, d_count, work,
+                                                 (cudaStream_t)stream),
+                       "igs_quadtree_init");
 }
 
 igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_t count, double lr, double b1, double b2,

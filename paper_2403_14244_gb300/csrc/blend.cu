@@ -15,6 +15,7 @@
 // saved T_final, and reduces the per-pixel gradient terms of each entry over
 // the tile before one vector atomic per (entry, 4 floats).
 #include "blendtile.cuh"
+#include "warp.cuh"
 
 namespace igs {
 namespace {
@@ -34,33 +35,6 @@ __global__ void __launch_bounds__(TS* TS) k_blend_fwd(const uint2* __restrict__ 
                            P.alpha_max, P.t_min, P.bg, s_a, s_c, img, T_final, n_contrib);
 }
 
-// Butterfly reduce-scatter of 8 values over a warp in 9 shuffles: afterwards
-// lane l holds the warp total of value (l >> 2) & 7.
-__device__ __forceinline__ float warp_reduce8(float v[8], int lane) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool hi = lane & 16;
-        const float send = hi ? v[i] : v[i + 4];
-        const float keep = hi ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool hi = lane & 8;
-        const float send = hi ? v[i] : v[i + 2];
-        const float keep = hi ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    {
-        const bool hi = lane & 4;
-        const float send = hi ? v[0] : v[1];
-        const float keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-    return v[0];
-}
 
 // Entries staged per barrier pair in the backward: 64 (two ballot words per
 // warp), 32 for 32x32 tiles (whose per-warp partials would not fit otherwise).

@@ -104,6 +104,14 @@ SYMBOLS = {
     "igs_ssim_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "igs_l1_ssim_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "igs_fit2d_render": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "igs_fit2d_backward": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_int32, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]),
+    "igs_fit2d_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_float),
+                                 C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "igs_quadtree_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "igs_quadtree_init": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
     "igs_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double,
                            C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "igs_frame_status": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_uint32), C.c_void_p]),
@@ -356,6 +364,50 @@ def l1_ssim_loss(img, target, lam, loss, dL_dimg, work, ssim=None, stream=None):
     _check(load().igs_l1_ssim_loss(_ptr(img), _ptr(target), shp[0], shp[1], shp[2], float(lam), _ptr(loss),
                                    _ptr(ssim) if ssim is not None else None, _ptr(dL_dimg), _ptr(work),
                                    _stream(stream)), "igs_l1_ssim_loss")
+
+
+# ------------------------------------------------------------ 2D fitting --
+
+def _particles(p):
+    if p.dim() != 2 or p.shape[1] != 8 or p.dtype != torch.float32 or not p.is_contiguous():
+        raise ValueError("particles must be a contiguous float32 [k][8] tensor")
+    return p
+
+
+def fit2d_render(particles, D, img, stream=None):
+    """img ([3][H][W]) = sum of the particles' kernels within distance D."""
+    _particles(particles)
+    _check(load().igs_fit2d_render(_ptr(particles), particles.shape[0], float(D), img.shape[2], img.shape[1],
+                                   _ptr(img), _stream(stream)), "igs_fit2d_render")
+
+
+def fit2d_backward(particles, D, dL_dimg, d_particles, stream=None):
+    _particles(particles)
+    _check(load().igs_fit2d_backward(_ptr(particles), particles.shape[0], float(D), dL_dimg.shape[2],
+                                     dL_dimg.shape[1], _ptr(dL_dimg), _ptr(d_particles), _stream(stream)),
+           "igs_fit2d_backward")
+
+
+def fit2d_adam(particles, d_particles, m, v, lr, state, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    """Adam over the particles with per-slot learning rates lr (8 floats); state:
+    device int32[2] step counter, zero before the first step."""
+    _particles(particles)
+    lrs = (C.c_float * 8)(*[float(x) for x in lr])
+    _check(load().igs_fit2d_adam(_ptr(particles), _ptr(d_particles), _ptr(m), _ptr(v), particles.shape[0], lrs,
+                                 float(b1), float(b2), float(eps), _ptr(state), _stream(stream)), "igs_fit2d_adam")
+
+
+def quadtree_work_bytes(side, min_cell):
+    return int(load().igs_quadtree_work_bytes(int(side), int(min_cell)))
+
+
+def quadtree_init(img, k_max, min_cell, particles, count, work, stream=None):
+    """QuadTree initialisation of a [3][S][S] image into particles (>= k_max x 8)
+    and the particle count into count (device int32)."""
+    if img.dim() != 3 or img.shape[0] != 3 or img.shape[1] != img.shape[2]:
+        raise ValueError("img must be [3][S][S]")
+    _check(load().igs_quadtree_init(_ptr(img), img.shape[1], int(k_max), int(min_cell), _ptr(particles),
+                                    _ptr(count), _ptr(work), _stream(stream)), "igs_quadtree_init")
 
 
 def adam(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
