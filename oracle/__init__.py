@@ -90,6 +90,9 @@ def _load():
             lib.orc_fit2d_backward.argtypes = [i64, P, C.c_float, C.c_int32, C.c_int32, P, P]
             lib.orc_quadtree_init.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P]
             lib.orc_quadtree_init.restype = i64
+            lib.orc_fit2d_densify.argtypes = [i64, P, P, P, P, C.c_int32, C.c_float, C.c_float, C.c_float, i64,
+                                              P, P, P]
+            lib.orc_fit2d_densify.restype = i64
             _lib = lib
     return _lib
 
@@ -344,3 +347,17 @@ def quadtree_init(img, k_max, min_cell):
     if n < 0:
         raise ValueError("side must be a power of two <= 512, k_max and min_cell >= 1")
     return out[:n].copy()
+
+
+def fit2d_densify(params, m, v, accum, n_iters, tau_a, tau_g, log_sigma_min, capacity):
+    """Delete particles with max |A| < tau_a; divide those whose summed
+    position-gradient norm exceeds tau_g * n_iters and whose log sigma >=
+    log_sigma_min into four sigma/2 children at mu +- sigma/2 (the first
+    candidates that fit `capacity`); keep the rest. Returns (params, m, v)."""
+    p, mm, vv = _c32(params).reshape(-1, 8), _c32(m).reshape(-1, 8), _c32(v).reshape(-1, 8)
+    acc = _c32(accum).reshape(-1)
+    out = np.zeros((capacity, 8), np.float32)
+    om, ov = np.zeros_like(out), np.zeros_like(out)
+    n = _load().orc_fit2d_densify(p.shape[0], _ptr(p), _ptr(mm), _ptr(vv), _ptr(acc), int(n_iters), float(tau_a),
+                                  float(tau_g), float(log_sigma_min), int(capacity), _ptr(out), _ptr(om), _ptr(ov))
+    return out[:n].copy(), om[:n].copy(), ov[:n].copy()

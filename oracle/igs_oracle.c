@@ -1050,3 +1050,70 @@ int64_t orc_quadtree_init(const float* img, int32_t side, int32_t k_max, int32_t
     free(q);
     return n_leaves;
 }
+
+/* Densify / prune of the 2D particles (Sec. 3.2: particles "can be deleted if
+ * A_k is smaller than a threshold", and divided, Sec. 2's multiscale property).
+ * Reading: particle i is
+ *   deleted  if max_c |A_c| < tau_a;
+ *   divided  otherwise, if its summed position-gradient norm accum_i exceeds
+ *            tau_g * n_iters (FP32 product) and log sigma >= log_sigma_min,
+ *            into four children with sigma / 2 at mu + (-/+ sigma/2, -/+ sigma/2)
+ *            (order: (-,-), (+,-), (-,+), (+,+)), sigma = exp(log sigma) in FP64
+ *            rounded to FP32, half of it exact; child log sigma = log sigma -
+ *            ln 2 (FP32), same A;
+ *   kept     otherwise.
+ * If the result would exceed `capacity`, only the first (by index) division
+ * candidates that fit divide (each adds 3), the others are kept. Output in
+ * index order (children in place of their parent); kept particles keep their
+ * Adam moments, children start with zero moments. Returns the output count. */
+int64_t orc_fit2d_densify(int64_t k, const float* params, const float* m, const float* v, const float* accum,
+                          int32_t n_iters, float tau_a, float tau_g, float log_sigma_min, int64_t capacity,
+                          float* out, float* out_m, float* out_v) {
+    const float thr = tau_g * (float)n_iters;
+    int64_t keep = 0, cand = 0;
+    for (int64_t i = 0; i < k; ++i) {
+        const float* p = params + 8 * i;
+        float amax = fabsf(p[3]);
+        if (fabsf(p[4]) > amax) amax = fabsf(p[4]);
+        if (fabsf(p[5]) > amax) amax = fabsf(p[5]);
+        if (amax < tau_a) continue;
+        ++keep;
+        if (accum[i] > thr && p[2] >= log_sigma_min) ++cand;
+    }
+    int64_t allowed = capacity > keep ? (capacity - keep) / 3 : 0;
+    if (allowed > cand) allowed = cand;
+    int64_t o = 0, seen = 0;
+    for (int64_t i = 0; i < k; ++i) {
+        const float* p = params + 8 * i;
+        float amax = fabsf(p[3]);
+        if (fabsf(p[4]) > amax) amax = fabsf(p[4]);
+        if (fabsf(p[5]) > amax) amax = fabsf(p[5]);
+        if (amax < tau_a) continue;
+        int divide = accum[i] > thr && p[2] >= log_sigma_min;
+        if (divide) divide = seen++ < allowed;
+        if (!divide) {
+            if (o >= capacity) break;
+            for (int j = 0; j < 8; ++j) {
+                out[8 * o + j] = p[j];
+                out_m[8 * o + j] = m[8 * i + j];
+                out_v[8 * o + j] = v[8 * i + j];
+            }
+            ++o;
+            continue;
+        }
+        const float h = 0.5f * (float)exp((double)p[2]);
+        for (int c = 0; c < 4; ++c) {
+            float* q = out + 8 * o;
+            q[0] = (c & 1) ? p[0] + h : p[0] - h;
+            q[1] = (c & 2) ? p[1] + h : p[1] - h;
+            q[2] = p[2] - 0.6931472f;
+            q[3] = p[3];
+            q[4] = p[4];
+            q[5] = p[5];
+            q[6] = q[7] = 0.f;
+            for (int j = 0; j < 8; ++j) out_m[8 * o + j] = out_v[8 * o + j] = 0.f;
+            ++o;
+        }
+    }
+    return o;
+}

@@ -7,7 +7,11 @@ Gradient: FP64 central differences (support far away), torch autograd of a
 dense formulation with the same support mask. QuadTree: K = 1 is the image
 mean; four constant quadrants give their colours; the leaves tile the image;
 the greedy rule holds (every split cell's error is at least every splittable
-leaf's, recomputed with numpy); the leaf count is 3m + 1 <= K."""
+leaf's, recomputed with numpy); the leaf count is 3m + 1 <= K. Densify/prune:
+identity with the thresholds off; pruning keeps exactly the rows numpy selects;
+a division gives four children centred on the parent on a square of side sigma
+with half its scale and zero moments; the capacity divides the first
+candidates."""
 import numpy as np
 import pytest
 import torch
@@ -170,3 +174,73 @@ def test_quadtree_rejects_bad_sizes():
         oracle.quadtree_init(np.zeros((3, 48, 48), np.float32), 10, 2)
     with pytest.raises(ValueError):
         oracle.quadtree_init(np.zeros((3, 1024, 1024), np.float32), 10, 2)
+
+
+# ------------------------------------------------------------ densify/prune --
+
+def _moments(k, seed):
+    rng = np.random.default_rng(seed)
+    return rng.random((k, 8)).astype(np.float32), rng.random((k, 8)).astype(np.float32)
+
+
+def test_densify_thresholds_off_is_identity():
+    p = scenes.fit2d_particles(50, 64, 11)
+    m, v = _moments(50, 12)
+    acc = np.random.default_rng(13).random(50).astype(np.float32)
+    q, qm, qv = oracle.fit2d_densify(p, m, v, acc, 10, 0.0, np.inf, -np.inf, 200)
+    np.testing.assert_array_equal(q, p)
+    np.testing.assert_array_equal(qm, m)
+    np.testing.assert_array_equal(qv, v)
+
+
+def test_densify_prunes_small_amplitudes():
+    p = scenes.fit2d_particles(200, 64, 14)
+    p[::3, 3:6] *= 0.01
+    p[1::7, 4] = -0.5                  # |A| counts, not A
+    m, v = _moments(200, 15)
+    acc = np.zeros(200, np.float32)
+    tau = 0.05
+    keep = np.abs(p[:, 3:6]).max(1) >= tau
+    q, qm, qv = oracle.fit2d_densify(p, m, v, acc, 1, tau, np.inf, 0.0, 200)
+    np.testing.assert_array_equal(q, p[keep])
+    np.testing.assert_array_equal(qm, m[keep])
+    np.testing.assert_array_equal(qv, v[keep])
+
+
+def test_densify_divides_into_four_half_size_children():
+    p = scenes.fit2d_particles(40, 64, 16, sigma=(1.0, 8.0))
+    m, v = _moments(40, 17)
+    acc = np.random.default_rng(18).random(40).astype(np.float32)
+    n_it, tau_g, lsm = 4, 0.1, float(np.log(2.0))
+    cand = (acc > np.float32(tau_g) * np.float32(n_it)) & (p[:, 2] >= np.float32(lsm))
+    q, qm, qv = oracle.fit2d_densify(p, m, v, acc, n_it, 0.0, tau_g, lsm, 1000)
+    assert q.shape[0] == 40 + 3 * cand.sum()
+    o = 0
+    for i in range(40):
+        if not cand[i]:
+            np.testing.assert_array_equal(q[o], p[i])
+            np.testing.assert_array_equal(qm[o], m[i])
+            o += 1
+            continue
+        kids = q[o:o + 4]
+        s = np.exp(np.float64(p[i, 2]))
+        np.testing.assert_allclose(kids[:, :2].mean(0), p[i, :2], rtol=1e-6, atol=1e-5)    # centred on the parent
+        np.testing.assert_allclose(np.ptp(kids[:, 0]), s, rtol=1e-5)                       # a square of side sigma
+        np.testing.assert_allclose(np.ptp(kids[:, 1]), s, rtol=1e-5)
+        np.testing.assert_allclose(np.exp(kids[:, 2].astype(np.float64)), s / 2, rtol=1e-6)  # half the scale
+        np.testing.assert_array_equal(kids[:, 3:6], np.repeat(p[i:i + 1, 3:6], 4, 0))
+        assert np.all(qm[o:o + 4] == 0) and np.all(qv[o:o + 4] == 0)
+        o += 4
+    assert o == q.shape[0]
+
+
+def test_densify_capacity_divides_the_first_candidates():
+    p = scenes.fit2d_particles(30, 64, 19, sigma=(2.0, 8.0))
+    m, v = _moments(30, 20)
+    acc = np.full(30, 10.0, np.float32)
+    q, _, _ = oracle.fit2d_densify(p, m, v, acc, 1, 0.0, 1.0, -np.inf, 30 + 3 * 5 + 2)
+    assert q.shape[0] == 45
+    # the first five parents divided: their children come first, then the rest unchanged
+    np.testing.assert_array_equal(q[20:], p[5:])
+    for i in range(5):
+        np.testing.assert_allclose(q[4 * i:4 * i + 4, :2].mean(0), p[i, :2], rtol=1e-6, atol=1e-5)
