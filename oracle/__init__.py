@@ -93,6 +93,7 @@ def _load():
             lib.orc_fit2d_densify.argtypes = [i64, P, P, P, P, C.c_int32, C.c_float, C.c_float, C.c_float, i64,
                                               P, P, P]
             lib.orc_fit2d_densify.restype = i64
+            lib.orc_fit2d_grad_accum.argtypes = [i64, P, P]
             _lib = lib
     return _lib
 
@@ -347,6 +348,17 @@ def quadtree_init(img, k_max, min_cell):
     if n < 0:
         raise ValueError("side must be a power of two <= 512, k_max and min_cell >= 1")
     return out[:n].copy()
+
+
+def fit2d_grad_accum(d_particles, accum):
+    """accum_i + |dL/dmu_i| (FP32, one rounding per step) for the 2D particles'
+    gradients d_particles [k][8]; returns the new accumulator."""
+    g = _c32(d_particles).reshape(-1, 8)
+    acc = _c32(accum).reshape(-1).copy()
+    if acc.shape[0] != g.shape[0]:
+        raise ValueError("accum must hold one value per particle")
+    _load().orc_fit2d_grad_accum(g.shape[0], _ptr(g), _ptr(acc))
+    return acc
 
 
 def fit2d_densify(params, m, v, accum, n_iters, tau_a, tau_g, log_sigma_min, capacity):

@@ -1051,6 +1051,18 @@ int64_t orc_quadtree_init(const float* img, int32_t side, int32_t k_max, int32_t
     return n_leaves;
 }
 
+/* Accumulated position-gradient norm of each 2D particle, the statistic the
+ * division rule below reads (Sec. 3.2 names no statistic; reading: the norm of
+ * dL/dmu summed over the iterations since the last densify). FP32, one rounding
+ * per step: accum_i += sqrt(g_x * g_x + g_y * g_y), g = d_particles[i][0..1]. */
+void orc_fit2d_grad_accum(int64_t k, const float* d_particles, float* accum) {
+    for (int64_t i = 0; i < k; ++i) {
+        const float gx = d_particles[8 * i], gy = d_particles[8 * i + 1];
+        const float sq = gx * gx + gy * gy;
+        accum[i] = accum[i] + sqrtf(sq);
+    }
+}
+
 /* Densify / prune of the 2D particles (Sec. 3.2: particles "can be deleted if
  * A_k is smaller than a threshold", and divided, Sec. 2's multiscale property).
  * Reading: particle i is

@@ -244,3 +244,28 @@ def test_densify_capacity_divides_the_first_candidates():
     np.testing.assert_array_equal(q[20:], p[5:])
     for i in range(5):
         np.testing.assert_allclose(q[4 * i:4 * i + 4, :2].mean(0), p[i, :2], rtol=1e-6, atol=1e-5)
+
+
+def test_densify_capacity_below_kept_count_truncates():
+    p = scenes.fit2d_particles(30, 64, 21)
+    m, v = _moments(30, 22)
+    acc = np.full(30, 10.0, np.float32)
+    q, qm, _ = oracle.fit2d_densify(p, m, v, acc, 1, 0.0, 1.0, -np.inf, 12)
+    # no room to divide anything: the first 12 particles, unchanged
+    np.testing.assert_array_equal(q, p[:12])
+    np.testing.assert_array_equal(qm, m[:12])
+
+
+def test_grad_accum_is_the_fp32_norm_sum():
+    g = np.zeros((4, 8), np.float32)
+    g[0, :2] = (3.0, 4.0)              # a 3-4-5 triangle: exactly 5
+    g[1, :2] = (-6.0, 8.0)             # signs do not matter: 10
+    g[2, 2:] = 7.0                     # other slots do not count
+    acc = oracle.fit2d_grad_accum(g, np.array([1.0, 0.5, 2.0, 0.0], np.float32))
+    np.testing.assert_array_equal(acc, np.array([6.0, 10.5, 2.0, 0.0], np.float32))
+    rng = np.random.default_rng(23)
+    g = rng.normal(size=(1000, 8)).astype(np.float32)
+    a0 = rng.random(1000).astype(np.float32)
+    want = a0 + np.sqrt(g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1])    # numpy float32: one rounding per step
+    np.testing.assert_array_equal(oracle.fit2d_grad_accum(g, a0), want)
+    assert np.allclose(want, a0 + np.hypot(g[:, 0].astype(np.float64), g[:, 1]), rtol=1e-6)
