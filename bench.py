@@ -519,7 +519,48 @@ def run_fit2d(dev, iters=2000, side=512, min_cell=3):
             "eager_split_ms": split, "loss_first": round(loss0, 5), "loss_last": round(float(f.loss), 5),
             "ssim_last": round(float(f.ssim), 4), "psnr_init_db": psnr0, "psnr_last_db": psnr(f)}
         del f
+    out["densify_D15"] = run_fit2d_densify(dev, target, iters, min_cell, psnr)
     return out
+
+
+def run_fit2d_densify(dev, target, iters, min_cell, psnr, D=15.0, k0=256, capacity=1000, every=500):
+    """Densify / prune during the 2D fit: start from a QuadTree of k0 particles;
+    every `every` iterations delete particles with max |A| < 0.01 and divide
+    those whose mean position-gradient norm is in the top quarter (threshold
+    read from the accumulated statistic on the host) into four half-scale
+    children, within `capacity` particles. Reports the densify kernel's time,
+    the particle counts and the fit, to compare with the QuadTree started at
+    `capacity` particles above."""
+    import numpy as np
+    import torch
+
+    from paper_2403_14244_gb300.fit2d import Fit2D
+
+    f = Fit2D(target, k0, D, min_cell=min_cell)
+    f.track_grad_norm()
+    f.capture(inner=50)
+    counts, dens_ms = [f.k], []
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    done = 1
+    while done < iters:
+        done += f.run(min(every, iters - done))
+        if done >= iters:
+            break
+        tau_g = float(np.quantile(f.accum.cpu().numpy(), 0.75)) / f.accum_iters
+        a.record()
+        f.densify(0.01, tau_g, 0.0, capacity)   # includes the count read-back
+        b.record()
+        torch.cuda.synchronize(dev)
+        dens_ms.append(round(a.elapsed_time(b), 4))
+        counts.append(f.k)
+        f.capture(inner=50)
+        done += 1
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    return {"D": D, "k_start": k0, "capacity": capacity, "every": every, "iters": done, "particles": counts,
+            "densify_ms": dens_ms, "wall_s": round(wall, 3), "psnr_last_db": psnr(f)}
 
 
 def run_batched(dev, reps=10):

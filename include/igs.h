@@ -307,6 +307,38 @@ IGS_API igs_status igs_fit2d_adam(float* particles, const float* d_particles, fl
                                   const float* lr, double b1, double b2, double eps, int32_t* d_state,
                                   void* stream);
 
+/* Densify / prune of the 2D particles (Sec. 3.2: particles may be deleted when
+ * A_k falls below a threshold, and divided; Sec. 2's multiscale property).
+ *
+ * igs_fit2d_grad_accum: accum[i] += sqrt(g_x^2 + g_y^2) for each particle,
+ * g = d_particles[i][0..1] (the position gradient from igs_fit2d_backward);
+ * FP32, each step rounded once. accum: device float[k], caller-owned, zeroed by
+ * the caller when a densify interval starts. Asynchronous.
+ *
+ * igs_fit2d_densify: from particles, m, v (device [k][8], the Adam moments) and
+ * accum (device float[k], summed over the n_iters iterations since the last
+ * densify), writes new particles and moments to out, out_m, out_v (device
+ * [capacity][8], caller-owned, 16-byte aligned, not overlapping the inputs) and
+ * their number to *d_count (device int32). Particle i is
+ *   deleted  if max_c |A_c| < tau_a (compared in channel order);
+ *   divided  else, if accum[i] > tau_g * n_iters (one FP32 product) and
+ *            log sigma >= log_sigma_min, into four children of half the scale
+ *            (log sigma - ln 2 in FP32) at mu + (-h, -h), (+h, -h), (-h, +h),
+ *            (+h, +h), h = sigma / 2 with sigma = exp(log sigma) in double
+ *            rounded to FP32; same A; zero moments;
+ *   kept     otherwise, with its moments.
+ * Output is in index order, children in place of their parent. If the result
+ * would exceed capacity, only the first candidates (by index) that fit divide,
+ * each adding 3; if even the kept particles exceed it, the first capacity of
+ * them are written. One CTA; intended for periodic use (e.g. every 100
+ * iterations). Errors: k or capacity outside 0..2^27, n_iters < 1, a NaN
+ * threshold, NULL, misaligned or overlapping buffers -> IGS_ERR_INVALID_ARG. */
+IGS_API igs_status igs_fit2d_grad_accum(const float* d_particles, int32_t k, float* accum, void* stream);
+IGS_API igs_status igs_fit2d_densify(const float* particles, const float* m, const float* v, const float* accum,
+                                     int32_t k, int32_t n_iters, float tau_a, float tau_g, float log_sigma_min,
+                                     int32_t capacity, float* out, float* out_m, float* out_v, int32_t* d_count,
+                                     void* stream);
+
 /* Bytes of device scratch igs_quadtree_init needs (0 for an invalid size). */
 IGS_API size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell);
 

@@ -404,6 +404,41 @@ igs_status igs_fit2d_adam(float* particles, const float* d_particles, float* m, 
                        "igs_fit2d_adam");
 }
 
+igs_status igs_fit2d_grad_accum(const float* d_particles, int32_t k, float* accum, void* stream) {
+    if (k < 0 || k > (1 << 27)) return fail(IGS_ERR_INVALID_ARG, "fit2d_grad_accum: k must be 0..2^27");
+    if (k > 0 && (!d_particles || !accum)) return fail(IGS_ERR_INVALID_ARG, "fit2d_grad_accum: NULL buffer");
+    if (!aligned16(d_particles)) return fail(IGS_ERR_INVALID_ARG, "fit2d_grad_accum: d_particles must be 16-byte aligned");
+    return cuda_status(igs::launch_fit2d_grad_accum(d_particles, k, accum, (cudaStream_t)stream),
+                       "igs_fit2d_grad_accum");
+}
+
+igs_status igs_fit2d_densify(const float* particles, const float* m, const float* v, const float* accum, int32_t k,
+                             int32_t n_iters, float tau_a, float tau_g, float log_sigma_min, int32_t capacity,
+                             float* out, float* out_m, float* out_v, int32_t* d_count, void* stream) {
+    if (k < 0 || k > (1 << 27)) return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: k must be 0..2^27");
+    if (capacity < 0 || capacity > (1 << 27)) return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: capacity must be 0..2^27");
+    if (n_iters < 1) return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: n_iters must be >= 1");
+    if (std::isnan(tau_a) || std::isnan(tau_g) || std::isnan(log_sigma_min))
+        return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: NaN threshold");
+    if (!d_count) return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: d_count is NULL");
+    if (k > 0 && (!particles || !m || !v || !accum)) return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: NULL input");
+    if (capacity > 0 && (!out || !out_m || !out_v)) return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: NULL output");
+    if (!aligned16(particles) || !aligned16(m) || !aligned16(v) || !aligned16(out) || !aligned16(out_m) ||
+        !aligned16(out_v))
+        return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: particle buffers must be 16-byte aligned");
+    const auto overlaps = [](const float* a, int64_t na, const float* b, int64_t nb) {
+        return a && b && na > 0 && nb > 0 && a < b + nb && b < a + na;
+    };
+    const int64_t ni = 8 * (int64_t)k, no = 8 * (int64_t)capacity;
+    for (const float* o : {(const float*)out, (const float*)out_m, (const float*)out_v})
+        for (const float* in : {particles, m, v})
+            if (overlaps(o, no, in, ni)) return fail(IGS_ERR_INVALID_ARG, "fit2d_densify: outputs overlap inputs");
+    const float thr = tau_g * (float)n_iters;  // one FP32 rounding
+    return cuda_status(igs::launch_fit2d_densify(particles, m, v, accum, k, thr, tau_a, log_sigma_min, capacity, out,
+                                                 out_m, out_v, d_count, (cudaStream_t)stream),
+                       "igs_fit2d_densify");
+}
+
 size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell) {
     if (side < 1 || side > 512 || (side & (side - 1)) || min_cell < 1) return 0;
     return igs::quadtree_work_bytes(side, min_cell);

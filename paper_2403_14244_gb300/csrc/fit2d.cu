@@ -415,6 +415,151 @@ __global__ void __launch_bounds__(kQtThreads) k_qt_emit(const CellStats* __restr
     if (threadIdx.x == 0) *count = min(s_base, k_max);
 }
 
+// ------------------------------------------------------- densify / prune ----
+//
+// Sec. 3.2 deletes particles whose amplitude falls below a threshold, and
+// Sec. 2's multiscale property divides coarse particles into finer ones. The
+// statistic for division is the position-gradient norm summed over the
+// iterations since the last densify (k_fit2d_grad_accum, called after each
+// adjoint). One CTA walks the particles in chunks of kDensThreads: a first pass
+// counts the kept particles and the division candidates (which fixes how many
+// candidates fit the capacity), a second pass gives each particle its output
+// slot (exclusive scan of 0 / 1 / 4 outputs, carried across chunks) and writes
+// the kept particle or its four children, so the output is in index order with
+// children in place of their parent.
+
+constexpr int kDensThreads = 1024;
+
+struct DensifyParams {
+    float thr, tau_a, log_sigma_min;
+    int k, capacity;
+};
+
+// accum_i += |dL/dmu_i| in FP32, one rounding per step.
+__global__ void __launch_bounds__(256) k_fit2d_grad_accum(const float4* __restrict__ g, int k,
+                                                         float* __restrict__ accum) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const float4 a = g[2 * i];
+        const float sq = __fadd_rn(__fmul_rn(a.x, a.x), __fmul_rn(a.y, a.y));
+        accum[i] = __fadd_rn(accum[i], __fsqrt_rn(sq));
+    }
+}
+
+// Keep: max_c |A_c| is not below tau_a (the comparisons run in this order, so a
+// NaN amplitude keeps its particle). Candidate: kept, accum_i > thr and
+// log sigma >= log_sigma_min.
+__device__ __forceinline__ void densify_flags(const float4* __restrict__ pr, const float* __restrict__ accum, int i,
+                                              const DensifyParams& P, bool& keep, bool& cand) {
+    const float4 a = pr[2 * i], b = pr[2 * i + 1];
+    float amax = fabsf(a.w);
+    if (fabsf(b.x) > amax) amax = fabsf(b.x);
+    if (fabsf(b.y) > amax) amax = fabsf(b.y);
+    keep = !(amax < P.tau_a);
+    cand = keep && accum[i] > P.thr && a.z >= P.log_sigma_min;
+}
+
+__global__ void __launch_bounds__(kDensThreads) k_fit2d_densify(const float4* __restrict__ pr,
+                                                               const float4* __restrict__ m,
+                                                               const float4* __restrict__ v,
+                                                               const float* __restrict__ accum, DensifyParams P,
+                                                               float4* __restrict__ out, float4* __restrict__ om,
+                                                               float4* __restrict__ ov, int32_t* __restrict__ count) {
+    __shared__ uint32_t s_warp[kDensThreads / 32];
+    __shared__ uint32_t s_tot[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // pass 1: kept particles and division candidates
+    uint32_t nk = 0, nc = 0;
+    for (int i = threadIdx.x; i < P.k; i += kDensThreads) {
+        bool keep, cand;
+        densify_flags(pr, accum, i, P, keep, cand);
+        nk += keep;
+        nc += cand;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nk += __shfl_xor_sync(0xffffffffu, nk, o);
+        nc += __shfl_xor_sync(0xffffffffu, nc, o);
+    }
+    if (threadIdx.x == 0) s_tot[0] = s_tot[1] = 0;
+    __syncthreads();
+    if (lane == 0) {
+        atomicAdd(&s_tot[0], nk);
+        atomicAdd(&s_tot[1], nc);
+    }
+    __syncthreads();
+    const long long keep_total = s_tot[0], cand_total = s_tot[1];
+    const long long allowed = min(P.capacity > keep_total ? ((long long)P.capacity - keep_total) / 3 : 0LL, cand_total);
+    // pass 2: slots (outputs in the low 16 bits, candidates in the high 16 bits of one scan)
+    long long base_out = 0, base_cand = 0;
+    for (int c0 = 0; c0 < P.k; c0 += kDensThreads) {
+        const int i = c0 + threadIdx.x;
+        bool keep = false, cand = false;
+        if (i < P.k) densify_flags(pr, accum, i, P, keep, cand);
+        // a candidate divides iff its rank among candidates is < allowed; outputs
+        // depend on that rank, so scan the candidates first
+        uint32_t x = cand ? 1u : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[w] = incl;
+        __syncthreads();
+        uint32_t wpre = 0, ctot = 0;
+        for (int j = 0; j < kDensThreads / 32; ++j) {
+            if (j < w) wpre += s_warp[j];
+            ctot += s_warp[j];
+        }
+        const long long crank = base_cand + wpre + incl - x;
+        const bool divide = cand && crank < allowed;
+        __syncthreads();
+        const uint32_t n_out = divide ? 4u : (keep ? 1u : 0u);
+        incl = n_out;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[w] = incl;
+        __syncthreads();
+        uint32_t opre = 0, otot = 0;
+        for (int j = 0; j < kDensThreads / 32; ++j) {
+            if (j < w) opre += s_warp[j];
+            otot += s_warp[j];
+        }
+        const long long slot = base_out + opre + incl - n_out;
+        if (divide) {
+            // four children with half the scale at mu +- sigma / 2, zero moments
+            const float4 a = pr[2 * i], b = pr[2 * i + 1];
+            const float h = __fmul_rn(0.5f, (float)exp((double)a.z));
+            const float ls = __fsub_rn(a.z, 0.6931472f);
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float x0 = (c & 1) ? __fadd_rn(a.x, h) : __fsub_rn(a.x, h);
+                const float y0 = (c & 2) ? __fadd_rn(a.y, h) : __fsub_rn(a.y, h);
+                const long long o = slot + c;
+                out[2 * o] = make_float4(x0, y0, ls, a.w);
+                out[2 * o + 1] = make_float4(b.x, b.y, 0.f, 0.f);
+                om[2 * o] = om[2 * o + 1] = zero;
+                ov[2 * o] = ov[2 * o + 1] = zero;
+            }
+        } else if (keep && slot < P.capacity) {
+            out[2 * slot] = pr[2 * i];
+            out[2 * slot + 1] = pr[2 * i + 1];
+            om[2 * slot] = m[2 * i];
+            om[2 * slot + 1] = m[2 * i + 1];
+            ov[2 * slot] = v[2 * i];
+            ov[2 * slot + 1] = v[2 * i + 1];
+        }
+        base_out += otot;
+        base_cand += ctot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = (int32_t)min(base_out, (long long)P.capacity);
+}
+
 int finest_level(int side, int min_cell) {
     int lf = 0;
     while ((side >> (lf + 1)) >= min_cell && (side >> (lf + 1)) >= 1) ++lf;
@@ -461,6 +606,31 @@ cudaError_t launch_fit2d_adam(float* particles, const float* d_particles, float*
     k_fit2d_adam<<<blocks, 256, 0, st>>>(reinterpret_cast<float4*>(particles),
                                          reinterpret_cast<const float4*>(d_particles), reinterpret_cast<float4*>(m),
                                          reinterpret_cast<float4*>(v), n4, a, state);
+    count_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit2d_grad_accum(const float* d_particles, int k, float* accum, cudaStream_t st) {
+    if (k == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>(ceil_div(k, 256), 152 * 4);
+    k_fit2d_grad_accum<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(d_particles), k, accum);
+    count_launches();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit2d_densify(const float* particles, const float* m, const float* v, const float* accum, int k,
+                                 float thr, float tau_a, float log_sigma_min, int capacity, float* out, float* out_m,
+                                 float* out_v, int32_t* count, cudaStream_t st) {
+    DensifyParams P;
+    P.thr = thr;
+    P.tau_a = tau_a;
+    P.log_sigma_min = log_sigma_min;
+    P.k = k;
+    P.capacity = capacity;
+    k_fit2d_densify<<<1, kDensThreads, 0, st>>>(
+        reinterpret_cast<const float4*>(particles), reinterpret_cast<const float4*>(m),
+        reinterpret_cast<const float4*>(v), accum, P, reinterpret_cast<float4*>(out), reinterpret_cast<float4*>(out_m),
+        reinterpret_cast<float4*>(out_v), count);
     count_launches();
     return cudaGetLastError();
 }

@@ -20,6 +20,12 @@ cudaError_t launch_fit2d_backward(const float* particles, int k, float D, int wi
                                   float* d_particles, cudaStream_t s);
 cudaError_t launch_fit2d_adam(float* particles, const float* d_particles, float* m, float* v, int k,
                               const Fit2dAdam& a, int32_t* state, cudaStream_t s);
+// Densify / prune: the accumulated position-gradient norm, and one pass that
+// deletes, divides and keeps particles into new buffers (count to *count).
+cudaError_t launch_fit2d_grad_accum(const float* d_particles, int k, float* accum, cudaStream_t s);
+cudaError_t launch_fit2d_densify(const float* particles, const float* m, const float* v, const float* accum, int k,
+                                 float thr, float tau_a, float log_sigma_min, int capacity, float* out, float* out_m,
+                                 float* out_v, int32_t* count, cudaStream_t s);
 // QuadTree initialisation: scratch size and the chain of launches.
 size_t quadtree_work_bytes(int side, int min_cell);
 cudaError_t launch_quadtree_init(const float* img, int side, int k_max, int min_cell, float* particles,

@@ -47,6 +47,8 @@ class Fit2D:
         self.work = torch.empty(igs.ssim_work_bytes(3, S, S) // 4, dtype=torch.float32, device=device)
         self.graph = None
         self.inner = 0
+        self.accum = None       # summed position-gradient norms (densify statistic), when tracked
+        self.accum_iters = 0    # iterations summed into accum
 
     def render(self, stream=None):
         igs.fit2d_render(self.particles, self.D, self.img, stream)
@@ -58,13 +60,45 @@ class Fit2D:
         igs.l1_ssim_loss(self.img, self.target, self.lam, self.loss, self.dimg, self.work, ssim=self.ssim,
                          stream=stream)
         igs.fit2d_backward(self.particles, self.D, self.dimg, self.grad, stream)
+        if self.accum is not None:
+            igs.fit2d_grad_accum(self.grad, self.accum, stream)
+            self.accum_iters += 1
         igs.fit2d_adam(self.particles, self.grad, self.m, self.v, self.lr, self.state, stream=stream)
+
+    def track_grad_norm(self):
+        """Start summing each particle's position-gradient norm (the statistic
+        densify() divides by); drops a captured graph, which did not sum it."""
+        self.accum = torch.zeros(self.k, dtype=torch.float32, device=self.particles.device)
+        self.accum_iters = 0
+        self.graph = None
+
+    def densify(self, tau_a, tau_g, log_sigma_min, capacity):
+        """Delete particles with max |A| < tau_a, divide those whose mean
+        position-gradient norm since the last densify exceeds tau_g (and whose
+        log sigma >= log_sigma_min) into four half-scale children, within
+        `capacity` particles (libigs's igs_fit2d_densify). Reads the new count
+        back (one synchronisation) and drops the captured graph."""
+        if self.accum is None or self.accum_iters == 0:
+            raise RuntimeError("densify needs track_grad_norm() and at least one step")
+        dev = self.particles.device
+        out = torch.empty((capacity, 8), dtype=torch.float32, device=dev)
+        om, ov = torch.empty_like(out), torch.empty_like(out)
+        count = torch.zeros(1, dtype=torch.int32, device=dev)
+        igs.fit2d_densify(self.particles, self.m, self.v, self.accum, self.accum_iters, tau_a, tau_g, log_sigma_min,
+                          out, om, ov, count)
+        k = int(count.item())
+        self.particles, self.m, self.v = out[:k].clone(), om[:k].clone(), ov[:k].clone()
+        self.k = k
+        self.grad = torch.zeros_like(self.particles)
+        self.track_grad_norm()
+        return k
 
     def capture(self, inner=10):
         """Record `inner` iterations into one CUDA graph (after one eager step,
         which also loads the kernels)."""
         self.step()
         torch.cuda.synchronize()
+        iters0 = self.accum_iters
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -73,6 +107,7 @@ class Fit2D:
                 for _ in range(inner):
                     self.step()
         torch.cuda.current_stream().wait_stream(s)
+        self.accum_iters = iters0       # recording ran nothing
         self.graph, self.inner = g, inner
         return g
 
@@ -84,6 +119,8 @@ class Fit2D:
         while n < iters:
             self.graph.replay()
             n += self.inner
+            if self.accum is not None:
+                self.accum_iters += self.inner
         return n
 
     def steps_done(self):

@@ -109,6 +109,10 @@ SYMBOLS = {
                                      C.c_void_p, C.c_void_p]),
     "igs_fit2d_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_float),
                                  C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "igs_fit2d_grad_accum": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "igs_fit2d_densify": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float,
+                                    C.c_float, C.c_float, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
     "igs_quadtree_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
     "igs_quadtree_init": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
@@ -395,6 +399,24 @@ def fit2d_adam(particles, d_particles, m, v, lr, state, b1=0.9, b2=0.999, eps=1e
     lrs = (C.c_float * 8)(*[float(x) for x in lr])
     _check(load().igs_fit2d_adam(_ptr(particles), _ptr(d_particles), _ptr(m), _ptr(v), particles.shape[0], lrs,
                                  float(b1), float(b2), float(eps), _ptr(state), _stream(stream)), "igs_fit2d_adam")
+
+
+def fit2d_grad_accum(d_particles, accum, stream=None):
+    """accum ([k] float32, device) += the norm of each particle's position gradient."""
+    _particles(d_particles)
+    _check(load().igs_fit2d_grad_accum(_ptr(d_particles), d_particles.shape[0], _ptr(accum), _stream(stream)),
+           "igs_fit2d_grad_accum")
+
+
+def fit2d_densify(particles, m, v, accum, n_iters, tau_a, tau_g, log_sigma_min, out, out_m, out_v, count,
+                  stream=None):
+    """Delete (max |A| < tau_a), divide (accum > tau_g * n_iters and log sigma >=
+    log_sigma_min: four half-scale children) or keep each particle into out,
+    out_m, out_v ([capacity][8]); the new count goes to count (device int32)."""
+    _particles(particles)
+    _check(load().igs_fit2d_densify(_ptr(particles), _ptr(m), _ptr(v), _ptr(accum), particles.shape[0], int(n_iters),
+                                    float(tau_a), float(tau_g), float(log_sigma_min), out.shape[0], _ptr(out),
+                                    _ptr(out_m), _ptr(out_v), _ptr(count), _stream(stream)), "igs_fit2d_densify")
 
 
 def quadtree_work_bytes(side, min_cell):

@@ -177,3 +177,85 @@ def test_bad_arguments_raise():
         igs.quadtree_init(torch.zeros(3, 48, 48, device="cuda"), 10, 2, p, torch.zeros(1, dtype=torch.int32,
                           device="cuda"), torch.empty(1024, dtype=torch.uint8, device="cuda"))
     assert igs.quadtree_work_bytes(48, 2) == 0
+
+
+# ------------------------------------------------------------ densify/prune --
+
+def test_grad_accum_bit_exact():
+    rng = np.random.default_rng(31)
+    g = rng.normal(size=(3000, 8)).astype(np.float32) * np.float32(1e-2)
+    g[::17, :2] = 0.0
+    a0 = rng.random(3000).astype(np.float32)
+    acc = torch.from_numpy(a0).cuda()
+    igs.fit2d_grad_accum(torch.from_numpy(g).cuda(), acc)
+    igs.fit2d_grad_accum(torch.from_numpy(g[::-1].copy()).cuda(), acc)
+    want = oracle.fit2d_grad_accum(g[::-1], oracle.fit2d_grad_accum(g, a0))
+    np.testing.assert_array_equal(acc.cpu().numpy(), want)
+
+
+def _densify_inputs(k, seed):
+    p = scenes.fit2d_particles(k, 256, seed, sigma=(0.5, 16.0))
+    rng = np.random.default_rng(seed + 1)
+    p[rng.random(k) < 0.2, 3:6] *= np.float32(0.02)        # faint: below tau_a
+    if k > 3:
+        p[1, 3] = np.nan                                    # a NaN first amplitude keeps its particle
+        p[2, 3:6] = -0.9                                    # |A| counts, not A
+    m = rng.normal(size=(k, 8)).astype(np.float32)
+    v = rng.random((k, 8)).astype(np.float32)
+    acc = (rng.random(k) * 2.0).astype(np.float32)
+    if k > 5:
+        acc[5] = np.nan                                     # never a candidate
+    return p, m, v, acc
+
+
+@pytest.mark.parametrize("k,capacity", [(0, 16), (1, 8), (1500, 6000), (1500, 1500), (5000, 9000), (5000, 3000),
+                                        (5000, 100), (4096, 4096 * 4)])
+def test_densify_bit_exact(k, capacity):
+    p, m, v, acc = _densify_inputs(k, 40 + k)
+    n_it, tau_a, tau_g, lsm = 7, 0.05, 0.15, float(np.log(1.5))
+    want_p, want_m, want_v = oracle.fit2d_densify(p, m, v, acc, n_it, tau_a, tau_g, lsm, capacity)
+    t = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (p, m, v, acc)]
+    out = torch.full((capacity, 8), 3.0, device="cuda")
+    om, ov = torch.full_like(out, 3.0), torch.full_like(out, 3.0)
+    count = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    igs.fit2d_densify(*t, n_it, tau_a, tau_g, lsm, out, om, ov, count)
+    n = int(count.item())
+    assert n == want_p.shape[0]
+    np.testing.assert_array_equal(out[:n].cpu().numpy(), want_p)
+    np.testing.assert_array_equal(om[:n].cpu().numpy(), want_m)
+    np.testing.assert_array_equal(ov[:n].cpu().numpy(), want_v)
+    assert torch.all(out[n:] == 3.0)                         # nothing written past the count
+
+
+def test_densify_rejects_overlap_and_bad_args():
+    p = torch.zeros((16, 8), device="cuda")
+    acc = torch.zeros(16, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.zeros((32, 8), device="cuda")
+    with pytest.raises(igs.IgsError):
+        igs.fit2d_densify(p, p, p, acc, 1, 0.1, 0.1, 0.0, out, p, out, count)   # out_m is an input
+    with pytest.raises(igs.IgsError):
+        igs.fit2d_densify(p, p, p, acc, 0, 0.1, 0.1, 0.0, out, out.clone(), out.clone(), count)
+
+
+def test_fit2d_driver_densify_matches_oracle():
+    img = torch.from_numpy(scenes.fit2d_image(128, 6)).cuda()
+    f = Fit2D(img, k_max=100, D=15.0, min_cell=3)
+    f.track_grad_norm()
+    for _ in range(5):
+        f.step()
+    f.run(20)                                              # graph replays sum the statistic too
+    assert f.accum_iters == 5 + 1 + 20                     # 5 eager, 1 eager at capture, 2 replays of 10
+    p, m, v, acc = (x.cpu().numpy() for x in (f.particles, f.m, f.v, f.accum))
+    n_it = f.accum_iters
+    tau_g = float(np.median(acc)) / n_it
+    want_p, want_m, want_v = oracle.fit2d_densify(p, m, v, acc, n_it, 0.02, tau_g, 0.0, 400)
+    k = f.densify(0.02, tau_g, 0.0, 400)
+    assert k == want_p.shape[0] and k > p.shape[0]
+    np.testing.assert_array_equal(f.particles.cpu().numpy(), want_p)
+    np.testing.assert_array_equal(f.m.cpu().numpy(), want_m)
+    np.testing.assert_array_equal(f.v.cpu().numpy(), want_v)
+    assert float(f.accum.abs().sum()) == 0.0 and f.accum_iters == 0
+    f.run(20)                                              # continues with the new particle set
+    torch.cuda.synchronize()
+    _img_close(f.render().cpu().numpy(), oracle.fit2d_render(f.particles.cpu().numpy(), 15.0, 128, 128))
