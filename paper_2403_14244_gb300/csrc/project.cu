@@ -36,11 +36,14 @@ struct ColorTile {
 constexpr int kPbThreads = 128;
 
 // Adam on one parameter (the fused kernel's hot loop: 53 updates per Gaussian);
-// the bias correction is a multiplication and the step a fast division (2 ulp).
+// the bias correction is a multiplication, the square root the SFU's
+// approximation (sqrt.approx, a few ulp) and the step a fast division (2 ulp).
 __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, const AdamParams& a) {
     m = a.b1 * m + a.omb1 * g;
     v = a.b2 * v + a.omb2 * g * g;
-    p -= __fdividef(a.step_size * m, fmaf(sqrtf(v), a.inv_bc2_sqrt, a.eps));
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    p -= __fdividef(a.step_size * m, fmaf(r, a.inv_bc2_sqrt, a.eps));
 }
 __device__ __forceinline__ void adam_update4(float4& p, float4 g, float4& m, float4& v, const AdamParams& a) {
     adam_update(p.x, g.x, m.x, v.x, a);
