@@ -94,6 +94,9 @@ def _load():
                                               P, P, P]
             lib.orc_fit2d_densify.restype = i64
             lib.orc_fit2d_grad_accum.argtypes = [i64, P, P]
+            lib.orc_grad_accum3d.argtypes = [i64, P, P, P, P]
+            lib.orc_densify3d.argtypes = [i64, C.c_int32, C.c_int32] + [P] * 11 + [C.c_float] * 3 + [i64] + [P] * 9
+            lib.orc_densify3d.restype = i64
             _lib = lib
     return _lib
 
@@ -373,3 +376,42 @@ def fit2d_densify(params, m, v, accum, n_iters, tau_a, tau_g, log_sigma_min, cap
     n = _load().orc_fit2d_densify(p.shape[0], _ptr(p), _ptr(mm), _ptr(vv), _ptr(acc), int(n_iters), float(tau_a),
                                   float(tau_g), float(log_sigma_min), int(capacity), _ptr(out), _ptr(om), _ptr(ov))
     return out[:n].copy(), om[:n].copy(), ov[:n].copy()
+
+
+def grad_accum3d(g2d, count, accum, vis):
+    """Densify statistic of the 3D Gaussians after one step: for every Gaussian
+    that touched a tile (count > 0), accum += |(du, dv)| (FP32, one rounding per
+    step) and vis += 1. Returns (accum, vis)."""
+    g = _c32(g2d).reshape(-1, 8)
+    cnt = np.ascontiguousarray(count, np.uint32).reshape(-1)
+    acc = _c32(accum).reshape(-1).copy()
+    vv = np.ascontiguousarray(vis, np.uint32).reshape(-1).copy()
+    if not (g.shape[0] == cnt.shape[0] == acc.shape[0] == vv.shape[0]):
+        raise ValueError("g2d, count, accum and vis must describe the same Gaussians")
+    _load().orc_grad_accum3d(g.shape[0], _ptr(g), _ptr(cnt), _ptr(acc), _ptr(vv))
+    return acc, vv
+
+
+def densify3d(params, m, v, accum, vis, param_mode, op_min, tau_g, scale_min, capacity):
+    """Delete (stored opacity < op_min), divide (mean screen-space position
+    gradient accum / vis > tau_g and stored scale >= scale_min: eight half-scale
+    children, one per octant at mu +- sigma / 2) or keep each 3D Gaussian, within
+    `capacity`. params, m, v: (means_sigma [n][4], opacity [n], color [n][C]).
+    Returns (params, m, v) of the result, same layout."""
+    ms, op, col = (_c32(a) for a in params)
+    n = ms.shape[0]
+    C = col.reshape(n, -1).shape[1] if n else col.shape[-1]
+    col = col.reshape(n, C)
+    mm = [_c32(a) for a in m]
+    vv = [_c32(a) for a in v]
+    acc = _c32(accum).reshape(-1)
+    vis_ = np.ascontiguousarray(vis, np.uint32).reshape(-1)
+    outs = [np.zeros((capacity, 4), np.float32), np.zeros(capacity, np.float32), np.zeros((capacity, C), np.float32)]
+    om = [np.zeros_like(a) for a in outs]
+    ov = [np.zeros_like(a) for a in outs]
+    k = _load().orc_densify3d(n, C, int(param_mode), _ptr(ms), _ptr(op), _ptr(col), *[_ptr(a) for a in mm],
+                              *[_ptr(a) for a in vv], _ptr(acc), _ptr(vis_), float(op_min), float(tau_g),
+                              float(scale_min), int(capacity), *[_ptr(a) for a in outs], *[_ptr(a) for a in om],
+                              *[_ptr(a) for a in ov])
+    cut = lambda arrs: tuple(a[:k].copy() for a in arrs)  # noqa: E731
+    return cut(outs), cut(om), cut(ov)

@@ -1129,3 +1129,93 @@ int64_t orc_fit2d_densify(int64_t k, const float* params, const float* m, const 
     }
     return o;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Densify / prune of the 3D Gaussians (Sec. 3.2: particles whose A_k falls
+ * below a threshold are deleted, and particles may be divided; Sec. 2.5's
+ * multiscale property, with the Octree of Sec. 3.1 as the division pattern).
+ *
+ * Statistic, per training step in which Gaussian i touched a tile (count_i > 0):
+ *   accum_i += sqrt(du^2 + dv^2)   (its screen-space position gradient, g2d
+ *   slots 0 and 1; FP32, one rounding per step),  vis_i += 1. */
+void orc_grad_accum3d(int64_t n, const float* g2d, const uint32_t* count, float* accum, uint32_t* vis) {
+    for (int64_t i = 0; i < n; ++i) {
+        if (count[i] == 0) continue;
+        const float du = g2d[8 * i], dv = g2d[8 * i + 1];
+        const float sq = du * du + dv * dv;
+        accum[i] = accum[i] + sqrtf(sq);
+        vis[i] += 1u;
+    }
+}
+
+/* Reading (parameters as stored: param_mode 1 keeps log sigma and the opacity
+ * logit, 0 keeps sigma and the opacity). Gaussian i is
+ *   deleted  if its stored opacity < op_min (op_min given in the same
+ *            parameterisation, so the test is one FP32 comparison);
+ *   divided  otherwise, if vis_i > 0, accum_i > tau_g * vis_i (one FP32
+ *            product) and its stored scale >= scale_min, into eight children
+ *            (one per octant, child c at mu + (+-h, +-h, +-h) with the sign of
+ *            axis a from bit a of c, '-' for 0), h = sigma / 2 (sigma = exp(log
+ *            sigma) in double rounded to FP32, or sigma itself), child scale
+ *            log sigma - ln 2 (FP32) or sigma / 2; same opacity and colour; zero
+ *            Adam moments;
+ *   kept     otherwise, with its moments.
+ * Output in index order, children in place of their parent; when the result
+ * would exceed `capacity`, only the first candidates (by index) that fit
+ * divide (each adds 7); if even the kept Gaussians exceed it, the first
+ * `capacity` of them are written. Arrays: means_sigma [n][4], opacity [n],
+ * color [n][C]; the moments m_*, v_* alike; outputs [capacity] alike. */
+int64_t orc_densify3d(int64_t n, int32_t C, int32_t param_mode, const float* ms, const float* op, const float* col,
+                      const float* m_ms, const float* m_op, const float* m_col, const float* v_ms, const float* v_op,
+                      const float* v_col, const float* accum, const uint32_t* vis, float op_min, float tau_g,
+                      float scale_min, int64_t capacity, float* o_ms, float* o_op, float* o_col, float* om_ms,
+                      float* om_op, float* om_col, float* ov_ms, float* ov_op, float* ov_col) {
+    int64_t keep = 0, cand = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (op[i] < op_min) continue;
+        ++keep;
+        if (vis[i] > 0 && accum[i] > tau_g * (float)vis[i] && ms[4 * i + 3] >= scale_min) ++cand;
+    }
+    int64_t allowed = capacity > keep ? (capacity - keep) / 7 : 0;
+    if (allowed > cand) allowed = cand;
+    int64_t o = 0, seen = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (op[i] < op_min) continue;
+        int divide = vis[i] > 0 && accum[i] > tau_g * (float)vis[i] && ms[4 * i + 3] >= scale_min;
+        if (divide) divide = seen++ < allowed;
+        if (!divide) {
+            if (o >= capacity) break;
+            memcpy(o_ms + 4 * o, ms + 4 * i, 16);
+            memcpy(om_ms + 4 * o, m_ms + 4 * i, 16);
+            memcpy(ov_ms + 4 * o, v_ms + 4 * i, 16);
+            o_op[o] = op[i];
+            om_op[o] = m_op[i];
+            ov_op[o] = v_op[i];
+            memcpy(o_col + (size_t)C * o, col + (size_t)C * i, 4 * (size_t)C);
+            memcpy(om_col + (size_t)C * o, m_col + (size_t)C * i, 4 * (size_t)C);
+            memcpy(ov_col + (size_t)C * o, v_col + (size_t)C * i, 4 * (size_t)C);
+            ++o;
+            continue;
+        }
+        const float s = ms[4 * i + 3];
+        const float sigma = param_mode == 1 ? (float)exp((double)s) : s;
+        const float h = 0.5f * sigma;
+        const float child_scale = param_mode == 1 ? s - 0.6931472f : 0.5f * s;
+        for (int c = 0; c < 8; ++c) {
+            for (int a = 0; a < 3; ++a) {
+                const float mu = ms[4 * i + a];
+                o_ms[4 * o + a] = ((c >> a) & 1) ? mu + h : mu - h;
+            }
+            o_ms[4 * o + 3] = child_scale;
+            o_op[o] = op[i];
+            memcpy(o_col + (size_t)C * o, col + (size_t)C * i, 4 * (size_t)C);
+            memset(om_ms + 4 * o, 0, 16);
+            memset(ov_ms + 4 * o, 0, 16);
+            om_op[o] = ov_op[o] = 0.f;
+            memset(om_col + (size_t)C * o, 0, 4 * (size_t)C);
+            memset(ov_col + (size_t)C * o, 0, 4 * (size_t)C);
+            ++o;
+        }
+    }
+    return o;
+}
