@@ -339,6 +339,59 @@ IGS_API igs_status igs_fit2d_densify(const float* particles, const float* m, con
                                      int32_t capacity, float* out, float* out_m, float* out_v, int32_t* d_count,
                                      void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Densify / prune of the 3D Gaussians (Sec. 3.2: a particle whose A_k falls
+ * below a threshold is deleted, and particles may be divided; Sec. 2.5's
+ * multiscale property, with the Octree of Sec. 3.1 as the division pattern).
+ * ------------------------------------------------------------------------- */
+
+/* Mutable parameter arrays of n Gaussians (device, caller-owned): means_sigma
+ * [n][4] (16-byte aligned), opacity [n], color [n][C] (16-byte aligned),
+ * C = 3 (RGB) or 3 (deg + 1)^2 (SH). Also used for Adam moments. */
+typedef struct igs_params {
+    float* means_sigma;
+    float* opacity;
+    float* color;
+} igs_params;
+
+/* Densify statistic after one training step: for every Gaussian i with
+ * count[i] > 0 (it touched a tile of the view: igs_frame::count), accum[i] +=
+ * sqrt(du^2 + dv^2) of its screen-space position gradient (g2d [n][8], slots 0
+ * and 1, from igs_blend_bwd; FP32, each step rounded once) and vis[i] += 1.
+ * accum (float[n]) and vis (uint32[n]) are device, caller-owned, zeroed by the
+ * caller when an interval starts. Asynchronous. */
+IGS_API igs_status igs_grad_accum(const float* g2d, const uint32_t* count, int64_t n, float* accum, uint32_t* vis,
+                                  void* stream);
+
+/* Bytes of device scratch igs_densify needs for n Gaussians. */
+IGS_API size_t igs_densify_work_bytes(int64_t n);
+
+/* From the scene (stored parameters), its Adam moments m, v (same layout) and
+ * the statistic (accum, vis over the steps since the last densify), writes the
+ * new parameters and moments to out, out_m, out_v (device arrays of `capacity`
+ * Gaussians, caller-owned, not overlapping any input) and their number to
+ * *d_count (device int64). With parameters as stored (param_mode 1: log sigma
+ * and the opacity logit; 0: sigma and opacity), Gaussian i is
+ *   deleted  if opacity_i < op_min (op_min in the same parameterisation);
+ *   divided  else, if vis_i > 0, accum_i > tau_g * vis_i (one FP32 product)
+ *            and its scale (means_sigma slot 3) >= scale_min, into eight
+ *            children, child c at mu + (+-h, +-h, +-h) with the sign of axis a
+ *            from bit a of c ('-' for 0), h = sigma / 2 (sigma = exp(log sigma)
+ *            in double rounded to FP32, or sigma itself), child scale log sigma
+ *            - ln 2 (FP32) or sigma / 2; same opacity and colour; zero moments;
+ *   kept     otherwise, with its moments.
+ * Output in index order, children in place of their parent. When the result
+ * would exceed capacity, only the first candidates (by index) that fit divide
+ * (each adds 7); if even the kept Gaussians exceed it, the first capacity of
+ * them are written. work: igs_densify_work_bytes(n) bytes of device scratch,
+ * 16-byte aligned. Three launches, no host synchronisation.
+ * Errors: NULL, misaligned or overlapping buffers, n or capacity outside
+ * 0..2^31, a bad sh_degree or param_mode, a NaN threshold -> IGS_ERR_INVALID_ARG. */
+IGS_API igs_status igs_densify(const igs_scene* scene, const igs_params* m, const igs_params* v, int32_t sh_degree,
+                               int32_t param_mode, const float* accum, const uint32_t* vis, float op_min, float tau_g,
+                               float scale_min, int64_t capacity, const igs_params* out, const igs_params* out_m,
+                               const igs_params* out_v, int64_t* d_count, void* work, void* stream);
+
 /* Bytes of device scratch igs_quadtree_init needs (0 for an invalid size). */
 IGS_API size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell);
 

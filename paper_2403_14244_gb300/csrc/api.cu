@@ -439,6 +439,75 @@ igs_status igs_fit2d_densify(const float* particles, const float* m, const float
                        "igs_fit2d_densify");
 }
 
+igs_status igs_grad_accum(const float* g2d, const uint32_t* count, int64_t n, float* accum, uint32_t* vis,
+                          void* stream) {
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "grad_accum: n out of range");
+    if (n > 0 && (!g2d || !count || !accum || !vis)) return fail(IGS_ERR_INVALID_ARG, "grad_accum: NULL buffer");
+    if (!aligned16(g2d)) return fail(IGS_ERR_INVALID_ARG, "grad_accum: g2d must be 16-byte aligned");
+    return cuda_status(igs::launch_grad_accum3d(g2d, count, n, accum, vis, (cudaStream_t)stream), "igs_grad_accum");
+}
+
+size_t igs_densify_work_bytes(int64_t n) {
+    if (n < 0 || n >= ((int64_t)1 << 31)) return 0;
+    return igs::densify_work_bytes(n);
+}
+
+igs_status igs_densify(const igs_scene* scene, const igs_params* m, const igs_params* v, int32_t sh_degree,
+                       int32_t param_mode, const float* accum, const uint32_t* vis, float op_min, float tau_g,
+                       float scale_min, int64_t capacity, const igs_params* out, const igs_params* out_m,
+                       const igs_params* out_v, int64_t* d_count, void* work, void* stream) {
+    igs_status st;
+    if ((st = check_scene(scene))) return st;
+    if (!m || !v || !out || !out_m || !out_v || !d_count || !work)
+        return fail(IGS_ERR_INVALID_ARG, "densify: NULL argument");
+    if (sh_degree < -1 || sh_degree > 3) return fail(IGS_ERR_INVALID_ARG, "densify: sh_degree must be -1..3");
+    if (param_mode != 0 && param_mode != 1) return fail(IGS_ERR_INVALID_ARG, "densify: param_mode must be 0 or 1");
+    if (capacity < 0 || capacity >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "densify: capacity out of range");
+    if (std::isnan(op_min) || std::isnan(tau_g) || std::isnan(scale_min))
+        return fail(IGS_ERR_INVALID_ARG, "densify: NaN threshold");
+    const int64_t n = scene->n;
+    const int C = sh_degree < 0 ? 3 : 3 * (sh_degree + 1) * (sh_degree + 1);
+    if (n > 0 && (!accum || !vis || !m->means_sigma || !m->opacity || !m->color || !v->means_sigma || !v->opacity ||
+                  !v->color))
+        return fail(IGS_ERR_INVALID_ARG, "densify: NULL input array");
+    const igs_params* outs[3] = {out, out_m, out_v};
+    if (capacity > 0)
+        for (const igs_params* o : outs)
+            if (!o->means_sigma || !o->opacity || !o->color)
+                return fail(IGS_ERR_INVALID_ARG, "densify: NULL output array");
+    if (!aligned16(work)) return fail(IGS_ERR_INVALID_ARG, "densify: work must be 16-byte aligned");
+    for (const igs_params* o : {m, v, out, out_m, out_v})
+        if (!aligned16(o->means_sigma) || !aligned16(o->color))
+            return fail(IGS_ERR_INVALID_ARG, "densify: means_sigma and color arrays must be 16-byte aligned");
+    // no output array may overlap an input array
+    struct Span { const void* p; size_t bytes; };
+    const Span ins[] = {{scene->means_sigma, 16 * (size_t)n}, {scene->opacity, 4 * (size_t)n},
+                        {scene->color, 4 * (size_t)C * n},    {m->means_sigma, 16 * (size_t)n},
+                        {m->opacity, 4 * (size_t)n},          {m->color, 4 * (size_t)C * n},
+                        {v->means_sigma, 16 * (size_t)n},     {v->opacity, 4 * (size_t)n},
+                        {v->color, 4 * (size_t)C * n},        {accum, 4 * (size_t)n},
+                        {vis, 4 * (size_t)n}};
+    for (const igs_params* o : outs) {
+        const Span os[] = {{o->means_sigma, 16 * (size_t)capacity}, {o->opacity, 4 * (size_t)capacity},
+                           {o->color, 4 * (size_t)C * capacity}};
+        for (const Span& a : os)
+            for (const Span& b : ins) {
+                const char *pa = (const char*)a.p, *pb = (const char*)b.p;
+                if (pa && pb && a.bytes && b.bytes && pa < pb + b.bytes && pb < pa + a.bytes)
+                    return fail(IGS_ERR_INVALID_ARG, "densify: an output overlaps an input");
+            }
+    }
+    const float* in_p[3] = {scene->means_sigma, scene->opacity, scene->color};
+    const float* in_m[3] = {m->means_sigma, m->opacity, m->color};
+    const float* in_v[3] = {v->means_sigma, v->opacity, v->color};
+    float* out_p[3] = {out->means_sigma, out->opacity, out->color};
+    float* o_m[3] = {out_m->means_sigma, out_m->opacity, out_m->color};
+    float* o_v[3] = {out_v->means_sigma, out_v->opacity, out_v->color};
+    return cuda_status(igs::launch_densify(in_p, in_m, in_v, accum, vis, n, C, param_mode, op_min, tau_g, scale_min,
+                                           capacity, out_p, o_m, o_v, d_count, work, (cudaStream_t)stream),
+                       "igs_densify");
+}
+
 size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell) {
     if (side < 1 || side > 512 || (side & (side - 1)) || min_cell < 1) return 0;
     return igs::quadtree_work_bytes(side, min_cell);

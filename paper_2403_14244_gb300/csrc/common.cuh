@@ -166,6 +166,17 @@ struct AdamParams {
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, const AdamParams& a,
                         cudaStream_t s);
 
+// Densify / prune of the 3D Gaussians (densify.cu): the per-step statistic and the
+// keep / delete / divide pass into new buffers (arrays: means_sigma, opacity, color).
+cudaError_t launch_grad_accum3d(const float* g2d, const uint32_t* count, int64_t n, float* accum, uint32_t* vis,
+                                cudaStream_t s);
+size_t densify_work_bytes(int64_t n);
+cudaError_t launch_densify(const float* const in_p[3], const float* const in_m[3], const float* const in_v[3],
+                           const float* accum, const uint32_t* vis, int64_t n, int C, int param_mode, float op_min,
+                           float tau_g, float scale_min, int64_t capacity, float* const out_p[3],
+                           float* const out_m[3], float* const out_v[3], int64_t* d_count, void* work,
+                           cudaStream_t s);
+
 // Multi-view batch (batch.cu): per-view record in device memory (the view table).
 struct BatchView {
     ViewParams vp;

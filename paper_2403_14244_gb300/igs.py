@@ -49,6 +49,10 @@ class IgsScene(C.Structure):
     _fields_ = [("means_sigma", C.c_void_p), ("opacity", C.c_void_p), ("color", C.c_void_p), ("n", C.c_int64)]
 
 
+class IgsParams(C.Structure):
+    _fields_ = [("means_sigma", C.c_void_p), ("opacity", C.c_void_p), ("color", C.c_void_p)]
+
+
 class IgsFrame(C.Structure):
     _fields_ = [("n", C.c_int64), ("capacity", C.c_int64), ("width", C.c_int32), ("height", C.c_int32),
                 ("tile", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("sort_chunks", C.c_int32),
@@ -113,6 +117,12 @@ SYMBOLS = {
     "igs_fit2d_densify": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float,
                                     C.c_float, C.c_float, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "igs_grad_accum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "igs_densify_work_bytes": (C.c_size_t, [C.c_int64]),
+    "igs_densify": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsParams), C.POINTER(IgsParams), C.c_int32, C.c_int32,
+                              C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_int64,
+                              C.POINTER(IgsParams), C.POINTER(IgsParams), C.POINTER(IgsParams), C.c_void_p,
+                              C.c_void_p, C.c_void_p]),
     "igs_quadtree_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
     "igs_quadtree_init": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
@@ -417,6 +427,37 @@ def fit2d_densify(particles, m, v, accum, n_iters, tau_a, tau_g, log_sigma_min, 
     _check(load().igs_fit2d_densify(_ptr(particles), _ptr(m), _ptr(v), _ptr(accum), particles.shape[0], int(n_iters),
                                     float(tau_a), float(tau_g), float(log_sigma_min), out.shape[0], _ptr(out),
                                     _ptr(out_m), _ptr(out_v), _ptr(count), _stream(stream)), "igs_fit2d_densify")
+
+
+def _params(arrs):
+    p = IgsParams()
+    p.means_sigma, p.opacity, p.color = (_ptr(a).value if a.numel() else None for a in arrs)
+    return p
+
+
+def grad_accum(g2d, count, accum, vis, stream=None):
+    """Densify statistic of one step: for Gaussians with count > 0 (the frame's
+    per-Gaussian tile count), accum += |(du, dv)| from g2d [n][8] and vis += 1."""
+    n = int(accum.shape[0])
+    _check(load().igs_grad_accum(_ptr(g2d), _ptr(count), n, _ptr(accum), _ptr(vis), _stream(stream)),
+           "igs_grad_accum")
+
+
+def densify_work_bytes(n):
+    return int(load().igs_densify_work_bytes(int(n)))
+
+
+def densify(scene: Scene, m, v, sh_degree, param_mode, accum, vis, op_min, tau_g, scale_min, out, out_m, out_v,
+            count, work, stream=None):
+    """Delete / divide / keep every Gaussian of `scene` (stored parameters) with
+    its Adam moments m, v = (means_sigma, opacity, color) tensors into out,
+    out_m, out_v (same layout, capacity = out[0].shape[0]); the new count goes to
+    count (device int64)."""
+    _check(load().igs_densify(C.byref(scene.struct), C.byref(_params(m)), C.byref(_params(v)), int(sh_degree),
+                              int(param_mode), _ptr(accum), _ptr(vis), float(op_min), float(tau_g),
+                              float(scale_min), int(out[0].shape[0]), C.byref(_params(out)),
+                              C.byref(_params(out_m)), C.byref(_params(out_v)), _ptr(count), _ptr(work),
+                              _stream(stream)), "igs_densify")
 
 
 def quadtree_work_bytes(side, min_cell):

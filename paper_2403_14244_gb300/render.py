@@ -153,6 +153,11 @@ class TrainStep:
         self.t = 0
         self._img = {}
         self._dimg = {}
+        self.sh_degree = sh_degree
+        self.device = device
+        self.tile, self.footprint = tile, footprint
+        self.accum = None    # densify statistic (summed screen-space position-gradient norms), when tracked
+        self.vis = None      # steps in which each Gaussian touched a tile
 
     def _views(self, flat):
         n, C = self.n, self.C
@@ -191,6 +196,8 @@ class TrainStep:
             mark("l1")
         igs.blend_bwd(frame, r.opts, dimg, self.g2d, stream)
         mark("blend_bwd")
+        if self.accum is not None:
+            igs.grad_accum(self.g2d, frame.count(), self.accum, self.vis, stream)
         self.t += 1
         if self.fused:
             igs.project_bwd_adam(self.scene, c, r.opts, frame, self.g2d, self.m_views, self.v_views, self.t,
@@ -202,3 +209,58 @@ class TrainStep:
             igs.adam(self.flat, self.grad, self.m, self.v, self.t, lr=self.lr, stream=stream)
             mark("adam")
         return frame
+
+    def track_grad_norm(self):
+        """Start (or restart) the densify statistic: every later step adds each
+        visible Gaussian's screen-space position-gradient norm to accum and one
+        to vis."""
+        self.accum = torch.zeros(self.n, dtype=torch.float32, device=self.flat.device)
+        self.vis = torch.zeros(self.n, dtype=torch.int32, device=self.flat.device)
+
+    def densify(self, op_min, tau_g, scale_min, capacity):
+        """Delete Gaussians whose stored opacity logit is below op_min, divide those
+        whose mean screen-space gradient norm since track_grad_norm() exceeds tau_g
+        (and whose log sigma >= scale_min) into eight half-scale children, within
+        `capacity` Gaussians (libigs's igs_densify); parameters and Adam moments
+        move to new flat buffers. Reads the new count back (one synchronisation);
+        the Adam step count continues. The next step of each view should run with
+        check=True (the entry capacity of the new scene is not known yet)."""
+        if self.accum is None:
+            raise RuntimeError("densify needs track_grad_norm() first")
+        dev = self.flat.device
+        cap = int(capacity)
+        C = self.C
+        outs = [(torch.empty((cap, 4), device=dev), torch.empty(cap, device=dev), torch.empty((cap, C), device=dev))
+                for _ in range(3)]
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        work = torch.empty(igs.densify_work_bytes(self.n), dtype=torch.uint8, device=dev)
+        igs.densify(self.scene, self.m_views, self.v_views, self.sh_degree, 1, self.accum, self.vis, op_min, tau_g,
+                    scale_min, outs[0], outs[1], outs[2], count, work)
+        k = int(count.item())
+        self._relayout(k, outs)
+        self.track_grad_norm()
+        return k
+
+    def _relayout(self, n, arrays):
+        """New flat buffers for n Gaussians, filled from (params, m, v) arrays."""
+        self.n = n
+        a = lambda x: (x + 63) // 64 * 64  # noqa: E731
+        self.o_op = a(4 * n)
+        self.o_col = a(self.o_op + n)
+        size = a(self.o_col + self.C * n)
+        dev = self.flat.device
+        self.flat = torch.zeros(size, dtype=torch.float32, device=dev)
+        self.grad = torch.zeros_like(self.flat)
+        self.m = torch.zeros_like(self.flat)
+        self.v = torch.zeros_like(self.flat)
+        for flat, (ms, op, col) in zip((self.flat, self.m, self.v), arrays):
+            a_ms, a_op, a_col = self._views(flat)
+            a_ms.copy_(ms[:n])
+            a_op.copy_(op[:n])
+            a_col.copy_(col[:n])
+        self.ms, self.op, self.col = self._views(self.flat)
+        self.g_ms, self.g_op, self.g_col = self._views(self.grad)
+        self.m_views = self._views(self.m)
+        self.v_views = self._views(self.v)
+        self.scene = igs.Scene(self.ms, self.op, self.col)
+        self.g2d = torch.empty((n, 8), dtype=torch.float32, device=dev)
