@@ -333,6 +333,7 @@ def run_mine(args, world, rank, local):
         extra["train_step_l1_ssim"] = run_ssim_steps(ts, cam_s, targets, stream, dev, min(args.steps, 100),
                                                      peak_hbm)
     if not args.no_extra:
+        extra["densify_3M"] = run_densify3d(ts, cam_s, targets, stream, dev, peak_hbm)
         extra.update(run_extra(dev, np))
 
     result = {
@@ -358,6 +359,74 @@ def run_mine(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_densify3d(ts, cam_s, targets, stream, dev, peak_hbm, steps=32, reps=3):
+    """Densify / prune of the training scene: the cost of the per-step statistic
+    (steps/s with and without it), and one keep / delete / divide pass
+    (igs_densify) over all Gaussians after `steps` tracked steps: delete opacity
+    below 0.005, divide the Gaussians whose mean screen-space gradient norm is in
+    the top tenth of those with a non-zero gradient (threshold read on the host)
+    and whose sigma >= 0.01, capacity
+    2n. Bandwidth over the pass's algorithmic bytes: 28 B per Gaussian twice
+    (flags: opacity, statistic, scale), 2 x 636 B per kept Gaussian (parameters
+    and moments read and written), 212 + 8 x 636 B per divided one."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2403_14244_gb300 import igs
+
+    V = len(cam_s)
+
+    def timed(n_steps):
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(n_steps):
+            ts.step(cam_s[k % V], targets[k % V])
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / n_steps
+
+    plain_ms = timed(steps)
+    ts.track_grad_norm()
+    tracked_ms = timed(steps)
+    n, C = ts.n, ts.C
+    acc, vis = ts.accum.cpu().numpy(), ts.vis.cpu().numpy().view(np.uint32)
+    moved = (vis > 0) & (acc > 0)
+    tau_g = float(np.quantile(acc[moved] / vis[moved], 0.9)) if moved.any() else 0.0
+    op_min, scale_min = math.log(0.005 / 0.995), math.log(0.01)
+    cap = 2 * n
+    outs = [(torch.empty((cap, 4), device=dev), torch.empty(cap, device=dev), torch.empty((cap, C), device=dev))
+            for _ in range(3)]
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    work = torch.empty(igs.densify_work_bytes(n), dtype=torch.uint8, device=dev)
+    args = (ts.scene, ts.m_views, ts.v_views, 3, 1, ts.accum, ts.vis, op_min, tau_g, scale_min, outs[0], outs[1],
+            outs[2], count, work)
+    igs.densify(*args)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        igs.densify(*args, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / reps
+    k = int(count.item())
+    op = ts.op.cpu().numpy()
+    kept = int((~(op < op_min)).sum())
+    divided = (k - kept) // 7
+    row = 4 * (5 + C)
+    nbytes = 2 * 28 * n + 2 * 3 * row * (kept - divided) + divided * (row + 8 * 3 * row)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    ts.accum = ts.vis = None
+    return {"n": n, "steps_tracked": steps, "step_ms": round(plain_ms, 4), "step_ms_with_statistic":
+            round(tracked_ms, 4), "tau_g": tau_g, "with_gradient": int(moved.sum()), "kept": kept, "deleted": n - kept, "divided": divided,
+            "out": k, "densify_ms": round(ms, 4),
+            "roofline": {"bound": "hbm", "bytes": nbytes, "achieved": round(gbs, 1), "peak": peak_hbm,
+                         "unit": "GB/s", "frac": round(gbs / peak_hbm, 4)}}
 
 
 def run_ssim_steps(ts, cam_s, targets, stream, dev, steps, peak_hbm, lam=0.2):

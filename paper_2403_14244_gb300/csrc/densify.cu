@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(kDensScanThreads) k_dens_scan(const uint2* __r
     }
 }
 
+template <int C>
 __global__ void __launch_bounds__(kDensThreads) k_dens_write(DensIn in, DensOut out, DensParams P,
                                                              const unsigned long long* __restrict__ base,
                                                              const long long* __restrict__ meta) {
@@ -202,7 +203,6 @@ __global__ void __launch_bounds__(kDensThreads) k_dens_write(DensIn in, DensOut 
     const long long allowed = meta[0], cap = P.capacity;
     long long slot = (long long)base[2 * blockIdx.x];
     long long crank = (long long)base[2 * blockIdx.x + 1];
-    const int C = P.C;
     for (int r = 0; r < kDensRounds; ++r) {
         const int64_t r0 = b0 + r * kDensThreads;
         if (r0 >= P.n) break;
@@ -336,7 +336,13 @@ cudaError_t launch_densify(const float* const in_p[3], const float* const in_m[3
     k_dens_scan<<<1, kDensScanThreads, 0, st>>>(blk, blocks, P, base, meta, d_count);
     count_launches();
     if (n > 0) {
-        k_dens_write<<<(unsigned)blocks, kDensThreads, 0, st>>>(in, out, P, base, meta);
+        switch (C) {  // colour floats per Gaussian: a compile-time row length for the cooperative copies
+            case 3: k_dens_write<3><<<(unsigned)blocks, kDensThreads, 0, st>>>(in, out, P, base, meta); break;
+            case 12: k_dens_write<12><<<(unsigned)blocks, kDensThreads, 0, st>>>(in, out, P, base, meta); break;
+            case 27: k_dens_write<27><<<(unsigned)blocks, kDensThreads, 0, st>>>(in, out, P, base, meta); break;
+            case 48: k_dens_write<48><<<(unsigned)blocks, kDensThreads, 0, st>>>(in, out, P, base, meta); break;
+            default: return cudaErrorInvalidValue;
+        }
         count_launches();
     }
     return cudaGetLastError();
