@@ -82,9 +82,9 @@ __device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, float4 a4, c
     return true;
 }
 
-// Two pixels per thread: warp w holds rows [w 2R, w 2R + 2R) of the tile (R =
-// 32 / TS), pixel A in the first R rows and pixel B R rows below, so one warp
-// reduction per entry serves 64 pixels.
+// Two pixels per thread: warp w holds an 8 x 8 block of the tile, pixel A in its
+// upper 8 x 4 half and pixel B four rows below, so one warp reduction per entry
+// serves 64 pixels (a compact block is reached by fewer entries than whole rows).
 template <int TS>
 __global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                       const float4* __restrict__ rec, BlendParams P,
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(cons
                                                       float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
     constexpr int NT = TS * TS / 2;
     constexpr int NW = NT / 32;
-    constexpr int R = 32 / TS;
+    constexpr int BPR = TS / 8;  // 8 x 8 warp blocks per block row of the tile
     constexpr int BB = bwd_batch<TS>();
     constexpr int NBW = BB / 32;  // ballot words per warp
     __shared__ float4 s_a[BB];
@@ -106,10 +106,11 @@ __global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(cons
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x;
     const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-    const int x = tx * TS + (lane % TS);
-    const int yA = ty * TS + w * 2 * R + lane / TS, yB = yA + R;
-    const float bx0 = (float)(tx * TS) + 0.5f, bx1 = bx0 + (float)(TS - 1);
-    const float by0 = (float)(ty * TS + w * 2 * R) + 0.5f, by1 = by0 + (float)(2 * R - 1);
+    const int bx = tx * TS + (w % BPR) * 8, by = ty * TS + (w / BPR) * 8;  // the warp's block
+    const int x = bx + (lane & 7);
+    const int yA = by + (lane >> 3), yB = yA + 4;
+    const float bx0 = (float)bx + 0.5f, bx1 = bx0 + 7.f;
+    const float by0 = (float)by + 0.5f, by1 = by0 + 7.f;
     const uint2 rg = ranges[tile];
     const size_t plane = (size_t)P.width * P.height;
     BwdPixel q[2];

@@ -39,10 +39,12 @@ __device__ __forceinline__ bool may_reach(float4 a, float xlo, float xhi, float 
 
 // One CTA of TS*TS threads composites one tile (one thread per pixel), staging
 // B entries at a time in shared memory (s_a, s_c hold B float4 each), and leaves
-// the batch loop once every pixel has stopped. Each warp owns 32 / TS rows of the
-// tile and walks, in order, only the staged entries that may reach them (one
-// ballot per 32 entries). Writes img (planar, `plane` floats per channel, row
-// stride `width`) and, if given, T_final / n_contrib.
+// the batch loop once every pixel has stopped. Each warp owns an 8 x 4 block of
+// the tile (compact blocks are reached by fewer entries than whole rows, and
+// their pixels stop at similar depths) and walks, in order, only the staged
+// entries that may reach it (one ballot per 32 entries). Writes img (planar,
+// `plane` floats per channel, row stride `width`) and, if given, T_final /
+// n_contrib.
 template <int TS, int B>
 __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int height, uint2 rg,
                                                const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
@@ -50,16 +52,17 @@ __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int he
                                                float4* s_a, float4* s_c, float* __restrict__ img,
                                                float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
     constexpr int NT = TS * TS;
-    constexpr int ROWS = 32 / TS;  // rows of the tile per warp
+    constexpr int BPR = TS / 8;  // 8 x 4 warp blocks per block row of the tile
     static_assert(B <= NT, "staging batch larger than the tile");
-    static_assert(TS >= 8 && TS <= 32, "a warp covers whole rows of the tile");
-    const int lane = threadIdx.x & 31;
-    const int x = tx * TS + (threadIdx.x % TS), y = ty * TS + (threadIdx.x / TS);
+    static_assert(TS >= 8 && TS <= 32, "the tile holds whole 8 x 4 warp blocks");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int bx = tx * TS + (w % BPR) * 8, by = ty * TS + (w / BPR) * 4;  // the warp's block
+    const int x = bx + (lane & 7), y = by + (lane >> 3);
     const bool inside = x < width && y < height;
     const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-    // pixel centres of this warp's rows
-    const float bx0 = (float)(tx * TS) + 0.5f, bx1 = bx0 + (float)(TS - 1);
-    const float by0 = (float)(ty * TS + (threadIdx.x >> 5) * ROWS) + 0.5f, by1 = by0 + (float)(ROWS - 1);
+    // pixel centres of this warp's block
+    const float bx0 = (float)bx + 0.5f, bx1 = bx0 + 7.f;
+    const float by0 = (float)by + 0.5f, by1 = by0 + 3.f;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
     bool done = !inside;
