@@ -95,8 +95,12 @@ def stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm):
     for s, ms in stage_ms.items():
         bound, nbytes = model[s]
         gbs = nbytes / (ms / 1e3) / 1e9
-        out.append({"stage": s, "ms": round(ms, 4), "share": round(ms / total, 4), "bound": bound,
-                    "bytes": int(nbytes), "achieved": round(gbs, 1), "frac": round(gbs / peak_hbm, 4)})
+        row = {"stage": s, "ms": round(ms, 4), "share": round(ms / total, 4), "bound": bound, "bytes": int(nbytes)}
+        if bound == "hbm":
+            row.update({"achieved": round(gbs, 1), "frac": round(gbs / peak_hbm, 4)})
+        else:  # issue-bound: the bytes (mostly L2 gathers) are context, not a roofline
+            row.update({"bytes_per_s_context": round(gbs, 1), "frac": None})
+        out.append(row)
     return out
 
 

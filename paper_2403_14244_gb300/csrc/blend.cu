@@ -82,15 +82,16 @@ __device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, float4 a4, c
     return true;
 }
 
-// Two pixels per thread: warp w holds an 8 x 8 block of the tile, pixel A in its
-// upper 8 x 4 half and pixel B four rows below, so one warp reduction per entry
-// serves 64 pixels (a compact block is reached by fewer entries than whole rows).
+// Two pixels per thread: warp w holds an 8 x 8 block of the TS x TS pixel tile
+// (tx, ty), pixel A in its upper 8 x 4 half and pixel B four rows below, so one
+// warp reduction per entry serves 64 pixels (a compact block is reached by fewer
+// entries than whole rows). rg: the entries to walk (those of the tile, or of an
+// enclosing binning tile).
 template <int TS>
-__global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                                                      const float4* __restrict__ rec, BlendParams P,
-                                                      const float* __restrict__ dL, const float* __restrict__ T_final,
-                                                      const uint32_t* __restrict__ n_contrib,
-                                                      float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
+__device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const uint32_t* __restrict__ vals,
+                                               const float4* __restrict__ rec, const BlendParams& P,
+                                               const float* __restrict__ dL, const float* __restrict__ T_final,
+                                               const uint32_t* __restrict__ n_contrib, float4* __restrict__ g2d) {
     constexpr int NT = TS * TS / 2;
     constexpr int NW = NT / 32;
     constexpr int BPR = TS / 8;  // 8 x 8 warp blocks per block row of the tile
@@ -102,16 +103,12 @@ __global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(cons
     __shared__ float s_red[NW][BB][8];
     __shared__ uint32_t s_bits[NW][NBW];
     __shared__ uint32_t s_max;
-    if (info[kInfoAbort]) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tile = blockIdx.x;
-    const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
     const int bx = tx * TS + (w % BPR) * 8, by = ty * TS + (w / BPR) * 8;  // the warp's block
     const int x = bx + (lane & 7);
     const int yA = by + (lane >> 3), yB = yA + 4;
     const float bx0 = (float)bx + 0.5f, bx1 = bx0 + 7.f;
     const float by0 = (float)by + 0.5f, by1 = by0 + 7.f;
-    const uint2 rg = ranges[tile];
     const size_t plane = (size_t)P.width * P.height;
     BwdPixel q[2];
 #pragma unroll
@@ -155,7 +152,7 @@ __global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(cons
         __syncthreads();
 #pragma unroll
         for (int hw = 0; hw < NBW; ++hw) {
-            // the entries this warp may have blended: before its last contributor, reaching its rows
+            // the entries this warp may have blended: before its last contributor, reaching its block
             const int kl = hw * 32 + lane;
             const bool reach = kl < nb && hi - 1 - kl - rg.x < wmax && may_reach(s_a[kl], bx0, bx1, by0, by1);
             uint32_t bits = __ballot_sync(0xffffffffu, reach);
@@ -197,6 +194,55 @@ __global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(cons
     }
 }
 
+template <int TS>
+__global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                                      const float4* __restrict__ rec, BlendParams P,
+                                                      const float* __restrict__ dL, const float* __restrict__ T_final,
+                                                      const uint32_t* __restrict__ n_contrib,
+                                                      float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
+    if (info[kInfoAbort]) return;
+    const int tile = blockIdx.x;
+    blend_tile_bwd<TS>(tile % P.tiles_x, tile / P.tiles_x, ranges[tile], vals, rec, P, dL, T_final, n_contrib, g2d);
+}
+
+// Sub-tile kernels: one CTA per 8 x 8 pixel block of a TS x TS binning tile,
+// walking the binning tile's entries; each block stops on its own (its
+// pixels' last contributors), and entries that miss it cost one reach test.
+// Per pixel the walk, the arithmetic and the result are those of the whole-tile
+// kernels.
+template <int TS>
+__global__ void __launch_bounds__(64) k_blend_fwd_sub(const uint2* __restrict__ ranges,
+                                                      const uint32_t* __restrict__ vals,
+                                                      const float4* __restrict__ rec, BlendParams P,
+                                                      float* __restrict__ img, float* __restrict__ T_final,
+                                                      uint32_t* __restrict__ n_contrib,
+                                                      const uint32_t* __restrict__ info) {
+    constexpr int SUB = TS / 8;
+    __shared__ float4 s_a[64];
+    __shared__ float4 s_c[64];
+    if (info[kInfoAbort]) return;
+    const int tile = blockIdx.x / (SUB * SUB), q = blockIdx.x % (SUB * SUB);
+    const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+    blend_tile_fwd<8, 64>(tx * SUB + q % SUB, ty * SUB + q / SUB, P.width, P.height, ranges[tile], vals, rec,
+                          P.alpha_min, P.alpha_max, P.t_min, P.bg, s_a, s_c, img, T_final, n_contrib);
+}
+
+template <int TS>
+__global__ void __launch_bounds__(32, 32) k_blend_bwd_sub(const uint2* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ vals,
+                                                          const float4* __restrict__ rec, BlendParams P,
+                                                          const float* __restrict__ dL,
+                                                          const float* __restrict__ T_final,
+                                                          const uint32_t* __restrict__ n_contrib,
+                                                          float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
+    constexpr int SUB = TS / 8;
+    if (info[kInfoAbort]) return;
+    const int tile = blockIdx.x / (SUB * SUB), q = blockIdx.x % (SUB * SUB);
+    const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+    blend_tile_bwd<8>(tx * SUB + q % SUB, ty * SUB + q / SUB, ranges[tile], vals, rec, P, dL, T_final, n_contrib,
+                      g2d);
+}
+
 }  // namespace
 
 cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t st) {
@@ -206,7 +252,7 @@ cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* i
     auto rec = reinterpret_cast<const float4*>(f.rec);
     switch (f.tile) {
         case 8: k_blend_fwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
-        case 16: k_blend_fwd<16><<<tiles, 256, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        case 16: k_blend_fwd_sub<16><<<tiles * 4, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
         case 32: k_blend_fwd<32><<<tiles, 1024, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
         default: return cudaErrorInvalidValue;
     }
@@ -222,7 +268,7 @@ cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const fl
     auto g = reinterpret_cast<float4*>(g2d);
     switch (f.tile) {
         case 8: k_blend_bwd<8><<<tiles, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 16: k_blend_bwd<16><<<tiles, 128, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 16: k_blend_bwd_sub<16><<<tiles * 4, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
         case 32: k_blend_bwd<32><<<tiles, 512, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
         default: return cudaErrorInvalidValue;
     }
