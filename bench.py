@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the 1080p forward / fwd+bwd lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--tile", type=int, default=32, choices=(8, 16, 32),
+                    help="binning tile edge in pixels (the blends run per 8 x 8 block of it)")
     ap.add_argument("--footprint", type=int, default=0, choices=(0, 1),
                     help="tiles of a Gaussian: 0 its bounding rectangle, 1 the tiles its disc meets")
     ap.add_argument("--ssim", type=float, default=0.0,
@@ -208,7 +210,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------- GPU arm --------
 
-def build_workload(n, device, footprint=0):
+def build_workload(n, device, footprint=0, tile=32):
     import numpy as np
     import torch
 
@@ -217,7 +219,7 @@ def build_workload(n, device, footprint=0):
 
     sc, cams = scenes.workload_train_3m(n=n)
     ts = TrainStep(torch.from_numpy(sc.means_sigma).to(device), torch.from_numpy(sc.opacity).to(device),
-                   torch.from_numpy(sc.color).to(device), sh_degree=3, tile=16, lr=1e-3, device=device,
+                   torch.from_numpy(sc.color).to(device), sh_degree=3, tile=tile, lr=1e-3, device=device,
                    footprint=footprint)
     targets_host = [torch.from_numpy(scenes.train_target(k)).pin_memory() for k in range(len(cams))]
     targets = [t.to(device) for t in targets_host]
@@ -236,7 +238,7 @@ def run_mine(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     igs.load()
-    sc, cams, cam_s, ts, targets, targets_host, np = build_workload(args.n, dev, args.footprint)
+    sc, cams, cam_s, ts, targets, targets_host, np = build_workload(args.n, dev, args.footprint, args.tile)
     ts.ssim_lambda = args.ssim
     STAGES = STAGES_L1 if args.ssim == 0 else STAGES_SSIM
     V = len(cams)
@@ -338,14 +340,14 @@ def run_mine(args, world, rank, local):
                                                      peak_hbm)
     if not args.no_extra:
         extra["densify_3M"] = run_densify3d(ts, cam_s, targets, stream, dev, peak_hbm)
-        extra.update(run_extra(dev, np))
+        extra.update(run_extra(dev, np, args.tile))
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators, no dataset)",
         "config": {"workload": WORKLOAD, "n_gaussians": n, "sh_degree": 3, "image": [cams[0].width, cams[0].height],
-                   "views": V, "tile": 16, "footprint": "rectangle" if args.footprint == 0 else "disc rows",
+                   "views": V, "tile": args.tile, "footprint": "rectangle" if args.footprint == 0 else "disc rows",
                    "optimizer": "adam lr 1e-3", "params": "mu, log sigma, logit o, SH",
                    "loss": "l1" if args.ssim == 0 else f"(1 - {args.ssim}) l1 + {args.ssim} (1 - ssim)",
                    "l2": "no flush: per-step working set 2.5 GB > 129 MB L2",
@@ -472,7 +474,7 @@ def run_ssim_steps(ts, cam_s, targets, stream, dev, steps, peak_hbm, lam=0.2):
                                  "unit": "GB/s", "frac": round(gbs / peak_hbm, 4)}}
 
 
-def run_extra(dev, np):
+def run_extra(dev, np, tile=32):
     """1080p forward frames/s and fwd+bwd steps/s on the 1M clustered SH3 scene."""
     import torch
 
@@ -481,7 +483,7 @@ def run_extra(dev, np):
 
     sc, cam, target = scenes.workload_fwd_bwd_1m()
     scene = igs.Scene.from_numpy(sc, dev)
-    r = Renderer(tile=16, sh_degree=3, param_mode=0, device=dev)
+    r = Renderer(tile=tile, sh_degree=3, param_mode=0, device=dev)
     c = igs.camera(cam)
     img, f = r.run_forward(scene, c, check=True)
     tg = torch.from_numpy(target).to(dev)
@@ -649,7 +651,7 @@ def run_batched(dev, reps=10):
     scene = igs.Scene.from_numpy(sc, dev)
     cams = [igs.camera(c) for c in scenes.sphere_cameras(32, 4)]
     cache = os.environ.get("IGS_AUTOTUNE_CACHE")  # where to keep the tuner's choice, if anywhere
-    (tile, bb), timings = autotune(scene, cams, candidates=[(8, 64), (16, 128), (16, 256), (32, 512)], reps=3,
+    (tile, bb), timings = autotune(scene, cams, candidates=[(8, 64), (16, 64), (16, 256), (32, 64), (32, 512)], reps=3,
                                    cache_path=cache, use_cache=False, device=dev)
     br = BatchRenderer(scene, cams, tile=tile, blend_batch=bb, device=dev)
     br.capture()

@@ -468,7 +468,10 @@ typedef struct igs_batch {
 /* Lay out a batch for n Gaussians and the V cameras' image sizes (the poses may
  * change later, the sizes may not). capacity = entries over all views;
  * blend_batch = entries per shared-memory batch of the blend: 32 or 64 for tile
- * 8, 64, 128 or 256 for tile 16, 256, 512 or 1024 for tile 32 (0 = tile^2).
+ * 8, 64, 128 or 256 for tile 16, 64, 256, 512 or 1024 for tile 32 (0 = tile^2).
+ * 64 with tile 16 or 32 selects the sub-tile blend: one 64-thread CTA per 8 x 8
+ * pixel block, walking its tile's entries and stopping on its own (not
+ * persistent); the others run the persistent whole-tile blend.
  * Requires V n < 2^32. workspace == NULL: only *bytes. Host-only, no launch. */
 IGS_API igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, const igs_opts* opts,
                                     int64_t capacity, int32_t blend_batch, void* workspace, size_t* bytes,

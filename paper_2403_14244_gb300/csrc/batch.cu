@@ -278,31 +278,70 @@ __global__ void __launch_bounds__(TS* TS) k_blend_persistent(const uint2* __rest
     }
 }
 
+// Sub-tile blend: one 64-thread CTA per 8 x 8 pixel block of every view's
+// binning tiles (item w: tile w / (TS/8)^2, block w % (TS/8)^2), walking the
+// tile's entries; each block stops on its own. The hardware block scheduler
+// balances the mixed view sizes, so the launch is not persistent.
+template <int TS>
+__global__ void __launch_bounds__(64) k_blend_batch_sub(const uint2* __restrict__ ranges,
+                                                        const uint32_t* __restrict__ vals,
+                                                        const float4* __restrict__ rec,
+                                                        const BatchView* __restrict__ views, int V,
+                                                        uint32_t tiles_total, BlendParams P,
+                                                        float* __restrict__ images, uint32_t* __restrict__ work,
+                                                        const uint32_t* __restrict__ info) {
+    constexpr int SUB = TS / 8, NS = SUB * SUB;
+    __shared__ float4 s_a[64];
+    __shared__ float4 s_c[64];
+    if (info[kInfoAbort]) return;
+    const uint32_t w = blockIdx.x / NS, q = blockIdx.x % NS;
+    int lo = 0, hi = V;  // view: largest v with tile_base[v] <= w
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (views[mid].tile_base <= w) lo = mid; else hi = mid;
+    }
+    const ViewParams& vp = views[lo].vp;
+    const uint32_t t = w - views[lo].tile_base;
+    const int tx = (int)(t % (uint32_t)vp.tiles_x), ty = (int)(t / (uint32_t)vp.tiles_x);
+    blend_tile_fwd<8, 64>(tx * SUB + (int)(q % SUB), ty * SUB + (int)(q / SUB), vp.width, vp.height, ranges[w], vals,
+                          rec, P.alpha_min, P.alpha_max, P.t_min, P.bg, s_a, s_c, images + views[lo].img_off, nullptr,
+                          nullptr);
+}
+
 template <int TS, int B>
 void* persistent_kernel() {
     return reinterpret_cast<void*>(k_blend_persistent<TS, B>);
 }
 
-// The blend variants the batch path (and its autotuner) can pick.
-bool blend_variant(int tile, int batch, void** fn) {
+// The blend variants the batch path (and its autotuner) can pick: a staging
+// depth of 64 with 16- or 32-pixel tiles selects the sub-tile blend (`sub`:
+// one CTA of 64 threads per 8 x 8 block), the others the persistent whole-tile
+// blend.
+bool blend_variant(int tile, int batch, void** fn, bool* sub = nullptr) {
+    bool sb = false;
     switch (tile * 10000 + batch) {
-        case 8 * 10000 + 32: *fn = persistent_kernel<8, 32>(); return true;
-        case 8 * 10000 + 64: *fn = persistent_kernel<8, 64>(); return true;
-        case 16 * 10000 + 64: *fn = persistent_kernel<16, 64>(); return true;
-        case 16 * 10000 + 128: *fn = persistent_kernel<16, 128>(); return true;
-        case 16 * 10000 + 256: *fn = persistent_kernel<16, 256>(); return true;
-        case 32 * 10000 + 256: *fn = persistent_kernel<32, 256>(); return true;
-        case 32 * 10000 + 512: *fn = persistent_kernel<32, 512>(); return true;
-        case 32 * 10000 + 1024: *fn = persistent_kernel<32, 1024>(); return true;
+        case 8 * 10000 + 32: *fn = persistent_kernel<8, 32>(); break;
+        case 8 * 10000 + 64: *fn = persistent_kernel<8, 64>(); break;
+        case 16 * 10000 + 64: *fn = reinterpret_cast<void*>(k_blend_batch_sub<16>); sb = true; break;
+        case 16 * 10000 + 128: *fn = persistent_kernel<16, 128>(); break;
+        case 16 * 10000 + 256: *fn = persistent_kernel<16, 256>(); break;
+        case 32 * 10000 + 64: *fn = reinterpret_cast<void*>(k_blend_batch_sub<32>); sb = true; break;
+        case 32 * 10000 + 256: *fn = persistent_kernel<32, 256>(); break;
+        case 32 * 10000 + 512: *fn = persistent_kernel<32, 512>(); break;
+        case 32 * 10000 + 1024: *fn = persistent_kernel<32, 1024>(); break;
         default: return false;
     }
+    if (sub) *sub = sb;
+    return true;
 }
 
 }  // namespace
 
 int batch_persistent_blocks(int tile, int batch) {
     void* fn = nullptr;
-    if (!blend_variant(tile, batch, &fn)) return 0;
+    bool sub = false;
+    if (!blend_variant(tile, batch, &fn, &sub)) return 0;
+    if (sub) return 1;  // not persistent: one CTA per 8 x 8 block
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
@@ -488,15 +527,18 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const B
     }
     // 7. persistent blend over every (view, tile)
     void* fn = nullptr;
-    if (!blend_variant(b.tile, b.blend_batch, &fn)) return cudaErrorInvalidValue;
-    const unsigned nblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(b.persistent_blocks, b.tiles_total));
+    bool sub = false;
+    if (!blend_variant(b.tile, b.blend_batch, &fn, &sub)) return cudaErrorInvalidValue;
+    const int64_t per_tile = sub ? (int64_t)(b.tile / 8) * (b.tile / 8) : 1;
+    const unsigned nblocks = (unsigned)(sub ? std::max<int64_t>(1, b.tiles_total * per_tile)
+                                            : std::max<int64_t>(1, std::min<int64_t>(b.persistent_blocks, b.tiles_total)));
     const float4* recp = reinterpret_cast<const float4*>(b.rec);
     const uint2* rg = reinterpret_cast<const uint2*>(b.ranges);
     uint32_t tt = (uint32_t)b.tiles_total;
     BlendParams bpp = bp;
     void* args[] = {(void*)&rg, (void*)&b.vals, (void*)&recp, (void*)&s.views, (void*)&V, (void*)&tt, (void*)&bpp,
                     (void*)&images, (void*)&s.work, (void*)&b.info};
-    CK(cudaLaunchKernel(fn, dim3(nblocks), dim3(b.tile * b.tile), args, 0, st));
+    CK(cudaLaunchKernel(fn, dim3(nblocks), dim3(sub ? 64 : b.tile * b.tile), args, 0, st));
     count_launches();
 #undef CK
     return cudaSuccess;

@@ -253,7 +253,7 @@ cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* i
     switch (f.tile) {
         case 8: k_blend_fwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
         case 16: k_blend_fwd_sub<16><<<tiles * 4, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
-        case 32: k_blend_fwd<32><<<tiles, 1024, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        case 32: k_blend_fwd_sub<32><<<tiles * 16, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();
@@ -269,7 +269,7 @@ cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const fl
     switch (f.tile) {
         case 8: k_blend_bwd<8><<<tiles, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
         case 16: k_blend_bwd_sub<16><<<tiles * 4, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 32: k_blend_bwd<32><<<tiles, 512, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 32: k_blend_bwd_sub<32><<<tiles * 16, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();

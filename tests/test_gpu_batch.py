@@ -29,7 +29,7 @@ def _single(scene_np, cam, tile, footprint=0):
     return _gpu.run_forward(scene_np, cam, tile=tile, footprint=footprint)[3]
 
 
-@pytest.mark.parametrize("tile,bb,footprint", [(16, 0, 0), (16, 64, 0), (8, 32, 0), (32, 512, 0), (16, 128, 1),
+@pytest.mark.parametrize("tile,bb,footprint", [(16, 0, 0), (16, 64, 0), (8, 32, 0), (32, 512, 0), (32, 64, 0), (16, 128, 1),
                                                (8, 64, 1)])
 def test_batch_bit_identical_to_single_renders(tile, bb, footprint):
     sc = scenes.uniform_scene(200_000, 41)
