@@ -239,6 +239,20 @@ IGS_API igs_status igs_project_bwd_adam(const igs_scene* scene, const igs_camera
                                         float* v_color, double lr, double b1, double b2, double eps, int64_t step,
                                         void* stream);
 
+/* igs_project_bwd_adam with the Adam step count on the device, so that a
+ * training step can be captured in a CUDA graph and replayed: d_state (device
+ * int32[4], 16-byte aligned, zero before the first step, caller-owned) holds
+ * the count of steps taken; the call first advances it (t = d_state[0] + 1,
+ * stored back) and writes that step's bias-corrected constants (lr / (1 - b1^t),
+ * 1 / sqrt(1 - b2^t), sqrt(1 - b2^t), formed in double, rounded to FP32) to
+ * d_state[1..3], then applies the same update as igs_project_bwd_adam. Two
+ * launches; errors as igs_project_bwd_adam, plus a NULL or misaligned d_state. */
+IGS_API igs_status igs_project_bwd_adam_dev(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                            const igs_frame* frame, const float* g2d, float* m_means_sigma,
+                                            float* m_opacity, float* m_color, float* v_means_sigma, float* v_opacity,
+                                            float* v_color, double lr, double b1, double b2, double eps,
+                                            int32_t* d_state, void* stream);
+
 /* L1 loss of Sec. 3 (lambda = 0): loss = mean |img - target| over `count`
  * entries, written to *loss (device float, overwritten), and
  * dL_dimg = sign(img - target) / count (device, count entries; sign(0) = 0). */

@@ -282,6 +282,7 @@ static igs_status adam_params(double lr, double b1, double b2, double eps, int64
     a->bc2_sqrt = (float)std::sqrt(bc2);
     a->inv_bc2_sqrt = (float)(1.0 / std::sqrt(bc2));
     a->eps = (float)eps;
+    a->dev_consts = nullptr;
     return IGS_OK;
 }
 
@@ -305,6 +306,33 @@ igs_status igs_project_bwd_adam(const igs_scene* scene, const igs_camera* cam, c
     return cuda_status(igs::launch_project_bwd_adam(*scene, vp, *frame, g2d, m_means_sigma, m_opacity, m_color,
                                                     v_means_sigma, v_opacity, v_color, a, (cudaStream_t)stream),
                        "igs_project_bwd_adam");
+}
+
+igs_status igs_project_bwd_adam_dev(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                    const igs_frame* frame, const float* g2d, float* m_means_sigma, float* m_opacity,
+                                    float* m_color, float* v_means_sigma, float* v_opacity, float* v_color, double lr,
+                                    double b1, double b2, double eps, int32_t* d_state, void* stream) {
+    if (!d_state || (reinterpret_cast<uintptr_t>(d_state) & 15))
+        return fail(IGS_ERR_INVALID_ARG, "d_state must be a 16-byte aligned device buffer of 4 words");
+    igs_status st;
+    if ((st = check_scene(scene)) || (st = check_camera(cam)) || (st = check_opts(opts)) || (st = check_frame(frame)) ||
+        (st = frame_matches(frame, scene, cam, opts)))
+        return st;
+    if (!g2d || !m_means_sigma || !m_opacity || !m_color || !v_means_sigma || !v_opacity || !v_color)
+        return fail(IGS_ERR_INVALID_ARG, "g2d or an Adam moment buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(g2d) | reinterpret_cast<uintptr_t>(m_means_sigma) |
+         reinterpret_cast<uintptr_t>(v_means_sigma) | reinterpret_cast<uintptr_t>(m_color) |
+         reinterpret_cast<uintptr_t>(v_color)) & 15)
+        return fail(IGS_ERR_INVALID_ARG, "g2d, means_sigma and color moments must be 16-byte aligned");
+    igs::AdamParams a;
+    if ((st = adam_params(lr, b1, b2, eps, 1, &a))) return st;  // b1, b2, eps; the step's constants come from d_state
+    a.dev_consts = reinterpret_cast<const float*>(d_state + 1);
+    const igs::ViewParams vp = view_params(cam, opts, frame);
+    cudaError_t e = igs::launch_adam_advance(d_state, lr, b1, b2, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e, "igs_project_bwd_adam_dev");
+    return cuda_status(igs::launch_project_bwd_adam(*scene, vp, *frame, g2d, m_means_sigma, m_opacity, m_color,
+                                                    v_means_sigma, v_opacity, v_color, a, (cudaStream_t)stream),
+                       "igs_project_bwd_adam_dev");
 }
 
 igs_status igs_render_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts, const igs_frame* frame,

@@ -162,7 +162,13 @@ struct AdamParams {
     float bc2_sqrt;            // sqrt(1 - beta2^t)
     float inv_bc2_sqrt;        // 1 / sqrt(1 - beta2^t)
     float eps;
+    // If set: device floats (step_size, inv_bc2_sqrt, bc2_sqrt) written by
+    // k_adam_advance, which replace the three host values (step count on the device).
+    const float* dev_consts;
 };
+// Advance a device Adam step count (state[0] += 1) and write the bias-corrected
+// constants of that step to state[1..3] as floats (one thread).
+cudaError_t launch_adam_advance(int32_t* state, double lr, double b1, double b2, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, const AdamParams& a,
                         cudaStream_t s);
 

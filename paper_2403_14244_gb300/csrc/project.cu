@@ -72,6 +72,12 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
     constexpr int C = DEG < 0 ? 3 : 3 * (DEG + 1) * (DEG + 1);
     using CT = ColorTile<C>;
     extern __shared__ float4 s_tiles[];
+    AdamParams a = ap;
+    if (ADAM && ap.dev_consts) {  // this step's constants from the device step count
+        a.step_size = __ldg(ap.dev_consts);
+        a.inv_bc2_sqrt = __ldg(ap.dev_consts + 1);
+        a.bc2_sqrt = __ldg(ap.dev_consts + 2);
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t wb = ((int64_t)blockIdx.x * (kPbThreads / 32) + w) * 32;
     if (wb >= n) return;  // whole warp past the end (no block-wide barrier below)
@@ -163,10 +169,10 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
         const float4 g4 = make_float4(dmx, dmy, dmz, dsig_out);
         if constexpr (ADAM) {
             float4 mm = st.m_ms[i], vv = st.v_ms[i];
-            adam_update4(m, g4, mm, vv, ap);
+            adam_update4(m, g4, mm, vv, a);
             ms[i] = m; st.m_ms[i] = mm; st.v_ms[i] = vv;
             float mo = st.m_op[i], vo = st.v_op[i];
-            adam_update(raw_op, dop_out, mo, vo, ap);
+            adam_update(raw_op, dop_out, mo, vo, a);
             op[i] = raw_op; st.m_op[i] = mo; st.v_op[i] = vo;
         } else {
             d_ms[i] = g4;
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
                 float4 p4 = A[g * CT::kStride + (q - g * CT::kF4)];
                 float4 mm = reinterpret_cast<float4*>(st.m_col)[row0 + q];
                 float4 vv = reinterpret_cast<float4*>(st.v_col)[row0 + q];
-                adam_update4(p4, g4, mm, vv, ap);
+                adam_update4(p4, g4, mm, vv, a);
                 reinterpret_cast<float4*>(col)[row0 + q] = p4;
                 reinterpret_cast<float4*>(st.m_col)[row0 + q] = mm;
                 reinterpret_cast<float4*>(st.v_col)[row0 + q] = vv;
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
             const float gk = has_grad ? dcoef(k) : 0.f;
             if constexpr (ADAM) {
                 float pk = col[r + k], mk = st.m_col[r + k], vk = st.v_col[r + k];
-                adam_update(pk, gk, mk, vk, ap);
+                adam_update(pk, gk, mk, vk, a);
                 col[r + k] = pk; st.m_col[r + k] = mk; st.v_col[r + k] = vk;
             } else {
                 d_col[r + k] = gk;
@@ -254,7 +260,23 @@ cudaError_t dispatch_pb(const igs_scene& sc, const ViewParams& vp, const igs_fra
     }
 }
 
+__global__ void k_adam_advance(int32_t* __restrict__ state, double lr, double b1, double b2) {
+    const int t = state[0] + 1;
+    state[0] = t;
+    const double bc1 = 1.0 - pow(b1, (double)t), bc2 = 1.0 - pow(b2, (double)t);
+    float* f = reinterpret_cast<float*>(state + 1);
+    f[0] = (float)(lr / bc1);
+    f[1] = (float)(1.0 / sqrt(bc2));
+    f[2] = (float)sqrt(bc2);
+}
+
 }  // namespace
+
+cudaError_t launch_adam_advance(int32_t* state, double lr, double b1, double b2, cudaStream_t st) {
+    k_adam_advance<<<1, 1, 0, st>>>(state, lr, b1, b2);
+    count_launches();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, cudaStream_t st) {
     if (sc.n == 0) return cudaSuccess;

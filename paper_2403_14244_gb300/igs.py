@@ -104,6 +104,9 @@ SYMBOLS = {
     "igs_project_bwd_adam": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
                                        C.POINTER(IgsFrame), C.c_void_p] + [C.c_void_p] * 6 +
                              [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, C.c_void_p]),
+    "igs_project_bwd_adam_dev": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
+                                           C.POINTER(IgsFrame), C.c_void_p] + [C.c_void_p] * 6 +
+                                 [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
     "igs_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_ssim_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "igs_l1_ssim_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float,
@@ -354,6 +357,16 @@ def project_bwd_adam(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d
     _check(load().igs_project_bwd_adam(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                        _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
                                        int(step), _stream(stream)), "igs_project_bwd_adam")
+
+
+def project_bwd_adam_dev(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, m, v, state, lr=1e-3,
+                         b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    """project_bwd_adam with the step count on the device: state is an int32[4]
+    tensor (zero before the first step) that the call advances, so the step can
+    be captured in a CUDA graph and replayed."""
+    _check(load().igs_project_bwd_adam_dev(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
+                                           _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
+                                           _ptr(state), _stream(stream)), "igs_project_bwd_adam_dev")
 
 
 def l1_loss(img, target, loss, dL_dimg, stream=None):

@@ -158,6 +158,9 @@ class TrainStep:
         self.tile, self.footprint = tile, footprint
         self.accum = None    # densify statistic (summed screen-space position-gradient norms), when tracked
         self.vis = None      # steps in which each Gaussian touched a tile
+        # Adam step count and the step's constants on the device (fused path), so steps can be graph-replayed
+        self.adam_state = torch.zeros(4, dtype=torch.int32, device=device)
+        self.graphs = None
 
     def _views(self, flat):
         n, C = self.n, self.C
@@ -200,8 +203,8 @@ class TrainStep:
             igs.grad_accum(self.g2d, frame.count(), self.accum, self.vis, stream)
         self.t += 1
         if self.fused:
-            igs.project_bwd_adam(self.scene, c, r.opts, frame, self.g2d, self.m_views, self.v_views, self.t,
-                                 lr=self.lr, stream=stream)
+            igs.project_bwd_adam_dev(self.scene, c, r.opts, frame, self.g2d, self.m_views, self.v_views,
+                                     self.adam_state, lr=self.lr, stream=stream)
             mark("project_bwd_adam")
         else:
             igs.project_bwd(self.scene, c, r.opts, frame, self.g2d, self.g_ms, self.g_op, self.g_col, stream)
@@ -209,6 +212,35 @@ class TrainStep:
             igs.adam(self.flat, self.grad, self.m, self.v, self.t, lr=self.lr, stream=stream)
             mark("adam")
         return frame
+
+    def capture(self, cams, targets):
+        """Record one training step per (camera, target) into its own CUDA graph
+        (fused path: the Adam step count lives on the device, so replays keep
+        counting). Each view must have run once with check=True before (its entry
+        capacity is then known). Replay with replay(k); the graphs read the
+        `targets` tensors as they are at replay time."""
+        if not self.fused:
+            raise RuntimeError("graph capture needs the fused projection backward + Adam")
+        t0 = self.t
+        cur = torch.cuda.current_stream()
+        s = torch.cuda.Stream(device=self.flat.device)
+        s.wait_stream(cur)
+        graphs = []
+        with torch.cuda.stream(s):
+            for c, tgt in zip(cams, targets):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    self.step(c, tgt, stream=s)
+                graphs.append(g)
+        cur.wait_stream(s)
+        self.t = t0  # recording ran nothing
+        self.graphs = graphs
+        return graphs
+
+    def replay(self, k):
+        """Replay the captured step of view k on the current stream."""
+        self.graphs[k].replay()
+        self.t += 1
 
     def track_grad_norm(self):
         """Start (or restart) the densify statistic: every later step adds each
@@ -264,3 +296,4 @@ class TrainStep:
         self.v_views = self._views(self.v)
         self.scene = igs.Scene(self.ms, self.op, self.col)
         self.g2d = torch.empty((n, 8), dtype=torch.float32, device=dev)
+        self.graphs = None  # captured steps refer to the old buffers

@@ -1,6 +1,8 @@
 """GPU parity of the adjoint (backward blend + projection backward) against
 the oracle's FP64 analytic gradients (themselves pinned by finite differences
 and torch autograd), and of the L1 loss and Adam kernels."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -157,5 +159,32 @@ def test_fused_adam_ragged_and_repeated():
         for _ in range(3):
             ts.step(cam, target, check=True)
         torch.cuda.synchronize()
+        states.append(torch.cat([ts.flat, ts.m, ts.v]).cpu().numpy())
+    np.testing.assert_allclose(states[0], states[1], rtol=1e-4, atol=1e-6)
+
+
+def test_train_step_graph_replay_matches_eager():
+    """Training steps replayed from CUDA graphs (one per view, the Adam step
+    count on the device) follow the same trajectory as eager steps: same
+    parameters and moments up to the backward's atomic summation order, and the
+    device step count advances once per replay."""
+    sc, cam = random_small(2000, 49, w=128, h=96, sh_degree=3, log_params=True, spread=0.8)
+    cams = [cam, dataclasses.replace(cam, t=(np.asarray(cam.t, np.float32) + np.float32(0.05)).astype(np.float32))]
+    targets = [torch.from_numpy(scenes.target_image(cam.width, cam.height, 20 + k)).cuda() for k in range(2)]
+    states = []
+    for graphed in (False, True):
+        ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                       torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-2)
+        for k in range(2):  # capacity calibration (also the first two steps)
+            ts.step(cams[k], targets[k], check=True)
+        if graphed:
+            ts.capture(cams, targets)
+            for k in range(6):
+                ts.replay(k % 2)
+        else:
+            for k in range(6):
+                ts.step(cams[k % 2], targets[k % 2])
+        torch.cuda.synchronize()
+        assert int(ts.adam_state[0]) == 8
         states.append(torch.cat([ts.flat, ts.m, ts.v]).cpu().numpy())
     np.testing.assert_allclose(states[0], states[1], rtol=1e-4, atol=1e-6)
