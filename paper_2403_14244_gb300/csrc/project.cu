@@ -63,7 +63,7 @@ struct AdamState {
 // applies one Adam step to the parameters in place (ms / op / col) instead,
 // without materialising the gradient.
 template <int DEG, bool ADAM>
-__global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restrict__ ms, float* __restrict__ op,
+__global__ void __launch_bounds__(kPbThreads, 5) k_project_bwd(float4* __restrict__ ms, float* __restrict__ op,
                                                             float* __restrict__ col, int64_t n, ViewParams P,
                                                             const uint32_t* __restrict__ count,
                                                             const float4* __restrict__ g2d, float4* __restrict__ d_ms,
@@ -104,10 +104,18 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
     float drgb[3] = {0.f, 0.f, 0.f}, draw[3] = {0.f, 0.f, 0.f};
     float Y[16];
     float dx = 0.f, dy = 0.f, dz = 0.f;
+    float4 e_mm = make_float4(0.f, 0.f, 0.f, 0.f), e_vv = e_mm;
+    float e_mo = 0.f, e_vo = 0.f;
     if (active) {
         m = ms[i];
         raw_op = op[i];
         has_grad = count[i] != 0;
+        if constexpr (ADAM) {  // independent of the gradient: in flight during the compute
+            e_mm = st.m_ms[i];
+            e_vv = st.v_ms[i];
+            e_mo = st.m_op[i];
+            e_vo = st.v_op[i];
+        }
     }
     if (has_grad) {
         float sg, o;
@@ -168,10 +176,10 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
     if (active) {
         const float4 g4 = make_float4(dmx, dmy, dmz, dsig_out);
         if constexpr (ADAM) {
-            float4 mm = st.m_ms[i], vv = st.v_ms[i];
+            float4 mm = e_mm, vv = e_vv;
             adam_update4(m, g4, mm, vv, a);
             ms[i] = m; st.m_ms[i] = mm; st.v_ms[i] = vv;
-            float mo = st.m_op[i], vo = st.v_op[i];
+            float mo = e_mo, vo = e_vo;
             adam_update(raw_op, dop_out, mo, vo, a);
             op[i] = raw_op; st.m_op[i] = mo; st.v_op[i] = vo;
         } else {
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(kPbThreads, 6) k_project_bwd(float4* __restric
         }
         __syncwarp();
         const size_t row0 = (size_t)wb * CT::kF4;
-#pragma unroll 4
+#pragma unroll 6
         for (int q = lane; q < nv * CT::kF4; q += 32) {
             const int g = q / CT::kF4;
             const int c0 = 4 * (q - g * CT::kF4);  // first coefficient of this float4
