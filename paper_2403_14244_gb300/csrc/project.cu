@@ -17,10 +17,12 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ ms, 
     project_one<DEG>(ms, op, col, i, P, rec + 2 * i, rect + i, disc + i, count + i, depth_key + i);
 }
 
-// Colour rows of a warp's 32 Gaussians are staged in shared memory so that
-// global reads and writes of the (3 (deg+1)^2)-float rows are coalesced float4
-// accesses; the row stride (in float4) is odd, so lane-strided float4 reads of
-// one row per lane hit distinct banks.
+// Colour rows of a warp's 32 Gaussians are staged in shared memory (16-byte
+// asynchronous copies) so that global reads and writes of the (3 (deg+1)^2)-float
+// rows are coalesced float4 accesses; the row stride (in float4) is odd, so
+// lane-strided float4 reads of one row per lane hit distinct banks. With Adam
+// fused, the rows' moments m, v are staged the same way (dense) and stream in
+// while the warp computes the gradient.
 // The gradient of coefficient (k, ch) is Y_k * drgb_ch, so instead of staging 3K
 // gradients per Gaussian the warp stages the K basis values and the 3 masked
 // colour gradients (one row of kYStride floats per Gaussian).
@@ -33,7 +35,19 @@ struct ColorTile {
     static constexpr int kWarpFloat4 = 32 * kStride + (32 * kYStride + 3) / 4;     // params, then basis rows
 };
 
-constexpr int kPbThreads = 128;
+// One warp per CTA: a CTA's shared memory (21.5 KB with the Adam moments staged)
+// is released as soon as its 32 Gaussians are done, so the ten resident warps
+// of an SM run out of phase and keep HBM busy while others compute.
+constexpr int kPbThreads = 32;
+
+// 16-byte asynchronous global -> shared copy (completed by cp_async_wait).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Adam on one parameter (the fused kernel's hot loop: 53 updates per Gaussian);
 // the bias correction is a multiplication, the square root the SFU's
@@ -63,7 +77,7 @@ struct AdamState {
 // applies one Adam step to the parameters in place (ms / op / col) instead,
 // without materialising the gradient.
 template <int DEG, bool ADAM>
-__global__ void __launch_bounds__(kPbThreads, 5) k_project_bwd(float4* __restrict__ ms, float* __restrict__ op,
+__global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restrict__ ms, float* __restrict__ op,
                                                             float* __restrict__ col, int64_t n, ViewParams P,
                                                             const uint32_t* __restrict__ count,
                                                             const float4* __restrict__ g2d, float4* __restrict__ d_ms,
@@ -84,14 +98,30 @@ __global__ void __launch_bounds__(kPbThreads, 5) k_project_bwd(float4* __restric
     const int nv = (int)min((int64_t)32, n - wb);
     const int64_t i = wb + lane;
     const bool active = lane < nv;
-    float4* A = s_tiles + (size_t)w * CT::kWarpFloat4;           // this warp's parameter rows
+    constexpr int kWarpF4 = CT::kWarpFloat4 + (ADAM && CT::kStaged ? 2 * 32 * CT::kF4 : 0);
+    float4* A = s_tiles + (size_t)w * kWarpF4;                   // this warp's parameter rows
     float* Ys = reinterpret_cast<float*>(A + 32 * CT::kStride);  // this warp's basis rows
     float* Af = reinterpret_cast<float*>(A) + lane * CT::kStride * 4;
+    float4* Mrows = A + CT::kWarpFloat4;                         // Adam moments of the colour rows (dense)
+    float4* Vrows = Mrows + 32 * CT::kF4;
     if constexpr (CT::kStaged) {
         const float4* src = reinterpret_cast<const float4*>(col) + wb * CT::kF4;
         for (int q = lane; q < nv * CT::kF4; q += 32) {
             const int g = q / CT::kF4;
-            A[g * CT::kStride + (q - g * CT::kF4)] = src[q];
+            cp_async16(&A[g * CT::kStride + (q - g * CT::kF4)], src + q);
+        }
+        cp_async_commit();
+        if constexpr (ADAM) {  // the colour moments stream in while the gradient is computed
+            const float4* m4 = reinterpret_cast<const float4*>(st.m_col) + wb * CT::kF4;
+            const float4* v4 = reinterpret_cast<const float4*>(st.v_col) + wb * CT::kF4;
+            for (int q = lane; q < nv * CT::kF4; q += 32) {
+                cp_async16(&Mrows[q], m4 + q);
+                cp_async16(&Vrows[q], v4 + q);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncwarp();
     }
@@ -196,6 +226,7 @@ __global__ void __launch_bounds__(kPbThreads, 5) k_project_bwd(float4* __restric
             for (int k = 0; k < K; ++k) yr[k] = has_grad ? Y[k] : 0.f;
             yr[K] = draw[0]; yr[K + 1] = draw[1]; yr[K + 2] = draw[2];
         }
+        if constexpr (ADAM) cp_async_wait<0>();
         __syncwarp();
         const size_t row0 = (size_t)wb * CT::kF4;
 #pragma unroll 6
@@ -210,8 +241,8 @@ __global__ void __launch_bounds__(kPbThreads, 5) k_project_bwd(float4* __restric
             g4.w = yr[(c0 + 3) / 3] * yr[K + (c0 + 3) % 3];
             if constexpr (ADAM) {
                 float4 p4 = A[g * CT::kStride + (q - g * CT::kF4)];
-                float4 mm = reinterpret_cast<float4*>(st.m_col)[row0 + q];
-                float4 vv = reinterpret_cast<float4*>(st.v_col)[row0 + q];
+                float4 mm = Mrows[q];
+                float4 vv = Vrows[q];
                 adam_update4(p4, g4, mm, vv, a);
                 reinterpret_cast<float4*>(col)[row0 + q] = p4;
                 reinterpret_cast<float4*>(st.m_col)[row0 + q] = mm;
@@ -240,7 +271,9 @@ template <int DEG, bool ADAM>
 cudaError_t launch_pb(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d, float* d_ms,
                       float* d_op, float* d_col, const AdamState& st, const AdamParams& ap, cudaStream_t stream) {
     constexpr int C = DEG < 0 ? 3 : 3 * (DEG + 1) * (DEG + 1);
-    const size_t smem = (size_t)(kPbThreads / 32) * ColorTile<C>::kWarpFloat4 * sizeof(float4);
+    const size_t smem = (size_t)(kPbThreads / 32) *
+                        (ColorTile<C>::kWarpFloat4 + (ADAM && ColorTile<C>::kStaged ? 2 * 32 * ColorTile<C>::kF4 : 0)) *
+                        sizeof(float4);
     auto k = k_project_bwd<DEG, ADAM>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
