@@ -438,6 +438,16 @@ IGS_API igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_
  * `stream`. Returns the recorded device error (IGS_OK if none). Synchronous. */
 IGS_API igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info, void* stream);
 
+/* For failure-detection tests (the paper has no counterpart): the next
+ * igs_bin_sort in this process runs its first depth-sort pass with one block
+ * that never publishes its digit counts, so every later block's bounded wait
+ * for them runs out (about half a second). Those blocks record
+ * IGS_ERR_DEVICE_TIMEOUT, the frame is aborted (later kernels of the frame skip
+ * their work and leave their outputs untouched) and igs_frame_status reports
+ * the error; the GPU context stays usable. Needs n > 8192 (three or more
+ * blocks). Host-only, takes effect once. */
+IGS_API void igs_debug_silence_lookback_once(void);
+
 /* Clear the frame's status words (asynchronous). */
 IGS_API igs_status igs_frame_reset_status(igs_frame* frame, void* stream);
 

@@ -693,6 +693,8 @@ igs_status igs_batch_status(const igs_batch* batch, uint32_t* host_info, void* s
     return IGS_OK;
 }
 
+void igs_debug_silence_lookback_once(void) { igs::g_silence_next.store(1); }
+
 igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info, void* stream) {
     igs_status st;
     if ((st = check_frame(frame))) return st;

@@ -105,7 +105,7 @@ template <bool IN_KEYS32, bool OUT_VALS>
 __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
     const void* __restrict__ in_, void* __restrict__ out_, const uint32_t* __restrict__ d_count, uint32_t count_host,
     int shift, const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ status,
-    uint32_t* __restrict__ block_counter, uint32_t* __restrict__ info) {
+    uint32_t* __restrict__ block_counter, uint32_t* __restrict__ info, uint32_t silent_blk = 0xFFFFFFFFu) {
     {
         const uint64_t seg = blockIdx.y;
         if (IN_KEYS32)
@@ -174,7 +174,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
         if (wbase + i * 32 < valid) atomicAdd(&s_cnt[(uint32_t)(it[i] >> (32 + shift)) & 0xFFu], 1u);
     __syncthreads();
     uint32_t* my = status + (size_t)blk * kRadix;
-    st_relaxed_u32(&my[tid], (blk == 0 ? kFlagPre : kFlagAgg) | (s_cnt[tid] & kValMask));
+    // silent_blk (failure-detection tests only): that block never publishes, so
+    // every later block's bounded look-back runs out
+    const bool silent = blk == silent_blk;
+    if (!silent) st_relaxed_u32(&my[tid], (blk == 0 ? kFlagPre : kFlagAgg) | (s_cnt[tid] & kValMask));
     // rank within the warp, in item order
     uint32_t rank2[kSortIpt / 2];  // two 16-bit ranks per register (ranks < 4096)
     const uint32_t lt = (1u << lane) - 1u;
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
             }
             b -= nw;
         }
-        st_relaxed_u32(&my[tid], kFlagPre | ((excl + cnt) & kValMask));
+        if (!silent) st_relaxed_u32(&my[tid], kFlagPre | ((excl + cnt) & kValMask));
     }
     s_delta[tid] = (int32_t)(digit_base[tid] + excl) - (int32_t)local;
     __syncthreads();

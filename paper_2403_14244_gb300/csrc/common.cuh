@@ -37,6 +37,8 @@ constexpr int kDupTile = 2048;
 // Upper bound on polls of a look-back flag before a block gives up (about 0.1 s).
 constexpr int kMaxSpin = 1 << 21;
 
+// Set by igs_debug_silence_lookback_once, consumed by the next launch_bin_sort.
+extern std::atomic<int> g_silence_next;
 // Kernel launches made by the library (igs_launch_count).
 extern std::atomic<uint64_t> g_launches;
 inline void count_launches(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }

@@ -786,6 +786,10 @@ SortScratch sort_scratch(const igs_frame& f) {
     return s;
 }
 
+// Failure-detection tests: when set, the next binning's first depth pass runs
+// with one silent block (igs_debug_silence_lookback_once).
+std::atomic<int> g_silence_next{0};
+
 cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) {
     const SortScratch s = sort_scratch(f);
     const int64_t n = f.n, cap = f.capacity;
@@ -845,7 +849,8 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         const uint32_t* hist = s.hist + p * kRadix;
         if (p == 0)
             k_radix_pass<true, false><<<(unsigned)bn, kSortThreads, 0, st>>>(
-                f.depth_key, s.ditems_a, nullptr, nn, 0, hist, status, s.counters + 0, f.info);
+                f.depth_key, s.ditems_a, nullptr, nn, 0, hist, status, s.counters + 0, f.info,
+                g_silence_next.exchange(0) ? 1u : 0xFFFFFFFFu);
         else if (p == 3)
             k_radix_pass<false, true><<<(unsigned)bn, kSortThreads, 0, st>>>(
                 s.ditems_a, f.order, nullptr, nn, 24, hist, status, s.counters + 3, f.info);

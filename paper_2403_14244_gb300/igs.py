@@ -133,6 +133,7 @@ SYMBOLS = {
                            C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "igs_frame_status": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_uint32), C.c_void_p]),
     "igs_frame_reset_status": (C.c_int, [C.POINTER(IgsFrame), C.c_void_p]),
+    "igs_debug_silence_lookback_once": (None, []),
     "igs_sort_depth_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "igs_batch_layout": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.c_int64,
                                    C.c_int32, C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(IgsBatch)]),
@@ -606,6 +607,13 @@ class Server:
 def launch_count() -> int:
     """Kernels the library has launched in this process."""
     return int(load().igs_launch_count())
+
+
+def debug_silence_lookback_once():
+    """Failure-detection tests: the next bin_sort's first depth pass has one
+    block that never publishes, so the later blocks' bounded waits run out and
+    the frame reports ERR_DEVICE_TIMEOUT."""
+    load().igs_debug_silence_lookback_once()
 
 
 def frame_reset_status(frame: Frame, stream=None):
