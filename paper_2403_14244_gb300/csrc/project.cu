@@ -17,6 +17,43 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ ms, 
     project_one<DEG>(ms, op, col, i, P, rec + 2 * i, rect + i, disc + i, count + i, depth_key + i);
 }
 
+// Projection with one warp per CTA and the warp's 32 colour rows (SH degree 3)
+// staged in shared memory by coalesced 16-byte asynchronous copies (odd row
+// stride: conflict-free row reads), instead of 32 rows read lane by lane.
+constexpr int kProjRowStride = 13;  // float4 per staged row (12 used)
+
+__global__ void __launch_bounds__(32) k_project_rows3(const float4* __restrict__ ms, const float* __restrict__ op,
+                                                      const float* __restrict__ col, int64_t n, ViewParams P,
+                                                      float4* __restrict__ rec, uint2* __restrict__ rect,
+                                                      float4* __restrict__ disc, uint32_t* __restrict__ count,
+                                                      uint32_t* __restrict__ depth_key) {
+    __shared__ float4 s_rows[32 * kProjRowStride];
+    const int lane = threadIdx.x;
+    const int64_t wb = (int64_t)blockIdx.x * 32;
+    const int nv = (int)min((int64_t)32, n - wb);
+    const float4* src = reinterpret_cast<const float4*>(col) + wb * 12;
+    for (int q = lane; q < nv * 12; q += 32) {
+        const int g = q / 12;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_rows[g * kProjRowStride + (q - g * 12)])),
+                     "l"(src + q)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    if (lane >= nv) return;
+    const int64_t i = wb + lane;
+    const float4* row = s_rows + lane * kProjRowStride;
+    project_one_with<3>(ms, op, [&](float c[48]) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const float4 v = row[q];
+            c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+        }
+    }, i, P, rec + 2 * i, rect + i, disc + i, count + i, depth_key + i);
+}
+
 // Colour rows of a warp's 32 Gaussians are staged in shared memory (16-byte
 // asynchronous copies) so that global reads and writes of the (3 (deg+1)^2)-float
 // rows are coalesced float4 accesses; the row stride (in float4) is odd, so
@@ -327,6 +364,13 @@ cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_
     auto rec = reinterpret_cast<float4*>(f.rec);
     auto rect = reinterpret_cast<uint2*>(f.rect);
 #define IGS_PROJ(D) k_project<D><<<blocks, threads, 0, st>>>(ms, sc.opacity, sc.color, sc.n, vp, rec, rect, reinterpret_cast<float4*>(f.disc), f.count, f.depth_key)
+    if (vp.sh_degree == 3 && (reinterpret_cast<uintptr_t>(sc.color) & 15) == 0) {
+        k_project_rows3<<<(unsigned)ceil_div(sc.n, 32), 32, 0, st>>>(ms, sc.opacity, sc.color, sc.n, vp, rec, rect,
+                                                                      reinterpret_cast<float4*>(f.disc), f.count,
+                                                                      f.depth_key);
+        count_launches();
+        return cudaGetLastError();
+    }
     switch (vp.sh_degree) {
         case -1: IGS_PROJ(-1); break;
         case 0: IGS_PROJ(0); break;

@@ -162,12 +162,14 @@ __device__ __forceinline__ float support_radius(float s, float o) {
     return __fmul_rn(__fmul_rn(s, k), 1.000244140625f);
 }
 
-template <int DEG>
-__device__ __forceinline__ void project_one(const float4* __restrict__ ms, const float* __restrict__ op,
-                                            const float* __restrict__ col, int64_t i, const ViewParams& P,
-                                            float4* __restrict__ rec, uint2* __restrict__ rect,
-                                            float4* __restrict__ disc, uint32_t* __restrict__ count,
-                                            uint32_t* __restrict__ depth_key) {
+// load_c(c) fills c[0 .. C) with the Gaussian's colour coefficients; it is
+// called only for Gaussians that are kept.
+template <int DEG, typename LoadC>
+__device__ __forceinline__ void project_one_with(const float4* __restrict__ ms, const float* __restrict__ op,
+                                                 LoadC load_c, int64_t i, const ViewParams& P,
+                                                 float4* __restrict__ rec, uint2* __restrict__ rect,
+                                                 float4* __restrict__ disc, uint32_t* __restrict__ count,
+                                                 uint32_t* __restrict__ depth_key) {
     const float4 m = __ldg(ms + i);
     float sg, o;
     activate(P.param_mode, m.w, __ldg(op + i), sg, o);
@@ -227,7 +229,7 @@ __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const
     *rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
     // colour
     float c[48];
-    load_color<DEG>(col, i, c);
+    load_c(c);
     float rgb[3];
     if constexpr (DEG < 0) {
         rgb[0] = c[0]; rgb[1] = c[1]; rgb[2] = c[2];
@@ -251,6 +253,16 @@ __device__ __forceinline__ void project_one(const float4* __restrict__ ms, const
     const float pmax = __fadd_rn(log2f(__fdiv_rn(o, P.alpha_min)), kPowMargin);
     rec[0] = make_float4(u, v, w2, pmax);
     rec[1] = make_float4(rgb[0], rgb[1], rgb[2], o);
+}
+
+template <int DEG>
+__device__ __forceinline__ void project_one(const float4* __restrict__ ms, const float* __restrict__ op,
+                                            const float* __restrict__ col, int64_t i, const ViewParams& P,
+                                            float4* __restrict__ rec, uint2* __restrict__ rect,
+                                            float4* __restrict__ disc, uint32_t* __restrict__ count,
+                                            uint32_t* __restrict__ depth_key) {
+    project_one_with<DEG>(ms, op, [&](float c[48]) { load_color<DEG>(col, i, c); }, i, P, rec, rect, disc, count,
+                          depth_key);
 }
 
 }  // namespace
