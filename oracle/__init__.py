@@ -97,6 +97,9 @@ def _load():
             lib.orc_grad_accum3d.argtypes = [i64, P, P, P, P]
             lib.orc_densify3d.argtypes = [i64, C.c_int32, C.c_int32] + [P] * 11 + [C.c_float] * 3 + [i64] + [P] * 9
             lib.orc_densify3d.restype = i64
+            lib.orc_octree_init.argtypes = [i64, P, P, P, C.c_float, C.c_int32, i64, C.c_float, C.c_int32, C.c_int32,
+                                            P, P, P]
+            lib.orc_octree_init.restype = i64
             _lib = lib
     return _lib
 
@@ -415,3 +418,24 @@ def densify3d(params, m, v, accum, vis, param_mode, op_min, tau_g, scale_min, ca
                               *[_ptr(a) for a in ov])
     cut = lambda arrs: tuple(a[:k].copy() for a in arrs)  # noqa: E731
     return cut(outs), cut(om), cut(ov)
+
+
+def octree_init(points, colors, lo, side, levels, k_max, opacity=0.5, sh_degree=-1, param_mode=0):
+    """Octree initialisation of 3D Gaussians from a coloured point set: greedy
+    splits of the leaf with the largest squared colour error (12-bit exact
+    statistics) while the non-empty leaves stay <= k_max; one Gaussian per
+    non-empty leaf (cell centre, sigma = half the cell side, mean colour).
+    Returns (means_sigma [K][4], opacity [K], color [K][C])."""
+    p = _c32(points).reshape(-1, 3)
+    c = _c32(colors).reshape(-1, 3)
+    lo3 = _c32(np.asarray(lo, np.float32).reshape(3))
+    C = 3 if sh_degree < 0 else 3 * (sh_degree + 1) ** 2
+    cap = max(int(k_max), 1)
+    ms = np.zeros((cap, 4), np.float32)
+    op = np.zeros(cap, np.float32)
+    col = np.zeros((cap, C), np.float32)
+    k = _load().orc_octree_init(p.shape[0], _ptr(p), _ptr(c), _ptr(lo3), float(side), int(levels), int(k_max),
+                                float(opacity), int(sh_degree), int(param_mode), _ptr(ms), _ptr(op), _ptr(col))
+    if k < 0:
+        raise ValueError("need 0 <= levels <= 7, k_max >= 1, side > 0, sh_degree in -1..3")
+    return ms[:k].copy(), op[:k].copy(), col[:k].copy()

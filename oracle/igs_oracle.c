@@ -1219,3 +1219,150 @@ int64_t orc_densify3d(int64_t n, int32_t C, int32_t param_mode, const float* ms,
     }
     return o;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Octree initialisation of 3D Gaussians (Sec. 3.1: an Octree for 3D, as the
+ * QuadTree for 2D; colour = the cell average, sigma = half the cell width),
+ * from a coloured point set standing in for the points a reconstruction
+ * starts from. Reading:
+ *   - domain: the cube [lo, lo + side)^3, levels 0..L (L <= 7), cell of level l
+ *     = a cube of side side / 2^l; point p falls in finest cell
+ *     i_a = clamp(floor((p_a - lo_a) * inv), 0, 2^L - 1), inv = 2^L / side in
+ *     FP32, each operation rounded once; non-finite points are ignored;
+ *   - cell id = (8^l - 1) / 7 + Morton index (bits of x, y, z interleaved,
+ *     x lowest);
+ *   - statistics on colours quantised to 12 bits, q = rint(clamp(c, 0, 1) 4096):
+ *     n, S1_c, S2_c exact integers;
+ *   - error of a cell with n >= 2 points and level < L (splittable):
+ *     e = max(0, sum_c (S2_c - S1_c * S1_c / n)) in double, one rounding per
+ *     step in channel order; order: e descending, id ascending;
+ *   - growth: start from the root (one leaf); repeatedly take the splittable
+ *     leaf first in that order; splitting it replaces it by its non-empty
+ *     children; stop when that would make more than k_max leaves (or no leaf
+ *     is splittable);
+ *   - one Gaussian per non-empty leaf in id order: mean = cell centre
+ *     lo + (i + 1/2) side / 2^l (double, rounded once), sigma = half the cell
+ *     side, colour = S1_c / (4096 n) (double, rounded once) as RGB, or as the
+ *     DC coefficient (colour - 1/2) / Y00 of SH of degree sh_degree with the
+ *     others 0, opacity `opacity`; param_mode 1 stores log sigma and the
+ *     opacity logit (double, rounded once).
+ * Returns the number of Gaussians, or -1 for invalid arguments. */
+typedef struct {
+    int64_t n, s1[3], s2[3];
+} orc_ocell;
+
+static int64_t oct_off(int l) { return ((((int64_t)1) << (3 * l)) - 1) / 7; }
+
+static uint32_t oct_morton(uint32_t x, uint32_t y, uint32_t z, int L) {
+    uint32_t m = 0;
+    for (int b = 0; b < L; ++b)
+        m |= (((x >> b) & 1u) << (3 * b)) | (((y >> b) & 1u) << (3 * b + 1)) | (((z >> b) & 1u) << (3 * b + 2));
+    return m;
+}
+
+static double oct_err(const orc_ocell* c) {
+    const double n = (double)c->n;
+    double e = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+        const double s1 = (double)c->s1[ch];
+        e = e + ((double)c->s2[ch] - s1 * s1 / n);
+    }
+    return e > 0.0 ? e : 0.0;
+}
+
+int64_t orc_octree_init(int64_t npts, const float* pts, const float* cols, const float* lo, float side, int32_t L,
+                        int64_t k_max, float opacity, int32_t sh_degree, int32_t param_mode, float* out_ms,
+                        float* out_op, float* out_col) {
+    if (L < 0 || L > 7 || k_max < 1 || !(side > 0.f) || sh_degree < -1 || sh_degree > 3) return -1;
+    const int64_t cells = oct_off(L + 1);
+    orc_ocell* st = (orc_ocell*)calloc((size_t)cells, sizeof(orc_ocell));
+    uint8_t* split = (uint8_t*)calloc((size_t)cells, 1);
+    uint8_t* leaf = (uint8_t*)calloc((size_t)cells, 1);
+    const float inv = (float)((double)(1 << L) / (double)side);
+    const int32_t top = (1 << L) - 1;
+    for (int64_t i = 0; i < npts; ++i) {
+        const float* p = pts + 3 * i;
+        if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) continue;
+        int32_t ix[3];
+        for (int a = 0; a < 3; ++a) {
+            const float t = floorf((p[a] - lo[a]) * inv);
+            ix[a] = t < 0.f ? 0 : (t > (float)top ? top : (int32_t)t);
+        }
+        orc_ocell* c = st + oct_off(L) + oct_morton((uint32_t)ix[0], (uint32_t)ix[1], (uint32_t)ix[2], L);
+        c->n += 1;
+        for (int ch = 0; ch < 3; ++ch) {
+            float v = cols[3 * i + ch];
+            v = v < 0.f ? 0.f : (v > 1.f ? 1.f : v);
+            const int64_t q = (int64_t)rintf(v * 4096.f);
+            c->s1[ch] += q;
+            c->s2[ch] += q * q;
+        }
+    }
+    for (int l = L - 1; l >= 0; --l)
+        for (int64_t m = 0; m < ((int64_t)1 << (3 * l)); ++m) {
+            orc_ocell* c = st + oct_off(l) + m;
+            for (int d = 0; d < 8; ++d) {
+                const orc_ocell* k = st + oct_off(l + 1) + 8 * m + d;
+                c->n += k->n;
+                for (int ch = 0; ch < 3; ++ch) {
+                    c->s1[ch] += k->s1[ch];
+                    c->s2[ch] += k->s2[ch];
+                }
+            }
+        }
+    int64_t leaves = st[0].n > 0 ? 1 : 0;
+    if (leaves) leaf[0] = 1;
+    for (;;) {  /* the greedy rule as written: scan the leaves for the first in the order */
+        int64_t best = -1;
+        double be = -1.0;
+        for (int l = 0; l < L; ++l)
+            for (int64_t m = 0; m < ((int64_t)1 << (3 * l)); ++m) {
+                const int64_t id = oct_off(l) + m;
+                if (!leaf[id] || st[id].n < 2) continue;
+                const double e = oct_err(st + id);
+                if (e > be) {
+                    be = e;
+                    best = id;
+                }
+            }
+        if (best < 0) break;
+        int l = 0;
+        while (oct_off(l + 1) <= best) ++l;
+        const int64_t m = best - oct_off(l);
+        int64_t kids = 0;
+        for (int d = 0; d < 8; ++d) kids += st[oct_off(l + 1) + 8 * m + d].n > 0;
+        if (leaves + kids - 1 > k_max) break;
+        leaf[best] = 0;
+        split[best] = 1;
+        for (int d = 0; d < 8; ++d)
+            if (st[oct_off(l + 1) + 8 * m + d].n > 0) leaf[oct_off(l + 1) + 8 * m + d] = 1;
+        leaves += kids - 1;
+    }
+    const int C = sh_degree < 0 ? 3 : 3 * (sh_degree + 1) * (sh_degree + 1);
+    const double y00 = 0.5 / sqrt(3.14159265358979323846);
+    int64_t o = 0;
+    for (int l = 0; l <= L; ++l)
+        for (int64_t m = 0; m < ((int64_t)1 << (3 * l)); ++m) {
+            const int64_t id = oct_off(l) + m;
+            if (!leaf[id]) continue;
+            uint32_t c3[3] = {0, 0, 0};
+            for (int b = 0; b < l; ++b)
+                for (int a = 0; a < 3; ++a) c3[a] |= (uint32_t)((m >> (3 * b + a)) & 1) << b;
+            const double cs = (double)side / (double)(1 << l);
+            float* q = out_ms + 4 * o;
+            for (int a = 0; a < 3; ++a) q[a] = (float)((double)lo[a] + ((double)c3[a] + 0.5) * cs);
+            q[3] = param_mode == 1 ? (float)log(0.5 * cs) : (float)(0.5 * cs);
+            out_op[o] = param_mode == 1 ? (float)log((double)opacity / (1.0 - (double)opacity)) : opacity;
+            float* cc = out_col + (size_t)C * o;
+            for (int k = 0; k < C; ++k) cc[k] = 0.f;
+            for (int ch = 0; ch < 3; ++ch) {
+                const double mean = (double)st[id].s1[ch] / (4096.0 * (double)st[id].n);
+                cc[ch] = sh_degree < 0 ? (float)mean : (float)((mean - 0.5) / y00);
+            }
+            ++o;
+        }
+    free(st);
+    free(split);
+    free(leaf);
+    return o;
+}
