@@ -551,10 +551,40 @@ def run_extra(dev, np, tile=32):
     out["fwd_bwd_1080p_1M"]["entries_M"] = info[0]
     del scene, r, f, img, g2d, grads
     torch.cuda.empty_cache()
+    out["octree_init"] = run_octree(dev)
     out["fit2d_512"] = run_fit2d(dev)
     out["batched_32view_2M"] = run_batched(dev)
     out["serve_4scenes_poisson200"] = run_serving(dev)
     return out
+
+
+def run_octree(dev, n=2_000_000, levels=7, k_max=500_000, reps=3):
+    """Octree initialisation of 3D Gaussians from a seeded coloured point set
+    (n points: 64 clusters and a uniform background in [-1, 1]^3, colours with
+    structure at several scales), cells down to side 2 / 2^levels, at most
+    k_max Gaussians: time per call (statistics, up-sweep, one-CTA selection,
+    emission) and the Gaussians made."""
+    import numpy as np
+    import torch
+
+    from paper_2403_14244_gb300 import igs
+
+    rng = np.random.default_rng(8)
+    centres = rng.uniform(-0.8, 0.8, (64, 3))
+    p = np.concatenate([centres[rng.integers(0, 64, n // 2)] + rng.normal(0, 0.05, (n // 2, 3)),
+                        rng.uniform(-1, 1, (n - n // 2, 3))]).astype(np.float32)
+    c = np.clip(np.stack([0.5 + 0.4 * np.sin(4 * p[:, 0]), 0.5 + 0.4 * np.cos(6 * p[:, 1] * p[:, 2]),
+                          (p[:, 2] > 0.1) * 0.7 + 0.15], 1) + rng.normal(0, 0.03, (n, 3)), 0, 1).astype(np.float32)
+    tp, tc = torch.from_numpy(p).to(dev), torch.from_numpy(c).to(dev)
+    igs.octree_init(tp, tc, (-1, -1, -1), 2.0, levels, k_max)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ms, _, _ = igs.octree_init(tp, tc, (-1, -1, -1), 2.0, levels, k_max)
+    torch.cuda.synchronize(dev)
+    ms_per = (time.perf_counter() - t0) / reps * 1e3
+    return {"points": n, "levels": levels, "k_max": k_max, "gaussians": int(ms.shape[0]),
+            "ms_per_call": round(ms_per, 3), "note": "includes the count read-back (one synchronisation)"}
 
 
 def run_fit2d(dev, iters=2000, side=512, min_cell=3):

@@ -406,6 +406,38 @@ IGS_API igs_status igs_densify(const igs_scene* scene, const igs_params* m, cons
                                float scale_min, int64_t capacity, const igs_params* out, const igs_params* out_m,
                                const igs_params* out_v, int64_t* d_count, void* work, void* stream);
 
+/* Bytes of device scratch igs_octree_init needs for `levels` (0..7; 0 otherwise). */
+IGS_API size_t igs_octree_work_bytes(int32_t levels);
+
+/* Octree initialisation of 3D Gaussians (Sec. 3.1: an Octree for 3D, as the
+ * QuadTree for 2D; colour = the cell average, sigma = half the cell width) from a
+ * coloured point set: points [n][3] and colors [n][3] (device FP32, RGB in
+ * [0, 1], clamped), in the cube [lo, lo + side)^3 (lo: host float[3]; points
+ * outside are clamped into the boundary cells, non-finite points ignored),
+ * cells down to level `levels` (cube side / 2^levels, levels <= 7). Cell of a
+ * point: i_a = clamp(floor((p_a - lo_a) * inv), 0, 2^levels - 1) with inv =
+ * 2^levels / side in FP32, each step rounded once. Statistics use colours
+ * quantised to 12 bits (exact integers). A cell's error is
+ * max(0, sum_c (S2_c - S1_c^2 / n)) (double, one rounding per step), its key
+ * the smaller of its error and its parent's key; cells with >= 2 points above
+ * the finest level can split. Growth: from the root, split the splittable leaf
+ * first in the order (key descending, id = (8^l - 1)/7 + Morton index
+ * ascending), replacing it by its non-empty children, and stop when that would
+ * make more than k_max leaves. Writes one Gaussian per non-empty leaf in id
+ * order to means_sigma [k_max][4] (cell centre, double rounded once; sigma =
+ * half the cell side, or its log with param_mode 1), opacity [k_max]
+ * (`opacity` in (0, 1), or its logit with param_mode 1) and color [k_max][C]
+ * (mean colour as RGB, C = 3, for sh_degree -1; for sh_degree 0..3 the DC
+ * coefficient (mean - 1/2) / Y00 and zeros), and their number to *d_count
+ * (device int32). work: igs_octree_work_bytes(levels) bytes of device scratch,
+ * 16-byte aligned. Errors: n outside 0..2^31, levels outside 0..7, k_max < 1,
+ * side <= 0, opacity outside (0, 1), bad sh_degree / param_mode, NULL or
+ * misaligned buffers -> IGS_ERR_INVALID_ARG. */
+IGS_API igs_status igs_octree_init(const float* points, const float* colors, int64_t n, const float* lo, float side,
+                                   int32_t levels, int32_t k_max, float opacity, int32_t sh_degree,
+                                   int32_t param_mode, float* means_sigma, float* opacity_out, float* color,
+                                   int32_t* d_count, void* work, void* stream);
+
 /* Bytes of device scratch igs_quadtree_init needs (0 for an invalid size). */
 IGS_API size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell);
 

@@ -1233,9 +1233,12 @@ int64_t orc_densify3d(int64_t n, int32_t C, int32_t param_mode, const float* ms,
  *     x lowest);
  *   - statistics on colours quantised to 12 bits, q = rint(clamp(c, 0, 1) 4096):
  *     n, S1_c, S2_c exact integers;
- *   - error of a cell with n >= 2 points and level < L (splittable):
- *     e = max(0, sum_c (S2_c - S1_c * S1_c / n)) in double, one rounding per
- *     step in channel order; order: e descending, id ascending;
+ *   - error of a cell: e = max(0, sum_c (S2_c - S1_c * S1_c / n)) in double,
+ *     one rounding per step in channel order; its key = min(e, key of its
+ *     parent) (the parent's error is never below the child's; the cap only
+ *     keeps rounding from putting a child before its parent); a cell with
+ *     n >= 2 points and level < L is splittable; order: key descending, id
+ *     ascending;
  *   - growth: start from the root (one leaf); repeatedly take the splittable
  *     leaf first in that order; splitting it replaces it by its non-empty
  *     children; stop when that would make more than k_max leaves (or no leaf
@@ -1310,6 +1313,14 @@ int64_t orc_octree_init(int64_t npts, const float* pts, const float* cols, const
                 }
             }
         }
+    double* key = (double*)calloc((size_t)cells, sizeof(double));
+    for (int l = 0; l <= L; ++l)
+        for (int64_t m = 0; m < ((int64_t)1 << (3 * l)); ++m) {
+            const int64_t id = oct_off(l) + m;
+            const double e = st[id].n > 0 ? oct_err(st + id) : 0.0;
+            const double kp = l > 0 ? key[oct_off(l - 1) + (m >> 3)] : e;
+            key[id] = e < kp ? e : kp;
+        }
     int64_t leaves = st[0].n > 0 ? 1 : 0;
     if (leaves) leaf[0] = 1;
     for (;;) {  /* the greedy rule as written: scan the leaves for the first in the order */
@@ -1319,7 +1330,7 @@ int64_t orc_octree_init(int64_t npts, const float* pts, const float* cols, const
             for (int64_t m = 0; m < ((int64_t)1 << (3 * l)); ++m) {
                 const int64_t id = oct_off(l) + m;
                 if (!leaf[id] || st[id].n < 2) continue;
-                const double e = oct_err(st + id);
+                const double e = key[id];
                 if (e > be) {
                     be = e;
                     best = id;
@@ -1364,5 +1375,6 @@ int64_t orc_octree_init(int64_t npts, const float* pts, const float* cols, const
     free(st);
     free(split);
     free(leaf);
+    free(key);
     return o;
 }

@@ -536,6 +536,31 @@ igs_status igs_densify(const igs_scene* scene, const igs_params* m, const igs_pa
                        "igs_densify");
 }
 
+size_t igs_octree_work_bytes(int32_t levels) { return igs::octree_work_bytes(levels); }
+
+igs_status igs_octree_init(const float* points, const float* colors, int64_t n, const float* lo, float side,
+                           int32_t levels, int32_t k_max, float opacity, int32_t sh_degree, int32_t param_mode,
+                           float* means_sigma, float* opacity_out, float* color, int32_t* d_count, void* work,
+                           void* stream) {
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "octree_init: n out of range");
+    if (levels < 0 || levels > 7) return fail(IGS_ERR_INVALID_ARG, "octree_init: levels must be 0..7");
+    if (k_max < 1 || k_max > (1 << 27)) return fail(IGS_ERR_INVALID_ARG, "octree_init: k_max must be 1..2^27");
+    if (!(side > 0.f) || !std::isfinite(side)) return fail(IGS_ERR_INVALID_ARG, "octree_init: side must be > 0");
+    if (!(opacity > 0.f && opacity < 1.f)) return fail(IGS_ERR_INVALID_ARG, "octree_init: opacity must be in (0, 1)");
+    if (sh_degree < -1 || sh_degree > 3 || (param_mode != 0 && param_mode != 1))
+        return fail(IGS_ERR_INVALID_ARG, "octree_init: bad sh_degree or param_mode");
+    if (!lo || !std::isfinite(lo[0]) || !std::isfinite(lo[1]) || !std::isfinite(lo[2]))
+        return fail(IGS_ERR_INVALID_ARG, "octree_init: lo must be 3 finite floats");
+    if ((n > 0 && (!points || !colors)) || !means_sigma || !opacity_out || !color || !d_count || !work)
+        return fail(IGS_ERR_INVALID_ARG, "octree_init: NULL buffer");
+    if (!aligned16(means_sigma) || !aligned16(work))
+        return fail(IGS_ERR_INVALID_ARG, "octree_init: means_sigma and work must be 16-byte aligned");
+    return cuda_status(igs::launch_octree_init(points, colors, n, lo, side, levels, k_max, opacity, sh_degree,
+                                               param_mode, means_sigma, opacity_out, color, d_count, work,
+                                               (cudaStream_t)stream),
+                       "igs_octree_init");
+}
+
 size_t igs_quadtree_work_bytes(int32_t side, int32_t min_cell) {
     if (side < 1 || side > 512 || (side & (side - 1)) || min_cell < 1) return 0;
     return igs::quadtree_work_bytes(side, min_cell);

@@ -185,6 +185,12 @@ cudaError_t launch_densify(const float* const in_p[3], const float* const in_m[3
                            float* const out_m[3], float* const out_v[3], int64_t* d_count, void* work,
                            cudaStream_t s);
 
+// Octree initialisation of 3D Gaussians from a coloured point set (octree.cu).
+size_t octree_work_bytes(int L);
+cudaError_t launch_octree_init(const float* pts, const float* cols, long long npts, const float lo[3], float side,
+                               int L, long long k_max, float opacity, int sh_degree, int param_mode, float* out_ms,
+                               float* out_op, float* out_col, int32_t* count, void* work, cudaStream_t s);
+
 // Multi-view batch (batch.cu): per-view record in device memory (the view table).
 struct BatchView {
     ViewParams vp;

@@ -126,6 +126,10 @@ SYMBOLS = {
                               C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_int64,
                               C.POINTER(IgsParams), C.POINTER(IgsParams), C.POINTER(IgsParams), C.c_void_p,
                               C.c_void_p, C.c_void_p]),
+    "igs_octree_work_bytes": (C.c_size_t, [C.c_int32]),
+    "igs_octree_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float), C.c_float, C.c_int32,
+                                  C.c_int32, C.c_float, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_quadtree_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32]),
     "igs_quadtree_init": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
@@ -472,6 +476,30 @@ def densify(scene: Scene, m, v, sh_degree, param_mode, accum, vis, op_min, tau_g
                               float(scale_min), int(out[0].shape[0]), C.byref(_params(out)),
                               C.byref(_params(out_m)), C.byref(_params(out_v)), _ptr(count), _ptr(work),
                               _stream(stream)), "igs_densify")
+
+
+def octree_work_bytes(levels):
+    return int(load().igs_octree_work_bytes(int(levels)))
+
+
+def octree_init(points, colors, lo, side, levels, k_max, opacity=0.5, sh_degree=-1, param_mode=0, stream=None):
+    """Octree initialisation of 3D Gaussians from a coloured point set (device
+    [n][3] tensors); returns (means_sigma [K][4], opacity [K], color [K][C]) on
+    the device (one synchronisation to read K)."""
+    dev = points.device
+    nc = 3 if sh_degree < 0 else 3 * (sh_degree + 1) ** 2
+    ms = torch.empty((k_max, 4), dtype=torch.float32, device=dev)
+    op = torch.empty(k_max, dtype=torch.float32, device=dev)
+    col = torch.empty((k_max, nc), dtype=torch.float32, device=dev)
+    count = torch.zeros(1, dtype=torch.int32, device=dev)
+    work = torch.empty(octree_work_bytes(levels), dtype=torch.uint8, device=dev)
+    lo3 = (C.c_float * 3)(*[float(x) for x in lo])
+    n = int(points.shape[0])
+    _check(load().igs_octree_init(_ptr(points) if n else None, _ptr(colors) if n else None, n, lo3, float(side),
+                                  int(levels), int(k_max), float(opacity), int(sh_degree), int(param_mode), _ptr(ms),
+                                  _ptr(op), _ptr(col), _ptr(count), _ptr(work), _stream(stream)), "igs_octree_init")
+    k = int(count.item())
+    return ms[:k], op[:k], col[:k]
 
 
 def quadtree_work_bytes(side, min_cell):
