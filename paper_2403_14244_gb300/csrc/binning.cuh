@@ -401,6 +401,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ view_tile_base) {
     __shared__ uint32_t s_off[kDupTile + 2];
     __shared__ uint32_t s_ord[kDupTile + 1];
+    __shared__ u64 s_items[kDupTile];  // the block's entries, written out coalesced at the end
     if (info[kInfoAbort]) return;
     const uint32_t M = info[kInfoM];
     const uint64_t e0 = (uint64_t)blockIdx.x * kDupTile;
@@ -417,8 +418,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
     // end of each view of a batch; those entries search the global offsets.
     const uint32_t reach = s_off[cnt];
     // each thread: kDupPerThread consecutive entries, one search then a walk
-    const uint32_t first = (uint32_t)e0 + threadIdx.x * kDupPerThread;
-    if (first >= e_end) return;
+    const uint32_t first = min((uint32_t)e0 + threadIdx.x * kDupPerThread, e_end);
     const uint32_t last = min(first + kDupPerThread, e_end);
     uint32_t k;       // window slot (or global position) of the current Gaussian
     bool global;
@@ -441,8 +441,8 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
             global = true;
         }
     };
-    locate(first);
     uint32_t e = first;
+    if (e < last) locate(first);
     while (e < last) {
         const uint32_t g = global ? order[k] : s_ord[k];
         const uint32_t start = global ? offset[k] : s_off[k];
@@ -475,10 +475,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
             for (; e < stop; ++e) {
                 if (col > sp.y) break;  // never: the count is the total of the spans
                 const uint32_t t = base + (uint32_t)ty * tpr + (uint32_t)col;
-                if (vals_direct)
-                    vals_direct[e] = g;
-                else
-                    items[e] = ((u64)t << 32) | g;
+                s_items[e - (uint32_t)e0] = ((u64)t << 32) | g;
                 // next touched tile, row by row
                 if (++col > sp.y) {
                     while (ty < y1) {
@@ -501,6 +498,13 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
             locate(e);
         }
     }
+    __syncthreads();
+    // coalesced write-out of the block's entries [e0, e_end)
+    const uint32_t ne = e_end - (uint32_t)e0;
+    if (vals_direct)
+        for (uint32_t q = threadIdx.x; q < ne; q += blockDim.x) vals_direct[e0 + q] = (uint32_t)s_items[q];
+    else
+        for (uint32_t q = threadIdx.x; q < ne; q += blockDim.x) items[e0 + q] = s_items[q];
 }
 
 }  // namespace
