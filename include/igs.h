@@ -182,7 +182,7 @@ IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* st
  * output being the indices. depth_key (device, n) is read; order (device, n)
  * is overwritten. Limit: n <= 1048576 (2^20); larger n returns
  * IGS_ERR_INVALID_ARG and launches nothing.
- * Scratch lives in one fixed 17.8 MB device array compiled into the library,
+ * Scratch lives in one fixed 17.6 MB device array compiled into the library,
  * which every GPU that loads the library holds until the process exits. The
  * first call on each device looks up that array's device address; make that
  * first call before any stream capture. Every call on a device shares the

@@ -2,7 +2,7 @@
 // (sort.cu) and the multi-view batch path (batch.cu). Internal to libigs.
 //
 // Each radix pass is a single sweep over (key | value) items: a block counts
-// the digits of its 4096 items and publishes those counts at once, ranks the
+// the digits of its 5120 items and publishes those counts at once, ranks the
 // items within each warp with ballots, looks back over earlier blocks (eight
 // at a time) for its global digit offsets, and scatters the items staged in
 // digit order. Every wait on another block is bounded (kMaxSpin polls); on
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
     const bool silent = blk == silent_blk;
     if (!silent) st_relaxed_u32(&my[tid], (blk == 0 ? kFlagPre : kFlagAgg) | (s_cnt[tid] & kValMask));
     // rank within the warp, in item order
-    uint32_t rank2[kSortIpt / 2];  // two 16-bit ranks per register (ranks < 4096)
+    uint32_t rank2[kSortIpt / 2];  // two 16-bit ranks per register (ranks < kSortTile)
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int i = 0; i < kSortIpt; ++i) {

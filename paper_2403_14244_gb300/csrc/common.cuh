@@ -24,9 +24,10 @@ constexpr float kPowMargin = 1.0f / 1024.0f;
 enum : int { kInfoM = 0, kInfoKept = 1, kInfoErr = 2, kInfoNeed = 3, kInfoAbort = 4, kInfoTileTotal = 5,
              kInfoWords = 16 };
 
-// Radix sort geometry: 256 threads x 16 (key | value) items per block, 8-bit digits.
+// Radix sort geometry: 256 threads x 20 (key | value) items per block, 8-bit digits
+// (5120 items: a 3M-key pass fits one wave of four blocks per SM).
 constexpr int kSortThreads = 256;
-constexpr int kSortIpt = 16;
+constexpr int kSortIpt = 20;
 constexpr int kSortTile = kSortThreads * kSortIpt;
 constexpr int kRadix = 256;
 constexpr int kScanThreads = 256;

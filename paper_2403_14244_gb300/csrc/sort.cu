@@ -29,7 +29,7 @@
 // column meets its footprint disc: row_span.)
 //
 // Each radix pass is a single sweep over (key | value) items: a block counts
-// the digits of its 4096 items and publishes those counts at once, ranks the
+// the digits of its 5120 items and publishes those counts at once, ranks the
 // items within each warp with ballots, looks back over earlier blocks (eight
 // at a time) for its global digit offsets, and scatters the items staged in
 // digit order. Every wait on another block or warp is bounded (kMaxSpin polls);
@@ -959,7 +959,7 @@ namespace igs {
 namespace {
 
 constexpr int64_t kNoAllocMaxKeys = (int64_t)1 << 20;
-constexpr int64_t kNoAllocBlocks = kNoAllocMaxKeys / kSortTile;
+constexpr int64_t kNoAllocBlocks = (kNoAllocMaxKeys + kSortTile - 1) / kSortTile;
 // 32-bit word offsets inside the static scratch
 constexpr int64_t kNaItemsA = 0;                                // [max] u64
 constexpr int64_t kNaItemsB = kNaItemsA + 2 * kNoAllocMaxKeys;  // [max] u64
@@ -971,7 +971,7 @@ constexpr int64_t kNaWords = kNaStatus + 4 * kNoAllocBlocks * kRadix;
 // words that must be zero at the start of every call
 constexpr int64_t kNaZeroFrom = kNaHist;
 
-// 17.8 MB (4457600 words), held by every device that loads the library until the process exits.
+// 17.6 MB (4405376 words), held by every device that loads the library until the process exits.
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNaWords];
 
 std::mutex g_noalloc_mu;
