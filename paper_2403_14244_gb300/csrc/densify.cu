@@ -15,6 +15,7 @@
 //                 time), then the block copies parameters and moments (kept) or
 //                 writes the eight children (zero moments), rows cooperatively.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -265,27 +266,38 @@ __global__ void __launch_bounds__(kDensThreads) k_dens_write(DensIn in, DensOut 
             out.v_op[opre] = in.v_op[i];
         }
         __syncthreads();
-        // colour rows and their moments, cooperatively (consecutive floats per thread)
+        // colour rows and their moments, cooperatively: consecutive float4 (rows of
+        // a multiple of 4 floats, 16-byte aligned) or floats per thread
         const int nr = (int)min((int64_t)kDensThreads, P.n - r0);
-        for (int q = threadIdx.x; q < nr * C; q += kDensThreads) {
-            const int j = q / C, f = q - j * C;
+        constexpr int V = (C % 4 == 0) ? 4 : 1;  // floats per access
+        constexpr int CV = C / V;                // accesses per row
+        using T = typename std::conditional<V == 4, float4, float>::type;
+        const T zero{};
+        const T* icol = reinterpret_cast<const T*>(in.col);
+        const T* imc = reinterpret_cast<const T*>(in.m_col);
+        const T* ivc = reinterpret_cast<const T*>(in.v_col);
+        T* ocol = reinterpret_cast<T*>(out.col);
+        T* omc = reinterpret_cast<T*>(out.m_col);
+        T* ovc = reinterpret_cast<T*>(out.v_col);
+        for (int q = threadIdx.x; q < nr * CV; q += kDensThreads) {
+            const int j = q / CV, f = q - j * CV;
             const int no = s_nout[j];
             if (no == 0) continue;
             const long long d = s_dst[j];
-            const size_t src = (size_t)(r0 + j) * C + f;
-            const float cv = in.col[src];
+            const size_t src = (size_t)(r0 + j) * CV + f;
+            const T cv = icol[src];
             if (no == 1) {
                 if (d < cap) {
-                    out.col[(size_t)d * C + f] = cv;
-                    out.m_col[(size_t)d * C + f] = in.m_col[src];
-                    out.v_col[(size_t)d * C + f] = in.v_col[src];
+                    ocol[(size_t)d * CV + f] = cv;
+                    omc[(size_t)d * CV + f] = imc[src];
+                    ovc[(size_t)d * CV + f] = ivc[src];
                 }
             } else {
                 for (int c = 0; c < 8; ++c) {
-                    const size_t o = (size_t)(d + c) * C + f;
-                    out.col[o] = cv;
-                    out.m_col[o] = 0.f;
-                    out.v_col[o] = 0.f;
+                    const size_t o = (size_t)(d + c) * CV + f;
+                    ocol[o] = cv;
+                    omc[o] = zero;
+                    ovc[o] = zero;
                 }
             }
         }

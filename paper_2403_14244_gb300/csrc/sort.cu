@@ -232,7 +232,7 @@ constexpr int kRowWalkMax = 2048;          // tiles per axis for route a (shared
 constexpr uint32_t kL1ChunksMax = 16384;   // most level-1 chunks (columns of H1), fewer for tall frames
 constexpr uint32_t kL1ChunksMin = 1024;
 constexpr uint32_t kH1Words = 1u << 22;    // H1 budget: rows x chunks
-constexpr uint32_t kStage = 2048;          // staged items per chunk
+constexpr uint32_t kStage = 1536;          // staged items per chunk
 constexpr uint32_t kChunkTarget = kStage * 4 / 5;
 constexpr int kWalkWarps = 4;              // warps per CTA of the walk kernels (one chunk each)
 constexpr int kWalkUnroll = 4;             // items per lane per round of the counting walks
