@@ -61,6 +61,24 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the slowest rank's time); x itself
+    when one process runs. Every rank must call it (a collective)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units of all ranks (each does the same work: weak scaling) per second of
+    the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -293,12 +311,7 @@ def run_mine(args, world, rank, local):
     barrier()
     launches = launches_per_step * args.steps
     clk = clocks.stop()
-    elapsed_ms = start.elapsed_time(end)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(start.elapsed_time(end), world, dev)
     # the entry capacity used in the timed region held for every view: re-run
     # each view's binning at that capacity (untimed) and read its status
     entries = []
@@ -309,7 +322,7 @@ def run_mine(args, world, rank, local):
         entries.append(int(info[0]))
     tiles = f.tiles
     ms_per_step = elapsed_ms / args.steps
-    value = world * args.steps / (elapsed_ms / 1e3)
+    value = whole_job_rate(args.steps, world, elapsed_ms / 1e3)
 
     # -------- end to end: host target in pinned memory -> device, step, loss -> host. The copy of
     # the next step's target (into the buffer its graph reads) runs on a copy stream while the
@@ -338,13 +351,8 @@ def run_mine(args, world, rank, local):
         used[v].record(stream)
         loss_host.copy_(ts.loss, non_blocking=True)
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": "steps/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": whole_job_rate(e2e_steps, world, e2e_s), "unit": "steps/s",
            "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4,
            "overlap": "next step's target copied on a second stream during the current step"}
 
