@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
     const void* __restrict__ in_, void* __restrict__ out_, const uint32_t* __restrict__ d_count, uint32_t count_host,
     int shift, const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ status,
     uint32_t* __restrict__ block_counter, uint32_t* __restrict__ info, uint32_t silent_blk = 0xFFFFFFFFu) {
+    pdl_wait();
     {
         const uint64_t seg = blockIdx.y;
         if (IN_KEYS32)

@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(64) k_blend_fwd_sub(const uint2* __restrict__ 
                                                       float* __restrict__ img, float* __restrict__ T_final,
                                                       uint32_t* __restrict__ n_contrib,
                                                       const uint32_t* __restrict__ info) {
+    pdl_wait();
     constexpr int SUB = TS / 8;
     __shared__ float4 s_a[64];
     __shared__ float4 s_c[64];
@@ -237,6 +238,7 @@ __global__ void __launch_bounds__(32, 32) k_blend_bwd_sub(const uint2* __restric
                                                           const float* __restrict__ T_final,
                                                           const uint32_t* __restrict__ n_contrib,
                                                           float4* __restrict__ g2d, const uint32_t* __restrict__ info) {
+    pdl_wait();
     constexpr int SUB = TS / 8;
     if (info[kInfoAbort]) return;
     const int tile = blockIdx.x / (SUB * SUB), q = blockIdx.x % (SUB * SUB);
@@ -252,14 +254,15 @@ cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* i
     if (tiles == 0) return cudaSuccess;
     auto rg = reinterpret_cast<const uint2*>(f.ranges);
     auto rec = reinterpret_cast<const float4*>(f.rec);
+    cudaError_t e = cudaSuccess;
     switch (f.tile) {
         case 8: k_blend_fwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
-        case 16: k_blend_fwd_sub<16><<<tiles * 4, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
-        case 32: k_blend_fwd_sub<32><<<tiles * 16, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        case 16: e = launch_pdl(k_blend_fwd_sub<16>, dim3(tiles * 4), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        case 32: e = launch_pdl(k_blend_fwd_sub<32>, dim3(tiles * 16), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const float* dL, float* g2d, cudaStream_t st) {
@@ -268,14 +271,15 @@ cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const fl
     auto rg = reinterpret_cast<const uint2*>(f.ranges);
     auto rec = reinterpret_cast<const float4*>(f.rec);
     auto g = reinterpret_cast<float4*>(g2d);
+    cudaError_t e = cudaSuccess;
     switch (f.tile) {
         case 8: k_blend_bwd<8><<<tiles, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 16: k_blend_bwd_sub<16><<<tiles * 4, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 32: k_blend_bwd_sub<32><<<tiles * 16, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 16: e = launch_pdl(k_blend_bwd_sub<16>, dim3(tiles * 4), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 32: e = launch_pdl(k_blend_bwd_sub<32>, dim3(tiles * 16), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace igs

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <utility>
 
 #include "igs.h"
 
@@ -49,6 +50,29 @@ extern thread_local const char* g_failed_call;
 #define IGS_STR(x) IGS_STR2(x)
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Programmatic dependent launch: a kernel launched with launch_pdl is set up
+// while its stream predecessor (a kernel) still runs, and calls pdl_wait()
+// before it touches memory, which returns once the predecessor has finished and
+// its writes are visible. Without the launch attribute pdl_wait() is a no-op.
+// (Kernels do not trigger their successors early: resident waiting CTAs then
+// slowed the predecessors' last waves, measured.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Record the first device error of a frame and tell every later step to skip
 // its work (outputs are left untouched).

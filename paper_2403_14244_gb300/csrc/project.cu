@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(32) k_project_rows3(const float4* __restrict__
                                                       float4* __restrict__ rec, uint2* __restrict__ rect,
                                                       float4* __restrict__ disc, uint32_t* __restrict__ count,
                                                       uint32_t* __restrict__ depth_key) {
+    pdl_wait();
     __shared__ float4 s_rows[32 * kProjRowStride];
     const int lane = threadIdx.x;
     const int64_t wb = (int64_t)blockIdx.x * 32;
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restri
                                                             const float4* __restrict__ g2d, float4* __restrict__ d_ms,
                                                             float* __restrict__ d_op, float* __restrict__ d_col,
                                                             AdamState st, AdamParams ap) {
+    pdl_wait();
     constexpr int C = DEG < 0 ? 3 : 3 * (DEG + 1) * (DEG + 1);
     using CT = ColorTile<C>;
     extern __shared__ float4 s_tiles[];
@@ -317,12 +319,13 @@ cudaError_t launch_pb(const igs_scene& sc, const ViewParams& vp, const igs_frame
         if (e != cudaSuccess) return e;
     }
     const unsigned blocks = (unsigned)ceil_div(sc.n, kPbThreads);
-    k<<<blocks, kPbThreads, smem, stream>>>(const_cast<float4*>(reinterpret_cast<const float4*>(sc.means_sigma)),
-                                            const_cast<float*>(sc.opacity), const_cast<float*>(sc.color), sc.n, vp,
-                                            f.count, reinterpret_cast<const float4*>(g2d),
-                                            reinterpret_cast<float4*>(d_ms), d_op, d_col, st, ap);
+    cudaError_t e = launch_pdl(k, dim3(blocks), dim3(kPbThreads), smem, stream,
+                               const_cast<float4*>(reinterpret_cast<const float4*>(sc.means_sigma)),
+                               const_cast<float*>(sc.opacity), const_cast<float*>(sc.color), sc.n, vp, f.count,
+                               reinterpret_cast<const float4*>(g2d), reinterpret_cast<float4*>(d_ms), d_op, d_col, st,
+                               ap);
     count_launches();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <bool ADAM>
@@ -339,6 +342,7 @@ cudaError_t dispatch_pb(const igs_scene& sc, const ViewParams& vp, const igs_fra
 }
 
 __global__ void k_adam_advance(int32_t* __restrict__ state, double lr, double b1, double b2) {
+    pdl_wait();
     const int t = state[0] + 1;
     state[0] = t;
     const double bc1 = 1.0 - pow(b1, (double)t), bc2 = 1.0 - pow(b2, (double)t);
@@ -351,9 +355,9 @@ __global__ void k_adam_advance(int32_t* __restrict__ state, double lr, double b1
 }  // namespace
 
 cudaError_t launch_adam_advance(int32_t* state, double lr, double b1, double b2, cudaStream_t st) {
-    k_adam_advance<<<1, 1, 0, st>>>(state, lr, b1, b2);
+    cudaError_t e = launch_pdl(k_adam_advance, dim3(1), dim3(1), 0, st, state, lr, b1, b2);
     count_launches();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, cudaStream_t st) {
@@ -365,11 +369,11 @@ cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_
     auto rect = reinterpret_cast<uint2*>(f.rect);
 #define IGS_PROJ(D) k_project<D><<<blocks, threads, 0, st>>>(ms, sc.opacity, sc.color, sc.n, vp, rec, rect, reinterpret_cast<float4*>(f.disc), f.count, f.depth_key)
     if (vp.sh_degree == 3 && (reinterpret_cast<uintptr_t>(sc.color) & 15) == 0) {
-        k_project_rows3<<<(unsigned)ceil_div(sc.n, 32), 32, 0, st>>>(ms, sc.opacity, sc.color, sc.n, vp, rec, rect,
-                                                                      reinterpret_cast<float4*>(f.disc), f.count,
-                                                                      f.depth_key);
+        cudaError_t e = launch_pdl(k_project_rows3, dim3((unsigned)ceil_div(sc.n, 32)), dim3(32), 0, st, ms,
+                                   sc.opacity, sc.color, sc.n, vp, rec, rect, reinterpret_cast<float4*>(f.disc),
+                                   f.count, f.depth_key);
         count_launches();
-        return cudaGetLastError();
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     switch (vp.sh_degree) {
         case -1: IGS_PROJ(-1); break;

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
                                                   const uint32_t* __restrict__ count, uint32_t n, int gx,
                                                   int gy, uint32_t* __restrict__ hist, int32_t* __restrict__ grid,
                                                   uint32_t* __restrict__ info) {
+    pdl_wait();
     extern __shared__ int32_t s_grid[];
     __shared__ uint32_t s_h[4][kRadix];
     const int cells = gx * gy;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
                                                                     uint2* __restrict__ ranges,
                                                                     uint32_t* __restrict__ hist,
                                                                     uint32_t* __restrict__ info, uint64_t capacity) {
+    pdl_wait();
     extern __shared__ int32_t s_g[];
     __shared__ uint32_t s_h[8][kRadix];
     __shared__ uint32_t s_warp[kTilesSmallThreads / 32];
@@ -346,6 +348,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* 
                                                                 const uint2* __restrict__ rect, uint32_t rows,
                                                                 uint32_t cmax, uint32_t* __restrict__ H1,
                                                                 const uint32_t* __restrict__ info) {
+    pdl_wait();
     extern __shared__ uint32_t s_walk[];
     const int lane = threadIdx.x & 31;
     uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * rows;
@@ -383,6 +386,7 @@ constexpr int kRowScanThreads = 256;
 __global__ void __launch_bounds__(kRowScanThreads) k_rows_scan(uint32_t* __restrict__ H1, uint32_t cmax,
                                                                uint32_t* __restrict__ len,
                                                                const uint32_t* __restrict__ info) {
+    pdl_wait();
     __shared__ uint32_t s_warp[kRowScanThreads / 32];
     if (info[kInfoAbort]) return;
     uint32_t* row = H1 + (size_t)blockIdx.x * cmax;
@@ -410,6 +414,7 @@ __global__ void __launch_bounds__(kLayoutThreads) k_rows_layout(const uint32_t* 
                                                                 uint32_t tiles_x, uint32_t max_chunks,
                                                                 uint32_t* __restrict__ rowinfo,
                                                                 uint32_t* __restrict__ info) {
+    pdl_wait();
     __shared__ uint32_t s_warp[kLayoutThreads / 32];
     __shared__ unsigned long long s_entries[kRowWalkMax];
     if (info[kInfoAbort]) return;
@@ -454,6 +459,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* 
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 uint32_t* __restrict__ R1,
                                                                 const uint32_t* __restrict__ info) {
+    pdl_wait();
     extern __shared__ uint32_t s_walk[];
     const int lane = threadIdx.x & 31;
     if (info[kInfoAbort]) return;
@@ -528,6 +534,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* 
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 uint32_t* __restrict__ H2,
                                                                 const uint32_t* __restrict__ info) {
+    pdl_wait();
     extern __shared__ uint32_t s_walk[];
     const int lane = threadIdx.x & 31;
     uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * tiles_x;
@@ -565,6 +572,7 @@ __global__ void __launch_bounds__(32 * kColScanWarps) k_cols_scan(uint32_t* __re
                                                                   uint32_t tiles_x, const uint2* __restrict__ ranges,
                                                                   const uint32_t* __restrict__ rowinfo,
                                                                   const uint32_t* __restrict__ info) {
+    pdl_wait();
     __shared__ uint32_t s_seg[kColScanWarps][32];
     if (info[kInfoAbort]) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -602,6 +610,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* 
                                                                 const uint2* __restrict__ ranges,
                                                                 uint32_t* __restrict__ vals,
                                                                 const uint32_t* __restrict__ info) {
+    pdl_wait();
     extern __shared__ uint32_t s_walk[];
     const int lane = threadIdx.x & 31;
     if (info[kInfoAbort]) return;
@@ -815,19 +824,19 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
     // 0. depth-digit histograms; footprint rows -> per-tile counts -> ranges, tile-digit histograms
     const int prep_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 4);
     if ((int64_t)gx * gy <= kGridSmemCells)
-        k_bin_prep<true><<<prep_blocks, 256, (size_t)gx * gy * 4, st>>>(
+        CK(launch_pdl(k_bin_prep<true>, dim3(prep_blocks), dim3(256), (size_t)gx * gy * 4, st, 
             f.depth_key, reinterpret_cast<const uint2*>(f.rect), reinterpret_cast<const float4*>(f.disc), f.tile,
-            footprint, f.count, nn, gx, gy, s.hist, s.grid, f.info);
+            footprint, f.count, nn, gx, gy, s.hist, s.grid, f.info));
     else
-        k_bin_prep<false><<<prep_blocks, 256, 0, st>>>(f.depth_key, reinterpret_cast<const uint2*>(f.rect),
+        CK(launch_pdl(k_bin_prep<false>, dim3(prep_blocks), dim3(256), 0, st, f.depth_key, reinterpret_cast<const uint2*>(f.rect),
                                                        reinterpret_cast<const float4*>(f.disc), f.tile, footprint,
-                                                       f.count, nn, gx, gy, s.hist, s.grid, f.info);
+                                                       f.count, nn, gx, gy, s.hist, s.grid, f.info));
     count_launches();
     CK(cudaGetLastError());
     if ((int64_t)gx * gy <= kGridSmemCells) {
-        k_tiles_small<<<1, kTilesSmallThreads, (size_t)gx * gy * 4, st>>>(s.grid, f.tiles_x, f.tiles_y, tp,
+        CK(launch_pdl(k_tiles_small, dim3(1), dim3(kTilesSmallThreads), (size_t)gx * gy * 4, st, s.grid, f.tiles_x, f.tiles_y, tp,
                                                                            reinterpret_cast<uint2*>(f.ranges), s.hist,
-                                                                           f.info, (uint64_t)cap);
+                                                                           f.info, (uint64_t)cap));
         count_launches();
         CK(cudaGetLastError());
     } else {
@@ -848,16 +857,16 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         uint32_t* status = s.status_depth + (size_t)p * bn * kRadix;
         const uint32_t* hist = s.hist + p * kRadix;
         if (p == 0)
-            k_radix_pass<true, false><<<(unsigned)bn, kSortThreads, 0, st>>>(
+            CK(launch_pdl(k_radix_pass<true, false>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
                 f.depth_key, s.ditems_a, nullptr, nn, 0, hist, status, s.counters + 0, f.info,
-                g_silence_next.exchange(0) ? 1u : 0xFFFFFFFFu);
+                g_silence_next.exchange(0) ? 1u : 0xFFFFFFFFu));
         else if (p == 3)
-            k_radix_pass<false, true><<<(unsigned)bn, kSortThreads, 0, st>>>(
-                s.ditems_a, f.order, nullptr, nn, 24, hist, status, s.counters + 3, f.info);
+            CK(launch_pdl(k_radix_pass<false, true>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
+                s.ditems_a, f.order, nullptr, nn, 24, hist, status, s.counters + 3, f.info, 0xFFFFFFFFu));
         else
-            k_radix_pass<false, false><<<(unsigned)bn, kSortThreads, 0, st>>>(
+            CK(launch_pdl(k_radix_pass<false, false>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
                 p == 1 ? s.ditems_a : s.ditems_b, p == 1 ? s.ditems_b : s.ditems_a, nullptr, nn, 8 * p, hist,
-                status, s.counters + p, f.info);
+                status, s.counters + p, f.info, 0xFFFFFFFFu));
         count_launches();
         CK(cudaGetLastError());
     }
@@ -875,29 +884,29 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
 
         const uint2* rect = reinterpret_cast<const uint2*>(f.rect);
         const uint2* rg = reinterpret_cast<const uint2*>(f.ranges);
-        k_rows_count<<<walk_blocks((const void*)k_rows_count, count1, cmax), 32 * kWalkWarps, count1, st>>>(f.order, rect, rows, cmax, s.walk_h1, f.info);
+        CK(launch_pdl(k_rows_count, dim3(walk_blocks((const void*)k_rows_count, count1, cmax)), dim3(32 * kWalkWarps), count1, st, f.order, rect, rows, cmax, s.walk_h1, f.info));
         count_launches();
         CK(cudaGetLastError());
-        k_rows_scan<<<rows, kRowScanThreads, 0, st>>>(s.walk_h1, cmax, s.walk_len, f.info);
+        CK(launch_pdl(k_rows_scan, dim3(rows), dim3(kRowScanThreads), 0, st, s.walk_h1, cmax, s.walk_len, f.info));
         count_launches();
         CK(cudaGetLastError());
-        k_rows_layout<<<1, kLayoutThreads, 0, st>>>(s.walk_len, rg, rows, cols, (uint32_t)max2, s.walk_rows, f.info);
+        CK(launch_pdl(k_rows_layout, dim3(1), dim3(kLayoutThreads), 0, st, s.walk_len, rg, rows, cols, (uint32_t)max2, s.walk_rows, f.info));
         count_launches();
         CK(cudaGetLastError());
-        k_rows_place<<<walk_blocks((const void*)k_rows_place, place1, cmax), 32 * kWalkWarps, place1, st>>>(f.order, rect, rows, cmax, s.walk_h1, s.walk_len,
-                                                                s.walk_rows, R1, f.info);
+        CK(launch_pdl(k_rows_place, dim3(walk_blocks((const void*)k_rows_place, place1, cmax)), dim3(32 * kWalkWarps), place1, st, f.order, rect, rows, cmax, s.walk_h1, s.walk_len,
+                                                                s.walk_rows, R1, f.info));
         count_launches();
         CK(cudaGetLastError());
         const DiscRef disc{rect, reinterpret_cast<const float4*>(f.disc), f.tile, 1.0f / (float)f.tile, footprint};
-        k_cols_count<<<walk_blocks((const void*)k_cols_count, count2, max2), 32 * kWalkWarps, count2, st>>>(R1, disc, rows, cols, s.walk_len, s.walk_rows,
-                                                                s.walk_h2, f.info);
+        CK(launch_pdl(k_cols_count, dim3(walk_blocks((const void*)k_cols_count, count2, max2)), dim3(32 * kWalkWarps), count2, st, R1, disc, rows, cols, s.walk_len, s.walk_rows,
+                                                                s.walk_h2, f.info));
         count_launches();
         CK(cudaGetLastError());
-        k_cols_scan<<<rows, 32 * kColScanWarps, 0, st>>>(s.walk_h2, rows, cols, rg, s.walk_rows, f.info);
+        CK(launch_pdl(k_cols_scan, dim3(rows), dim3(32 * kColScanWarps), 0, st, s.walk_h2, rows, cols, rg, s.walk_rows, f.info));
         count_launches();
         CK(cudaGetLastError());
-        k_cols_place<<<walk_blocks((const void*)k_cols_place, place2, max2), 32 * kWalkWarps, place2, st>>>(R1, disc, rows, cols, s.walk_len, s.walk_rows,
-                                                                s.walk_h2, rg, f.vals, f.info);
+        CK(launch_pdl(k_cols_place, dim3(walk_blocks((const void*)k_cols_place, place2, max2)), dim3(32 * kWalkWarps), place2, st, R1, disc, rows, cols, s.walk_len, s.walk_rows,
+                                                                s.walk_h2, rg, f.vals, f.info));
         count_launches();
         CK(cudaGetLastError());
         return cudaSuccess;
@@ -922,12 +931,12 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         uint32_t* status = s.status_tile + (size_t)p * bc * kRadix;
         const uint32_t* hist = s.hist + (4 + p) * kRadix;
         if (p == tp - 1)
-            k_radix_pass<false, true><<<(unsigned)bc, kSortThreads, 0, st>>>(
-                in, f.vals, f.info + kInfoM, 0u, 8 * p, hist, status, s.counters + 5 + p, f.info);
+            CK(launch_pdl(k_radix_pass<false, true>, dim3((unsigned)bc), dim3(kSortThreads), 0, st, 
+                in, f.vals, f.info + kInfoM, 0u, 8 * p, hist, status, s.counters + 5 + p, f.info, 0xFFFFFFFFu));
         else
-            k_radix_pass<false, false><<<(unsigned)bc, kSortThreads, 0, st>>>(
+            CK(launch_pdl(k_radix_pass<false, false>, dim3((unsigned)bc), dim3(kSortThreads), 0, st, 
                 in, (p % 2 == 0) ? s.items_b : s.items_a, f.info + kInfoM, 0u, 8 * p, hist, status,
-                s.counters + 5 + p, f.info);
+                s.counters + 5 + p, f.info, 0xFFFFFFFFu));
         count_launches();
         CK(cudaGetLastError());
     }

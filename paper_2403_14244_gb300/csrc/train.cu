@@ -11,6 +11,7 @@ namespace {
 __global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const float* __restrict__ target,
                                             int64_t count, float inv_count, float* __restrict__ loss,
                                             float* __restrict__ grad) {
+    pdl_wait();
     __shared__ float s_w[8];
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
