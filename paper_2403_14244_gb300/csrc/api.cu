@@ -246,7 +246,11 @@ igs_status igs_blend_bwd(const igs_frame* frame, const igs_opts* opts, const flo
     if (!dL_dimg || !g2d) return fail(IGS_ERR_INVALID_ARG, "dL_dimg or g2d is NULL");
     if (reinterpret_cast<uintptr_t>(g2d) & 15) return fail(IGS_ERR_INVALID_ARG, "g2d must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(g2d, 0, (size_t)frame->n * 32, s);
+    igs::ZeroRanges z = {};
+    z.ptr[0] = g2d;
+    z.bytes[0] = (unsigned long long)frame->n * 32;
+    z.count = frame->n > 0 ? 1 : 0;
+    cudaError_t e = igs::launch_zero(z, s);
     if (e != cudaSuccess) return cuda_status(e, "igs_blend_bwd");
     const igs::BlendParams bp = blend_params(frame, opts);
     return cuda_status(igs::launch_blend_bwd(*frame, bp, dL_dimg, g2d, s), "igs_blend_bwd");

@@ -74,6 +74,16 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Zero up to kZeroRanges byte ranges in one launch (16-byte aligned starts and
+// sizes multiple of 4), so that a chain of kernels is not split by memset nodes.
+constexpr int kZeroRanges = 8;
+struct ZeroRanges {
+    void* ptr[kZeroRanges];
+    unsigned long long bytes[kZeroRanges];
+    int count;
+};
+cudaError_t launch_zero(const ZeroRanges& z, cudaStream_t s);
+
 // Record the first device error of a frame and tell every later step to skip
 // its work (outputs are left untouched).
 __device__ __forceinline__ void record_error(uint32_t* info, uint32_t code) {

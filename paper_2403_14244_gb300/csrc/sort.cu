@@ -808,18 +808,24 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
     const int gx = f.tiles_x + 1, gy = f.tiles_y + 1;
     cudaError_t e;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { g_failed_call = #x " (sort.cu:" IGS_STR(__LINE__) ")"; return e; } } while (0)
-    // reset state: status words, histograms, counters, look-back words, difference grid
-    CK(cudaMemsetAsync(f.info, 0, kInfoWords * 4, st));
-    CK(cudaMemsetAsync(s.hist, 0, 8 * kRadix * 4, st));
-    CK(cudaMemsetAsync(s.counters, 0, 16 * 4, st));
-    CK(cudaMemsetAsync(s.status_depth, 0, (size_t)4 * bn * kRadix * 4, st));
-    if (tp > 0) CK(cudaMemsetAsync(s.status_tile, 0, (size_t)tp * bc * kRadix * 4, st));
-    CK(cudaMemsetAsync(s.scan_status, 0, (size_t)bs * 8, st));
-    CK(cudaMemsetAsync(s.grid, 0, (size_t)gx * gy * 4, st));
-    if (n == 0) {
-        CK(cudaMemsetAsync(f.ranges, 0, (size_t)tiles * 8, st));
-        return cudaSuccess;
+    // reset state: status words, histograms, counters, look-back words, difference grid (one launch)
+    {
+        ZeroRanges z = {};
+        auto add = [&](void* p, size_t bytes) {
+            z.ptr[z.count] = p;
+            z.bytes[z.count++] = bytes;
+        };
+        add(f.info, kInfoWords * 4);
+        add(s.hist, 8 * kRadix * 4);
+        add(s.counters, 16 * 4);
+        add(s.status_depth, (size_t)4 * bn * kRadix * 4);
+        if (tp > 0) add(s.status_tile, (size_t)tp * bc * kRadix * 4);
+        add(s.scan_status, (size_t)bs * 8);
+        add(s.grid, (size_t)gx * gy * 4);
+        if (n == 0) add(f.ranges, (size_t)tiles * 8);
+        CK(launch_zero(z, st));
     }
+    if (n == 0) return cudaSuccess;
     const uint32_t nn = (uint32_t)n;
     // 0. depth-digit histograms; footprint rows -> per-tile counts -> ranges, tile-digit histograms
     const int prep_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 4);

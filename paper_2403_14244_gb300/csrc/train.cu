@@ -67,7 +67,31 @@ __global__ void k_adam_scalar(float* __restrict__ p, const float* __restrict__ g
         adam1(p[i], g[i], m[i], v[i], a);
 }
 
+// Range blockIdx.y of z, as 16-byte stores with a 4-byte tail.
+__global__ void __launch_bounds__(256) k_zero(ZeroRanges z) {
+    pdl_wait();
+    const int r = blockIdx.y;
+    if (r >= z.count) return;
+    char* p = static_cast<char*>(z.ptr[r]);
+    const unsigned long long n16 = z.bytes[r] / 16;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n16;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        reinterpret_cast<float4*>(p)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const unsigned long long tail = (z.bytes[r] - 16 * n16) / 4;
+    if (blockIdx.x == 0 && threadIdx.x < tail) reinterpret_cast<float*>(p + 16 * n16)[threadIdx.x] = 0.f;
+}
+
 }  // namespace
+
+cudaError_t launch_zero(const ZeroRanges& z, cudaStream_t st) {
+    if (z.count <= 0) return cudaSuccess;
+    unsigned long long most = 0;
+    for (int r = 0; r < z.count; ++r) most = std::max(most, z.bytes[r]);
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)(most / 16), 256), 152 * 8));
+    cudaError_t e = launch_pdl(k_zero, dim3(gx, (unsigned)z.count), dim3(256), 0, st, z);
+    count_launches();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 cudaError_t launch_l1(const float* img, const float* target, int64_t count, float* loss, float* grad,
                       cudaStream_t st) {
