@@ -11,8 +11,10 @@
 // (the children partition its points) and its id is smaller, so every cell
 // comes after its ancestors, and the greedy stops at the first cell of the
 // order whose split (adding its non-empty children minus one) does not fit.
-// One CTA finds that prefix by bisection on the 64-bit error key, weighted by
-// the leaves each split adds, and then on the id among equal keys.
+// The prefix is found by a radix selection on the 64-bit key (8 bits at a time,
+// histograms weighted by the leaves each split adds), and then on the id among
+// equal keys: each pass a histogram over all cells by many CTAs and a one-thread
+// pick of the digit. The leaves are then emitted in id order, a CTA per chunk.
 #include <algorithm>
 #include <cmath>
 
@@ -90,7 +92,9 @@ __global__ void k_oct_up(OctCell* __restrict__ st, int l) {
     }
 }
 
-constexpr int kOctThreads = 1024;
+constexpr int kOctThreads = 256;
+constexpr int kOctChunk = kOctThreads * 8;  // cells per CTA of the emission
+constexpr int kOctPasses = 11;              // 8 digits of the key, then 3 of the id (ids < 2^24)
 
 // Error of a cell: max(0, sum_c (S2_c - S1_c^2 / n)) in double, one rounding per
 // step in channel order (0 for an empty cell).
@@ -115,7 +119,179 @@ __device__ __forceinline__ uint32_t oct_inc(const OctCell* __restrict__ st, long
     return kids - 1;
 }
 
-__device__ __forceinline__ long long block_sum(long long v, long long* s_tmp) {
+__device__ __forceinline__ int oct_level(long long id) {
+    int l = 0;
+    while (oct_off(l + 1) <= id) ++l;
+    return l;
+}
+
+// The selection's state between passes. X = max{X : 1 + W(X) > k_max}, W(X) the
+// increments of the splittable cells with key >= X, is found 8 bits at a time
+// from the top: `above` = 1 + the increments of keys whose fixed high bits exceed
+// `prefix`. Then, among keys == X, the first id (in id order) whose cumulative
+// increments no longer fit k_max - above is found the same way on the id bits.
+struct OctSel {
+    unsigned long long prefix;  // key bits fixed so far; X once the key passes end
+    long long above;
+    unsigned long long idp;     // id bits fixed so far
+    long long below;            // increments of keys == X with ids below the fixed id bits
+    long long ihi;              // the last id of key X that splits
+    int done;                   // no pass left to run
+    int all;                    // every splittable cell splits
+};
+
+// Keys and increments of level l (one launch per level, top down): key = min(error,
+// parent's key), which keeps every child after its parent in the order whatever
+// the rounding, stored as bits ordered like the value.
+__global__ void k_oct_keys(const OctCell* __restrict__ st, int l, int L, unsigned long long* __restrict__ keys,
+                           uint8_t* __restrict__ inc8) {
+    const long long cells = 1LL << (3 * l);
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < cells;
+         m += (long long)gridDim.x * blockDim.x) {
+        const long long id = oct_off(l) + m;
+        double k = oct_err(st[id]);
+        if (l > 0) k = fmin(k, __longlong_as_double((long long)keys[oct_off(l - 1) + (m >> 3)]));
+        keys[id] = (unsigned long long)__double_as_longlong(k);
+        inc8[id] = (uint8_t)oct_inc(st, id, l, L);
+    }
+}
+
+// One pass of the selection: the histogram, over one 8-bit digit, of the
+// increments of the cells still in the running (a CTA-local histogram, then one
+// atomic per bin and CTA).
+__global__ void __launch_bounds__(kOctThreads) k_oct_hist(const unsigned long long* __restrict__ keys,
+                                                          const uint8_t* __restrict__ inc8, long long items,
+                                                          const OctSel* __restrict__ sel, int pass,
+                                                          uint32_t* __restrict__ hist) {
+    __shared__ uint32_t s_h[256];
+    if (sel->done) return;
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned long long prefix = sel->prefix, idp = sel->idp;
+    if (pass < 8) {
+        const int sh = 8 * (7 - pass);
+        const unsigned long long hi = pass == 0 ? 0ull : (~0ull << (sh + 8));
+        for (long long i = blockIdx.x * (long long)kOctThreads + threadIdx.x; i < items;
+             i += (long long)gridDim.x * kOctThreads) {
+            const uint32_t c = inc8[i];
+            if (c == 0xFFu || c == 0) continue;
+            const unsigned long long k = keys[i];
+            if ((k & hi) == prefix) atomicAdd(&s_h[(k >> sh) & 0xFFu], c);
+        }
+    } else {
+        const int sh = 8 * (10 - pass);
+        const unsigned long long hi = ~0ull << (sh + 8);
+        for (long long i = blockIdx.x * (long long)kOctThreads + threadIdx.x; i < items;
+             i += (long long)gridDim.x * kOctThreads) {
+            const uint32_t c = inc8[i];
+            if (c == 0xFFu || c == 0) continue;
+            if (keys[i] == prefix && ((unsigned long long)i & hi) == idp)
+                atomicAdd(&s_h[((unsigned long long)i >> sh) & 0xFFu], c);
+        }
+    }
+    __syncthreads();
+    if (s_h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_h[threadIdx.x]);
+}
+
+// One CTA of 256 fixes the pass's digit from its histogram: thread t holds one bin
+// (bin 255 - t for the key, taken from the top; bin t for the id) and an
+// inclusive scan gives each bin the increments at and above it (key) or at and
+// below it (id).
+__global__ void __launch_bounds__(256) k_oct_pick(const OctCell* __restrict__ st, const uint32_t* __restrict__ hist,
+                                                  int pass, long long items, long long k_max,
+                                                  OctSel* __restrict__ sel) {
+    __shared__ long long s_scan[256];
+    __shared__ OctSel s;
+    __shared__ int s_b;
+    const int t = threadIdx.x;
+    const bool key = pass < 8;
+    if (t == 0) {
+        s = *sel;
+        s_b = key ? 0 : 256;
+    }
+    __syncthreads();
+    if (s.done) return;  // uniform over the CTA
+    const int bin = key ? 255 - t : t;
+    const long long h = hist[bin];
+    long long v = h;
+    s_scan[t] = v;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const long long add = t >= o ? s_scan[t - o] : 0;
+        __syncthreads();
+        v += add;
+        s_scan[t] = v;
+        __syncthreads();
+    }
+    long long above = s.above;
+    if (pass == 0) {
+        // 1 + W(0): the leaves if every splittable cell split
+        if (st[0].n == 0 || 1 + s_scan[255] <= k_max) {
+            if (t == 0) {
+                s.all = 1;
+                s.done = 1;
+                *sel = s;
+            }
+            return;
+        }
+        above = 1;
+    }
+    if (key) {
+        // the highest digit at which above + the increments at and above it exceed k_max (0 if none)
+        if (bin >= 1 && above + v > k_max) atomicMax(&s_b, bin);
+    } else {
+        // the lowest digit at which the increments of key X, in id order, leave k_max - above
+        if (s.below + v > k_max - above) atomicMin(&s_b, bin);
+    }
+    __syncthreads();
+    if (t != 0) return;
+    const int d = s_b;
+    if (key) {
+        s.prefix |= (unsigned long long)d << (8 * (7 - pass));
+        s.above = above + s_scan[255 - d] - (long long)hist[d];  // + the increments above digit d
+    } else if (d == 256) {  // every cell of key X fits
+        s.ihi = items - 1;
+        s.done = 1;
+    } else {
+        s.idp |= (unsigned long long)d << (8 * (10 - pass));
+        s.below += s_scan[d] - (long long)hist[d];  // + the increments below digit d
+        if (pass == kOctPasses - 1) {
+            s.ihi = (long long)s.idp - 1;  // idp: the first id whose increment does not fit
+            s.done = 1;
+        }
+    }
+    *sel = s;
+}
+
+__global__ void k_oct_split(const OctCell* __restrict__ st, const unsigned long long* __restrict__ keys,
+                            const uint8_t* __restrict__ inc8, long long items, const OctSel* __restrict__ sel,
+                            uint8_t* __restrict__ split) {
+    const bool root = st[0].n > 0;
+    const bool all = sel->all != 0;
+    const unsigned long long X = sel->prefix;
+    const long long ihi = sel->ihi;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < items;
+         i += (long long)gridDim.x * blockDim.x) {
+        bool sp = false;
+        if (root && inc8[i] != 0xFFu) sp = all || keys[i] > X || (keys[i] == X && i <= ihi);
+        split[i] = sp ? 1 : 0;
+    }
+}
+
+// Whether cell id holds a Gaussian: non-empty, its parent split (or the root), and
+// itself not split (or the finest level).
+__device__ __forceinline__ bool oct_leaf(const OctCell* __restrict__ st, const uint8_t* __restrict__ split,
+                                         long long id, long long cells, int L, int* lvl, long long* mor) {
+    if (id >= cells || st[id].n == 0) return false;
+    const int l = oct_level(id);
+    const long long m = id - oct_off(l);
+    *lvl = l;
+    *mor = m;
+    const bool parent_split = l == 0 || split[oct_off(l - 1) + (m >> 3)];
+    return parent_split && (l == L || !split[id]);
+}
+
+__device__ __forceinline__ long long oct_block_sum(long long v, long long* s_tmp) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
@@ -126,104 +302,54 @@ __device__ __forceinline__ long long block_sum(long long v, long long* s_tmp) {
     return t;
 }
 
-__device__ __forceinline__ int oct_level(long long id) {
-    int l = 0;
-    while (oct_off(l + 1) <= id) ++l;
-    return l;
-}
-
-// One CTA: keys and increments of every cell below the finest level, the split
-// prefix of the order, and the split flags.
-__global__ void __launch_bounds__(kOctThreads) k_oct_select(const OctCell* __restrict__ st, OctParams P,
-                                                           unsigned long long* __restrict__ keys,
-                                                           uint8_t* __restrict__ inc8, uint8_t* __restrict__ split) {
+// Leaves per chunk of kOctChunk cells.
+__global__ void __launch_bounds__(kOctThreads) k_oct_count(const OctCell* __restrict__ st,
+                                                           const uint8_t* __restrict__ split, int L,
+                                                           uint32_t* __restrict__ chunk_leaves) {
     __shared__ long long s_tmp[kOctThreads / 32];
-    const long long items = oct_off(P.L);
-    // key = min(error, parent's key), level by level (keeps every child after its
-    // parent in the order whatever the rounding), as bits ordered like the value
-    for (int l = 0; l < P.L; ++l) {
-        for (long long m = threadIdx.x; m < (1LL << (3 * l)); m += kOctThreads) {
-            const long long id = oct_off(l) + m;
-            double k = oct_err(st[id]);
-            if (l > 0) k = fmin(k, __longlong_as_double((long long)keys[oct_off(l - 1) + (m >> 3)]));
-            keys[id] = (unsigned long long)__double_as_longlong(k);
-            inc8[id] = (uint8_t)oct_inc(st, id, l, P.L);
-        }
-        __syncthreads();
+    const long long cells = oct_off(L + 1), c0 = (long long)blockIdx.x * kOctChunk;
+    long long n = 0;
+    for (int j = threadIdx.x; j < kOctChunk; j += kOctThreads) {
+        int l;
+        long long m;
+        n += oct_leaf(st, split, c0 + j, cells, L, &l, &m);
     }
-    const bool root = st[0].n > 0;
-    // W(X) = sum of the increments of splittable cells with key >= X
-    auto W = [&](unsigned long long X) {
-        long long w = 0;
-        for (long long i = threadIdx.x; i < items; i += kOctThreads)
-            if (inc8[i] != 0xFFu && keys[i] >= X) w += inc8[i];
-        return block_sum(w, s_tmp);
-    };
-    bool all = true;
-    unsigned long long X = 0;
-    long long Ihi = -1;
-    if (root && 1 + W(0) > P.k_max) {
-        all = false;
-        // X = max{X : 1 + W(X) > k_max}; invariant: 1 + W(lo) > k_max, 1 + W(hi + 1) <= k_max
-        unsigned long long lo = 0, hi = ~0ULL;
-        while (lo < hi) {
-            const unsigned long long mid = lo + (hi - lo) / 2 + 1;
-            if (1 + W(mid) > P.k_max) lo = mid; else hi = mid - 1;
-        }
-        X = lo;
-        long long gt = 0;
-        for (long long i = threadIdx.x; i < items; i += kOctThreads)
-            if (inc8[i] != 0xFFu && keys[i] > X) gt += inc8[i];
-        const long long base = 1 + block_sum(gt, s_tmp);  // <= k_max
-        // Ihi = max{I : base + sum of increments of cells with key == X and id <= I <= k_max} (-1: none)
-        long long a = -1, b = items - 1;
-        while (a < b) {
-            const long long mid = a + (b - a + 1) / 2;
-            long long w = 0;
-            for (long long i = threadIdx.x; i <= mid; i += kOctThreads)
-                if (inc8[i] != 0xFFu && keys[i] == X) w += inc8[i];
-            if (base + block_sum(w, s_tmp) <= P.k_max) a = mid; else b = mid - 1;
-        }
-        Ihi = a;
-    }
-    for (long long i = threadIdx.x; i < items; i += kOctThreads) {
-        bool sp = false;
-        if (root && inc8[i] != 0xFFu) sp = all || keys[i] > X || (keys[i] == X && i <= Ihi);
-        split[i] = sp ? 1 : 0;
-    }
+    n = oct_block_sum(n, s_tmp);
+    if (threadIdx.x == 0) chunk_leaves[blockIdx.x] = (uint32_t)n;
 }
 
-// One CTA: the non-empty leaves in id order, one Gaussian each.
+// The non-empty leaves in id order, one Gaussian each: a CTA per chunk, placed
+// after the leaves of the chunks before it.
 __global__ void __launch_bounds__(kOctThreads) k_oct_emit(const OctCell* __restrict__ st,
-                                                         const uint8_t* __restrict__ split, OctParams P,
+                                                         const uint8_t* __restrict__ split,
+                                                         const uint32_t* __restrict__ chunk_leaves, OctParams P,
                                                          float4* __restrict__ out_ms, float* __restrict__ out_op,
                                                          float* __restrict__ out_col, int32_t* __restrict__ count) {
+    __shared__ long long s_tmp[kOctThreads / 32];
     __shared__ int s_warp[kOctThreads / 32];
-    __shared__ long long s_base;
-    if (threadIdx.x == 0) s_base = 0;
-    __syncthreads();
+    __shared__ float s_dc[3 * kOctThreads];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long cells = oct_off(P.L + 1);
-    for (long long c0 = 0; c0 < cells; c0 += kOctThreads) {
-        const long long id = c0 + threadIdx.x;
-        bool leaf = false;
+    long long before = 0;
+    for (unsigned b = threadIdx.x; b < blockIdx.x; b += kOctThreads) before += chunk_leaves[b];
+    long long base = oct_block_sum(before, s_tmp);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        *count = (int32_t)min(base + (long long)chunk_leaves[blockIdx.x], P.k_max);
+    if (base >= P.k_max) return;  // uniform over the CTA
+    const long long cells = oct_off(P.L + 1), c0 = (long long)blockIdx.x * kOctChunk;
+    for (int j0 = 0; j0 < kOctChunk; j0 += kOctThreads) {
+        const long long id = c0 + j0 + threadIdx.x;
         int l = 0;
         long long m = 0;
-        if (id < cells && st[id].n > 0) {
-            l = oct_level(id);
-            m = id - oct_off(l);
-            const bool parent_split = l == 0 || split[oct_off(l - 1) + (m >> 3)];
-            leaf = parent_split && (l == P.L || !split[id]);
-        }
+        const bool leaf = oct_leaf(st, split, id, cells, P.L, &l, &m);
         const uint32_t bal = __ballot_sync(0xffffffffu, leaf);
         if (lane == 0) s_warp[w] = __popc(bal);
         __syncthreads();
-        long long before = s_base, total = 0;
+        long long pos = base, total = 0;
         for (int i = 0; i < kOctThreads / 32; ++i) {
-            if (i < w) before += s_warp[i];
+            if (i < w) pos += s_warp[i];
             total += s_warp[i];
         }
-        const long long pos = before + __popc(bal & ((1u << lane) - 1u));
+        pos += __popc(bal & ((1u << lane) - 1u));
         if (leaf && pos < P.k_max) {
             const OctCell& s = st[id];
             uint32_t c3[3] = {0u, 0u, 0u};
@@ -235,39 +361,77 @@ __global__ void __launch_bounds__(kOctThreads) k_oct_emit(const OctCell* __restr
                                       (float)__dadd_rn((double)P.lo[2], __dmul_rn((double)c3[2] + 0.5, cs)),
                                       P.log_half[l]);
             out_op[pos] = P.op_value;
-            float* cc = out_col + (size_t)P.C * pos;
-            for (int k = 3; k < P.C; ++k) cc[k] = 0.f;
+            float* dc = s_dc + 3 * (pos - base);
             for (int ch = 0; ch < 3; ++ch) {
                 const double mean = __ddiv_rn((double)s.s1[ch], __dmul_rn(4096.0, (double)s.n));
-                cc[ch] = P.sh < 0 ? (float)mean : (float)__ddiv_rn(__dsub_rn(mean, 0.5), P.y00);
+                dc[ch] = P.sh < 0 ? (float)mean : (float)__ddiv_rn(__dsub_rn(mean, 0.5), P.y00);
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_base += total;
-        __syncthreads();
+        // the round's leaves hold positions [base, base + total): their colour rows are one
+        // contiguous range, written by the whole CTA (DC from shared memory, the rest 0)
+        const long long rows = min(total, P.k_max - base);
+        for (long long i = threadIdx.x; i < rows * P.C; i += kOctThreads) {
+            const long long r = i / P.C;
+            const int k = (int)(i - r * P.C);
+            out_col[(size_t)P.C * base + i] = k < 3 ? s_dc[3 * r + k] : 0.f;
+        }
+        base += total;
+        __syncthreads();  // s_warp is rewritten by the next round
     }
-    if (threadIdx.x == 0) *count = (int32_t)min(s_base, P.k_max);
 }
 
 }  // namespace
 
+// Scratch: cell statistics, keys and increments of the cells above the finest
+// level, split flags, leaves per emission chunk, the selection's state and its
+// histograms (one per pass).
+struct OctWork {
+    OctCell* stats;
+    unsigned long long* keys;
+    uint8_t *inc8, *split;
+    uint32_t* chunk_leaves;
+    OctSel* sel;
+    uint32_t* hist;
+    size_t bytes;
+};
+
+OctWork oct_work(int L, void* base) {
+    const size_t cells = (size_t)oct_off(L + 1), items = (size_t)oct_off(L);
+    const size_t chunks = (cells + kOctChunk - 1) / kOctChunk;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const uintptr_t w = reinterpret_cast<uintptr_t>(base);
+    OctWork o;
+    size_t at = 0;
+    o.stats = reinterpret_cast<OctCell*>(w + at);
+    at += up(cells * sizeof(OctCell));
+    o.keys = reinterpret_cast<unsigned long long*>(w + at);
+    at += up(items * 8);
+    o.inc8 = reinterpret_cast<uint8_t*>(w + at);
+    at += up(items + 1);
+    o.split = reinterpret_cast<uint8_t*>(w + at);
+    at += up(items + 1);
+    o.chunk_leaves = reinterpret_cast<uint32_t*>(w + at);
+    at += up(chunks * 4);
+    o.sel = reinterpret_cast<OctSel*>(w + at);  // the state and the histograms are zeroed together
+    at += up(sizeof(OctSel));
+    o.hist = reinterpret_cast<uint32_t*>(w + at);
+    at += up((size_t)kOctPasses * 256 * 4);
+    o.bytes = at;
+    return o;
+}
+
 size_t octree_work_bytes(int L) {
     if (L < 0 || L > 7) return 0;
-    const size_t cells = (size_t)oct_off(L + 1), items = (size_t)oct_off(L);
-    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    return up(cells * sizeof(OctCell)) + up(items * 8) + up(items + 1) + up(items + 1);
+    return oct_work(L, nullptr).bytes;
 }
 
 cudaError_t launch_octree_init(const float* pts, const float* cols, long long npts, const float lo[3], float side,
                                int L, long long k_max, float opacity, int sh_degree, int param_mode, float* out_ms,
                                float* out_op, float* out_col, int32_t* count, void* work, cudaStream_t st) {
-    const size_t cells = (size_t)oct_off(L + 1), items = (size_t)oct_off(L);
-    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    char* w = static_cast<char*>(work);
-    auto* stats = reinterpret_cast<OctCell*>(w);
-    auto* keys = reinterpret_cast<unsigned long long*>(w + up(cells * sizeof(OctCell)));
-    auto* inc8 = reinterpret_cast<uint8_t*>(w + up(cells * sizeof(OctCell)) + up(items * 8));
-    auto* split = inc8 + up(items + 1);
+    const long long cells = oct_off(L + 1), items = oct_off(L);
+    const OctWork o = oct_work(L, work);
+    OctCell* stats = o.stats;
     OctParams P;
     for (int a = 0; a < 3; ++a) P.lo[a] = lo[a];
     P.inv = (float)((double)(1 << L) / (double)side);
@@ -297,9 +461,30 @@ cudaError_t launch_octree_init(const float* pts, const float* cols, long long np
         ++launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_oct_select<<<1, kOctThreads, 0, st>>>(stats, P, keys, inc8, split);
-    k_oct_emit<<<1, kOctThreads, 0, st>>>(stats, split, P, reinterpret_cast<float4*>(out_ms), out_op, out_col,
-                                          count);
+    for (int l = 0; l < L; ++l) {
+        const long long n = 1LL << (3 * l);
+        k_oct_keys<<<(unsigned)std::min<long long>(ceil_div(n, 256), 152 * 8), 256, 0, st>>>(stats, l, L, o.keys,
+                                                                                           o.inc8);
+        ++launches;
+    }
+    if (L > 0) {
+        e = cudaMemsetAsync(o.sel, 0, reinterpret_cast<char*>(o.hist + kOctPasses * 256) -
+                                          reinterpret_cast<char*>(o.sel), st);
+        if (e != cudaSuccess) return e;
+        const unsigned hblocks = (unsigned)std::min<long long>(ceil_div(items, kOctThreads * 4), 152 * 4);
+        for (int pass = 0; pass < kOctPasses; ++pass) {
+            k_oct_hist<<<hblocks, kOctThreads, 0, st>>>(o.keys, o.inc8, items, o.sel, pass, o.hist + 256 * pass);
+            k_oct_pick<<<1, 256, 0, st>>>(stats, o.hist + 256 * pass, pass, items, k_max, o.sel);
+            launches += 2;
+        }
+        k_oct_split<<<(unsigned)std::min<long long>(ceil_div(items, 256), 152 * 8), 256, 0, st>>>(
+            stats, o.keys, o.inc8, items, o.sel, o.split);
+        ++launches;
+    }
+    const unsigned chunks = (unsigned)ceil_div(cells, kOctChunk);
+    k_oct_count<<<chunks, kOctThreads, 0, st>>>(stats, o.split, L, o.chunk_leaves);
+    k_oct_emit<<<chunks, kOctThreads, 0, st>>>(stats, o.split, o.chunk_leaves, P, reinterpret_cast<float4*>(out_ms),
+                                               out_op, out_col, count);
     launches += 2;
     count_launches(launches);
     return cudaGetLastError();
