@@ -570,19 +570,13 @@ def run_octree(dev, n=2_000_000, levels=7, k_max=500_000, reps=3):
     """Octree initialisation of 3D Gaussians from a seeded coloured point set
     (n points: 64 clusters and a uniform background in [-1, 1]^3, colours with
     structure at several scales), cells down to side 2 / 2^levels, at most
-    k_max Gaussians: time per call (statistics, up-sweep, one-CTA selection,
-    emission) and the Gaussians made."""
-    import numpy as np
+    k_max Gaussians: time per call (statistics, up-sweep, radix selection of
+    the splits, emission) and the Gaussians made."""
     import torch
 
-    from paper_2403_14244_gb300 import igs
+    from paper_2403_14244_gb300 import igs, scenes
 
-    rng = np.random.default_rng(8)
-    centres = rng.uniform(-0.8, 0.8, (64, 3))
-    p = np.concatenate([centres[rng.integers(0, 64, n // 2)] + rng.normal(0, 0.05, (n // 2, 3)),
-                        rng.uniform(-1, 1, (n - n // 2, 3))]).astype(np.float32)
-    c = np.clip(np.stack([0.5 + 0.4 * np.sin(4 * p[:, 0]), 0.5 + 0.4 * np.cos(6 * p[:, 1] * p[:, 2]),
-                          (p[:, 2] > 0.1) * 0.7 + 0.15], 1) + rng.normal(0, 0.03, (n, 3)), 0, 1).astype(np.float32)
+    p, c = scenes.point_cloud(n, seed=8)
     tp, tc = torch.from_numpy(p).to(dev), torch.from_numpy(c).to(dev)
     igs.octree_init(tp, tc, (-1, -1, -1), 2.0, levels, k_max)
     torch.cuda.synchronize(dev)

@@ -267,3 +267,18 @@ def fit2d_particles(k, side, seed, sigma=(1.0, 12.0)):
     p[:, 2] = rng.uniform(np.log(sigma[0]), np.log(sigma[1]), size=k)
     p[:, 3:6] = rng.uniform(0.0, 1.0, size=(k, 3))
     return p
+
+
+def point_cloud(n, seed=8, clusters=64, spread=0.05):
+    """Seeded coloured point set for the Octree initialisation: half the points
+    from `clusters` Gaussian clusters (centres U[-0.8, 0.8]^3, std `spread`),
+    half uniform in [-1, 1]^3; colours with structure at several scales (two
+    smooth waves and a step in z) plus N(0, 0.03^2) noise, clipped to [0, 1].
+    Returns (points float32 [n, 3], colours float32 [n, 3])."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(-0.8, 0.8, (clusters, 3))
+    p = np.concatenate([centres[rng.integers(0, clusters, n // 2)] + rng.normal(0, spread, (n // 2, 3)),
+                        rng.uniform(-1, 1, (n - n // 2, 3))]).astype(np.float32)
+    c = np.clip(np.stack([0.5 + 0.4 * np.sin(4 * p[:, 0]), 0.5 + 0.4 * np.cos(6 * p[:, 1] * p[:, 2]),
+                          (p[:, 2] > 0.1) * 0.7 + 0.15], 1) + rng.normal(0, 0.03, (n, 3)), 0, 1).astype(np.float32)
+    return p, c

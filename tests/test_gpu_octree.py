@@ -55,3 +55,35 @@ def test_octree_renders():
     img, f = Renderer(tile=16).run_forward(igs.Scene(ms.contiguous(), op.contiguous(), col.contiguous()), cam)
     st, info = igs.frame_status(f)
     assert st == igs.OK and info[0] > 0 and float(img.mean()) > 0.01
+
+
+@pytest.mark.parametrize("k_max", [64, 200, 1000, 5000])
+def test_octree_ties_at_the_budget(k_max):
+    """Colours constant on the 64 level-2 cells: every cell below level 2 has error exactly 0 (its
+    key 0), so once the 64 level-2 leaves exist the budget ends inside one run of equal keys and the
+    split set is decided by id order alone (the id digits of the selection)."""
+    rng = np.random.default_rng(11)
+    n = 60000
+    p = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    cell = np.clip(np.floor((p + 1) * 2), 0, 3).astype(np.int64)
+    palette = rng.uniform(0, 1, (64, 3)).astype(np.float32)
+    c = palette[cell[:, 0] + 4 * cell[:, 1] + 16 * cell[:, 2]]
+    lo, side, L = (-1.0, -1.0, -1.0), 2.0, 5
+    want = oracle.octree_init(p, c, lo, side, L, k_max, opacity=0.4)
+    got = igs.octree_init(torch.from_numpy(p).cuda(), torch.from_numpy(c).cuda(), lo, side, L, k_max, opacity=0.4)
+    assert got[0].shape[0] == want[0].shape[0] <= k_max
+    for g, w in zip(got, want):
+        np.testing.assert_array_equal(g.cpu().numpy(), w)
+
+
+def test_octree_full_size_properties():
+    """The benchmark's workload (2M clustered points, 7 levels, budget 500K), where the oracle's
+    literal greedy loop is too slow: the exact properties that fix the greedy tree and every value
+    (tests/_octree_props.py), recomputed in numpy."""
+    from tests._octree_props import check_octree
+    from paper_2403_14244_gb300 import scenes
+    p, c = scenes.point_cloud(2_000_000, seed=8)
+    lo, side, L, k_max = (-1.0, -1.0, -1.0), 2.0, 7, 500_000
+    ms, op, col = igs.octree_init(torch.from_numpy(p).cuda(), torch.from_numpy(c).cuda(), lo, side, L, k_max,
+                                  opacity=0.5)
+    check_octree(p, c, lo, side, L, k_max, ms.cpu().numpy(), op.cpu().numpy(), col.cpu().numpy(), 0.5)

@@ -126,3 +126,39 @@ def test_nonfinite_ignored_outside_clamped():
     ms, _, col = oracle.octree_init(p2, c2, (-1, -1, -1), 2.0, 3, 1)
     want = _q(np.concatenate([c, c2[-2:]])).mean(0) / 4096.0      # the two finite outliers count, clamped in
     np.testing.assert_allclose(col[0], want, rtol=1e-6)
+
+
+def test_property_checker_accepts_the_oracle_and_catches_mistakes():
+    """The vectorised checker used at full size on the GPU (tests/_octree_props.py) accepts the
+    oracle's trees and rejects planted mistakes: a missing leaf, a colour one ulp off, two leaves
+    swapped, a tree grown with a smaller budget, a leaf's centre moved, and a tree grown from other
+    colours (the same colours on other points) but given its cells' true means, which only the
+    order of the splits gives away."""
+    from tests._octree_props import check_octree
+    lo, side, L = (-1.0, -1.0, -1.0), 2.0, 6
+    p, c = _cloud(30000, 21, lo, side)
+    for k_max in (1, 9, 300, 2500):
+        ms, op, col = oracle.octree_init(p, c, lo, side, L, k_max, opacity=0.4)
+        check_octree(p, c, lo, side, L, k_max, ms, op, col, 0.4)
+    ms, op, col = oracle.octree_init(p, c, lo, side, L, 2500, opacity=0.4)
+    bad = [
+        (ms[:-1], op[:-1], col[:-1], 2500),
+        (ms, op, np.where(np.arange(len(col))[:, None] == 7, np.nextafter(col, np.float32(2)), col), 2500),
+        (ms[[1, 0] + list(range(2, len(ms)))], op, col[[1, 0] + list(range(2, len(col)))], 2500),
+    ]
+    ms2, op2, col2 = oracle.octree_init(p, c, lo, side, L, 2000, opacity=0.4)
+    bad.append((ms2, op2, col2, 2500))
+    moved = ms.copy()
+    moved[5, 0] = np.nextafter(moved[5, 0], np.float32(9))
+    bad.append((moved, op, col, 2500))
+    other = np.ascontiguousarray(c[np.random.default_rng(5).permutation(len(c))])
+    ms3, op3, _ = oracle.octree_init(p, other, lo, side, L, 2500, opacity=0.4)
+    lv, ij = _leaves(ms3, lo, side, L)
+    fine = _cell_index(p, lo, side, L)
+    col3 = np.stack([(_q(c[np.all((fine >> (L - lv[k])) == ij[k], axis=1)]).sum(0) /
+                      (4096.0 * np.all((fine >> (L - lv[k])) == ij[k], axis=1).sum())).astype(np.float32)
+                     for k in range(len(ms3))])
+    bad.append((ms3, op3, col3, 2500))
+    for m_, o_, c_, k_ in bad:
+        with pytest.raises(AssertionError):
+            check_octree(p, c, lo, side, L, k_, m_, o_, c_, 0.4)
