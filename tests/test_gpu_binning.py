@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_2403_14244_gb300 import igs, scenes
 from tests import _gpu
-from tests._tiny import random_small, scene_from, small_camera
+from tests._tiny import scene_from, small_camera
 
 pytestmark = pytest.mark.gpu
 

@@ -14,7 +14,6 @@ import pytest
 import torch
 
 import oracle
-from paper_2403_14244_gb300 import scenes
 from tests._tiny import random_small
 
 A_MIN = float(np.float32(1 / 255))

@@ -6,7 +6,6 @@ holds every pixel a Gaussian can reach with alpha >= 1/255, up to the
 footprint radius, itself pinned against FP64 logarithms), the order by numpy's
 stable sort, the ranges by searchsorted.
 """
-import math
 
 import numpy as np
 import pytest

@@ -90,7 +90,7 @@ def test_l1_matches_torch():
     ti = torch.tensor(img, requires_grad=True)
     tl = torch.nn.functional.l1_loss(ti, torch.tensor(tg, dtype=torch.float64))
     tl.backward()
-    assert loss == pytest.approx(float(tl), rel=1e-14)
+    assert loss == pytest.approx(float(tl.detach()), rel=1e-14)
     np.testing.assert_allclose(grad, ti.grad.numpy(), rtol=1e-14)
 
 
