@@ -197,7 +197,7 @@ __device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const u
 }
 
 template <int TS>
-__global__ void __launch_bounds__(TS* TS / 2, 2560 / (TS * TS)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(TS * TS / 2, (2560 / (TS * TS) < 32 ? 2560 / (TS * TS) : 32)) k_blend_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                       const float4* __restrict__ rec, BlendParams P,
                                                       const float* __restrict__ dL, const float* __restrict__ T_final,
                                                       const uint32_t* __restrict__ n_contrib,
