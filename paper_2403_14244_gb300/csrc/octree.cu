@@ -13,8 +13,9 @@
 // order whose split (adding its non-empty children minus one) does not fit.
 // The prefix is found by a radix selection on the 64-bit key (8 bits at a time,
 // histograms weighted by the leaves each split adds), and then on the id among
-// equal keys: each pass a histogram over all cells by many CTAs and a one-thread
-// pick of the digit. The leaves are then emitted in id order, a CTA per chunk.
+// equal keys: each pass a histogram over all cells by many CTAs, then a scan of
+// its 256 bins by one CTA picks the digit. The leaves are then emitted in id
+// order, a CTA per chunk of cells placed after the leaves of the chunks before it.
 #include <algorithm>
 #include <cmath>
 
