@@ -162,3 +162,17 @@ def test_property_checker_accepts_the_oracle_and_catches_mistakes():
     for m_, o_, c_, k_ in bad:
         with pytest.raises(AssertionError):
             check_octree(p, c, lo, side, L, k_, m_, o_, c_, 0.4)
+
+
+@pytest.mark.parametrize("k_max", [64, 200, 1000])
+def test_property_checker_accepts_ties(k_max):
+    """Colours constant on the 64 level-2 cells (every finer cell has error 0): the oracle's trees
+    end inside a run of equal keys, and the checker's id order among equal keys accepts them."""
+    from tests._octree_props import check_octree
+    rng = np.random.default_rng(11)
+    p = rng.uniform(-1, 1, (20000, 3)).astype(np.float32)
+    cell = np.clip(np.floor((p + 1) * 2), 0, 3).astype(np.int64)
+    c = rng.uniform(0, 1, (64, 3)).astype(np.float32)[cell[:, 0] + 4 * cell[:, 1] + 16 * cell[:, 2]]
+    lo, side, L = (-1.0, -1.0, -1.0), 2.0, 5
+    ms, op, col = oracle.octree_init(p, c, lo, side, L, k_max, opacity=0.4)
+    check_octree(p, c, lo, side, L, k_max, ms, op, col, 0.4)
