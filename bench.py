@@ -90,8 +90,9 @@ def load_peaks():
 
 
 def stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm):
-    """Algorithmic bytes per launch of every stage (per-unit figures in the design doc)
-    and the bandwidth they imply over the stage's measured time. The blends are
+    """Algorithmic bytes per launch of every stage (per-unit figures in the
+    comments of `model`, times the units of one step) and the bandwidth they
+    imply over the stage's measured time. The blends are
     bound by issue slots, not HBM: their bytes (entry gathers, per-pixel buffers)
     are listed for context."""
     params = 5 + C
