@@ -486,6 +486,10 @@ def octree_init(points, colors, lo, side, levels, k_max, opacity=0.5, sh_degree=
     """Octree initialisation of 3D Gaussians from a coloured point set (device
     [n][3] tensors); returns (means_sigma [K][4], opacity [K], color [K][C]) on
     the device (one synchronisation to read K)."""
+    if points.dtype != torch.float32 or colors.dtype != torch.float32:
+        raise ValueError("octree_init: points and colors must be float32")
+    if points.dim() != 2 or points.shape[1] != 3 or tuple(colors.shape) != tuple(points.shape):
+        raise ValueError("octree_init: points and colors must be [n, 3] tensors with the same n")
     dev = points.device
     nc = 3 if sh_degree < 0 else 3 * (sh_degree + 1) ** 2
     ms = torch.empty((k_max, 4), dtype=torch.float32, device=dev)

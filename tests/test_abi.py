@@ -91,3 +91,14 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
                     text = f.read()
                 assert "import oracle" not in text and "from oracle" not in text, name
                 assert "liboracle" not in text, name
+
+
+@pytest.mark.parametrize("pts,cols", [((5, 3, "f64"), (5, 3, "f32")), ((5, 4, "f32"), (5, 4, "f32")),
+                                      ((5, 3, "f32"), (6, 3, "f32"))])
+def test_octree_init_rejects_bad_tensors_before_any_launch(pts, cols):
+    """float64 points, [n, 4] rows or colours of another n raise in the binding, before any
+    allocation or launch."""
+    import torch
+    mk = lambda n, c, dt: torch.zeros((n, c), dtype=torch.float64 if dt == "f64" else torch.float32)  # noqa: E731
+    with pytest.raises(ValueError, match="octree_init"):
+        igs.octree_init(mk(*pts), mk(*cols), (-1, -1, -1), 2.0, 4, 100)
