@@ -225,12 +225,31 @@ def opts(tile=16, sh_degree=-1, param_mode=0, alpha_min=1.0 / 255.0, alpha_max=0
     return o
 
 
+def _check_color_width(scene, sh_degree, where):
+    """The colour rows must hold the coefficients the SH degree implies (3 for
+    RGB, 3 (d + 1)^2 for degree d): the kernels read that many floats per row."""
+    want = 3 if sh_degree < 0 else 3 * (sh_degree + 1) ** 2
+    if int(scene.color.shape[1]) != want:
+        raise ValueError(f"{where}: color has {int(scene.color.shape[1])} floats per Gaussian, "
+                         f"sh_degree {sh_degree} needs {want}")
+
+
 class Scene:
     """Device scene: means_sigma [N,4], opacity [N], color [N,C] (FP32, CUDA)."""
 
     def __init__(self, means_sigma, opacity, color):
+        for name, t in (("means_sigma", means_sigma), ("opacity", opacity), ("color", color)):
+            if t.dtype != torch.float32:
+                raise ValueError(f"Scene: {name} must be float32")
+        n = int(means_sigma.shape[0]) if means_sigma.dim() == 2 else -1
+        if n < 0 or means_sigma.shape[1] != 4:
+            raise ValueError("Scene: means_sigma must be [N, 4]")
+        if opacity.dim() != 1 or opacity.shape[0] != n:
+            raise ValueError("Scene: opacity must be [N]")
+        if color.dim() != 2 or color.shape[0] != n or color.shape[1] not in (3, 12, 27, 48):
+            raise ValueError("Scene: color must be [N, C] with C = 3, 12, 27 or 48")
         self.means_sigma, self.opacity, self.color = means_sigma, opacity, color
-        self.n = int(means_sigma.shape[0])
+        self.n = n
         s = IgsScene()
         s.means_sigma = _ptr(means_sigma).value if self.n else None
         s.opacity = _ptr(opacity).value if self.n else None
@@ -318,6 +337,7 @@ class Frame:
 # ------------------------------------------------------------ entry points --
 
 def project(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, stream=None):
+    _check_color_width(scene, o.sh_degree, "project")
     _check(load().igs_project(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                               _stream(stream)), "igs_project")
 
@@ -338,6 +358,7 @@ def render_fwd(frame: Frame, o: IgsOpts, img, stream=None):
 
 def render_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, dL_dimg, g2d, d_means_sigma, d_opacity,
                d_color, stream=None):
+    _check_color_width(scene, o.sh_degree, "render_bwd")
     _check(load().igs_render_bwd(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                  _ptr(dL_dimg), _ptr(g2d), _ptr(d_means_sigma), _ptr(d_opacity), _ptr(d_color),
                                  _stream(stream)), "igs_render_bwd")
@@ -350,6 +371,7 @@ def blend_bwd(frame: Frame, o: IgsOpts, dL_dimg, g2d, stream=None):
 
 def project_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, d_means_sigma, d_opacity, d_color,
                 stream=None):
+    _check_color_width(scene, o.sh_degree, "project_bwd")
     _check(load().igs_project_bwd(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                   _ptr(g2d), _ptr(d_means_sigma), _ptr(d_opacity), _ptr(d_color),
                                   _stream(stream)), "igs_project_bwd")
@@ -359,6 +381,7 @@ def project_bwd_adam(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d
                      b2=0.999, eps=1e-8, stream=None):
     """Projection backward fused with Adam: scene parameters and the moments
     m = (m_ms, m_op, m_col), v = (v_ms, v_op, v_col) are updated in place."""
+    _check_color_width(scene, o.sh_degree, "project_bwd_adam")
     _check(load().igs_project_bwd_adam(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                        _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
                                        int(step), _stream(stream)), "igs_project_bwd_adam")
@@ -369,6 +392,7 @@ def project_bwd_adam_dev(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame,
     """project_bwd_adam with the step count on the device: state is an int32[4]
     tensor (zero before the first step) that the call advances, so the step can
     be captured in a CUDA graph and replayed."""
+    _check_color_width(scene, o.sh_degree, "project_bwd_adam_dev")
     _check(load().igs_project_bwd_adam_dev(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                            _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
                                            _ptr(state), _stream(stream)), "igs_project_bwd_adam_dev")
@@ -471,6 +495,7 @@ def densify(scene: Scene, m, v, sh_degree, param_mode, accum, vis, op_min, tau_g
     its Adam moments m, v = (means_sigma, opacity, color) tensors into out,
     out_m, out_v (same layout, capacity = out[0].shape[0]); the new count goes to
     count (device int64)."""
+    _check_color_width(scene, sh_degree, "densify")
     _check(load().igs_densify(C.byref(scene.struct), C.byref(_params(m)), C.byref(_params(v)), int(sh_degree),
                               int(param_mode), _ptr(accum), _ptr(vis), float(op_min), float(tau_g),
                               float(scale_min), int(out[0].shape[0]), C.byref(_params(out)),
@@ -569,6 +594,7 @@ class Batch:
                "igs_batch_set_views")
 
     def render(self, scene: "Scene", stream=None):
+        _check_color_width(scene, self.opts.sh_degree, "Batch.render")
         _check(load().igs_render_batch(C.byref(self.struct), C.byref(scene.struct), C.byref(self.opts),
                                        _ptr(self.images), _stream(stream)), "igs_render_batch")
 
@@ -600,6 +626,7 @@ class Server:
         self.scenes = []
 
     def add_scene(self, scene: Scene, sh_degree=-1, param_mode=0):
+        _check_color_width(scene, sh_degree, "Server.add_scene")
         sid = C.c_int32()
         _check(load().igs_serve_add_scene(self.handle, C.byref(scene.struct), int(sh_degree), int(param_mode),
                                           C.byref(sid)), "igs_serve_add_scene")

@@ -102,3 +102,24 @@ def test_octree_init_rejects_bad_tensors_before_any_launch(pts, cols):
     mk = lambda n, c, dt: torch.zeros((n, c), dtype=torch.float64 if dt == "f64" else torch.float32)  # noqa: E731
     with pytest.raises(ValueError, match="octree_init"):
         igs.octree_init(mk(*pts), mk(*cols), (-1, -1, -1), 2.0, 4, 100)
+
+
+def test_scene_and_colour_width_checked_in_the_binding():
+    """A scene of the wrong dtype or shape, or colour rows that do not match the SH degree (the
+    kernels read 3 (d + 1)^2 floats per row), raise in the binding before any launch."""
+    import types
+
+    import torch
+    z = torch.zeros
+    for ms, op, col in ((z(4, 4, dtype=torch.float64), z(4), z(4, 3)), (z(4, 3), z(4), z(4, 3)),
+                        (z(4, 4), z(5), z(4, 3)), (z(4, 4), z(4), z(4, 5)), (z(4, 4), z(4, 1), z(4, 3))):
+        with pytest.raises(ValueError, match="Scene"):
+            igs.Scene(ms, op, col)
+    for C, ok in ((3, (-1, 0)), (12, (1,)), (27, (2,)), (48, (3,))):
+        sc = types.SimpleNamespace(color=z(2, C))
+        for d in (-1, 0, 1, 2, 3):
+            if d in ok:
+                igs._check_color_width(sc, d, "t")
+            else:
+                with pytest.raises(ValueError, match="sh_degree"):
+                    igs._check_color_width(sc, d, "t")
