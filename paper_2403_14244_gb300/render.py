@@ -4,13 +4,15 @@
 keeps one frame workspace per image size, and sizes the (Gaussian, tile) entry
 capacity from the last frame it saw (a frame that overflows reports the entries
 it needed and is redone with room to spare). ``IGSRender`` is the
-torch.autograd.Function over the same path; ``TrainStep`` is one
-forward + L1 + backward + Adam step with no host synchronisation except the
-optional loss read.
+torch.autograd.Function over the same path: each of its forwards leases a frame
+of its own from the renderer's pool, so several renders of one image size can
+wait for one backward; ``TrainStep`` is one forward + L1 + backward + Adam step
+with no host synchronisation except the optional loss read.
 """
 from __future__ import annotations
 
 import math
+import weakref
 
 import torch
 
@@ -27,8 +29,11 @@ class Renderer:
         self.device = device
         self._frames = {}
         self._cap_hint = {}
+        self._free = {}  # frames returned to the lease pool, per (n, width, height)
 
     def frame(self, n, cam, capacity):
+        """The renderer's shared frame of this size: every call of that size
+        reuses it (run_forward, TrainStep)."""
         key = (n, cam.width, cam.height)
         f = self._frames.get(key)
         if f is None or f.capacity < capacity:
@@ -36,6 +41,34 @@ class Renderer:
             self._frames[key] = f
         f.cam = cam
         return f
+
+    def lease(self, n, cam, capacity):
+        """A frame that no other caller holds until release(): a free pooled frame
+        of this size with enough capacity, else a new one. Each lease bumps the
+        frame's generation, so a holder can tell whether it was leased again."""
+        free = self._free.get((n, cam.width, cam.height), [])
+        f = None
+        while free and f is None:
+            cand = free.pop()
+            if cand.capacity >= capacity:
+                f = cand  # (too small ones are dropped)
+        if f is None:
+            f = igs.Frame(n, capacity, cam, self.opts, self.device)
+            f.generation = 0
+        f.cam = cam
+        f.generation += 1
+        f.leased = True
+        return f
+
+    def release(self, frame, generation=None):
+        """Return a leased frame to the pool (no-op if it is not leased, or if
+        `generation` is given and the frame has been leased again since)."""
+        if not getattr(frame, "leased", False):
+            return
+        if generation is not None and frame.generation != generation:
+            return
+        frame.leased = False
+        self._free.setdefault((frame.n, frame.width, frame.height), []).append(frame)
 
     def capacity_for(self, n, cam):
         key = (n, cam.width, cam.height)
@@ -51,15 +84,19 @@ class Renderer:
         want = int(min(math.ceil(needed * 1.15) + 4096, (1 << 30) - 1))
         self._cap_hint[key] = max(want, self._cap_hint.get(key, 0))
 
-    def run_forward(self, scene: igs.Scene, cam, img=None, check=True, stream=None):
+    def run_forward(self, scene: igs.Scene, cam, img=None, check=True, stream=None, lease=False):
         """project + bin_sort + render_fwd. Returns (img [3,H,W], frame). With
         check=True the stream is synchronised to read the frame status, and an
-        overflowing frame is redone with the capacity it reported."""
+        overflowing frame is redone with the capacity it reported. With
+        lease=True the frame is leased (release() it when done); otherwise it
+        is the renderer's shared frame of this size, which the next call of the
+        same size overwrites."""
         c = cam if isinstance(cam, igs.IgsCamera) else igs.camera(cam)
         if img is None:
             img = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.device)
         for _ in range(3):
-            f = self.frame(scene.n, c, self.capacity_for(scene.n, c))
+            cap = self.capacity_for(scene.n, c)
+            f = self.lease(scene.n, c, cap) if lease else self.frame(scene.n, c, cap)
             igs.project(scene, c, self.opts, f, stream)
             igs.bin_sort(f, self.opts, stream)
             igs.render_fwd(f, self.opts, img, stream)
@@ -69,6 +106,8 @@ class Renderer:
             if st == igs.OK:
                 self.note_needed(scene.n, c, max(info[0], 1))
                 return img, f
+            if lease:
+                self.release(f)
             if st != igs.ERR_CAPACITY:
                 raise igs.IgsError(st, "device error during render")
             self.note_needed(scene.n, c, info[3])
@@ -86,20 +125,45 @@ class Renderer:
         return grads
 
 
+class _FrameLease:
+    """A forward's hold on its leased frame; the frame goes back to the pool when
+    the backward has used it or when the autograd graph that owns this object
+    is freed, whichever comes first."""
+
+    __slots__ = ("frame", "generation", "__weakref__")
+
+    def __init__(self, renderer, frame):
+        self.frame, self.generation = frame, frame.generation
+        weakref.finalize(self, renderer.release, frame, frame.generation)
+
+
 class IGSRender(torch.autograd.Function):
-    """img = render(means_sigma, opacity, color; camera) with the CUDA adjoint."""
+    """img = render(means_sigma, opacity, color; camera) with the CUDA adjoint.
+
+    The forward saves its frame (depth order, tile lists, per-pixel T_final and
+    contributor counts) for the backward, which walks those lists back to front
+    without re-running the forward. Every forward leases its own frame, so
+    several views of one size can be rendered into one loss before backward()."""
 
     @staticmethod
     def forward(ctx, means_sigma, opacity, color, renderer: Renderer, cam):
         scene = igs.Scene(means_sigma.contiguous(), opacity.contiguous(), color.contiguous())
-        img, frame = renderer.run_forward(scene, cam, check=True)
-        ctx.renderer, ctx.cam, ctx.frame, ctx.scene = renderer, cam, frame, scene
+        img, frame = renderer.run_forward(scene, cam, check=True, lease=True)
+        ctx.renderer, ctx.cam = renderer, cam
+        ctx.lease = _FrameLease(renderer, frame)
         ctx.save_for_backward(means_sigma, opacity, color)
         return img
 
     @staticmethod
     def backward(ctx, dimg):
-        d_ms, d_op, d_col = ctx.renderer.run_backward(ctx.scene, ctx.cam, ctx.frame, dimg.contiguous())
+        means_sigma, opacity, color = ctx.saved_tensors  # (checks that no input changed in place)
+        lease = ctx.lease
+        if lease.frame.generation != lease.generation:
+            raise RuntimeError("IGSRender: this render's frame was reused by a later forward; a second "
+                               "backward through the same graph needs its forward run again")
+        scene = igs.Scene(means_sigma.contiguous(), opacity.contiguous(), color.contiguous())
+        d_ms, d_op, d_col = ctx.renderer.run_backward(scene, ctx.cam, lease.frame, dimg.contiguous())
+        ctx.renderer.release(lease.frame, lease.generation)
         return d_ms, d_op, d_col, None, None
 
 
