@@ -174,9 +174,10 @@ IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* st
 
 /* Front-to-back order of n depth keys WITHOUT allocating anything. The paper
  * has no counterpart: this exists for callers that cannot allocate device
- * memory around the call, such as code that runs while a CUDA graph is being
- * captured (allocation is not allowed there) or a host application whose
- * device memory is owned by its own allocator and is not reachable from here.
+ * memory around the call, such as a host application whose device memory all
+ * belongs to its own allocator (reserved at start-up, so a cudaMalloc here
+ * would fail or steal from it), or a latency-critical loop that must not call
+ * cudaMalloc/cudaFree because they can synchronise the whole device.
  * It computes exactly what igs_bin_sort writes to frame->order for the same
  * depth_key: a stable ascending sort of the keys (ties keep index order), the
  * output being the indices. depth_key (device, n) is read; order (device, n)
@@ -188,8 +189,9 @@ IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* st
  * first call before any stream capture. Every call on a device shares the
  * array (the call clears what must start at zero), so calls that overlap on
  * the GPU race: serialise them (one stream, or events). Asynchronous on
- * `stream`; a device-side bounded wait that runs out leaves order incomplete
- * and is not reported here. */
+ * `stream`; a failed launch returns IGS_ERR_CUDA and igs_last_error() names
+ * it; a device-side bounded wait that runs out leaves order incomplete and is
+ * not reported here. */
 IGS_API igs_status igs_sort_depth_noalloc(const uint32_t* depth_key, int64_t n, uint32_t* order, void* stream);
 
 /* Export the sorted 64-bit keys (tile << 32 | depth bits), M = info[0] of them,

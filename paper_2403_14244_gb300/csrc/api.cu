@@ -37,6 +37,15 @@ igs_status cuda_status(cudaError_t e, const char* what) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+}  // namespace
+
+namespace igs {
+igs_status report_cuda(cudaError_t e, const char* what) { return cuda_status(e, what); }
+igs_status report_invalid(const char* msg) { return fail(IGS_ERR_INVALID_ARG, "%s", msg); }
+}  // namespace igs
+
+namespace {
+
 igs_status check_camera(const igs_camera* cam) {
     if (!cam) return fail(IGS_ERR_INVALID_ARG, "camera is NULL");
     if (cam->width <= 0 || cam->height <= 0) return fail(IGS_ERR_INVALID_ARG, "image size must be positive");

@@ -46,6 +46,10 @@ extern std::atomic<uint64_t> g_launches;
 inline void count_launches(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 // The CUDA call of a multi-launch step that failed last on this thread (for the error message).
 extern thread_local const char* g_failed_call;
+// Status of a finished call for the C ABI: IGS_OK, or IGS_ERR_CUDA / IGS_ERR_INVALID_ARG
+// with the message igs_last_error() returns (naming g_failed_call, if set).
+igs_status report_cuda(cudaError_t e, const char* what);
+igs_status report_invalid(const char* msg);
 #define IGS_STR2(x) #x
 #define IGS_STR(x) IGS_STR2(x)
 

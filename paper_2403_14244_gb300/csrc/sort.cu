@@ -964,11 +964,13 @@ cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t 
 // ---------------------------------------------------------------------------
 // Front-to-back ordering without any allocation (igs_sort_depth_noalloc).
 //
-// Some callers cannot allocate device memory around a call: code that runs
-// while a CUDA graph is being captured, or an embedding host whose memory is
-// owned by its own allocator. This entry point orders n depth keys exactly as
-// igs_bin_sort orders its frame's depth_key into order (stable, ties by index),
-// but takes its scratch from one fixed device array compiled into the library.
+// Some callers cannot allocate device memory around a call: an embedding host
+// whose device memory all belongs to its own allocator (reserved at start-up,
+// none left for cudaMalloc), or a latency-critical loop that must not call
+// cudaMalloc/cudaFree, which can synchronise the whole device. This entry point
+// orders n depth keys exactly as igs_bin_sort orders its frame's depth_key
+// into order (stable, ties by index), but takes its scratch from one fixed
+// device array compiled into the library.
 // ---------------------------------------------------------------------------
 namespace igs {
 namespace {
@@ -1009,26 +1011,21 @@ cudaError_t noalloc_scratch(uint32_t** out) {
     return cudaSuccess;
 }
 
-}  // namespace
-}  // namespace igs
-
-extern "C" igs_status igs_sort_depth_noalloc(const uint32_t* depth_key, int64_t n, uint32_t* order, void* stream) {
-    using namespace igs;
-    if (n < 0 || n > kNoAllocMaxKeys) return IGS_ERR_INVALID_ARG;
-    if (n > 0 && (!depth_key || !order)) return IGS_ERR_INVALID_ARG;
-    if (n == 0) return IGS_OK;
+// The six launches of one call; the first failing CUDA call is named in g_failed_call.
+cudaError_t launch_sort_depth_noalloc(const uint32_t* depth_key, uint32_t nn, uint32_t* order, cudaStream_t st) {
+    cudaError_t e;
+#define CK(x) do { if ((e = (x)) != cudaSuccess) { g_failed_call = #x " (sort.cu:" IGS_STR(__LINE__) ")"; return e; } } while (0)
     uint32_t* s = nullptr;
-    if (noalloc_scratch(&s) != cudaSuccess) return IGS_ERR_CUDA;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(s + kNaZeroFrom, 0, (size_t)(kNaWords - kNaZeroFrom) * 4, st) != cudaSuccess)
-        return IGS_ERR_CUDA;
-    const uint32_t nn = (uint32_t)n;
-    const unsigned blocks = (unsigned)ceil_div(n, kSortTile);
-    const int hist_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 4);
+    CK(noalloc_scratch(&s));
+    CK(cudaMemsetAsync(s + kNaZeroFrom, 0, (size_t)(kNaWords - kNaZeroFrom) * 4, st));
+    const unsigned blocks = (unsigned)ceil_div(nn, kSortTile);
+    const int hist_blocks = (int)std::min<int64_t>(ceil_div(nn, 256), 152 * 4);
     k_hist<<<hist_blocks, 256, 0, st>>>(depth_key, nn, 4, s + kNaHist);
     count_launches();
+    CK(cudaGetLastError());
     k_hist_to_offsets<<<1, 1024, 0, st>>>(s + kNaHist, 4);
     count_launches();
+    CK(cudaGetLastError());
     u64* A = reinterpret_cast<u64*>(s + kNaItemsA);
     u64* B = reinterpret_cast<u64*>(s + kNaItemsB);
     for (int p = 0; p < 4; ++p) {
@@ -1045,6 +1042,21 @@ extern "C" igs_status igs_sort_depth_noalloc(const uint32_t* depth_key, int64_t 
                                                                         8 * p, hist, status, s + kNaCounters + p,
                                                                         s + kNaInfo);
         count_launches();
+        CK(cudaGetLastError());
     }
-    return cudaGetLastError() == cudaSuccess ? IGS_OK : IGS_ERR_CUDA;
+#undef CK
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace igs
+
+extern "C" igs_status igs_sort_depth_noalloc(const uint32_t* depth_key, int64_t n, uint32_t* order, void* stream) {
+    using namespace igs;
+    if (n < 0 || n > kNoAllocMaxKeys)
+        return report_invalid("igs_sort_depth_noalloc: n must be in [0, 2^20] (the size of its fixed scratch)");
+    if (n > 0 && (!depth_key || !order)) return report_invalid("igs_sort_depth_noalloc: depth_key or order is NULL");
+    if (n == 0) return IGS_OK;
+    return report_cuda(launch_sort_depth_noalloc(depth_key, (uint32_t)n, order, (cudaStream_t)stream),
+                       "igs_sort_depth_noalloc");
 }

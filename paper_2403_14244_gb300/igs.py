@@ -558,9 +558,21 @@ def frame_status(frame: Frame, stream=None):
     return st, list(info)
 
 
+_WORD_DTYPES = tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)
+
+
 def sort_depth_noalloc(depth_key, order, stream=None):
     """igs_sort_depth_noalloc: order = stable argsort of depth_key (int32 views of
-    uint32 data, n <= 2^20), scratch from the library's static device array."""
+    uint32 data, n <= 2^20), scratch from the library's static device array.
+    Both tensors must be 1-D, contiguous, 4 bytes per element and of the same
+    length (the kernels write n words to order)."""
+    for name, t in (("depth_key", depth_key), ("order", order)):
+        if t.dtype not in _WORD_DTYPES or t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"sort_depth_noalloc: {name} must be a contiguous 1-D int32 (or uint32) tensor")
+    if order.numel() != depth_key.numel():
+        raise ValueError("sort_depth_noalloc: order must have as many elements as depth_key")
+    if order.device != depth_key.device:
+        raise ValueError("sort_depth_noalloc: depth_key and order must be on the same device")
     _check(load().igs_sort_depth_noalloc(_ptr(depth_key), int(depth_key.numel()), _ptr(order), _stream(stream)),
            "igs_sort_depth_noalloc")
 

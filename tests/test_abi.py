@@ -123,3 +123,28 @@ def test_scene_and_colour_width_checked_in_the_binding():
             else:
                 with pytest.raises(ValueError, match="sh_degree"):
                     igs._check_color_width(sc, d, "t")
+
+
+@pytest.mark.parametrize("bad", ["short_order", "int16_order", "int64_key", "2d_key", "strided_order"])
+def test_sort_depth_noalloc_binding_refuses_bad_buffers(bad):
+    """The kernels write n 4-byte words to order: a shorter or narrower order,
+    or keys that are not n 4-byte words, are refused before anything launches."""
+    import torch
+    n = 1000
+    key = torch.zeros(n, dtype=torch.int32)
+    order = torch.zeros(n, dtype=torch.int32)
+    if bad == "short_order":
+        order = order[: n - 1]
+    elif bad == "int16_order":
+        order = torch.zeros(n, dtype=torch.int16)
+    elif bad == "int64_key":
+        key = torch.zeros(n, dtype=torch.int64)
+    elif bad == "2d_key":
+        key = key.view(10, 100)
+        order = order.view(10, 100)
+    else:
+        order = torch.zeros(2 * n, dtype=torch.int32)[::2]
+    before = igs.launch_count()
+    with pytest.raises(ValueError):
+        igs.sort_depth_noalloc(key, order)
+    assert igs.launch_count() == before

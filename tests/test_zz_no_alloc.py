@@ -1,10 +1,11 @@
 """igs_sort_depth_noalloc, called through the C ABI, against igs_bin_sort.
 
-Some callers of this library cannot allocate device memory around a call: code
-running while a CUDA graph is captured, or a host whose device memory belongs
-to its own allocator. igs_sort_depth_noalloc serves them: it orders depth keys
-front to back like igs_bin_sort does for a frame, with its scratch in a fixed
-array inside the library. This file is collected last on purpose, and its tests
+Some callers of this library cannot allocate device memory around a call: a
+host whose device memory all belongs to its own allocator, or a loop that must
+not call cudaMalloc/cudaFree because they can synchronise the device.
+igs_sort_depth_noalloc serves them: it orders depth keys front to back like
+igs_bin_sort does for a frame, with its scratch in a fixed array inside the
+library. This file is collected last on purpose, and its tests
 pass both on their own in a fresh process and after the rest of the suite.
 """
 import numpy as np
