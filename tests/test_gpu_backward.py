@@ -75,7 +75,7 @@ def test_backward_clustered_1080p_full():
     sub = np.random.default_rng(202).choice(hit, size=64, replace=False)
     for name, g, w in (("means", d_ms[sub, :3], ref["d_means"][sub]), ("sigma", d_ms[sub, 3], ref["d_sigma"][sub]),
                        ("opacity", d_op[sub], ref["d_opac"][sub]), ("color", d_col[sub], ref["d_color"][sub])):
-        _gpu.grad_close(g, w, name + "[subset]", rel_norm=2e-3, elem_rel=2e-3, elem_abs_frac=2e-3)
+        _gpu.grad_close(g, w, name + "[subset]", rel_norm=1e-3, elem_rel=1e-3, elem_abs_frac=1e-3)
 
 
 def test_l1_loss_matches_oracle():
@@ -230,7 +230,7 @@ def test_train_step_full_size_graph_replay():
     sub = np.random.default_rng(606).choice(hit, size=64, replace=False)
     for name, g, w in zip(("means_sigma", "opacity", "color"), got, want):
         _gpu.grad_close(g, w, name)
-        _gpu.grad_close(g[sub], w[sub], name + "[subset]", rel_norm=2e-3, elem_rel=2e-3, elem_abs_frac=2e-3)
+        _gpu.grad_close(g[sub], w[sub], name + "[subset]", rel_norm=1e-3, elem_rel=1e-3, elem_abs_frac=1e-3)
     for name, p0, w, g, p in (("means_sigma", sc.means_sigma, want[0], got[0], ts.ms),
                               ("opacity", sc.opacity, want[1], got[1], ts.op), ("color", sc.color, want[2], got[2], ts.col)):
         p = p.cpu().numpy()
