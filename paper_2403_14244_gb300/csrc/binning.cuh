@@ -101,12 +101,17 @@ __global__ void __launch_bounds__(1024) k_hist_to_offsets(uint32_t* __restrict__
 // count_host items each (segment y at items [y * count_host, ...)); every
 // segment has its own counter, look-back words and digit bases, and the first
 // pass's values are the global item index.
-template <bool IN_KEYS32, bool OUT_VALS>
+// SKIPPABLE (one segment only): when *skip_flag is set, the pass writes only
+// the values, to skip_vals, or, without skip_vals, does nothing (the redundant
+// top pass of a depth sort whose third pass wrote the order).
+template <bool IN_KEYS32, bool OUT_VALS, bool SKIPPABLE = false>
 __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
     const void* __restrict__ in_, void* __restrict__ out_, const uint32_t* __restrict__ d_count, uint32_t count_host,
     int shift, const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ status,
-    uint32_t* __restrict__ block_counter, uint32_t* __restrict__ info, uint32_t silent_blk = 0xFFFFFFFFu) {
+    uint32_t* __restrict__ block_counter, uint32_t* __restrict__ info, uint32_t silent_blk = 0xFFFFFFFFu,
+    const uint32_t* __restrict__ skip_flag = nullptr, uint32_t* __restrict__ skip_vals = nullptr) {
     pdl_wait();
+    if (SKIPPABLE && !skip_vals && *skip_flag) return;
     {
         const uint64_t seg = blockIdx.y;
         if (IN_KEYS32)
@@ -252,6 +257,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
         if (!silent) st_relaxed_u32(&my[tid], kFlagPre | ((excl + cnt) & kValMask));
     }
     s_delta[tid] = (int32_t)(digit_base[tid] + excl) - (int32_t)local;
+    const bool skipped = SKIPPABLE && !OUT_VALS && skip_vals && *skip_flag;  // (read late: fewer live registers)
     __syncthreads();
     // write out: runs of one digit land contiguously; past-the-end items hold the last slots
 #pragma unroll
@@ -263,6 +269,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_radix_pass(
         if (pos >= count) continue;  // only after a look-back that gave up
         if (OUT_VALS)
             static_cast<uint32_t*>(out_)[pos] = (uint32_t)item;
+        else if (skipped)
+            skip_vals[pos] = (uint32_t)item;
         else
             static_cast<u64*>(out_)[pos] = item;
     }

@@ -21,9 +21,11 @@ constexpr float kLn2 = 0.6931471805599453f;
 // (both below 2^-19), so w2 d^2 > pmax proves alpha < alpha_min.
 constexpr float kPowMargin = 1.0f / 1024.0f;
 
-// Status words of a frame (igs_frame::info).
+// Status words of a frame (igs_frame::info). kInfoKeyWrap: some depth key other
+// than the culled 0xFFFFFFFF has its low 24 bits all ones or its top byte 0xFF;
+// kInfoSkipTop: the depth sort's top-byte pass is redundant and skipped (below).
 enum : int { kInfoM = 0, kInfoKept = 1, kInfoErr = 2, kInfoNeed = 3, kInfoAbort = 4, kInfoTileTotal = 5,
-             kInfoWords = 16 };
+             kInfoKeyWrap = 6, kInfoSkipTop = 7, kInfoWords = 16 };
 
 // Radix sort geometry: 256 threads x 20 (key | value) items per block, 8-bit digits
 // (5120 items: a 3M-key pass fits one wave of four blocks per SM).
@@ -265,6 +267,8 @@ struct SortScratch {
     uint32_t* walk_len;               // [tiles_y] items per tile-row list
     uint32_t* walk_rows;              // [tiles_y] list starts, first level-2 chunks, chunk sizes; [1] chunk total
     uint32_t* walk_h2;                // [level-2 chunks][tiles_x] level-2 tile counts per chunk, then slots
+    uint2* walk_rect;                 // [n] rectangle of order[p] (level-1 count writes, level-1 place reads)
+    uint32_t* walk_span;              // [capacity] tiles xa | xb << 16 of each level-1 item's row ((1, 0): none)
     int64_t walk_chunks;              // > 0: counting sort of the entries; 0: duplication + tile radix passes
     int tile_passes;
     int tile_bits;

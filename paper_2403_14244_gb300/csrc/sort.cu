@@ -5,7 +5,12 @@
 // in depth order. Instead of one radix sort over 64-bit (tile << 32 | depth)
 // keys, this does:
 //   1. a stable 32-bit LSD radix sort of the n depth keys (culled ones carry
-//      0xFFFFFFFF and sort last), which gives `order`;
+//      0xFFFFFFFF and sort last), which gives `order`. When every other key
+//      has the same top byte (depths within one pair of binary exponents) and
+//      none has its low 24 bits all ones, sorting the low 24 bits alone gives
+//      the same order (culled keys, 0xFFFFFF there, still sort last and by
+//      index), so the third pass writes `order` and the fourth does nothing;
+//      the decision is taken on the device from the digit histograms;
 //   2. an exclusive scan of the tile counts in that order (M, capacity check);
 //   3. the entries in tile order, by one of two routes:
 //      a. counting sort (at most 2048 tiles per axis): the tile ranges are
@@ -65,10 +70,12 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
     __syncthreads();
     int32_t* g = SMEM_GRID ? s_grid : grid;
     uint32_t kept = 0;
+    bool wrap = false;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t k = depth_key[i];
 #pragma unroll
         for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(k >> (8 * p)) & 0xFF], 1u);
+        wrap |= k != 0xFFFFFFFFu && ((k & 0xFFFFFFu) == 0xFFFFFFu || (k >> 24) == 0xFFu);
         if (count[i]) {
             ++kept;
             const uint2 r = rect[i];
@@ -84,6 +91,7 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
     }
     kept = __reduce_add_sync(0xffffffffu, kept);
     if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&info[kInfoKept], kept);
+    if (__any_sync(0xffffffffu, wrap) && (threadIdx.x & 31) == 0) atomicOr(&info[kInfoKeyWrap], 1u);
     __syncthreads();
     for (int k = threadIdx.x; k < 4 * kRadix; k += blockDim.x) {
         const uint32_t v = (&s_h[0][0])[k];
@@ -180,6 +188,12 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
     for (int k = tid; k < 4 * kRadix; k += blockDim.x) (&s_h[0][0])[k] = hist[k];          // depth counts
     for (int k = tid; k < 4 * kRadix; k += blockDim.x) (&s_h[4][0])[k] = 0;                // tile counts
     __syncthreads();
+    if (tid < 32) {  // skip the top depth pass: at most one top byte other than the culled 0xFF, no wrap
+        uint32_t nz = 0;
+        for (int b = tid; b < kRadix - 1; b += 32) nz += s_h[3][b] != 0u;
+        nz = __reduce_add_sync(0xffffffffu, nz);
+        if (tid == 0) info[kInfoSkipTop] = (nz <= 1u && info[kInfoKeyWrap] == 0u) ? 1u : 0u;
+    }
     for (int y = tid; y < tiles_y; y += blockDim.x) {
         int32_t run = 0;
         for (int x = 0; x < tiles_x; ++x) { run += s_g[y * gx + x]; s_g[y * gx + x] = run; }
@@ -343,10 +357,12 @@ struct Placer {
 
 // Level 1, count: for each of its chunks c (grid-stride over warps), a warp adds,
 // for each Gaussian of the chunk, one to every row of its rectangle; writes
-// column c of H1 [rows][cmax].
+// column c of H1 [rows][cmax], and the rectangles in depth order (srect[p] =
+// rect[order[p]]) so that the placement reads them without a gather.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* __restrict__ order,
                                                                 const uint2* __restrict__ rect, uint32_t rows,
                                                                 uint32_t cmax, uint32_t* __restrict__ H1,
+                                                                uint2* __restrict__ srect,
                                                                 const uint32_t* __restrict__ info) {
     pdl_wait();
     extern __shared__ uint32_t s_walk[];
@@ -370,6 +386,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* 
             for (int k = 0; k < kWalkUnroll; ++k) {
                 const uint2 r = g[k] != 0xFFFFFFFFu ? rect[g[k]] : make_uint2(1u << 16, 0u);  // rows 1..0: none
                 ry[k] = (r.x >> 16) | (r.y & 0xFFFF0000u);
+                if (g[k] != 0xFFFFFFFFu) srect[b + k * 32 + lane] = r;  // the placement reads it in order
             }
 #pragma unroll
             for (int k = 0; k < kWalkUnroll; ++k)
@@ -453,7 +470,7 @@ __global__ void __launch_bounds__(kLayoutThreads) k_rows_layout(const uint32_t* 
 // Level 1, place: a warp walks each of its chunks again and puts each Gaussian
 // id into the list of every row of its rectangle (R1, rows one after another).
 __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* __restrict__ order,
-                                                                const uint2* __restrict__ rect, uint32_t rows,
+                                                                const uint2* __restrict__ srect, uint32_t rows,
                                                                 uint32_t cmax, const uint32_t* __restrict__ H1,
                                                                 const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
@@ -473,10 +490,13 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* 
             return (c + 1 < ch.used ? h[c + 1] : len[y]) - h[c];
         });
         uint32_t g_next = ch.p0 + lane < ch.p1 ? order[ch.p0 + lane] : 0xFFFFFFFFu;
+        uint2 r_next = ch.p0 + lane < ch.p1 ? srect[ch.p0 + lane] : make_uint2(1u << 16, 0u);  // rows 1..0: none
         for (uint32_t b = ch.p0; b < ch.p1; b += 32) {
             const uint32_t g = g_next;
-            const uint2 r = g != 0xFFFFFFFFu ? rect[g] : make_uint2(1u << 16, 0u);  // rows 1..0: none
-            g_next = b + 32 + lane < ch.p1 ? order[b + 32 + lane] : 0xFFFFFFFFu;
+            const uint2 r = r_next;
+            const bool more = b + 32 + lane < ch.p1;
+            g_next = more ? order[b + 32 + lane] : 0xFFFFFFFFu;
+            r_next = more ? srect[b + 32 + lane] : make_uint2(1u << 16, 0u);
             rs.batch(r.x >> 16, r.y >> 16, g, lane, R1);
         }
         rs.flush(R1, lane);
@@ -527,12 +547,14 @@ struct DiscRef {
 
 // Level 2, count: for each of its chunks j, a warp adds, for each item of the
 // chunk, one to every tile of the row that the item's Gaussian touches; writes
-// row j of H2 [chunks][tiles_x].
+// row j of H2 [chunks][tiles_x], and each item's tiles (span[i] = xa | xb << 16,
+// (1, 0) for none) so that the placement reads them without a gather.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* __restrict__ R1,
                                                                 DiscRef disc, uint32_t rows,
                                                                 uint32_t tiles_x, const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 uint32_t* __restrict__ H2,
+                                                                uint32_t* __restrict__ span,
                                                                 const uint32_t* __restrict__ info) {
     pdl_wait();
     extern __shared__ uint32_t s_walk[];
@@ -553,7 +575,11 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* 
                 g[k] = i < rc.i1 ? R1[i] : 0xFFFFFFFFu;
             }
 #pragma unroll
-            for (int k = 0; k < kWalkUnroll; ++k) sp[k] = disc.span(g[k], (int)rc.y);
+            for (int k = 0; k < kWalkUnroll; ++k) {
+                sp[k] = disc.span(g[k], (int)rc.y);
+                const uint32_t i = b + k * 32 + lane;
+                if (i < rc.i1) span[i] = (uint32_t)sp[k].x | ((uint32_t)sp[k].y << 16);
+            }
 #pragma unroll
             for (int k = 0; k < kWalkUnroll; ++k)
                 for (int x = sp[k].x; x <= sp[k].y; ++x) atomicAdd(&cnt[x], 1u);
@@ -603,7 +629,7 @@ __global__ void __launch_bounds__(32 * kColScanWarps) k_cols_scan(uint32_t* __re
 // Level 2, place: a warp walks each of its chunks again and puts each item's
 // Gaussian id into its slot in every tile of the row that the Gaussian touches.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* __restrict__ R1,
-                                                                DiscRef disc, uint32_t rows,
+                                                                const uint32_t* __restrict__ span, uint32_t rows,
                                                                 uint32_t tiles_x, const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 const uint32_t* __restrict__ H2,
@@ -624,11 +650,13 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* 
         auto first = [&](uint32_t x) { return h[x]; };
         rs.init(lane, first, [&](uint32_t x) { return (last ? rg[x].y : h[x + tiles_x]) - h[x]; });
         uint32_t g_next = rc.i0 + lane < rc.i1 ? R1[rc.i0 + lane] : 0xFFFFFFFFu;
+        uint32_t s_next = rc.i0 + lane < rc.i1 ? span[rc.i0 + lane] : 1u;  // (1, 0): no tiles
         for (uint32_t b = rc.i0; b < rc.i1; b += 32) {
-            const uint32_t g = g_next;
-            const int2 sp = disc.span(g, (int)rc.y);
-            g_next = b + 32 + lane < rc.i1 ? R1[b + 32 + lane] : 0xFFFFFFFFu;
-            rs.batch((uint32_t)sp.x, (uint32_t)sp.y, g, lane, vals);
+            const uint32_t g = g_next, sp = s_next;
+            const bool more = b + 32 + lane < rc.i1;
+            g_next = more ? R1[b + 32 + lane] : 0xFFFFFFFFu;
+            s_next = more ? span[b + 32 + lane] : 1u;
+            rs.batch(sp & 0xFFFFu, sp >> 16, g, lane, vals);
         }
         rs.flush(vals, lane);
         __syncwarp();  // the next chunk's init rewrites what the flush reads
@@ -754,6 +782,8 @@ size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t 
     b += align256((size_t)rows * 4);                                         // walk_len
     b += align256((size_t)(3 * rows + 1) * 4);                               // walk_rows
     b += align256((size_t)(chunks > 0 ? l2_chunks_max(capacity, tiles_y) * tiles_x : 0) * 4);  // walk_h2
+    b += align256((size_t)(chunks > 0 ? n : 0) * 8);                         // walk_rect
+    b += align256((size_t)(chunks > 0 ? capacity : 0) * 4);                  // walk_span
     return b;
 }
 
@@ -784,6 +814,8 @@ SortScratch sort_scratch(const igs_frame& f) {
     s.walk_len = (uint32_t*)take((size_t)rows * 4);
     s.walk_rows = (uint32_t*)take((size_t)(3 * rows + 1) * 4);
     s.walk_h2 = (uint32_t*)take((size_t)(chunks > 0 ? l2_chunks_max(cap, f.tiles_y) * f.tiles_x : 0) * 4);
+    s.walk_rect = (uint2*)take((size_t)(chunks > 0 ? n : 0) * 8);
+    s.walk_span = (uint32_t*)take((size_t)(chunks > 0 ? cap : 0) * 4);
     // the last tile pass (p = passes - 1) reads items_a when p is even, items_b when odd
     const bool last_reads_a = s.tile_passes > 0 && (s.tile_passes - 1) % 2 == 0;
     s.vals = reinterpret_cast<uint32_t*>(last_reads_a ? s.items_b : s.items_a);
@@ -858,21 +890,31 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         count_launches();
         CK(cudaGetLastError());
     }
-    // 1. depth sort: (depth_key, index) -> A -> B -> A -> order
+    // 1. depth sort: (depth_key, index) -> A -> B -> A -> order (or -> order after the third pass)
+    const bool small_grid = (int64_t)gx * gy <= kGridSmemCells;  // k_tiles_small decides the top-pass skip
     for (int p = 0; p < 4; ++p) {
         uint32_t* status = s.status_depth + (size_t)p * bn * kRadix;
         const uint32_t* hist = s.hist + p * kRadix;
         if (p == 0)
             CK(launch_pdl(k_radix_pass<true, false>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
                 f.depth_key, s.ditems_a, nullptr, nn, 0, hist, status, s.counters + 0, f.info,
-                g_silence_next.exchange(0) ? 1u : 0xFFFFFFFFu));
+                g_silence_next.exchange(0) ? 1u : 0xFFFFFFFFu, nullptr, nullptr));
+        else if (p == 3 && small_grid)  // nothing to do when the top pass is skipped (k_tiles_small decides)
+            CK(launch_pdl(k_radix_pass<false, true, true>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
+                s.ditems_a, f.order, nullptr, nn, 24, hist, status, s.counters + 3, f.info, 0xFFFFFFFFu,
+                f.info + kInfoSkipTop, nullptr));
         else if (p == 3)
             CK(launch_pdl(k_radix_pass<false, true>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
-                s.ditems_a, f.order, nullptr, nn, 24, hist, status, s.counters + 3, f.info, 0xFFFFFFFFu));
+                s.ditems_a, f.order, nullptr, nn, 24, hist, status, s.counters + 3, f.info, 0xFFFFFFFFu,
+                nullptr, nullptr));
+        else if (p == 2 && small_grid)  // writes the order itself when the top pass is skipped
+            CK(launch_pdl(k_radix_pass<false, false, true>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
+                s.ditems_b, s.ditems_a, nullptr, nn, 16, hist, status, s.counters + 2, f.info, 0xFFFFFFFFu,
+                f.info + kInfoSkipTop, f.order));
         else
             CK(launch_pdl(k_radix_pass<false, false>, dim3((unsigned)bn), dim3(kSortThreads), 0, st, 
                 p == 1 ? s.ditems_a : s.ditems_b, p == 1 ? s.ditems_b : s.ditems_a, nullptr, nn, 8 * p, hist,
-                status, s.counters + p, f.info, 0xFFFFFFFFu));
+                status, s.counters + p, f.info, 0xFFFFFFFFu, nullptr, nullptr));
         count_launches();
         CK(cudaGetLastError());
     }
@@ -890,7 +932,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
 
         const uint2* rect = reinterpret_cast<const uint2*>(f.rect);
         const uint2* rg = reinterpret_cast<const uint2*>(f.ranges);
-        CK(launch_pdl(k_rows_count, dim3(walk_blocks((const void*)k_rows_count, count1, cmax)), dim3(32 * kWalkWarps), count1, st, f.order, rect, rows, cmax, s.walk_h1, f.info));
+        CK(launch_pdl(k_rows_count, dim3(walk_blocks((const void*)k_rows_count, count1, cmax)), dim3(32 * kWalkWarps), count1, st, f.order, rect, rows, cmax, s.walk_h1, s.walk_rect, f.info));
         count_launches();
         CK(cudaGetLastError());
         CK(launch_pdl(k_rows_scan, dim3(rows), dim3(kRowScanThreads), 0, st, s.walk_h1, cmax, s.walk_len, f.info));
@@ -899,19 +941,19 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         CK(launch_pdl(k_rows_layout, dim3(1), dim3(kLayoutThreads), 0, st, s.walk_len, rg, rows, cols, (uint32_t)max2, s.walk_rows, f.info));
         count_launches();
         CK(cudaGetLastError());
-        CK(launch_pdl(k_rows_place, dim3(walk_blocks((const void*)k_rows_place, place1, cmax)), dim3(32 * kWalkWarps), place1, st, f.order, rect, rows, cmax, s.walk_h1, s.walk_len,
+        CK(launch_pdl(k_rows_place, dim3(walk_blocks((const void*)k_rows_place, place1, cmax)), dim3(32 * kWalkWarps), place1, st, f.order, s.walk_rect, rows, cmax, s.walk_h1, s.walk_len,
                                                                 s.walk_rows, R1, f.info));
         count_launches();
         CK(cudaGetLastError());
         const DiscRef disc{rect, reinterpret_cast<const float4*>(f.disc), f.tile, 1.0f / (float)f.tile, footprint};
         CK(launch_pdl(k_cols_count, dim3(walk_blocks((const void*)k_cols_count, count2, max2)), dim3(32 * kWalkWarps), count2, st, R1, disc, rows, cols, s.walk_len, s.walk_rows,
-                                                                s.walk_h2, f.info));
+                                                                s.walk_h2, s.walk_span, f.info));
         count_launches();
         CK(cudaGetLastError());
         CK(launch_pdl(k_cols_scan, dim3(rows), dim3(32 * kColScanWarps), 0, st, s.walk_h2, rows, cols, rg, s.walk_rows, f.info));
         count_launches();
         CK(cudaGetLastError());
-        CK(launch_pdl(k_cols_place, dim3(walk_blocks((const void*)k_cols_place, place2, max2)), dim3(32 * kWalkWarps), place2, st, R1, disc, rows, cols, s.walk_len, s.walk_rows,
+        CK(launch_pdl(k_cols_place, dim3(walk_blocks((const void*)k_cols_place, place2, max2)), dim3(32 * kWalkWarps), place2, st, R1, s.walk_span, rows, cols, s.walk_len, s.walk_rows,
                                                                 s.walk_h2, rg, f.vals, f.info));
         count_launches();
         CK(cudaGetLastError());
@@ -938,11 +980,12 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         const uint32_t* hist = s.hist + (4 + p) * kRadix;
         if (p == tp - 1)
             CK(launch_pdl(k_radix_pass<false, true>, dim3((unsigned)bc), dim3(kSortThreads), 0, st, 
-                in, f.vals, f.info + kInfoM, 0u, 8 * p, hist, status, s.counters + 5 + p, f.info, 0xFFFFFFFFu));
+                in, f.vals, f.info + kInfoM, 0u, 8 * p, hist, status, s.counters + 5 + p, f.info, 0xFFFFFFFFu,
+                nullptr, nullptr));
         else
             CK(launch_pdl(k_radix_pass<false, false>, dim3((unsigned)bc), dim3(kSortThreads), 0, st, 
                 in, (p % 2 == 0) ? s.items_b : s.items_a, f.info + kInfoM, 0u, 8 * p, hist, status,
-                s.counters + 5 + p, f.info, 0xFFFFFFFFu));
+                s.counters + 5 + p, f.info, 0xFFFFFFFFu, nullptr, nullptr));
         count_launches();
         CK(cudaGetLastError());
     }

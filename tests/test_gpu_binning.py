@@ -148,3 +148,46 @@ def test_invalid_arguments_rejected():
     cam.fy = cam.fx * 1.01
     with pytest.raises(igs.IgsError):
         igs.Frame(sc.n, 1 << 16, igs.camera(cam), igs.opts(tile=16))
+
+
+def _depth_scene(z, seed, W=640, H=480, f=500.0):
+    """Gaussians at depths z (exactly: the camera sits at the origin with R = I),
+    spread over the image; a tenth of them behind the camera (culled)."""
+    rng = np.random.default_rng(seed)
+    n = len(z)
+    z = np.asarray(z, np.float32).copy()
+    z[rng.random(n) < 0.1] *= np.float32(-1.0)
+    u, v = rng.uniform(0, W, n), rng.uniform(0, H, n)
+    means = np.stack([(u - W / 2) * np.abs(z) / f, (v - H / 2) * np.abs(z) / f, np.zeros(n)], 1)
+    sc = scene_from(means, rng.uniform(0.005, 0.02, n), rng.uniform(0.2, 0.9, n), rng.uniform(0, 1, (n, 3)))
+    sc.means_sigma[:, 2] = z                       # the depth bits exactly as drawn
+    cam = scenes.Camera(R=np.eye(3, dtype=np.float32), t=np.zeros(3, np.float32), fx=f, fy=f, cx=W / 2, cy=H / 2,
+                        width=W, height=H)
+    return sc, cam
+
+
+@pytest.mark.parametrize("case,skip", [("one_top_byte", 1), ("three_top_bytes", 0), ("low24_all_ones", 0)])
+def test_depth_order_top_pass_skip(case, skip):
+    """The depth sort skips its top-byte pass exactly when every kept key shares
+    its top byte and none has its low 24 bits all ones; either way the order is
+    the stable argsort of the depth keys (culled keys last, by index), and the
+    keys and ranges stay bit-exact."""
+    rng = np.random.default_rng(91)
+    n = 60_001                                     # several radix blocks and a ragged last one
+    if case == "three_top_bytes":
+        z = rng.uniform(1.2, 12.0, n)              # exponents 127..130: top bytes 0x3F, 0x40, 0x41
+    else:
+        z = rng.uniform(2.3, 5.7, n)               # exponents 128, 129: top byte 0x40
+    z = z.astype(np.float32)
+    z[::7] = z[1::7][: z[::7].shape[0]]            # equal depths: ties by index
+    sc, cam = _depth_scene(z, 92)
+    if case == "low24_all_ones":                   # at the image centre, 7.9999995: kept, low 24 bits all ones
+        sc.means_sigma[12345, :3] = np.array([0.0, 0.0, np.uint32(0x40FFFFFF).view(np.float32)], np.float32)
+    _check_bitexact(sc, cam, 16)
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=16)
+    info = f.info().cpu().numpy().view(np.uint32)
+    assert int(info[7]) == skip
+    dk = f.depth_key().cpu().numpy().view(np.uint32)
+    want = np.argsort(dk, kind="stable").astype(np.uint32)
+    np.testing.assert_array_equal(f.order().cpu().numpy().view(np.uint32), want)
+    assert (dk == 0xFFFFFFFF).sum() > 1000
