@@ -196,9 +196,10 @@ igs_status igs_frame_layout(int64_t n, int64_t capacity, const igs_camera* cam, 
     frame->info = reinterpret_cast<uint32_t*>(b + o_info);
     frame->scratch = b + o_scr;
     frame->scratch_bytes = scr;
-    // vals and tile_key live in the sort's entry buffers: a frame costs 8 bytes per
-    // entry of capacity (counting sort) or 16 (radix tile passes: the ping-pong
-    // item buffers, each free when they are written)
+    // vals and tile_key live in the sort's entry buffers: a frame costs 12 bytes per
+    // entry of capacity (counting sort: vals, and the 8-byte level-1 items whose
+    // buffer later takes tile_key) or 16 (radix tile passes: the ping-pong item
+    // buffers, each free when they are written)
     const igs::SortScratch ss = igs::sort_scratch(*frame);
     frame->vals = ss.vals;
     frame->tile_key = ss.tile_key;

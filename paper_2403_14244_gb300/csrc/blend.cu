@@ -43,9 +43,12 @@ __global__ void __launch_bounds__(TS* TS) k_blend_fwd(const uint2* __restrict__ 
 template <int TS>
 constexpr int bwd_batch() { return TS == 16 ? 64 : 32; }
 
-// One pixel's state in the reverse walk.
+// One pixel's state in the reverse walk. The colour composited behind the
+// current entry, S, enters the adjoint only through G . S, so the walk carries
+// that scalar (GS = G . (T_final bg) at the start, then GS += w T (G . c) per
+// blended entry) instead of S itself.
 struct BwdPixel {
-    float px, py, G0, G1, G2, T, S0, S1, S2;
+    float px, py, G0, G1, G2, T, GS;
     uint32_t nc;
 };
 
@@ -68,10 +71,9 @@ __device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, float4 a4, c
     v[4] += wT * q.G0;
     v[5] += wT * q.G1;
     v[6] += wT * q.G2;
-    const float dalpha = Tk * (q.G0 * c.x + q.G1 * c.y + q.G2 * c.z) - (q.G0 * q.S0 + q.G1 * q.S1 + q.G2 * q.S2) * inv;
-    q.S0 = fmaf(wT, c.x, q.S0);
-    q.S1 = fmaf(wT, c.y, q.S1);
-    q.S2 = fmaf(wT, c.z, q.S2);
+    const float Gc = q.G0 * c.x + q.G1 * c.y + q.G2 * c.z;
+    const float dalpha = Tk * Gc - q.GS * inv;
+    q.GS = fmaf(wT, Gc, q.GS);
     q.T = Tk;
     if (og <= P.alpha_max) {                    // alpha not clamped
         v[3] += dalpha * g;                     // d/do
@@ -130,9 +132,7 @@ __device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const u
             p.T = T_final[pix];
             p.nc = n_contrib[pix];
         }
-        p.S0 = p.T * P.bg[0];
-        p.S1 = p.T * P.bg[1];
-        p.S2 = p.T * P.bg[2];
+        p.GS = p.T * (p.G0 * P.bg[0] + p.G1 * P.bg[1] + p.G2 * P.bg[2]);
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();

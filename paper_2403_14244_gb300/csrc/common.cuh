@@ -253,7 +253,7 @@ struct SortScratch {
     unsigned long long* ditems_a;     // [n] (depth key | index) items
     unsigned long long* ditems_b;     // [n]
     unsigned long long* items_a;      // [capacity] (tile id | Gaussian id) items
-    unsigned long long* items_b;      // [capacity]
+    unsigned long long* items_b;      // [capacity] (route a: the level-1 items, then the exported tile ids)
     uint32_t* hist;                   // [8][256]: 4 depth passes, then up to 4 tile passes
     uint32_t* counters;               // [16] virtual block counters
     uint32_t* status_depth;           // [4][blocks(n)][256]
@@ -268,7 +268,6 @@ struct SortScratch {
     uint32_t* walk_rows;              // [tiles_y] list starts, first level-2 chunks, chunk sizes; [1] chunk total
     uint32_t* walk_h2;                // [level-2 chunks][tiles_x] level-2 tile counts per chunk, then slots
     uint2* walk_rect;                 // [n] rectangle of order[p] (level-1 count writes, level-1 place reads)
-    uint32_t* walk_span;              // [capacity] tiles xa | xb << 16 of each level-1 item's row ((1, 0): none)
     int64_t walk_chunks;              // > 0: counting sort of the entries; 0: duplication + tile radix passes
     int tile_passes;
     int tile_bits;

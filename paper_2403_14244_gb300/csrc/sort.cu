@@ -53,7 +53,10 @@ constexpr int kGridSmemCells = 10240;
 // Depth-digit histograms of all n depth keys, the kept count, and for every kept
 // Gaussian, in each tile row, +1 at its first touched tile and -1 past its last
 // in the (tiles_y+1) x (tiles_x+1) grid (a prefix sum along each row then gives
-// the entries of every tile).
+// the entries of every tile). Each thread has kPrepUnroll Gaussians in flight;
+// the two top bytes of a view's depths take few values, so a warp adds their
+// counts once per distinct digit (match.any) instead of once per lane.
+constexpr int kPrepUnroll = 4;
 template <bool SMEM_GRID>
 __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ depth_key, const uint2* __restrict__ rect,
                                                   const float4* __restrict__ disc, int tile, int footprint,
@@ -64,34 +67,60 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
     extern __shared__ int32_t s_grid[];
     __shared__ uint32_t s_h[4][kRadix];
     const int cells = gx * gy;
+    const int lane = threadIdx.x & 31;
     for (int k = threadIdx.x; k < 4 * kRadix; k += blockDim.x) (&s_h[0][0])[k] = 0;
     if (SMEM_GRID)
         for (int k = threadIdx.x; k < cells; k += blockDim.x) s_grid[k] = 0;
     __syncthreads();
     int32_t* g = SMEM_GRID ? s_grid : grid;
+    const float inv = 1.0f / (float)tile;
     uint32_t kept = 0;
     bool wrap = false;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t k = depth_key[i];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // every lane of a warp runs the same iterations (the counts below are warp-collective)
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < n;
+         i0 += (uint64_t)stride * kPrepUnroll) {
+        uint32_t key[kPrepUnroll], cnt[kPrepUnroll];
+        uint2 r[kPrepUnroll];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(k >> (8 * p)) & 0xFF], 1u);
-        wrap |= k != 0xFFFFFFFFu && ((k & 0xFFFFFFu) == 0xFFFFFFu || (k >> 24) == 0xFFu);
-        if (count[i]) {
-            ++kept;
-            const uint2 r = rect[i];
-            const float inv = 1.0f / (float)tile;
-            const int y0 = r.x >> 16, y1 = r.y >> 16;
-            for (int ty = y0; ty <= y1; ++ty) {  // +1 at the row's first touched tile, -1 past its last
-                const int2 sp = tile_span(footprint, r, disc, i, tile, inv, ty);
-                if (sp.y < sp.x) continue;
-                atomicAdd(&g[ty * gx + sp.x], 1);
-                atomicAdd(&g[ty * gx + sp.y + 1], -1);
+        for (int u = 0; u < kPrepUnroll; ++u) {  // independent loads first
+            const uint64_t i = i0 + (uint64_t)u * stride + lane;
+            const bool ok = i < n;
+            key[u] = ok ? depth_key[i] : 0u;
+            cnt[u] = ok ? count[i] : 0u;
+            r[u] = ok ? rect[i] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kPrepUnroll; ++u) {
+            const uint64_t i = i0 + (uint64_t)u * stride + lane;
+            const bool ok = i < n;
+            const uint32_t k = key[u];
+            if (ok) {
+                atomicAdd(&s_h[0][k & 0xFF], 1u);
+                atomicAdd(&s_h[1][(k >> 8) & 0xFF], 1u);
+            }
+#pragma unroll
+            for (int p = 2; p < 4; ++p) {
+                const uint32_t d = (k >> (8 * p)) & 0xFF;
+                const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u + lane);
+                if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_h[p][d], __popc(peers));
+            }
+            wrap |= ok && k != 0xFFFFFFFFu && ((k & 0xFFFFFFu) == 0xFFFFFFu || (k >> 24) == 0xFFu);
+            if (cnt[u]) {
+                ++kept;
+                const int y0 = r[u].x >> 16, y1 = r[u].y >> 16;
+                for (int ty = y0; ty <= y1; ++ty) {  // +1 at the row's first touched tile, -1 past its last
+                    const int2 sp = tile_span(footprint, r[u], disc, i, tile, inv, ty);
+                    if (sp.y < sp.x) continue;
+                    atomicAdd(&g[ty * gx + sp.x], 1);
+                    atomicAdd(&g[ty * gx + sp.y + 1], -1);
+                }
             }
         }
     }
     kept = __reduce_add_sync(0xffffffffu, kept);
-    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&info[kInfoKept], kept);
-    if (__any_sync(0xffffffffu, wrap) && (threadIdx.x & 31) == 0) atomicOr(&info[kInfoKeyWrap], 1u);
+    if (lane == 0 && kept) atomicAdd(&info[kInfoKept], kept);
+    if (__any_sync(0xffffffffu, wrap) && lane == 0) atomicOr(&info[kInfoKeyWrap], 1u);
     __syncthreads();
     for (int k = threadIdx.x; k < 4 * kRadix; k += blockDim.x) {
         const uint32_t v = (&s_h[0][0])[k];
@@ -248,13 +277,15 @@ constexpr int kRowWalkMax = 2048;          // tiles per axis for route a (shared
 constexpr uint32_t kL1ChunksMax = 16384;   // most level-1 chunks (columns of H1), fewer for tall frames
 constexpr uint32_t kL1ChunksMin = 1024;
 constexpr uint32_t kH1Words = 1u << 22;    // H1 budget: rows x chunks
-constexpr uint32_t kStage = 1536;          // staged items per chunk
+constexpr uint32_t kStage = 1536;          // staged entries per level-2 chunk
 constexpr uint32_t kChunkTarget = kStage * 4 / 5;
+constexpr uint32_t kStage1 = 1024;         // staged 8-byte items per level-1 chunk
+constexpr uint32_t kChunkTarget1 = kStage1 * 4 / 5;
 constexpr int kWalkWarps = 4;              // warps per CTA of the walk kernels (one chunk each)
 constexpr int kWalkUnroll = 4;             // items per lane per round of the counting walks
 
 // Level-1 chunk c: positions [p0, p1) of the depth order among the kept
-// Gaussians; `used` chunks hold Gaussians. A chunk takes about kChunkTarget /
+// Gaussians; `used` chunks hold Gaussians. A chunk takes about kChunkTarget1 /
 // sqrt(M / kept) Gaussians (the rows of an isotropic footprint are about the
 // square root of its tiles).
 struct Chunk {
@@ -263,7 +294,7 @@ struct Chunk {
 __device__ __forceinline__ Chunk l1_chunk(uint32_t c, uint32_t cmax, const uint32_t* __restrict__ info) {
     const uint32_t kept = info[kInfoKept], M = info[kInfoM];
     const float rows_per = kept ? fmaxf(1.f, sqrtf((float)M / (float)kept)) : 1.f;
-    const uint32_t target = max(32u, (uint32_t)((float)kChunkTarget / rows_per));
+    const uint32_t target = max(32u, (uint32_t)((float)kChunkTarget1 / rows_per));
     const uint32_t per = max(target, (uint32_t)ceil_div(kept, cmax));
     Chunk ch;
     ch.used = (uint32_t)ceil_div(kept, per);
@@ -279,18 +310,24 @@ __device__ __forceinline__ Chunk l1_chunk(uint32_t c, uint32_t cmax, const uint3
 // highest lane of the mask advances the cursor by the mask's size and clears
 // it. Items go to a shared-memory stage grouped by bucket and leave as one run
 // per bucket written by consecutive lanes (a chunk too large for the stage
-// writes its items directly). Shared memory: words(B).
+// writes its items directly). Items are of type T (the value an item takes in
+// bucket q comes from a functor); the stage holds S of them. Shared memory:
+// words(B) 32-bit words, an even count (8-byte items stay aligned).
+template <typename T, uint32_t S>
 struct Placer {
-    uint32_t *pos, *mask, *first, *lstart, *stage;
+    uint32_t *pos, *mask, *first, *lstart;
+    T* stage;
     uint32_t B;
     bool staged;
-    __host__ __device__ static constexpr uint32_t words(uint32_t B) { return 4 * B + 1 + kStage; }
+    __host__ __device__ static constexpr uint32_t words(uint32_t B) {
+        return 4 * B + 2 + S * (uint32_t)(sizeof(T) / 4);
+    }
     __device__ __forceinline__ Placer(uint32_t* ws, uint32_t nb) : B(nb), staged(false) {
         pos = ws;
         mask = pos + nb;
         first = mask + nb;
         lstart = first + nb;
-        stage = lstart + nb + 1;
+        stage = reinterpret_cast<T*>(lstart + nb + 2);  // 4 nb + 2 words: even
     }
     // first_slot(q): the chunk's first slot in bucket q of the output; count(q): its items there
     template <typename First, typename Count>
@@ -310,7 +347,7 @@ struct Placer {
             if (lane >= o) incl += y;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        staged = total <= kStage;
+        staged = total <= S;
         uint32_t run = incl - sum;
         for (uint32_t q = q0; q < q1; ++q) {
             const uint32_t c = lstart[q];
@@ -322,15 +359,16 @@ struct Placer {
         if (lane == 31) lstart[B] = total;
         __syncwarp();
     }
-    // one batch: this lane's item (none if lo > hi) spans buckets lo..hi
-    __device__ __forceinline__ void batch(uint32_t lo, uint32_t hi, uint32_t item, int lane,
-                                          uint32_t* __restrict__ out) {
+    // one batch: this lane's item (none if lo > hi) spans buckets lo..hi and takes value item(q) in bucket q
+    template <typename Item>
+    __device__ __forceinline__ void batch(uint32_t lo, uint32_t hi, Item item, int lane, T* __restrict__ out) {
         const uint32_t bit = 1u << lane, lt = bit - 1u;
         for (uint32_t q = lo; q <= hi; ++q) atomicOr(&mask[q], bit);
         __syncwarp();
         for (uint32_t q = lo; q <= hi; ++q) {
             const uint32_t at = pos[q] + __popc(mask[q] & lt);
-            if (staged) stage[at] = item; else out[at] = item;
+            const T v = item(q);
+            if (staged) stage[at] = v; else out[at] = v;
         }
         __syncwarp();
         // the highest lane of a mask advances the bucket and clears the mask; any
@@ -345,7 +383,7 @@ struct Placer {
         __syncwarp();
     }
     // staged chunk: every bucket's run to out[first[q] ...], consecutive lanes
-    __device__ __forceinline__ void flush(uint32_t* __restrict__ out, int lane) {
+    __device__ __forceinline__ void flush(T* __restrict__ out, int lane) {
         if (!staged) return;
         for (uint32_t q = 0; q < B; ++q) {
             const uint32_t s0 = lstart[q], n = lstart[q + 1] - s0;
@@ -354,6 +392,29 @@ struct Placer {
         }
     }
 };
+// Tiles of row y that Gaussian g touches (row_span within its rectangle); none
+// (returned as (1, 0)) for an id of ~0 (past the chunk) or an empty span.
+struct DiscRef {
+    const uint2* rect;
+    const float4* disc;
+    int tile;
+    float inv_tile;
+    int footprint;
+    __device__ __forceinline__ int2 span(uint32_t g, int y) const {
+        if (g == 0xFFFFFFFFu) return make_int2(1, 0);
+        int2 sp;
+        if (footprint == 0) {
+            const uint2 r = rect[g];
+            sp = make_int2((int)(r.x & 0xFFFF), (int)(r.y & 0xFFFF));
+        } else {
+            sp = disc_span(disc[g], tile, inv_tile, y);
+        }
+        return sp.y < sp.x ? make_int2(1, 0) : sp;  // an empty span as (1, 0): lo > hi, both >= 0
+    }
+};
+
+using Placer1 = Placer<u64, kStage1>;      // level 1: (column span << 32 | Gaussian id) items
+using Placer2 = Placer<uint32_t, kStage>;  // level 2: Gaussian ids
 
 // Level 1, count: for each of its chunks c (grid-stride over warps), a warp adds,
 // for each Gaussian of the chunk, one to every row of its rectangle; writes
@@ -468,13 +529,16 @@ __global__ void __launch_bounds__(kLayoutThreads) k_rows_layout(const uint32_t* 
 }
 
 // Level 1, place: a warp walks each of its chunks again and puts each Gaussian
-// id into the list of every row of its rectangle (R1, rows one after another).
+// into the list of every row of its rectangle (R1, rows one after another), as
+// the item (xa | xb << 16) << 32 | id with the tiles [xa, xb] it touches in
+// that row ((1, 0): none), so that level 2 reads its items without a gather.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* __restrict__ order,
-                                                                const uint2* __restrict__ srect, uint32_t rows,
+                                                                const uint2* __restrict__ srect, DiscRef disc,
+                                                                uint32_t rows,
                                                                 uint32_t cmax, const uint32_t* __restrict__ H1,
                                                                 const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
-                                                                uint32_t* __restrict__ R1,
+                                                                u64* __restrict__ R1,
                                                                 const uint32_t* __restrict__ info) {
     pdl_wait();
     extern __shared__ uint32_t s_walk[];
@@ -483,7 +547,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* 
     const uint32_t used = l1_chunk(0, cmax, info).used;
     for (uint32_t c = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); c < used; c += gridDim.x * kWalkWarps) {
         const Chunk ch = l1_chunk(c, cmax, info);
-        Placer rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer::words(rows), rows);
+        Placer1 rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer1::words(rows), rows);
         auto first = [&](uint32_t y) { return rowinfo[y] + H1[(size_t)y * cmax + c]; };
         rs.init(lane, first, [&](uint32_t y) {
             const uint32_t* h = H1 + (size_t)y * cmax;
@@ -497,7 +561,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* 
             const bool more = b + 32 + lane < ch.p1;
             g_next = more ? order[b + 32 + lane] : 0xFFFFFFFFu;
             r_next = more ? srect[b + 32 + lane] : make_uint2(1u << 16, 0u);
-            rs.batch(r.x >> 16, r.y >> 16, g, lane, R1);
+            if (disc.footprint == 0) {  // every row: the rectangle's columns
+                const u64 item = (u64)g | ((u64)((r.x & 0xFFFFu) | (r.y << 16)) << 32);
+                rs.batch(r.x >> 16, r.y >> 16, [&](uint32_t) { return item; }, lane, R1);
+            } else {  // per row: the columns the disc meets there
+                const float4 d = g != 0xFFFFFFFFu ? disc.disc[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+                rs.batch(r.x >> 16, r.y >> 16, [&](uint32_t y) {
+                    int2 sp = disc_span(d, disc.tile, disc.inv_tile, (int)y);
+                    if (sp.y < sp.x) sp = make_int2(1, 0);
+                    return (u64)g | ((u64)((uint32_t)sp.x | ((uint32_t)sp.y << 16)) << 32);
+                }, lane, R1);
+            }
         }
         rs.flush(R1, lane);
         __syncwarp();  // the next chunk's init rewrites what the flush reads
@@ -524,37 +598,13 @@ __device__ __forceinline__ RowChunk l2_chunk(uint32_t j, uint32_t rows, const ui
     return rc;
 }
 
-// Tiles of row y that Gaussian g touches (row_span within its rectangle); none
-// (returned as (1, 0)) for an id of ~0 (past the chunk) or an empty span.
-struct DiscRef {
-    const uint2* rect;
-    const float4* disc;
-    int tile;
-    float inv_tile;
-    int footprint;
-    __device__ __forceinline__ int2 span(uint32_t g, int y) const {
-        if (g == 0xFFFFFFFFu) return make_int2(1, 0);
-        int2 sp;
-        if (footprint == 0) {
-            const uint2 r = rect[g];
-            sp = make_int2((int)(r.x & 0xFFFF), (int)(r.y & 0xFFFF));
-        } else {
-            sp = disc_span(disc[g], tile, inv_tile, y);
-        }
-        return sp.y < sp.x ? make_int2(1, 0) : sp;  // an empty span as (1, 0): lo > hi, both >= 0
-    }
-};
-
 // Level 2, count: for each of its chunks j, a warp adds, for each item of the
-// chunk, one to every tile of the row that the item's Gaussian touches; writes
-// row j of H2 [chunks][tiles_x], and each item's tiles (span[i] = xa | xb << 16,
-// (1, 0) for none) so that the placement reads them without a gather.
-__global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* __restrict__ R1,
-                                                                DiscRef disc, uint32_t rows,
+// chunk, one to every tile of the row that the item's Gaussian touches (the
+// span the item carries); writes row j of H2 [chunks][tiles_x].
+__global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const u64* __restrict__ R1, uint32_t rows,
                                                                 uint32_t tiles_x, const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 uint32_t* __restrict__ H2,
-                                                                uint32_t* __restrict__ span,
                                                                 const uint32_t* __restrict__ info) {
     pdl_wait();
     extern __shared__ uint32_t s_walk[];
@@ -567,22 +617,15 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const uint32_t* 
         for (uint32_t x = lane; x < tiles_x; x += 32) cnt[x] = 0u;
         __syncwarp();
         for (uint32_t b = rc.i0; b < rc.i1; b += 32 * kWalkUnroll) {
-            uint32_t g[kWalkUnroll];
-            int2 sp[kWalkUnroll];
+            uint32_t sp[kWalkUnroll];
 #pragma unroll
             for (int k = 0; k < kWalkUnroll; ++k) {
                 const uint32_t i = b + k * 32 + lane;
-                g[k] = i < rc.i1 ? R1[i] : 0xFFFFFFFFu;
-            }
-#pragma unroll
-            for (int k = 0; k < kWalkUnroll; ++k) {
-                sp[k] = disc.span(g[k], (int)rc.y);
-                const uint32_t i = b + k * 32 + lane;
-                if (i < rc.i1) span[i] = (uint32_t)sp[k].x | ((uint32_t)sp[k].y << 16);
+                sp[k] = i < rc.i1 ? (uint32_t)(R1[i] >> 32) : 1u;  // (1, 0): no tiles
             }
 #pragma unroll
             for (int k = 0; k < kWalkUnroll; ++k)
-                for (int x = sp[k].x; x <= sp[k].y; ++x) atomicAdd(&cnt[x], 1u);
+                for (uint32_t x = sp[k] & 0xFFFFu; x <= (sp[k] >> 16); ++x) atomicAdd(&cnt[x], 1u);
         }
         __syncwarp();
         uint32_t* out = H2 + (size_t)j * tiles_x;
@@ -628,8 +671,7 @@ __global__ void __launch_bounds__(32 * kColScanWarps) k_cols_scan(uint32_t* __re
 
 // Level 2, place: a warp walks each of its chunks again and puts each item's
 // Gaussian id into its slot in every tile of the row that the Gaussian touches.
-__global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* __restrict__ R1,
-                                                                const uint32_t* __restrict__ span, uint32_t rows,
+__global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const u64* __restrict__ R1, uint32_t rows,
                                                                 uint32_t tiles_x, const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
                                                                 const uint32_t* __restrict__ H2,
@@ -644,19 +686,18 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const uint32_t* 
     for (uint32_t j = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); j < total; j += gridDim.x * kWalkWarps) {
         const RowChunk rc = l2_chunk(j, rows, rowinfo, len);
         const bool last = j + 1 == (rc.y + 1 < rows ? rowinfo[rows + rc.y + 1] : rowinfo[3 * rows]);
-        Placer rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer::words(tiles_x), tiles_x);
+        Placer2 rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer2::words(tiles_x), tiles_x);
         const uint32_t* h = H2 + (size_t)j * tiles_x;
         const uint2* rg = ranges + (size_t)rc.y * tiles_x;
         auto first = [&](uint32_t x) { return h[x]; };
         rs.init(lane, first, [&](uint32_t x) { return (last ? rg[x].y : h[x + tiles_x]) - h[x]; });
-        uint32_t g_next = rc.i0 + lane < rc.i1 ? R1[rc.i0 + lane] : 0xFFFFFFFFu;
-        uint32_t s_next = rc.i0 + lane < rc.i1 ? span[rc.i0 + lane] : 1u;  // (1, 0): no tiles
+        const u64 none = 0xFFFFFFFFull | (1ull << 32);  // past the chunk: (1, 0), no tiles
+        u64 it_next = rc.i0 + lane < rc.i1 ? R1[rc.i0 + lane] : none;
         for (uint32_t b = rc.i0; b < rc.i1; b += 32) {
-            const uint32_t g = g_next, sp = s_next;
-            const bool more = b + 32 + lane < rc.i1;
-            g_next = more ? R1[b + 32 + lane] : 0xFFFFFFFFu;
-            s_next = more ? span[b + 32 + lane] : 1u;
-            rs.batch(sp & 0xFFFFu, sp >> 16, g, lane, vals);
+            const u64 it = it_next;
+            it_next = b + 32 + lane < rc.i1 ? R1[b + 32 + lane] : none;
+            const uint32_t g = (uint32_t)it, sp = (uint32_t)(it >> 32);
+            rs.batch(sp & 0xFFFFu, sp >> 16, [&](uint32_t) { return g; }, lane, vals);
         }
         rs.flush(vals, lane);
         __syncwarp();  // the next chunk's init rewrites what the flush reads
@@ -736,9 +777,10 @@ static cudaError_t walk_opt_in() {
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return cudaSuccess;
-    const int bytes = kWalkWarps * (int)Placer::words(kRowWalkMax) * 4;
-    if ((e = cudaFuncSetAttribute(k_rows_place, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_cols_place, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    const int bytes1 = kWalkWarps * (int)Placer1::words(kRowWalkMax) * 4;
+    const int bytes2 = kWalkWarps * (int)Placer2::words(kRowWalkMax) * 4;
+    if ((e = cudaFuncSetAttribute(k_rows_place, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes1)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_cols_place, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes2)) != cudaSuccess)
         return e;
     done[dev] = true;
     return cudaSuccess;
@@ -759,9 +801,10 @@ static int64_t l2_chunks_max(int64_t capacity, int64_t tiles_y) {
 }
 
 // The difference grid has (tiles_y + 1)(tiles_x + 1) = tiles + tiles_x + tiles_y + 1
-// <= 2 tiles + 2 cells. Route a needs no item buffers: vals and tile_key take
-// 4 bytes per entry each (the level-1 lists live in tile_key's buffer until the
-// keys are exported); route b's two 8-byte item buffers hold them.
+// <= 2 tiles + 2 cells. Route a: vals takes 4 bytes per entry and the second
+// buffer 8 (the 8-byte level-1 items, which never outnumber the entries, live
+// there until the keys are exported into it as tile ids); route b's two 8-byte
+// item buffers hold vals and tile_key.
 size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t tiles_y, int64_t chunks) {
     const int64_t tiles = tiles_x * tiles_y;
     const int64_t bn = ceil_div(n, kSortTile), bc = ceil_div(capacity, kSortTile), bs = ceil_div(n, kScanTile);
@@ -770,7 +813,8 @@ size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t 
     const int64_t rows = chunks > 0 ? tiles_y : 0;
     size_t b = 0;
     b += 2 * align256((size_t)n * 8);                                        // ditems_a, ditems_b
-    b += 2 * align256((size_t)capacity * entry);                             // items_a, items_b
+    b += align256((size_t)capacity * entry);                                 // items_a
+    b += align256((size_t)capacity * 8);                                     // items_b
     b += align256(8 * kRadix * 4);                                           // hist
     b += align256(16 * 4);                                                   // counters
     b += align256((size_t)4 * bn * kRadix * 4);                              // status_depth
@@ -783,7 +827,6 @@ size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t 
     b += align256((size_t)(3 * rows + 1) * 4);                               // walk_rows
     b += align256((size_t)(chunks > 0 ? l2_chunks_max(capacity, tiles_y) * tiles_x : 0) * 4);  // walk_h2
     b += align256((size_t)(chunks > 0 ? n : 0) * 8);                         // walk_rect
-    b += align256((size_t)(chunks > 0 ? capacity : 0) * 4);                  // walk_span
     return b;
 }
 
@@ -801,7 +844,7 @@ SortScratch sort_scratch(const igs_frame& f) {
     s.ditems_a = (u64*)take((size_t)n * 8);
     s.ditems_b = (u64*)take((size_t)n * 8);
     s.items_a = (u64*)take((size_t)cap * entry);
-    s.items_b = (u64*)take((size_t)cap * entry);
+    s.items_b = (u64*)take((size_t)cap * 8);
     s.hist = (uint32_t*)take(8 * kRadix * 4);
     s.counters = (uint32_t*)take(16 * 4);
     s.status_depth = (uint32_t*)take((size_t)4 * bn * kRadix * 4);
@@ -815,7 +858,6 @@ SortScratch sort_scratch(const igs_frame& f) {
     s.walk_rows = (uint32_t*)take((size_t)(3 * rows + 1) * 4);
     s.walk_h2 = (uint32_t*)take((size_t)(chunks > 0 ? l2_chunks_max(cap, f.tiles_y) * f.tiles_x : 0) * 4);
     s.walk_rect = (uint2*)take((size_t)(chunks > 0 ? n : 0) * 8);
-    s.walk_span = (uint32_t*)take((size_t)(chunks > 0 ? cap : 0) * 4);
     // the last tile pass (p = passes - 1) reads items_a when p is even, items_b when odd
     const bool last_reads_a = s.tile_passes > 0 && (s.tile_passes - 1) % 2 == 0;
     s.vals = reinterpret_cast<uint32_t*>(last_reads_a ? s.items_b : s.items_a);
@@ -922,10 +964,10 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
     if (s.walk_chunks > 0) {
         // 3a. two-level counting sort: Gaussians into tile-row lists, then row items into tiles
         const uint32_t rows = (uint32_t)f.tiles_y, cols = (uint32_t)f.tiles_x;
-        uint32_t* R1 = f.tile_key;  // level-1 lists: free until the keys are exported
+        u64* R1 = s.items_b;  // level-1 lists: free until the keys are exported (as tile_key) into it
         const size_t count1 = (size_t)kWalkWarps * rows * 4, count2 = (size_t)kWalkWarps * cols * 4;
-        const size_t place1 = (size_t)kWalkWarps * Placer::words(rows) * 4;
-        const size_t place2 = (size_t)kWalkWarps * Placer::words(cols) * 4;
+        const size_t place1 = (size_t)kWalkWarps * Placer1::words(rows) * 4;
+        const size_t place2 = (size_t)kWalkWarps * Placer2::words(cols) * 4;
         if (std::max(place1, place2) > 48 * 1024) CK(walk_opt_in());
         const int64_t max2 = l2_chunks_max(cap, rows);
         const uint32_t cmax = (uint32_t)s.walk_chunks;
@@ -941,19 +983,19 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         CK(launch_pdl(k_rows_layout, dim3(1), dim3(kLayoutThreads), 0, st, s.walk_len, rg, rows, cols, (uint32_t)max2, s.walk_rows, f.info));
         count_launches();
         CK(cudaGetLastError());
-        CK(launch_pdl(k_rows_place, dim3(walk_blocks((const void*)k_rows_place, place1, cmax)), dim3(32 * kWalkWarps), place1, st, f.order, s.walk_rect, rows, cmax, s.walk_h1, s.walk_len,
+        const DiscRef disc{rect, reinterpret_cast<const float4*>(f.disc), f.tile, 1.0f / (float)f.tile, footprint};
+        CK(launch_pdl(k_rows_place, dim3(walk_blocks((const void*)k_rows_place, place1, cmax)), dim3(32 * kWalkWarps), place1, st, f.order, s.walk_rect, disc, rows, cmax, s.walk_h1, s.walk_len,
                                                                 s.walk_rows, R1, f.info));
         count_launches();
         CK(cudaGetLastError());
-        const DiscRef disc{rect, reinterpret_cast<const float4*>(f.disc), f.tile, 1.0f / (float)f.tile, footprint};
-        CK(launch_pdl(k_cols_count, dim3(walk_blocks((const void*)k_cols_count, count2, max2)), dim3(32 * kWalkWarps), count2, st, R1, disc, rows, cols, s.walk_len, s.walk_rows,
-                                                                s.walk_h2, s.walk_span, f.info));
+        CK(launch_pdl(k_cols_count, dim3(walk_blocks((const void*)k_cols_count, count2, max2)), dim3(32 * kWalkWarps), count2, st, (const u64*)R1, rows, cols, s.walk_len, s.walk_rows,
+                                                                s.walk_h2, f.info));
         count_launches();
         CK(cudaGetLastError());
         CK(launch_pdl(k_cols_scan, dim3(rows), dim3(32 * kColScanWarps), 0, st, s.walk_h2, rows, cols, rg, s.walk_rows, f.info));
         count_launches();
         CK(cudaGetLastError());
-        CK(launch_pdl(k_cols_place, dim3(walk_blocks((const void*)k_cols_place, place2, max2)), dim3(32 * kWalkWarps), place2, st, R1, s.walk_span, rows, cols, s.walk_len, s.walk_rows,
+        CK(launch_pdl(k_cols_place, dim3(walk_blocks((const void*)k_cols_place, place2, max2)), dim3(32 * kWalkWarps), place2, st, (const u64*)R1, rows, cols, s.walk_len, s.walk_rows,
                                                                 s.walk_h2, rg, f.vals, f.info));
         count_launches();
         CK(cudaGetLastError());
