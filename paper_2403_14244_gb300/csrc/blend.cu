@@ -52,14 +52,22 @@ struct BwdPixel {
     uint32_t nc;
 };
 
+// Per-entry factors of the adjoint, shared by the pixels that walk the entry:
+// d alpha / d power = -ln 2 o g, d power / d(u, v) = -2 w2 (dx, dy).
+struct BwdEntry {
+    float4 a, c;
+    float ocl;  // -ln 2 o
+    float m2z;  // -2 w2
+};
+
 // The adjoint of one (pixel, entry) pair, added to v[0..6]; false if the pixel
 // did not blend the entry.
-__device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, float4 a4, const float4* s_c, int k,
-                                         const BlendParams& P, float v[8]) {
+__device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, const BwdEntry& e, const BlendParams& P,
+                                         float v[8]) {
     if (pos >= q.nc) return false;
+    const float4 a4 = e.a, c = e.c;
     const Dist d = eval_dist(q.px, q.py, a4);
     if (d.pw > a4.w) return false;
-    const float4 c = s_c[k];
     const float g = fast_exp2(-d.pw);
     const float og = __fmul_rn(c.w, g);
     const float alpha = fminf(P.alpha_max, og);
@@ -76,10 +84,11 @@ __device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, float4 a4, c
     q.GS = fmaf(wT, Gc, q.GS);
     q.T = Tk;
     if (og <= P.alpha_max) {                    // alpha not clamped
-        v[3] += dalpha * g;                     // d/do
-        const float dpow = -kLn2 * g * (dalpha * c.w);  // d/d(power), power = w2 d^2
+        const float dg = dalpha * g;
+        v[3] += dg;                             // d/do
+        const float dpow = dg * e.ocl;          // d/d(power), power = w2 d^2
         v[2] += dpow * d.d2;                    // d/dw2
-        const float k2 = -2.f * dpow * a4.z;
+        const float k2 = dpow * e.m2z;
         v[0] += k2 * d.dx;                      // d/du  (dx = px - u)
         v[1] += k2 * d.dy;                      // d/dv
     }
@@ -163,10 +172,14 @@ __device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const u
                 const int k = hw * 32 + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const uint32_t pos = hi - 1 - k - rg.x;  // list position within the tile
-                const float4 a4 = s_a[k];
+                BwdEntry e;
+                e.a = s_a[k];
+                e.c = s_c[k];
+                e.ocl = -kLn2 * e.c.w;
+                e.m2z = -2.f * e.a.z;
                 float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                const bool active0 = bwd_pair(q[0], pos, a4, s_c, k, P, v);
-                const bool active1 = bwd_pair(q[1], pos, a4, s_c, k, P, v);
+                const bool active0 = bwd_pair(q[0], pos, e, P, v);
+                const bool active1 = bwd_pair(q[1], pos, e, P, v);
                 if (__any_sync(0xffffffffu, active0 || active1)) {
                     const float r = warp_reduce8(v, lane);
                     if ((lane & 3) == 0) s_red[w][k][lane >> 2] = r;

@@ -458,14 +458,64 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* 
     }
 }
 
-// Level 1, scan: block y turns row y of H1 (the used chunks' counts) into
-// exclusive offsets in place and writes the row's item count to len[y].
+// Row layout. rowinfo = [rows] list starts, [rows] first level-2 chunk, [rows]
+// items per level-2 chunk, [1] level-2 chunk total. A row's chunk takes about
+// kChunkTarget entries: kChunkTarget * items / entries of the row items, at
+// least 32. Records an error if the chunks exceed `max_chunks`. One block of NT
+// threads; len is read through L2 (other blocks wrote it).
 constexpr int kRowScanThreads = 256;
+template <int NT>
+__device__ __forceinline__ void row_layout(const uint32_t* __restrict__ len, const uint2* __restrict__ ranges,
+                                           uint32_t rows, uint32_t tiles_x, uint32_t max_chunks,
+                                           uint32_t* __restrict__ rowinfo, uint32_t* __restrict__ info,
+                                           unsigned long long* s_entries, uint32_t* s_warp) {
+    for (uint32_t y = threadIdx.x; y < rows; y += NT) s_entries[y] = 0ull;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < rows * tiles_x; t += NT) {
+        const uint2 r = __ldcg(ranges + t);
+        if (r.y > r.x) atomicAdd(&s_entries[t / tiles_x], (unsigned long long)(r.y - r.x));
+    }
+    __syncthreads();
+    const uint32_t per = (rows + NT - 1) / NT;
+    const uint32_t y0 = min(rows, threadIdx.x * per), y1 = min(rows, y0 + per);
+    uint32_t items = 0, chunks = 0;
+    for (uint32_t y = y0; y < y1; ++y) {
+        const uint64_t entries = s_entries[y];
+        const uint32_t ly = __ldcg(len + y);
+        const uint32_t size =
+            (uint32_t)max((uint64_t)32, entries ? (uint64_t)kChunkTarget * ly / entries : (uint64_t)kChunkTarget);
+        rowinfo[2 * rows + y] = size;
+        items += ly;
+        chunks += (ly + size - 1) / size;
+    }
+    uint32_t start = block_excl_scan<NT>(items, s_warp);
+    uint32_t base = block_excl_scan<NT>(chunks, s_warp);
+    if (threadIdx.x == NT - 1) {
+        rowinfo[3 * rows] = base + chunks;
+        if (base + chunks > max_chunks) record_error(info, IGS_ERR_CUDA);  // never expected: chunks are bounded
+    }
+    for (uint32_t y = y0; y < y1; ++y) {
+        const uint32_t ly = __ldcg(len + y);
+        rowinfo[y] = start;
+        rowinfo[rows + y] = base;
+        start += ly;
+        base += (ly + rowinfo[2 * rows + y] - 1) / rowinfo[2 * rows + y];
+    }
+}
+
+// Level 1, scan: block y turns row y of H1 (the used chunks' counts) into
+// exclusive offsets in place and writes the row's item count to len[y]; the
+// last block to finish (a ticket on `done`, zero on entry) lays out the rows.
 __global__ void __launch_bounds__(kRowScanThreads) k_rows_scan(uint32_t* __restrict__ H1, uint32_t cmax,
                                                                uint32_t* __restrict__ len,
-                                                               const uint32_t* __restrict__ info) {
+                                                               const uint2* __restrict__ ranges, uint32_t tiles_x,
+                                                               uint32_t max_chunks, uint32_t* __restrict__ rowinfo,
+                                                               uint32_t* __restrict__ done,
+                                                               uint32_t* __restrict__ info) {
     pdl_wait();
     __shared__ uint32_t s_warp[kRowScanThreads / 32];
+    __shared__ unsigned long long s_entries[kRowWalkMax];
+    __shared__ bool s_last;
     if (info[kInfoAbort]) return;
     uint32_t* row = H1 + (size_t)blockIdx.x * cmax;
     const uint32_t used = l1_chunk(0, cmax, info).used;
@@ -480,52 +530,13 @@ __global__ void __launch_bounds__(kRowScanThreads) k_rows_scan(uint32_t* __restr
         row[c] = run;
         run += h;
     }
-}
-
-// Row layout (one block). rowinfo = [rows] list starts, [rows] first level-2
-// chunk, [rows] items per level-2 chunk, [1] level-2 chunk total. A row's chunk
-// takes about kChunkTarget entries: kChunkTarget * items / entries of the row
-// items, at least 32. Records an error if the chunks exceed `max_chunks`.
-constexpr int kLayoutThreads = 1024;
-__global__ void __launch_bounds__(kLayoutThreads) k_rows_layout(const uint32_t* __restrict__ len,
-                                                                const uint2* __restrict__ ranges, uint32_t rows,
-                                                                uint32_t tiles_x, uint32_t max_chunks,
-                                                                uint32_t* __restrict__ rowinfo,
-                                                                uint32_t* __restrict__ info) {
-    pdl_wait();
-    __shared__ uint32_t s_warp[kLayoutThreads / 32];
-    __shared__ unsigned long long s_entries[kRowWalkMax];
-    if (info[kInfoAbort]) return;
-    for (uint32_t y = threadIdx.x; y < rows; y += kLayoutThreads) s_entries[y] = 0ull;
+    __threadfence();  // len[y] before the ticket
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < rows * tiles_x; t += kLayoutThreads) {
-        const uint2 r = ranges[t];
-        if (r.y > r.x) atomicAdd(&s_entries[t / tiles_x], (unsigned long long)(r.y - r.x));
-    }
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
     __syncthreads();
-    const uint32_t per = (rows + kLayoutThreads - 1) / kLayoutThreads;
-    const uint32_t y0 = min(rows, threadIdx.x * per), y1 = min(rows, y0 + per);
-    uint32_t items = 0, chunks = 0;
-    for (uint32_t y = y0; y < y1; ++y) {
-        const uint64_t entries = s_entries[y];
-        const uint32_t size =
-            (uint32_t)max((uint64_t)32, entries ? (uint64_t)kChunkTarget * len[y] / entries : (uint64_t)kChunkTarget);
-        rowinfo[2 * rows + y] = size;
-        items += len[y];
-        chunks += (len[y] + size - 1) / size;
-    }
-    uint32_t start = block_excl_scan<kLayoutThreads>(items, s_warp);
-    uint32_t base = block_excl_scan<kLayoutThreads>(chunks, s_warp);
-    if (threadIdx.x == kLayoutThreads - 1) {
-        rowinfo[3 * rows] = base + chunks;
-        if (base + chunks > max_chunks) record_error(info, IGS_ERR_CUDA);  // never expected: chunks are bounded
-    }
-    for (uint32_t y = y0; y < y1; ++y) {
-        rowinfo[y] = start;
-        rowinfo[rows + y] = base;
-        start += len[y];
-        base += (len[y] + rowinfo[2 * rows + y] - 1) / rowinfo[2 * rows + y];
-    }
+    if (!s_last) return;
+    __threadfence();
+    row_layout<kRowScanThreads>(len, ranges, gridDim.x, tiles_x, max_chunks, rowinfo, info, s_entries, s_warp);
 }
 
 // Level 1, place: a warp walks each of its chunks again and puts each Gaussian
@@ -977,10 +988,8 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         CK(launch_pdl(k_rows_count, dim3(walk_blocks((const void*)k_rows_count, count1, cmax)), dim3(32 * kWalkWarps), count1, st, f.order, rect, rows, cmax, s.walk_h1, s.walk_rect, f.info));
         count_launches();
         CK(cudaGetLastError());
-        CK(launch_pdl(k_rows_scan, dim3(rows), dim3(kRowScanThreads), 0, st, s.walk_h1, cmax, s.walk_len, f.info));
-        count_launches();
-        CK(cudaGetLastError());
-        CK(launch_pdl(k_rows_layout, dim3(1), dim3(kLayoutThreads), 0, st, s.walk_len, rg, rows, cols, (uint32_t)max2, s.walk_rows, f.info));
+        CK(launch_pdl(k_rows_scan, dim3(rows), dim3(kRowScanThreads), 0, st, s.walk_h1, cmax, s.walk_len, rg, cols,
+                      (uint32_t)max2, s.walk_rows, s.counters + 12, f.info));
         count_launches();
         CK(cudaGetLastError());
         const DiscRef disc{rect, reinterpret_cast<const float4*>(f.disc), f.tile, 1.0f / (float)f.tile, footprint};
