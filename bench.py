@@ -632,7 +632,7 @@ def run_extra(dev, np, tile=32):
     out["octree_init"] = run_octree(dev)
     out["fit2d_512"] = run_fit2d(dev)
     out["batched_32view_2M"] = run_batched(dev)
-    out["serve_4scenes_poisson200"] = run_serving(dev)
+    out["serve_4scenes_poisson"] = run_serving(dev)
     return out
 
 
@@ -916,10 +916,17 @@ def run_batched(dev, reps=10):
             "loop_frames_per_s": round(len(cams) * 1e3 / loop[lt], 1)}
 
 
+SERVE_RATES = (200.0, 800.0, 1100.0, 1500.0)
+SERVE_MODES = {"slots1": (1, 1), "slots4": (4, 1), "slots4_group8": (4, 8)}
+
+
 def run_serving(dev, n_req=2000, warm=200, rate=200.0, budget=8 << 30, seed=5, tile=32):
-    """Four resident scenes (0.5, 1, 2, 4M Gaussians), open-loop Poisson arrivals
-    at `rate`/s, random scene, sphere pose, 480p..2160p; served with 4 slots
-    (continuous batching) and strictly one at a time, on the same arrivals."""
+    """Four resident scenes (0.5, 1, 2, 4M Gaussians), open-loop Poisson arrivals,
+    random scene, sphere pose, 480p..2160p, on the same arrival pattern (gaps
+    scaled) at each rate of SERVE_RATES (the workload's own 200/s first) and all
+    at once (burst); served strictly one at a time (slots1), with 4 slots
+    (continuous batching), and with 4 slots whose queued requests of one scene
+    share a batched chain (up to 8 views)."""
     import threading
 
     import numpy as np
@@ -938,8 +945,8 @@ def run_serving(dev, n_req=2000, warm=200, rate=200.0, budget=8 << 30, seed=5, t
     bufs = {(w, h): [torch.empty((3, h, w), device=dev) for _ in range(ring)] for w, h in scenes.RESOLUTIONS_SERVE}
     out = {}
 
-    def serve(slots, gaps):
-        srv = igs.Server(pool_bytes=budget, slots=slots, tile=tile, device=dev)
+    def serve(slots, gaps, group=1):
+        srv = igs.Server(pool_bytes=budget, slots=slots, tile=tile, device=dev, group=group)
         sids = [srv.add_scene(sc) for sc in scs]
         cam_s = [igs.camera(c) for c in cams]
         ids = [None] * total
@@ -978,15 +985,20 @@ def run_serving(dev, n_req=2000, warm=200, rate=200.0, budget=8 << 30, seed=5, t
         bad = sum(1 for i in range(warm, total) if timings[i][0] != igs.OK)
         lat = np.array([(t["done_ns"] - t["arrival_ns"]) / 1e6 for t in meas])
         span = (max(t["done_ns"] for t in meas) - min(t["arrival_ns"] for t in meas)) / 1e9
+        grp = [t["group"] for t in meas]
         return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                 "max_ms": round(float(lat.max()), 3), "frames_per_s": round((n_req - bad) / span, 1), "failed": bad,
-                "pool_peak_bytes": int(stats["pool_peak"]), "retries": int(sum(t["retries"] for t in meas))}
+                "pool_peak_bytes": int(stats["pool_peak"]), "retries": int(sum(t["retries"] for t in meas)),
+                "mean_group": round(float(np.mean(grp)), 2)}
 
-    for slots in (4, 1):
-        out["poisson_slots%d" % slots] = serve(slots, gaps)
+    for r in SERVE_RATES:
+        for name, (slots, group) in SERVE_MODES.items():
+            if r == rate and name == "slots4_group8":
+                continue  # at the workload's own rate requests rarely wait: grouping has nothing to group
+            out[f"poisson{int(r)}_{name}"] = serve(slots, gaps * (rate / r), group)
     # the same requests submitted back to back: the throughput each mode can sustain
-    for slots in (4, 1):
-        out["burst_slots%d" % slots] = serve(slots, np.zeros(total))
+    for name, (slots, group) in SERVE_MODES.items():
+        out[f"burst_{name}"] = serve(slots, np.zeros(total), group)
     out["tile"] = tile
     out["requests"] = n_req
     out["warmup"] = warm

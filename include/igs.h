@@ -558,9 +558,11 @@ IGS_API igs_status igs_batch_status(const igs_batch* batch, uint32_t* host_info,
  * workspace fits in the caller's device pool, so requests that arrive while
  * others run overlap with them on the GPU. The entries a request needs are
  * sized from earlier requests of the same scene and image size; a request that
- * overflows is re-queued at the head with the capacity it reported. One host
- * thread per server schedules; the library allocates no device memory (the pool
- * is the caller's) and 16 bytes of pinned host memory per slot.
+ * overflows is re-queued at the head with the capacity it reported. With
+ * grouping on (igs_serve_set_grouping), requests of one scene that wait
+ * together share one batched chain of launches. One host thread per server
+ * schedules; the library allocates no device memory (the pool is the caller's)
+ * and 80 bytes of pinned host memory per slot.
  * ------------------------------------------------------------------------- */
 typedef struct igs_server igs_server;
 
@@ -572,7 +574,7 @@ typedef struct igs_timing {
     uint32_t entries;    /* (Gaussian, tile) entries of the view */
     int32_t status;      /* igs_status of the request */
     int32_t retries;     /* re-queues after a capacity overflow */
-    int32_t _pad;
+    int32_t group;       /* views rendered by the same chain of launches (1: alone) */
 } igs_timing;
 
 /* Create a server on the current device. pool (device, 256-byte aligned,
@@ -581,6 +583,15 @@ typedef struct igs_timing {
  * apply to every request; sh_degree / param_mode come with each scene. */
 IGS_API igs_status igs_serve_create(void* pool, size_t pool_bytes, int32_t max_slots, const igs_opts* opts,
                                     igs_server** out);
+/* Grouping: requests of one scene that wait together (among the first 64
+ * queued) are rendered, up to max_views of them, by one batched chain of
+ * launches (igs_render_batch: one projection, binning and blend launch for all
+ * of them) on one slot, each image then copied to its request's output. The
+ * pixels are those of rendering each request alone. 1 (the default) renders
+ * every request by itself; 1 <= max_views <= 16. A group whose entries
+ * overflow is split: its requests are redone one by one. Takes effect for
+ * admissions after the call. */
+IGS_API igs_status igs_serve_set_grouping(igs_server* server, int32_t max_views);
 /* Register a resident scene (device buffers, layout as above); *scene_id
  * identifies it in igs_serve_submit. */
 IGS_API igs_status igs_serve_add_scene(igs_server* server, const igs_scene* scene, int32_t sh_degree,

@@ -369,6 +369,12 @@ int64_t batch_max_cells(const igs_batch& b) {
 
 size_t batch_scratch_bytes(const igs_batch& b) { return carve(sizes_of(b, batch_grid_cells(b)), nullptr, nullptr); }
 
+const uint32_t* batch_view_totals(const igs_batch& b) {
+    BatchScratch s;
+    carve(sizes_of(b, batch_grid_cells(b)), static_cast<char*>(b.scratch), &s);
+    return s.view_total;
+}
+
 bool batch_blend_variant_ok(int tile, int batch) {
     void* fn;
     return blend_variant(tile, batch, &fn);

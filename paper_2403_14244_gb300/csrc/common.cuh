@@ -247,6 +247,8 @@ cudaError_t batch_prepare_kernels(const igs_batch& b);
 cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const BlendParams& bp, int sh_degree,
                                 float* images, cudaStream_t st, int footprint);
 int batch_persistent_blocks(int tile, int batch);
+// Device address of the per-view entry totals of a rendered batch ([views] words).
+const uint32_t* batch_view_totals(const igs_batch& b);
 
 // Scratch layout of a frame (pieces of igs_frame::scratch).
 struct SortScratch {

@@ -10,6 +10,11 @@
 // capacity from earlier requests of the same scene and image size (15 % margin)
 // and, if a request overflows, re-queues it at the head with the capacity it
 // reported. A request that can never fit the pool fails with IGS_ERR_CAPACITY.
+// With grouping on, the scheduler takes with the head request the other
+// requests of its scene among the first kGroupWindow queued (up to max_group
+// views) and renders them by one batched chain (igs_render_batch, images then
+// copied to each request's output); a group that overflows is split and its
+// requests are redone one by one.
 // The library allocates no device memory: frames are carved from the pool.
 #include <algorithm>
 #include <atomic>
@@ -88,6 +93,11 @@ struct SceneRec {
     igs_opts opts;
 };
 
+constexpr int kMaxGroup = 16;      // views of one grouped chain
+constexpr int kGroupWindow = 64;   // queued requests the scheduler looks through for a group
+constexpr int kBlendBatch = 64;    // batched blend: one 64-thread CTA per 8 x 8 block (8: persistent)
+constexpr int kStatusWords = 4 + kMaxGroup;  // per slot: frame/batch status, then per-view entries
+
 struct Request {
     uint64_t id = 0;
     int32_t scene = 0;
@@ -95,12 +105,18 @@ struct Request {
     float* img = nullptr;
     int64_t capacity = 0;
     igs_timing t{};
-    // in flight
-    int slot = -1;
+    bool solo = false;  // redo by itself (its group overflowed)
+    bool done = false;
+};
+
+// Work in flight on one slot: one request, or a group of one scene's requests.
+struct Job {
+    std::vector<Request*> reqs;
+    bool batched = false;
     char* ws = nullptr;
     size_t ws_bytes = 0;
     igs_frame frame{};
-    bool done = false;
+    igs_batch batch{};
 };
 
 }  // namespace
@@ -112,8 +128,9 @@ struct igs_server {
     int max_slots = 1;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
-    std::vector<uint32_t*> status_host;  // pinned, 4 words per slot
-    std::vector<Request*> slot_req;
+    std::vector<uint32_t*> status_host;  // pinned, kStatusWords per slot
+    std::vector<Job*> slot_job;
+    int max_group = 1;
     std::vector<SceneRec> scenes;
     std::map<std::tuple<int, int, int>, int64_t> cap_hint;  // (scene, W, H) -> entries
     std::deque<Request*> pending;
@@ -143,24 +160,137 @@ int64_t capacity_for(igs_server* s, const Request* r) {
     return std::min<int64_t>(c, (1 << 30) - 1);
 }
 
+// Pool bytes of a group's batch workspace plus its packed images; -1 if it cannot be laid out.
+int64_t group_bytes(const igs_server* s, const std::vector<Request*>& g, int64_t capacity) {
+    const SceneRec& sc = s->scenes[g[0]->scene];
+    igs_camera cams[kMaxGroup];
+    int64_t floats = 0;
+    for (size_t v = 0; v < g.size(); ++v) {
+        cams[v] = g[v]->cam;
+        floats += 3 * (int64_t)g[v]->cam.width * g[v]->cam.height;
+    }
+    size_t bytes = 0;
+    if (igs_batch_layout(sc.scene.n, (int32_t)g.size(), cams, &sc.opts, capacity, kBlendBatch, nullptr, &bytes,
+                         nullptr) != IGS_OK)
+        return -1;
+    return (int64_t)(al(bytes) + al((size_t)floats * 4));
+}
+
+void fail_job(igs_server* s, int slot, igs_status e) {
+    std::memset(s->status_host[slot], 0, kStatusWords * 4);
+    s->status_host[slot][igs::kInfoErr] = (uint32_t)e;
+    cudaEventRecord(s->events[slot], s->streams[slot]);
+}
+
 // Launch one admitted request on its slot's stream (no host synchronisation).
-void launch(igs_server* s, Request* r) {
-    const SceneRec& sc = s->scenes[r->scene];
-    cudaStream_t st = s->streams[r->slot];
-    igs_status e = igs_frame_layout(sc.scene.n, r->capacity, &r->cam, &sc.opts, r->ws, &r->ws_bytes, &r->frame);
-    if (e == IGS_OK) e = igs_project(&sc.scene, &r->cam, &sc.opts, &r->frame, st);
-    if (e == IGS_OK) e = igs_bin_sort(&r->frame, &sc.opts, st);
-    if (e == IGS_OK) e = igs_render_fwd(&r->frame, &sc.opts, r->img, st);
+void launch_single(igs_server* s, Job* j, int slot, const SceneRec& sc) {
+    Request* r = j->reqs[0];
+    cudaStream_t st = s->streams[slot];
+    size_t bytes = j->ws_bytes;
+    igs_status e = igs_frame_layout(sc.scene.n, r->capacity, &r->cam, &sc.opts, j->ws, &bytes, &j->frame);
+    if (e == IGS_OK) e = igs_project(&sc.scene, &r->cam, &sc.opts, &j->frame, st);
+    if (e == IGS_OK) e = igs_bin_sort(&j->frame, &sc.opts, st);
+    if (e == IGS_OK) e = igs_render_fwd(&j->frame, &sc.opts, r->img, st);
     if (e == IGS_OK &&
-        cudaMemcpyAsync(s->status_host[r->slot], r->frame.info, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st) !=
+        cudaMemcpyAsync(s->status_host[slot], j->frame.info, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess)
         e = IGS_ERR_CUDA;
-    if (e == IGS_OK && cudaEventRecord(s->events[r->slot], st) != cudaSuccess) e = IGS_ERR_CUDA;
-    if (e != IGS_OK) {
-        std::memset(s->status_host[r->slot], 0, 16);
-        s->status_host[r->slot][igs::kInfoErr] = (uint32_t)e;
-        cudaEventRecord(s->events[r->slot], st);
+    if (e == IGS_OK && cudaEventRecord(s->events[slot], st) != cudaSuccess) e = IGS_ERR_CUDA;
+    if (e != IGS_OK) fail_job(s, slot, e);
+}
+
+// Launch one admitted group: one batched chain, then each view's image to its
+// request's output, the batch status and the per-view entry totals to the host.
+void launch_group(igs_server* s, Job* j, int slot, int64_t capacity, const SceneRec& sc) {
+    cudaStream_t st = s->streams[slot];
+    const int V = (int)j->reqs.size();
+    igs_camera cams[kMaxGroup];
+    for (int v = 0; v < V; ++v) cams[v] = j->reqs[v]->cam;
+    size_t bytes = 0;
+    igs_status e = igs_batch_layout(sc.scene.n, V, cams, &sc.opts, capacity, kBlendBatch, j->ws, &bytes, &j->batch);
+    float* images = reinterpret_cast<float*>(j->ws + al(bytes));
+    if (e == IGS_OK) e = igs_batch_set_views(&j->batch, cams, &sc.opts, st);
+    if (e == IGS_OK) e = igs_render_batch(&j->batch, &sc.scene, &sc.opts, images, st);
+    for (int v = 0; v < V && e == IGS_OK; ++v)
+        if (cudaMemcpyAsync(j->reqs[v]->img, images + j->batch.image_offset[v],
+                            (size_t)3 * cams[v].width * cams[v].height * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            e = IGS_ERR_CUDA;
+    if (e == IGS_OK &&
+        (cudaMemcpyAsync(s->status_host[slot], j->batch.info, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(s->status_host[slot] + 4, igs::batch_view_totals(j->batch), (size_t)V * 4,
+                         cudaMemcpyDeviceToHost, st) != cudaSuccess))
+        e = IGS_ERR_CUDA;
+    if (e == IGS_OK && cudaEventRecord(s->events[slot], st) != cudaSuccess) e = IGS_ERR_CUDA;
+    if (e != IGS_OK) fail_job(s, slot, e);
+}
+
+void note_entries(igs_server* s, const Request* r, uint32_t entries) {
+    auto& h = s->cap_hint[{r->scene, r->cam.width, r->cam.height}];
+    h = std::max<int64_t>(h, (int64_t)(entries * 1.15) + 4096);
+}
+
+void finish(igs_server* s, Request* r, uint32_t entries, uint32_t err, int group) {
+    r->t.done_ns = now_ns();
+    r->t.entries = entries;
+    r->t.status = (int32_t)err;
+    r->t.group = group;
+    if (!err) note_entries(s, r, entries);
+    r->done = true;
+}
+
+// A finished job: results, hints, or the re-queue of what overflowed.
+void complete(igs_server* s, int k) {
+    Job* j = s->slot_job[k];
+    const uint32_t* info = s->status_host[k];
+    const uint32_t err = info[igs::kInfoErr];
+    s->pool.give(j->ws, j->ws_bytes);
+    s->slot_job[k] = nullptr;
+    if (j->batched) {
+        if (err == IGS_ERR_CAPACITY) {  // split: every request redone by itself, in its queue order
+            for (auto it = j->reqs.rbegin(); it != j->reqs.rend(); ++it) {
+                (*it)->solo = true;
+                (*it)->capacity = 0;
+                (*it)->t.retries += 1;
+                s->pending.push_front(*it);
+            }
+        } else {
+            for (size_t v = 0; v < j->reqs.size(); ++v)
+                finish(s, j->reqs[v], err ? 0u : info[4 + v], err, (int)j->reqs.size());
+        }
+        delete j;
+        return;
     }
+    Request* r = j->reqs[0];
+    delete j;
+    if (err == IGS_ERR_CAPACITY && (int64_t)info[igs::kInfoNeed] > r->capacity) {
+        // re-queue at the head with the entries the view reported (plus margin),
+        // unless that frame could never fit the pool: then this request fails alone
+        const int64_t need = std::min<int64_t>((int64_t)(info[igs::kInfoNeed] * 1.15) + 4096, (1 << 30) - 1);
+        const int64_t bytes = frame_bytes(s, r, need);
+        if (bytes >= 0 && (size_t)bytes <= s->pool.size()) {
+            r->capacity = need;
+            auto& h = s->cap_hint[{r->scene, r->cam.width, r->cam.height}];
+            h = std::max(h, need);
+            r->t.retries += 1;
+            s->pending.push_front(r);
+            return;
+        }
+    }
+    finish(s, r, info[igs::kInfoM], err, 1);
+}
+
+// The head request and, with grouping on, the other queued requests of its
+// scene among the first kGroupWindow (in queue order, at most max_group).
+std::vector<Request*> pick_group(igs_server* s) {
+    std::vector<Request*> g{s->pending.front()};
+    if (s->max_group < 2 || g[0]->solo) return g;
+    int seen = 0;
+    for (auto it = std::next(s->pending.begin()); it != s->pending.end() && seen < kGroupWindow &&
+                                                   (int)g.size() < s->max_group;
+         ++it, ++seen)
+        if ((*it)->scene == g[0]->scene && !(*it)->solo) g.push_back(*it);
+    return g;
 }
 
 void worker_main(igs_server* s) {
@@ -170,74 +300,64 @@ void worker_main(igs_server* s) {
         // completions
         bool progressed = false;
         for (int k = 0; k < s->max_slots; ++k) {
-            Request* r = s->slot_req[k];
-            if (!r || cudaEventQuery(s->events[k]) != cudaSuccess) continue;
-            const uint32_t* info = s->status_host[k];
-            const uint32_t err = info[igs::kInfoErr];
-            s->pool.give(r->ws, r->ws_bytes);
-            s->slot_req[k] = nullptr;
+            if (!s->slot_job[k] || cudaEventQuery(s->events[k]) != cudaSuccess) continue;
+            complete(s, k);
             progressed = true;
-            if (err == IGS_ERR_CAPACITY && (int64_t)info[igs::kInfoNeed] > r->capacity) {
-                // re-queue at the head with the entries the view reported (plus margin),
-                // unless that frame could never fit the pool: then this request fails alone
-                const int64_t need = std::min<int64_t>((int64_t)(info[igs::kInfoNeed] * 1.15) + 4096, (1 << 30) - 1);
-                const int64_t bytes = frame_bytes(s, r, need);
-                if (bytes >= 0 && (size_t)bytes <= s->pool.size()) {
-                    r->capacity = need;
-                    auto& h = s->cap_hint[{r->scene, r->cam.width, r->cam.height}];
-                    h = std::max(h, need);
-                    r->t.retries += 1;
-                    s->pending.push_front(r);
-                    continue;
-                }
-            }
-            r->t.done_ns = now_ns();
-            r->t.entries = info[igs::kInfoM];
-            r->t.status = (int32_t)err;
-            if (!err) {
-                auto& h = s->cap_hint[{r->scene, r->cam.width, r->cam.height}];
-                h = std::max<int64_t>(h, (int64_t)(info[igs::kInfoM] * 1.15) + 4096);
-            }
-            r->done = true;
         }
         if (progressed) s->cv_done.notify_all();
-        // admissions, in arrival order; a request that does not fit waits (no overtaking)
+        // admissions, in arrival order; a request that does not fit waits (no overtaking,
+        // except by the requests a group takes along)
         while (!s->pending.empty()) {
             int slot = -1;
             for (int k = 0; k < s->max_slots; ++k)
-                if (!s->slot_req[k]) {
+                if (!s->slot_job[k]) {
                     slot = k;
                     break;
                 }
             if (slot < 0) break;
-            Request* r = s->pending.front();
-            r->capacity = capacity_for(s, r);
-            const int64_t bytes = frame_bytes(s, r, r->capacity);
+            std::vector<Request*> g = pick_group(s);
+            int64_t cap_total = 0, gbytes = -1;
+            for (Request* q : g) {
+                q->capacity = capacity_for(s, q);
+                cap_total += q->capacity;
+            }
+            if (g.size() > 1 && cap_total < ((int64_t)1 << 30)) gbytes = group_bytes(s, g, cap_total);
+            if (gbytes < 0 || (size_t)gbytes > s->pool.size()) g.resize(1);  // alone, if the group cannot fit
+            Request* r = g[0];
+            const int64_t bytes = g.size() > 1 ? gbytes : frame_bytes(s, r, r->capacity);
             if (bytes < 0 || (size_t)bytes > s->pool.size()) {
                 s->pending.pop_front();
-                r->t.status = IGS_ERR_CAPACITY;
-                r->t.done_ns = now_ns();
-                r->done = true;
+                finish(s, r, 0u, IGS_ERR_CAPACITY, 1);
                 s->cv_done.notify_all();
                 continue;
             }
             char* ws = s->pool.take((size_t)bytes);
             if (!ws) break;  // wait for memory
-            s->pending.pop_front();
-            r->ws = ws;
-            r->ws_bytes = (size_t)bytes;
-            r->slot = slot;
-            s->slot_req[slot] = r;
-            r->t.admit_ns = now_ns();
+            for (Request* q : g) s->pending.erase(std::find(s->pending.begin(), s->pending.end(), q));
+            Job* j = new Job();
+            j->reqs = g;
+            j->batched = g.size() > 1;
+            j->ws = ws;
+            j->ws_bytes = (size_t)bytes;
+            s->slot_job[slot] = j;
+            const int64_t t_admit = now_ns();
             int64_t used = (int64_t)s->pool.used();
             if (used > s->admitted_bytes_peak) s->admitted_bytes_peak = used;
+            const SceneRec sc = s->scenes[r->scene];  // (a copy: add_scene may grow the table meanwhile)
             lk.unlock();
-            r->t.start_ns = now_ns();
-            launch(s, r);
+            const int64_t t_start = now_ns();
+            for (Request* q : g) {
+                q->t.admit_ns = t_admit;
+                q->t.start_ns = t_start;
+            }
+            if (j->batched)
+                launch_group(s, j, slot, cap_total, sc);
+            else
+                launch_single(s, j, slot, sc);
             lk.lock();
         }
         bool busy = false;
-        for (int k = 0; k < s->max_slots; ++k) busy |= s->slot_req[k] != nullptr;
+        for (int k = 0; k < s->max_slots; ++k) busy |= s->slot_job[k] != nullptr;
         if (s->stop && !busy && s->pending.empty()) break;
         if (busy)
             s->cv_work.wait_for(lk, std::chrono::microseconds(20));
@@ -267,17 +387,24 @@ igs_status igs_serve_create(void* pool, size_t pool_bytes, int32_t max_slots, co
     s->streams.resize(max_slots);
     s->events.resize(max_slots);
     s->status_host.resize(max_slots);
-    s->slot_req.assign(max_slots, nullptr);
+    s->slot_job.assign(max_slots, nullptr);
     for (int k = 0; k < max_slots; ++k) {
         if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->events[k], cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost(&s->status_host[k], 4 * sizeof(uint32_t)) != cudaSuccess) {
+            cudaMallocHost(&s->status_host[k], kStatusWords * sizeof(uint32_t)) != cudaSuccess) {
             igs_serve_destroy(s);
             return IGS_ERR_CUDA;
         }
     }
     s->worker = std::thread(worker_main, s);
     *out = s;
+    return IGS_OK;
+}
+
+igs_status igs_serve_set_grouping(igs_server* s, int32_t max_views) {
+    if (!s || max_views < 1 || max_views > kMaxGroup) return IGS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->max_group = max_views;
     return IGS_OK;
 }
 
@@ -353,7 +480,8 @@ igs_status igs_serve_stats(igs_server* s, int64_t* pending, int64_t* in_flight, 
     if (!s) return IGS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     int64_t busy = 0;
-    for (auto* r : s->slot_req) busy += r != nullptr;
+    for (auto* j : s->slot_job)
+        if (j) busy += (int64_t)j->reqs.size();
     if (pending) *pending = (int64_t)s->pending.size();
     if (in_flight) *in_flight = busy;
     if (pool_used) *pool_used = (int64_t)s->pool.used();

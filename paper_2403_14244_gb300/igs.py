@@ -79,7 +79,7 @@ class IgsBatch(C.Structure):
 
 class IgsTiming(C.Structure):
     _fields_ = [("arrival_ns", C.c_int64), ("admit_ns", C.c_int64), ("start_ns", C.c_int64), ("done_ns", C.c_int64),
-                ("entries", C.c_uint32), ("status", C.c_int32), ("retries", C.c_int32), ("_pad", C.c_int32)]
+                ("entries", C.c_uint32), ("status", C.c_int32), ("retries", C.c_int32), ("group", C.c_int32)]
 
 
 SYMBOLS = {
@@ -146,6 +146,7 @@ SYMBOLS = {
                                    C.c_void_p]),
     "igs_batch_status": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(C.c_uint32), C.c_void_p]),
     "igs_serve_create": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(IgsOpts), C.POINTER(C.c_void_p)]),
+    "igs_serve_set_grouping": (C.c_int, [C.c_void_p, C.c_int32]),
     "igs_serve_add_scene": (C.c_int, [C.c_void_p, C.POINTER(IgsScene), C.c_int32, C.c_int32,
                                       C.POINTER(C.c_int32)]),
     "igs_serve_submit": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(IgsCamera), C.c_void_p,
@@ -625,9 +626,11 @@ class Batch:
 
 class Server:
     """Render server (igs_serve_*): resident scenes, continuous batching over
-    `slots` streams, admission against a device pool of `pool_bytes`."""
+    `slots` streams, admission against a device pool of `pool_bytes`; with
+    group > 1, up to `group` queued requests of one scene share one batched
+    chain of launches."""
 
-    def __init__(self, pool_bytes, slots=4, tile=16, bg=(0.0, 0.0, 0.0), device="cuda"):
+    def __init__(self, pool_bytes, slots=4, tile=16, bg=(0.0, 0.0, 0.0), device="cuda", group=1):
         self.pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=device)
         base = self.pool.data_ptr()
         self.opts = opts(tile=tile, bg=bg)
@@ -636,6 +639,8 @@ class Server:
                                        C.byref(self.opts), C.byref(h)), "igs_serve_create")
         self.handle = h
         self.scenes = []
+        if group != 1:
+            _check(load().igs_serve_set_grouping(self.handle, int(group)), "igs_serve_set_grouping")
 
     def add_scene(self, scene: Scene, sh_degree=-1, param_mode=0):
         _check_color_width(scene, sh_degree, "Server.add_scene")
@@ -656,7 +661,7 @@ class Server:
         """(status, timing dict); status NOT_READY if still running after the timeout."""
         t = IgsTiming()
         st = load().igs_serve_poll(self.handle, C.c_uint64(req_id), int(timeout_s * 1e9), C.byref(t))
-        return st, {k: getattr(t, k) for k, _ in IgsTiming._fields_ if k != "_pad"}
+        return st, {k: getattr(t, k) for k, _ in IgsTiming._fields_}
 
     def stats(self):
         v = [C.c_int64() for _ in range(4)]

@@ -36,21 +36,48 @@ def _serve(srv, sids, reqs):
     return outs, timings
 
 
-@pytest.mark.parametrize("slots", [1, 4])
-def test_results_identical_alone_and_in_the_mix(slots):
+@pytest.mark.parametrize("slots,group,tile", [(1, 1, 16), (4, 1, 16), (1, 8, 16), (4, 8, 32), (2, 4, 8)])
+def test_results_identical_alone_and_in_the_mix(slots, group, tile):
+    """Every image served in a concurrent mix, with or without grouping of a
+    scene's waiting requests into one batched chain, equals the image of
+    rendering that request alone, bit for bit. With grouping on, groups form
+    once every (scene, size) has been seen (a second round of the same
+    requests) and the requests of one group report its size."""
     scs = [scenes.uniform_scene(150_000, 51), scenes.clustered_scene(100_000, 52, sh_degree=3)]
     devs = [_gpu.to_device(s) for s in scs]
-    srv = igs.Server(pool_bytes=3 << 30, slots=slots, tile=16)
+    srv = igs.Server(pool_bytes=3 << 30, slots=slots, tile=tile, group=group)
     sids = [srv.add_scene(d, sh_degree=s.sh_degree) for d, s in zip(devs, scs)]
     reqs = _requests(14, 53, len(scs))
+    _serve(srv, sids, reqs)                 # first round: the capacity of every (scene, size) becomes known
     outs, timings = _serve(srv, sids, reqs)
     stats = srv.stats()
     srv.close()
     assert stats["pool_peak"] <= 3 << 30
     for (s, cam), o, t in zip(reqs, outs, timings):
-        alone = _gpu.run_forward(scs[s], cam, tile=16)[3]
+        alone = _gpu.run_forward(scs[s], cam, tile=tile)[3]
         np.testing.assert_array_equal(o.cpu().numpy().astype(np.float64), alone)
         assert t["arrival_ns"] <= t["admit_ns"] <= t["start_ns"] <= t["done_ns"]
+        assert 1 <= t["group"] <= group
+    if group > 1:
+        assert max(t["group"] for t in timings) > 1
+
+
+def test_group_that_overflows_is_split_and_redone():
+    """A group sized from small views of a scene, then asked for larger ones,
+    overflows as a whole: its requests are redone one by one, each correct."""
+    sc = scenes.uniform_scene(60_000, 57)
+    sc.means_sigma[:, 3] *= 6.0
+    dev = _gpu.to_device(sc)
+    srv = igs.Server(pool_bytes=3 << 30, slots=1, tile=16, group=8)
+    sid = srv.add_scene(dev)
+    far = [scenes.pinhole((0.0, 0.0, -12.0 - 0.1 * k), 640, 360, 554.0) for k in range(6)]
+    near = [scenes.pinhole((0.0, 0.0, -2.2 - 0.01 * k), 640, 360, 554.0) for k in range(6)]
+    _serve(srv, [sid], [(0, c) for c in far])          # capacity hint from far (few entries per Gaussian)
+    outs, timings = _serve(srv, [sid], [(0, c) for c in near])
+    srv.close()
+    assert any(t["retries"] >= 1 for t in timings)
+    for cam, o in zip(near, outs):
+        np.testing.assert_array_equal(o.cpu().numpy().astype(np.float64), _gpu.run_forward(sc, cam, tile=16)[3])
 
 
 def test_overflow_is_requeued_with_the_needed_capacity():
