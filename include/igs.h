@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define IGS_ABI_VERSION 2
+#define IGS_ABI_VERSION 3
 
 #if defined(__GNUC__)
 #define IGS_API __attribute__((visibility("default")))
@@ -488,18 +488,20 @@ IGS_API igs_status igs_frame_reset_status(igs_frame* frame, void* stream);
 /* ---------------------------------------------------------------------------
  * Multi-view batch: V views of one scene, each with its own pose and image
  * size, rendered by one chain of launches with no host synchronisation: one
- * projection launch over every (view, Gaussian), per-view depth sorts in one
- * segmented launch per pass, one scan and one duplication over all views with
- * global tile ids, one tile-id sort, and one persistent blend whose CTAs take
- * (view, tile) work items from an atomic counter. The chain can be captured in
- * a CUDA graph once and replayed. Each view's image is bit-identical to
- * rendering it alone with igs_project / igs_bin_sort / igs_render_fwd.
+ * projection launch over every (view, Gaussian), each view's binning (depth
+ * sort and tile lists, as igs_bin_sort) on one of up to 8 streams that run
+ * concurrently, and one blend launch over the tiles of every view (the
+ * hardware block scheduler, or for the persistent variant an atomic work
+ * counter, balances views of different sizes). The chain can be captured in a
+ * CUDA graph once and replayed with new poses. Each view's image is
+ * bit-identical to rendering it alone with igs_project / igs_bin_sort /
+ * igs_render_fwd.
  * ------------------------------------------------------------------------- */
 #define IGS_MAX_VIEWS 256
 
 typedef struct igs_batch {
     int64_t n;                  /* Gaussians */
-    int64_t capacity;           /* (view, Gaussian, tile) entries over all views */
+    int64_t capacity;           /* (Gaussian, tile) entries over all views: the sum of view_capacity */
     int32_t views;              /* V, 1 .. IGS_MAX_VIEWS */
     int32_t tile;               /* 8, 16 or 32 */
     int32_t blend_batch;        /* entries staged per shared-memory batch in the blend */
@@ -507,49 +509,58 @@ typedef struct igs_batch {
     int64_t tiles_total;        /* tiles over all views */
     int64_t image_floats;       /* size of the packed image buffer: sum over views of 3 W H */
     int64_t image_offset[IGS_MAX_VIEWS];  /* first float of view v's [3][H][W] image */
-    uint32_t tile_base[IGS_MAX_VIEWS];    /* global id of view v's first tile */
+    uint32_t tile_base[IGS_MAX_VIEWS];    /* global id of view v's first tile (blend work items) */
     int32_t width[IGS_MAX_VIEWS], height[IGS_MAX_VIEWS];
-    float* rec;                 /* [V n][8] records of every (view, Gaussian), view-major */
-    uint32_t* rect;             /* [V n][2] */
-    float* disc;                /* [V n][4] */
-    uint32_t* count;            /* [V n] */
-    uint32_t* depth_key;        /* [V n] */
-    uint32_t* order;            /* [V n] record ids front to back, view after view */
-    uint32_t* offset;           /* [V n] */
-    uint32_t* vals;             /* [capacity] record id of each entry, sorted by global tile */
-    uint32_t* ranges;           /* [tiles_total][2] */
-    uint32_t* info;             /* [16] status words, as for a frame */
-    void* scratch;
-    size_t scratch_bytes;
+    int64_t view_capacity[IGS_MAX_VIEWS]; /* entries of view v's frame */
+    int64_t frame_offset[IGS_MAX_VIEWS];  /* byte offset of view v's frame in the workspace */
+    char* workspace;            /* the caller's buffer (device) */
+    uint32_t* info;             /* [16] status words of the batch: info[0] = entries of all views, info[2]
+                                   = the first error of a view, info[3] = entries all views need */
+    uint32_t* view_entries;     /* [V] entries of each view (device), after igs_render_batch */
+    void* table;                /* device view table (poses, frame pointers), written by igs_batch_set_views */
+    void* fanout;               /* library-owned host object: the streams the views' binnings fan out
+                                   to; made by igs_batch_set_views, freed by igs_batch_release */
 } igs_batch;
 
 /* Lay out a batch for n Gaussians and the V cameras' image sizes (the poses may
- * change later, the sizes may not). capacity = entries over all views;
+ * change later, the sizes may not). Each view gets a frame of its own (as from
+ * igs_frame_layout) with capacities[v] entries (host array of V);
  * blend_batch = entries per shared-memory batch of the blend: 32 or 64 for tile
  * 8, 64, 128 or 256 for tile 16, 64, 256, 512 or 1024 for tile 32 (0 = tile^2).
  * 64 with tile 16 or 32 selects the sub-tile blend: one 64-thread CTA per 8 x 8
  * pixel block, walking its tile's entries and stopping on its own (not
  * persistent); the others run the persistent whole-tile blend.
- * Requires V n < 2^32. workspace == NULL: only *bytes. Host-only, no launch. */
+ * workspace == NULL: only *bytes. Host-only, no launch. Laying out a batch
+ * struct again forgets its fan-out streams: igs_batch_release it first. */
 IGS_API igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, const igs_opts* opts,
-                                    int64_t capacity, int32_t blend_batch, void* workspace, size_t* bytes,
+                                    const int64_t* capacities, int32_t blend_batch, void* workspace, size_t* bytes,
                                     igs_batch* batch);
 
-/* Upload the V cameras (same sizes as at layout) to the batch's device view
- * table, asynchronously on `stream` (cams may be reused on return). Call it
- * before igs_render_batch whenever the poses change, outside any stream capture. */
+/* Upload the V cameras (same sizes as at layout) and the views' frame pointers
+ * to the batch's device view table, asynchronously on `stream` (cams may be
+ * reused on return). Call it before igs_render_batch whenever the poses
+ * change, outside any stream capture. The first call also makes the batch's
+ * fan-out streams (min(V, 8) CUDA streams and their events; no device memory). */
 IGS_API igs_status igs_batch_set_views(igs_batch* batch, const igs_camera* cams, const igs_opts* opts,
                                        void* stream);
 
 /* Render every view of the batch into `images` (device, batch->image_floats
- * floats; view v at image_offset[v], [3][H][W]). No host synchronisation, so
- * the call can be captured in a CUDA graph. An entry overflow sets info[2] to
- * IGS_ERR_CAPACITY (info[3] = entries needed) and leaves the images untouched. */
+ * floats; view v at image_offset[v], [3][H][W]): one projection launch for all
+ * views (poses read from the view table), then each view's binning (as
+ * igs_bin_sort) on one of the fan-out streams, joined back into `stream`, then
+ * one blend launch over every view's tiles. No host synchronisation, so the
+ * call can be captured in a CUDA graph (the fan-out streams join the capture).
+ * A view whose entries overflow its frame leaves its image untouched; info[2]
+ * = IGS_ERR_CAPACITY and info[3] = the entries the views need. */
 IGS_API igs_status igs_render_batch(igs_batch* batch, const igs_scene* scene, const igs_opts* opts, float* images,
                                     void* stream);
 
 /* Copy the batch's four status words to host_info and wait for `stream`. */
 IGS_API igs_status igs_batch_status(const igs_batch* batch, uint32_t* host_info, void* stream);
+
+/* Free the batch's fan-out streams and events (after its work has finished).
+ * The workspace is the caller's. Safe on a batch that never made them. */
+IGS_API void igs_batch_release(igs_batch* batch);
 
 /* ---------------------------------------------------------------------------
  * Render server with continuous batching. Scenes stay resident (the caller

@@ -2,9 +2,11 @@
 
 ``BatchRenderer`` renders many views of one scene (mixed image sizes) through
 igs_render_batch: views are packed into groups whose (view, Gaussian, tile)
-entries fit one batch workspace (the entry budget), each group is one chain of
-launches ending in one persistent blend, and the chain of every group is
-captured once in a CUDA graph and replayed for each new set of poses.
+entries fit one batch workspace (the entry budget), each view gets a frame
+sized from a calibrating render of it, each group is one chain of launches
+(one projection launch, the views' binnings on concurrent streams, one blend
+launch), and the chain of every group is captured once in a CUDA graph and
+replayed for each new set of poses.
 
 ``autotune`` times every supported (tile size, blend staging depth) pair on the
 caller's workload and caches the fastest, keyed by the workload's shape.
@@ -64,8 +66,8 @@ class BatchRenderer:
         self.groups = pack_groups([int(m * margin) + 65536 for m in ent], cap_budget)
         self.batches = []
         for g in self.groups:
-            cap = sum(int(ent[v] * margin) + 65536 for v in g)
-            b = igs.Batch(scene.n, [self.cams[v] for v in g], self.opts, cap, blend_batch, device)
+            caps = [int(ent[v] * margin) + 65536 for v in g]
+            b = igs.Batch(scene.n, [self.cams[v] for v in g], self.opts, caps, blend_batch, device)
             b.set_views()
             self.batches.append(b)
         self.graph = None

@@ -605,72 +605,73 @@ igs_status igs_adam(float* p, const float* g, float* m, float* v, int64_t count,
 
 // ------------------------------------------------------------------- batch --
 
-igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, const igs_opts* opts, int64_t capacity,
-                            int32_t blend_batch, void* workspace, size_t* bytes, igs_batch* batch) {
+// View v's frame inside a batch workspace (the layout igs_frame_layout gives a
+// view of that size with view_capacity[v] entries, at frame_offset[v]).
+static igs_status batch_frame(const igs_batch* b, const igs_opts* opts, int v, igs_frame* f) {
+    igs_camera cam;
+    std::memset(&cam, 0, sizeof cam);
+    cam.R[0] = cam.R[4] = cam.R[8] = 1.f;
+    cam.fx = cam.fy = 1.f;
+    cam.znear = 0.01f;
+    cam.width = b->width[v];
+    cam.height = b->height[v];
+    size_t bytes = 0;
+    return igs_frame_layout(b->n, b->view_capacity[v], &cam, opts, b->workspace + b->frame_offset[v], &bytes, f);
+}
+
+igs_status igs_batch_layout(int64_t n, int32_t views, const igs_camera* cams, const igs_opts* opts,
+                            const int64_t* capacities, int32_t blend_batch, void* workspace, size_t* bytes,
+                            igs_batch* batch) {
     igs_status st;
     if ((st = check_opts(opts))) return st;
-    if (!bytes || !cams) return fail(IGS_ERR_INVALID_ARG, "bytes or cams is NULL");
+    if (!bytes || !cams || !capacities) return fail(IGS_ERR_INVALID_ARG, "bytes, cams or capacities is NULL");
     if (views < 1 || views > IGS_MAX_VIEWS) return fail(IGS_ERR_INVALID_ARG, "views must be 1..%d", IGS_MAX_VIEWS);
-    if (n < 0 || n * views >= ((int64_t)1 << 32)) return fail(IGS_ERR_INVALID_ARG, "views * n must be < 2^32");
-    if (capacity < 0 || capacity >= ((int64_t)1 << 30)) return fail(IGS_ERR_INVALID_ARG, "capacity must be < 2^30");
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "n out of range");
     const int bb = blend_batch == 0 ? opts->tile * opts->tile : blend_batch;
     if (!igs::batch_blend_variant_ok(opts->tile, bb))
         return fail(IGS_ERR_INVALID_ARG, "unsupported blend batch %d for tile %d", bb, opts->tile);
     igs_batch b;
     std::memset(&b, 0, sizeof b);
     b.n = n;
-    b.capacity = capacity;
     b.views = views;
     b.tile = opts->tile;
     b.blend_batch = bb;
-    int64_t tiles = 0, floats = 0;
+    int64_t tiles = 0, floats = 0, cap = 0;
+    size_t off = align256(4 * ((size_t)igs::kBatchCtrlWords + (size_t)views));  // status, work counter, entries
+    const size_t o_table = off;
+    off += align256(igs::batch_table_bytes(views));
     for (int v = 0; v < views; ++v) {
         if ((st = check_camera(&cams[v]))) return st;
+        if (capacities[v] < 0 || capacities[v] >= ((int64_t)1 << 30))
+            return fail(IGS_ERR_INVALID_ARG, "view %d: capacity must be in [0, 2^30)", v);
         const int64_t tx = (cams[v].width + opts->tile - 1) / opts->tile, ty = (cams[v].height + opts->tile - 1) / opts->tile;
-        if (tx >= 65536 || ty >= 65536) return fail(IGS_ERR_INVALID_ARG, "too many tiles per axis");
         b.width[v] = cams[v].width;
         b.height[v] = cams[v].height;
         b.tile_base[v] = (uint32_t)tiles;
         b.image_offset[v] = floats;
+        b.view_capacity[v] = capacities[v];
         tiles += tx * ty;
         floats += 3 * (int64_t)cams[v].width * cams[v].height;
+        cap += capacities[v];
+        size_t fb = 0;
+        if ((st = igs_frame_layout(n, capacities[v], &cams[v], opts, nullptr, &fb, nullptr))) return st;
+        b.frame_offset[v] = (int64_t)off;
+        off += align256(fb);
     }
     if (tiles >= ((int64_t)1 << 31)) return fail(IGS_ERR_INVALID_ARG, "too many tiles");
     b.tiles_total = tiles;
     b.image_floats = floats;
-    const int64_t Vn = n * views;
-    size_t off = 0;
-    const size_t o_rec = off; off += align256((size_t)Vn * 32);
-    const size_t o_rect = off; off += align256((size_t)Vn * 8);
-    const size_t o_disc = off; off += align256((size_t)Vn * 16);
-    const size_t o_count = off; off += align256((size_t)Vn * 4);
-    const size_t o_dkey = off; off += align256((size_t)Vn * 4);
-    const size_t o_order = off; off += align256((size_t)Vn * 4);
-    const size_t o_offset = off; off += align256((size_t)Vn * 4);
-    const size_t o_vals = off; off += align256((size_t)capacity * 4);
-    const size_t o_ranges = off; off += align256((size_t)tiles * 8);
-    const size_t o_info = off; off += align256(igs::kInfoWords * 4);
-    const size_t o_scr = off;
-    const size_t scr = igs::batch_scratch_bytes(b);
-    off += align256(scr);
+    b.capacity = cap;
     *bytes = off;
     if (!workspace) return IGS_OK;
     if (!batch) return fail(IGS_ERR_INVALID_ARG, "batch is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return fail(IGS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     char* w = static_cast<char*>(workspace);
-    b.rec = reinterpret_cast<float*>(w + o_rec);
-    b.rect = reinterpret_cast<uint32_t*>(w + o_rect);
-    b.disc = reinterpret_cast<float*>(w + o_disc);
-    b.count = reinterpret_cast<uint32_t*>(w + o_count);
-    b.depth_key = reinterpret_cast<uint32_t*>(w + o_dkey);
-    b.order = reinterpret_cast<uint32_t*>(w + o_order);
-    b.offset = reinterpret_cast<uint32_t*>(w + o_offset);
-    b.vals = reinterpret_cast<uint32_t*>(w + o_vals);
-    b.ranges = reinterpret_cast<uint32_t*>(w + o_ranges);
-    b.info = reinterpret_cast<uint32_t*>(w + o_info);
-    b.scratch = w + o_scr;
-    b.scratch_bytes = scr;
-    *batch = b;
+    b.workspace = w;
+    b.info = reinterpret_cast<uint32_t*>(w);
+    b.view_entries = b.info + igs::kBatchCtrlWords;
+    b.table = w + o_table;
+    *batch = b;  // (no fan-out streams yet: igs_batch_set_views makes them)
     return IGS_OK;
 }
 
@@ -684,21 +685,30 @@ igs_status igs_batch_set_views(igs_batch* batch, const igs_camera* cams, const i
         if ((st = check_camera(&cams[v]))) return st;
         if (cams[v].width != batch->width[v] || cams[v].height != batch->height[v])
             return fail(IGS_ERR_INVALID_ARG, "view %d: image size differs from the layout", v);
-        host[v].vp = view_params(&cams[v], opts, nullptr);
-        host[v].tile_base = batch->tile_base[v];
-        host[v].img_off = batch->image_offset[v];
+        igs_frame f;
+        if ((st = batch_frame(batch, opts, v, &f))) return st;
+        igs::BatchView& h = host[v];
+        std::memset(&h, 0, sizeof h);
+        h.vp = view_params(&cams[v], opts, &f);
+        h.tile_base = batch->tile_base[v];
+        h.img_off = batch->image_offset[v];
+        h.rec = reinterpret_cast<float4*>(f.rec);
+        h.rect = reinterpret_cast<uint2*>(f.rect);
+        h.disc = reinterpret_cast<float4*>(f.disc);
+        h.count = f.count;
+        h.depth_key = f.depth_key;
+        h.ranges = reinterpret_cast<const uint2*>(f.ranges);
+        h.vals = f.vals;
+        h.info = f.info;
     }
-    uint32_t goff = 0;
-    for (int v = 0; v < batch->views; ++v) {
-        host[v].grid_off = goff;
-        goff += (uint32_t)((host[v].vp.tiles_x + 1) * (host[v].vp.tiles_y + 1));
-    }
-    cudaError_t e = igs::batch_prepare_kernels(*batch);
-    if (e != cudaSuccess) return cuda_status(e, "igs_batch_set_views");
+    cudaError_t e = igs::batch_fanout_make(*batch);
+    if (e != cudaSuccess) return cuda_status(e, "igs_batch_set_views (fan-out streams)");
     const int pb = igs::batch_persistent_blocks(batch->tile, batch->blend_batch);
     if (pb <= 0) return fail(IGS_ERR_CUDA, "could not size the persistent blend");
     batch->persistent_blocks = pb;
-    return cuda_status(igs::batch_set_views(*batch, host, (cudaStream_t)stream), "igs_batch_set_views");
+    return cuda_status(cudaMemcpyAsync(batch->table, host, sizeof(igs::BatchView) * batch->views,
+                                       cudaMemcpyHostToDevice, (cudaStream_t)stream),
+                       "igs_batch_set_views");
 }
 
 igs_status igs_render_batch(igs_batch* batch, const igs_scene* scene, const igs_opts* opts, float* images,
@@ -709,14 +719,21 @@ igs_status igs_render_batch(igs_batch* batch, const igs_scene* scene, const igs_
     if (scene->n != batch->n) return fail(IGS_ERR_INVALID_ARG, "batch laid out for another n");
     if (opts->tile != batch->tile) return fail(IGS_ERR_INVALID_ARG, "batch laid out for another tile size");
     if (!images) return fail(IGS_ERR_INVALID_ARG, "images is NULL");
-    if (batch->persistent_blocks <= 0) return fail(IGS_ERR_INVALID_ARG, "call igs_batch_set_views first");
+    if (batch->persistent_blocks <= 0 || !batch->fanout) return fail(IGS_ERR_INVALID_ARG, "call igs_batch_set_views first");
+    static thread_local igs_frame frames[IGS_MAX_VIEWS];
+    for (int v = 0; v < batch->views; ++v)
+        if ((st = batch_frame(batch, opts, v, &frames[v]))) return st;
     igs::BlendParams bp;
     bp.width = bp.height = bp.tiles_x = bp.tiles_y = 0;
     bp.alpha_min = opts->alpha_min; bp.alpha_max = opts->alpha_max; bp.t_min = opts->t_min;
     for (int i = 0; i < 3; ++i) bp.bg[i] = opts->bg[i];
-    return cuda_status(igs::launch_render_batch(*batch, *scene, bp, opts->sh_degree, images, (cudaStream_t)stream,
-                                                opts->footprint),
+    return cuda_status(igs::launch_render_batch(*batch, frames, *scene, bp, opts->sh_degree, images,
+                                                (cudaStream_t)stream, opts->footprint),
                        "igs_render_batch");
+}
+
+void igs_batch_release(igs_batch* batch) {
+    if (batch) igs::batch_fanout_free(*batch);
 }
 
 igs_status igs_batch_status(const igs_batch* batch, uint32_t* host_info, void* stream) {

@@ -1,5 +1,5 @@
-// Radix-sort, scan and duplication kernels shared by the one-view path
-// (sort.cu) and the multi-view batch path (batch.cu). Internal to libigs.
+// Radix-sort, scan and duplication kernels of the binning (sort.cu) and the
+// allocation-free ordering. Internal to libigs.
 //
 // Each radix pass is a single sweep over (key | value) items: a block counts
 // the digits of its 5120 items and publishes those counts at once, ranks the
@@ -395,9 +395,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* _
 // search of the block's window of offsets, then its tile among the tiles the
 // Gaussian touches (row by row of its rectangle, row_span in each row). Writes (tile id << 32 | Gaussian id), or only the
 // Gaussian id when no tile pass follows.
-// Batched (several views): Gaussian ids are record indices v * view_len + g,
-// and view v's tile ids start at view_tile_base[v] with view_tiles_x[v] per row.
-template <bool BATCHED>
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ offset,
                                                    const uint32_t* __restrict__ dup_start,
@@ -405,9 +402,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                                                    const float4* __restrict__ disc, int tile, int footprint,
                                                    uint32_t n, int tiles_x,
                                                    u64* __restrict__ items, uint32_t* __restrict__ vals_direct,
-                                                   const uint32_t* __restrict__ info, uint32_t view_len,
-                                                   const int32_t* __restrict__ view_tiles_x,
-                                                   const uint32_t* __restrict__ view_tile_base) {
+                                                   const uint32_t* __restrict__ info) {
     __shared__ uint32_t s_off[kDupTile + 2];
     __shared__ uint32_t s_ord[kDupTile + 1];
     __shared__ u64 s_items[kDupTile];  // the block's entries, written out coalesced at the end
@@ -422,9 +417,9 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
     for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) s_ord[k] = order[pb + k];
     __syncthreads();
     const uint32_t e_end = (uint32_t)(e0 + kDupTile < (uint64_t)M ? e0 + kDupTile : (uint64_t)M);
-    // Entries at or past `reach` belong to Gaussians after the window: that only
-    // happens when culled Gaussians (no entries) sit inside the order, i.e. at the
-    // end of each view of a batch; those entries search the global offsets.
+    // Entries at or past `reach` belong to Gaussians after the window (when
+    // Gaussians without entries sit inside it); those entries search the
+    // global offsets.
     const uint32_t reach = s_off[cnt];
     // each thread: kDupPerThread consecutive entries, one search then a walk
     const uint32_t first = min((uint32_t)e0 + threadIdx.x * kDupPerThread, e_end);
@@ -471,19 +466,10 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
                 j -= w;
                 sp = tile_span(footprint, r, disc, g, tile, inv, ++ty);
             }
-            uint32_t tpr, base;  // tiles per row and first tile id of the view
-            if (BATCHED) {
-                const uint32_t v = g / view_len;
-                tpr = (uint32_t)view_tiles_x[v];
-                base = view_tile_base[v];
-            } else {
-                tpr = (uint32_t)tiles_x;
-                base = 0;
-            }
             int col = sp.x + (int)j;
             for (; e < stop; ++e) {
                 if (col > sp.y) break;  // never: the count is the total of the spans
-                const uint32_t t = base + (uint32_t)ty * tpr + (uint32_t)col;
+                const uint32_t t = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)col;
                 s_items[e - (uint32_t)e0] = ((u64)t << 32) | g;
                 // next touched tile, row by row
                 if (++col > sp.y) {

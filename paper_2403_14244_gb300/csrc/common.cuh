@@ -232,23 +232,32 @@ cudaError_t launch_octree_init(const float* pts, const float* cols, long long np
                                int L, long long k_max, float opacity, int sh_degree, int param_mode, float* out_ms,
                                float* out_op, float* out_col, int32_t* count, void* work, cudaStream_t s);
 
-// Multi-view batch (batch.cu): per-view record in device memory (the view table).
+// Multi-view batch (batch.cu): per-view record in device memory (the view table):
+// the pose, where the view's tiles and image sit in the batch, and its frame.
 struct BatchView {
     ViewParams vp;
-    uint32_t tile_base;  // global id of the view's first tile
-    uint32_t grid_off;   // first cell of the view's corner grid
+    uint32_t tile_base;  // global id of the view's first tile (blend work items)
+    uint32_t pad;
     int64_t img_off;     // first float of the view's image in the packed buffer
+    float4* rec;         // the view's frame: projection outputs ...
+    uint2* rect;
+    float4* disc;
+    uint32_t* count;
+    uint32_t* depth_key;
+    const uint2* ranges;  // ... and the binning's
+    const uint32_t* vals;
+    const uint32_t* info;
 };
-int64_t batch_grid_cells(const igs_batch& b);
-size_t batch_scratch_bytes(const igs_batch& b);
+// Control words of a batch (igs_batch::info points at them): [16] status, [16] work counter, [V] entries.
+constexpr int kBatchCtrlWords = 32;
+size_t batch_table_bytes(int views);
 bool batch_blend_variant_ok(int tile, int batch);
-cudaError_t batch_set_views(const igs_batch& b, const BatchView* host_views, cudaStream_t st);
-cudaError_t batch_prepare_kernels(const igs_batch& b);
-cudaError_t launch_render_batch(const igs_batch& b, const igs_scene& sc, const BlendParams& bp, int sh_degree,
-                                float* images, cudaStream_t st, int footprint);
 int batch_persistent_blocks(int tile, int batch);
-// Device address of the per-view entry totals of a rendered batch ([views] words).
-const uint32_t* batch_view_totals(const igs_batch& b);
+// Fan-out streams of a batch (igs_batch::fanout), made once outside any capture.
+cudaError_t batch_fanout_make(igs_batch& b);
+void batch_fanout_free(igs_batch& b);
+cudaError_t launch_render_batch(const igs_batch& b, const igs_frame* frames, const igs_scene& sc,
+                                const BlendParams& bp, int sh_degree, float* images, cudaStream_t st, int footprint);
 
 // Scratch layout of a frame (pieces of igs_frame::scratch).
 struct SortScratch {

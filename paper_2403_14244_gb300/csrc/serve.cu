@@ -130,6 +130,7 @@ struct igs_server {
     std::vector<cudaEvent_t> events;
     std::vector<uint32_t*> status_host;  // pinned, kStatusWords per slot
     std::vector<Job*> slot_job;
+    std::vector<void*> slot_fanout;  // per slot: the fan-out streams of its batched groups
     int max_group = 1;
     std::vector<SceneRec> scenes;
     std::map<std::tuple<int, int, int>, int64_t> cap_hint;  // (scene, W, H) -> entries
@@ -160,17 +161,20 @@ int64_t capacity_for(igs_server* s, const Request* r) {
     return std::min<int64_t>(c, (1 << 30) - 1);
 }
 
-// Pool bytes of a group's batch workspace plus its packed images; -1 if it cannot be laid out.
-int64_t group_bytes(const igs_server* s, const std::vector<Request*>& g, int64_t capacity) {
+// Pool bytes of a group's batch workspace plus its packed images (each view
+// with its request's capacity); -1 if it cannot be laid out.
+int64_t group_bytes(const igs_server* s, const std::vector<Request*>& g) {
     const SceneRec& sc = s->scenes[g[0]->scene];
     igs_camera cams[kMaxGroup];
+    int64_t caps[kMaxGroup];
     int64_t floats = 0;
     for (size_t v = 0; v < g.size(); ++v) {
         cams[v] = g[v]->cam;
+        caps[v] = g[v]->capacity;
         floats += 3 * (int64_t)g[v]->cam.width * g[v]->cam.height;
     }
     size_t bytes = 0;
-    if (igs_batch_layout(sc.scene.n, (int32_t)g.size(), cams, &sc.opts, capacity, kBlendBatch, nullptr, &bytes,
+    if (igs_batch_layout(sc.scene.n, (int32_t)g.size(), cams, &sc.opts, caps, kBlendBatch, nullptr, &bytes,
                          nullptr) != IGS_OK)
         return -1;
     return (int64_t)(al(bytes) + al((size_t)floats * 4));
@@ -201,15 +205,21 @@ void launch_single(igs_server* s, Job* j, int slot, const SceneRec& sc) {
 
 // Launch one admitted group: one batched chain, then each view's image to its
 // request's output, the batch status and the per-view entry totals to the host.
-void launch_group(igs_server* s, Job* j, int slot, int64_t capacity, const SceneRec& sc) {
+void launch_group(igs_server* s, Job* j, int slot, const SceneRec& sc) {
     cudaStream_t st = s->streams[slot];
     const int V = (int)j->reqs.size();
     igs_camera cams[kMaxGroup];
-    for (int v = 0; v < V; ++v) cams[v] = j->reqs[v]->cam;
+    int64_t caps[kMaxGroup];
+    for (int v = 0; v < V; ++v) {
+        cams[v] = j->reqs[v]->cam;
+        caps[v] = j->reqs[v]->capacity;
+    }
     size_t bytes = 0;
-    igs_status e = igs_batch_layout(sc.scene.n, V, cams, &sc.opts, capacity, kBlendBatch, j->ws, &bytes, &j->batch);
+    igs_status e = igs_batch_layout(sc.scene.n, V, cams, &sc.opts, caps, kBlendBatch, j->ws, &bytes, &j->batch);
     float* images = reinterpret_cast<float*>(j->ws + al(bytes));
+    j->batch.fanout = s->slot_fanout[slot];  // the slot's fan-out streams, made once
     if (e == IGS_OK) e = igs_batch_set_views(&j->batch, cams, &sc.opts, st);
+    s->slot_fanout[slot] = j->batch.fanout;
     if (e == IGS_OK) e = igs_render_batch(&j->batch, &sc.scene, &sc.opts, images, st);
     for (int v = 0; v < V && e == IGS_OK; ++v)
         if (cudaMemcpyAsync(j->reqs[v]->img, images + j->batch.image_offset[v],
@@ -218,7 +228,7 @@ void launch_group(igs_server* s, Job* j, int slot, int64_t capacity, const Scene
     if (e == IGS_OK &&
         (cudaMemcpyAsync(s->status_host[slot], j->batch.info, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st) !=
              cudaSuccess ||
-         cudaMemcpyAsync(s->status_host[slot] + 4, igs::batch_view_totals(j->batch), (size_t)V * 4,
+         cudaMemcpyAsync(s->status_host[slot] + 4, j->batch.view_entries, (size_t)V * 4,
                          cudaMemcpyDeviceToHost, st) != cudaSuccess))
         e = IGS_ERR_CUDA;
     if (e == IGS_OK && cudaEventRecord(s->events[slot], st) != cudaSuccess) e = IGS_ERR_CUDA;
@@ -316,12 +326,9 @@ void worker_main(igs_server* s) {
                 }
             if (slot < 0) break;
             std::vector<Request*> g = pick_group(s);
-            int64_t cap_total = 0, gbytes = -1;
-            for (Request* q : g) {
-                q->capacity = capacity_for(s, q);
-                cap_total += q->capacity;
-            }
-            if (g.size() > 1 && cap_total < ((int64_t)1 << 30)) gbytes = group_bytes(s, g, cap_total);
+            int64_t gbytes = -1;
+            for (Request* q : g) q->capacity = capacity_for(s, q);
+            if (g.size() > 1) gbytes = group_bytes(s, g);
             if (gbytes < 0 || (size_t)gbytes > s->pool.size()) g.resize(1);  // alone, if the group cannot fit
             Request* r = g[0];
             const int64_t bytes = g.size() > 1 ? gbytes : frame_bytes(s, r, r->capacity);
@@ -351,7 +358,7 @@ void worker_main(igs_server* s) {
                 q->t.start_ns = t_start;
             }
             if (j->batched)
-                launch_group(s, j, slot, cap_total, sc);
+                launch_group(s, j, slot, sc);
             else
                 launch_single(s, j, slot, sc);
             lk.lock();
@@ -388,6 +395,7 @@ igs_status igs_serve_create(void* pool, size_t pool_bytes, int32_t max_slots, co
     s->events.resize(max_slots);
     s->status_host.resize(max_slots);
     s->slot_job.assign(max_slots, nullptr);
+    s->slot_fanout.assign(max_slots, nullptr);
     for (int k = 0; k < max_slots; ++k) {
         if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->events[k], cudaEventDisableTiming) != cudaSuccess ||
@@ -502,6 +510,12 @@ void igs_serve_destroy(igs_server* s) {
         if (s->streams[k]) cudaStreamDestroy(s->streams[k]);
         if (s->events[k]) cudaEventDestroy(s->events[k]);
         if (s->status_host[k]) cudaFreeHost(s->status_host[k]);
+        if (k < (int)s->slot_fanout.size() && s->slot_fanout[k]) {
+            igs_batch b;
+            std::memset(&b, 0, sizeof b);
+            b.fanout = s->slot_fanout[k];
+            igs_batch_release(&b);
+        }
     }
     for (auto& kv : s->all) delete kv.second;
     delete s;

@@ -1017,11 +1017,9 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
     CK(cudaGetLastError());
     // 3b. duplication, in depth order, by output position
     const unsigned dup_blocks = (unsigned)std::max<int64_t>(1, ceil_div(cap, kDupTile));
-    k_duplicate<false><<<dup_blocks, 256, 0, st>>>(f.order, f.offset, s.dup_start,
-                                                   reinterpret_cast<const uint2*>(f.rect),
-                                                   reinterpret_cast<const float4*>(f.disc), f.tile, footprint, nn,
-                                                   f.tiles_x, s.items_a,
-                                                   tp == 0 ? f.vals : nullptr, f.info, nn, nullptr, nullptr);
+    k_duplicate<<<dup_blocks, 256, 0, st>>>(f.order, f.offset, s.dup_start, reinterpret_cast<const uint2*>(f.rect),
+                                            reinterpret_cast<const float4*>(f.disc), f.tile, footprint, nn, f.tiles_x,
+                                            s.items_a, tp == 0 ? f.vals : nullptr, f.info);
     count_launches();
     CK(cudaGetLastError());
     // 4b. stable tile-id sort of the M items (M read on the device; grid sized by capacity)

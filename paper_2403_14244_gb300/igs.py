@@ -19,7 +19,7 @@ import torch
 
 from . import _build
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 _lock = threading.Lock()
 _lib = None
 
@@ -71,10 +71,9 @@ class IgsBatch(C.Structure):
                 ("blend_batch", C.c_int32), ("persistent_blocks", C.c_int32), ("tiles_total", C.c_int64),
                 ("image_floats", C.c_int64), ("image_offset", C.c_int64 * MAX_VIEWS),
                 ("tile_base", C.c_uint32 * MAX_VIEWS), ("width", C.c_int32 * MAX_VIEWS),
-                ("height", C.c_int32 * MAX_VIEWS), ("rec", C.c_void_p), ("rect", C.c_void_p), ("disc", C.c_void_p),
-                ("count", C.c_void_p),
-                ("depth_key", C.c_void_p), ("order", C.c_void_p), ("offset", C.c_void_p), ("vals", C.c_void_p),
-                ("ranges", C.c_void_p), ("info", C.c_void_p), ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t)]
+                ("height", C.c_int32 * MAX_VIEWS), ("view_capacity", C.c_int64 * MAX_VIEWS),
+                ("frame_offset", C.c_int64 * MAX_VIEWS), ("workspace", C.c_void_p), ("info", C.c_void_p),
+                ("view_entries", C.c_void_p), ("table", C.c_void_p), ("fanout", C.c_void_p)]
 
 
 class IgsTiming(C.Structure):
@@ -139,8 +138,10 @@ SYMBOLS = {
     "igs_frame_reset_status": (C.c_int, [C.POINTER(IgsFrame), C.c_void_p]),
     "igs_debug_silence_lookback_once": (None, []),
     "igs_sort_depth_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
-    "igs_batch_layout": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.c_int64,
-                                   C.c_int32, C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(IgsBatch)]),
+    "igs_batch_layout": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(IgsCamera), C.POINTER(IgsOpts),
+                                   C.POINTER(C.c_int64), C.c_int32, C.c_void_p, C.POINTER(C.c_size_t),
+                                   C.POINTER(IgsBatch)]),
+    "igs_batch_release": (None, [C.POINTER(IgsBatch)]),
     "igs_batch_set_views": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.c_void_p]),
     "igs_render_batch": (C.c_int, [C.POINTER(IgsBatch), C.POINTER(IgsScene), C.POINTER(IgsOpts), C.c_void_p,
                                    C.c_void_p]),
@@ -579,25 +580,32 @@ def sort_depth_noalloc(depth_key, order, stream=None):
 
 
 class Batch:
-    """One multi-view batch: workspace from igs_batch_layout and the packed image buffer."""
+    """One multi-view batch: workspace from igs_batch_layout (a frame per view,
+    `capacity` entries each: one number for every view, or one per view) and
+    the packed image buffer."""
 
     def __init__(self, n, cams, o, capacity, blend_batch=0, device="cuda"):
         lib = load()
         self.cams = [c if isinstance(c, IgsCamera) else camera(c) for c in cams]
         self.opts = o
-        arr = (IgsCamera * len(self.cams))(*self.cams)
+        V = len(self.cams)
+        caps = [int(capacity)] * V if isinstance(capacity, int) else [int(c) for c in capacity]
+        if len(caps) != V:
+            raise ValueError("Batch: one capacity per view")
+        arr = (IgsCamera * V)(*self.cams)
+        carr = (C.c_int64 * V)(*caps)
         nbytes = C.c_size_t(0)
-        _check(lib.igs_batch_layout(int(n), len(self.cams), arr, C.byref(o), int(capacity), int(blend_batch), None,
-                                    C.byref(nbytes), None), "igs_batch_layout")
+        _check(lib.igs_batch_layout(int(n), V, arr, C.byref(o), carr, int(blend_batch), None, C.byref(nbytes), None),
+               "igs_batch_layout")
         self.nbytes = int(nbytes.value)
         self.ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
         base = self.ws.data_ptr()
         self.struct = IgsBatch()
-        _check(lib.igs_batch_layout(int(n), len(self.cams), arr, C.byref(o), int(capacity), int(blend_batch),
+        _check(lib.igs_batch_layout(int(n), V, arr, C.byref(o), carr, int(blend_batch),
                                     C.c_void_p(base + (-base) % 256), C.byref(nbytes), C.byref(self.struct)),
                "igs_batch_layout")
         self.images = torch.empty(int(self.struct.image_floats), dtype=torch.float32, device=device)
-        self.n, self.capacity = int(n), int(capacity)
+        self.n, self.capacities, self.capacity = int(n), caps, sum(caps)
 
     def set_views(self, cams=None, stream=None):
         if cams is not None:
@@ -622,6 +630,24 @@ class Batch:
         off = int(self.struct.image_offset[v])
         h, w = int(self.struct.height[v]), int(self.struct.width[v])
         return self.images[off:off + 3 * h * w].view(3, h, w)
+
+    def view_entries(self):
+        """Entries of each view in the last render (device int32 [V] view)."""
+        V = int(self.struct.views)
+        off = int(self.struct.view_entries) - self.ws.data_ptr()
+        return self.ws[off:off + 4 * V].view(torch.int32)
+
+    def release(self):
+        """Free the fan-out streams (after the batch's work has finished)."""
+        if getattr(self, "struct", None) is not None and self.struct.fanout:
+            torch.cuda.synchronize(self.ws.device)
+            load().igs_batch_release(C.byref(self.struct))
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
 
 class Server:
