@@ -54,8 +54,8 @@ constexpr int kGridSmemCells = 10240;
 // Gaussian, in each tile row, +1 at its first touched tile and -1 past its last
 // in the (tiles_y+1) x (tiles_x+1) grid (a prefix sum along each row then gives
 // the entries of every tile). Each thread has kPrepUnroll Gaussians in flight;
-// the two top bytes of a view's depths take few values, so a warp adds their
-// counts once per distinct digit (match.any) instead of once per lane.
+// the top byte of a view's depths is mostly one value, so a warp whose lanes
+// share it adds its count once instead of 32 times to one shared-memory word.
 constexpr int kPrepUnroll = 4;
 template <bool SMEM_GRID>
 __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ depth_key, const uint2* __restrict__ rect,
@@ -99,11 +99,15 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
                 atomicAdd(&s_h[0][k & 0xFF], 1u);
                 atomicAdd(&s_h[1][(k >> 8) & 0xFF], 1u);
             }
-#pragma unroll
-            for (int p = 2; p < 4; ++p) {
-                const uint32_t d = (k >> (8 * p)) & 0xFF;
-                const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u + lane);
-                if (ok && lane == __ffs(peers) - 1) atomicAdd(&s_h[p][d], __popc(peers));
+            if (ok) atomicAdd(&s_h[2][(k >> 16) & 0xFF], 1u);
+            {  // the top byte: one count per warp when all its lanes share it (a view's depths do)
+                const uint32_t d3 = k >> 24, okm = __ballot_sync(0xffffffffu, ok);
+                const uint32_t lead = __shfl_sync(0xffffffffu, d3, okm ? __ffs(okm) - 1 : 0);
+                if (__all_sync(0xffffffffu, !ok || d3 == lead)) {
+                    if (okm && lane == __ffs(okm) - 1) atomicAdd(&s_h[3][lead], (uint32_t)__popc(okm));
+                } else if (ok) {
+                    atomicAdd(&s_h[3][d3], 1u);
+                }
             }
             wrap |= ok && k != 0xFFFFFFFFu && ((k & 0xFFFFFFu) == 0xFFFFFFu || (k >> 24) == 0xFFu);
             if (cnt[u]) {
@@ -279,7 +283,7 @@ constexpr uint32_t kL1ChunksMin = 1024;
 constexpr uint32_t kH1Words = 1u << 22;    // H1 budget: rows x chunks
 constexpr uint32_t kStage = 1536;          // staged entries per level-2 chunk
 constexpr uint32_t kChunkTarget = kStage * 4 / 5;
-constexpr uint32_t kStage1 = 1024;         // staged 8-byte items per level-1 chunk
+constexpr uint32_t kStage1 = 768;          // staged 8-byte items per level-1 chunk
 constexpr uint32_t kChunkTarget1 = kStage1 * 4 / 5;
 constexpr int kWalkWarps = 4;              // warps per CTA of the walk kernels (one chunk each)
 constexpr int kWalkUnroll = 4;             // items per lane per round of the counting walks
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* 
 // kChunkTarget entries: kChunkTarget * items / entries of the row items, at
 // least 32. Records an error if the chunks exceed `max_chunks`. One block of NT
 // threads; len is read through L2 (other blocks wrote it).
-constexpr int kRowScanThreads = 256;
+constexpr int kRowScanThreads = 1024;
 template <int NT>
 __device__ __forceinline__ void row_layout(const uint32_t* __restrict__ len, const uint2* __restrict__ ranges,
                                            uint32_t rows, uint32_t tiles_x, uint32_t max_chunks,
