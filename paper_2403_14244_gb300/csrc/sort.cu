@@ -53,7 +53,9 @@ constexpr int kGridSmemCells = 10240;
 // Depth-digit histograms of all n depth keys, the kept count, and for every kept
 // Gaussian, in each tile row, +1 at its first touched tile and -1 past its last
 // in the (tiles_y+1) x (tiles_x+1) grid (a prefix sum along each row then gives
-// the entries of every tile). Each thread has kPrepUnroll Gaussians in flight;
+// the entries of every tile); with rectangle footprints on the shared-memory
+// grid, +1/-1 at the rectangle's four corners instead (a prefix down each
+// column, then along each row). Each thread has kPrepUnroll Gaussians in flight;
 // the top byte of a view's depths is mostly one value, so a warp whose lanes
 // share it adds its count once instead of 32 times to one shared-memory word.
 constexpr int kPrepUnroll = 4;
@@ -113,11 +115,19 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
             if (cnt[u]) {
                 ++kept;
                 const int y0 = r[u].x >> 16, y1 = r[u].y >> 16;
-                for (int ty = y0; ty <= y1; ++ty) {  // +1 at the row's first touched tile, -1 past its last
-                    const int2 sp = tile_span(footprint, r[u], disc, i, tile, inv, ty);
-                    if (sp.y < sp.x) continue;
-                    atomicAdd(&g[ty * gx + sp.x], 1);
-                    atomicAdd(&g[ty * gx + sp.y + 1], -1);
+                if (SMEM_GRID && footprint == 0) {  // the rectangle's four corners (a 2D difference)
+                    const int x0 = r[u].x & 0xFFFF, x1 = r[u].y & 0xFFFF;
+                    atomicAdd(&g[y0 * gx + x0], 1);
+                    atomicAdd(&g[y0 * gx + x1 + 1], -1);
+                    atomicAdd(&g[(y1 + 1) * gx + x0], -1);
+                    atomicAdd(&g[(y1 + 1) * gx + x1 + 1], 1);
+                } else {
+                    for (int ty = y0; ty <= y1; ++ty) {  // +1 at the row's first touched tile, -1 past its last
+                        const int2 sp = tile_span(footprint, r[u], disc, i, tile, inv, ty);
+                        if (sp.y < sp.x) continue;
+                        atomicAdd(&g[ty * gx + sp.x], 1);
+                        atomicAdd(&g[ty * gx + sp.y + 1], -1);
+                    }
                 }
             }
         }
@@ -205,7 +215,7 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* _
 // histogram (4 depth + `passes` tile rows) turned into exclusive offsets.
 constexpr int kTilesSmallThreads = 1024;
 __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_t* __restrict__ grid, int tiles_x,
-                                                                    int tiles_y, int passes,
+                                                                    int tiles_y, int passes, int diff2d,
                                                                     uint2* __restrict__ ranges,
                                                                     uint32_t* __restrict__ hist,
                                                                     uint32_t* __restrict__ info, uint64_t capacity) {
@@ -226,6 +236,13 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
         for (int b = tid; b < kRadix - 1; b += 32) nz += s_h[3][b] != 0u;
         nz = __reduce_add_sync(0xffffffffu, nz);
         if (tid == 0) info[kInfoSkipTop] = (nz <= 1u && info[kInfoKeyWrap] == 0u) ? 1u : 0u;
+    }
+    if (diff2d) {  // rectangles were added as 2D differences: a prefix down each column first
+        for (int x = tid; x < tiles_x; x += blockDim.x) {
+            int32_t run = 0;
+            for (int y = 0; y < tiles_y; ++y) { run += s_g[y * gx + x]; s_g[y * gx + x] = run; }
+        }
+        __syncthreads();
     }
     for (int y = tid; y < tiles_y; y += blockDim.x) {
         int32_t run = 0;
@@ -648,9 +665,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const u64* __res
     }
 }
 
-// Level 2, scan: block y turns, for every tile x of row y, the counts of the
-// row's chunks into slots (tile start + earlier chunks), in place. Lanes take
-// tiles, the block's warps take consecutive segments of the row's chunks.
+// Level 2, scan: block (y, b) turns, for tiles 32 b .. 32 b + 31 of row y, the
+// counts of the row's chunks into slots (tile start + earlier chunks), in
+// place. Lanes take tiles, the block's warps take consecutive segments of the
+// row's chunks.
 constexpr int kColScanWarps = 16;
 __global__ void __launch_bounds__(32 * kColScanWarps) k_cols_scan(uint32_t* __restrict__ H2, uint32_t rows,
                                                                   uint32_t tiles_x, const uint2* __restrict__ ranges,
@@ -664,7 +682,7 @@ __global__ void __launch_bounds__(32 * kColScanWarps) k_cols_scan(uint32_t* __re
     const uint32_t j0 = rowinfo[rows + y], j1 = y + 1 < rows ? rowinfo[rows + y + 1] : rowinfo[3 * rows];
     const uint32_t per = (j1 - j0 + kColScanWarps - 1) / kColScanWarps;
     const uint32_t s0 = min(j1, j0 + w * per), s1 = min(j1, s0 + per);
-    for (uint32_t x0 = 0; x0 < tiles_x; x0 += 32) {
+    for (uint32_t x0 = blockIdx.y * 32; x0 < min(tiles_x, blockIdx.y * 32 + 32); x0 += 32) {
         const uint32_t x = x0 + lane;
         const bool on = x < tiles_x;
         uint32_t sum = 0;
@@ -930,6 +948,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
     CK(cudaGetLastError());
     if ((int64_t)gx * gy <= kGridSmemCells) {
         CK(launch_pdl(k_tiles_small, dim3(1), dim3(kTilesSmallThreads), (size_t)gx * gy * 4, st, s.grid, f.tiles_x, f.tiles_y, tp,
+                      footprint == 0 ? 1 : 0,
                                                                            reinterpret_cast<uint2*>(f.ranges), s.hist,
                                                                            f.info, (uint64_t)cap));
         count_launches();
@@ -1005,7 +1024,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
                                                                 s.walk_h2, f.info));
         count_launches();
         CK(cudaGetLastError());
-        CK(launch_pdl(k_cols_scan, dim3(rows), dim3(32 * kColScanWarps), 0, st, s.walk_h2, rows, cols, rg, s.walk_rows, f.info));
+        CK(launch_pdl(k_cols_scan, dim3(rows, (unsigned)ceil_div(cols, 32)), dim3(32 * kColScanWarps), 0, st, s.walk_h2, rows, cols, rg, s.walk_rows, f.info));
         count_launches();
         CK(cudaGetLastError());
         CK(launch_pdl(k_cols_place, dim3(walk_blocks((const void*)k_cols_place, place2, max2)), dim3(32 * kWalkWarps), place2, st, (const u64*)R1, rows, cols, s.walk_len, s.walk_rows,
