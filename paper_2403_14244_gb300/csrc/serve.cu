@@ -258,11 +258,13 @@ void complete(igs_server* s, int k) {
     s->slot_job[k] = nullptr;
     if (j->batched) {
         if (err == IGS_ERR_CAPACITY) {  // split: every request redone by itself, in its queue order
-            for (auto it = j->reqs.rbegin(); it != j->reqs.rend(); ++it) {
-                (*it)->solo = true;
-                (*it)->capacity = 0;
-                (*it)->t.retries += 1;
-                s->pending.push_front(*it);
+            for (size_t v = j->reqs.size(); v-- > 0;) {
+                Request* r = j->reqs[v];
+                if ((int64_t)info[4 + v] > r->capacity) note_entries(s, r, info[4 + v]);  // the entries it needs
+                r->solo = true;
+                r->capacity = 0;  // sized again from the hint
+                r->t.retries += 1;
+                s->pending.push_front(r);
             }
         } else {
             for (size_t v = 0; v < j->reqs.size(); ++v)
