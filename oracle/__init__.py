@@ -97,6 +97,8 @@ def _load():
             lib.orc_grad_accum3d.argtypes = [i64, P, P, P, P]
             lib.orc_densify3d.argtypes = [i64, C.c_int32, C.c_int32] + [P] * 11 + [C.c_float] * 3 + [i64] + [P] * 9
             lib.orc_densify3d.restype = i64
+            lib.orc_merge3d.argtypes = [i64, C.c_int32, C.c_int32] + [P] * 9 + [P, C.c_float, C.c_float] + [P] * 9
+            lib.orc_merge3d.restype = i64
             lib.orc_octree_init.argtypes = [i64, P, P, P, C.c_float, C.c_int32, i64, C.c_float, C.c_int32, C.c_int32,
                                             P, P, P]
             lib.orc_octree_init.restype = i64
@@ -416,6 +418,32 @@ def densify3d(params, m, v, accum, vis, param_mode, op_min, tau_g, scale_min, ca
                               *[_ptr(a) for a in vv], _ptr(acc), _ptr(vis_), float(op_min), float(tau_g),
                               float(scale_min), int(capacity), *[_ptr(a) for a in outs], *[_ptr(a) for a in om],
                               *[_ptr(a) for a in ov])
+    cut = lambda arrs: tuple(a[:k].copy() for a in arrs)  # noqa: E731
+    return cut(outs), cut(om), cut(ov)
+
+
+def merge3d(params, m, v, param_mode, lo, h, scale_max):
+    """Merging of the 3D Gaussians, read as the inverse of the octant division
+    (Sec. 3.2, 2.5, 3.1): the eligible Gaussians (finite mean, stored scale <=
+    scale_max, opacity > 0, cell of side h from lo within 1024 per axis) that
+    share a cell, two or more of them, become one Gaussian at the place of the
+    first (opacity-weighted mean and colour, moment-matched isotropic scale,
+    opacity min(0.99, 1 - prod (1 - o_k)), zero moments); the rest are kept.
+    params, m, v: (means_sigma [n][4], opacity [n], color [n][C]); returns
+    (params, m, v) of the result in index order."""
+    ms, op, col = (_c32(a) for a in params)
+    n = ms.shape[0]
+    C = col.reshape(n, -1).shape[1] if n else col.shape[-1]
+    col = col.reshape(n, C)
+    mm = [_c32(a) for a in m]
+    vv = [_c32(a) for a in v]
+    lo3 = _c32(np.asarray(lo, np.float32).reshape(3))
+    outs = [np.zeros((max(n, 1), 4), np.float32), np.zeros(max(n, 1), np.float32), np.zeros((max(n, 1), C), np.float32)]
+    om = [np.zeros_like(a) for a in outs]
+    ov = [np.zeros_like(a) for a in outs]
+    k = _load().orc_merge3d(n, C, int(param_mode), _ptr(ms), _ptr(op), _ptr(col), *[_ptr(a) for a in mm],
+                            *[_ptr(a) for a in vv], _ptr(lo3), float(h), float(scale_max), *[_ptr(a) for a in outs],
+                            *[_ptr(a) for a in om], *[_ptr(a) for a in ov])
     cut = lambda arrs: tuple(a[:k].copy() for a in arrs)  # noqa: E731
     return cut(outs), cut(om), cut(ov)
 

@@ -1221,6 +1221,147 @@ int64_t orc_densify3d(int64_t n, int32_t C, int32_t param_mode, const float* ms,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Merging of 3D Gaussians (Sec. 3.2: particles may be merged or divided;
+ * Sec. 2.5's multiscale property; the Octree of Sec. 3.1 as the pattern, so
+ * merging is read as the inverse of the octant division). Reading:
+ *   - grid: cells of side h from the corner lo, at most 1024 per axis; with
+ *     inv = 1 / h in FP32, Gaussian i's cell index on axis a is
+ *     floor((mu_a - lo_a) * inv), each operation rounded once in FP32;
+ *   - eligible: finite mean, stored scale <= scale_max (the same
+ *     parameterisation as stored), opacity above 0 (linear), and all three
+ *     cell indices in [0, 1024);
+ *   - the eligible Gaussians of one cell, two or more of them, become one
+ *     Gaussian at the place (in index order) of the first; with o_k the linear
+ *     opacity and sigma_k the linear scale of member k (sums over members in
+ *     index order, FP64):
+ *       W = sum o_k,  mu = sum o_k mu_k / W,
+ *       sigma^2 = sum o_k (sigma_k^2 + |mu_k - mu|^2 / 3) / W   (the mixture's
+ *                 covariance, made isotropic by its mean eigenvalue),
+ *       o = min(0.99, 1 - prod (1 - o_k)),   colour = sum o_k c_k / W,
+ *     stored back in the input's parameterisation and rounded once to FP32;
+ *     zero Adam moments;
+ *   - every other Gaussian is kept with its moments; output in index order.
+ * Returns the number of Gaussians written (at most n).                     */
+typedef struct {
+    uint32_t key;
+    int64_t idx;
+} merge_entry;
+
+static int cmp_merge(const void* a, const void* b) {
+    const merge_entry* x = (const merge_entry*)a;
+    const merge_entry* y = (const merge_entry*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx ? 1 : 0);
+}
+
+/* Cell key (x | y << 10 | z << 20) of Gaussian i, or 0xFFFFFFFF if it is not eligible. */
+static uint32_t merge_key(const float* ms, const float* op, int64_t i, int32_t param_mode, const float* lo,
+                          float inv, float scale_max) {
+    const float* m = ms + 4 * i;
+    if (!isfinite(m[0]) || !isfinite(m[1]) || !isfinite(m[2])) return 0xFFFFFFFFu;
+    if (!(m[3] <= scale_max)) return 0xFFFFFFFFu;
+    const double o = param_mode == 1 ? 1.0 / (1.0 + exp(-(double)op[i])) : (double)op[i];
+    if (!(o > 0.0)) return 0xFFFFFFFFu;
+    uint32_t key = 0;
+    for (int a = 0; a < 3; ++a) {
+        const float t = m[a] - lo[a];
+        const float c = floorf(t * inv);
+        if (!(c >= 0.0f && c < 1024.0f)) return 0xFFFFFFFFu;
+        key |= (uint32_t)c << (10 * a);
+    }
+    return key;
+}
+
+int64_t orc_merge3d(int64_t n, int32_t C, int32_t param_mode, const float* ms, const float* op, const float* col,
+                    const float* m_ms, const float* m_op, const float* m_col, const float* v_ms, const float* v_op,
+                    const float* v_col, const float* lo, float h, float scale_max, float* o_ms, float* o_op,
+                    float* o_col, float* om_ms, float* om_op, float* om_col, float* ov_ms, float* ov_op,
+                    float* ov_col) {
+    const float inv = 1.0f / h;
+    merge_entry* e = (merge_entry*)malloc(sizeof(merge_entry) * (size_t)(n > 0 ? n : 1));
+    int64_t* first = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));   /* group head of each i */
+    int64_t* gbeg = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));    /* sorted range of a head */
+    int64_t* gend = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        e[i].key = merge_key(ms, op, i, param_mode, lo, inv, scale_max);
+        e[i].idx = i;
+        first[i] = i;
+        gbeg[i] = gend[i] = -1;
+    }
+    qsort(e, (size_t)n, sizeof(merge_entry), cmp_merge);
+    for (int64_t p = 0; p < n;) {
+        int64_t q = p + 1;
+        while (q < n && e[q].key == e[p].key) ++q;
+        if (e[p].key != 0xFFFFFFFFu && q - p >= 2) {
+            for (int64_t r = p; r < q; ++r) first[e[r].idx] = e[p].idx;
+            gbeg[e[p].idx] = p;
+            gend[e[p].idx] = q;
+        }
+        p = q;
+    }
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (first[i] != i) continue;               /* merged into an earlier Gaussian */
+        if (gbeg[i] < 0) {                          /* kept */
+            memcpy(o_ms + 4 * o, ms + 4 * i, 16);
+            memcpy(om_ms + 4 * o, m_ms + 4 * i, 16);
+            memcpy(ov_ms + 4 * o, v_ms + 4 * i, 16);
+            o_op[o] = op[i];
+            om_op[o] = m_op[i];
+            ov_op[o] = v_op[i];
+            memcpy(o_col + (size_t)C * o, col + (size_t)C * i, 4 * (size_t)C);
+            memcpy(om_col + (size_t)C * o, m_col + (size_t)C * i, 4 * (size_t)C);
+            memcpy(ov_col + (size_t)C * o, v_col + (size_t)C * i, 4 * (size_t)C);
+            ++o;
+            continue;
+        }
+        double W = 0.0, mu[3] = {0.0, 0.0, 0.0}, keep = 1.0;
+        for (int64_t r = gbeg[i]; r < gend[i]; ++r) {
+            const int64_t k = e[r].idx;
+            const double ok = param_mode == 1 ? 1.0 / (1.0 + exp(-(double)op[k])) : (double)op[k];
+            W += ok;
+            for (int a = 0; a < 3; ++a) mu[a] += ok * (double)ms[4 * k + a];
+            keep *= 1.0 - ok;
+        }
+        for (int a = 0; a < 3; ++a) mu[a] /= W;
+        double var = 0.0;
+        double* acc = (double*)calloc((size_t)C, sizeof(double));
+        for (int64_t r = gbeg[i]; r < gend[i]; ++r) {
+            const int64_t k = e[r].idx;
+            const double ok = param_mode == 1 ? 1.0 / (1.0 + exp(-(double)op[k])) : (double)op[k];
+            const double sk = param_mode == 1 ? exp((double)ms[4 * k + 3]) : (double)ms[4 * k + 3];
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = (double)ms[4 * k + a] - mu[a];
+                d2 += d * d;
+            }
+            var += ok * (sk * sk + d2 / 3.0);
+            for (int c = 0; c < C; ++c) acc[c] += ok * (double)col[(size_t)C * k + c];
+        }
+        var /= W;
+        const double sigma = sqrt(var);
+        double om = 1.0 - keep;
+        if (om > 0.99) om = 0.99;
+        for (int a = 0; a < 3; ++a) o_ms[4 * o + a] = (float)mu[a];
+        o_ms[4 * o + 3] = param_mode == 1 ? (float)log(sigma) : (float)sigma;
+        o_op[o] = param_mode == 1 ? (float)log(om / (1.0 - om)) : (float)om;
+        for (int c = 0; c < C; ++c) o_col[(size_t)C * o + c] = (float)(acc[c] / W);
+        free(acc);
+        memset(om_ms + 4 * o, 0, 16);
+        memset(ov_ms + 4 * o, 0, 16);
+        om_op[o] = ov_op[o] = 0.f;
+        memset(om_col + (size_t)C * o, 0, 4 * (size_t)C);
+        memset(ov_col + (size_t)C * o, 0, 4 * (size_t)C);
+        ++o;
+    }
+    free(e);
+    free(first);
+    free(gbeg);
+    free(gend);
+    return o;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Octree initialisation of 3D Gaussians (Sec. 3.1: an Octree for 3D, as the
  * QuadTree for 2D; colour = the cell average, sigma = half the cell width),
  * from a coloured point set standing in for the points a reconstruction

@@ -233,9 +233,10 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_frame* frames, con
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { g_failed_call = #x " (batch.cu:" IGS_STR(__LINE__) ")"; return e; } } while (0)
     if (!fo || fo->k < 1) return cudaErrorInvalidValue;
     CK(cudaMemsetAsync(b.info, 0, 4 * (size_t)kBatchCtrlWords, st));
-    if (n == 0 || V == 0) return cudaSuccess;
-    // 1. projection of every (view, Gaussian) into the views' frames
-    {
+    if (V == 0) return cudaSuccess;
+    // 1. projection of every (view, Gaussian) into the views' frames (an empty
+    //    scene still bins to empty tiles and blends the background)
+    if (n > 0) {
         const dim3 grid((unsigned)ceil_div(n, 256), (unsigned)V);
         auto ms = reinterpret_cast<const float4*>(sc.means_sigma);
 #define IGS_PB(D) k_project_batch<D><<<grid, 256, 0, st>>>(ms, sc.opacity, sc.color, n, table)

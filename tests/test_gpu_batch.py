@@ -110,6 +110,26 @@ def test_batch_capacity_overflow_reported():
     assert torch.all(b.images == -1.0)
 
 
+def test_batch_empty_and_all_culled_scenes_give_the_background():
+    """An empty scene, and one whose Gaussians are all culled (opacity below
+    1/255), render the background in every view, as a single render does."""
+    cams = _cams(15)[:3]
+    bg = (0.25, 0.5, 1.0)
+    for sc in (scenes.Scene(means_sigma=np.zeros((0, 4), np.float32), opacity=np.zeros(0, np.float32),
+                            color=np.zeros((0, 3), np.float32), sh_degree=-1, log_params=False),
+               scenes.uniform_scene(1000, 47)):
+        if sc.n:
+            sc.opacity[:] = np.float32(0.001)             # can never reach alpha_min: culled
+        scene = _gpu.to_device(sc)
+        br = BatchRenderer(scene, cams, tile=16, bg=bg)
+        br.render()
+        torch.cuda.synchronize()
+        br.check()
+        for v, cam in enumerate(cams):
+            got = br.image(v).cpu().numpy()
+            np.testing.assert_array_equal(got, np.broadcast_to(np.array(bg, np.float32)[:, None, None], got.shape))
+
+
 def test_pack_groups():
     assert pack_groups([5, 5, 5, 5], 10) == [[0, 1], [2, 3]]
     assert pack_groups([20, 1], 10) == [[0], [1]]
