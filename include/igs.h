@@ -408,6 +408,40 @@ IGS_API igs_status igs_densify(const igs_scene* scene, const igs_params* m, cons
                                float scale_min, int64_t capacity, const igs_params* out, const igs_params* out_m,
                                const igs_params* out_v, int64_t* d_count, void* work, void* stream);
 
+/* Bytes of device scratch igs_merge needs for n Gaussians (0 for n outside 0..2^30 - 1). */
+IGS_API size_t igs_merge_work_bytes(int64_t n);
+
+/* Merging of the 3D Gaussians (Sec. 3.2: particles are merged as well as
+ * divided; Sec. 2.5: the scale of a particle follows the detail it covers;
+ * Sec. 3.1's Octree as the pattern, so a merge undoes an octant division):
+ * the grid has cells of side `cell` from the corner lo (host float[3]), at
+ * most 1024 per axis; with inv = 1 / cell in FP32, Gaussian i lies in the cell
+ * floor((mu_a - lo_a) * inv) on each axis a (each operation rounded once in
+ * FP32). Gaussian i is eligible if its mean is finite, its stored scale
+ * (means_sigma slot 3, as stored) <= scale_max, its linear opacity > 0 and all
+ * three cell indices are in [0, 1024). The eligible Gaussians of one cell, two
+ * or more of them, become one Gaussian at the place (in index order) of the
+ * first; with o_k the linear opacity and sigma_k the linear scale of member k
+ * (sums over the members in index order, FP64):
+ *   W = sum o_k,  mu = sum o_k mu_k / W,
+ *   sigma^2 = sum o_k (sigma_k^2 + |mu_k - mu|^2 / 3) / W,
+ *   opacity = min(0.99, 1 - prod (1 - o_k)),  colour = sum o_k c_k / W,
+ * stored in the input's parameterisation (param_mode 1: log sigma and the
+ * opacity logit; 0: sigma and opacity), rounded once to FP32, with zero Adam
+ * moments. Every other Gaussian is kept with its moments. Output in index
+ * order to out, out_m, out_v (device arrays of at least n Gaussians,
+ * caller-owned, not overlapping any input); their number to *d_count (device
+ * int64; -1 if the device sort gave up on a bounded wait, nothing written).
+ * work: igs_merge_work_bytes(n) bytes of device scratch, 16-byte aligned.
+ * Eleven launches, no host synchronisation.
+ * Errors: NULL, misaligned or overlapping buffers, n outside 0..2^30 - 1, a bad
+ * sh_degree or param_mode, cell not finite and > 0, a NaN scale_max or a
+ * non-finite lo -> IGS_ERR_INVALID_ARG. */
+IGS_API igs_status igs_merge(const igs_scene* scene, const igs_params* m, const igs_params* v, int32_t sh_degree,
+                             int32_t param_mode, const float* lo, float cell, float scale_max, const igs_params* out,
+                             const igs_params* out_m, const igs_params* out_v, int64_t* d_count, void* work,
+                             void* stream);
+
 /* Bytes of device scratch igs_octree_init needs for `levels` (0..7; 0 otherwise). */
 IGS_API size_t igs_octree_work_bytes(int32_t levels);
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libigs.so")
 
-SOURCES = ["api.cu", "project.cu", "sort.cu", "blend.cu", "train.cu", "ssim.cu", "fit2d.cu", "densify.cu", "octree.cu", "batch.cu", "serve.cu"]
+SOURCES = ["api.cu", "project.cu", "sort.cu", "blend.cu", "train.cu", "ssim.cu", "fit2d.cu", "densify.cu", "merge.cu", "octree.cu", "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

@@ -550,6 +550,62 @@ igs_status igs_densify(const igs_scene* scene, const igs_params* m, const igs_pa
                        "igs_densify");
 }
 
+size_t igs_merge_work_bytes(int64_t n) {
+    if (n < 0 || n >= ((int64_t)1 << 30)) return 0;
+    return igs::merge_work_bytes(n);
+}
+
+igs_status igs_merge(const igs_scene* scene, const igs_params* m, const igs_params* v, int32_t sh_degree,
+                     int32_t param_mode, const float* lo, float cell, float scale_max, const igs_params* out,
+                     const igs_params* out_m, const igs_params* out_v, int64_t* d_count, void* work, void* stream) {
+    igs_status st;
+    if ((st = check_scene(scene))) return st;
+    if (!m || !v || !out || !out_m || !out_v || !d_count || !work || !lo)
+        return fail(IGS_ERR_INVALID_ARG, "merge: NULL argument");
+    const int64_t n = scene->n;
+    if (n >= ((int64_t)1 << 30)) return fail(IGS_ERR_INVALID_ARG, "merge: n must be below 2^30");
+    if (sh_degree < -1 || sh_degree > 3) return fail(IGS_ERR_INVALID_ARG, "merge: sh_degree must be -1..3");
+    if (param_mode != 0 && param_mode != 1) return fail(IGS_ERR_INVALID_ARG, "merge: param_mode must be 0 or 1");
+    if (!(std::isfinite(cell) && cell > 0.f)) return fail(IGS_ERR_INVALID_ARG, "merge: cell must be finite and > 0");
+    if (std::isnan(scale_max)) return fail(IGS_ERR_INVALID_ARG, "merge: NaN scale_max");
+    if (!std::isfinite(lo[0]) || !std::isfinite(lo[1]) || !std::isfinite(lo[2]))
+        return fail(IGS_ERR_INVALID_ARG, "merge: lo must be finite");
+    const int C = sh_degree < 0 ? 3 : 3 * (sh_degree + 1) * (sh_degree + 1);
+    const igs_params* arrays[5] = {m, v, out, out_m, out_v};
+    if (n > 0)
+        for (const igs_params* o : arrays)
+            if (!o->means_sigma || !o->opacity || !o->color) return fail(IGS_ERR_INVALID_ARG, "merge: NULL array");
+    if (!aligned16(work)) return fail(IGS_ERR_INVALID_ARG, "merge: work must be 16-byte aligned");
+    for (const igs_params* o : arrays)
+        if (!aligned16(o->means_sigma) || !aligned16(o->color))
+            return fail(IGS_ERR_INVALID_ARG, "merge: means_sigma and color arrays must be 16-byte aligned");
+    // no output array may overlap an input array or the scratch
+    struct Span { const void* p; size_t bytes; };
+    const size_t n_ = (size_t)n;
+    const Span ins[] = {{scene->means_sigma, 16 * n_}, {scene->opacity, 4 * n_}, {scene->color, 4 * (size_t)C * n_},
+                        {m->means_sigma, 16 * n_},     {m->opacity, 4 * n_},     {m->color, 4 * (size_t)C * n_},
+                        {v->means_sigma, 16 * n_},     {v->opacity, 4 * n_},     {v->color, 4 * (size_t)C * n_},
+                        {work, igs::merge_work_bytes(n)}};
+    for (const igs_params* o : {out, out_m, out_v}) {
+        const Span os[] = {{o->means_sigma, 16 * n_}, {o->opacity, 4 * n_}, {o->color, 4 * (size_t)C * n_}};
+        for (const Span& a : os)
+            for (const Span& b : ins) {
+                const char *pa = (const char*)a.p, *pb = (const char*)b.p;
+                if (pa && pb && a.bytes && b.bytes && pa < pb + b.bytes && pb < pa + a.bytes)
+                    return fail(IGS_ERR_INVALID_ARG, "merge: an output overlaps an input or the scratch");
+            }
+    }
+    const float* in_p[3] = {scene->means_sigma, scene->opacity, scene->color};
+    const float* in_m[3] = {m->means_sigma, m->opacity, m->color};
+    const float* in_v[3] = {v->means_sigma, v->opacity, v->color};
+    float* out_p[3] = {out->means_sigma, out->opacity, out->color};
+    float* o_m[3] = {out_m->means_sigma, out_m->opacity, out_m->color};
+    float* o_v[3] = {out_v->means_sigma, out_v->opacity, out_v->color};
+    return cuda_status(igs::launch_merge(in_p, in_m, in_v, n, C, param_mode, lo, cell, scale_max, out_p, o_m, o_v,
+                                         d_count, work, (cudaStream_t)stream),
+                       "igs_merge");
+}
+
 size_t igs_octree_work_bytes(int32_t levels) { return igs::octree_work_bytes(levels); }
 
 igs_status igs_octree_init(const float* points, const float* colors, int64_t n, const float* lo, float side,

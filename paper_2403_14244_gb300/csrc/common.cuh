@@ -226,6 +226,12 @@ cudaError_t launch_densify(const float* const in_p[3], const float* const in_m[3
                            float* const out_m[3], float* const out_v[3], int64_t* d_count, void* work,
                            cudaStream_t s);
 
+// Merging of the 3D Gaussians that share a grid cell (merge.cu).
+size_t merge_work_bytes(int64_t n);
+cudaError_t launch_merge(const float* const in_p[3], const float* const in_m[3], const float* const in_v[3], int64_t n,
+                         int C, int param_mode, const float lo[3], float cell, float scale_max, float* const out_p[3],
+                         float* const out_m[3], float* const out_v[3], int64_t* d_count, void* work, cudaStream_t st);
+
 // Octree initialisation of 3D Gaussians from a coloured point set (octree.cu).
 size_t octree_work_bytes(int L);
 cudaError_t launch_octree_init(const float* pts, const float* cols, long long npts, const float lo[3], float side,

@@ -125,6 +125,10 @@ SYMBOLS = {
                               C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_int64,
                               C.POINTER(IgsParams), C.POINTER(IgsParams), C.POINTER(IgsParams), C.c_void_p,
                               C.c_void_p, C.c_void_p]),
+    "igs_merge_work_bytes": (C.c_size_t, [C.c_int64]),
+    "igs_merge": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsParams), C.POINTER(IgsParams), C.c_int32, C.c_int32,
+                            C.POINTER(C.c_float), C.c_float, C.c_float, C.POINTER(IgsParams), C.POINTER(IgsParams),
+                            C.POINTER(IgsParams), C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_octree_work_bytes": (C.c_size_t, [C.c_int32]),
     "igs_octree_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float), C.c_float, C.c_int32,
                                   C.c_int32, C.c_float, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -503,6 +507,28 @@ def densify(scene: Scene, m, v, sh_degree, param_mode, accum, vis, op_min, tau_g
                               float(scale_min), int(out[0].shape[0]), C.byref(_params(out)),
                               C.byref(_params(out_m)), C.byref(_params(out_v)), _ptr(count), _ptr(work),
                               _stream(stream)), "igs_densify")
+
+
+def merge_work_bytes(n):
+    return int(load().igs_merge_work_bytes(int(n)))
+
+
+def merge(scene: Scene, m, v, sh_degree, param_mode, lo, cell, scale_max, out, out_m, out_v, count, work,
+          stream=None):
+    """Merge the eligible Gaussians of `scene` (stored parameters) that share a
+    grid cell of side `cell` from the corner lo, with their Adam moments m, v =
+    (means_sigma, opacity, color) tensors, into out, out_m, out_v (same layout,
+    at least scene.n Gaussians); the new count goes to count (device int64, -1
+    if the device sort gave up)."""
+    _check_color_width(scene, sh_degree, "merge")
+    for o in (out, out_m, out_v):
+        if int(o[0].shape[0]) < scene.n or int(o[1].shape[0]) < scene.n or int(o[2].shape[0]) < scene.n:
+            raise ValueError("merge: every output array needs room for scene.n Gaussians")
+    lo3 = (C.c_float * 3)(*[float(x) for x in lo])
+    _check(load().igs_merge(C.byref(scene.struct), C.byref(_params(m)), C.byref(_params(v)), int(sh_degree),
+                            int(param_mode), lo3, float(cell), float(scale_max), C.byref(_params(out)),
+                            C.byref(_params(out_m)), C.byref(_params(out_v)), _ptr(count), _ptr(work),
+                            _stream(stream)), "igs_merge")
 
 
 def octree_work_bytes(levels):

@@ -337,6 +337,29 @@ class TrainStep:
         self.track_grad_norm()
         return k
 
+    def merge(self, lo, cell, scale_max):
+        """Merge the eligible Gaussians (log sigma <= scale_max, finite mean,
+        opacity > 0) that share a grid cell of side `cell` from the corner lo
+        into one each (libigs's igs_merge: opacity-weighted mean and colour,
+        moment-matched scale, opacity 1 - prod (1 - o_k) capped at 0.99, zero
+        moments); parameters and Adam moments move to new flat buffers. Reads the
+        new count back (one synchronisation); the Adam step count continues."""
+        dev = self.flat.device
+        n, C = self.n, self.C
+        outs = [(torch.empty((max(n, 1), 4), device=dev), torch.empty(max(n, 1), device=dev),
+                 torch.empty((max(n, 1), C), device=dev)) for _ in range(3)]
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        work = torch.empty(igs.merge_work_bytes(n), dtype=torch.uint8, device=dev)
+        igs.merge(self.scene, self.m_views, self.v_views, self.sh_degree, 1, lo, cell, scale_max, outs[0], outs[1],
+                  outs[2], count, work)
+        k = int(count.item())
+        if k < 0:
+            raise igs.IgsError(igs.ERR_DEVICE_TIMEOUT, "merge: the device sort gave up on a bounded wait")
+        self._relayout(k, outs)
+        if self.accum is not None:
+            self.track_grad_norm()
+        return k
+
     def _relayout(self, n, arrays):
         """New flat buffers for n Gaussians, filled from (params, m, v) arrays."""
         self.n = n
