@@ -425,7 +425,7 @@ def densify3d(params, m, v, accum, vis, param_mode, op_min, tau_g, scale_min, ca
 def merge3d(params, m, v, param_mode, lo, h, scale_max):
     """Merging of the 3D Gaussians, read as the inverse of the octant division
     (Sec. 3.2, 2.5, 3.1): the eligible Gaussians (finite mean, stored scale <=
-    scale_max, opacity > 0, cell of side h from lo within 1024 per axis) that
+    scale_max, opacity >= 2^-60, cell of side h from lo within 1024 per axis) that
     share a cell, two or more of them, become one Gaussian at the place of the
     first (opacity-weighted mean and colour, moment-matched isotropic scale,
     opacity min(0.99, 1 - prod (1 - o_k)), zero moments); the rest are kept.

@@ -1228,8 +1228,10 @@ int64_t orc_densify3d(int64_t n, int32_t C, int32_t param_mode, const float* ms,
  *     inv = 1 / h in FP32, Gaussian i's cell index on axis a is
  *     floor((mu_a - lo_a) * inv), each operation rounded once in FP32;
  *   - eligible: finite mean, stored scale <= scale_max (the same
- *     parameterisation as stored), opacity above 0 (linear), and all three
- *     cell indices in [0, 1024);
+ *     parameterisation as stored), opacity at least 2^-60 (a lighter one
+ *     weighs nothing in the merged sums), tested on the stored value: 2^-60 <=
+ *     opacity <= 1, or logit >= -41.58883f (the FP32 value nearest the logit of
+ *     2^-60) with param_mode 1; and all three cell indices in [0, 1024);
  *   - the eligible Gaussians of one cell, two or more of them, become one
  *     Gaussian at the place (in index order) of the first; with o_k the linear
  *     opacity and sigma_k the linear scale of member k (sums over members in
@@ -1238,6 +1240,8 @@ int64_t orc_densify3d(int64_t n, int32_t C, int32_t param_mode, const float* ms,
  *       sigma^2 = sum o_k (sigma_k^2 + |mu_k - mu|^2 / 3) / W   (the mixture's
  *                 covariance, made isotropic by its mean eigenvalue),
  *       o = min(0.99, 1 - prod (1 - o_k)),   colour = sum o_k c_k / W,
+ *     with 1 - prod (1 - o_k) evaluated as -expm1(sum log1p(-o_k)) (the same
+ *     value, without the cancellation that loses small opacities),
  *     stored back in the input's parameterisation and rounded once to FP32;
  *     zero Adam moments;
  *   - every other Gaussian is kept with its moments; output in index order.
@@ -1260,8 +1264,9 @@ static uint32_t merge_key(const float* ms, const float* op, int64_t i, int32_t p
     const float* m = ms + 4 * i;
     if (!isfinite(m[0]) || !isfinite(m[1]) || !isfinite(m[2])) return 0xFFFFFFFFu;
     if (!(m[3] <= scale_max)) return 0xFFFFFFFFu;
-    const double o = param_mode == 1 ? 1.0 / (1.0 + exp(-(double)op[i])) : (double)op[i];
-    if (!(o > 0.0)) return 0xFFFFFFFFu;
+    const float op_floor = param_mode == 1 ? -41.58883f : 0x1p-60f;
+    if (!(op[i] >= op_floor)) return 0xFFFFFFFFu;
+    if (param_mode == 0 && !(op[i] <= 1.0f)) return 0xFFFFFFFFu;
     uint32_t key = 0;
     for (int a = 0; a < 3; ++a) {
         const float t = m[a] - lo[a];
@@ -1315,13 +1320,13 @@ int64_t orc_merge3d(int64_t n, int32_t C, int32_t param_mode, const float* ms, c
             ++o;
             continue;
         }
-        double W = 0.0, mu[3] = {0.0, 0.0, 0.0}, keep = 1.0;
+        double W = 0.0, mu[3] = {0.0, 0.0, 0.0}, log_keep = 0.0;
         for (int64_t r = gbeg[i]; r < gend[i]; ++r) {
             const int64_t k = e[r].idx;
             const double ok = param_mode == 1 ? 1.0 / (1.0 + exp(-(double)op[k])) : (double)op[k];
             W += ok;
             for (int a = 0; a < 3; ++a) mu[a] += ok * (double)ms[4 * k + a];
-            keep *= 1.0 - ok;
+            log_keep += log1p(-ok);
         }
         for (int a = 0; a < 3; ++a) mu[a] /= W;
         double var = 0.0;
@@ -1340,7 +1345,7 @@ int64_t orc_merge3d(int64_t n, int32_t C, int32_t param_mode, const float* ms, c
         }
         var /= W;
         const double sigma = sqrt(var);
-        double om = 1.0 - keep;
+        double om = -expm1(log_keep);
         if (om > 0.99) om = 0.99;
         for (int a = 0; a < 3; ++a) o_ms[4 * o + a] = (float)mu[a];
         o_ms[4 * o + 3] = param_mode == 1 ? (float)log(sigma) : (float)sigma;

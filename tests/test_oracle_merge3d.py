@@ -65,6 +65,8 @@ def test_order_cells_and_eligibility_against_numpy():
     sigma = np.exp(rng.uniform(np.log(0.002), np.log(0.05), n))
     opac = rng.uniform(0.0, 0.9, n)
     opac[::53] = 0.0
+    opac[::59] = 2.0 ** -61                            # below the floor: never merged
+    opac[::61] = 2.0 ** -60                            # at the floor: eligible
     col = rng.uniform(0, 1, (n, 3))
     p = _params(means, sigma, opac, col)
     h, smax = 0.125, 0.02
@@ -72,7 +74,7 @@ def test_order_cells_and_eligibility_against_numpy():
     inv = np.float32(1.0) / np.float32(h)
     cell = np.floor((p[0][:, :3] - np.float32(-1.0)) * inv)
     with np.errstate(invalid="ignore"):
-        ok = (np.isfinite(p[0][:, :3]).all(1) & (p[0][:, 3] <= np.float32(smax)) & (p[1] > 0)
+        ok = (np.isfinite(p[0][:, :3]).all(1) & (p[0][:, 3] <= np.float32(smax)) & (p[1] >= np.float32(2.0 ** -60))
               & (cell >= 0).all(1) & (cell < 1024).all(1))
     ci = np.where(ok[:, None], cell, 0).astype(np.int64)
     key = np.where(ok, ci[:, 0] + 1024 * ci[:, 1] + 1024 * 1024 * ci[:, 2], -1)
@@ -157,3 +159,40 @@ def test_translation_by_whole_cells():
     assert a.shape == b.shape
     np.testing.assert_allclose(b[:, 0] - a[:, 0], 2 * h, atol=2e-6)
     np.testing.assert_allclose(b[:, 1:], a[:, 1:], rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_opacity_floor_on_the_stored_value(mode):
+    """Eligibility needs opacity >= 2^-60, tested on the stored value: 2^-60
+    itself, or the FP32 logit -41.58883f, merges; the next float below does not."""
+    floor = np.float32(2.0 ** -60) if mode == 0 else np.float32(-41.58883)
+    below = np.nextafter(floor, np.float32(-np.inf))
+    for o, merges in ((floor, True), (below, False)):
+        ms = np.array([[0.1, 0.1, 0.1, 0.01], [0.12, 0.1, 0.1, 0.01]], np.float32)
+        if mode == 1:
+            ms[:, 3] = np.log(ms[:, 3])
+        op = np.array([o, 0.5 if mode == 0 else 0.0], np.float32)
+        p = (ms, op, np.ones((2, 3), np.float32))
+        (out, _, _), _, _ = _merge(p, scale_max=1.0, param_mode=mode)
+        assert len(out) == (1 if merges else 2)
+
+
+def test_small_opacities_add_up():
+    # 1 - prod(1 - o_k) for opacities far below the FP64 epsilon: about sum o_k
+    # (1 - o rounds to 1 there, so the product form would give 0)
+    o = [1e-17, 2e-17, 3e-17]
+    p = _params([[0.1, 0.1, 0.1]] * 3, [0.01] * 3, o, [[0.0, 0.5, 1.0]] * 3)
+    (ms, op, col), _, _ = _merge(p)
+    assert len(op) == 1 and op[0] == pytest.approx(6e-17, rel=1e-6)
+    np.testing.assert_allclose(col[0], [0.0, 0.5, 1.0], rtol=1e-6)
+    # the same in logits: log(o / (1 - o)) of the sum
+    lp = _params([[0.1, 0.1, 0.1]] * 3, np.log([0.01] * 3), np.log(o), [[0.0, 0.5, 1.0]] * 3)
+    (_, op_l, _), _, _ = _merge(lp, scale_max=0.0, param_mode=1)
+    assert op_l[0] == pytest.approx(np.log(6e-17), rel=1e-6)
+
+
+def test_opacity_above_one_not_merged():
+    p = _params([[0.1, 0.1, 0.1]] * 3, [0.01] * 3, [1.5, 0.5, 1.0], [[1, 1, 1]] * 3)
+    (ms, op, _), _, _ = _merge(p)
+    assert len(op) == 2 and op[0] == np.float32(1.5)   # kept first, then the merged pair at index 1
+    assert op[1] == np.float32(0.99)                    # 1 - (1 - 0.5)(1 - 1) = 1, capped
