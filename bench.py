@@ -51,6 +51,8 @@ def parse():
                     help="tiles of a Gaussian: 0 its bounding rectangle, 1 the tiles its disc meets")
     ap.add_argument("--ssim", type=float, default=0.0,
                     help="lambda of the loss (1 - lambda) L1 + lambda (1 - SSIM) in the timed step (0: L1)")
+    ap.add_argument("--only", choices=("merge",), default=None,
+                    help="measure one side line alone on the training scene (no training step, no JSON contract)")
     return ap.parse_args()
 
 
@@ -449,6 +451,7 @@ def run_mine(args, world, rank, local):
                                                      peak_hbm)
     if not args.no_extra:
         extra["densify_3M"] = run_densify3d(ts, cam_s, targets, stream, dev, peak_hbm)
+        extra["merge_3M"] = run_merge3d(ts, stream, dev, peak_hbm)
         extra.update(run_extra(dev, np, args.tile))
 
     result = {
@@ -539,6 +542,59 @@ def run_densify3d(ts, cam_s, targets, stream, dev, peak_hbm, steps=32, reps=3):
     return {"n": n, "steps_tracked": steps, "step_ms": round(plain_ms, 4), "step_ms_with_statistic":
             round(tracked_ms, 4), "tau_g": tau_g, "with_gradient": int(moved.sum()), "kept": kept, "deleted": n - kept, "divided": divided,
             "out": k, "densify_ms": round(ms, 4),
+            "roofline": {"bound": "hbm", "bytes": nbytes, "achieved": round(gbs, 1), "peak": peak_hbm,
+                         "unit": "GB/s", "frac": round(gbs / peak_hbm, 4)}}
+
+
+def run_merge3d(ts, stream, dev, peak_hbm, reps=3, cells=128):
+    """Merging of the training scene's Gaussians (igs_merge) into new buffers: a
+    grid of `cells` cells per axis over the scene's bounding box, the Gaussians
+    with sigma at most the median eligible. Groups are counted on the host from
+    the same FP32 cell rule. Bandwidth over the pass's algorithmic bytes: 20 B per
+    Gaussian (mean, scale and opacity for its cell key), 2 x 3 rows per kept
+    Gaussian (parameters and moments read and written), one row read per member
+    of a merged cell and 3 rows written per merged Gaussian (row = 4 (5 + C) B)."""
+    import numpy as np
+    import torch
+
+    from paper_2403_14244_gb300 import igs
+
+    n, C = ts.n, ts.C
+    ms = ts.ms.cpu().numpy()
+    op = ts.op.cpu().numpy()
+    lo = ms[:, :3].min(0)
+    h = float((ms[:, :3].max(0) - lo).max()) / cells * 1.0001
+    smax = float(np.median(ms[:, 3]))
+    inv = np.float32(1.0) / np.float32(h)
+    cell = np.floor((ms[:, :3] - lo.astype(np.float32)) * inv)
+    with np.errstate(invalid="ignore", over="ignore"):
+        ok = (np.isfinite(ms[:, :3]).all(1) & (ms[:, 3] <= np.float32(smax)) & (1 / (1 + np.exp(-op.astype(np.float64))) > 0)
+              & (cell >= 0).all(1) & (cell < 1024).all(1))
+    ci = cell[ok].astype(np.int64)
+    _, cnt = np.unique(ci[:, 0] | (ci[:, 1] << 10) | (ci[:, 2] << 20), return_counts=True)
+    groups, members = int((cnt >= 2).sum()), int(cnt[cnt >= 2].sum())
+    outs = [(torch.empty((n, 4), device=dev), torch.empty(n, device=dev), torch.empty((n, C), device=dev))
+            for _ in range(3)]
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    work = torch.empty(igs.merge_work_bytes(n), dtype=torch.uint8, device=dev)
+    args = (ts.scene, ts.m_views, ts.v_views, 3, 1, [float(x) for x in lo], h, smax, outs[0], outs[1], outs[2], count,
+            work)
+    igs.merge(*args)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        igs.merge(*args, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_t = a.elapsed_time(b) / reps
+    k = int(count.item())
+    kept = n - members
+    row = 4 * (5 + C)
+    nbytes = 20 * n + 2 * 3 * row * kept + row * members + 3 * row * groups
+    gbs = nbytes / (ms_t / 1e3) / 1e9
+    return {"n": n, "cells_per_axis": cells, "cell": h, "scale_max_log": smax, "merged_cells": groups,
+            "members": members, "out": k, "out_expected": kept + groups, "merge_ms": round(ms_t, 4),
             "roofline": {"bound": "hbm", "bytes": nbytes, "achieved": round(gbs, 1), "peak": peak_hbm,
                          "unit": "GB/s", "frac": round(gbs / peak_hbm, 4)}}
 
@@ -1111,6 +1167,13 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.only == "merge":
+        import torch
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        _, _, _, ts, _, _, _ = build_workload(args.n, dev, args.footprint, args.tile)
+        print(json.dumps({"merge_3M": run_merge3d(ts, torch.cuda.current_stream(dev), dev, load_peaks()[0])}))
         return
     run_mine(args, world, rank, local)
 

@@ -418,22 +418,26 @@ IGS_API size_t igs_merge_work_bytes(int64_t n);
  * most 1024 per axis; with inv = 1 / cell in FP32, Gaussian i lies in the cell
  * floor((mu_a - lo_a) * inv) on each axis a (each operation rounded once in
  * FP32). Gaussian i is eligible if its mean is finite, its stored scale
- * (means_sigma slot 3, as stored) <= scale_max, its linear opacity > 0 and all
- * three cell indices are in [0, 1024). The eligible Gaussians of one cell, two
+ * (means_sigma slot 3, as stored) <= scale_max, its stored opacity is in
+ * [2^-60, 1] (param_mode 0) or its stored logit >= -41.58883f (param_mode 1,
+ * the logit of 2^-60) and all three cell indices are in [0, 1024). The eligible Gaussians of one cell, two
  * or more of them, become one Gaussian at the place (in index order) of the
  * first; with o_k the linear opacity and sigma_k the linear scale of member k
- * (sums over the members in index order, FP64):
+ * (sums over the members in index order):
  *   W = sum o_k,  mu = sum o_k mu_k / W,
  *   sigma^2 = sum o_k (sigma_k^2 + |mu_k - mu|^2 / 3) / W,
  *   opacity = min(0.99, 1 - prod (1 - o_k)),  colour = sum o_k c_k / W,
  * stored in the input's parameterisation (param_mode 1: log sigma and the
- * opacity logit; 0: sigma and opacity), rounded once to FP32, with zero Adam
- * moments. Every other Gaussian is kept with its moments. Output in index
+ * opacity logit; 0: sigma and opacity), with zero Adam moments. Arithmetic:
+ * FP32 with compensated sums and the means as offsets from the first member
+ * (with u = 2^-24 and h = cell: mean within 32u h + 4u |mu| of the exact value,
+ * scale within 64u relative, opacity within 16u relative, colour within
+ * 16u max|c| + 4u |c|). Every other Gaussian is kept with its moments. Output in index
  * order to out, out_m, out_v (device arrays of at least n Gaussians,
  * caller-owned, not overlapping any input); their number to *d_count (device
  * int64; -1 if the device sort gave up on a bounded wait, nothing written).
  * work: igs_merge_work_bytes(n) bytes of device scratch, 16-byte aligned.
- * Eleven launches, no host synchronisation.
+ * Twelve launches, no host synchronisation.
  * Errors: NULL, misaligned or overlapping buffers, n outside 0..2^30 - 1, a bad
  * sh_degree or param_mode, cell not finite and > 0, a NaN scale_max or a
  * non-finite lo -> IGS_ERR_INVALID_ARG. */

@@ -339,7 +339,7 @@ class TrainStep:
 
     def merge(self, lo, cell, scale_max):
         """Merge the eligible Gaussians (log sigma <= scale_max, finite mean,
-        opacity > 0) that share a grid cell of side `cell` from the corner lo
+        opacity logit >= -41.58883, i.e. opacity >= 2^-60) that share a grid cell of side `cell` from the corner lo
         into one each (libigs's igs_merge: opacity-weighted mean and colour,
         moment-matched scale, opacity 1 - prod (1 - o_k) capped at 0.99, zero
         moments); parameters and Adam moments move to new flat buffers. Reads the
