@@ -120,6 +120,9 @@ def stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm):
         "blend_bwd": ("alu", M * (4 + 32) + P * (12 + 4 + 4) + n * 32),
         # read params, 2D gradient, count, m, v; write params, m, v
         "project_bwd_adam": ("hbm", n * (4 * params + 32 + 4 + 8 * params) + n * 12 * params),
+        # the same, and the next view's record, rectangle, count and depth key written
+        "project_bwd_adam_next": ("hbm", n * (4 * params + 32 + 4 + 8 * params) + n * 12 * params
+                                  + n * (32 + 8 + 4 + 4)),
     }
     total = sum(stage_ms.values())
     out = []
@@ -140,6 +143,7 @@ def stage_rooflines(stage_ms, n, C, P, M, tiles, peak_hbm):
 # sources hash to the value recorded with the capture.
 TRAFFIC_SOURCES = {
     "project_bwd_adam": ("project.cu", "projection.cuh", "common.cuh"),
+    "project_bwd_adam_next": ("project.cu", "projection.cuh", "common.cuh"),
     "project": ("project.cu", "projection.cuh", "common.cuh"),
     "l1": ("train.cu", "common.cuh"),
     "blend_fwd": ("blend.cu", "blendtile.cuh", "common.cuh"),
@@ -349,17 +353,20 @@ def run_mine(args, world, rank, local):
     # capacity calibration: every view once with a status check (untimed set-up)
     for k in range(V):
         ts.step(cam_s[k], targets[k], check=True)
+    # every step ends by projecting the next view (views in cyclic order), so the
+    # next step starts at its binning
     for k in range(args.warmup):
-        ts.step(cam_s[k % V], targets[k % V])
+        ts.step(cam_s[k % V], targets[k % V], next_cam=cam_s[(k + 1) % V])
     torch.cuda.synchronize(dev)
     # per-stage times: eager steps with CUDA events between the stages (untimed for the headline)
     stage_steps = min(args.steps, 128)
     stage_ev = []
-    for k in range(stage_steps):
+    for k in range(args.warmup, args.warmup + stage_steps):
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
         evs[0].record(stream)
         it = iter(evs[1:])
-        ts.step(cam_s[k % V], targets[k % V], marks=lambda name, it=it: next(it).record(stream))
+        ts.step(cam_s[k % V], targets[k % V], marks=lambda name, it=it: next(it).record(stream),
+                next_cam=cam_s[(k + 1) % V])
         stage_ev.append(evs)
     torch.cuda.synchronize(dev)
     stage_ms = {s: 0.0 for s in STAGES}
@@ -367,10 +374,14 @@ def run_mine(args, world, rank, local):
         for i, s in enumerate(STAGES):
             stage_ms[s] += evs[i].elapsed_time(evs[i + 1])
     stage_ms = {s: v / stage_steps for s, v in stage_ms.items()}
+    # the projection ran inside the previous step's last pass: its own interval is empty
+    stage_ms.pop("project")
+    stage_ms["project_bwd_adam_next"] = stage_ms.pop("project_bwd_adam")
     eager_ms = sum(stage_ms.values())
-    # one CUDA graph per view's step (the Adam step count lives on the device)
+    # one CUDA graph per view's step (the Adam step count lives on the device), chained:
+    # graph k ends by projecting view k + 1
     launches0 = igs.launch_count()
-    ts.capture(cam_s, targets)
+    ts.capture(cam_s, targets, chain=True)
     launches_per_step = (igs.launch_count() - launches0) / V
     for k in range(V):
         ts.replay(k)
@@ -502,7 +513,7 @@ def run_densify3d(ts, cam_s, targets, stream, dev, peak_hbm, steps=32, reps=3):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for k in range(n_steps):
-            ts.step(cam_s[k % V], targets[k % V])
+            ts.step(cam_s[k % V], targets[k % V], next_cam=cam_s[(k + 1) % V])
         b.record(stream)
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / n_steps
@@ -607,21 +618,22 @@ def run_ssim_steps(ts, cam_s, targets, stream, dev, steps, peak_hbm, lam=0.2):
     gradient written by the backward kernel: 44 bytes)."""
     import torch
 
-    stages = ("project", "bin_sort", "blend_fwd", "l1_ssim", "blend_bwd", "project_bwd_adam")
+    stages = ("project", "bin_sort", "blend_fwd", "l1_ssim", "blend_bwd", "project_bwd_adam_next")
     V = len(cam_s)
     ts.ssim_lambda = lam
-    try:
+    try:  # as the headline step: each step projects the next view in its last pass
         for k in range(3):
-            ts.step(cam_s[k % V], targets[k % V])
+            ts.step(cam_s[k % V], targets[k % V], next_cam=cam_s[(k + 1) % V])
         torch.cuda.synchronize(dev)
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stage_ev = []
         start.record(stream)
-        for k in range(steps):
+        for k in range(3, 3 + steps):
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
             evs[0].record(stream)
             it = iter(evs[1:])
-            ts.step(cam_s[k % V], targets[k % V], marks=lambda name, it=it: next(it).record(stream))
+            ts.step(cam_s[k % V], targets[k % V], marks=lambda name, it=it: next(it).record(stream),
+                    next_cam=cam_s[(k + 1) % V])
             stage_ev.append(evs)
         end.record(stream)
         torch.cuda.synchronize(dev)
@@ -629,6 +641,7 @@ def run_ssim_steps(ts, cam_s, targets, stream, dev, steps, peak_hbm, lam=0.2):
         ts.ssim_lambda = 0.0
     ms = start.elapsed_time(end) / steps
     stage_ms = {s: sum(e[i].elapsed_time(e[i + 1]) for e in stage_ev) / steps for i, s in enumerate(stages)}
+    stage_ms.pop("project")  # (inside the previous step's last pass)
     entries = targets[0].numel()
     nbytes = 44 * entries
     gbs = nbytes / (stage_ms["l1_ssim"] / 1e3) / 1e9

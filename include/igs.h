@@ -255,6 +255,24 @@ IGS_API igs_status igs_project_bwd_adam_dev(const igs_scene* scene, const igs_ca
                                             float* v_color, double lr, double b1, double b2, double eps,
                                             int32_t* d_state, void* stream);
 
+/* igs_project_bwd_adam_dev followed, in the same pass over the Gaussians, by
+ * the projection of the NEXT view (Eq. 7 with Sigma = sigma^2 I, Sec. 2.4: as
+ * igs_project) from the parameters just updated: next_frame receives exactly
+ * what igs_project(scene after this step, next_cam, opts, next_frame) would
+ * write (rec, rect, disc, count, depth_key, bit for bit), so that the next
+ * view's step starts at igs_bin_sort. next_frame (laid out for next_cam's size
+ * and scene->n) may be `frame` itself: each Gaussian's count of this view is
+ * read before the next view's is written. The parameters are read once for
+ * both: one pass over HBM instead of two. Two launches; errors as
+ * igs_project_bwd_adam_dev, plus a NULL, invalid or mismatched next_cam or
+ * next_frame. */
+IGS_API igs_status igs_project_bwd_adam_next(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                             const igs_frame* frame, const float* g2d, float* m_means_sigma,
+                                             float* m_opacity, float* m_color, float* v_means_sigma,
+                                             float* v_opacity, float* v_color, double lr, double b1, double b2,
+                                             double eps, int32_t* d_state, const igs_camera* next_cam,
+                                             const igs_frame* next_frame, void* stream);
+
 /* L1 loss of Sec. 3 (lambda = 0): loss = mean |img - target| over `count`
  * entries, written to *loss (device float, overwritten), and
  * dL_dimg = sign(img - target) / count (device, count entries; sign(0) = 0). */

@@ -322,15 +322,20 @@ igs_status igs_project_bwd_adam(const igs_scene* scene, const igs_camera* cam, c
                        "igs_project_bwd_adam");
 }
 
-igs_status igs_project_bwd_adam_dev(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
-                                    const igs_frame* frame, const float* g2d, float* m_means_sigma, float* m_opacity,
-                                    float* m_color, float* v_means_sigma, float* v_opacity, float* v_color, double lr,
-                                    double b1, double b2, double eps, int32_t* d_state, void* stream) {
+static igs_status project_bwd_adam_dev(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                       const igs_frame* frame, const float* g2d, float* m_means_sigma,
+                                       float* m_opacity, float* m_color, float* v_means_sigma, float* v_opacity,
+                                       float* v_color, double lr, double b1, double b2, double eps, int32_t* d_state,
+                                       const igs_camera* next_cam, const igs_frame* next_frame, void* stream,
+                                       const char* name) {
     if (!d_state || (reinterpret_cast<uintptr_t>(d_state) & 15))
         return fail(IGS_ERR_INVALID_ARG, "d_state must be a 16-byte aligned device buffer of 4 words");
     igs_status st;
     if ((st = check_scene(scene)) || (st = check_camera(cam)) || (st = check_opts(opts)) || (st = check_frame(frame)) ||
         (st = frame_matches(frame, scene, cam, opts)))
+        return st;
+    if (next_cam && ((st = check_camera(next_cam)) || (st = check_frame(next_frame)) ||
+                     (st = frame_matches(next_frame, scene, next_cam, opts))))
         return st;
     if (!g2d || !m_means_sigma || !m_opacity || !m_color || !v_means_sigma || !v_opacity || !v_color)
         return fail(IGS_ERR_INVALID_ARG, "g2d or an Adam moment buffer is NULL");
@@ -342,11 +347,33 @@ igs_status igs_project_bwd_adam_dev(const igs_scene* scene, const igs_camera* ca
     if ((st = adam_params(lr, b1, b2, eps, 1, &a))) return st;  // b1, b2, eps; the step's constants come from d_state
     a.dev_consts = reinterpret_cast<const float*>(d_state + 1);
     const igs::ViewParams vp = view_params(cam, opts, frame);
+    const igs::ViewParams vp_next = next_cam ? view_params(next_cam, opts, next_frame) : vp;
     cudaError_t e = igs::launch_adam_advance(d_state, lr, b1, b2, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_status(e, "igs_project_bwd_adam_dev");
+    if (e != cudaSuccess) return cuda_status(e, name);
     return cuda_status(igs::launch_project_bwd_adam(*scene, vp, *frame, g2d, m_means_sigma, m_opacity, m_color,
-                                                    v_means_sigma, v_opacity, v_color, a, (cudaStream_t)stream),
-                       "igs_project_bwd_adam_dev");
+                                                    v_means_sigma, v_opacity, v_color, a, (cudaStream_t)stream,
+                                                    next_cam ? &vp_next : nullptr, next_cam ? next_frame : nullptr),
+                       name);
+}
+
+igs_status igs_project_bwd_adam_dev(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                    const igs_frame* frame, const float* g2d, float* m_means_sigma, float* m_opacity,
+                                    float* m_color, float* v_means_sigma, float* v_opacity, float* v_color, double lr,
+                                    double b1, double b2, double eps, int32_t* d_state, void* stream) {
+    return project_bwd_adam_dev(scene, cam, opts, frame, g2d, m_means_sigma, m_opacity, m_color, v_means_sigma,
+                                v_opacity, v_color, lr, b1, b2, eps, d_state, nullptr, nullptr, stream,
+                                "igs_project_bwd_adam_dev");
+}
+
+igs_status igs_project_bwd_adam_next(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
+                                     const igs_frame* frame, const float* g2d, float* m_means_sigma,
+                                     float* m_opacity, float* m_color, float* v_means_sigma, float* v_opacity,
+                                     float* v_color, double lr, double b1, double b2, double eps, int32_t* d_state,
+                                     const igs_camera* next_cam, const igs_frame* next_frame, void* stream) {
+    if (!next_cam || !next_frame) return fail(IGS_ERR_INVALID_ARG, "next_cam or next_frame is NULL");
+    return project_bwd_adam_dev(scene, cam, opts, frame, g2d, m_means_sigma, m_opacity, m_color, v_means_sigma,
+                                v_opacity, v_color, lr, b1, b2, eps, d_state, next_cam, next_frame, stream,
+                                "igs_project_bwd_adam_next");
 }
 
 igs_status igs_render_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts, const igs_frame* frame,

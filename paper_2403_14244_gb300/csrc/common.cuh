@@ -184,9 +184,12 @@ cudaError_t launch_project(const igs_scene& sc, const ViewParams& vp, const igs_
 cudaError_t launch_project_bwd(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d,
                                float* d_ms, float* d_op, float* d_col, cudaStream_t s);
 struct AdamParams;
+// With vp_next and f_next, the same pass also projects every Gaussian for the
+// next view from its updated parameters (what launch_project would write there).
 cudaError_t launch_project_bwd_adam(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d,
                                     float* m_ms, float* m_op, float* m_col, float* v_ms, float* v_op, float* v_col,
-                                    const AdamParams& ap, cudaStream_t s);
+                                    const AdamParams& ap, cudaStream_t s, const ViewParams* vp_next = nullptr,
+                                    const igs_frame* f_next = nullptr);
 cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t s);
 cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t s);

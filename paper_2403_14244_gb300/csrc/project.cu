@@ -109,18 +109,27 @@ struct AdamState {
     float4* v_ms; float* v_op; float* v_col;
 };
 
+// Where the projection of the next view goes (a frame's per-Gaussian arrays).
+struct ProjOut {
+    float4* rec; uint2* rect; float4* disc; uint32_t* count; uint32_t* depth_key;
+};
+
 // Adjoint of the projection and colour: g2d holds (du, dv, dw2, do, dr, dg, db, -)
 // per Gaussian, accumulated by the backward blend. ADAM = false writes the
 // gradients w.r.t. the stored parameters to d_ms / d_op / d_col; ADAM = true
 // applies one Adam step to the parameters in place (ms / op / col) instead,
-// without materialising the gradient.
-template <int DEG, bool ADAM>
+// without materialising the gradient. NEXT (with ADAM): each Gaussian is then
+// projected for the next view (P2, into o2) from its updated parameters, still
+// in registers and shared memory, so the next step needs no projection pass of
+// its own. o2 may be the frame of this view: each thread reads its Gaussian's
+// count before it writes the next view's.
+template <int DEG, bool ADAM, bool NEXT = false>
 __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restrict__ ms, float* __restrict__ op,
                                                             float* __restrict__ col, int64_t n, ViewParams P,
-                                                            const uint32_t* __restrict__ count,
+                                                            const uint32_t* count,
                                                             const float4* __restrict__ g2d, float4* __restrict__ d_ms,
                                                             float* __restrict__ d_op, float* __restrict__ d_col,
-                                                            AdamState st, AdamParams ap) {
+                                                            AdamState st, AdamParams ap, ViewParams P2, ProjOut o2) {
     pdl_wait();
     constexpr int C = DEG < 0 ? 3 : 3 * (DEG + 1) * (DEG + 1);
     using CT = ColorTile<C>;
@@ -242,6 +251,7 @@ __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restri
         else return Y[k / 3] * draw[k % 3];
     };
     // means, sigma, opacity: one lane per Gaussian (coalesced rows of 16 and 4 bytes)
+    ProjGeom pg{};
     if (active) {
         const float4 g4 = make_float4(dmx, dmy, dmz, dsig_out);
         if constexpr (ADAM) {
@@ -251,6 +261,9 @@ __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restri
             float mo = e_mo, vo = e_vo;
             adam_update(raw_op, dop_out, mo, vo, a);
             op[i] = raw_op; st.m_op[i] = mo; st.v_op[i] = vo;
+            // the next view's geometry while the colour moments are still in flight
+            if constexpr (NEXT) pg = project_geom(m, raw_op, P2, o2.rec + 2 * i, o2.rect + i, o2.disc + i,
+                                                  o2.count + i, o2.depth_key + i);
         } else {
             d_ms[i] = g4;
             d_op[i] = dop_out;
@@ -283,6 +296,7 @@ __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restri
                 float4 mm = Mrows[q];
                 float4 vv = Vrows[q];
                 adam_update4(p4, g4, mm, vv, a);
+                if constexpr (NEXT) A[g * CT::kStride + (q - g * CT::kF4)] = p4;  // for the next view's colour
                 reinterpret_cast<float4*>(col)[row0 + q] = p4;
                 reinterpret_cast<float4*>(st.m_col)[row0 + q] = mm;
                 reinterpret_cast<float4*>(st.v_col)[row0 + q] = vv;
@@ -304,16 +318,36 @@ __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restri
             }
         }
     }
+    if constexpr (NEXT) {  // the next view's colour from the updated coefficients
+        static_assert(ADAM, "the next view is projected from the updated parameters");
+        if constexpr (CT::kStaged) __syncwarp();  // the staged rows hold the updated coefficients
+        if (active && pg.keep) {
+            float c[48];
+            if constexpr (CT::kStaged) {
+                const float4* row = A + lane * CT::kStride;  // odd float4 stride: conflict-free
+#pragma unroll
+                for (int q = 0; q < CT::kF4; ++q) {
+                    const float4 t = row[q];
+                    c[4 * q] = t.x; c[4 * q + 1] = t.y; c[4 * q + 2] = t.z; c[4 * q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < C; ++k) c[k] = col[(size_t)C * (size_t)i + k];  // this thread's own writes
+            }
+            project_color<DEG>(m, pg, c, P2, o2.rec + 2 * i);
+        }
+    }
 }
 
-template <int DEG, bool ADAM>
+template <int DEG, bool ADAM, bool NEXT = false>
 cudaError_t launch_pb(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d, float* d_ms,
-                      float* d_op, float* d_col, const AdamState& st, const AdamParams& ap, cudaStream_t stream) {
+                      float* d_op, float* d_col, const AdamState& st, const AdamParams& ap, cudaStream_t stream,
+                      const ViewParams& vp2 = ViewParams{}, const ProjOut& o2 = ProjOut{}) {
     constexpr int C = DEG < 0 ? 3 : 3 * (DEG + 1) * (DEG + 1);
     const size_t smem = (size_t)(kPbThreads / 32) *
                         (ColorTile<C>::kWarpFloat4 + (ADAM && ColorTile<C>::kStaged ? 2 * 32 * ColorTile<C>::kF4 : 0)) *
                         sizeof(float4);
-    auto k = k_project_bwd<DEG, ADAM>;
+    auto k = k_project_bwd<DEG, ADAM, NEXT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -323,20 +357,21 @@ cudaError_t launch_pb(const igs_scene& sc, const ViewParams& vp, const igs_frame
                                const_cast<float4*>(reinterpret_cast<const float4*>(sc.means_sigma)),
                                const_cast<float*>(sc.opacity), const_cast<float*>(sc.color), sc.n, vp, f.count,
                                reinterpret_cast<const float4*>(g2d), reinterpret_cast<float4*>(d_ms), d_op, d_col, st,
-                               ap);
+                               ap, vp2, o2);
     count_launches();
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <bool ADAM>
+template <bool ADAM, bool NEXT = false>
 cudaError_t dispatch_pb(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d, float* d_ms,
-                        float* d_op, float* d_col, const AdamState& st, const AdamParams& ap, cudaStream_t stream) {
+                        float* d_op, float* d_col, const AdamState& st, const AdamParams& ap, cudaStream_t stream,
+                        const ViewParams& vp2 = ViewParams{}, const ProjOut& o2 = ProjOut{}) {
     switch (vp.sh_degree) {
-        case -1: return launch_pb<-1, ADAM>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream);
-        case 0: return launch_pb<0, ADAM>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream);
-        case 1: return launch_pb<1, ADAM>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream);
-        case 2: return launch_pb<2, ADAM>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream);
-        case 3: return launch_pb<3, ADAM>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream);
+        case -1: return launch_pb<-1, ADAM, NEXT>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream, vp2, o2);
+        case 0: return launch_pb<0, ADAM, NEXT>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream, vp2, o2);
+        case 1: return launch_pb<1, ADAM, NEXT>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream, vp2, o2);
+        case 2: return launch_pb<2, ADAM, NEXT>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream, vp2, o2);
+        case 3: return launch_pb<3, ADAM, NEXT>(sc, vp, f, g2d, d_ms, d_op, d_col, st, ap, stream, vp2, o2);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -396,9 +431,15 @@ cudaError_t launch_project_bwd(const igs_scene& sc, const ViewParams& vp, const 
 
 cudaError_t launch_project_bwd_adam(const igs_scene& sc, const ViewParams& vp, const igs_frame& f, const float* g2d,
                                     float* m_ms, float* m_op, float* m_col, float* v_ms, float* v_op, float* v_col,
-                                    const AdamParams& ap, cudaStream_t st) {
+                                    const AdamParams& ap, cudaStream_t st, const ViewParams* vp_next,
+                                    const igs_frame* f_next) {
     if (sc.n == 0) return cudaSuccess;
     AdamState s{reinterpret_cast<float4*>(m_ms), m_op, m_col, reinterpret_cast<float4*>(v_ms), v_op, v_col};
+    if (vp_next && f_next) {
+        const ProjOut o2{reinterpret_cast<float4*>(f_next->rec), reinterpret_cast<uint2*>(f_next->rect),
+                         reinterpret_cast<float4*>(f_next->disc), f_next->count, f_next->depth_key};
+        return dispatch_pb<true, true>(sc, vp, f, g2d, nullptr, nullptr, nullptr, s, ap, st, *vp_next, o2);
+    }
     return dispatch_pb<true>(sc, vp, f, g2d, nullptr, nullptr, nullptr, s, ap, st);
 }
 

@@ -162,17 +162,23 @@ __device__ __forceinline__ float support_radius(float s, float o) {
     return __fmul_rn(__fmul_rn(s, k), 1.000244140625f);
 }
 
-// load_c(c) fills c[0 .. C) with the Gaussian's colour coefficients; it is
-// called only for Gaussians that are kept.
-template <int DEG, typename LoadC>
-__device__ __forceinline__ void project_one_with(const float4* __restrict__ ms, const float* __restrict__ op,
-                                                 LoadC load_c, int64_t i, const ViewParams& P,
+// The geometric half of a Gaussian's projection (culling, disc, tiles, depth),
+// kept for its colour half.
+struct ProjGeom {
+    bool keep;
+    float u, v, w2, pmax, o;
+};
+
+// Geometric half from the stored parameters m (mean, scale) and raw_op: writes
+// count, depth key, rectangle (and disc), or the culled values with a zero
+// record.
+__device__ __forceinline__ ProjGeom project_geom(float4 m, float raw_op, const ViewParams& P,
                                                  float4* __restrict__ rec, uint2* __restrict__ rect,
                                                  float4* __restrict__ disc, uint32_t* __restrict__ count,
                                                  uint32_t* __restrict__ depth_key) {
-    const float4 m = __ldg(ms + i);
+    ProjGeom g;
     float sg, o;
-    activate(P.param_mode, m.w, __ldg(op + i), sg, o);
+    activate(P.param_mode, m.w, raw_op, sg, o);
     bool keep = finite4(m.x, m.y, m.z, sg) && isfinite(o);
     float xc = 0.f, yc = 0.f, zc = 0.f;
     if (keep) {
@@ -214,6 +220,7 @@ __device__ __forceinline__ void project_one_with(const float4* __restrict__ ms, 
             }
         }
     }
+    g.keep = keep;
     if (!keep) {
         *count = 0;
         *depth_key = 0xFFFFFFFFu;
@@ -221,15 +228,26 @@ __device__ __forceinline__ void project_one_with(const float4* __restrict__ ms, 
         if (P.footprint) *disc = make_float4(0.f, 0.f, 0.f, 0.f);
         rec[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         rec[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+        return g;
     }
     *count = touched;
     if (P.footprint) *disc = make_disc(u, v, r, x0, x1);  // read only by the per-row walks
     *depth_key = __float_as_uint(zc);
     *rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
-    // colour
-    float c[48];
-    load_c(c);
+    g.u = u;
+    g.v = v;
+    g.w2 = 0.5f * kLog2e / (s * s);
+    // every pixel with w2 d^2 above pmax has alpha < alpha_min (skipped in Eq. 4)
+    g.pmax = __fadd_rn(log2f(__fdiv_rn(o, P.alpha_min)), kPowMargin);
+    g.o = o;
+    return g;
+}
+
+// Colour half of a kept Gaussian's projection: its colour from the
+// coefficients c[0 .. C) (SH evaluated toward the camera centre), and the record.
+template <int DEG>
+__device__ __forceinline__ void project_color(float4 m, const ProjGeom& g, const float* c, const ViewParams& P,
+                                              float4* __restrict__ rec) {
     float rgb[3];
     if constexpr (DEG < 0) {
         rgb[0] = c[0]; rgb[1] = c[1]; rgb[2] = c[2];
@@ -248,11 +266,32 @@ __device__ __forceinline__ void project_one_with(const float4* __restrict__ ms, 
             rgb[ch] = fmaxf(acc + 0.5f, 0.f);
         }
     }
-    const float w2 = 0.5f * kLog2e / (s * s);
-    // every pixel with w2 d^2 above pmax has alpha < alpha_min (skipped in Eq. 4)
-    const float pmax = __fadd_rn(log2f(__fdiv_rn(o, P.alpha_min)), kPowMargin);
-    rec[0] = make_float4(u, v, w2, pmax);
-    rec[1] = make_float4(rgb[0], rgb[1], rgb[2], o);
+    rec[0] = make_float4(g.u, g.v, g.w2, g.pmax);
+    rec[1] = make_float4(rgb[0], rgb[1], rgb[2], g.o);
+}
+
+// The Gaussian's stored parameters are m (mean, scale) and raw_op; load_c(c)
+// fills c[0 .. C) with its colour coefficients and is called only for
+// Gaussians that are kept.
+template <int DEG, typename LoadC>
+__device__ __forceinline__ void project_one_vals(float4 m, float raw_op, LoadC load_c, const ViewParams& P,
+                                                 float4* __restrict__ rec, uint2* __restrict__ rect,
+                                                 float4* __restrict__ disc, uint32_t* __restrict__ count,
+                                                 uint32_t* __restrict__ depth_key) {
+    const ProjGeom g = project_geom(m, raw_op, P, rec, rect, disc, count, depth_key);
+    if (!g.keep) return;
+    float c[48];
+    load_c(c);
+    project_color<DEG>(m, g, c, P, rec);
+}
+
+template <int DEG, typename LoadC>
+__device__ __forceinline__ void project_one_with(const float4* __restrict__ ms, const float* __restrict__ op,
+                                                 LoadC load_c, int64_t i, const ViewParams& P,
+                                                 float4* __restrict__ rec, uint2* __restrict__ rect,
+                                                 float4* __restrict__ disc, uint32_t* __restrict__ count,
+                                                 uint32_t* __restrict__ depth_key) {
+    project_one_vals<DEG>(__ldg(ms + i), __ldg(op + i), load_c, P, rec, rect, disc, count, depth_key);
 }
 
 template <int DEG>

@@ -106,6 +106,10 @@ SYMBOLS = {
     "igs_project_bwd_adam_dev": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
                                            C.POINTER(IgsFrame), C.c_void_p] + [C.c_void_p] * 6 +
                                  [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p]),
+    "igs_project_bwd_adam_next": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
+                                            C.POINTER(IgsFrame), C.c_void_p] + [C.c_void_p] * 6 +
+                                  [C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                   C.POINTER(IgsCamera), C.POINTER(IgsFrame), C.c_void_p]),
     "igs_l1_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_ssim_work_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "igs_l1_ssim_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float,
@@ -402,6 +406,17 @@ def project_bwd_adam_dev(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame,
     _check(load().igs_project_bwd_adam_dev(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                            _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
                                            _ptr(state), _stream(stream)), "igs_project_bwd_adam_dev")
+
+
+def project_bwd_adam_next(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, m, v, state, next_cam,
+                          next_frame: Frame, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    """project_bwd_adam_dev, then the projection of next_cam into next_frame from
+    the updated parameters in the same pass (what project() would write)."""
+    _check_color_width(scene, o.sh_degree, "project_bwd_adam_next")
+    _check(load().igs_project_bwd_adam_next(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
+                                            _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2,
+                                            eps, _ptr(state), C.byref(next_cam), C.byref(next_frame.struct),
+                                            _stream(stream)), "igs_project_bwd_adam_next")
 
 
 def l1_loss(img, target, loss, dL_dimg, stream=None):

@@ -98,6 +98,7 @@ class Renderer:
             cap = self.capacity_for(scene.n, c)
             f = self.lease(scene.n, c, cap) if lease else self.frame(scene.n, c, cap)
             igs.project(scene, c, self.opts, f, stream)
+            f.proj_gen = getattr(f, "proj_gen", 0) + 1  # the frame's projection arrays changed
             igs.bin_sort(f, self.opts, stream)
             igs.render_fwd(f, self.opts, img, stream)
             if not check:
@@ -225,15 +226,31 @@ class TrainStep:
         # Adam step count and the step's constants on the device (fused path), so steps can be graph-replayed
         self.adam_state = torch.zeros(4, dtype=torch.int32, device=device)
         self.graphs = None
+        self._pending = None     # (camera bytes, frame, its projection generation): a projection already made
+        self._graph_next = None  # per captured graph: the view whose projection it leaves behind (chained capture)
 
     def _views(self, flat):
         n, C = self.n, self.C
         return (flat[:4 * n].view(n, 4), flat[self.o_op:self.o_op + n], flat[self.o_col:self.o_col + C * n].view(n, C))
 
-    def step(self, cam, target, check=False, stream=None, marks=None):
+    def _projected(self, c, frame):
+        """Whether `frame` already holds this scene's projection for camera c
+        (left there by the previous step's fused pass, and not touched since)."""
+        p = self._pending
+        return (p is not None and p[0] == bytes(c) and p[1] is frame and p[2] == getattr(frame, "proj_gen", 0)
+                and frame.n == self.n)
+
+    def _mark_projected(self, c, frame):
+        frame.proj_gen = getattr(frame, "proj_gen", 0) + 1
+        self._pending = (bytes(c), frame, frame.proj_gen)
+
+    def step(self, cam, target, check=False, stream=None, marks=None, next_cam=None):
         """One training step on `stream`. `marks`, if given, is called with a
         stage name after each stage is enqueued (the benchmark records CUDA
-        events there)."""
+        events there). With next_cam (fused path), the step's last pass also
+        projects the updated scene for next_cam, and the next step on that
+        camera starts at the binning (the projection arrays of the returned
+        frame then hold next_cam's view when it has the same size)."""
         c = cam if isinstance(cam, igs.IgsCamera) else igs.camera(cam)
         key = (c.width, c.height)
         if key not in self._img:
@@ -246,7 +263,9 @@ class TrainStep:
             img, frame = r.run_forward(self.scene, c, img=img, check=True, stream=stream)
         else:
             frame = r.frame(self.scene.n, c, r.capacity_for(self.scene.n, c))
-            igs.project(self.scene, c, r.opts, frame, stream)
+            if not self._projected(c, frame):
+                igs.project(self.scene, c, r.opts, frame, stream)
+                frame.proj_gen = getattr(frame, "proj_gen", 0) + 1
             mark("project")
             igs.bin_sort(frame, r.opts, stream)
             mark("bin_sort")
@@ -266,7 +285,15 @@ class TrainStep:
         if self.accum is not None:
             igs.grad_accum(self.g2d, frame.count(), self.accum, self.vis, stream)
         self.t += 1
-        if self.fused:
+        self._pending = None
+        if self.fused and next_cam is not None:
+            nc = next_cam if isinstance(next_cam, igs.IgsCamera) else igs.camera(next_cam)
+            nframe = r.frame(self.scene.n, nc, r.capacity_for(self.scene.n, nc))
+            igs.project_bwd_adam_next(self.scene, c, r.opts, frame, self.g2d, self.m_views, self.v_views,
+                                      self.adam_state, nc, nframe, lr=self.lr, stream=stream)
+            self._mark_projected(nc, nframe)
+            mark("project_bwd_adam")
+        elif self.fused:
             igs.project_bwd_adam_dev(self.scene, c, r.opts, frame, self.g2d, self.m_views, self.v_views,
                                      self.adam_state, lr=self.lr, stream=stream)
             mark("project_bwd_adam")
@@ -277,33 +304,56 @@ class TrainStep:
             mark("adam")
         return frame
 
-    def capture(self, cams, targets):
+    def capture(self, cams, targets, chain=False):
         """Record one training step per (camera, target) into its own CUDA graph
         (fused path: the Adam step count lives on the device, so replays keep
         counting). Each view must have run once with check=True before (its entry
         capacity is then known). Replay with replay(k); the graphs read the
-        `targets` tensors as they are at replay time."""
+        `targets` tensors as they are at replay time. With chain=True, graph k
+        ends by projecting view k + 1 (cyclically) and starts at its binning:
+        replays in the order 0, 1, 2, ... skip every projection pass; replay(k)
+        after anything else first projects view k on the current stream."""
         if not self.fused:
             raise RuntimeError("graph capture needs the fused projection backward + Adam")
         t0 = self.t
+        cams = [c if isinstance(c, igs.IgsCamera) else igs.camera(c) for c in cams]
+        V = len(cams)
+        r = self.renderer
         cur = torch.cuda.current_stream()
         s = torch.cuda.Stream(device=self.flat.device)
         s.wait_stream(cur)
-        graphs = []
+        graphs, frames, nexts = [], [], []
         with torch.cuda.stream(s):
-            for c, tgt in zip(cams, targets):
+            for k, (c, tgt) in enumerate(zip(cams, targets)):
+                frame = r.frame(self.scene.n, c, r.capacity_for(self.scene.n, c))
+                if chain:  # recorded as if the previous graph had projected this view
+                    self._mark_projected(c, frame)
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=s):
-                    self.step(c, tgt, stream=s)
+                    self.step(c, tgt, stream=s, next_cam=cams[(k + 1) % V] if chain else None)
                 graphs.append(g)
+                frames.append(frame)
+                nexts.append((k + 1) % V if chain else None)
         cur.wait_stream(s)
         self.t = t0  # recording ran nothing
+        self._pending = None
         self.graphs = graphs
+        self._graph_cams, self._graph_frames, self._graph_next = cams, frames, nexts
         return graphs
 
     def replay(self, k):
         """Replay the captured step of view k on the current stream."""
-        self.graphs[k].replay()
+        if self._graph_next[k] is not None:  # chained graph: it starts at the binning
+            c, frame = self._graph_cams[k], self._graph_frames[k]
+            if not self._projected(c, frame):
+                igs.project(self.scene, c, self.renderer.opts, frame)
+                frame.proj_gen = getattr(frame, "proj_gen", 0) + 1
+            self.graphs[k].replay()
+            j = self._graph_next[k]
+            self._mark_projected(self._graph_cams[j], self._graph_frames[j])
+        else:
+            self.graphs[k].replay()
+            self._pending = None
         self.t += 1
 
     def track_grad_norm(self):
@@ -384,3 +434,4 @@ class TrainStep:
         self.scene = igs.Scene(self.ms, self.op, self.col)
         self.g2d = torch.empty((n, 8), dtype=torch.float32, device=dev)
         self.graphs = None  # captured steps refer to the old buffers
+        self._pending = None

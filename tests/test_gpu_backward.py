@@ -239,3 +239,70 @@ def test_train_step_full_size_graph_replay():
         assert moved.sum() > 100, name
         np.testing.assert_allclose(p[moved], p_ref[moved], atol=2e-6, err_msg=name)
         np.testing.assert_array_equal(p[g == 0], p0[g == 0])
+
+
+def _frame_arrays(f, footprint):
+    out = [f.rec(), f.rect(), f.count(), f.depth_key()] + ([f.disc()] if footprint else [])
+    return [a.cpu().numpy().view(np.uint32) for a in out]
+
+
+@pytest.mark.parametrize("sh,footprint", [(3, 0), (3, 1), (-1, 0), (1, 1)])
+def test_fused_next_projection_bit_exact(sh, footprint):
+    """A step with next_cam projects the updated scene for the next view in its
+    last pass: the frame then holds exactly what a separate projection of the
+    updated parameters writes (same size: in the step's own frame; another
+    size: in that size's frame), for staged (SH 3, 1) and unstaged (RGB) colour
+    rows, both footprints, a ragged last warp of Gaussians."""
+    C = 3 if sh < 0 else 3 * (sh + 1) ** 2
+    sc, cam = random_small(1001, 46, w=96, h=64, sh_degree=sh, log_params=True, spread=0.8)
+    cam2 = dataclasses.replace(cam, t=(np.asarray(cam.t, np.float32) + np.float32(0.07)).astype(np.float32))
+    cam3 = dataclasses.replace(cam2, width=80, height=72, cx=40.0, cy=36.0)
+    target = torch.from_numpy(scenes.target_image(cam.width, cam.height, 12)).cuda()
+    ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                   torch.from_numpy(sc.color.reshape(sc.n, C)).cuda(), sh_degree=sh, lr=1e-2, footprint=footprint)
+    for nxt in (cam2, cam3):
+        ts.step(cam, target, check=True)           # capacity of the view
+        ts.step(igs.camera(nxt), torch.zeros((3, nxt.height, nxt.width), device="cuda"), check=True)
+        ts.step(cam, target, next_cam=nxt)
+        torch.cuda.synchronize()
+        r = ts.renderer
+        c = igs.camera(nxt)
+        f_fused = r.frame(ts.n, c, r.capacity_for(ts.n, c))
+        got = _frame_arrays(f_fused, footprint)
+        ref = igs.Frame(ts.n, 1 << 16, c, r.opts)
+        igs.project(ts.scene, c, r.opts, ref)
+        torch.cuda.synchronize()
+        for g, w in zip(got, _frame_arrays(ref, footprint)):
+            np.testing.assert_array_equal(g, w)
+        assert (got[2] > 0).sum() > 500
+
+
+def test_chained_steps_and_graphs_match_plain_steps():
+    """Steps that project the next view in their last pass (eager, and replayed
+    from chained CUDA graphs in order and out of order) follow the trajectory of
+    plain steps: parameters and moments agree up to the backward's atomic
+    summation order, and the device step count advances once per step."""
+    sc, cam = random_small(2000, 49, w=128, h=96, sh_degree=3, log_params=True, spread=0.8)
+    cams = [igs.camera(dataclasses.replace(cam, t=(np.asarray(cam.t, np.float32) + np.float32(0.04 * k))
+                                           .astype(np.float32))) for k in range(3)]
+    targets = [torch.from_numpy(scenes.target_image(cam.width, cam.height, 30 + k)).cuda() for k in range(3)]
+    order = [0, 1, 2, 0, 1, 2, 2, 1, 0, 1]            # in order, then out of order
+    states = []
+    for mode in ("plain", "chained", "graphs"):
+        ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                       torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-2)
+        for k in range(3):
+            ts.step(cams[k], targets[k], check=True)
+        if mode == "graphs":
+            ts.capture(cams, targets, chain=True)
+            for k in order:
+                ts.replay(k)
+        else:
+            for j, k in enumerate(order):
+                nxt = cams[order[j + 1]] if mode == "chained" and j + 1 < len(order) else None
+                ts.step(cams[k], targets[k], next_cam=nxt)
+        torch.cuda.synchronize()
+        assert int(ts.adam_state[0]) == 3 + len(order)
+        states.append(torch.cat([ts.flat, ts.m, ts.v]).cpu().numpy())
+    np.testing.assert_allclose(states[1], states[0], rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(states[2], states[0], rtol=1e-4, atol=1e-6)
