@@ -150,15 +150,48 @@ __device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const u
     __syncthreads();
     // no pixel blended anything at or past this entry
     const uint32_t hi_end = rg.x + min(s_max, rg.y - rg.x);
+    // Batches walk [lo, hi) downwards, BB entries each; k = 0 is the last entry
+    // of a batch. With one thread per staged entry, the staging is software
+    // pipelined: the thread's entry ids come two batches ahead and its records
+    // one batch ahead, so a long walk does not wait out two dependent gathers
+    // per batch.
+    const uint32_t st = threadIdx.x;  // this thread's staged entry (NT == BB)
+    auto stages = [&](uint32_t h) { return h > rg.x && st < min((uint32_t)BB, h - rg.x); };
+    auto next_hi = [&](uint32_t h) { return h > rg.x ? h - min((uint32_t)BB, h - rg.x) : rg.x; };
+    uint32_t g_cur = 0, g_nxt = 0;
+    float4 a_cur = make_float4(0.f, 0.f, 0.f, 0.f), c_cur = a_cur;
+    if constexpr (NT == BB) {
+        if (stages(hi_end)) {
+            g_cur = vals[hi_end - 1 - st];
+            a_cur = rec[2 * g_cur];
+            c_cur = rec[2 * g_cur + 1];
+        }
+        const uint32_t h1 = next_hi(hi_end);
+        if (stages(h1)) g_nxt = vals[h1 - 1 - st];
+    }
     for (uint32_t hi = hi_end; hi > rg.x;) {
         const uint32_t lo = hi - min((uint32_t)BB, hi - rg.x);
         const int nb = (int)(hi - lo);
-        for (int t = threadIdx.x; t < nb; t += NT) {
-            const uint32_t j = hi - 1 - t;  // k = 0 is the last entry of the batch
-            const uint32_t g = vals[j];
-            s_id[t] = g;
-            s_a[t] = rec[2 * g];
-            s_c[t] = rec[2 * g + 1];
+        if constexpr (NT == BB) {
+            if ((int)st < nb) {
+                s_id[st] = g_cur;
+                s_a[st] = a_cur;
+                s_c[st] = c_cur;
+            }
+            if (stages(lo)) {  // the next batch's records, then the ids of the one after it
+                a_cur = rec[2 * g_nxt];
+                c_cur = rec[2 * g_nxt + 1];
+            }
+            g_cur = g_nxt;
+            const uint32_t h2 = next_hi(lo);
+            if (stages(h2)) g_nxt = vals[h2 - 1 - st];
+        } else {
+            for (int t = threadIdx.x; t < nb; t += NT) {
+                const uint32_t g = vals[hi - 1 - t];
+                s_id[t] = g;
+                s_a[t] = rec[2 * g];
+                s_c[t] = rec[2 * g + 1];
+            }
         }
         __syncthreads();
 #pragma unroll

@@ -66,13 +66,34 @@ __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int he
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
     bool done = !inside;
+    // Software-pipelined staging: thread t < B stages entry b0 + t of every
+    // batch, its ids fetched two batches ahead and its records one batch ahead,
+    // so that a long walk does not wait out two dependent gathers per batch.
+    const bool stager = threadIdx.x < B;
+    uint32_t g_nxt = 0;
+    float4 a_cur = make_float4(0.f, 0.f, 0.f, 0.f), c_cur = a_cur;
+    if (stager) {
+        const uint32_t j0 = rg.x + threadIdx.x, j1 = j0 + B;
+        if (j0 < rg.y) {
+            const uint32_t g = vals[j0];
+            a_cur = rec[2 * g];
+            c_cur = rec[2 * g + 1];
+        }
+        if (j1 < rg.y) g_nxt = vals[j1];
+    }
     for (uint32_t b0 = rg.x; b0 < rg.y; b0 += B) {
         if (__syncthreads_count(done) == NT) break;
-        const uint32_t j = b0 + threadIdx.x;
-        if (threadIdx.x < B && j < rg.y) {
-            const uint32_t g = vals[j];
-            s_a[threadIdx.x] = rec[2 * g];
-            s_c[threadIdx.x] = rec[2 * g + 1];
+        if (stager) {
+            const uint32_t j = b0 + threadIdx.x;
+            if (j < rg.y) {
+                s_a[threadIdx.x] = a_cur;
+                s_c[threadIdx.x] = c_cur;
+            }
+            if (j + B < rg.y) {  // the next batch's record, then the id of the one after it
+                a_cur = rec[2 * g_nxt];
+                c_cur = rec[2 * g_nxt + 1];
+            }
+            if (j + 2 * B < rg.y) g_nxt = vals[j + 2 * B];
         }
         __syncthreads();
         const int nb = (int)min((uint32_t)B, rg.y - b0);
