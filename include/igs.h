@@ -538,6 +538,17 @@ IGS_API igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info,
  * blocks). Host-only, takes effect once. */
 IGS_API void igs_debug_silence_lookback_once(void);
 
+/* Walk segments (observability; the paper has no counterpart). With 16- and
+ * 32-pixel tiles the forward blend (igs_render_fwd) cuts the walk of an 8 x 8
+ * pixel block through its tile's entries every 1024 list positions where the
+ * block has blended since the previous cut, and saves the pixels' state there,
+ * so that igs_blend_bwd walks the pieces in parallel (Eq. 4's adjoint is the same;
+ * only the order of the additions changes). Writes to *host_count the pool slots
+ * the last forward of this frame took (cut segments, and at most one slot per
+ * block taken ahead and left unused); -1 when the frame has no segments (8-pixel
+ * tiles, or no room). Waits for `stream`. Synchronous. */
+IGS_API igs_status igs_frame_walk_segments(const igs_frame* frame, int64_t* host_count, void* stream);
+
 /* Clear the frame's status words (asynchronous). */
 IGS_API igs_status igs_frame_reset_status(igs_frame* frame, void* stream);
 

@@ -257,9 +257,14 @@ igs_status igs_blend_bwd(const igs_frame* frame, const igs_opts* opts, const flo
     if (reinterpret_cast<uintptr_t>(g2d) & 15) return fail(IGS_ERR_INVALID_ARG, "g2d must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     igs::ZeroRanges z = {};
-    z.ptr[0] = g2d;
-    z.bytes[0] = (unsigned long long)frame->n * 32;
-    z.count = frame->n > 0 ? 1 : 0;
+    if (frame->n > 0) {
+        z.ptr[z.count] = g2d;
+        z.bytes[z.count++] = (unsigned long long)frame->n * 32;
+    }
+    if (void* next = igs::blend_bwd_counter(*frame)) {  // the backward's work counter
+        z.ptr[z.count] = next;
+        z.bytes[z.count++] = 4;
+    }
     cudaError_t e = igs::launch_zero(z, s);
     if (e != cudaSuccess) return cuda_status(e, "igs_blend_bwd");
     const igs::BlendParams bp = blend_params(frame, opts);
@@ -846,6 +851,24 @@ igs_status igs_frame_status(const igs_frame* frame, uint32_t* host_info, void* s
         const igs_status d = (igs_status)host_info[igs::kInfoErr];
         return fail(d, "device reported: %s (M needed = %u)", igs_status_string(d), host_info[igs::kInfoNeed]);
     }
+    return IGS_OK;
+}
+
+igs_status igs_frame_walk_segments(const igs_frame* frame, int64_t* host_count, void* stream) {
+    igs_status st;
+    if ((st = check_frame(frame))) return st;
+    if (!host_count) return fail(IGS_ERR_INVALID_ARG, "host_count is NULL");
+    const uint32_t* used = igs::blend_segments_used(*frame);
+    if (!used) {
+        *host_count = -1;
+        return IGS_OK;
+    }
+    uint32_t v = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&v, used, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "igs_frame_walk_segments");
+    *host_count = (int64_t)v;
     return IGS_OK;
 }
 

@@ -99,12 +99,16 @@ __device__ __forceinline__ bool bwd_pair(BwdPixel& q, uint32_t pos, const BwdEnt
 // (tx, ty), pixel A in its upper 8 x 4 half and pixel B four rows below, so one
 // warp reduction per entry serves 64 pixels (a compact block is reached by fewer
 // entries than whole rows). rg: the entries to walk (those of the tile, or of an
-// enclosing binning tile).
+// enclosing binning tile). A walk segment (TS = 8) walks only list positions
+// [seg_lo, seg_hi) from the pixels' saved state at seg_hi (seg_state: 64 pixels
+// (T, colour behind); nullptr: the final state).
 template <int TS>
 __device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const uint32_t* __restrict__ vals,
                                                const float4* __restrict__ rec, const BlendParams& P,
                                                const float* __restrict__ dL, const float* __restrict__ T_final,
-                                               const uint32_t* __restrict__ n_contrib, float4* __restrict__ g2d) {
+                                               const uint32_t* __restrict__ n_contrib, float4* __restrict__ g2d,
+                                               uint32_t seg_lo = 0, uint32_t seg_hi = kSegNone,
+                                               const float4* __restrict__ seg_state = nullptr) {
     constexpr int NT = TS * TS / 2;
     constexpr int NW = NT / 32;
     constexpr int BPR = TS / 8;  // 8 x 8 warp blocks per block row of the tile
@@ -142,22 +146,28 @@ __device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const u
             p.nc = n_contrib[pix];
         }
         p.GS = p.T * (p.G0 * P.bg[0] + p.G1 * P.bg[1] + p.G2 * P.bg[2]);
+        if (TS == 8 && seg_state) {  // pixel index in the 8 x 8 block: row * 8 + column = lane + 32 i
+            const float4 v = seg_state[lane + 32 * i];
+            p.T = v.x;
+            p.GS = p.G0 * v.y + p.G1 * v.z + p.G2 * v.w;
+        }
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(q[0].nc, q[1].nc));  // nothing blended past wmax
     if (lane == 0 && wmax) atomicMax(&s_max, wmax);
     __syncthreads();
-    // no pixel blended anything at or past this entry
-    const uint32_t hi_end = rg.x + min(s_max, rg.y - rg.x);
+    // no pixel blended anything at or past this entry; the walk ends at L
+    const uint32_t hi_end = rg.x + min(min(s_max, seg_hi), rg.y - rg.x);
+    const uint32_t L = rg.x + min(seg_lo, rg.y - rg.x);
     // Batches walk [lo, hi) downwards, BB entries each; k = 0 is the last entry
     // of a batch. With one thread per staged entry, the staging is software
     // pipelined: the thread's entry ids come two batches ahead and its records
     // one batch ahead, so a long walk does not wait out two dependent gathers
     // per batch.
     const uint32_t st = threadIdx.x;  // this thread's staged entry (NT == BB)
-    auto stages = [&](uint32_t h) { return h > rg.x && st < min((uint32_t)BB, h - rg.x); };
-    auto next_hi = [&](uint32_t h) { return h > rg.x ? h - min((uint32_t)BB, h - rg.x) : rg.x; };
+    auto stages = [&](uint32_t h) { return h > L && st < min((uint32_t)BB, h - L); };
+    auto next_hi = [&](uint32_t h) { return h > L ? h - min((uint32_t)BB, h - L) : L; };
     uint32_t g_cur = 0, g_nxt = 0;
     float4 a_cur = make_float4(0.f, 0.f, 0.f, 0.f), c_cur = a_cur;
     if constexpr (NT == BB) {
@@ -169,8 +179,8 @@ __device__ __forceinline__ void blend_tile_bwd(int tx, int ty, uint2 rg, const u
         const uint32_t h1 = next_hi(hi_end);
         if (stages(h1)) g_nxt = vals[h1 - 1 - st];
     }
-    for (uint32_t hi = hi_end; hi > rg.x;) {
-        const uint32_t lo = hi - min((uint32_t)BB, hi - rg.x);
+    for (uint32_t hi = hi_end; hi > L;) {
+        const uint32_t lo = hi - min((uint32_t)BB, hi - L);
         const int nb = (int)(hi - lo);
         if constexpr (NT == BB) {
             if ((int)st < nb) {
@@ -264,7 +274,7 @@ __global__ void __launch_bounds__(64) k_blend_fwd_sub(const uint2* __restrict__ 
                                                       const float4* __restrict__ rec, BlendParams P,
                                                       float* __restrict__ img, float* __restrict__ T_final,
                                                       uint32_t* __restrict__ n_contrib,
-                                                      const uint32_t* __restrict__ info) {
+                                                      const uint32_t* __restrict__ info, SegLayout seg) {
     pdl_wait();
     constexpr int SUB = TS / 8;
     __shared__ float4 s_a[64];
@@ -272,10 +282,13 @@ __global__ void __launch_bounds__(64) k_blend_fwd_sub(const uint2* __restrict__ 
     if (info[kInfoAbort]) return;
     const int tile = blockIdx.x / (SUB * SUB), q = blockIdx.x % (SUB * SUB);
     const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-    blend_tile_fwd<8, 64>(tx * SUB + q % SUB, ty * SUB + q / SUB, P.width, P.height, ranges[tile], vals, rec,
-                          P.alpha_min, P.alpha_max, P.t_min, P.bg, s_a, s_c, img, T_final, n_contrib);
+    blend_tile_fwd<8, 64, true>(tx * SUB + q % SUB, ty * SUB + q / SUB, P.width, P.height, ranges[tile], vals, rec,
+                                P.alpha_min, P.alpha_max, P.t_min, P.bg, s_a, s_c, img, T_final, n_contrib, seg,
+                                blockIdx.x);
 }
 
+// The backward of a block's whole walk (no walk segments: the forward cut none,
+// or the frame has no room for them).
 template <int TS>
 __global__ void __launch_bounds__(32, 32) k_blend_bwd_sub(const uint2* __restrict__ ranges,
                                                           const uint32_t* __restrict__ vals,
@@ -293,23 +306,90 @@ __global__ void __launch_bounds__(32, 32) k_blend_bwd_sub(const uint2* __restric
                       g2d);
 }
 
+// The backward over walk segments: one-warp CTAs, all resident, take work from
+// one counter: first the segments the forward closed, then each block's last
+// segment (its whole walk when it closed none). Every piece walks at most
+// kSegStride list positions (unless the pool ran out), so no block's long walk
+// sets the kernel's length.
+template <int TS>
+__global__ void __launch_bounds__(32, 32) k_blend_bwd_segs(const uint2* __restrict__ ranges,
+                                                           const uint32_t* __restrict__ vals,
+                                                           const float4* __restrict__ rec, BlendParams P,
+                                                           const float* __restrict__ dL,
+                                                           const float* __restrict__ T_final,
+                                                           const uint32_t* __restrict__ n_contrib,
+                                                           float4* __restrict__ g2d,
+                                                           const uint32_t* __restrict__ info, SegLayout seg) {
+    pdl_wait();
+    constexpr int SUB = TS / 8;
+    if (info[kInfoAbort]) return;
+    const uint32_t items = min(seg.ctrl->slots_used, seg.slots);  // closed segments, by pool slot
+    const uint32_t total = items + seg.blocks;                       // then each block's last segment
+    for (;;) {
+        uint32_t u = 0;
+        if (threadIdx.x == 0) u = atomicAdd(&seg.ctrl->next, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= total) break;
+        uint32_t block, lo, hi, slot = kSegNone;
+        if (u < items) {
+            const uint4 it = seg.items[u];
+            if (it.x == kSegNone) continue;  // a slot taken ahead and not used
+            block = it.x;
+            lo = it.y;
+            hi = it.z;
+            slot = it.w;
+        } else {
+            block = u - items;
+            const uint4 l = seg.last[block];
+            if (l.y == kSegNone) continue;  // its last segment holds no blend
+            lo = l.y;
+            hi = l.z;
+        }
+        const int tile = (int)(block / (SUB * SUB)), q = (int)(block % (SUB * SUB));
+        const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+        blend_tile_bwd<8>(tx * SUB + q % SUB, ty * SUB + q / SUB, ranges[tile], vals, rec, P, dL, T_final,
+                          n_contrib, g2d, lo, hi, slot == kSegNone ? nullptr : seg.pool + (size_t)slot * 64);
+        __syncthreads();  // the shared staging of the next piece
+    }
+}
+
 }  // namespace
+
+// Walk segments of the sub-tile blends of frame f (off for 8-pixel tiles and
+// when the frame's depth-item buffers cannot hold a useful pool).
+SegLayout frame_segments(const igs_frame& f) {
+    if (f.tile != 16 && f.tile != 32) return SegLayout{};
+    const SortScratch s = sort_scratch(f);
+    const int64_t sub = f.tile / 8;
+    return seg_layout(s.seg_base, s.seg_bytes, (int64_t)f.tiles_x * f.tiles_y * sub * sub);
+}
 
 cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t st) {
     const unsigned tiles = (unsigned)(f.tiles_x * f.tiles_y);
     if (tiles == 0) return cudaSuccess;
     auto rg = reinterpret_cast<const uint2*>(f.ranges);
     auto rec = reinterpret_cast<const float4*>(f.rec);
+    const SegLayout seg = frame_segments(f);
     cudaError_t e = cudaSuccess;
+    if (seg.slots) {  // a fresh list of segments for this forward
+        ZeroRanges z = {};
+        z.ptr[0] = seg.ctrl;
+        z.bytes[0] = sizeof(SegCtrl);
+        z.count = 1;
+        if ((e = launch_zero(z, st)) != cudaSuccess) return e;
+    }
     switch (f.tile) {
         case 8: k_blend_fwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
-        case 16: e = launch_pdl(k_blend_fwd_sub<16>, dim3(tiles * 4), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
-        case 32: e = launch_pdl(k_blend_fwd_sub<32>, dim3(tiles * 16), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
+        case 16: e = launch_pdl(k_blend_fwd_sub<16>, dim3(tiles * 4), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info, seg); break;
+        case 32: e = launch_pdl(k_blend_fwd_sub<32>, dim3(tiles * 16), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info, seg); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();
     return e != cudaSuccess ? e : cudaGetLastError();
 }
+
+// The segmented backward: one-warp CTAs, 32 resident per SM.
+constexpr unsigned kSegCtas = 152 * 32;
 
 cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const float* dL, float* g2d, cudaStream_t st) {
     const unsigned tiles = (unsigned)(f.tiles_x * f.tiles_y);
@@ -317,15 +397,38 @@ cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const fl
     auto rg = reinterpret_cast<const uint2*>(f.ranges);
     auto rec = reinterpret_cast<const float4*>(f.rec);
     auto g = reinterpret_cast<float4*>(g2d);
+    const SegLayout seg = frame_segments(f);
     cudaError_t e = cudaSuccess;
     switch (f.tile) {
         case 8: k_blend_bwd<8><<<tiles, 32, 0, st>>>(rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 16: e = launch_pdl(k_blend_bwd_sub<16>, dim3(tiles * 4), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
-        case 32: e = launch_pdl(k_blend_bwd_sub<32>, dim3(tiles * 16), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info); break;
+        case 16:
+            if (seg.slots)
+                e = launch_pdl(k_blend_bwd_segs<16>, dim3(kSegCtas), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info, seg);
+            else
+                e = launch_pdl(k_blend_bwd_sub<16>, dim3(tiles * 4), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info);
+            break;
+        case 32:
+            if (seg.slots)
+                e = launch_pdl(k_blend_bwd_segs<32>, dim3(kSegCtas), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info, seg);
+            else
+                e = launch_pdl(k_blend_bwd_sub<32>, dim3(tiles * 16), dim3(32), 0, st, rg, f.vals, rec, bp, dL, f.T_final, f.n_contrib, g, f.info);
+            break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// The backward's work counter of frame f (zeroed with the 2D gradient before
+// each backward), or nullptr when the frame has no walk segments.
+void* blend_bwd_counter(const igs_frame& f) {
+    const SegLayout seg = frame_segments(f);
+    return seg.slots ? &seg.ctrl->next : nullptr;
+}
+
+const uint32_t* blend_segments_used(const igs_frame& f) {
+    const SegLayout seg = frame_segments(f);
+    return seg.slots ? &seg.ctrl->slots_used : nullptr;
 }
 
 }  // namespace igs

@@ -37,6 +37,13 @@ __device__ __forceinline__ bool may_reach(float4 a, float xlo, float xhi, float 
     return !(eval_dist(cx, cy, a).pw > a.w);
 }
 
+// Block-wide last blend (max of last, +1 positions) into *s_hi of the caller's
+// shared memory.
+__device__ __forceinline__ void seg_reduce_into(uint32_t last, int lane, uint32_t* s_hi) {
+    const uint32_t whi = __reduce_max_sync(0xffffffffu, last);
+    if (lane == 0) atomicMax(s_hi, whi);
+}
+
 // One CTA of TS*TS threads composites one tile (one thread per pixel), staging
 // B entries at a time in shared memory (s_a, s_c hold B float4 each), and leaves
 // the batch loop once every pixel has stopped. Each warp owns an 8 x 4 block of
@@ -44,14 +51,33 @@ __device__ __forceinline__ bool may_reach(float4 a, float xlo, float xhi, float 
 // their pixels stop at similar depths) and walks, in order, only the staged
 // entries that may reach it (one ballot per 32 entries). Writes img (planar,
 // `plane` floats per channel, row stride `width`) and, if given, T_final /
-// n_contrib.
-template <int TS, int B>
+// n_contrib. SEG (one 8 x 8 block per CTA): the walk is cut into segments for
+// the backward (SegLayout), `block` naming this block.
+template <int TS, int B, bool SEG = false>
 __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int height, uint2 rg,
                                                const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
                                                float alpha_min, float alpha_max, float t_min, const float* bg,
                                                float4* s_a, float4* s_c, float* __restrict__ img,
-                                               float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
+                                               float* __restrict__ T_final, uint32_t* __restrict__ n_contrib,
+                                               const SegLayout seg = SegLayout{}, uint32_t block = 0) {
     constexpr int NT = TS * TS;
+    static_assert(!SEG || NT == 64, "segments are cut per 8 x 8 block, one thread per pixel");
+    // segment state: where the open segment starts (the last cut), the block's
+    // last blend, and the slots of the segments closed so far
+    __shared__ uint32_t s_lo, s_hi, s_slot, s_n, s_stop;
+    __shared__ uint32_t s_slots[SEG ? kSegMaxPerBlock : 1];
+    uint32_t reserved = kSegNone;  // thread 0: the pool slot taken for the next close (its atomic
+                                   // is in flight meanwhile, off the block's path)
+    const bool segs = SEG && seg.slots != 0;
+    if (segs) {
+        if (threadIdx.x == 0) {
+            s_lo = 0;
+            s_hi = 0;
+            s_n = 0;
+            s_stop = 0;
+        }
+        __syncthreads();
+    }
     constexpr int BPR = TS / 8;  // 8 x 4 warp blocks per block row of the tile
     static_assert(B <= NT, "staging batch larger than the tile");
     static_assert(TS >= 8 && TS <= 32, "the tile holds whole 8 x 4 warp blocks");
@@ -83,6 +109,39 @@ __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int he
     }
     for (uint32_t b0 = rg.x; b0 < rg.y; b0 += B) {
         if (__syncthreads_count(done) == NT) break;
+        if constexpr (SEG) {
+            const uint32_t P = b0 - rg.x;
+            if (segs && P > 0 && P % kSegStride == 0) {
+                // close the open segment here if it holds blends: each pixel's state is
+                // that after every entry before P (its colour is turned into the colour
+                // behind once the walk has ended)
+                seg_reduce_into(last, lane, &s_hi);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    uint32_t slot = kSegNone;
+                    if (s_hi > s_lo && !s_stop && s_n < kSegMaxPerBlock) {  // blends since the last cut
+                        if (reserved == kSegNone) {  // first close: this slot and the next one
+                            slot = atomicAdd(&seg.ctrl->slots_used, 2u);
+                            reserved = slot + 1;
+                        } else {
+                            slot = reserved;
+                            reserved = atomicAdd(&seg.ctrl->slots_used, 1u);
+                        }
+                        if (slot >= seg.slots) {
+                            slot = kSegNone;
+                            s_stop = 1;  // pool full: the block's last segment takes the rest
+                        } else {
+                            seg.items[slot] = make_uint4(block, s_lo, s_hi, slot);
+                            s_slots[s_n++] = slot;
+                            s_lo = P;
+                        }
+                    }
+                    s_slot = slot;
+                }
+                __syncthreads();
+                if (s_slot != kSegNone) seg.pool[(size_t)s_slot * 64 + threadIdx.x] = make_float4(T, C0, C1, C2);
+            }
+        }
         if (stager) {
             const uint32_t j = b0 + threadIdx.x;
             if (j < rg.y) {
@@ -121,6 +180,26 @@ __device__ __forceinline__ void blend_tile_fwd(int tx, int ty, int width, int he
                 C2 = fmaf(c.z, w, C2);
                 T = Tn;
                 last = b0 - rg.x + k + 1;
+            }
+        }
+    }
+    if constexpr (SEG) {
+        if (segs) {
+            seg_reduce_into(last, lane, &s_hi);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                // (no segment closed: the last segment is the whole walk; lo = kSegNone:
+                // no blend after the last cut)
+                seg.last[block] = s_n == 0 ? make_uint4(0u, 0u, kSegNone, 0u)
+                                           : make_uint4(s_n, s_hi > s_lo ? s_lo : kSegNone, s_hi, 0u);
+                if (reserved != kSegNone && reserved < seg.slots)
+                    seg.items[reserved] = make_uint4(kSegNone, 0u, 0u, kSegNone);  // taken, not used
+            }
+            // the saved colours become the colour composited behind each cut
+            for (uint32_t i = 0; i < s_n; ++i) {
+                float4* q = seg.pool + (size_t)s_slots[i] * 64 + threadIdx.x;
+                const float4 v = *q;
+                *q = make_float4(v.x, fmaf(T, bg[0], C0 - v.y), fmaf(T, bg[1], C1 - v.z), fmaf(T, bg[2], C2 - v.w));
             }
         }
     }

@@ -193,6 +193,11 @@ cudaError_t launch_project_bwd_adam(const igs_scene& sc, const ViewParams& vp, c
 cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t s);
 cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t s);
+// The segmented backward's work counter of a frame (4 bytes, 16-byte aligned), to
+// be zeroed before each launch_blend_bwd; nullptr when the frame has none.
+void* blend_bwd_counter(const igs_frame& f);
+// The pool slots the last forward of a frame took; nullptr when it has no segments.
+const uint32_t* blend_segments_used(const igs_frame& f);
 cudaError_t launch_blend_bwd(const igs_frame& f, const BlendParams& bp, const float* dL, float* g2d,
                              cudaStream_t s);
 cudaError_t launch_l1(const float* img, const float* target, int64_t count, float* loss, float* grad,
@@ -288,12 +293,60 @@ struct SortScratch {
     uint32_t* walk_rows;              // [tiles_y] list starts, first level-2 chunks, chunk sizes; [1] chunk total
     uint32_t* walk_h2;                // [level-2 chunks][tiles_x] level-2 tile counts per chunk, then slots
     uint2* walk_rect;                 // [n] rectangle of order[p] (level-1 count writes, level-1 place reads)
+    void* seg_base;                   // the depth items' buffers (ditems_a, ditems_b), reused by the blends'
+    size_t seg_bytes;                 // walk segments once binning is done
     int64_t walk_chunks;              // > 0: counting sort of the entries; 0: duplication + tile radix passes
     int tile_passes;
     int tile_bits;
 };
 SortScratch sort_scratch(const igs_frame& f);
 size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t tiles_y, int64_t chunks);
+
+// Walk segments of the one-view blends (16- and 32-pixel binning tiles, one
+// 8 x 8 pixel block per CTA). A block whose walk is long closes a segment at
+// a list position that is a multiple of kSegStride when the open segment holds
+// blends: it saves each pixel's state there (T, and the colour composited
+// behind that position, once the walk has ended) in a pool slot, so that the
+// backward can walk every segment in parallel instead of one block walking its
+// whole list. A closed segment is items[slot] = (block, lo, hi, slot): list
+// positions relative to the tile's first entry, lo = the cut it starts at, hi =
+// one past its last blend, the state at hi in pool[slot]; a slot taken but not used
+// holds block = kSegNone. A block's last segment, which ends with the final
+// state (T_final and the background), is last[block] = (segments closed, lo,
+// hi, -); lo = kSegNone when it holds no blend. The pieces live in the frame's
+// depth-sort item buffers, which binning no longer needs once the entries are
+// placed.
+constexpr uint32_t kSegStride = 1024;        // list positions; a multiple of the forward's 64-entry batches
+constexpr uint32_t kSegNone = 0xFFFFFFFFu;
+constexpr int kSegMaxPerBlock = 64;          // segments a block closes at most (the rest stay in its last one)
+struct SegCtrl {                             // all zeroed before each forward; next (the
+    uint32_t next, slots_used, pad0, pad1;   // backward's work counter) also before each backward
+};
+struct SegLayout {
+    SegCtrl* ctrl;
+    uint4* last;      // [blocks] (closed, lo, hi, -) of each block's last segment
+    uint4* items;     // [slots] (block, lo, hi, slot) of each closed segment
+    float4* pool;     // [slots][64] (T, S_r, S_g, S_b) per pixel of the block, pixel = row * 8 + column
+    uint32_t slots;   // 0: segments off
+    uint32_t blocks;
+};
+// Carved from [base, base + bytes) for `blocks` 8 x 8 blocks (slots = 0 when it does not fit).
+__host__ __device__ inline SegLayout seg_layout(void* base, size_t bytes, int64_t blocks) {
+    SegLayout L{};
+    const size_t head = 256 + (((size_t)blocks * 16 + 255) & ~(size_t)255);
+    if (!base || bytes < head + 1040 || blocks <= 0 || blocks >= (1 << 24)) return L;
+    int64_t slots = (int64_t)((bytes - head) / 1040);  // 16 B item + 1 KB of pixel states per slot
+    if (slots > (1 << 20)) slots = 1 << 20;
+    char* p = static_cast<char*>(base);
+    L.ctrl = reinterpret_cast<SegCtrl*>(p);
+    L.last = reinterpret_cast<uint4*>(p + 256);
+    L.items = reinterpret_cast<uint4*>(p + head);
+    L.pool = reinterpret_cast<float4*>(p + head + (((size_t)slots * 16 + 255) & ~(size_t)255));
+    if ((size_t)(reinterpret_cast<char*>(L.pool) - p) + (size_t)slots * 1024 > bytes) --slots;
+    L.slots = slots > 0 ? (uint32_t)slots : 0;
+    L.blocks = (uint32_t)blocks;
+    return L;
+}
 int64_t sort_walk_chunks(int64_t tiles_x, int64_t tiles_y);
 int tile_passes_for(int64_t tiles);
 

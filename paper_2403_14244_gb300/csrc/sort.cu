@@ -876,6 +876,8 @@ SortScratch sort_scratch(const igs_frame& f) {
     auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
     s.ditems_a = (u64*)take((size_t)n * 8);
     s.ditems_b = (u64*)take((size_t)n * 8);
+    s.seg_base = s.ditems_a;
+    s.seg_bytes = 2 * align256((size_t)n * 8);
     s.items_a = (u64*)take((size_t)cap * entry);
     s.items_b = (u64*)take((size_t)cap * 8);
     s.hist = (uint32_t*)take(8 * kRadix * 4);

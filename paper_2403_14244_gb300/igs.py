@@ -143,6 +143,7 @@ SYMBOLS = {
     "igs_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double,
                            C.c_double, C.c_double, C.c_int64, C.c_void_p]),
     "igs_frame_status": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_uint32), C.c_void_p]),
+    "igs_frame_walk_segments": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(C.c_int64), C.c_void_p]),
     "igs_frame_reset_status": (C.c_int, [C.POINTER(IgsFrame), C.c_void_p]),
     "igs_debug_silence_lookback_once": (None, []),
     "igs_sort_depth_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -599,6 +600,15 @@ def frame_status(frame: Frame, stream=None):
     if st not in (OK, ERR_CAPACITY, ERR_DEVICE_TIMEOUT):
         _check(st, "igs_frame_status")
     return st, list(info)
+
+
+def frame_walk_segments(frame: Frame, stream=None):
+    """Pool slots the frame's last forward blend took for walk segments (-1: the
+    frame has none); synchronises the stream."""
+    out = C.c_int64(0)
+    _check(load().igs_frame_walk_segments(C.byref(frame.struct), C.byref(out), _stream(stream)),
+           "igs_frame_walk_segments")
+    return int(out.value)
 
 
 _WORD_DTYPES = tuple(d for d in (torch.int32, getattr(torch, "uint32", None)) if d is not None)

@@ -11,7 +11,7 @@ import oracle
 from paper_2403_14244_gb300 import igs, scenes
 from paper_2403_14244_gb300.render import TrainStep
 from tests import _gpu
-from tests._tiny import random_small
+from tests._tiny import random_small, scene_from, small_camera
 
 pytestmark = pytest.mark.gpu
 
@@ -306,3 +306,28 @@ def test_chained_steps_and_graphs_match_plain_steps():
         states.append(torch.cat([ts.flat, ts.m, ts.v]).cpu().numpy())
     np.testing.assert_allclose(states[1], states[0], rtol=1e-4, atol=1e-6)
     np.testing.assert_allclose(states[2], states[0], rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+def test_backward_long_walks_cut_into_segments(tile):
+    """Many faint, wide Gaussians over a small image: no pixel saturates, so each
+    8 x 8 block walks thousands of its tile's entries and the forward cuts the
+    walks into segments of 1024 list positions, which the backward walks in
+    parallel from the saved states. The gradients match the oracle's as a single
+    reverse walk's do; the image is unaffected."""
+    rng = np.random.default_rng(47)
+    n = 5000
+    cam = small_camera(64, 48, 80.0)
+    means = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.45, 0.45, n), rng.uniform(-0.5, 0.5, n)], 1)
+    # opacity 0.0042-0.006: only the core of each disc blends (alpha >= 1/255), a
+    # few hundred Gaussians per pixel, and no pixel reaches t_min
+    sc = scene_from(means, rng.uniform(0.3, 0.6, n), rng.uniform(0.0042, 0.006, n), rng.uniform(0, 1, (n, 3)))
+    W = rng.normal(size=(3, cam.height, cam.width))
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile)
+    assert igs.frame_walk_segments(f) > 20            # the walks were cut
+    ref = oracle.render(sc, cam, mode=1, flag_margin=1e-5)
+    assert ref["T"].min() > 2e-4 and ref["last"].max() > 4000   # no pixel stops; walks of ~5000 entries
+    # opacities this close to 1/255 put some 2 % of pixels within the oracle's
+    # margin of an alpha_min decision (flagged, left out of the comparison)
+    _gpu.compare_images(img, ref["img"], ref["flag"], atol=2e-4, max_flag_frac=0.03)
+    _compare(sc, cam, W, tile=tile)
