@@ -326,29 +326,35 @@ __device__ __forceinline__ Chunk l1_chunk(uint32_t c, uint32_t cmax, const uint3
 
 // A warp's stable placement of one chunk whose items each span a contiguous
 // range of buckets [lo, hi], one batch of 32 items (one per lane, in order) at
-// a time, in three passes over each item's buckets: mark the item's lane bit
-// in the bucket's mask; slot = bucket cursor + earlier lanes in the mask; the
-// highest lane of the mask advances the cursor by the mask's size and clears
-// it. Items go to a shared-memory stage grouped by bucket and leave as one run
-// per bucket written by consecutive lanes (a chunk too large for the stage
-// writes its items directly). Items are of type T (the value an item takes in
-// bucket q comes from a functor); the stage holds S of them. Shared memory:
-// words(B) 32-bit words, an even count (8-byte items stay aligned).
+// a time. Each lane marks its bit at the start of its range (smask[lo]) and
+// past its end (emask[hi + 1]); a warp-wide XOR prefix over the batch's
+// buckets turns the marks into each bucket's covering mask (the lanes whose
+// range holds it: a bit marked at both ends cancels); an item's slot in
+// bucket q = the bucket's cursor + the earlier lanes of the covering mask, and
+// each bucket's cursor then advances by the mask's size. Two marks per item
+// instead of one per (item, bucket), and no per-bucket pass diverges but the
+// slot writes. Items go to a shared-memory stage grouped by bucket and leave
+// as one run per bucket written by consecutive lanes (a chunk too large for
+// the stage writes its items directly). Items are of type T (the value an item
+// takes in bucket q comes from a functor); the stage holds S of them. Shared
+// memory: words(B) 32-bit words, an even count (8-byte items stay aligned).
 template <typename T, uint32_t S>
 struct Placer {
-    uint32_t *pos, *mask, *first, *lstart;
+    uint32_t *pos, *smask, *emask, *cov, *first, *lstart;
     T* stage;
     uint32_t B;
     bool staged;
     __host__ __device__ static constexpr uint32_t words(uint32_t B) {
-        return 4 * B + 2 + S * (uint32_t)(sizeof(T) / 4);
+        return 6 * B + 6 + S * (uint32_t)(sizeof(T) / 4);
     }
     __device__ __forceinline__ Placer(uint32_t* ws, uint32_t nb) : B(nb), staged(false) {
         pos = ws;
-        mask = pos + nb;
-        first = mask + nb;
-        lstart = first + nb;
-        stage = reinterpret_cast<T*>(lstart + nb + 2);  // 4 nb + 2 words: even
+        smask = pos + nb;          // nb + 1 words
+        emask = smask + nb + 1;    // nb + 2 words
+        cov = emask + nb + 2;      // nb words
+        first = cov + nb;
+        lstart = first + nb;       // nb + 1 words (+ 2 pad)
+        stage = reinterpret_cast<T*>(ws + 6 * nb + 6);
     }
     // first_slot(q): the chunk's first slot in bucket q of the output; count(q): its items there
     template <typename First, typename Count>
@@ -356,6 +362,10 @@ struct Placer {
         for (uint32_t q = lane; q < B; q += 32) {  // coalesced, independent loads
             first[q] = first_slot(q);
             lstart[q] = count(q);
+        }
+        for (uint32_t q = lane; q < B + 2; q += 32) {
+            emask[q] = 0u;
+            if (q <= B) smask[q] = 0u;
         }
         __syncwarp();
         const uint32_t per = (B + 31) / 32, q0 = min(B, lane * per), q1 = min(B, q0 + per);
@@ -372,7 +382,6 @@ struct Placer {
         uint32_t run = incl - sum;
         for (uint32_t q = q0; q < q1; ++q) {
             const uint32_t c = lstart[q];
-            mask[q] = 0u;
             lstart[q] = run;
             pos[q] = staged ? run : first[q];
             run += c;
@@ -384,23 +393,45 @@ struct Placer {
     template <typename Item>
     __device__ __forceinline__ void batch(uint32_t lo, uint32_t hi, Item item, int lane, T* __restrict__ out) {
         const uint32_t bit = 1u << lane, lt = bit - 1u;
-        for (uint32_t q = lo; q <= hi; ++q) atomicOr(&mask[q], bit);
+        const bool any = lo <= hi;
+        if (any) {
+            atomicOr(&smask[lo], bit);
+            atomicOr(&emask[hi + 1], bit);
+        }
+        const uint32_t qmin = __reduce_min_sync(0xffffffffu, any ? lo : 0xFFFFFFFFu);
+        const uint32_t qmax = __reduce_max_sync(0xffffffffu, any ? hi : 0u);
+        if (qmin > qmax) return;  // warp-uniform: no item spans a bucket
+        __syncwarp();
+        // covering masks: lanes whose span holds q = XOR of start and end marks up to q
+        uint32_t carry = 0u;
+        for (uint32_t base = qmin; base <= qmax; base += 32) {
+            const uint32_t q = base + lane;
+            uint32_t x = q <= qmax ? (smask[q] ^ emask[q]) : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x ^= y;
+            }
+            x ^= carry;
+            if (q <= qmax) cov[q] = x;
+            carry = __shfl_sync(0xffffffffu, x, 31);
+        }
         __syncwarp();
         for (uint32_t q = lo; q <= hi; ++q) {
-            const uint32_t at = pos[q] + __popc(mask[q] & lt);
+            const uint32_t at = pos[q] + __popc(cov[q] & lt);
             const T v = item(q);
             if (staged) stage[at] = v; else out[at] = v;
         }
         __syncwarp();
-        // the highest lane of a mask advances the bucket and clears the mask; any
-        // other lane reads either a mask with a higher bit or zero, and does nothing
-        for (uint32_t q = lo; q <= hi; ++q) {
-            const uint32_t m = mask[q];
-            if ((m >> lane) == 1u) {
-                pos[q] += __popc(m);
-                mask[q] = 0u;
+        for (uint32_t base = qmin; base <= qmax; base += 32) {
+            const uint32_t q = base + lane;
+            if (q <= qmax) {
+                pos[q] += __popc(cov[q]);
+                smask[q] = 0u;
+                emask[q] = 0u;
             }
         }
+        if (lane == 0) emask[qmax + 1] = 0u;  // ends past the last bucket of the batch
         __syncwarp();
     }
     // staged chunk: every bucket's run to out[first[q] ...], consecutive lanes
@@ -437,8 +468,30 @@ struct DiscRef {
 using Placer1 = Placer<u64, kStage1>;      // level 1: (column span << 32 | Gaussian id) items
 using Placer2 = Placer<uint32_t, kStage>;  // level 2: Gaussian ids
 
+// In place: the warp turns the difference counts d[0..B) (+1 where an item's
+// bucket range starts, -1 past its end) into each bucket's item count, and
+// writes count q to out(q). Lanes take consecutive runs of buckets.
+template <typename Out>
+__device__ __forceinline__ void diff_to_counts(const uint32_t* d, uint32_t B, int lane, Out out) {
+    const uint32_t per = (B + 31) / 32, q0 = min(B, lane * per), q1 = min(B, q0 + per);
+    uint32_t sum = 0;
+    for (uint32_t q = q0; q < q1; ++q) sum += d[q];
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;  // modulo 2^32: the prefix of the differences is a count
+    for (uint32_t q = q0; q < q1; ++q) {
+        run += d[q];
+        out(q, run);
+    }
+}
+
 // Level 1, count: for each of its chunks c (grid-stride over warps), a warp adds,
-// for each Gaussian of the chunk, one to every row of its rectangle; writes
+// for each Gaussian of the chunk, one to every row of its rectangle (as +1 at
+// its first row and -1 past its last, summed along the rows at the end); writes
 // column c of H1 [rows][cmax], and the rectangles in depth order (srect[p] =
 // rect[order[p]]) so that the placement reads them without a gather.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* __restrict__ order,
@@ -449,12 +502,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* 
     pdl_wait();
     extern __shared__ uint32_t s_walk[];
     const int lane = threadIdx.x & 31;
-    uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * rows;
+    uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * (rows + 1);  // difference counts
     if (info[kInfoAbort]) return;
     const uint32_t used = l1_chunk(0, cmax, info).used;
     for (uint32_t c = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); c < used; c += gridDim.x * kWalkWarps) {
         const Chunk ch = l1_chunk(c, cmax, info);
-        for (uint32_t y = lane; y < rows; y += 32) cnt[y] = 0u;
+        for (uint32_t y = lane; y <= rows; y += 32) cnt[y] = 0u;
         __syncwarp();
         for (uint32_t b = ch.p0; b < ch.p1; b += 32 * kWalkUnroll) {
             uint32_t g[kWalkUnroll];
@@ -471,11 +524,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* 
                 if (g[k] != 0xFFFFFFFFu) srect[b + k * 32 + lane] = r;  // the placement reads it in order
             }
 #pragma unroll
-            for (int k = 0; k < kWalkUnroll; ++k)
-                for (uint32_t y = ry[k] & 0xFFFF; y <= (ry[k] >> 16); ++y) atomicAdd(&cnt[y], 1u);
+            for (int k = 0; k < kWalkUnroll; ++k) {
+                const uint32_t y0 = ry[k] & 0xFFFF, y1 = ry[k] >> 16;
+                if (y0 <= y1) {
+                    atomicAdd(&cnt[y0], 1u);
+                    atomicAdd(&cnt[y1 + 1], 0xFFFFFFFFu);
+                }
+            }
         }
         __syncwarp();
-        for (uint32_t y = lane; y < rows; y += 32) H1[(size_t)y * cmax + c] = cnt[y];
+        diff_to_counts(cnt, rows, lane, [&](uint32_t y, uint32_t v) { H1[(size_t)y * cmax + c] = v; });
+        __syncwarp();  // the next chunk clears what this one read
     }
 }
 
@@ -632,7 +691,8 @@ __device__ __forceinline__ RowChunk l2_chunk(uint32_t j, uint32_t rows, const ui
 
 // Level 2, count: for each of its chunks j, a warp adds, for each item of the
 // chunk, one to every tile of the row that the item's Gaussian touches (the
-// span the item carries); writes row j of H2 [chunks][tiles_x].
+// span the item carries, as +1 at its first tile and -1 past its last, summed
+// along the row at the end); writes row j of H2 [chunks][tiles_x].
 __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const u64* __restrict__ R1, uint32_t rows,
                                                                 uint32_t tiles_x, const uint32_t* __restrict__ len,
                                                                 const uint32_t* __restrict__ rowinfo,
@@ -641,12 +701,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const u64* __res
     pdl_wait();
     extern __shared__ uint32_t s_walk[];
     const int lane = threadIdx.x & 31;
-    uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * tiles_x;
+    uint32_t* cnt = s_walk + (size_t)(threadIdx.x >> 5) * (tiles_x + 1);  // difference counts
     if (info[kInfoAbort]) return;
     const uint32_t total = rowinfo[3 * rows];
     for (uint32_t j = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); j < total; j += gridDim.x * kWalkWarps) {
         const RowChunk rc = l2_chunk(j, rows, rowinfo, len);
-        for (uint32_t x = lane; x < tiles_x; x += 32) cnt[x] = 0u;
+        for (uint32_t x = lane; x <= tiles_x; x += 32) cnt[x] = 0u;
         __syncwarp();
         for (uint32_t b = rc.i0; b < rc.i1; b += 32 * kWalkUnroll) {
             uint32_t sp[kWalkUnroll];
@@ -656,12 +716,18 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_count(const u64* __res
                 sp[k] = i < rc.i1 ? (uint32_t)(R1[i] >> 32) : 1u;  // (1, 0): no tiles
             }
 #pragma unroll
-            for (int k = 0; k < kWalkUnroll; ++k)
-                for (uint32_t x = sp[k] & 0xFFFFu; x <= (sp[k] >> 16); ++x) atomicAdd(&cnt[x], 1u);
+            for (int k = 0; k < kWalkUnroll; ++k) {
+                const uint32_t x0 = sp[k] & 0xFFFFu, x1 = sp[k] >> 16;
+                if (x0 <= x1) {
+                    atomicAdd(&cnt[x0], 1u);
+                    atomicAdd(&cnt[x1 + 1], 0xFFFFFFFFu);
+                }
+            }
         }
         __syncwarp();
         uint32_t* out = H2 + (size_t)j * tiles_x;
-        for (uint32_t x = lane; x < tiles_x; x += 32) out[x] = cnt[x];
+        diff_to_counts(cnt, tiles_x, lane, [&](uint32_t x, uint32_t v) { out[x] = v; });
+        __syncwarp();  // the next chunk clears what this one read
     }
 }
 
@@ -1001,7 +1067,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         // 3a. two-level counting sort: Gaussians into tile-row lists, then row items into tiles
         const uint32_t rows = (uint32_t)f.tiles_y, cols = (uint32_t)f.tiles_x;
         u64* R1 = s.items_b;  // level-1 lists: free until the keys are exported (as tile_key) into it
-        const size_t count1 = (size_t)kWalkWarps * rows * 4, count2 = (size_t)kWalkWarps * cols * 4;
+        const size_t count1 = (size_t)kWalkWarps * (rows + 1) * 4, count2 = (size_t)kWalkWarps * (cols + 1) * 4;
         const size_t place1 = (size_t)kWalkWarps * Placer1::words(rows) * 4;
         const size_t place2 = (size_t)kWalkWarps * Placer2::words(cols) * 4;
         if (std::max(place1, place2) > 48 * 1024) CK(walk_opt_in());
