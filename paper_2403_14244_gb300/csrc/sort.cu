@@ -50,6 +50,18 @@ namespace {
 // Difference grid kept in shared memory by the preparation kernel up to this many cells.
 constexpr int kGridSmemCells = 10240;
 
+// Counting sort of the entries (route a), below.
+constexpr int kRowWalkMax = 2048;          // tiles per axis for route a (shared-memory buckets)
+constexpr uint32_t kL1ChunksMax = 16384;   // most level-1 chunks (columns of H1), fewer for tall frames
+constexpr uint32_t kL1ChunksMin = 1024;
+constexpr uint32_t kH1Words = 1u << 22;    // H1 budget: rows x chunks
+constexpr uint32_t kStage = 1536;          // staged entries per level-2 chunk
+constexpr uint32_t kChunkTarget = kStage * 4 / 5;
+constexpr uint32_t kStage1 = 768;          // staged 8-byte items per level-1 chunk
+constexpr uint32_t kChunkTarget1 = kStage1 * 4 / 5;
+constexpr int kWalkWarps = 4;              // warps per CTA of the walk kernels (one chunk each)
+constexpr int kWalkUnroll = 4;             // items per lane per round of the counting walks
+
 // Depth-digit histograms of all n depth keys, the kept count, and for every kept
 // Gaussian, in each tile row, +1 at its first touched tile and -1 past its last
 // in the (tiles_y+1) x (tiles_x+1) grid (a prefix sum along each row then gives
@@ -58,21 +70,27 @@ constexpr int kGridSmemCells = 10240;
 // column, then along each row). Each thread has kPrepUnroll Gaussians in flight;
 // the top byte of a view's depths is mostly one value, so a warp whose lanes
 // share it adds its count once instead of 32 times to one shared-memory word.
+// With rowd (the counting-sort route), also +1 at the first row of every kept
+// Gaussian's rectangle and -1 past its last in rowd[tiles_y + 1] (a prefix
+// sum over the rows then gives each tile row's level-1 list length); on the
+// shared-memory grid these sit after the grid's cells.
 constexpr int kPrepUnroll = 4;
 template <bool SMEM_GRID>
 __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ depth_key, const uint2* __restrict__ rect,
                                                   const float4* __restrict__ disc, int tile, int footprint,
                                                   const uint32_t* __restrict__ count, uint32_t n, int gx,
                                                   int gy, uint32_t* __restrict__ hist, int32_t* __restrict__ grid,
-                                                  uint32_t* __restrict__ info) {
+                                                  int32_t* __restrict__ rowd, uint32_t* __restrict__ info) {
     pdl_wait();
     extern __shared__ int32_t s_grid[];
     __shared__ uint32_t s_h[4][kRadix];
     const int cells = gx * gy;
+    const int rowd_cells = rowd ? gy : 0;
+    int32_t* rd = SMEM_GRID ? s_grid + cells : rowd;
     const int lane = threadIdx.x & 31;
     for (int k = threadIdx.x; k < 4 * kRadix; k += blockDim.x) (&s_h[0][0])[k] = 0;
     if (SMEM_GRID)
-        for (int k = threadIdx.x; k < cells; k += blockDim.x) s_grid[k] = 0;
+        for (int k = threadIdx.x; k < cells + rowd_cells; k += blockDim.x) s_grid[k] = 0;
     __syncthreads();
     int32_t* g = SMEM_GRID ? s_grid : grid;
     const float inv = 1.0f / (float)tile;
@@ -115,6 +133,10 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
             if (cnt[u]) {
                 ++kept;
                 const int y0 = r[u].x >> 16, y1 = r[u].y >> 16;
+                if (rowd) {
+                    atomicAdd(&rd[y0], 1);
+                    atomicAdd(&rd[y1 + 1], -1);
+                }
                 if (SMEM_GRID && footprint == 0) {  // the rectangle's four corners (a 2D difference)
                     const int x0 = r[u].x & 0xFFFF, x1 = r[u].y & 0xFFFF;
                     atomicAdd(&g[y0 * gx + x0], 1);
@@ -140,9 +162,12 @@ __global__ void __launch_bounds__(256) k_bin_prep(const uint32_t* __restrict__ d
         const uint32_t v = (&s_h[0][0])[k];
         if (v) atomicAdd(&hist[k], v);
     }
-    if (SMEM_GRID)
+    if (SMEM_GRID) {
         for (int k = threadIdx.x; k < cells; k += blockDim.x)
             if (s_grid[k]) atomicAdd(&grid[k], s_grid[k]);
+        for (int k = threadIdx.x; k < rowd_cells; k += blockDim.x)
+            if (s_grid[cells + k]) atomicAdd(&rowd[k], s_grid[cells + k]);
+    }
 }
 
 // Inclusive prefix of the difference grid along each row: afterwards grid[y][x]
@@ -180,14 +205,70 @@ __device__ __forceinline__ void publish_tile_total(unsigned long long* s_total, 
     }
 }
 
+// Row layout of the counting sort, by one block of NT threads once the tile
+// ranges are known (after publish_tile_total). len[y]: the kept Gaussians whose
+// rectangle spans tile row y (prefix of the row differences rowd), the length
+// of row y's level-1 list. rowinfo = [rows] list starts (prefix of len),
+// [rows] first level-2 chunk, [rows] items per level-2 chunk, [1] level-2 chunk
+// total. A row's level-2 chunks take about kChunkTarget entries each:
+// kChunkTarget * len / entries items, at least 32, where the row's entries are
+// rowstart[y + 1] - rowstart[y] (rowstart[y]: the first entry of the row's
+// tiles, held in column tiles_x of the grid g; rowstart[rows] = M). Records an
+// error if the chunks exceed max_chunks.
+template <int NT>
+__device__ __forceinline__ void row_layout(const int32_t* __restrict__ rowd, const int32_t* g, int gx, uint32_t rows,
+                                           uint32_t tiles_x, uint32_t M, uint32_t max_chunks,
+                                           uint32_t* __restrict__ len, uint32_t* __restrict__ rowinfo,
+                                           uint32_t* __restrict__ info, uint32_t* s_warp) {
+    __syncthreads();  // the row starts, written by other threads
+    auto rowstart = [&](uint32_t y) { return y < rows ? (uint32_t)g[(size_t)y * gx + tiles_x] : M; };
+    const uint32_t per = (rows + NT - 1) / NT;
+    const uint32_t y0 = min(rows, threadIdx.x * per), y1 = min(rows, y0 + per);
+    uint32_t dsum = 0;
+    for (uint32_t y = y0; y < y1; ++y) dsum += (uint32_t)rowd[y];
+    const uint32_t lfirst = block_excl_scan<NT>(dsum, s_warp);  // modulo 2^32: the differences' prefix
+    uint32_t items = 0, chunks = 0, run = lfirst;
+    for (uint32_t y = y0; y < y1; ++y) {
+        run += (uint32_t)rowd[y];
+        const uint32_t ly = run;
+        const uint64_t entries = rowstart(y + 1) - rowstart(y);
+        const uint32_t size =
+            (uint32_t)max((uint64_t)32, entries ? (uint64_t)kChunkTarget * ly / entries : (uint64_t)kChunkTarget);
+        len[y] = ly;
+        rowinfo[2 * rows + y] = size;
+        items += ly;
+        chunks += (ly + size - 1) / size;
+    }
+    uint32_t start = block_excl_scan<NT>(items, s_warp);
+    uint32_t base = block_excl_scan<NT>(chunks, s_warp);
+    if (threadIdx.x == NT - 1) {
+        rowinfo[3 * rows] = base + chunks;
+        if (base + chunks > max_chunks) record_error(info, IGS_ERR_CUDA);  // never expected: chunks are bounded
+    }
+    run = lfirst;
+    for (uint32_t y = y0; y < y1; ++y) {
+        run += (uint32_t)rowd[y];
+        const uint32_t size = rowinfo[2 * rows + y];
+        rowinfo[y] = start;
+        rowinfo[rows + y] = base;
+        start += run;
+        base += (run + size - 1) / size;
+    }
+}
+
 // One block: tile ranges = exclusive scan of the per-tile counts (row-major tile
-// order), (0, 0) for empty tiles; digit histograms of the tile-id passes.
+// order), (0, 0) for empty tiles; digit histograms of the tile-id passes; with
+// rowd, the row layout of the counting sort (row_layout).
 constexpr int kTileScanThreads = 1024;
-__global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* __restrict__ grid, int gx, int tiles_x,
+__global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* grid, int gx, int tiles_x,
                                                                 uint32_t tiles, int passes,
                                                                 uint2* __restrict__ ranges,
                                                                 uint32_t* __restrict__ hist_tile,
-                                                                uint32_t* __restrict__ info, uint64_t capacity) {
+                                                                uint32_t* __restrict__ info, uint64_t capacity,
+                                                                int32_t* __restrict__ grid_w,
+                                                                const int32_t* __restrict__ rowd,
+                                                                uint32_t max_chunks, uint32_t* __restrict__ len,
+                                                                uint32_t* __restrict__ rowinfo) {
     __shared__ uint32_t s_h[4][kRadix];
     __shared__ uint32_t s_warp[kTileScanThreads / 32];
     __shared__ unsigned long long s_total;
@@ -201,6 +282,7 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* _
     uint32_t start = block_excl_scan<kTileScanThreads>(sum, s_warp);
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t c = (uint32_t)grid[(size_t)(t / tiles_x) * gx + (t % tiles_x)];
+        if (rowd && t % tiles_x == 0) grid_w[(size_t)(t / tiles_x) * gx + tiles_x] = (int32_t)start;  // row start
         ranges[t] = c ? make_uint2(start, start + c) : make_uint2(0u, 0u);
         start += c;
         if (c)
@@ -208,17 +290,27 @@ __global__ void __launch_bounds__(kTileScanThreads) k_tile_scan(const int32_t* _
     }
     publish_tile_total(&s_total, sum, capacity, info);
     for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) hist_tile[k] = (&s_h[0][0])[k];
+    if (rowd) {
+        __threadfence_block();
+        row_layout<kTileScanThreads>(rowd, grid_w, gx, tiles / tiles_x, tiles_x,
+                                     (uint32_t)min(s_total, (unsigned long long)0xFFFFFFFFu), max_chunks, len,
+                                     rowinfo, info, s_warp);
+    }
 }
 
 // One block, grid in shared memory (cells <= kGridSmemCells): the row prefix of
-// the difference grid, the tile ranges, the tile-digit histograms, and every digit
-// histogram (4 depth + `passes` tile rows) turned into exclusive offsets.
+// the difference grid, the tile ranges, the tile-digit histograms, every digit
+// histogram (4 depth + `passes` tile rows) turned into exclusive offsets, and
+// with rowd the row layout of the counting sort (row_layout).
 constexpr int kTilesSmallThreads = 1024;
 __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_t* __restrict__ grid, int tiles_x,
                                                                     int tiles_y, int passes, int diff2d,
                                                                     uint2* __restrict__ ranges,
                                                                     uint32_t* __restrict__ hist,
-                                                                    uint32_t* __restrict__ info, uint64_t capacity) {
+                                                                    uint32_t* __restrict__ info, uint64_t capacity,
+                                                                    const int32_t* __restrict__ rowd,
+                                                                    uint32_t max_chunks, uint32_t* __restrict__ len,
+                                                                    uint32_t* __restrict__ rowinfo) {
     pdl_wait();
     extern __shared__ int32_t s_g[];
     __shared__ uint32_t s_h[8][kRadix];
@@ -257,6 +349,7 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
     uint32_t start = block_excl_scan<kTilesSmallThreads>(sum, s_warp);
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t c = (uint32_t)s_g[(t / tiles_x) * gx + (t % tiles_x)];
+        if (t % tiles_x == 0) s_g[(t / tiles_x) * gx + tiles_x] = (int32_t)start;  // row start (column tiles_x is free)
         ranges[t] = c ? make_uint2(start, start + c) : make_uint2(0u, 0u);
         start += c;
         if (c)
@@ -280,6 +373,10 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
         const int idx = tid + r * kTilesSmallThreads;
         if (idx < rows * kRadix) hist[idx] = v[r];
     }
+    if (rowd)
+        row_layout<kTilesSmallThreads>(rowd, s_g, gx, (uint32_t)tiles_y, (uint32_t)tiles_x,
+                                       (uint32_t)min(s_total, (unsigned long long)0xFFFFFFFFu), max_chunks, len,
+                                       rowinfo, info, s_warp);
 }
 
 // ---- counting sort of the entries by tile (route a) ----
@@ -293,17 +390,6 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
 // down each bucket over the chunks, and walks the chunks again placing items.
 // Placement keeps order within a bucket (Placer below). Chunks are sized
 // so that their items fill about 4/5 of a shared-memory stage.
-
-constexpr int kRowWalkMax = 2048;          // tiles per axis for route a (shared-memory buckets)
-constexpr uint32_t kL1ChunksMax = 16384;   // most level-1 chunks (columns of H1), fewer for tall frames
-constexpr uint32_t kL1ChunksMin = 1024;
-constexpr uint32_t kH1Words = 1u << 22;    // H1 budget: rows x chunks
-constexpr uint32_t kStage = 1536;          // staged entries per level-2 chunk
-constexpr uint32_t kChunkTarget = kStage * 4 / 5;
-constexpr uint32_t kStage1 = 768;          // staged 8-byte items per level-1 chunk
-constexpr uint32_t kChunkTarget1 = kStage1 * 4 / 5;
-constexpr int kWalkWarps = 4;              // warps per CTA of the walk kernels (one chunk each)
-constexpr int kWalkUnroll = 4;             // items per lane per round of the counting walks
 
 // Level-1 chunk c: positions [p0, p1) of the depth order among the kept
 // Gaussians; `used` chunks hold Gaussians. A chunk takes about kChunkTarget1 /
@@ -538,64 +624,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_count(const uint32_t* 
     }
 }
 
-// Row layout. rowinfo = [rows] list starts, [rows] first level-2 chunk, [rows]
-// items per level-2 chunk, [1] level-2 chunk total. A row's chunk takes about
-// kChunkTarget entries: kChunkTarget * items / entries of the row items, at
-// least 32. Records an error if the chunks exceed `max_chunks`. One block of NT
-// threads; len is read through L2 (other blocks wrote it).
-constexpr int kRowScanThreads = 1024;
-template <int NT>
-__device__ __forceinline__ void row_layout(const uint32_t* __restrict__ len, const uint2* __restrict__ ranges,
-                                           uint32_t rows, uint32_t tiles_x, uint32_t max_chunks,
-                                           uint32_t* __restrict__ rowinfo, uint32_t* __restrict__ info,
-                                           unsigned long long* s_entries, uint32_t* s_warp) {
-    for (uint32_t y = threadIdx.x; y < rows; y += NT) s_entries[y] = 0ull;
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < rows * tiles_x; t += NT) {
-        const uint2 r = __ldcg(ranges + t);
-        if (r.y > r.x) atomicAdd(&s_entries[t / tiles_x], (unsigned long long)(r.y - r.x));
-    }
-    __syncthreads();
-    const uint32_t per = (rows + NT - 1) / NT;
-    const uint32_t y0 = min(rows, threadIdx.x * per), y1 = min(rows, y0 + per);
-    uint32_t items = 0, chunks = 0;
-    for (uint32_t y = y0; y < y1; ++y) {
-        const uint64_t entries = s_entries[y];
-        const uint32_t ly = __ldcg(len + y);
-        const uint32_t size =
-            (uint32_t)max((uint64_t)32, entries ? (uint64_t)kChunkTarget * ly / entries : (uint64_t)kChunkTarget);
-        rowinfo[2 * rows + y] = size;
-        items += ly;
-        chunks += (ly + size - 1) / size;
-    }
-    uint32_t start = block_excl_scan<NT>(items, s_warp);
-    uint32_t base = block_excl_scan<NT>(chunks, s_warp);
-    if (threadIdx.x == NT - 1) {
-        rowinfo[3 * rows] = base + chunks;
-        if (base + chunks > max_chunks) record_error(info, IGS_ERR_CUDA);  // never expected: chunks are bounded
-    }
-    for (uint32_t y = y0; y < y1; ++y) {
-        const uint32_t ly = __ldcg(len + y);
-        rowinfo[y] = start;
-        rowinfo[rows + y] = base;
-        start += ly;
-        base += (ly + rowinfo[2 * rows + y] - 1) / rowinfo[2 * rows + y];
-    }
-}
-
 // Level 1, scan: block y turns row y of H1 (the used chunks' counts) into
-// exclusive offsets in place and writes the row's item count to len[y]; the
-// last block to finish (a ticket on `done`, zero on entry) lays out the rows.
+// exclusive offsets in place. The row's total must equal len[y], the list
+// length the row layout was built from (both count the kept Gaussians whose
+// rectangle spans row y); a difference records an error and aborts the frame
+// before any placement.
+constexpr int kRowScanThreads = 1024;
 __global__ void __launch_bounds__(kRowScanThreads) k_rows_scan(uint32_t* __restrict__ H1, uint32_t cmax,
-                                                               uint32_t* __restrict__ len,
-                                                               const uint2* __restrict__ ranges, uint32_t tiles_x,
-                                                               uint32_t max_chunks, uint32_t* __restrict__ rowinfo,
-                                                               uint32_t* __restrict__ done,
+                                                               const uint32_t* __restrict__ len,
                                                                uint32_t* __restrict__ info) {
     pdl_wait();
     __shared__ uint32_t s_warp[kRowScanThreads / 32];
-    __shared__ unsigned long long s_entries[kRowWalkMax];
-    __shared__ bool s_last;
     if (info[kInfoAbort]) return;
     uint32_t* row = H1 + (size_t)blockIdx.x * cmax;
     const uint32_t used = l1_chunk(0, cmax, info).used;
@@ -604,19 +643,13 @@ __global__ void __launch_bounds__(kRowScanThreads) k_rows_scan(uint32_t* __restr
     uint32_t sum = 0;
     for (uint32_t c = c0; c < c1; ++c) sum += row[c];
     uint32_t run = block_excl_scan<kRowScanThreads>(sum, s_warp);
-    if (threadIdx.x == kRowScanThreads - 1) len[blockIdx.x] = run + sum;
+    if (threadIdx.x == kRowScanThreads - 1 && run + sum != len[blockIdx.x])
+        record_error(info, IGS_ERR_CUDA);  // never expected: the row counts disagree
     for (uint32_t c = c0; c < c1; ++c) {
         const uint32_t h = row[c];
         row[c] = run;
         run += h;
     }
-    __threadfence();  // len[y] before the ticket
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    row_layout<kRowScanThreads>(len, ranges, gridDim.x, tiles_x, max_chunks, rowinfo, info, s_entries, s_warp);
 }
 
 // Level 1, place: a warp walks each of its chunks again and puts each Gaussian
@@ -920,7 +953,7 @@ size_t sort_scratch_bytes(int64_t n, int64_t capacity, int64_t tiles_x, int64_t 
     b += align256((size_t)(tp > 0 ? tp : 1) * bc * kRadix * 4);              // status_tile
     b += align256((size_t)bs * 8);                                           // scan_status
     b += align256((size_t)(ceil_div(capacity, kDupTile) + 1) * 4);           // dup_start
-    b += align256((size_t)(2 * tiles + 2) * 4);                              // grid
+    b += align256((size_t)(2 * tiles + 2 + tiles_y + 1) * 4);                // grid, row differences
     b += align256((size_t)chunks * rows * 4);                                // walk_h1 [rows][chunks]
     b += align256((size_t)rows * 4);                                         // walk_len
     b += align256((size_t)(3 * rows + 1) * 4);                               // walk_rows
@@ -952,7 +985,7 @@ SortScratch sort_scratch(const igs_frame& f) {
     s.status_tile = (uint32_t*)take((size_t)(s.tile_passes > 0 ? s.tile_passes : 1) * bc * kRadix * 4);
     s.scan_status = (unsigned long long*)take((size_t)bs * 8);
     s.dup_start = (uint32_t*)take((size_t)(ceil_div(cap, kDupTile) + 1) * 4);
-    s.grid = (int32_t*)take((size_t)(2 * tiles + 2) * 4);
+    s.grid = (int32_t*)take((size_t)(2 * tiles + 2 + f.tiles_y + 1) * 4);
     const int64_t rows = chunks > 0 ? f.tiles_y : 0;
     s.walk_h1 = (uint32_t*)take((size_t)chunks * rows * 4);
     s.walk_len = (uint32_t*)take((size_t)rows * 4);
@@ -995,30 +1028,34 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         add(s.counters, 16 * 4);
         add(s.status_depth, (size_t)4 * bn * kRadix * 4);
         if (tp > 0) add(s.status_tile, (size_t)tp * bc * kRadix * 4);
-        add(s.scan_status, (size_t)bs * 8);
-        add(s.grid, (size_t)gx * gy * 4);
+        if (s.walk_chunks == 0) add(s.scan_status, (size_t)bs * 8);
+        add(s.grid, (size_t)(gx * gy + (s.walk_chunks > 0 ? gy : 0)) * 4);  // grid (route a: and row differences)
         if (n == 0) add(f.ranges, (size_t)tiles * 8);
         CK(launch_zero(z, st));
     }
     if (n == 0) return cudaSuccess;
     const uint32_t nn = (uint32_t)n;
+    const bool walk = s.walk_chunks > 0;
+    int32_t* rowd = walk ? s.grid + (size_t)gx * gy : nullptr;  // row differences (route a)
+    const uint32_t max2 = walk ? (uint32_t)l2_chunks_max(cap, f.tiles_y) : 0u;
     // 0. depth-digit histograms; footprint rows -> per-tile counts -> ranges, tile-digit histograms
     const int prep_blocks = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 4);
     if ((int64_t)gx * gy <= kGridSmemCells)
-        CK(launch_pdl(k_bin_prep<true>, dim3(prep_blocks), dim3(256), (size_t)gx * gy * 4, st, 
+        CK(launch_pdl(k_bin_prep<true>, dim3(prep_blocks), dim3(256), (size_t)(gx * gy + (walk ? gy : 0)) * 4, st,
             f.depth_key, reinterpret_cast<const uint2*>(f.rect), reinterpret_cast<const float4*>(f.disc), f.tile,
-            footprint, f.count, nn, gx, gy, s.hist, s.grid, f.info));
+            footprint, f.count, nn, gx, gy, s.hist, s.grid, rowd, f.info));
     else
         CK(launch_pdl(k_bin_prep<false>, dim3(prep_blocks), dim3(256), 0, st, f.depth_key, reinterpret_cast<const uint2*>(f.rect),
                                                        reinterpret_cast<const float4*>(f.disc), f.tile, footprint,
-                                                       f.count, nn, gx, gy, s.hist, s.grid, f.info));
+                                                       f.count, nn, gx, gy, s.hist, s.grid, rowd, f.info));
     count_launches();
     CK(cudaGetLastError());
     if ((int64_t)gx * gy <= kGridSmemCells) {
         CK(launch_pdl(k_tiles_small, dim3(1), dim3(kTilesSmallThreads), (size_t)gx * gy * 4, st, s.grid, f.tiles_x, f.tiles_y, tp,
                       footprint == 0 ? 1 : 0,
                                                                            reinterpret_cast<uint2*>(f.ranges), s.hist,
-                                                                           f.info, (uint64_t)cap));
+                                                                           f.info, (uint64_t)cap, rowd, max2,
+                                                                           s.walk_len, s.walk_rows));
         count_launches();
         CK(cudaGetLastError());
     } else {
@@ -1027,7 +1064,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         CK(cudaGetLastError());
         k_tile_scan<<<1, kTileScanThreads, 0, st>>>(s.grid, gx, f.tiles_x, (uint32_t)tiles, tp,
                                                     reinterpret_cast<uint2*>(f.ranges), s.hist + 4 * kRadix, f.info,
-                                                    (uint64_t)cap);
+                                                    (uint64_t)cap, s.grid, rowd, max2, s.walk_len, s.walk_rows);
         count_launches();
         CK(cudaGetLastError());
         k_hist_to_offsets<<<1, 1024, 0, st>>>(s.hist, 4 + tp);
@@ -1071,7 +1108,6 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         const size_t place1 = (size_t)kWalkWarps * Placer1::words(rows) * 4;
         const size_t place2 = (size_t)kWalkWarps * Placer2::words(cols) * 4;
         if (std::max(place1, place2) > 48 * 1024) CK(walk_opt_in());
-        const int64_t max2 = l2_chunks_max(cap, rows);
         const uint32_t cmax = (uint32_t)s.walk_chunks;
 
         const uint2* rect = reinterpret_cast<const uint2*>(f.rect);
@@ -1079,8 +1115,7 @@ cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t st) 
         CK(launch_pdl(k_rows_count, dim3(walk_blocks((const void*)k_rows_count, count1, cmax)), dim3(32 * kWalkWarps), count1, st, f.order, rect, rows, cmax, s.walk_h1, s.walk_rect, f.info));
         count_launches();
         CK(cudaGetLastError());
-        CK(launch_pdl(k_rows_scan, dim3(rows), dim3(kRowScanThreads), 0, st, s.walk_h1, cmax, s.walk_len, rg, cols,
-                      (uint32_t)max2, s.walk_rows, s.counters + 12, f.info));
+        CK(launch_pdl(k_rows_scan, dim3(rows), dim3(kRowScanThreads), 0, st, s.walk_h1, cmax, s.walk_len, f.info));
         count_launches();
         CK(cudaGetLastError());
         const DiscRef disc{rect, reinterpret_cast<const float4*>(f.disc), f.tile, 1.0f / (float)f.tile, footprint};
