@@ -163,13 +163,19 @@ IGS_API igs_status igs_project(const igs_scene* scene, const igs_camera* cam, co
                        igs_frame* frame, void* stream);
 
 /* Order the kept Gaussians front to back (stable radix sort of the
- * depth keys; ties keep index order), scan their tile counts, duplicate each
- * into one entry per touched tile in that order, stable radix sort of the
- * entries by tile id, and per-tile ranges. The resulting entry order is that of
- * the 64-bit key (tile << 32 | depth bits) sorted stably: within a tile, front
- * to back as Eq. 4 requires. If M exceeds frame->capacity, info[2] is set to
- * IGS_ERR_CAPACITY, info[3] to M, and the later steps leave their outputs
- * untouched. Writes order, offset, tile_key, vals, ranges, info. */
+ * depth keys; ties keep index order), count every tile's entries from the
+ * footprints (the per-tile ranges), and place one entry per (Gaussian, touched
+ * tile) in tile order, front to back within each tile. Frames at most 2048
+ * tiles wide and high (frame->sort_chunks > 0) place the entries by two stable
+ * counting sorts (Gaussians into the lists of the tile rows they span, then
+ * each row's list into its tiles); wider frames duplicate each Gaussian, in
+ * depth order, into one (tile, Gaussian) item per touched tile and radix sort
+ * the items by tile id (and write offset). Either way the entry order is that
+ * of the 64-bit key (tile << 32 | depth bits) sorted stably: within a tile,
+ * front to back as Eq. 4 requires. If M exceeds frame->capacity, info[2] is
+ * set to IGS_ERR_CAPACITY, info[3] to M, and the later steps leave their
+ * outputs untouched. Writes order, vals, ranges, info (and offset on the
+ * radix route). */
 IGS_API igs_status igs_bin_sort(igs_frame* frame, const igs_opts* opts, void* stream);
 
 /* Front-to-back order of n depth keys WITHOUT allocating anything. The paper

@@ -285,7 +285,8 @@ struct SortScratch {
     uint32_t* status_tile;            // [tile_passes][blocks(capacity)][256]
     unsigned long long* scan_status;  // [scan blocks(n)]
     uint32_t* dup_start;              // [blocks(capacity) + 1] first Gaussian (in depth order) of each duplication block
-    int32_t* grid;                    // [(tiles_y + 1) * (tiles_x + 1)] rectangle corner counts -> per-tile counts
+    int32_t* grid;                    // [(tiles_y + 1) * (tiles_x + 1)] rectangle corner counts -> per-tile counts,
+                                      // then (counting-sort route) [tiles_y + 1] tile-row differences
     uint32_t* vals;                   // sorted values: in the item buffer the last tile pass does not read
     uint32_t* tile_key;               // exported tile ids: in the item buffer the last tile pass reads
     uint32_t* walk_h1;                // [tiles_y][walk_chunks] level-1 row counts per chunk, then offsets
