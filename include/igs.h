@@ -233,6 +233,24 @@ IGS_API igs_status igs_project_bwd(const igs_scene* scene, const igs_camera* cam
                                    const igs_frame* frame, const float* g2d, float* d_means_sigma,
                                    float* d_opacity, float* d_color, void* stream);
 
+/* The forward and the first half of the adjoint of a training step (Eq. 4 and
+ * its adjoint, Eq. 3 for the screen-space parameters), with the clearing of
+ * the 2D gradient moved into the forward: igs_render_fwd_clear is
+ * igs_render_fwd that also sets g2d ([n][8] floats, device, 16-byte aligned) to
+ * zero, its CTAs writing the zeros while they blend (the forward is bound by
+ * instruction issue, not by memory); igs_blend_bwd_acc is igs_blend_bwd
+ * without the clearing: it accumulates into g2d as that forward left it. Use
+ * them as a pair on one frame and stream, one igs_blend_bwd_acc per
+ * igs_render_fwd_clear, with nothing writing g2d in between (the forward also
+ * resets the backward's work counter of the frame). Same outputs as
+ * igs_render_fwd + igs_blend_bwd; g2d is cleared even when the frame is
+ * aborted (capacity), as igs_blend_bwd does. Errors as igs_render_fwd /
+ * igs_blend_bwd; a NULL or unaligned g2d returns IGS_ERR_INVALID_ARG. */
+IGS_API igs_status igs_render_fwd_clear(igs_frame* frame, const igs_opts* opts, float* img, float* g2d,
+                                        void* stream);
+IGS_API igs_status igs_blend_bwd_acc(const igs_frame* frame, const igs_opts* opts, const float* dL_dimg,
+                                     float* g2d, void* stream);
+
 /* The projection backward fused with one Adam step, for training: the same
  * gradient as igs_project_bwd, applied at once to the parameters without
  * writing it out. scene->means_sigma, scene->opacity and scene->color (device,

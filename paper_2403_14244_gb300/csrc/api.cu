@@ -248,6 +248,27 @@ igs_status igs_render_fwd(igs_frame* frame, const igs_opts* opts, float* img, vo
     return cuda_status(igs::launch_blend_fwd(*frame, bp, img, (cudaStream_t)stream), "igs_render_fwd");
 }
 
+igs_status igs_render_fwd_clear(igs_frame* frame, const igs_opts* opts, float* img, float* g2d, void* stream) {
+    igs_status st;
+    if ((st = check_opts(opts)) || (st = check_frame(frame)) || (st = frame_matches(frame, nullptr, nullptr, opts)))
+        return st;
+    if (!img || !g2d) return fail(IGS_ERR_INVALID_ARG, "img or g2d is NULL");
+    if (reinterpret_cast<uintptr_t>(g2d) & 15) return fail(IGS_ERR_INVALID_ARG, "g2d must be 16-byte aligned");
+    const igs::BlendParams bp = blend_params(frame, opts);
+    return cuda_status(igs::launch_blend_fwd(*frame, bp, img, (cudaStream_t)stream, g2d), "igs_render_fwd_clear");
+}
+
+igs_status igs_blend_bwd_acc(const igs_frame* frame, const igs_opts* opts, const float* dL_dimg, float* g2d,
+                             void* stream) {
+    igs_status st;
+    if ((st = check_opts(opts)) || (st = check_frame(frame)) || (st = frame_matches(frame, nullptr, nullptr, opts)))
+        return st;
+    if (!dL_dimg || !g2d) return fail(IGS_ERR_INVALID_ARG, "dL_dimg or g2d is NULL");
+    if (reinterpret_cast<uintptr_t>(g2d) & 15) return fail(IGS_ERR_INVALID_ARG, "g2d must be 16-byte aligned");
+    const igs::BlendParams bp = blend_params(frame, opts);
+    return cuda_status(igs::launch_blend_bwd(*frame, bp, dL_dimg, g2d, (cudaStream_t)stream), "igs_blend_bwd_acc");
+}
+
 igs_status igs_blend_bwd(const igs_frame* frame, const igs_opts* opts, const float* dL_dimg, float* g2d,
                          void* stream) {
     igs_status st;

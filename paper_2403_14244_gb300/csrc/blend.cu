@@ -20,15 +20,27 @@
 namespace igs {
 namespace {
 
+// Zeros to n4 float4 at p (none if p is null), spread over the grid: the
+// forward blend of a training step clears the 2D gradient for the adjoint that
+// follows. The blend is bound by instruction issue and leaves HBM mostly idle,
+// so the stores cost it a few instructions per thread, not a pass of their own.
+__device__ __forceinline__ void clear_slice(float4* __restrict__ p, uint64_t n4) {
+    if (!p) return;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 template <int TS>
 __global__ void __launch_bounds__(TS* TS) k_blend_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                       const float4* __restrict__ rec, BlendParams P,
                                                       float* __restrict__ img, float* __restrict__ T_final,
                                                       uint32_t* __restrict__ n_contrib,
-                                                      const uint32_t* __restrict__ info) {
+                                                      const uint32_t* __restrict__ info, float4* __restrict__ clear,
+                                                      uint64_t clear4) {
     constexpr int NT = TS * TS;
     __shared__ float4 s_a[NT];
     __shared__ float4 s_c[NT];
+    clear_slice(clear, clear4);
     if (info[kInfoAbort]) return;
     const int tile = blockIdx.x;
     blend_tile_fwd<TS, NT>(tile % P.tiles_x, tile / P.tiles_x, P.width, P.height, ranges[tile], vals, rec, P.alpha_min,
@@ -274,11 +286,13 @@ __global__ void __launch_bounds__(64) k_blend_fwd_sub(const uint2* __restrict__ 
                                                       const float4* __restrict__ rec, BlendParams P,
                                                       float* __restrict__ img, float* __restrict__ T_final,
                                                       uint32_t* __restrict__ n_contrib,
-                                                      const uint32_t* __restrict__ info, SegLayout seg) {
+                                                      const uint32_t* __restrict__ info, SegLayout seg,
+                                                      float4* __restrict__ clear, uint64_t clear4) {
     pdl_wait();
     constexpr int SUB = TS / 8;
     __shared__ float4 s_a[64];
     __shared__ float4 s_c[64];
+    clear_slice(clear, clear4);
     if (info[kInfoAbort]) return;
     const int tile = blockIdx.x / (SUB * SUB), q = blockIdx.x % (SUB * SUB);
     const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
@@ -364,9 +378,18 @@ SegLayout frame_segments(const igs_frame& f) {
     return seg_layout(s.seg_base, s.seg_bytes, (int64_t)f.tiles_x * f.tiles_y * sub * sub);
 }
 
-cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t st) {
+cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t st, float* clear_g2d) {
     const unsigned tiles = (unsigned)(f.tiles_x * f.tiles_y);
-    if (tiles == 0) return cudaSuccess;
+    auto clear = reinterpret_cast<float4*>(clear_g2d);
+    const uint64_t clear4 = clear_g2d ? 2 * (uint64_t)f.n : 0;  // [n][8] floats
+    if (tiles == 0) {  // nothing to blend; the gradient is still cleared for the adjoint
+        if (!clear || clear4 == 0) return cudaSuccess;
+        ZeroRanges z = {};
+        z.ptr[0] = clear;
+        z.bytes[0] = clear4 * 16;
+        z.count = 1;
+        return launch_zero(z, st);
+    }
     auto rg = reinterpret_cast<const uint2*>(f.ranges);
     auto rec = reinterpret_cast<const float4*>(f.rec);
     const SegLayout seg = frame_segments(f);
@@ -379,9 +402,9 @@ cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* i
         if ((e = launch_zero(z, st)) != cudaSuccess) return e;
     }
     switch (f.tile) {
-        case 8: k_blend_fwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info); break;
-        case 16: e = launch_pdl(k_blend_fwd_sub<16>, dim3(tiles * 4), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info, seg); break;
-        case 32: e = launch_pdl(k_blend_fwd_sub<32>, dim3(tiles * 16), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info, seg); break;
+        case 8: k_blend_fwd<8><<<tiles, 64, 0, st>>>(rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info, clear, clear4); break;
+        case 16: e = launch_pdl(k_blend_fwd_sub<16>, dim3(tiles * 4), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info, seg, clear, clear4); break;
+        case 32: e = launch_pdl(k_blend_fwd_sub<32>, dim3(tiles * 16), dim3(64), 0, st, rg, f.vals, rec, bp, img, f.T_final, f.n_contrib, f.info, seg, clear, clear4); break;
         default: return cudaErrorInvalidValue;
     }
     count_launches();

@@ -192,7 +192,11 @@ cudaError_t launch_project_bwd_adam(const igs_scene& sc, const ViewParams& vp, c
                                     const igs_frame* f_next = nullptr);
 cudaError_t launch_bin_sort(const igs_frame& f, int footprint, cudaStream_t s);
 cudaError_t launch_export_keys(const igs_frame& f, uint64_t* keys, cudaStream_t s);
-cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t s);
+// clear_g2d (optional, [n][8] floats, 16-byte aligned): zeroed by the blend's
+// CTAs for the adjoint that follows (the frame's backward work counter is
+// zeroed with the segment list whenever the frame has walk segments).
+cudaError_t launch_blend_fwd(const igs_frame& f, const BlendParams& bp, float* img, cudaStream_t s,
+                             float* clear_g2d = nullptr);
 // The segmented backward's work counter of a frame (4 bytes, 16-byte aligned), to
 // be zeroed before each launch_blend_bwd; nullptr when the frame has none.
 void* blend_bwd_counter(const igs_frame& f);

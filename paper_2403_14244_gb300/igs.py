@@ -97,6 +97,9 @@ SYMBOLS = {
     "igs_render_bwd": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts), C.POINTER(IgsFrame),
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_blend_bwd": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(IgsOpts), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "igs_render_fwd_clear": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(IgsOpts), C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
+    "igs_blend_bwd_acc": (C.c_int, [C.POINTER(IgsFrame), C.POINTER(IgsOpts), C.c_void_p, C.c_void_p, C.c_void_p]),
     "igs_project_bwd": (C.c_int, [C.POINTER(IgsScene), C.POINTER(IgsCamera), C.POINTER(IgsOpts),
                                   C.POINTER(IgsFrame), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
@@ -245,6 +248,16 @@ def _check_color_width(scene, sh_degree, where):
                          f"sh_degree {sh_degree} needs {want}")
 
 
+def _check_g2d(frame, g2d, where):
+    """The 2D gradient that a call clears or accumulates into: a contiguous
+    float32 tensor of at least 8 floats per Gaussian of the frame (the kernels
+    write 2 n float4 there)."""
+    if not isinstance(g2d, torch.Tensor) or g2d.dtype != torch.float32 or not g2d.is_contiguous():
+        raise ValueError(f"{where}: g2d must be a contiguous float32 tensor")
+    if g2d.numel() < 8 * frame.n:
+        raise ValueError(f"{where}: g2d holds {g2d.numel()} floats, the frame needs {8 * frame.n}")
+
+
 class Scene:
     """Device scene: means_sigma [N,4], opacity [N], color [N,C] (FP32, CUDA)."""
 
@@ -378,6 +391,20 @@ def render_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, dL_dimg, 
 def blend_bwd(frame: Frame, o: IgsOpts, dL_dimg, g2d, stream=None):
     _check(load().igs_blend_bwd(C.byref(frame.struct), C.byref(o), _ptr(dL_dimg), _ptr(g2d), _stream(stream)),
            "igs_blend_bwd")
+
+
+def render_fwd_clear(frame: Frame, o: IgsOpts, img, g2d, stream=None):
+    """render_fwd that also zeroes g2d ([n][8] float32) for blend_bwd_acc."""
+    _check_g2d(frame, g2d, "render_fwd_clear")
+    _check(load().igs_render_fwd_clear(C.byref(frame.struct), C.byref(o), _ptr(img), _ptr(g2d), _stream(stream)),
+           "igs_render_fwd_clear")
+
+
+def blend_bwd_acc(frame: Frame, o: IgsOpts, dL_dimg, g2d, stream=None):
+    """blend_bwd into a g2d that render_fwd_clear zeroed (no clearing here)."""
+    _check_g2d(frame, g2d, "blend_bwd_acc")
+    _check(load().igs_blend_bwd_acc(C.byref(frame.struct), C.byref(o), _ptr(dL_dimg), _ptr(g2d), _stream(stream)),
+           "igs_blend_bwd_acc")
 
 
 def project_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, d_means_sigma, d_opacity, d_color,

@@ -269,7 +269,7 @@ class TrainStep:
             mark("project")
             igs.bin_sort(frame, r.opts, stream)
             mark("bin_sort")
-            igs.render_fwd(frame, r.opts, img, stream)
+            igs.render_fwd_clear(frame, r.opts, img, self.g2d, stream)  # clears g2d for the adjoint below
         mark("blend_fwd")
         if self.ssim_lambda > 0.0:
             if key not in self._work:
@@ -280,7 +280,10 @@ class TrainStep:
         else:
             igs.l1_loss(img, target, self.loss, dimg, stream)
             mark("l1")
-        igs.blend_bwd(frame, r.opts, dimg, self.g2d, stream)
+        if check:
+            igs.blend_bwd(frame, r.opts, dimg, self.g2d, stream)
+        else:
+            igs.blend_bwd_acc(frame, r.opts, dimg, self.g2d, stream)
         mark("blend_bwd")
         if self.accum is not None:
             igs.grad_accum(self.g2d, frame.count(), self.accum, self.vis, stream)

@@ -331,3 +331,53 @@ def test_backward_long_walks_cut_into_segments(tile):
     # margin of an alpha_min decision (flagged, left out of the comparison)
     _gpu.compare_images(img, ref["img"], ref["flag"], atol=2e-4, max_flag_frac=0.03)
     _compare(sc, cam, W, tile=tile)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_forward_clear_then_accumulating_backward(tile):
+    """igs_render_fwd_clear + igs_blend_bwd_acc (the training step's pair: the
+    forward's CTAs zero g2d, the backward accumulates without a clearing pass)
+    give the image of igs_render_fwd bit for bit and the screen-space gradients
+    of igs_render_fwd + igs_blend_bwd, starting from a g2d full of garbage; the
+    backward's work counter is reset by the forward, so the pair repeats on one
+    frame. An aborted frame (capacity) still leaves g2d cleared."""
+    sc, cam = random_small(3000, 48, w=160, h=96, spread=0.8)
+    W = np.random.default_rng(5).normal(size=(3, cam.height, cam.width))
+    dimg = torch.from_numpy(np.ascontiguousarray(W, np.float32)).cuda()
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=tile)
+    o = r.opts
+    g_ref = torch.full((sc.n, 8), 7.0, device="cuda")
+    igs.blend_bwd(f, o, dimg, g_ref)
+    img_ref = torch.from_numpy(img.astype(np.float32)).cuda()   # the GPU image, back from float64 exactly
+    for _ in range(2):
+        g = torch.full((sc.n, 8), float("nan"), device="cuda")
+        out = torch.full_like(img_ref, -1.0)
+        igs.render_fwd_clear(f, o, out, g)
+        igs.blend_bwd_acc(f, o, dimg, g)
+        torch.cuda.synchronize()
+        assert torch.equal(out, img_ref)
+        a, b = g.cpu().numpy().astype(np.float64), g_ref.cpu().numpy().astype(np.float64)
+        assert np.isfinite(a).all()
+        # float atomics add in a different order from run to run: a few ulp
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max())
+    # capacity overflow: nothing is blended, g2d is still cleared
+    c = igs.camera(cam)
+    small = igs.Frame(scene.n, 16, c, o)
+    igs.project(scene, c, o, small)
+    igs.bin_sort(small, o)
+    g = torch.full((sc.n, 8), 3.0, device="cuda")
+    igs.render_fwd_clear(small, o, torch.zeros_like(img_ref), g)
+    igs.blend_bwd_acc(small, o, dimg, g)
+    st, _ = igs.frame_status(small)
+    assert st == igs.ERR_CAPACITY
+    assert torch.count_nonzero(g).item() == 0
+
+
+def test_forward_clear_binding_refuses_small_g2d():
+    sc, cam = random_small(50, 49, w=32, h=32)
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=16)
+    out = torch.zeros((3, 32, 32), device="cuda")
+    with pytest.raises(ValueError):
+        igs.render_fwd_clear(f, r.opts, out, torch.zeros((sc.n - 1, 8), device="cuda"))
+    with pytest.raises(ValueError):
+        igs.blend_bwd_acc(f, r.opts, out, torch.zeros((sc.n, 8), device="cuda", dtype=torch.float64))
