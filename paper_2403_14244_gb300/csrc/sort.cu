@@ -356,22 +356,34 @@ __global__ void __launch_bounds__(kTilesSmallThreads) k_tiles_small(const int32_
             for (int p = 0; p < passes; ++p) atomicAdd(&s_h[4 + p][(t >> (8 * p)) & 0xFF], c);
     }
     publish_tile_total(&s_total, sum, capacity, info);
-    // exclusive offsets of every histogram row
+    // exclusive offsets of every histogram row: a warp scans 32 consecutive digits of one
+    // row, then adds the totals of the row's earlier warps
     const int rows = 4 + passes;
+    __shared__ uint32_t s_wt[8 * kRadix / 32];
+    const int lane = tid & 31;
     uint32_t v[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int idx = tid + r * kTilesSmallThreads;
-        v[r] = 0;
-        if (idx < rows * kRadix) {
-            const uint32_t* row = &s_h[idx >> 8][0];
-            for (int k = 0; k < (idx & 255); ++k) v[r] += row[k];
+        const uint32_t x = idx < rows * kRadix ? (&s_h[0][0])[idx] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
+        if (lane == 31) s_wt[idx >> 5] = incl;
+        v[r] = incl - x;
     }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int idx = tid + r * kTilesSmallThreads;
-        if (idx < rows * kRadix) hist[idx] = v[r];
+        if (idx < rows * kRadix) {
+            uint32_t base = 0;
+            for (int k = (idx >> 8) * (kRadix / 32); k < (idx >> 5); ++k) base += s_wt[k];
+            hist[idx] = v[r] + base;
+        }
     }
     if (rowd)
         row_layout<kTilesSmallThreads>(rowd, s_g, gx, (uint32_t)tiles_y, (uint32_t)tiles_x,
