@@ -580,7 +580,7 @@ IGS_API igs_status igs_frame_reset_status(igs_frame* frame, void* stream);
  * Multi-view batch: V views of one scene, each with its own pose and image
  * size, rendered by one chain of launches with no host synchronisation: one
  * projection launch over every (view, Gaussian), each view's binning (depth
- * sort and tile lists, as igs_bin_sort) on one of up to 8 streams that run
+ * sort and tile lists, as igs_bin_sort) on one of up to 16 streams that run
  * concurrently, and one blend launch over the tiles of every view (the
  * hardware block scheduler, or for the persistent variant an atomic work
  * counter, balances views of different sizes). The chain can be captured in a

@@ -4,7 +4,7 @@
 //   project all (view, Gaussian) pairs     one launch, grid (blocks, V); the
 //                                          poses come from the device view table
 //   bin and sort each view                 each view's frame as igs_bin_sort does it,
-//                                          the views spread over up to 8 streams
+//                                          the views spread over up to 16 streams
 //                                          that fork from the caller's stream and
 //                                          join it again
 //   batch status                           one block: the views' status words summed
@@ -26,7 +26,7 @@ namespace igs {
 
 namespace {
 
-constexpr int kFanout = 8;  // most streams the views' binnings spread over
+constexpr int kFanout = 16;  // most streams the views' binnings spread over
 
 // Streams and events of one batch (host object behind igs_batch::fanout).
 struct Fanout {

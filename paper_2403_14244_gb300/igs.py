@@ -258,6 +258,27 @@ def _check_g2d(frame, g2d, where):
         raise ValueError(f"{where}: g2d holds {g2d.numel()} floats, the frame needs {8 * frame.n}")
 
 
+def _check_f32(t, need, where, name):
+    """A contiguous float32 tensor of at least `need` elements (a kernel reads or
+    writes that many floats through its pointer)."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{where}: {name} must be a contiguous float32 tensor")
+    if t.numel() < need:
+        raise ValueError(f"{where}: {name} holds {t.numel()} floats, {need} needed")
+
+
+def _check_image(frame, t, where, name):
+    """A planar [3][H][W] float32 image of the frame's size."""
+    _check_f32(t, 3 * int(frame.width) * int(frame.height), where, name)
+
+
+def _check_param_grads(scene, d_ms, d_op, d_col, where, names=("d_means_sigma", "d_opacity", "d_color")):
+    """Per-Gaussian outputs shaped like the scene's arrays: [n][4], [n], [n][C]."""
+    n, c = scene.n, int(scene.color.shape[1])
+    for t, need, name in ((d_ms, 4 * n, names[0]), (d_op, n, names[1]), (d_col, c * n, names[2])):
+        _check_f32(t, need, where, name)
+
+
 class Scene:
     """Device scene: means_sigma [N,4], opacity [N], color [N,C] (FP32, CUDA)."""
 
@@ -377,24 +398,31 @@ def export_keys(frame: Frame, stream=None):
 
 
 def render_fwd(frame: Frame, o: IgsOpts, img, stream=None):
+    _check_image(frame, img, "render_fwd", "img")
     _check(load().igs_render_fwd(C.byref(frame.struct), C.byref(o), _ptr(img), _stream(stream)), "igs_render_fwd")
 
 
 def render_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, dL_dimg, g2d, d_means_sigma, d_opacity,
                d_color, stream=None):
     _check_color_width(scene, o.sh_degree, "render_bwd")
+    _check_image(frame, dL_dimg, "render_bwd", "dL_dimg")
+    _check_g2d(frame, g2d, "render_bwd")
+    _check_param_grads(scene, d_means_sigma, d_opacity, d_color, "render_bwd")
     _check(load().igs_render_bwd(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                  _ptr(dL_dimg), _ptr(g2d), _ptr(d_means_sigma), _ptr(d_opacity), _ptr(d_color),
                                  _stream(stream)), "igs_render_bwd")
 
 
 def blend_bwd(frame: Frame, o: IgsOpts, dL_dimg, g2d, stream=None):
+    _check_image(frame, dL_dimg, "blend_bwd", "dL_dimg")
+    _check_g2d(frame, g2d, "blend_bwd")
     _check(load().igs_blend_bwd(C.byref(frame.struct), C.byref(o), _ptr(dL_dimg), _ptr(g2d), _stream(stream)),
            "igs_blend_bwd")
 
 
 def render_fwd_clear(frame: Frame, o: IgsOpts, img, g2d, stream=None):
     """render_fwd that also zeroes g2d ([n][8] float32) for blend_bwd_acc."""
+    _check_image(frame, img, "render_fwd_clear", "img")
     _check_g2d(frame, g2d, "render_fwd_clear")
     _check(load().igs_render_fwd_clear(C.byref(frame.struct), C.byref(o), _ptr(img), _ptr(g2d), _stream(stream)),
            "igs_render_fwd_clear")
@@ -402,6 +430,7 @@ def render_fwd_clear(frame: Frame, o: IgsOpts, img, g2d, stream=None):
 
 def blend_bwd_acc(frame: Frame, o: IgsOpts, dL_dimg, g2d, stream=None):
     """blend_bwd into a g2d that render_fwd_clear zeroed (no clearing here)."""
+    _check_image(frame, dL_dimg, "blend_bwd_acc", "dL_dimg")
     _check_g2d(frame, g2d, "blend_bwd_acc")
     _check(load().igs_blend_bwd_acc(C.byref(frame.struct), C.byref(o), _ptr(dL_dimg), _ptr(g2d), _stream(stream)),
            "igs_blend_bwd_acc")
@@ -410,6 +439,8 @@ def blend_bwd_acc(frame: Frame, o: IgsOpts, dL_dimg, g2d, stream=None):
 def project_bwd(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d, d_means_sigma, d_opacity, d_color,
                 stream=None):
     _check_color_width(scene, o.sh_degree, "project_bwd")
+    _check_g2d(frame, g2d, "project_bwd")
+    _check_param_grads(scene, d_means_sigma, d_opacity, d_color, "project_bwd")
     _check(load().igs_project_bwd(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                   _ptr(g2d), _ptr(d_means_sigma), _ptr(d_opacity), _ptr(d_color),
                                   _stream(stream)), "igs_project_bwd")
@@ -420,6 +451,9 @@ def project_bwd_adam(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame, g2d
     """Projection backward fused with Adam: scene parameters and the moments
     m = (m_ms, m_op, m_col), v = (v_ms, v_op, v_col) are updated in place."""
     _check_color_width(scene, o.sh_degree, "project_bwd_adam")
+    _check_g2d(frame, g2d, "project_bwd_adam")
+    _check_param_grads(scene, *m, "project_bwd_adam", ("m[0]", "m[1]", "m[2]"))
+    _check_param_grads(scene, *v, "project_bwd_adam", ("v[0]", "v[1]", "v[2]"))
     _check(load().igs_project_bwd_adam(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                        _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
                                        int(step), _stream(stream)), "igs_project_bwd_adam")
@@ -431,6 +465,9 @@ def project_bwd_adam_dev(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame,
     tensor (zero before the first step) that the call advances, so the step can
     be captured in a CUDA graph and replayed."""
     _check_color_width(scene, o.sh_degree, "project_bwd_adam_dev")
+    _check_g2d(frame, g2d, "project_bwd_adam_dev")
+    _check_param_grads(scene, *m, "project_bwd_adam_dev", ("m[0]", "m[1]", "m[2]"))
+    _check_param_grads(scene, *v, "project_bwd_adam_dev", ("v[0]", "v[1]", "v[2]"))
     _check(load().igs_project_bwd_adam_dev(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                            _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2, eps,
                                            _ptr(state), _stream(stream)), "igs_project_bwd_adam_dev")
@@ -441,6 +478,9 @@ def project_bwd_adam_next(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame
     """project_bwd_adam_dev, then the projection of next_cam into next_frame from
     the updated parameters in the same pass (what project() would write)."""
     _check_color_width(scene, o.sh_degree, "project_bwd_adam_next")
+    _check_g2d(frame, g2d, "project_bwd_adam_next")
+    _check_param_grads(scene, *m, "project_bwd_adam_next", ("m[0]", "m[1]", "m[2]"))
+    _check_param_grads(scene, *v, "project_bwd_adam_next", ("v[0]", "v[1]", "v[2]"))
     _check(load().igs_project_bwd_adam_next(C.byref(scene.struct), C.byref(cam), C.byref(o), C.byref(frame.struct),
                                             _ptr(g2d), *[_ptr(t) for t in m], *[_ptr(t) for t in v], lr, b1, b2,
                                             eps, _ptr(state), C.byref(next_cam), C.byref(next_frame.struct),
@@ -448,6 +488,9 @@ def project_bwd_adam_next(scene: Scene, cam: IgsCamera, o: IgsOpts, frame: Frame
 
 
 def l1_loss(img, target, loss, dL_dimg, stream=None):
+    for t, name in ((img, "img"), (target, "target"), (dL_dimg, "dL_dimg")):
+        _check_f32(t, int(img.numel()), "l1_loss", name)
+    _check_f32(loss, 1, "l1_loss", "loss")
     _check(load().igs_l1_loss(_ptr(img), _ptr(target), int(img.numel()), _ptr(loss), _ptr(dL_dimg),
                               _stream(stream)), "igs_l1_loss")
 
@@ -530,6 +573,12 @@ def grad_accum(g2d, count, accum, vis, stream=None):
     """Densify statistic of one step: for Gaussians with count > 0 (the frame's
     per-Gaussian tile count), accum += |(du, dv)| from g2d [n][8] and vis += 1."""
     n = int(accum.shape[0])
+    _check_f32(g2d, 8 * n, "grad_accum", "g2d")
+    _check_f32(accum, n, "grad_accum", "accum")
+    for t, name in ((count, "count"), (vis, "vis")):
+        if (not isinstance(t, torch.Tensor) or t.element_size() != 4 or t.dtype.is_floating_point
+                or not t.is_contiguous() or t.numel() < n):
+            raise ValueError(f"grad_accum: {name} must be a contiguous 32-bit integer tensor of at least {n} elements")
     _check(load().igs_grad_accum(_ptr(g2d), _ptr(count), n, _ptr(accum), _ptr(vis), _stream(stream)),
            "igs_grad_accum")
 

@@ -148,3 +148,50 @@ def test_sort_depth_noalloc_binding_refuses_bad_buffers(bad):
     with pytest.raises(ValueError):
         igs.sort_depth_noalloc(key, order)
     assert igs.launch_count() == before
+
+
+def _fake_frame_scene(n=10, w=8, h=6, c=3):
+    """Host stand-ins carrying what the binding's size checks read (no device memory)."""
+    import types
+
+    import torch
+    frame = types.SimpleNamespace(n=n, width=w, height=h)
+    scene = types.SimpleNamespace(n=n, color=torch.zeros(n, c))
+    return frame, scene
+
+
+@pytest.mark.parametrize("bad", ["short_img", "f64_img", "short_g2d", "strided_g2d", "short_d_color"])
+def test_gradient_and_image_bindings_refuse_bad_buffers(bad):
+    """The kernels write whole images ([3][H][W]), 8 floats per Gaussian of g2d
+    and per-Gaussian rows of the gradients: a buffer that is shorter, strided or
+    not float32 is refused before anything launches."""
+    import torch
+    n, w, h = 10, 8, 6
+    frame, scene = _fake_frame_scene(n, w, h)
+    o = igs.opts(tile=16)
+    img = torch.zeros(3, h, w)
+    g2d = torch.zeros(n, 8)
+    d_ms, d_op, d_col = torch.zeros(n, 4), torch.zeros(n), torch.zeros(n, 3)
+    if bad == "short_img":
+        img = img.view(-1)[:-1]
+    elif bad == "f64_img":
+        img = img.double()
+    elif bad == "short_g2d":
+        g2d = g2d[:-1]
+    elif bad == "strided_g2d":
+        g2d = torch.zeros(n, 16)[:, ::2]
+    else:
+        d_col = d_col[:-1]
+    before = igs.launch_count()
+    calls = [lambda: igs.render_bwd(scene, None, o, frame, img, g2d, d_ms, d_op, d_col)]
+    if bad != "short_d_color":
+        calls += [lambda: igs.render_fwd_clear(frame, o, img, g2d), lambda: igs.blend_bwd(frame, o, img, g2d),
+                  lambda: igs.blend_bwd_acc(frame, o, img, g2d)]
+    if bad in ("short_img", "f64_img"):
+        calls.append(lambda: igs.render_fwd(frame, o, img))
+    else:
+        calls.append(lambda: igs.project_bwd(scene, None, o, frame, g2d, d_ms, d_op, d_col))
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
+    assert igs.launch_count() == before
