@@ -1,8 +1,10 @@
 // Multi-view batch rendering: V views of one scene, each with its own pose and
 // image size, rendered by one chain of launches with no host synchronisation
 // (so the chain can be captured in a CUDA graph and replayed with new poses):
-//   project all (view, Gaussian) pairs     one launch, grid (blocks, V); the
-//                                          poses come from the device view table
+//   project all (view, Gaussian) pairs     one launch, a thread per Gaussian that
+//                                          reads it once and projects it for every
+//                                          view; the poses come from the device
+//                                          view table
 //   bin and sort each view                 each view's frame as igs_bin_sort does it,
 //                                          the views spread over up to 16 streams
 //                                          that fork from the caller's stream and
@@ -37,18 +39,45 @@ struct Fanout {
     cudaEvent_t join[kFanout] = {};
 };
 
+// Every view of the batch for one Gaussian per thread: the Gaussian's mean,
+// scale, opacity and colour row are read once and projected for each view in
+// turn (what project_one writes into that view's frame), the view table staged
+// kViewChunk entries at a time in shared memory. The scene is read once per
+// batch, not once per view; the per-view writes stay coalesced across a warp.
+constexpr int kViewChunk = 16;
 template <int DEG>
-__global__ void __launch_bounds__(256) k_project_batch(const float4* __restrict__ ms, const float* __restrict__ op,
+__global__ void __launch_bounds__(256) k_project_views(const float4* __restrict__ ms, const float* __restrict__ op,
                                                        const float* __restrict__ col, int64_t n,
-                                                       const BatchView* __restrict__ views) {
-    __shared__ BatchView s_v;
-    const int v = blockIdx.y;
-    if (threadIdx.x == 0) s_v = views[v];
-    __syncthreads();
+                                                       const BatchView* __restrict__ views, int V) {
+    constexpr int C = DEG < 0 ? 3 : 3 * (DEG + 1) * (DEG + 1);
+    static_assert(sizeof(BatchView) % 4 == 0, "the view table is staged as 32-bit words");
+    __shared__ BatchView s_v[kViewChunk];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    project_one<DEG>(ms, op, col, i, s_v.vp, s_v.rec + 2 * i, s_v.rect + i, s_v.disc + i, s_v.count + i,
-                     s_v.depth_key + i);
+    const bool on = i < n;
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    float o = 0.f;
+    float c[48];
+    if (on) {
+        m = __ldg(ms + i);
+        o = __ldg(op + i);
+        load_color<DEG>(col, i, c);
+    }
+    constexpr int kWords = (int)(sizeof(BatchView) / 4);
+    for (int v0 = 0; v0 < V; v0 += kViewChunk) {
+        const int nv = min(kViewChunk, V - v0);
+        __syncthreads();  // the previous chunk's views are no longer read
+        for (int k = threadIdx.x; k < nv * kWords; k += blockDim.x)
+            reinterpret_cast<uint32_t*>(s_v)[k] = reinterpret_cast<const uint32_t*>(views + v0)[k];
+        __syncthreads();
+        if (!on) continue;
+        for (int k = 0; k < nv; ++k) {
+            const BatchView& bv = s_v[k];
+            project_one_vals<DEG>(m, o, [&](float cc[48]) {
+#pragma unroll
+                for (int q = 0; q < C; ++q) cc[q] = c[q];
+            }, bv.vp, bv.rec + 2 * i, bv.rect + i, bv.disc + i, bv.count + i, bv.depth_key + i);
+        }
+    }
 }
 
 // One block: the batch's status words from the views' (entries summed, the
@@ -237,9 +266,9 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_frame* frames, con
     // 1. projection of every (view, Gaussian) into the views' frames (an empty
     //    scene still bins to empty tiles and blends the background)
     if (n > 0) {
-        const dim3 grid((unsigned)ceil_div(n, 256), (unsigned)V);
+        const unsigned grid = (unsigned)ceil_div(n, 256);
         auto ms = reinterpret_cast<const float4*>(sc.means_sigma);
-#define IGS_PB(D) k_project_batch<D><<<grid, 256, 0, st>>>(ms, sc.opacity, sc.color, n, table)
+#define IGS_PB(D) k_project_views<D><<<grid, 256, 0, st>>>(ms, sc.opacity, sc.color, n, table, V)
         switch (sh_degree) {
             case -1: IGS_PB(-1); break;
             case 0: IGS_PB(0); break;
