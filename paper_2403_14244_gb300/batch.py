@@ -5,8 +5,9 @@ igs_render_batch: views are packed into groups whose (view, Gaussian, tile)
 entries fit one batch workspace (the entry budget), each view gets a frame
 sized from a calibrating render of it, each group is one chain of launches
 (one projection launch, the views' binnings on concurrent streams, one blend
-launch), and the chain of every group is captured once in a CUDA graph and
-replayed for each new set of poses.
+launch), the groups' chains run on streams of their own (so one group's blend
+overlaps another's binnings), and all of it is captured once in a CUDA graph
+and replayed for each new set of poses.
 
 ``autotune`` times every supported (tile size, blend staging depth) pair on the
 caller's workload and caches the fastest, keyed by the workload's shape.
@@ -23,7 +24,7 @@ import torch
 from . import igs
 from .render import Renderer
 
-DEFAULT_ENTRY_BUDGET = 400_000_000
+DEFAULT_ENTRY_BUDGET = 300_000_000
 BLEND_BATCHES = {8: (32, 64), 16: (64, 128, 256), 32: (64, 256, 512, 1024)}  # 64 at 16 and 32: sub-tile blend
 
 
@@ -74,9 +75,19 @@ class BatchRenderer:
         self.stream = torch.cuda.Stream(device=device)
 
     def render(self, stream=None):
-        """Render every group (no host synchronisation)."""
-        for b in self.batches:
-            b.render(self.scene, stream)
+        """Render every group (no host synchronisation); groups run concurrently."""
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if len(self.batches) == 1:
+            self.batches[0].render(self.scene, main)
+            return
+        if not hasattr(self, "_gstreams"):
+            self._gstreams = [torch.cuda.Stream(device=self.device) for _ in self.batches]
+        for s in self._gstreams:
+            s.wait_stream(main)
+        for b, s in zip(self.batches, self._gstreams):
+            b.render(self.scene, s)
+        for s in self._gstreams:
+            main.wait_stream(s)
 
     def set_poses(self, cams, stream=None):
         """New poses (same image sizes, same order); effective for the next render or replay."""
