@@ -244,14 +244,32 @@ class TrainStep:
         frame.proj_gen = getattr(frame, "proj_gen", 0) + 1
         self._pending = (bytes(c), frame, frame.proj_gen)
 
-    def step(self, cam, target, check=False, stream=None, marks=None, next_cam=None):
+    def _side(self):
+        """The stream the step's host copies run on (created once)."""
+        if getattr(self, "_side_stream", None) is None:
+            self._side_stream = torch.cuda.Stream(device=self.flat.device)
+        return self._side_stream
+
+    def step(self, cam, target, check=False, stream=None, marks=None, next_cam=None, target_host=None,
+             loss_host=None):
         """One training step on `stream`. `marks`, if given, is called with a
         stage name after each stage is enqueued (the benchmark records CUDA
         events there). With next_cam (fused path), the step's last pass also
         projects the updated scene for next_cam, and the next step on that
         camera starts at the binning (the projection arrays of the returned
-        frame then hold next_cam's view when it has the same size)."""
+        frame then hold next_cam's view when it has the same size).
+        target_host (pinned host tensor): copied into `target` by the step itself,
+        on a side stream that overlaps the binning and the forward and joins
+        before the loss; loss_host (pinned, one float): the loss is copied there
+        on the side stream while the backward runs, joined at the step's end.
+        Both become part of a captured graph."""
         c = cam if isinstance(cam, igs.IgsCamera) else igs.camera(cam)
+        cur = stream if stream is not None else torch.cuda.current_stream(self.flat.device)
+        side = self._side() if (target_host is not None or loss_host is not None) else None
+        if target_host is not None:
+            side.wait_stream(cur)  # every earlier reader of `target` is done
+            with torch.cuda.stream(side):
+                target.copy_(target_host, non_blocking=True)
         key = (c.width, c.height)
         if key not in self._img:
             self._img[key] = torch.empty((3, c.height, c.width), dtype=torch.float32, device=self.flat.device)
@@ -271,6 +289,8 @@ class TrainStep:
             mark("bin_sort")
             igs.render_fwd_clear(frame, r.opts, img, self.g2d, stream)  # clears g2d for the adjoint below
         mark("blend_fwd")
+        if target_host is not None:
+            cur.wait_stream(side)  # the target has arrived
         if self.ssim_lambda > 0.0:
             if key not in self._work:
                 self._work[key] = torch.empty(igs.ssim_work_bytes(3, c.height, c.width) // 4, dtype=torch.float32,
@@ -280,6 +300,10 @@ class TrainStep:
         else:
             igs.l1_loss(img, target, self.loss, dimg, stream)
             mark("l1")
+        if loss_host is not None:
+            side.wait_stream(cur)  # the loss is final
+            with torch.cuda.stream(side):
+                loss_host.copy_(self.loss, non_blocking=True)
         if check:
             igs.blend_bwd(frame, r.opts, dimg, self.g2d, stream)
         else:
@@ -305,9 +329,11 @@ class TrainStep:
             mark("project_bwd")
             igs.adam(self.flat, self.grad, self.m, self.v, self.t, lr=self.lr, stream=stream)
             mark("adam")
+        if loss_host is not None:
+            cur.wait_stream(side)  # the loss copy joins the step
         return frame
 
-    def capture(self, cams, targets, chain=False):
+    def capture(self, cams, targets, chain=False, targets_host=None, losses_host=None):
         """Record one training step per (camera, target) into its own CUDA graph
         (fused path: the Adam step count lives on the device, so replays keep
         counting). Each view must have run once with check=True before (its entry
@@ -315,7 +341,10 @@ class TrainStep:
         `targets` tensors as they are at replay time. With chain=True, graph k
         ends by projecting view k + 1 (cyclically) and starts at its binning:
         replays in the order 0, 1, 2, ... skip every projection pass; replay(k)
-        after anything else first projects view k on the current stream."""
+        after anything else first projects view k on the current stream. With
+        targets_host / losses_host (pinned host tensors, one per view), each
+        graph also copies its target in from the host and its loss out to the
+        host (step's target_host / loss_host)."""
         if not self.fused:
             raise RuntimeError("graph capture needs the fused projection backward + Adam")
         t0 = self.t
@@ -333,7 +362,9 @@ class TrainStep:
                     self._mark_projected(c, frame)
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=s):
-                    self.step(c, tgt, stream=s, next_cam=cams[(k + 1) % V] if chain else None)
+                    self.step(c, tgt, stream=s, next_cam=cams[(k + 1) % V] if chain else None,
+                              target_host=targets_host[k] if targets_host is not None else None,
+                              loss_host=losses_host[k] if losses_host is not None else None)
                 graphs.append(g)
                 frames.append(frame)
                 nexts.append((k + 1) % V if chain else None)

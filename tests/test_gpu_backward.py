@@ -381,3 +381,45 @@ def test_forward_clear_binding_refuses_small_g2d():
         igs.render_fwd_clear(f, r.opts, out, torch.zeros((sc.n - 1, 8), device="cuda"))
     with pytest.raises(ValueError):
         igs.blend_bwd_acc(f, r.opts, out, torch.zeros((sc.n, 8), device="cuda", dtype=torch.float64))
+
+
+def test_graphs_with_host_copies_match_device_targets():
+    """Steps whose graphs copy the target in from pinned host memory and the loss
+    out to it (TrainStep.capture with targets_host / losses_host) follow the
+    trajectory of graphs that read targets already on the device, and each
+    view's host loss is that step's loss. The device target buffers start as
+    garbage, so a step that read them before its copy landed would diverge."""
+    sc, cam = random_small(2000, 51, w=128, h=96, sh_degree=3, log_params=True, spread=0.8)
+    cams = [igs.camera(dataclasses.replace(cam, t=(np.asarray(cam.t, np.float32) + np.float32(0.04 * k))
+                                           .astype(np.float32))) for k in range(3)]
+    host = [torch.from_numpy(scenes.target_image(cam.width, cam.height, 40 + k)).pin_memory() for k in range(3)]
+    order = [0, 1, 2, 0, 1, 2, 0]
+    states, losses = [], []
+    for mode in ("device", "host"):
+        ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                       torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-2)
+        targets = [t.cuda() for t in host]
+        for k in range(3):
+            ts.step(cams[k], targets[k], check=True)
+        if mode == "device":
+            ts.capture(cams, targets, chain=True)
+            got = []
+            for k in order:
+                ts.replay(k)
+                got.append(ts.loss.clone())
+        else:
+            lh = [torch.full((1,), float("nan")).pin_memory() for _ in range(3)]
+            ts.capture(cams, targets, chain=True, targets_host=host, losses_host=lh)
+            for t in targets:
+                t.fill_(-5.0)                       # the graphs must copy the real targets in
+            got = []
+            for k in order:
+                ts.replay(k)
+                torch.cuda.synchronize()
+                assert float(lh[k]) == float(ts.loss)
+                got.append(lh[k].clone())
+        torch.cuda.synchronize()
+        states.append(torch.cat([ts.flat, ts.m, ts.v]).cpu().numpy())
+        losses.append([float(x) for x in got])
+    np.testing.assert_allclose(states[1], states[0], rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(losses[1], losses[0], rtol=1e-5)
