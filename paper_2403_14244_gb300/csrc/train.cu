@@ -8,6 +8,13 @@ namespace igs {
 namespace {
 
 // loss += sum |img - target| / count (loss zeroed beforehand); grad = sign / count.
+// VEC: 16-byte aligned arrays and count a multiple of 4, read and written as float4.
+__device__ __forceinline__ float l1_term(float a, float b, float inv_count, float& acc) {
+    const float d = a - b;
+    acc += fabsf(d);
+    return d > 0.f ? inv_count : (d < 0.f ? -inv_count : 0.f);
+}
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const float* __restrict__ target,
                                             int64_t count, float inv_count, float* __restrict__ loss,
                                             float* __restrict__ grad) {
@@ -15,10 +22,22 @@ __global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const
     __shared__ float s_w[8];
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-        const float d = img[i] - target[i];
-        acc += fabsf(d);
-        grad[i] = d > 0.f ? inv_count : (d < 0.f ? -inv_count : 0.f);
+    if constexpr (VEC) {
+        const float4* a4 = reinterpret_cast<const float4*>(img);
+        const float4* b4 = reinterpret_cast<const float4*>(target);
+        float4* g4 = reinterpret_cast<float4*>(grad);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += stride) {
+            const float4 a = a4[i], b = b4[i];
+            float4 g;
+            g.x = l1_term(a.x, b.x, inv_count, acc);
+            g.y = l1_term(a.y, b.y, inv_count, acc);
+            g.z = l1_term(a.z, b.z, inv_count, acc);
+            g.w = l1_term(a.w, b.w, inv_count, acc);
+            g4[i] = g;
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+            grad[i] = l1_term(img[i], target[i], inv_count, acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -97,8 +116,13 @@ cudaError_t launch_l1(const float* img, const float* target, int64_t count, floa
                       cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), st);
     if (e != cudaSuccess || count == 0) return e;
-    const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), 152 * 8);
-    k_l1<<<blocks, 256, 0, st>>>(img, target, count, 1.f / (float)count, loss, grad);
+    const bool vec = count % 4 == 0 && ((reinterpret_cast<uintptr_t>(img) | reinterpret_cast<uintptr_t>(target) |
+                                         reinterpret_cast<uintptr_t>(grad)) & 15) == 0;
+    const int blocks = (int)std::min<int64_t>(ceil_div(vec ? count / 4 : count, 256), 152 * 8);
+    if (vec)
+        k_l1<true><<<blocks, 256, 0, st>>>(img, target, count, 1.f / (float)count, loss, grad);
+    else
+        k_l1<false><<<blocks, 256, 0, st>>>(img, target, count, 1.f / (float)count, loss, grad);
     count_launches();
     return cudaGetLastError();
 }

@@ -78,10 +78,11 @@ def test_backward_clustered_1080p_full():
         _gpu.grad_close(g, w, name + "[subset]", rel_norm=1e-3, elem_rel=1e-3, elem_abs_frac=1e-3)
 
 
-def test_l1_loss_matches_oracle():
+@pytest.mark.parametrize("shape", [(3, 70, 90), (3, 7, 5)])   # float4 path; a count not a multiple of 4
+def test_l1_loss_matches_oracle(shape):
     rng = np.random.default_rng(5)
-    img = rng.uniform(size=(3, 70, 90)).astype(np.float32)
-    tg = rng.uniform(size=(3, 70, 90)).astype(np.float32)
+    img = rng.uniform(size=shape).astype(np.float32)
+    tg = rng.uniform(size=shape).astype(np.float32)
     tg[0, :5, :5] = img[0, :5, :5]
     ti, tt = torch.from_numpy(img).cuda(), torch.from_numpy(tg).cuda()
     loss = torch.zeros(1, device="cuda")
