@@ -542,25 +542,14 @@ struct Placer {
         }
     }
 };
-// Tiles of row y that Gaussian g touches (row_span within its rectangle); none
-// (returned as (1, 0)) for an id of ~0 (past the chunk) or an empty span.
+// What the level-1 placement needs to give each row item the tiles its Gaussian
+// touches in that row: the rectangles, or with footprint 1 the discs (disc_span).
 struct DiscRef {
     const uint2* rect;
     const float4* disc;
     int tile;
     float inv_tile;
     int footprint;
-    __device__ __forceinline__ int2 span(uint32_t g, int y) const {
-        if (g == 0xFFFFFFFFu) return make_int2(1, 0);
-        int2 sp;
-        if (footprint == 0) {
-            const uint2 r = rect[g];
-            sp = make_int2((int)(r.x & 0xFFFF), (int)(r.y & 0xFFFF));
-        } else {
-            sp = disc_span(disc[g], tile, inv_tile, y);
-        }
-        return sp.y < sp.x ? make_int2(1, 0) : sp;  // an empty span as (1, 0): lo > hi, both >= 0
-    }
 };
 
 using Placer1 = Placer<u64, kStage1>;      // level 1: (column span << 32 | Gaussian id) items
