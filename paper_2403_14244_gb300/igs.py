@@ -678,6 +678,25 @@ def frame_status(frame: Frame, stream=None):
     return st, list(info)
 
 
+def frame_stats(frame: Frame, stream=None):
+    """Counters of the frame's last binning and forward, read from its own
+    buffers (synchronises the stream): Gaussians kept (visible), entries
+    (Gaussian, tile) M, their mean and largest count per tile, the share of
+    empty tiles, and the mean and largest number of list positions a pixel's
+    walk reached (n_contrib: the last blended entry + 1)."""
+    st, info = frame_status(frame, stream)
+    if st != OK:
+        raise IgsError(st, "frame_stats: the frame's last binning did not complete")
+    r = frame.ranges().to(torch.int64)
+    per_tile = (r[:, 1] - r[:, 0]).clamp(min=0)
+    nc = frame.n_contrib().to(torch.int64)
+    tiles = max(1, int(per_tile.numel()))
+    return {"kept": int(info[1]), "entries": int(info[0]),
+            "entries_per_tile_mean": float(per_tile.sum()) / tiles, "entries_per_tile_max": int(per_tile.max()),
+            "empty_tiles": float((per_tile == 0).sum()) / tiles,
+            "contrib_per_pixel_mean": float(nc.float().mean()), "contrib_per_pixel_max": int(nc.max())}
+
+
 def frame_walk_segments(frame: Frame, stream=None):
     """Pool slots the frame's last forward blend took for walk segments (-1: the
     frame has none); synchronises the stream."""

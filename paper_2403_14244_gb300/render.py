@@ -229,6 +229,47 @@ class TrainStep:
         self._pending = None     # (camera bytes, frame, its projection generation): a projection already made
         self._graph_next = None  # per captured graph: the view whose projection it leaves behind (chained capture)
 
+    def state_dict(self):
+        """The training state as host tensors, for a checkpoint: the parameters
+        (means_sigma with log sigma, logit opacity, colour), the Adam moments,
+        the step count (host and device copies), the densify statistic when it
+        is tracked, and the settings a resumed run needs. Captured graphs are not
+        part of it (capture again after resuming)."""
+        host = lambda ts: [t.detach().cpu().clone() for t in ts]  # noqa: E731
+        ms, op, col = host(self._views(self.flat))
+        d = {"means_sigma": ms, "opacity": op, "color": col, "m": host(self.m_views), "v": host(self.v_views),
+             "t": int(self.t), "adam_state": self.adam_state.cpu().clone(), "sh_degree": int(self.sh_degree),
+             "tile": int(self.tile), "lr": float(self.lr), "fused": bool(self.fused),
+             "footprint": int(self.footprint), "ssim_lambda": float(self.ssim_lambda)}
+        if self.accum is not None:
+            d["accum"], d["vis"] = self.accum.cpu().clone(), self.vis.cpu().clone()
+        return d
+
+    @classmethod
+    def from_state_dict(cls, d, device="cuda"):
+        """A TrainStep that continues from a state_dict(): the next step is the
+        one that followed the checkpoint. Entry capacities are not stored, so the
+        first step of each view runs with check=True."""
+        ts = cls(d["means_sigma"].to(device), d["opacity"].to(device), d["color"].to(device), d["sh_degree"],
+                 tile=d["tile"], lr=d["lr"], device=device, fused=d["fused"], footprint=d["footprint"],
+                 ssim_lambda=d["ssim_lambda"])
+        for dst, src in zip(ts.m_views + ts.v_views, list(d["m"]) + list(d["v"])):
+            dst.copy_(src)
+        ts.t = int(d["t"])
+        ts.adam_state.copy_(d["adam_state"])
+        if "accum" in d:
+            ts.accum, ts.vis = d["accum"].to(device), d["vis"].to(device)
+        return ts
+
+    def save(self, path):
+        """Write state_dict() to `path` (torch.save)."""
+        torch.save(self.state_dict(), path)
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        """from_state_dict of a file written by save()."""
+        return cls.from_state_dict(torch.load(path, map_location="cpu"), device)
+
     def _views(self, flat):
         n, C = self.n, self.C
         return (flat[:4 * n].view(n, 4), flat[self.o_op:self.o_op + n], flat[self.o_col:self.o_col + C * n].view(n, C))

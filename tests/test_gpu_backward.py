@@ -424,3 +424,35 @@ def test_graphs_with_host_copies_match_device_targets():
         losses.append([float(x) for x in got])
     np.testing.assert_allclose(states[1], states[0], rtol=1e-4, atol=1e-6)
     np.testing.assert_allclose(losses[1], losses[0], rtol=1e-5)
+
+
+def test_checkpoint_resume_matches_uninterrupted(tmp_path):
+    """Training state saved after some steps (parameters, Adam moments, step
+    count, densify statistic) and loaded into a new TrainStep continues as the
+    uninterrupted run does: same parameters and moments after five more steps,
+    up to the backward's atomic summation order, and the same step count."""
+    sc, cam = random_small(2000, 52, w=128, h=96, sh_degree=3, log_params=True, spread=0.8)
+    cams = [igs.camera(dataclasses.replace(cam, t=(np.asarray(cam.t, np.float32) + np.float32(0.04 * k))
+                                           .astype(np.float32))) for k in range(3)]
+    targets = [torch.from_numpy(scenes.target_image(cam.width, cam.height, 60 + k)).cuda() for k in range(3)]
+    ts = TrainStep(torch.from_numpy(sc.means_sigma).cuda(), torch.from_numpy(sc.opacity).cuda(),
+                   torch.from_numpy(sc.color).cuda(), sh_degree=3, lr=1e-2)
+    ts.track_grad_norm()
+    for k in (0, 1, 2, 0):
+        ts.step(cams[k], targets[k], check=True)
+    path = tmp_path / "train_state.pt"
+    ts.save(path)
+    after = (1, 2, 0, 1, 2)
+    for k in after:
+        ts.step(cams[k], targets[k], check=True)
+    ts2 = TrainStep.load(path)
+    assert ts2.t == 4 and ts2.accum is not None
+    for k in after:
+        ts2.step(cams[k], targets[k], check=True)
+    torch.cuda.synchronize()
+    assert ts2.t == ts.t and torch.equal(ts2.adam_state[:1], ts.adam_state[:1])
+    a = torch.cat([ts.flat, ts.m, ts.v]).cpu().numpy()
+    b = torch.cat([ts2.flat, ts2.m, ts2.v]).cpu().numpy()
+    np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(ts2.accum.cpu().numpy(), ts.accum.cpu().numpy(), rtol=1e-4, atol=1e-9)
+    np.testing.assert_array_equal(ts2.vis.cpu().numpy(), ts.vis.cpu().numpy())

@@ -153,3 +153,22 @@ def test_alpha_threshold_decisions_exact(tile):
     _, _, d_col = r.run_backward(scene, cam, fr, dimg)
     g = d_col.abs().sum(1).cpu().numpy()
     np.testing.assert_array_equal((g > 0)[sel], (eps_a > 0)[sel])
+
+
+def test_frame_stats_match_the_oracle():
+    """Per-frame counters (kept Gaussians, entries, per-tile list lengths)
+    against the oracle's projection and keys; the reached list positions per
+    pixel bounded by the tile lists."""
+    sc, cam = scenes.workload_forward_4k()
+    r, f, scene, img = _gpu.run_forward(sc, cam, tile=16)
+    st = igs.frame_stats(f)
+    keys, vals, ranges = oracle.keys(oracle.project(sc.means_sigma, sc.opacity, cam, 16), cam, 16)
+    per_tile = ranges[:, 1].astype(np.int64) - ranges[:, 0].astype(np.int64)
+    assert st["entries"] == len(keys) and st["entries_per_tile_max"] == per_tile.max()
+    assert st["entries_per_tile_mean"] == pytest.approx(per_tile.mean())
+    assert st["empty_tiles"] == pytest.approx(float((per_tile == 0).mean()))
+    assert st["kept"] == int((oracle.project(sc.means_sigma, sc.opacity, cam, 16)["count"] > 0).sum())
+    # a pixel's walk reaches at most its tile's list
+    assert 0.0 < st["contrib_per_pixel_mean"] <= st["contrib_per_pixel_max"] <= per_tile.max()
+    nc = f.n_contrib().cpu().numpy().astype(np.int64)
+    assert st["contrib_per_pixel_mean"] == pytest.approx(nc.mean())
