@@ -20,6 +20,7 @@
 // concurrently fills the GPU where one view's chain cannot.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "blendtile.cuh"
 #include "projection.cuh"
@@ -285,7 +286,20 @@ cudaError_t launch_render_batch(const igs_batch& b, const igs_frame* frames, con
     const int K = std::min(fo->k, V);
     CK(cudaEventRecord(fo->fork, st));
     for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(fo->st[k], fo->fork, 0));
-    for (int v = 0; v < V; ++v) CK(launch_bin_sort(frames[v], footprint, fo->st[v % K]));
+    {  // longest first, each onto the stream with the least work so far: a view's binning takes
+       // about a fixed latency plus time in proportion to its entries (its capacity stands in)
+        constexpr int64_t kViewFloor = 8 << 20;  // the fixed part, in entries
+        std::vector<int> order(V);
+        for (int v = 0; v < V; ++v) order[v] = v;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int c) { return frames[a].capacity > frames[c].capacity; });
+        std::vector<int64_t> load(K, 0);
+        for (int v : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            CK(launch_bin_sort(frames[v], footprint, fo->st[k]));
+            load[k] += frames[v].capacity + kViewFloor;
+        }
+    }
     for (int k = 0; k < K; ++k) {
         CK(cudaEventRecord(fo->join[k], fo->st[k]));
         CK(cudaStreamWaitEvent(st, fo->join[k], 0));
