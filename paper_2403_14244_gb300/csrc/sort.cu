@@ -532,13 +532,15 @@ struct Placer {
         if (lane == 0) emask[qmax + 1] = 0u;  // ends past the last bucket of the batch
         __syncwarp();
     }
-    // staged chunk: every bucket's run to out[first[q] ...], consecutive lanes
+    // staged chunk: every bucket's run to out[first[q] ...]; lane l takes stage slots l, l + 32, ...,
+    // each written to its bucket's output run (a warp store covers 32 consecutive slots)
     __device__ __forceinline__ void flush(T* __restrict__ out, int lane) {
         if (!staged) return;
-        for (uint32_t q = 0; q < B; ++q) {
-            const uint32_t s0 = lstart[q], n = lstart[q + 1] - s0;
-            const uint32_t f = first[q];
-            for (uint32_t i = lane; i < n; i += 32) out[f + i] = stage[s0 + i];
+        const uint32_t total = lstart[B];
+        uint32_t q = 0;  // the bucket holding stage slot e: slots rise, so q only moves forward
+        for (uint32_t e = lane; e < total; e += 32) {
+            while (lstart[q + 1] <= e) ++q;
+            out[first[q] + (e - lstart[q])] = stage[e];
         }
     }
 };
