@@ -432,8 +432,8 @@ __device__ __forceinline__ Chunk l1_chunk(uint32_t c, uint32_t cmax, const uint3
 // each bucket's cursor then advances by the mask's size. Two marks per item
 // instead of one per (item, bucket), and no per-bucket pass diverges but the
 // slot writes. Items go to a shared-memory stage grouped by bucket and leave
-// as one run per bucket written by consecutive lanes (a chunk too large for
-// the stage writes its items directly). Items are of type T (the value an item
+// by stage slot (lane l takes slots l, l + 32, ..., each to its bucket's run
+// in the output; a chunk too large for the stage writes its items directly). Items are of type T (the value an item
 // takes in bucket q comes from a functor); the stage holds S of them. Shared
 // memory: words(B) 32-bit words, an even count (8-byte items stay aligned).
 template <typename T, uint32_t S>
