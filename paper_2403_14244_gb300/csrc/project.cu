@@ -184,9 +184,14 @@ __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restri
     float dx = 0.f, dy = 0.f, dz = 0.f;
     float4 e_mm = make_float4(0.f, 0.f, 0.f, 0.f), e_vv = e_mm;
     float e_mo = 0.f, e_vo = 0.f;
+    float4 ga = e_mm, gb = e_mm;
     if (active) {
         m = ms[i];
         raw_op = op[i];
+        // the screen-space gradient with the other loads, not after the count that decides
+        // whether it is used: one memory round trip on the warp's path instead of two
+        ga = __ldg(g2d + 2 * i);
+        gb = __ldg(g2d + 2 * i + 1);
         has_grad = count[i] != 0;
         if constexpr (ADAM) {  // independent of the gradient: in flight during the compute
             e_mm = st.m_ms[i];
@@ -198,7 +203,6 @@ __global__ void __launch_bounds__(kPbThreads, 10) k_project_bwd(float4* __restri
     if (has_grad) {
         float sg, o;
         activate(P.param_mode, m.w, raw_op, sg, o);
-        const float4 ga = __ldg(g2d + 2 * i), gb = __ldg(g2d + 2 * i + 1);
         const float xc = P.R[0] * m.x + P.R[1] * m.y + P.R[2] * m.z + P.t[0];
         const float yc = P.R[3] * m.x + P.R[4] * m.y + P.R[5] * m.z + P.t[1];
         const float zc = P.R[6] * m.x + P.R[7] * m.y + P.R[8] * m.z + P.t[2];
