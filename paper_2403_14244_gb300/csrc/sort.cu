@@ -60,7 +60,7 @@ constexpr uint32_t kChunkTarget = kStage * 4 / 5;
 constexpr uint32_t kStage1 = 768;          // staged 8-byte items per level-1 chunk
 constexpr uint32_t kChunkTarget1 = kStage1 * 4 / 5;
 constexpr int kWalkWarps = 4;              // warps per CTA of the walk kernels (one chunk each)
-constexpr int kWalkUnroll = 4;             // items per lane per round of the counting walks
+constexpr int kWalkUnroll = 8;             // items per lane per round of the counting walks
 
 // Depth-digit histograms of all n depth keys, the kept count, and for every kept
 // Gaussian, in each tile row, +1 at its first touched tile and -1 past its last
@@ -674,14 +674,15 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_rows_place(const uint32_t* 
     const uint32_t used = l1_chunk(0, cmax, info).used;
     for (uint32_t c = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); c < used; c += gridDim.x * kWalkWarps) {
         const Chunk ch = l1_chunk(c, cmax, info);
+        // the first batch's items load while the placer reads the chunk's bucket offsets
+        uint32_t g_next = ch.p0 + lane < ch.p1 ? order[ch.p0 + lane] : 0xFFFFFFFFu;
+        uint2 r_next = ch.p0 + lane < ch.p1 ? srect[ch.p0 + lane] : make_uint2(1u << 16, 0u);  // rows 1..0: none
         Placer1 rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer1::words(rows), rows);
         auto first = [&](uint32_t y) { return rowinfo[y] + H1[(size_t)y * cmax + c]; };
         rs.init(lane, first, [&](uint32_t y) {
             const uint32_t* h = H1 + (size_t)y * cmax;
             return (c + 1 < ch.used ? h[c + 1] : len[y]) - h[c];
         });
-        uint32_t g_next = ch.p0 + lane < ch.p1 ? order[ch.p0 + lane] : 0xFFFFFFFFu;
-        uint2 r_next = ch.p0 + lane < ch.p1 ? srect[ch.p0 + lane] : make_uint2(1u << 16, 0u);  // rows 1..0: none
         for (uint32_t b = ch.p0; b < ch.p1; b += 32) {
             const uint32_t g = g_next;
             const uint2 r = r_next;
@@ -821,13 +822,14 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_cols_place(const u64* __res
     for (uint32_t j = blockIdx.x * kWalkWarps + (threadIdx.x >> 5); j < total; j += gridDim.x * kWalkWarps) {
         const RowChunk rc = l2_chunk(j, rows, rowinfo, len);
         const bool last = j + 1 == (rc.y + 1 < rows ? rowinfo[rows + rc.y + 1] : rowinfo[3 * rows]);
+        // the first batch's items load while the placer reads the chunk's tile offsets
+        const u64 none = 0xFFFFFFFFull | (1ull << 32);  // past the chunk: (1, 0), no tiles
+        u64 it_next = rc.i0 + lane < rc.i1 ? R1[rc.i0 + lane] : none;
         Placer2 rs(s_walk + (size_t)(threadIdx.x >> 5) * Placer2::words(tiles_x), tiles_x);
         const uint32_t* h = H2 + (size_t)j * tiles_x;
         const uint2* rg = ranges + (size_t)rc.y * tiles_x;
         auto first = [&](uint32_t x) { return h[x]; };
         rs.init(lane, first, [&](uint32_t x) { return (last ? rg[x].y : h[x + tiles_x]) - h[x]; });
-        const u64 none = 0xFFFFFFFFull | (1ull << 32);  // past the chunk: (1, 0), no tiles
-        u64 it_next = rc.i0 + lane < rc.i1 ? R1[rc.i0 + lane] : none;
         for (uint32_t b = rc.i0; b < rc.i1; b += 32) {
             const u64 it = it_next;
             it_next = b + 32 + lane < rc.i1 ? R1[b + 32 + lane] : none;
