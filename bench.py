@@ -51,8 +51,13 @@ def parse():
                     help="tiles of a Gaussian: 0 its bounding rectangle, 1 the tiles its disc meets")
     ap.add_argument("--ssim", type=float, default=0.0,
                     help="lambda of the loss (1 - lambda) L1 + lambda (1 - SSIM) in the timed step (0: L1)")
-    ap.add_argument("--only", choices=("merge",), default=None,
-                    help="measure one side line alone on the training scene (no training step, no JSON contract)")
+    ap.add_argument("--only", choices=("merge", "batched"), default=None,
+                    help="measure one side line alone (no training step, no JSON contract): merge on the training "
+                         "scene, or batched: one batched render of --batch-views sphere views of a --batch-n RGB "
+                         "scene at 32-pixel tiles and 64-entry staging (the autotuned setting of the batched line), "
+                         "captured once and replayed --steps times after --warmup replays")
+    ap.add_argument("--batch-n", type=int, default=2_000_000, help="Gaussians of the --only batched scene")
+    ap.add_argument("--batch-views", type=int, default=32, help="views of the --only batched render")
     return ap.parse_args()
 
 
@@ -913,6 +918,34 @@ def run_fit2d_densify(dev, target, iters, min_cell, psnr, D=15.0, k0=256, capaci
             "densify_ms": dens_ms, "wall_s": round(wall, 3), "psnr_last_db": psnr(f)}
 
 
+def run_batched_fixed(dev, n, views, warm, reps):
+    """One batched render of `views` sphere poses of an n-Gaussian RGB scene at
+    tile 32 / staging 64, captured once and replayed: ms per render (for a
+    launch list or a counter capture of the batched path without the tuner)."""
+    import torch
+
+    from paper_2403_14244_gb300 import igs, scenes
+    from paper_2403_14244_gb300.batch import BatchRenderer
+
+    scene = igs.Scene.from_numpy(scenes.uniform_scene(n, 4), dev)
+    cams = [igs.camera(c) for c in scenes.sphere_cameras(views, 4)]
+    br = BatchRenderer(scene, cams, tile=32, blend_batch=64, device=dev)
+    br.capture()
+    for _ in range(warm):
+        br.replay()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        br.replay()
+    b.record()
+    torch.cuda.synchronize(dev)
+    br.check()
+    ms = a.elapsed_time(b) / max(reps, 1)
+    return {"n": n, "views": views, "tile": 32, "blend_batch": 64, "groups": [len(g) for g in br.groups],
+            "entries": int(sum(br.entries)), "replays": reps, "ms": round(ms, 3)}
+
+
 def run_batched(dev, reps=10):
     """32 views (sphere poses, mixed 360p..1440p) of a 2M-Gaussian RGB scene:
     autotuned batched graph replays vs a loop of one-view renders, frames/s."""
@@ -1175,6 +1208,12 @@ def main():
         torch.cuda.set_device(dev)
         _, _, _, ts, _, _, _ = build_workload(args.n, dev, args.footprint, args.tile)
         print(json.dumps({"merge_3M": run_merge3d(ts, torch.cuda.current_stream(dev), dev, load_peaks()[0])}))
+        return
+    if args.only == "batched":
+        import torch
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"batched": run_batched_fixed(dev, args.batch_n, args.batch_views, args.warmup, args.steps)}))
         return
     run_mine(args, world, rank, local)
 
