@@ -57,3 +57,21 @@ def test_reference_arm_other_ranks_exit_without_work(capsys):
         n, steps, warmup = 1000, 1, 1
     assert bench.run_reference(A(), 2, 1) is None              # rank 1: returns at once, prints nothing
     assert capsys.readouterr().out == ""
+
+
+def test_single_line_modes_parse(monkeypatch):
+    """`--only batched` defaults to the batched line's workload (2M Gaussians,
+    32 views) and takes its size from --batch-n / --batch-views; the default
+    run measures the training step (no single-line mode)."""
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    a = bench.parse()
+    assert a.only is None and a.n == 3_000_000 and a.steps >= 1 and a.warmup >= 3
+    monkeypatch.setattr("sys.argv", ["bench.py", "--only", "batched", "--steps", "3", "--warmup", "2"])
+    a = bench.parse()
+    assert (a.only, a.batch_n, a.batch_views, a.steps, a.warmup) == ("batched", 2_000_000, 32, 3, 2)
+    monkeypatch.setattr("sys.argv", ["bench.py", "--only", "batched", "--batch-n", "1000000", "--batch-views", "8"])
+    a = bench.parse()
+    assert (a.batch_n, a.batch_views) == (1_000_000, 8)
+    monkeypatch.setattr("sys.argv", ["bench.py", "--only", "nothing"])
+    with pytest.raises(SystemExit):
+        bench.parse()
