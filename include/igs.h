@@ -226,7 +226,9 @@ IGS_API igs_status igs_render_bwd(const igs_scene* scene, const igs_camera* cam,
  * igs_blend_bwd clears g2d ([n][8], device) and accumulates the screen-space
  * gradients (du, dv, dw2, do, dr, dg, db, 0) of every Gaussian over all pixels;
  * igs_project_bwd chains g2d to the stored parameters (same outputs and rules
- * as igs_render_bwd). */
+ * as igs_render_bwd). The projection backward reads every Gaussian's row of
+ * g2d, culled ones included (their values are not used), so g2d must hold all
+ * n rows; the same holds for the fused variants below. */
 IGS_API igs_status igs_blend_bwd(const igs_frame* frame, const igs_opts* opts, const float* dL_dimg, float* g2d,
                                  void* stream);
 IGS_API igs_status igs_project_bwd(const igs_scene* scene, const igs_camera* cam, const igs_opts* opts,
