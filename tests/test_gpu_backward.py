@@ -456,3 +456,39 @@ def test_checkpoint_resume_matches_uninterrupted(tmp_path):
     np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6)
     np.testing.assert_allclose(ts2.accum.cpu().numpy(), ts.accum.cpu().numpy(), rtol=1e-4, atol=1e-9)
     np.testing.assert_array_equal(ts2.vis.cpu().numpy(), ts.vis.cpu().numpy())
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_projection_backward_ignores_culled_rows_of_g2d(fused):
+    """The projection backward loads every Gaussian's row of the 2D gradient
+    together with its other values, but uses only the rows of Gaussians that
+    touch a tile: NaN in the rows of culled Gaussians changes no output bit,
+    in the plain projection backward and in the one fused with Adam (whose
+    culled Gaussians take a zero gradient)."""
+    sc, cam = random_small(600, 48, w=80, h=60, sh_degree=3, log_params=True, spread=1.6)
+    r, f, scene, _ = _gpu.run_forward(sc, cam, tile=16)
+    c = igs.camera(cam)
+    n = scene.n
+    culled = f.count() == 0
+    assert 0 < int(culled.sum()) < n
+    dimg = torch.from_numpy(np.random.default_rng(5).normal(size=(3, cam.height, cam.width)).astype(np.float32)).cuda()
+    g2d = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    igs.blend_bwd(f, r.opts, dimg, g2d)
+    g_nan = g2d.clone()
+    g_nan[culled] = float("nan")
+    outs = []
+    for g in (g2d, g_nan):
+        if not fused:
+            ts = (torch.empty_like(scene.means_sigma), torch.empty_like(scene.opacity), torch.empty_like(scene.color))
+            igs.project_bwd(scene, c, r.opts, f, g, *ts)
+        else:
+            s2 = igs.Scene(scene.means_sigma.clone(), scene.opacity.clone(), scene.color.clone())
+            m = [torch.zeros_like(t) for t in (s2.means_sigma, s2.opacity, s2.color)]
+            v = [torch.zeros_like(t) for t in (s2.means_sigma, s2.opacity, s2.color)]
+            igs.project_bwd_adam(s2, c, r.opts, f, g, m, v, step=1, lr=1e-2)
+            ts = (s2.means_sigma, s2.opacity, s2.color, *m, *v)
+        torch.cuda.synchronize()
+        outs.append([t.cpu().numpy() for t in ts])
+    for a, b in zip(*outs):
+        assert np.isfinite(a).all()
+        np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
